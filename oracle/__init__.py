@@ -1,0 +1,317 @@
+"""FP64 CPU oracle for the selective-segmentation multigrid method (test infrastructure only).
+
+The oracle is a plain C restatement of the paper's discretisation, grid transfers, smoothers,
+FAS V-cycle and outer driver (``oracle.c``), plus the Local Fourier Analysis tooling
+(``lfa.py``).  It is the independent checker of the CUDA library: it shares no code with it,
+and only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg may use it.
+
+``build()`` compiles ``oracle.c`` with gcc into ``oracle/_build/liboracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (plain C, -O2, no fast-math)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class Params(C.Structure):
+    """Mirror of ``or_params`` (oracle.c)."""
+
+    _fields_ = [
+        ("model", C.c_int), ("mu", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
+        ("theta", C.c_double), ("nu", C.c_double), ("eps", C.c_double), ("beta", C.c_double),
+        ("beta_edge", C.c_double), ("sigma_blur", C.c_double), ("sigma_d", C.c_double),
+        ("Sigma", C.c_double), ("inv_tau", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
+        ("levels", C.c_int), ("smoother", C.c_int), ("coarse_maxit", C.c_int),
+        ("coarse_tol", C.c_double),
+    ]
+
+
+def params(n=None, m=None, **kw) -> Params:
+    """Default parameters: the Spencer-Chen model with mu = 1, lambda1 = lambda2 = 10,
+    theta = 1, eps = 1, beta = 1e-6, sigma_blur = 1, beta_edge = 1, Sigma = 2, tau = 1,
+    V(2,2), Hybrid Smoother 2 (parallel ordering).  sigma_d defaults to 0.05 max(n, m)."""
+    sd = 0.05 * max(n or 128, m or n or 128)
+    d = dict(model=0, mu=1.0, lambda1=10.0, lambda2=10.0, theta=1.0, nu=1.0, eps=1.0, beta=1e-6,
+             beta_edge=1.0, sigma_blur=1.0, sigma_d=sd, Sigma=2.0, inv_tau=1.0, nu1=2,
+             nu2=2, levels=5, smoother=0, coarse_maxit=100, coarse_tol=1e-13)
+    if "tau" in kw:
+        t = kw.pop("tau")
+        kw["inv_tau"] = 0.0 if t is None or t == float("inf") else 1.0 / t
+    d.update(kw)
+    return Params(**d)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            D = C.POINTER(C.c_double)
+            I = C.POINTER(C.c_int)
+            P = C.POINTER(Params)
+            sig = {
+                "or_gauss_blur": ([D, C.c_int, C.c_int, C.c_double, D], None),
+                "or_edge_detector": ([D, C.c_int, C.c_int, C.c_double, D], None),
+                "or_distance": ([C.c_int, C.c_int, D, D, C.c_int, C.c_double, D], None),
+                "or_initial_phi": ([C.c_int, C.c_int, D, D, C.c_int, C.c_double, D, D], C.c_int),
+                "or_region_means": ([D, D, C.c_int, C.c_int, C.c_double, D, D], None),
+                "or_restrict": ([D, C.c_int, C.c_int, D], None),
+                "or_interpolate_add": ([D, C.c_int, C.c_int, D, C.c_int, C.c_int], None),
+                "or_apply_L": ([D, D, D, C.c_int, C.c_int, C.c_double, P, C.c_double, C.c_double, D], None),
+                "or_fitting": ([D, D, D, C.c_int, C.c_int, C.c_double, C.c_double, P, D], None),
+                "or_classify": ([C.c_double] * 4 + [C.c_int] * 4 + [C.c_double], C.c_int),
+                "or_coarse_solve": ([D, D, D, D, C.c_int, C.c_int, C.c_double, P, C.c_double, C.c_double], C.c_int),
+                "or_create": ([D, C.c_int, C.c_int, D, D, C.c_int, P], C.c_void_p),
+                "or_destroy": ([C.c_void_p], None),
+                "or_begin_step": ([C.c_void_p], C.c_double),
+                "or_vcycle": ([C.c_void_p], C.c_double),
+                "or_end_step": ([C.c_void_p], C.c_double),
+                "or_get_phi": ([C.c_void_p, D], None),
+                "or_set_phi": ([C.c_void_p, D], None),
+                "or_get_level": ([C.c_void_p, C.c_int, C.c_int, D], None),
+                "or_get_scalars": ([C.c_void_p, D], None),
+                "or_set_c": ([C.c_void_p, C.c_double, C.c_double], None),
+                "or_frozen_coeffs": ([D, D, D, D, C.c_int, C.c_int, C.c_double, P, C.c_double, C.c_double, D], None),
+                "or_smooth_given": ([D, C.c_int, C.c_int, C.c_double, C.c_int, D], None),
+                "or_members": ([D, C.c_int, C.c_int, C.c_double, C.c_int, I], None),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ---- thin wrappers over the C routines -----------------------------------------------------
+
+def gauss_blur(z, sigma=1.0):
+    z, pz = _d(z)
+    out = np.empty_like(z)
+    lib().or_gauss_blur(pz, z.shape[0], z.shape[1], sigma, _d(out)[1])
+    return out
+
+
+def edge_detector(zb, beta_edge=1.0):
+    zb, p = _d(zb)
+    out = np.empty_like(zb)
+    lib().or_edge_detector(p, zb.shape[0], zb.shape[1], beta_edge, _d(out)[1])
+    return out
+
+
+def distance(n, m, markers, sigma_d):
+    mk = np.asarray(markers, dtype=np.float64).reshape(-1, 2)
+    mx, px = _d(mk[:, 0].copy())
+    my, py = _d(mk[:, 1].copy())
+    out = np.empty((n, m))
+    lib().or_distance(n, m, px, py, len(mk), sigma_d, _d(out)[1])
+    return out
+
+
+def initial_phi(n, m, markers, r0=None):
+    mk = np.asarray(markers, dtype=np.float64).reshape(-1, 2)
+    mx, px = _d(mk[:, 0].copy())
+    my, py = _d(mk[:, 1].copy())
+    out = np.empty((n, m))
+    area = np.zeros(1)
+    r0 = 0.05 * max(n, m) if r0 is None else r0
+    h = lib().or_initial_phi(n, m, px, py, len(mk), r0, _d(out)[1], _d(area)[1])
+    return out, float(area[0]), h
+
+
+def region_means(phi, z, eps=1.0):
+    phi, pp = _d(phi)
+    z, pz = _d(z)
+    c = np.zeros(2)
+    lib().or_region_means(pp, pz, phi.shape[0], phi.shape[1], eps,
+                          c[0:1].ctypes.data_as(C.POINTER(C.c_double)),
+                          c[1:2].ctypes.data_as(C.POINTER(C.c_double)))
+    return float(c[0]), float(c[1])
+
+
+def restrict(f):
+    f, p = _d(f)
+    out = np.empty((f.shape[0] // 2, f.shape[1] // 2))
+    lib().or_restrict(p, f.shape[0], f.shape[1], _d(out)[1])
+    return out
+
+
+def interpolate_add(e, f):
+    e, pe = _d(e)
+    out = np.array(f, dtype=np.float64, copy=True)
+    lib().or_interpolate_add(pe, e.shape[0], e.shape[1], _d(out)[1], out.shape[0], out.shape[1])
+    return out
+
+
+def apply_L(phi, w, Fn, h=1.0, p=None, n0m0=None, A1=0.0):
+    phi, pp = _d(phi)
+    w, pw = _d(w)
+    Fn, pf = _d(Fn)
+    p = p or params(*phi.shape)
+    out = np.empty_like(phi)
+    n0m0 = float(phi.size) if n0m0 is None else n0m0
+    lib().or_apply_L(pp, pw, pf, phi.shape[0], phi.shape[1], h, C.byref(p), n0m0, A1, _d(out)[1])
+    return out
+
+
+def fitting(z, d, phin, c1, c2, p):
+    z, pz = _d(z)
+    d, pd = _d(d)
+    phin, pn = _d(phin)
+    out = np.empty_like(z)
+    lib().or_fitting(pz, pd, pn, z.shape[0], z.shape[1], c1, c2, C.byref(p), _d(out)[1])
+    return out
+
+
+def frozen_coeffs(phi, w, Fn, rhs=None, h=1.0, p=None, n0m0=None, A1=0.0):
+    """Returns dict with A, B, C, D, S, f, delta (each n x m)."""
+    phi, pp = _d(phi)
+    w, pw = _d(w)
+    Fn, pf = _d(Fn)
+    prhs = None
+    if rhs is not None:
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        prhs = rhs.ctypes.data_as(C.POINTER(C.c_double))
+    p = p or params(*phi.shape)
+    n, m = phi.shape
+    out = np.empty((7, n, m))
+    n0m0 = float(phi.size) if n0m0 is None else n0m0
+    lib().or_frozen_coeffs(pp, pw, pf, prhs, n, m, h, C.byref(p), n0m0, A1, _d(out)[1])
+    return dict(zip("A B C D S f delta".split(), out))
+
+
+def smooth_given(coef, phi, Sigma=2.0, kind=0):
+    """One outer iteration of a smoother with explicit frozen coefficients.
+    coef: dict or array (6, n, m) with A, B, C, D, S, f."""
+    if isinstance(coef, dict):
+        coef = np.stack([coef[k] for k in "A B C D S f".split()])
+    coef, pc = _d(coef)
+    out, po = _d(np.array(phi, dtype=np.float64, copy=True))
+    lib().or_smooth_given(pc, phi.shape[0], phi.shape[1], Sigma, kind, po)
+    return out
+
+
+def members(coef, Sigma=2.0, piece=32):
+    """Member flags (4, n, m) of the four sweeps; piece <= 0 means whole lines."""
+    if isinstance(coef, dict):
+        coef = np.stack([coef[k] for k in "A B C D".split()] + [coef["A"]] * 2)
+    coef, pc = _d(coef)
+    n, m = coef.shape[1:]
+    out = np.zeros((4, n, m), dtype=np.int32)
+    lib().or_members(pc, n, m, Sigma, piece, out.ctypes.data_as(C.POINTER(C.c_int)))
+    return out.astype(bool)
+
+
+def classify(A, B, Cc, D, has=(1, 1, 1, 1), Sigma=2.0):
+    return lib().or_classify(A, B, Cc, D, *has, Sigma)
+
+
+def coarse_solve(phi, w, Fn, rhs, h=1.0, p=None, n0m0=None, A1=0.0):
+    phi, _ = _d(phi)
+    out, po = _d(phi.copy())
+    w, pw = _d(w)
+    Fn, pf = _d(Fn)
+    rhs, pr = _d(rhs)
+    p = p or params(*phi.shape)
+    n0m0 = float(phi.size) if n0m0 is None else n0m0
+    it = lib().or_coarse_solve(po, pw, pf, pr, phi.shape[0], phi.shape[1], h, C.byref(p), n0m0, A1)
+    return out, it
+
+
+class Solver:
+    """The oracle's FAS solver over one image (create / begin_step / vcycle / end_step)."""
+
+    def __init__(self, image, markers, p: Params):
+        img, pi = _d(image)
+        mk = np.asarray(markers, dtype=np.float64).reshape(-1, 2)
+        self._mx, px = _d(mk[:, 0].copy())
+        self._my, py = _d(mk[:, 1].copy())
+        self.n, self.m = img.shape
+        self.p = p
+        self._h = lib().or_create(pi, self.n, self.m, px, py, len(mk), C.byref(p))
+
+    def close(self):
+        if self._h:
+            lib().or_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def begin_step(self) -> float:
+        return lib().or_begin_step(self._h)
+
+    def vcycle(self) -> float:
+        return lib().or_vcycle(self._h)
+
+    def end_step(self) -> float:
+        return lib().or_end_step(self._h)
+
+    @property
+    def phi(self):
+        out = np.empty((self.n, self.m))
+        lib().or_get_phi(self._h, _d(out)[1])
+        return out
+
+    @phi.setter
+    def phi(self, v):
+        v, p = _d(v)
+        assert v.shape == (self.n, self.m)
+        lib().or_set_phi(self._h, p)
+
+    def level(self, l, which):
+        names = ["phi", "w", "z", "d", "Fn", "rhs", "tmp"]
+        idx = names.index(which)
+        n, m = self.n, self.m
+        for _ in range(l):
+            n, m = n // 2, m // 2
+        out = np.empty((n, m))
+        lib().or_get_level(self._h, l, idx, _d(out)[1])
+        return out
+
+    def scalars(self):
+        out = np.zeros(5)
+        lib().or_get_scalars(self._h, _d(out)[1])
+        return dict(c1=out[0], c2=out[1], A1=out[2], res0=out[3], picard=int(out[4]))
+
+    def set_c(self, c1, c2):
+        lib().or_set_c(self._h, c1, c2)
+
+    def solve_step(self, tol, max_cycles=50):
+        """One pseudo-time step: V-cycles until rho <= tol.  Returns list of rho."""
+        self.begin_step()
+        hist = []
+        for _ in range(max_cycles):
+            r = self.vcycle()
+            hist.append(r)
+            if r <= tol:
+                break
+        return hist

@@ -1,0 +1,131 @@
+"""Pins of the coarsest solve, the FAS V-cycle (Algorithm 1) and the driver invariants."""
+import numpy as np
+import pytest
+from scipy.linalg import lu_factor, lu_solve
+
+import oracle as O
+from paper_1807_02137_gb300 import synth
+
+
+def small_problem(n, seed=0, model=0):
+    img, mk, _ = synth.disc_square(n, 0.05, seed)
+    p = O.params(n, n, levels=1, model=model)
+    s = O.Solver(img, mk, p)
+    s.begin_step()
+    return s, p
+
+
+def dense_picard(phi, w, Fn, rhs, h, p, iters=200):
+    """Picard on the frozen coefficients with dense LU (scipy), rows divided by delta."""
+    n, m = phi.shape
+    N = n * m
+    for _ in range(iters):
+        k = O.frozen_coeffs(phi, w, Fn, rhs, h, p)
+        dl = k["delta"]
+        K = np.zeros((N, N))
+        b = -(k["f"] / dl).ravel()
+        for i in range(n):
+            for j in range(m):
+                q = i * m + j
+                K[q, q] = (k["A"][i, j] + k["B"][i, j] + k["C"][i, j] + k["D"][i, j]) / dl[i, j] + p.inv_tau
+                if i + 1 < n: K[q, q + m] = -k["A"][i, j] / dl[i, j]
+                if i > 0: K[q, q - m] = -k["B"][i, j] / dl[i, j]
+                if j + 1 < m: K[q, q + 1] = -k["C"][i, j] / dl[i, j]
+                if j > 0: K[q, q - 1] = -k["D"][i, j] / dl[i, j]
+        new = lu_solve(lu_factor(K), b).reshape(n, m)
+        if np.max(np.abs(new - phi)) <= 1e-14 * max(1.0, np.max(np.abs(new))):
+            return new
+        phi = new
+    return phi
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_coarse_solve_matches_dense_lu_picard(n):
+    s, p = small_problem(n)
+    phi0, w, Fn = s.phi, s.level(0, "w"), s.level(0, "Fn")
+    rhs = np.random.default_rng(1).normal(0, 0.1, (n, n))
+    p.coarse_maxit, p.coarse_tol = 500, 1e-15
+    got, it = O.coarse_solve(phi0, w, Fn, rhs, 2.0, p)
+    ref = dense_picard(phi0, w, Fn, rhs, 2.0, p)
+    assert it > 0
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+    # the fixed point solves the nonlinear equation L(phi) = rhs
+    res = rhs - O.apply_L(got, w, Fn, 2.0, p)
+    assert np.linalg.norm(res) <= 1e-8 * np.linalg.norm(rhs - O.apply_L(phi0, w, Fn, 2.0, p))
+
+
+@pytest.mark.parametrize("n,levels", [(16, 3), (32, 4), (37, 3)])
+def test_fas_vcycles_converge_to_the_direct_solution(n, levels):
+    img, mk, _ = synth.disc_square(n, 0.05, 3)
+    p = O.params(n, n, levels=levels)
+    s = O.Solver(img, mk, p)
+    s.begin_step()
+    phin, w, Fn = s.phi, s.level(0, "w"), s.level(0, "Fn")
+    for _ in range(60):
+        r = s.vcycle()
+        if r < 1e-12:
+            break
+    assert r < 1e-11
+    ref = dense_picard(phin, w, Fn, np.zeros((n, n)), 1.0, p)
+    assert np.max(np.abs(s.phi - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_first_step_residual_decreases_every_cycle():
+    W = synth.workload("disc128")
+    p = O.params(128, 128, levels=W.levels)
+    s = O.Solver(W.image, W.markers, p)
+    hist = s.solve_step(W.tol, 40)
+    assert hist[-1] <= W.tol
+    assert all(b < a for a, b in zip(hist, hist[1:]))
+
+
+def test_two_region_image_gives_the_exact_region_mask():
+    # A clean two-valued image (a disc on a background) with markers inside the disc: after a
+    # few pseudo-time steps sign(phi) is the disc exactly.
+    n = 64
+    i, j = np.mgrid[0:n, 0:n].astype(float)
+    disc = (i - 30) ** 2 + (j - 34) ** 2 <= 15 ** 2
+    img = np.where(disc, 0.8, 0.2)
+    ang = np.linspace(0, 2 * np.pi, 8, endpoint=False)
+    mk = np.stack([34 + 10 * np.cos(ang), 30 + 10 * np.sin(ang)], 1).round()
+    s = O.Solver(img, mk, O.params(n, n, levels=4))
+    for _ in range(14):
+        s.solve_step(1e-10, 60)
+        s.end_step()
+    assert np.array_equal(s.phi > 0, disc)
+
+
+def test_rada_chen_area_term():
+    # The Rada-Chen bracket adds 2 nu (h^2 sum H / |Omega| - A1 / |Omega|) to the fitting term
+    # (eqs. rcabcd and gslexrc); with w and the fitting field equal, the two models' operators
+    # differ by exactly that scalar.
+    n = 12
+    rng = np.random.default_rng(4)
+    phi, w, Fn = rng.normal(0, 2, (n, n)), rng.uniform(0.5, 1, (n, n)), rng.normal(size=(n, n))
+    psc = O.params(n, n, model=0)
+    prc = O.params(n, n, model=1, nu=0.7)
+    A1 = 30.0
+    d = O.apply_L(phi, w, Fn, 2.0, prc, n0m0=4.0 * n * n, A1=A1) - O.apply_L(phi, w, Fn, 2.0, psc)
+    H = 0.5 + np.arctan(phi) / np.pi
+    ref = -2 * 0.7 * (4.0 * H.sum() / (4.0 * n * n) - A1 / (4.0 * n * n))
+    assert np.allclose(d, ref, atol=1e-13)
+
+
+def test_rada_chen_fas_converges():
+    img, mk, _ = synth.disc_square(64, 0.05, 5)
+    s = O.Solver(img, mk, O.params(64, 64, levels=4, model=1))
+    hist = s.solve_step(1e-8, 60)
+    assert hist[-1] <= 1e-8
+
+
+def test_paper_orderings_converge_too():
+    # The lexicographic Hybrid Smoother 2 (the paper's Algorithm 3) and GSLINE-I (Algorithm 1)
+    # drive the same first step to the same solution.
+    img, mk, _ = synth.disc_square(64, 0.05, 6)
+    sols = []
+    for sm in (0, 1, 2):
+        s = O.Solver(img, mk, O.params(64, 64, levels=4, smoother=sm))
+        hist = s.solve_step(1e-10, 80)
+        assert hist[-1] <= 1e-10
+        sols.append(s.phi)
+    assert np.allclose(sols[0], sols[1], atol=1e-8) and np.allclose(sols[0], sols[2], atol=1e-8)
