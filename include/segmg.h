@@ -1,0 +1,198 @@
+/*
+ * segmg.h -- C ABI of the GB300 (sm_103a) multigrid solver for level-set selective
+ * segmentation.  Method: Roberts, Chen, Irion, "A multigrid algorithm with non-standard
+ * smoother for two selective models in variational segmentation" (arXiv 1807.02137).
+ *
+ * The library solves the discretised Euler-Lagrange equation of the Spencer-Chen model
+ * (Sec. 2.2, eq. scel) or the Rada-Chen model (eq. rcel, discretised as eqs. rcabcd/abcdrc) by
+ * nonlinear FAS V-cycles (Sec. 3.1, Algorithm 1) whose smoother is Hybrid Smoother 2
+ * (Sec. 4.3), run in a parallel ordering (checkerboard point updates plus partial-line solves
+ * on alternating lines).  Because the stationary equation has no bounded solution for generic
+ * images, each call to the solver advances one implicit pseudo-time step
+ *     N(phi) - delta(phi) (phi - phi^n) / tau = 0,
+ * whose solution set equals that of the row-scaled equation
+ *     L(phi) = mu div_h(w grad phi / |grad phi|_beta) - F - (phi - phi^n)/tau = 0,
+ * and the FAS residual is measured on L.  The paper's stationary equation is tau = inf.
+ *
+ * Conventions shared by every entry point:
+ *   - images and grid functions are n x m, row-major, element [i*m + j], i = row (down),
+ *     j = column (right); pixel units (finest spacing h = 1);
+ *   - markers are k pairs (x, y) = (column, row) of doubles in HOST memory;
+ *   - "device" pointers are CUDA device memory owned by the caller, "host" pointers are host
+ *     memory owned by the caller; the library never frees caller memory;
+ *   - the element type of an image / phi buffer is float for MG_F32 and double for MG_F64;
+ *   - every function returns MG_OK (0) or a negative MG_ERR_* code; mg_strerror() names it and
+ *     mg_last_error() returns the detail text of the last failure on the calling thread;
+ *   - work is enqueued on the handle's stream; only calls that return host values wait for it;
+ *   - handles are not thread-safe; distinct handles may be used from distinct threads.
+ */
+#ifndef SEGMG_H
+#define SEGMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MG_OK = 0,
+    MG_ERR_ARG = -1,        /* invalid argument (size, pointer, parameter) */
+    MG_ERR_NAN = -2,        /* NaN or Inf in the input image or in a residual norm */
+    MG_ERR_CUDA = -3,       /* a CUDA runtime call failed (detail in mg_last_error) */
+    MG_ERR_DIVERGED = -4,   /* residual grew by more than 1e3 over its initial value */
+    MG_ERR_TIMEOUT = -5,    /* an iteration cap was reached without meeting the tolerance */
+    MG_ERR_NOT_SPD = -6,    /* coarsest-grid Cholesky met a non-positive pivot */
+    MG_ERR_NOMEM = -7,      /* device allocation failed */
+    MG_ERR_STATE = -8       /* call out of order (e.g. mg_vcycle before mg_begin_step) */
+};
+
+enum { MG_MODEL_SC = 0, MG_MODEL_RC = 1 };       /* Spencer-Chen / Rada-Chen (Sec. 2.2) */
+enum { MG_F32 = 0, MG_F64 = 1 };                 /* storage and smoothing precision */
+enum { MG_SMOOTH_FUSED = 0, MG_SMOOTH_PHASED = 1 };   /* one kernel per sweep / per phase */
+
+typedef struct mg_handle_s *mg_handle;
+
+/* Parameters.  Model weights follow Sec. 2.2 (eqs. rcfunc, scfunc); the smoother and cycle
+ * settings follow Sec. 3-4 and Sec. 5 ("Parameter choices", "Number of smoothing steps"). */
+typedef struct {
+    int model;             /* MG_MODEL_SC or MG_MODEL_RC */
+    double mu;             /* length-term weight (> 0) */
+    double lambda1;        /* inside fitting weight (>= 0) */
+    double lambda2;        /* outside fitting weight (>= 0) */
+    double theta;          /* Spencer-Chen distance weight (>= 0) */
+    double nu;             /* Rada-Chen area weight (>= 0) */
+    double eps;            /* smoothed Heaviside width (> 0) */
+    double beta;           /* |grad phi|_beta = sqrt(|grad phi|^2 + beta) (> 0) */
+    double beta_edge;      /* edge detector g(s) = 1 / (1 + beta_edge s), s = |grad G*z|^2 */
+    double sigma_blur;     /* Gaussian blur of the image before differencing (px, > 0) */
+    double sigma_d;        /* width of the marker distance function (px, > 0) */
+    double Sigma;          /* jump threshold: max/min of the four coefficients (> 1) */
+    double tau;            /* pseudo-time step (px^2-time units, > 0; 0 means infinity) */
+    int nu1, nu2;          /* pre- and post-smoothing outer iterations (>= 0) */
+    int levels;            /* number of grids, finest included (>= 1) */
+    int precision;         /* MG_F32 or MG_F64 */
+    int smoother;          /* MG_SMOOTH_FUSED or MG_SMOOTH_PHASED (same results) */
+    int coarse_maxit;      /* Picard cap of the coarsest solve (>= 1) */
+    double coarse_tol;     /* relative residual target of the coarsest solve */
+    int use_graph;         /* 1: replay each V-cycle as a captured CUDA graph */
+} mg_params;
+
+/* Counters and scalars of the current state (mg_get_stats). */
+typedef struct {
+    int n, m, levels, precision;
+    int steps;             /* pseudo-time steps ended so far */
+    int cycles_step;       /* V-cycles in the current / last step */
+    int cycles_total;
+    int picard_last;       /* Picard iterations of the last coarsest solve */
+    double rho;            /* last ||L(phi)|| / ||L(phi^n)|| */
+    double res0;           /* ||L(phi^n)|| of the current step */
+    double eta;            /* last ||phi^{n+1} - phi^n|| / ||phi^n|| */
+    double c1, c2;         /* region averages (eq. c1c2) */
+    double A1;             /* area of the initial polygon (px^2) */
+    size_t device_bytes;   /* device memory held by the handle */
+    long long launches;    /* kernels launched by the handle so far (graph nodes included) */
+} mg_stats;
+
+/* Optional device allocator (for example a framework's caching allocator).  alloc returns a
+ * device pointer of at least `bytes` bytes, 256-byte aligned, usable on `stream`; free
+ * releases it.  A NULL mg_allocator selects cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} mg_allocator;
+
+/* Fills *p with the defaults: Spencer-Chen, mu = 1, lambda1 = lambda2 = 10, theta = 1,
+ * nu = 1, eps = 1, beta = 1e-6, beta_edge = 1, sigma_blur = 1, sigma_d = 0.05 max(n, m),
+ * Sigma = 2, tau = 1, V(2,2), levels = as many halvings as keep min(n, m) >= 4 (at most 12),
+ * MG_F32, fused smoother, coarse_maxit = 100, coarse_tol = 1e-13, use_graph = 1. */
+int mg_default_params(mg_params *p, int n, int m);
+
+/* Builds a solver for one n x m image (Sec. 2.2 data, Sec. 5 initialisation):
+ *   image      device, n*m elements of the precision's type, read during the call only;
+ *   markers_xy host, k (x, y) pairs inside [0, m-1] x [0, n-1], k >= 1;
+ *   p          parameters (copied);  alloc may be NULL;  stream may be NULL (the library
+ *              then creates its own non-blocking stream).
+ * Computes the blurred image, edge detector g, distance function d, weight w (g for SC,
+ * d g for RC), their restrictions to every grid, the initial level set (signed distance to
+ * the convex hull of the markers; a disc of radius 0.05 max(n, m) for fewer than three or
+ * collinear markers) and the initial c1, c2.  Allocates all device memory the solver needs
+ * (mg_stats.device_bytes).  Errors: MG_ERR_ARG (sizes, markers, parameters, a coarsest grid
+ * above 4096 cells or 64 cells on its shorter side), MG_ERR_NAN (non-finite image),
+ * MG_ERR_NOMEM, MG_ERR_CUDA.  On error *out is NULL and nothing is leaked. */
+int mg_setup(mg_handle *out, const void *image, int n, int m, const double *markers_xy, int k,
+             const mg_params *p, const mg_allocator *alloc, void *stream);
+
+/* Re-runs the set-up of mg_setup on a new image and marker set of the same size, reusing the
+ * handle's memory (no allocation).  Same arguments and errors as mg_setup. */
+int mg_reset(mg_handle h, const void *image, const double *markers_xy, int k);
+
+/* Starts a pseudo-time step from the current phi: phi^n = phi, fitting fields of every grid
+ * from c1, c2, and the reference norm ||L(phi^n)|| (written to *res0 if not NULL; waits for
+ * the stream). */
+int mg_begin_step(mg_handle h, double *res0);
+
+/* One FAS V-cycle (Algorithm 1, gamma = 1) with nu1 / nu2 outer iterations of Hybrid
+ * Smoother 2 per grid and the FP64 coarsest solve; writes rho = ||L(phi)|| / ||L(phi^n)||
+ * (FP64 accumulation) to *rho if not NULL (waits for the stream).  MG_ERR_STATE before
+ * mg_begin_step; MG_ERR_NAN / MG_ERR_DIVERGED / MG_ERR_NOT_SPD as detected. */
+int mg_vcycle(mg_handle h, double *rho);
+
+/* Ends the step: new c1, c2 from the current phi (Sec. 5) and
+ * eta = ||phi - phi^n|| / ||phi^n|| (to *eta if not NULL; waits). */
+int mg_end_step(mg_handle h, double *eta);
+
+/* mg_begin_step, then V-cycles until rho <= tol or max_cycles, then mg_end_step.  Returns
+ * MG_ERR_TIMEOUT (state still valid) when max_cycles is reached first. */
+int mg_solve_step(mg_handle h, double tol, int max_cycles, int *cycles, double *rho);
+
+/* Pseudo-time steps (each by mg_solve_step) until eta < eta_stop or max_steps; *steps gets
+ * the number taken.  A step that reaches its cycle cap does not stop the run. */
+int mg_solve(mg_handle h, double tol, int max_cycles, double eta_stop, int max_steps, int *steps);
+
+/* Segmentation mask: mask[i*m + j] = 1 where phi > 0 else 0.  mask: device, n*m bytes. */
+int mg_mask(mg_handle h, unsigned char *mask);
+
+/* Copies phi (device, n*m elements of the precision's type) out of / into the solver. */
+int mg_get_phi(mg_handle h, void *phi);
+int mg_set_phi(mg_handle h, const void *phi);
+
+/* Overrides c1, c2 (eq. c1c2) for the next mg_begin_step. */
+int mg_set_regions(mg_handle h, double c1, double c2);
+
+/* Copies one internal field of grid `level` (device, n_l*m_l elements of the precision's type;
+ * n_l = n >> level): field 0 = phi, 1 = w, 2 = z, 3 = d, 4 = F (fitting field of the step),
+ * 5 = FAS right-hand side.  For tests and diagnostics. */
+int mg_get_level(mg_handle h, int level, int field, void *out);
+
+int mg_get_stats(mg_handle h, mg_stats *s);
+
+/* Whole pipeline through host buffers: copies the float image to the device, runs mg_setup,
+ * then mg_solve(tol, max_cycles, eta_stop, max_steps) with the given parameters (precision
+ * forced to MG_F32), and copies the mask (and phi if phi_host is not NULL) back.  All host
+ * buffers are n*m elements; stats may be NULL.  Synchronous. */
+int mg_segment_host(const float *image_host, int n, int m, const double *markers_xy, int k,
+                    const mg_params *p, double tol, int max_cycles, double eta_stop,
+                    int max_steps, unsigned char *mask_host, float *phi_host, mg_stats *stats);
+
+/* Diagnostic timing of the smoother kernels on grid `level` at the current state: runs `reps`
+ * outer smoothing iterations eagerly with CUDA events on the handle's stream and writes the
+ * mean milliseconds per launch of [0] the snapshot kernel, [1..4] the sweeps A, B, C, D,
+ * [5] the residual kernel to ms[0..5].  Changes phi like real smoothing does.  Waits. */
+int mg_time_kernels(mg_handle h, int level, int reps, double *ms);
+
+/* The CUDA stream (cudaStream_t) the handle enqueues its work on: the caller's stream given
+ * to mg_setup, or the library's own non-blocking stream when that was NULL. */
+void *mg_get_stream(mg_handle h);
+
+/* Releases the handle and its device memory (after waiting for its stream). */
+void mg_destroy(mg_handle h);
+
+const char *mg_strerror(int code);
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,120 @@
+// arith.cuh -- device arithmetic shared by the smoother kernels.
+//
+// The fused and the per-phase smoother kernels must produce bit-identical results (the fused
+// kernel only reorganises memory traffic).  Every operation of the relaxation formulas below
+// is therefore written with explicitly rounded intrinsics, which the compiler never contracts
+// or reorders, so both kernels execute the same sequence of IEEE operations.
+#pragma once
+
+#include <cstdint>
+#include "internal.h"
+
+namespace segmg {
+
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+
+// Face coefficient of a face that exists: the arithmetic mean of the two cell values of
+// G = w / |grad phi|_beta (Sec. 2.2, eq. abcdrc: G_{i+1/2,j}); a boundary face carries no flux.
+template <typename T>
+__device__ __forceinline__ T face(T gc, T gn, bool has) {
+    return has ? mul_rn(add_rn(gc, gn), T(0.5)) : T(0);
+}
+
+// G = w / |grad phi|_beta at a cell from the four neighbour values of pn and u (central
+// differences, spacing h; mirror ghosts are supplied by the caller as clamped neighbours).
+template <typename T>
+__device__ __forceinline__ T cell_G(T w, T pS, T pN, T pE, T pW, T uS, T uN, T uE, T uW, T inv_2h,
+                                    T beta) {
+    T gy = mul_rn(add_rn(sub_rn(pS, pN), sub_rn(uS, uN)), inv_2h);
+    T gx = mul_rn(add_rn(sub_rn(pE, pW), sub_rn(uE, uW)), inv_2h);
+    T s = fma_rn(gx, gx, fma_rn(gy, gy, beta));
+    return div_rn(w, sqrt_rn(s));
+}
+
+// GSLEX-I point update (eq. gslexrc) in increment form.  With the row divided by delta the
+// frozen coefficients are a_X = mu G_X / h^2 and S = sum a_X + 1/tau; the snapshot has folded
+// phi^n and the right-hand sides into f, so the update of the increment is
+//     u = (sum_X a_X u_X - f) / (sum_X a_X + 1/tau).
+// aS..aW are the face values G_X (the factor mu/h^2 = cdiff is applied here).
+template <typename T>
+__device__ __forceinline__ T point_relax(T cdiff, T inv_tau, T aS, T aN, T aE, T aW, T uS, T uN,
+                                         T uE, T uW, T f) {
+    T num = mul_rn(aS, uS);
+    num = fma_rn(aN, uN, num);
+    num = fma_rn(aE, uE, num);
+    num = fma_rn(aW, uW, num);
+    T den = add_rn(add_rn(aS, aN), add_rn(aE, aW));
+    return div_rn(fma_rn(cdiff, num, -f), fma_rn(cdiff, den, inv_tau));
+}
+
+// One cell of a partial-line run: face values along the line (previous / next cell) and across
+// it (two sides), the two across-line neighbour values and f.
+template <typename T>
+struct RunCell {
+    T ap, an, ax1, ax2;
+    T ux1, ux2;
+    T f;
+};
+
+// Partial-line update (Sec. 4.3, step III): the rows of one run of cells on a line, coupled
+// through the in-line coefficients, solved exactly by the Thomas algorithm (the system is
+// diagonally dominant, Sec. 3.2).  at(t) returns the RunCell of run position t; endp / endn
+// are the values just before / after the run (their coefficients are zero at a domain edge).
+// The solution is written through put(t, value).
+template <typename T, typename At, typename Put>
+__device__ __forceinline__ void thomas_run(int len, T cdiff, T inv_tau, T endp, T endn, At at,
+                                           Put put) {
+    T cup[kChunk], cdi[kChunk], crh[kChunk];
+    for (int t = 0; t < len; ++t) {
+        RunCell<T> c = at(t);
+        T lo = mul_rn(cdiff, c.ap);
+        T up = mul_rn(cdiff, c.an);
+        T sum = add_rn(add_rn(c.ap, c.an), add_rn(c.ax1, c.ax2));
+        T di = -fma_rn(cdiff, sum, inv_tau);
+        T across = fma_rn(c.ax2, c.ux2, mul_rn(c.ax1, c.ux1));
+        T rhs = fma_rn(-cdiff, across, c.f);
+        if (t == 0) rhs = fma_rn(-lo, endp, rhs);
+        if (t == len - 1) rhs = fma_rn(-up, endn, rhs);
+        if (t > 0) {
+            T wgt = div_rn(lo, cdi[t - 1]);
+            di = fma_rn(-wgt, cup[t - 1], di);
+            rhs = fma_rn(-wgt, crh[t - 1], rhs);
+        }
+        cup[t] = up;
+        cdi[t] = di;
+        crh[t] = rhs;
+    }
+    T x = div_rn(crh[len - 1], cdi[len - 1]);
+    put(len - 1, x);
+    for (int t = len - 2; t >= 0; --t) {
+        x = div_rn(fma_rn(-cup[t], x, crh[t]), cdi[t]);
+        put(t, x);
+    }
+}
+
+// Member mask of one 32-cell piece of a line from its star mask (bit t = position t):
+// starred cells, plus for every starred cell without a starred neighbour its next cell, or
+// its previous cell when it is the last cell of the piece (Sec. 4.3, "a single starred
+// pixel is updated collectively with its immediate neighbour").  `len` = valid cells (1..32).
+__device__ __forceinline__ uint32_t members_of(uint32_t star, int len) {
+    uint32_t valid = len >= 32 ? 0xffffffffu : ((1u << len) - 1u);
+    star &= valid;
+    uint32_t single = star & ~(star << 1) & ~(star >> 1);
+    uint32_t next = (single << 1) & valid;
+    uint32_t last = single & ~(valid >> 1);   // singles at position len-1
+    uint32_t prev = last >> 1;
+    return star | next | prev;
+}
+
+}  // namespace segmg

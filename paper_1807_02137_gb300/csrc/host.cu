@@ -1,0 +1,731 @@
+// host.cu -- driver of the FAS V-cycle and the C ABI declared in include/segmg.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/segmg.h"
+#include "internal.h"
+
+namespace segmg {
+void prepare_smoother_kernels();
+}
+
+namespace {
+
+using namespace segmg;
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? MG_ERR_NOMEM : MG_ERR_CUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+#define CKL()                                                                                      \
+    do {                                                                                           \
+        cudaError_t e_ = cudaGetLastError();                                                       \
+        if (e_ != cudaSuccess) return fail(MG_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+__global__ void k_check_finite(const void *img, int is_double, size_t N, int *flag) {
+    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; q < N; q += (size_t)gridDim.x * blockDim.x) {
+        double v = is_double ? ((const double *)img)[q] : (double)((const float *)img)[q];
+        if (!isfinite(v)) { atomicOr(flag, 2); return; }
+    }
+}
+
+template <typename T>
+__global__ void k_phi_out(const T *pn, const T *u, int n, int m, int p, T *out) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i < n && j < m) out[(size_t)i * m + j] = pn[(size_t)i * p + j] + u[(size_t)i * p + j];
+}
+
+template <typename T>
+__global__ void k_phi_in(const T *in, int n, int m, int p, T *pn, T *u) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i < n && j < m) {
+        pn[(size_t)i * p + j] = in[(size_t)i * m + j];
+        u[(size_t)i * p + j] = T(0);
+    }
+}
+
+// Convex hull of 2-D points (monotone chain), counter-clockwise in (x, y); returns the hull
+// vertex list (x0, y0, x1, y1, ...).
+std::vector<double> hull_of(const double *xy, int k) {
+    std::vector<std::pair<double, double>> pts(k);
+    for (int q = 0; q < k; ++q) pts[q] = {xy[2 * q], xy[2 * q + 1]};
+    std::sort(pts.begin(), pts.end());
+    pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+    auto cross = [](const std::pair<double, double> &o, const std::pair<double, double> &a,
+                    const std::pair<double, double> &b) {
+        return (a.first - o.first) * (b.second - o.second) - (a.second - o.second) * (b.first - o.first);
+    };
+    std::vector<std::pair<double, double>> h(2 * pts.size() + 2);
+    int c = 0;
+    for (size_t q = 0; q < pts.size(); ++q) {
+        while (c >= 2 && cross(h[c - 2], h[c - 1], pts[q]) <= 0) --c;
+        h[c++] = pts[q];
+    }
+    for (int q = (int)pts.size() - 2, lo = c + 1; q >= 0; --q) {
+        while (c >= lo && cross(h[c - 2], h[c - 1], pts[q]) <= 0) --c;
+        h[c++] = pts[q];
+    }
+    if (c > 1) --c;
+    std::vector<double> out;
+    for (int q = 0; q < c; ++q) { out.push_back(h[q].first); out.push_back(h[q].second); }
+    return out;
+}
+
+struct SolverBase {
+    virtual ~SolverBase() {}
+    virtual int reset(const void *image, const double *mk, int k) = 0;
+    virtual int begin_step(double *res0) = 0;
+    virtual int vcycle(double *rho) = 0;
+    virtual int end_step(double *eta) = 0;
+    virtual int mask(unsigned char *out) = 0;
+    virtual int get_phi(void *out) = 0;
+    virtual int set_phi(const void *in) = 0;
+    virtual int set_regions(double c1, double c2) = 0;
+    virtual int get_level(int l, int field, void *out) = 0;
+    virtual int stats(mg_stats *s) = 0;
+    virtual cudaStream_t stream() const = 0;
+    virtual int time_kernels(int level, int reps, double *ms) = 0;
+};
+
+template <typename T>
+struct Level {
+    int n = 0, m = 0, pitch = 0;
+    double h = 1;
+    T *pn = nullptr, *u = nullptr, *u0 = nullptr, *rhs = nullptr, *w = nullptr, *z = nullptr, *d = nullptr;
+    T *F = nullptr, *G = nullptr, *f = nullptr, *r = nullptr, *upre = nullptr;
+    uint8_t *cls = nullptr;
+};
+
+template <typename T>
+struct Solver final : SolverBase {
+    mg_params p{};
+    int n = 0, m = 0, nlev = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    mg_allocator al{};
+    bool use_al = false;
+    void *pool = nullptr;
+    size_t pool_bytes = 0;
+    Level<T> lv[kMaxLevels];
+    Scalars *dsc = nullptr;
+    Scalars *hsc = nullptr;   // pinned host mirror
+    double *partials = nullptr;
+    int npart = 0;
+    double *coarse = nullptr;
+    double *dmk = nullptr;    // markers (2 * kcap)
+    double *dhull = nullptr;  // hull (2 * kcap + 4)
+    int kcap = 0;
+    double A1 = 0, res0 = 0, rho = 0, eta = 0;
+    int steps = 0, cycles_step = 0, cycles_total = 0;
+    bool in_step = false;
+    cudaGraphExec_t gexec = nullptr;
+    long long launches = 0, graph_nodes = 0;
+    ModelParams mp{};
+
+    ~Solver() override { release(); }
+
+    void release() {
+        if (st) cudaStreamSynchronize(st);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        if (pool) {
+            if (use_al) al.free(pool, pool_bytes, st, al.ctx);
+            else cudaFreeAsync(pool, st);
+            if (st) cudaStreamSynchronize(st);
+        }
+        pool = nullptr;
+        if (hsc) cudaFreeHost(hsc);
+        hsc = nullptr;
+        if (own_stream && st) cudaStreamDestroy(st);
+        st = nullptr;
+    }
+
+    cudaStream_t stream() const override { return st; }
+
+    LevelView<T> view(int l) const {
+        const Level<T> &L = lv[l];
+        LevelView<T> v;
+        v.n = L.n; v.m = L.m; v.pitch = L.pitch; v.level = l;
+        v.cdiff = (T)(p.mu / (L.h * L.h));
+        v.inv_tau = (T)(p.tau > 0 ? 1.0 / p.tau : 0.0);
+        v.Sigma = (T)p.Sigma;
+        v.inv_2h = (T)(1.0 / (2.0 * L.h));
+        v.beta = (T)p.beta;
+        v.pn = L.pn; v.u = L.u; v.u0 = L.u0; v.rhs = L.rhs; v.w = L.w; v.z = L.z; v.d = L.d;
+        v.F = L.F; v.G = L.G; v.f = L.f; v.r = L.r; v.upre = L.upre; v.cls = L.cls;
+        v.has_rhs = l > 0 ? 1 : 0;
+        return v;
+    }
+
+    double h2nm(int l) const { return lv[l].h * lv[l].h / ((double)n * m); }
+
+    int init(int n_, int m_, const mg_params &p_, const mg_allocator *a, cudaStream_t s, int k) {
+        p = p_; n = n_; m = m_; nlev = p.levels;
+        mp = ModelParams{p.model, p.mu, p.lambda1, p.lambda2, p.theta, p.nu, p.eps, p.beta};
+        if (s) st = s;
+        else { CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
+        if (a && a->alloc && a->free) { al = *a; use_al = true; }
+        // layout
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+        std::vector<std::pair<void **, size_t>> plan;
+        int nn = n, mm = m;
+        for (int l = 0; l < nlev; ++l) {
+            Level<T> &L = lv[l];
+            L.n = nn; L.m = mm; L.pitch = (mm + 31) / 32 * 32; L.h = std::ldexp(1.0, l);
+            size_t fb = (size_t)L.n * L.pitch * sizeof(T);
+            T **fields[] = {&L.pn, &L.u, &L.w, &L.z, &L.d, &L.F, &L.G, &L.f, &L.r};
+            for (T **f : fields) plan.push_back({(void **)f, take(fb)});
+            if (l > 0) {
+                plan.push_back({(void **)&L.u0, take(fb)});
+                plan.push_back({(void **)&L.rhs, take(fb)});
+            }
+            if (p.smoother == MG_SMOOTH_PHASED) plan.push_back({(void **)&L.upre, take(fb)});
+            plan.push_back({(void **)&L.cls, take((size_t)L.n * L.pitch)});
+            nn /= 2; mm /= 2;
+        }
+        npart = num_partials(n, m);
+        kcap = std::max(k, 16);
+        size_t o_sc = take(sizeof(Scalars));
+        size_t o_part = take(sizeof(double) * 8 * (size_t)npart);
+        size_t o_coarse = take(sizeof(double) * coarse_scratch_doubles(lv[nlev - 1].n, lv[nlev - 1].m));
+        size_t o_mk = take(sizeof(double) * 2 * kcap);
+        size_t o_hull = take(sizeof(double) * (4 * kcap + 8));
+        pool_bytes = off;
+        if (use_al) {
+            pool = al.alloc(pool_bytes, st, al.ctx);
+            if (!pool) return fail(MG_ERR_NOMEM, "allocator returned NULL");
+        } else {
+            CK(cudaMallocAsync(&pool, pool_bytes, st));
+        }
+        CK(cudaMemsetAsync(pool, 0, pool_bytes, st));
+        char *base = (char *)pool;
+        for (auto &pr : plan) *pr.first = base + pr.second;
+        dsc = (Scalars *)(base + o_sc);
+        partials = (double *)(base + o_part);
+        coarse = (double *)(base + o_coarse);
+        dmk = (double *)(base + o_mk);
+        dhull = (double *)(base + o_hull);
+        CK(cudaMallocHost(&hsc, sizeof(Scalars)));
+        return MG_OK;
+    }
+
+    int reset(const void *image, const double *mk, int k) override {
+        if (k > kcap) return fail(MG_ERR_ARG, "more markers than at set-up");
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }   // A1 is baked into the graph
+        in_step = false;
+        steps = cycles_step = cycles_total = 0;
+        rho = eta = res0 = 0;
+        Level<T> &L0 = lv[0];
+        CK(cudaMemsetAsync(dsc, 0, sizeof(Scalars), st));
+        {
+            size_t N = (size_t)n * m;
+            int blocks = (int)std::min<size_t>((N + 255) / 256, 4096);
+            k_check_finite<<<blocks, 256, 0, st>>>(image, sizeof(T) == 8, N, &dsc->err);
+            CKL();
+            int flag = 0;
+            CK(cudaMemcpyAsync(&flag, &dsc->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (flag & 2) return fail(MG_ERR_NAN, "image has NaN or Inf values");
+        }
+        launch_copy_in<T>((const T *)image, L0.z, n, m, L0.pitch, st);
+        // blur taps (Sec. 2.2 edge detector applied to the smoothed image)
+        int R = std::min(16, (int)std::ceil(3.0 * p.sigma_blur));
+        std::vector<double> taps(2 * R + 1);
+        double s = 0;
+        for (int t = -R; t <= R; ++t) { taps[t + R] = std::exp(-(double)t * t / (2 * p.sigma_blur * p.sigma_blur)); s += taps[t + R]; }
+        for (double &t : taps) t /= s;
+        launch_blur<T>(L0.z, L0.G, L0.f, n, m, L0.pitch, L0.pitch, taps.data(), R, st);
+        CK(cudaMemcpyAsync(dmk, mk, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, st));
+        launch_edge_distance<T>(L0.f, L0.w, L0.d, n, m, L0.pitch, p.beta_edge, dmk, k, p.sigma_d, p.model, st);
+        for (int l = 1; l < nlev; ++l) {
+            Level<T> &Pf = lv[l - 1], &Lc = lv[l];
+            launch_restrict<T>(Pf.w, Pf.n, Pf.m, Pf.pitch, Lc.w, nullptr, Lc.pitch, st);
+            launch_restrict<T>(Pf.z, Pf.n, Pf.m, Pf.pitch, Lc.z, nullptr, Lc.pitch, st);
+            launch_restrict<T>(Pf.d, Pf.n, Pf.m, Pf.pitch, Lc.d, nullptr, Lc.pitch, st);
+        }
+        // initial level set: convex hull of the markers (Sec. 5)
+        std::vector<double> hull = k >= 3 ? hull_of(mk, k) : std::vector<double>();
+        int nh = (int)hull.size() / 2;
+        double area = 0;
+        for (int q = 0; q < nh; ++q) {
+            int r = (q + 1) % nh;
+            area += hull[2 * q] * hull[2 * r + 1] - hull[2 * r] * hull[2 * q + 1];
+        }
+        area *= 0.5;
+        double cx = 0, cy = 0, r0 = 0.05 * std::max(n, m);
+        if (nh < 3 || !(area > 0)) {
+            nh = 0;
+            for (int q = 0; q < k; ++q) { cx += mk[2 * q]; cy += mk[2 * q + 1]; }
+            cx /= k; cy /= k;
+            area = M_PI * r0 * r0;
+        } else {
+            CK(cudaMemcpyAsync(dhull, hull.data(), sizeof(double) * hull.size(), cudaMemcpyHostToDevice, st));
+        }
+        A1 = area;
+        launch_initial_phi<T>(L0.pn, L0.u, n, m, L0.pitch, dhull, nh, cx, cy, r0, st);
+        double A1frac = area / ((double)n * m);
+        CK(cudaMemcpyAsync(&dsc->A1frac, &A1frac, sizeof(double), cudaMemcpyHostToDevice, st));
+        launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
+        CKL();
+        CK(cudaStreamSynchronize(st));   // host marker / hull buffers go out of scope
+        return MG_OK;
+    }
+
+    int area_term(int l, const T *uin) {
+        if (p.model != MG_MODEL_RC) return MG_OK;
+        launch_area<T>(view(l), uin, p.eps, p.nu, h2nm(l), partials, num_partials(lv[l].n, lv[l].m),
+                       &dsc->area[l], dsc, st);
+        return MG_OK;
+    }
+
+    const double *area_ptr() const { return p.model == MG_MODEL_RC ? dsc->area : nullptr; }
+
+    int begin_step(double *r0out) override {
+        launch_fold<T>(view(0), st);
+        for (int l = 1; l < nlev; ++l) {
+            Level<T> &Pf = lv[l - 1], &Lc = lv[l];
+            launch_restrict<T>(Pf.pn, Pf.n, Pf.m, Pf.pitch, Lc.pn, nullptr, Lc.pitch, st);
+        }
+        for (int l = 0; l < nlev; ++l) launch_fitting<T>(view(l), dsc, mp, st);
+        area_term(0, lv[0].u);
+        launch_residual<T>(view(0), lv[0].u, area_ptr(), lv[0].r, 0, partials, npart, &dsc->norm2_0, st);
+        CKL();
+        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        res0 = std::sqrt(hsc->norm2_0);
+        if (!std::isfinite(res0)) return fail(MG_ERR_NAN, "non-finite initial residual");
+        in_step = true;
+        cycles_step = 0;
+        if (r0out) *r0out = res0;
+        return MG_OK;
+    }
+
+    // kernels per call of each enqueue helper (for the launch counter)
+    int area_launches() const { return p.model == MG_MODEL_RC ? 2 : 0; }
+    int sweep_launches() const { return p.smoother == MG_SMOOTH_PHASED ? 4 : 1; }
+
+    void smooth(int l) {
+        area_term(l, lv[l].u);
+        LevelView<T> v = view(l);
+        launch_snapshot<T>(v, area_ptr(), st);
+        for (int k = 0; k < 4; ++k) {
+            if (p.smoother == MG_SMOOTH_PHASED) launch_sweep_phased<T>(v, k, st);
+            else launch_sweep_fused<T>(v, k, st);
+        }
+        launches += area_launches() + 1 + 4 * sweep_launches();
+    }
+
+    void cycle(int l) {
+        if (l == nlev - 1) {
+            launch_coarse_solve<T>(view(l), nullptr, mp, A1 / ((double)n * m), h2nm(l), p.coarse_maxit,
+                                   p.coarse_tol, coarse, dsc, st);
+            ++launches;
+            return;
+        }
+        for (int t = 0; t < p.nu1; ++t) smooth(l);
+        Level<T> &L = lv[l], &C = lv[l + 1];
+        area_term(l, L.u);
+        launch_residual<T>(view(l), L.u, area_ptr(), L.r, 0, partials, 0, nullptr, st);
+        launch_restrict<T>(L.r, L.n, L.m, L.pitch, C.rhs, nullptr, C.pitch, st);
+        launch_restrict<T>(L.u, L.n, L.m, L.pitch, C.u, C.u0, C.pitch, st);
+        area_term(l + 1, C.u0);
+        launch_residual<T>(view(l + 1), C.u0, area_ptr(), C.rhs, 1, partials, 0, nullptr, st);
+        launches += 2 * area_launches() + 4;
+        cycle(l + 1);
+        launch_interp_add<T>(view(l), view(l + 1), st);
+        ++launches;
+        for (int t = 0; t < p.nu2; ++t) smooth(l);
+    }
+
+    void enqueue_vcycle() {
+        cycle(0);
+        area_term(0, lv[0].u);
+        launch_residual<T>(view(0), lv[0].u, area_ptr(), lv[0].r, 0, partials, npart, &dsc->norm2, st);
+        launches += area_launches() + 2;
+        cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+    }
+
+    int vcycle(double *rhoout) override {
+        if (!in_step) return fail(MG_ERR_STATE, "mg_vcycle before mg_begin_step");
+        if (p.use_graph) {
+            if (!gexec) {
+                cudaGraph_t g;
+                CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                long long before = launches;
+                enqueue_vcycle();
+                graph_nodes = launches - before;
+                launches = before;
+                cudaError_t e = cudaStreamEndCapture(st, &g);
+                if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+                e = cudaGraphInstantiate(&gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) { gexec = nullptr; return fail(MG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+            }
+            CK(cudaGraphLaunch(gexec, st));
+            launches += graph_nodes;
+        } else {
+            enqueue_vcycle();
+            CKL();
+        }
+        CK(cudaStreamSynchronize(st));
+        ++cycles_step;
+        ++cycles_total;
+        rho = res0 > 0 ? std::sqrt(hsc->norm2) / res0 : std::sqrt(hsc->norm2);
+        if (rhoout) *rhoout = rho;
+        if (hsc->err & 1) return fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
+        if (!std::isfinite(rho)) return fail(MG_ERR_NAN, "non-finite residual");
+        if (rho > 1e3) return fail(MG_ERR_DIVERGED, "residual grew by more than 1e3");
+        return MG_OK;
+    }
+
+    int end_step(double *etaout) override {
+        if (!in_step) return fail(MG_ERR_STATE, "mg_end_step before mg_begin_step");
+        launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
+        CKL();
+        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        eta = hsc->sums[5] > 0 ? std::sqrt(hsc->sums[4] / hsc->sums[5]) : std::sqrt(hsc->sums[4]);
+        ++steps;
+        in_step = false;
+        if (etaout) *etaout = eta;
+        return MG_OK;
+    }
+
+    int mask(unsigned char *out) override {
+        launch_mask<T>(view(0), out, st);
+        CKL();
+        CK(cudaStreamSynchronize(st));
+        return MG_OK;
+    }
+
+    int get_phi(void *out) override {
+        dim3 grid((m + 31) / 32, (n + 7) / 8);
+        k_phi_out<T><<<grid, dim3(32, 8), 0, st>>>(lv[0].pn, lv[0].u, n, m, lv[0].pitch, (T *)out);
+        CKL();
+        CK(cudaStreamSynchronize(st));
+        return MG_OK;
+    }
+
+    int set_phi(const void *in) override {
+        dim3 grid((m + 31) / 32, (n + 7) / 8);
+        k_phi_in<T><<<grid, dim3(32, 8), 0, st>>>((const T *)in, n, m, lv[0].pitch, lv[0].pn, lv[0].u);
+        CKL();
+        in_step = false;
+        CK(cudaStreamSynchronize(st));
+        return MG_OK;
+    }
+
+    int set_regions(double c1, double c2) override {
+        double c[2] = {c1, c2};
+        CK(cudaMemcpyAsync(&dsc->c1, c, sizeof(c), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return MG_OK;
+    }
+
+    int get_level(int l, int field, void *out) override {
+        if (l < 0 || l >= nlev || field < 0 || field > 5) return fail(MG_ERR_ARG, "level / field out of range");
+        Level<T> &L = lv[l];
+        if (field == 0) {
+            dim3 grid((L.m + 31) / 32, (L.n + 7) / 8);
+            k_phi_out<T><<<grid, dim3(32, 8), 0, st>>>(L.pn, L.u, L.n, L.m, L.pitch, (T *)out);
+        } else {
+            const T *src = field == 1 ? L.w : field == 2 ? L.z : field == 3 ? L.d : field == 4 ? L.F : L.rhs;
+            if (!src) return fail(MG_ERR_ARG, "field not stored on this level");
+            launch_copy_out<T>(src, (T *)out, L.n, L.m, L.pitch, st);
+        }
+        CKL();
+        CK(cudaStreamSynchronize(st));
+        return MG_OK;
+    }
+
+    int stats(mg_stats *s) override {
+        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        s->n = n; s->m = m; s->levels = nlev; s->precision = p.precision;
+        s->steps = steps; s->cycles_step = cycles_step; s->cycles_total = cycles_total;
+        s->picard_last = hsc->picard;
+        s->rho = rho; s->res0 = res0; s->eta = eta;
+        s->c1 = hsc->c1; s->c2 = hsc->c2; s->A1 = A1;
+        s->device_bytes = pool_bytes;
+        s->launches = launches;
+        return MG_OK;
+    }
+
+    int time_kernels(int l, int reps, double *ms) override {
+        if (l < 0 || l >= nlev || reps < 1) return fail(MG_ERR_ARG, "level / reps");
+        if (!in_step) return fail(MG_ERR_STATE, "mg_time_kernels outside a step");
+        cudaEvent_t ev[7];
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        LevelView<T> v = view(l);
+        for (int r = 0; r < reps; ++r) {
+            area_term(l, lv[l].u);
+            cudaEventRecord(ev[0], st);
+            launch_snapshot<T>(v, area_ptr(), st);
+            cudaEventRecord(ev[1], st);
+            for (int k = 0; k < 4; ++k) {
+                if (p.smoother == MG_SMOOTH_PHASED) launch_sweep_phased<T>(v, k, st);
+                else launch_sweep_fused<T>(v, k, st);
+                cudaEventRecord(ev[2 + k], st);
+            }
+            launch_residual<T>(v, lv[l].u, area_ptr(), lv[l].r, 0, partials, 0, nullptr, st);
+            cudaEventRecord(ev[6], st);
+            launches += area_launches() + 2 + 4 * sweep_launches();
+            CKL();
+            CK(cudaEventSynchronize(ev[6]));
+            for (int k = 0; k < 6; ++k) {
+                float t = 0;
+                cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+                acc[k] += t;
+            }
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        for (int k = 0; k < 6; ++k) ms[k] = acc[k] / reps;
+        return MG_OK;
+    }
+};
+
+int check_params(const mg_params *p, int n, int m) {
+    if (!p) return fail(MG_ERR_ARG, "params is NULL");
+    if (n < 1 || m < 1) return fail(MG_ERR_ARG, "image size must be positive");
+    if (p->model != MG_MODEL_SC && p->model != MG_MODEL_RC) return fail(MG_ERR_ARG, "model");
+    if (p->precision != MG_F32 && p->precision != MG_F64) return fail(MG_ERR_ARG, "precision");
+    if (p->smoother != MG_SMOOTH_FUSED && p->smoother != MG_SMOOTH_PHASED) return fail(MG_ERR_ARG, "smoother");
+    const double pos[] = {p->mu, p->eps, p->beta, p->sigma_blur, p->sigma_d};
+    for (double v : pos)
+        if (!(v > 0) || !std::isfinite(v)) return fail(MG_ERR_ARG, "mu, eps, beta, sigma_blur, sigma_d must be > 0");
+    const double nonneg[] = {p->lambda1, p->lambda2, p->theta, p->nu, p->beta_edge, p->tau};
+    for (double v : nonneg)
+        if (!(v >= 0) || !std::isfinite(v)) return fail(MG_ERR_ARG, "weights and tau must be finite and >= 0");
+    if (!(p->Sigma > 1)) return fail(MG_ERR_ARG, "Sigma must exceed 1");
+    if (p->sigma_blur > 5.0) return fail(MG_ERR_ARG, "sigma_blur above 5 px is not supported");
+    if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 > 64) return fail(MG_ERR_ARG, "nu1, nu2");
+    if (p->levels < 1 || p->levels > kMaxLevels) return fail(MG_ERR_ARG, "levels");
+    int nc = n >> (p->levels - 1), mc = m >> (p->levels - 1);
+    if (nc < 1 || mc < 1) return fail(MG_ERR_ARG, "too many levels for the image size");
+    if ((long)nc * mc > kMaxCoarseCells || std::min(nc, mc) > kMaxCoarseBand)
+        return fail(MG_ERR_ARG, "coarsest grid too large for the direct solve (use more levels)");
+    if (p->coarse_maxit < 1 || !(p->coarse_tol >= 0)) return fail(MG_ERR_ARG, "coarse_maxit / coarse_tol");
+    if (p->model == MG_MODEL_SC && p->tau == 0 && p->lambda1 == 0 && p->lambda2 == 0 && p->theta == 0)
+        return fail(MG_ERR_ARG, "degenerate model");
+    return MG_OK;
+}
+
+int check_markers(const double *mk, int k, int n, int m) {
+    if (!mk || k < 1) return fail(MG_ERR_ARG, "at least one marker is required");
+    for (int q = 0; q < k; ++q) {
+        double x = mk[2 * q], y = mk[2 * q + 1];
+        if (!std::isfinite(x) || !std::isfinite(y) || x < 0 || y < 0 || x > m - 1 || y > n - 1)
+            return fail(MG_ERR_ARG, "marker outside the image");
+    }
+    return MG_OK;
+}
+
+}  // namespace
+
+struct mg_handle_s {
+    SolverBase *s;
+};
+
+extern "C" {
+
+int mg_default_params(mg_params *p, int n, int m) {
+    if (!p) return fail(MG_ERR_ARG, "params is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->model = MG_MODEL_SC;
+    p->mu = 1.0; p->lambda1 = 10.0; p->lambda2 = 10.0; p->theta = 1.0; p->nu = 1.0;
+    p->eps = 1.0; p->beta = 1e-6; p->beta_edge = 1.0; p->sigma_blur = 1.0;
+    p->sigma_d = 0.05 * std::max(n, m);
+    p->Sigma = 2.0; p->tau = 1.0;
+    p->nu1 = 2; p->nu2 = 2;
+    int lev = 1, s = std::min(n, m);
+    while (s / 2 >= 4 && lev < 12) { s /= 2; ++lev; }
+    p->levels = lev;
+    p->precision = MG_F32; p->smoother = MG_SMOOTH_FUSED;
+    p->coarse_maxit = 100; p->coarse_tol = 1e-13; p->use_graph = 1;
+    return MG_OK;
+}
+
+int mg_setup(mg_handle *out, const void *image, int n, int m, const double *markers_xy, int k,
+             const mg_params *p, const mg_allocator *alloc, void *stream) {
+    if (!out) return fail(MG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(p, n, m);
+    if (rc) return rc;
+    if (!image) return fail(MG_ERR_ARG, "image is NULL");
+    if ((rc = check_markers(markers_xy, k, n, m))) return rc;
+    prepare_smoother_kernels();
+    SolverBase *s = nullptr;
+    if (p->precision == MG_F32) {
+        auto *t = new Solver<float>();
+        rc = t->init(n, m, *p, alloc, (cudaStream_t)stream, k);
+        s = t;
+    } else {
+        auto *t = new Solver<double>();
+        rc = t->init(n, m, *p, alloc, (cudaStream_t)stream, k);
+        s = t;
+    }
+    if (!rc) rc = s->reset(image, markers_xy, k);
+    if (rc) {
+        std::string keep = g_err;
+        delete s;
+        g_err = keep;
+        return rc;
+    }
+    *out = new mg_handle_s{s};
+    return MG_OK;
+}
+
+int mg_reset(mg_handle h, const void *image, const double *markers_xy, int k) {
+    if (!h || !image) return fail(MG_ERR_ARG, "NULL argument");
+    mg_stats s;
+    h->s->stats(&s);
+    int rc = check_markers(markers_xy, k, s.n, s.m);
+    if (rc) return rc;
+    return h->s->reset(image, markers_xy, k);
+}
+
+int mg_begin_step(mg_handle h, double *res0) { return h ? h->s->begin_step(res0) : fail(MG_ERR_ARG, "NULL handle"); }
+int mg_vcycle(mg_handle h, double *rho) { return h ? h->s->vcycle(rho) : fail(MG_ERR_ARG, "NULL handle"); }
+int mg_end_step(mg_handle h, double *eta) { return h ? h->s->end_step(eta) : fail(MG_ERR_ARG, "NULL handle"); }
+
+int mg_solve_step(mg_handle h, double tol, int max_cycles, int *cycles, double *rho) {
+    if (!h || max_cycles < 1) return fail(MG_ERR_ARG, "NULL handle or max_cycles < 1");
+    int rc = h->s->begin_step(nullptr);
+    if (rc) return rc;
+    double r = 1.0;
+    int c = 0;
+    while (c < max_cycles) {
+        rc = h->s->vcycle(&r);
+        ++c;
+        if (rc) return rc;
+        if (r <= tol) break;
+    }
+    if (cycles) *cycles = c;
+    if (rho) *rho = r;
+    rc = h->s->end_step(nullptr);
+    if (rc) return rc;
+    return r <= tol ? MG_OK : fail(MG_ERR_TIMEOUT, "cycle cap reached before the tolerance");
+}
+
+int mg_solve(mg_handle h, double tol, int max_cycles, double eta_stop, int max_steps, int *steps) {
+    if (!h || max_steps < 1) return fail(MG_ERR_ARG, "NULL handle or max_steps < 1");
+    int taken = 0;
+    for (; taken < max_steps;) {
+        int rc = mg_solve_step(h, tol, max_cycles, nullptr, nullptr);
+        ++taken;
+        if (rc && rc != MG_ERR_TIMEOUT) { if (steps) *steps = taken; return rc; }
+        mg_stats s;
+        h->s->stats(&s);
+        if (s.eta < eta_stop) break;
+    }
+    if (steps) *steps = taken;
+    return MG_OK;
+}
+
+int mg_mask(mg_handle h, unsigned char *mask) {
+    if (!h || !mask) return fail(MG_ERR_ARG, "NULL argument");
+    return h->s->mask(mask);
+}
+int mg_get_phi(mg_handle h, void *phi) { return (h && phi) ? h->s->get_phi(phi) : fail(MG_ERR_ARG, "NULL argument"); }
+int mg_set_phi(mg_handle h, const void *phi) { return (h && phi) ? h->s->set_phi(phi) : fail(MG_ERR_ARG, "NULL argument"); }
+int mg_set_regions(mg_handle h, double c1, double c2) {
+    if (!h || !std::isfinite(c1) || !std::isfinite(c2)) return fail(MG_ERR_ARG, "bad argument");
+    return h->s->set_regions(c1, c2);
+}
+int mg_get_level(mg_handle h, int level, int field, void *out) {
+    return (h && out) ? h->s->get_level(level, field, out) : fail(MG_ERR_ARG, "NULL argument");
+}
+int mg_get_stats(mg_handle h, mg_stats *s) { return (h && s) ? h->s->stats(s) : fail(MG_ERR_ARG, "NULL argument"); }
+
+int mg_segment_host(const float *image_host, int n, int m, const double *markers_xy, int k,
+                    const mg_params *p, double tol, int max_cycles, double eta_stop, int max_steps,
+                    unsigned char *mask_host, float *phi_host, mg_stats *stats) {
+    if (!image_host || !mask_host || !p) return fail(MG_ERR_ARG, "NULL argument");
+    mg_params q = *p;
+    q.precision = MG_F32;
+    int rc = check_params(&q, n, m);
+    if (rc) return rc;
+    size_t N = (size_t)n * m;
+    float *dimg = nullptr;
+    unsigned char *dmask = nullptr;
+    float *dphi = nullptr;
+    cudaStream_t st;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    mg_handle h = nullptr;
+    auto cleanup = [&]() {
+        if (h) mg_destroy(h);
+        if (dimg) cudaFree(dimg);
+        if (dmask) cudaFree(dmask);
+        if (dphi) cudaFree(dphi);
+        cudaStreamDestroy(st);
+    };
+    cudaError_t e = cudaMalloc(&dimg, N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dmask, N);
+    if (e == cudaSuccess && phi_host) e = cudaMalloc(&dphi, N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dimg, image_host, N * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { cleanup(); return fail(MG_ERR_CUDA, cudaGetErrorString(e)); }
+    rc = mg_setup(&h, dimg, n, m, markers_xy, k, &q, nullptr, st);
+    if (!rc) rc = mg_solve(h, tol, max_cycles, eta_stop, max_steps, nullptr);
+    if (!rc) rc = mg_mask(h, dmask);
+    if (!rc && phi_host) rc = mg_get_phi(h, dphi);
+    if (!rc && stats) rc = mg_get_stats(h, stats);
+    if (!rc) {
+        e = cudaMemcpy(mask_host, dmask, N, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && phi_host) e = cudaMemcpy(phi_host, dphi, N * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = fail(MG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    std::string keep = g_err;
+    cleanup();
+    g_err = keep;
+    return rc;
+}
+
+void mg_destroy(mg_handle h) {
+    if (!h) return;
+    delete h->s;
+    delete h;
+}
+
+void *mg_get_stream(mg_handle h) { return h ? (void *)h->s->stream() : nullptr; }
+
+int mg_time_kernels(mg_handle h, int level, int reps, double *ms) {
+    return (h && ms) ? h->s->time_kernels(level, reps, ms) : fail(MG_ERR_ARG, "NULL argument");
+}
+
+const char *mg_strerror(int code) {
+    switch (code) {
+        case MG_OK: return "ok";
+        case MG_ERR_ARG: return "invalid argument";
+        case MG_ERR_NAN: return "non-finite value";
+        case MG_ERR_CUDA: return "CUDA error";
+        case MG_ERR_DIVERGED: return "diverged";
+        case MG_ERR_TIMEOUT: return "iteration cap reached";
+        case MG_ERR_NOT_SPD: return "coarsest system not positive definite";
+        case MG_ERR_NOMEM: return "out of device memory";
+        case MG_ERR_STATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+const char *mg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

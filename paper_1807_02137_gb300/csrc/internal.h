@@ -1,0 +1,110 @@
+// internal.h -- shared declarations of the CUDA library behind include/segmg.h.
+//
+// Storage: every grid function of level l is an n_l x m_l row-major array with a row pitch
+// (in elements) rounded up to a multiple of 32, so rows start on 128-byte (f32) or 256-byte
+// (f64) boundaries.  The unknown of a pseudo-time step is stored split as phi = pn + u:
+// pn is phi^n restricted to the level (fixed during the step) and u the increment.  This keeps
+// FP32 differences and the time term exact to the increment's own precision instead of the
+// precision of |phi| (which reaches hundreds of pixels).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace segmg {
+
+constexpr int kChunk = 32;        // partial-line groups are cut at multiples of 32 cells
+constexpr int kMaxLevels = 16;
+constexpr int kMaxCoarseCells = 4096;
+constexpr int kMaxCoarseBand = 64;
+
+// cls byte layout: bits 0..3 = member of a partial-line group in sweep A, B, C, D;
+// bit 4 = cell in the jump set D; bits 5..6 = index of its smallest coefficient.
+constexpr uint8_t kInD = 1u << 4;
+
+template <typename T>
+struct LevelView {
+    int n, m, pitch;
+    int level;
+    T cdiff;        // mu / h^2
+    T inv_tau;      // 1 / tau (0 for tau = inf)
+    T Sigma;
+    T inv_2h;       // 1 / (2h), central differences
+    T beta;
+    T *pn, *u, *u0, *rhs, *w, *z, *d, *F, *G, *f, *r, *upre;
+    uint8_t *cls;
+    int has_rhs;    // 0 on the finest grid (zero right-hand side)
+};
+
+// Device-resident scalars (double) shared by the kernels of one handle.
+struct Scalars {
+    double c1, c2;           // region averages
+    double A1frac;           // initial polygon area / (n m)
+    double area[kMaxLevels]; // Rada-Chen area term of each level (lagged)
+    double norm2;            // sum r^2 of the last finest residual
+    double norm2_0;          // sum r^2 of L(phi^n)
+    double sums[8];          // sum H z, sum H, sum (1-H) z, sum (1-H), sum u^2, sum phi_n^2
+    double coarse_res;       // last coarsest nonlinear residual
+    int picard;              // Picard iterations of the last coarsest solve
+    int err;                 // 1 = non-positive Cholesky pivot
+};
+
+struct ModelParams {
+    int model;
+    double mu, lambda1, lambda2, theta, nu, eps, beta;
+};
+
+// ---- launchers (each enqueues on `st`) -------------------------------------------------
+
+// setup_kernels.cu
+template <typename T>
+void launch_blur(const T *src, T *tmp, T *dst, int n, int m, int pitch_src, int pitch, const double *taps,
+                 int R, cudaStream_t st);
+template <typename T>
+void launch_edge_distance(const T *zb, T *w, T *d, int n, int m, int pitch, double beta_edge,
+                          const double *mk, int k, double sigma_d, int model, cudaStream_t st);
+template <typename T>
+void launch_copy_in(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st);
+template <typename T>
+void launch_copy_out(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st);
+template <typename T>
+void launch_initial_phi(T *pn, T *u, int n, int m, int pitch, const double *hull, int nh,
+                        double cx, double cy, double r0, cudaStream_t st);
+template <typename T>
+void launch_restrict(const T *f, int n, int m, int pf, T *c, T *c2, int pc, cudaStream_t st);
+template <typename T>
+void launch_fitting(const LevelView<T> &L, const Scalars *sc, ModelParams mp, cudaStream_t st);
+template <typename T>
+void launch_fold(const LevelView<T> &L, cudaStream_t st);
+template <typename T>
+void launch_region_sums(const LevelView<T> &L, double eps, double *partials, int npart,
+                        Scalars *sc, int finalize_c, cudaStream_t st);
+template <typename T>
+void launch_mask(const LevelView<T> &L, uint8_t *mask, cudaStream_t st);
+template <typename T>
+void launch_area(const LevelView<T> &L, const T *uin, double eps, double nu, double h2_over_nm,
+                 double *partials, int npart, double *out, const Scalars *sc, cudaStream_t st);
+int num_partials(int n, int m);
+
+// smooth_kernels.cu
+template <typename T>
+void launch_snapshot(const LevelView<T> &L, const double *area, cudaStream_t st);
+template <typename T>
+void launch_sweep_fused(const LevelView<T> &L, int sweep, cudaStream_t st);
+template <typename T>
+void launch_sweep_phased(const LevelView<T> &L, int sweep, cudaStream_t st);
+
+// cycle_kernels.cu
+template <typename T>
+void launch_residual(const LevelView<T> &L, const T *uin, const double *area, T *out, int mode,
+                     double *partials, int npart, double *norm_out, cudaStream_t st);
+template <typename T>
+void launch_interp_add(const LevelView<T> &Lf, const LevelView<T> &Lc, cudaStream_t st);
+template <typename T>
+void launch_coarse_solve(const LevelView<T> &L, const double *area_dummy, ModelParams mp,
+                         double A1frac_times, double h2_over_nm, int maxit, double tol,
+                         double *scratch, Scalars *sc, cudaStream_t st);
+size_t coarse_scratch_doubles(int n, int m);
+
+}  // namespace segmg

@@ -1,0 +1,290 @@
+// setup_kernels.cu -- image-derived data (Sec. 2.2), initial level set and per-step fields
+// (Sec. 5), region averages (eq. c1c2), mask and the Rada-Chen area term.
+#include "arith.cuh"
+
+namespace segmg {
+
+namespace {
+
+__device__ __forceinline__ int mirror(int t, int n) {
+    if (n == 1) return 0;
+    while (t < 0 || t >= n) {
+        if (t < 0) t = -t - 1;
+        if (t >= n) t = 2 * n - t - 1;
+    }
+    return t;
+}
+
+struct Taps {
+    double w[33];
+};
+
+template <typename T>
+__global__ void k_copy(const T *src, int ps, T *dst, int pd, int n, int m) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i < n && j < m) dst[(size_t)i * pd + j] = src[(size_t)i * ps + j];
+}
+
+// Separable Gaussian G_sigma * z with mirror boundary; `dir` 0 = along rows, 1 = along columns.
+template <typename T>
+__global__ void k_blur(const T *src, T *dst, int n, int m, int ps, int pd, Taps tp, int R, int dir) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= n || j >= m) return;
+    double a = 0.0;
+    for (int t = -R; t <= R; ++t) {
+        double v = dir == 0 ? (double)src[(size_t)i * ps + mirror(j + t, m)]
+                            : (double)src[(size_t)mirror(i + t, n) * ps + j];
+        a += tp.w[t + R] * v;
+    }
+    dst[(size_t)i * pd + j] = (T)a;
+}
+
+// Edge detector g = 1 / (1 + beta_edge |grad (G*z)|^2) (central differences, mirror ghosts),
+// distance function d = prod_k (1 - exp(-dx^2 / 2s^2) exp(-dy^2 / 2s^2)) and the length
+// weight w = g (Spencer-Chen) or d g (Rada-Chen).
+template <typename T>
+__global__ void k_edge_distance(const T *zb, T *w, T *d, int n, int m, int p, double beta_edge,
+                                const double *mk, int k, double sigma_d, int model) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= n || j >= m) return;
+    double zx = ((double)zb[(size_t)i * p + mirror(j + 1, m)] - (double)zb[(size_t)i * p + mirror(j - 1, m)]) * 0.5;
+    double zy = ((double)zb[(size_t)mirror(i + 1, n) * p + j] - (double)zb[(size_t)mirror(i - 1, n) * p + j]) * 0.5;
+    double g = 1.0 / (1.0 + beta_edge * (zx * zx + zy * zy));
+    double s2 = 2.0 * sigma_d * sigma_d, dd = 1.0;
+    for (int q = 0; q < k; ++q) {
+        double dx = mk[2 * q] - j, dy = mk[2 * q + 1] - i;
+        dd *= 1.0 - exp(-dx * dx / s2) * exp(-dy * dy / s2);
+    }
+    size_t o = (size_t)i * p + j;
+    d[o] = (T)dd;
+    w[o] = (T)(model == 1 ? dd * g : g);
+}
+
+// Signed distance (px, positive inside) to the boundary of a convex polygon given counter-
+// clockwise, or to a circle of radius r0 about (cx, cy) when nh == 0.
+template <typename T>
+__global__ void k_initial_phi(T *pn, T *u, int n, int m, int p, const double *hull, int nh,
+                              double cx, double cy, double r0) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= n || j >= m) return;
+    double px = j, py = i, val;
+    if (nh == 0) {
+        val = r0 - sqrt((px - cx) * (px - cx) + (py - cy) * (py - cy));
+    } else {
+        double dmin = 1e300;
+        bool inside = true;
+        for (int q = 0; q < nh; ++q) {
+            int r = q + 1 == nh ? 0 : q + 1;
+            double ax = hull[2 * q], ay = hull[2 * q + 1], bx = hull[2 * r], by = hull[2 * r + 1];
+            double ex = bx - ax, ey = by - ay;
+            if (ex * (py - ay) - ey * (px - ax) < 0) inside = false;
+            double t = ((px - ax) * ex + (py - ay) * ey) / (ex * ex + ey * ey);
+            t = t < 0 ? 0 : (t > 1 ? 1 : t);
+            double dx = px - (ax + t * ex), dy = py - (ay + t * ey);
+            dmin = fmin(dmin, sqrt(dx * dx + dy * dy));
+        }
+        val = inside ? dmin : -dmin;
+    }
+    size_t o = (size_t)i * p + j;
+    pn[o] = (T)val;
+    u[o] = T(0);
+}
+
+// Fitting field of the step: lambda1 (z - c1)^2 - lambda2 (z - c2)^2 (+ theta d for SC).
+template <typename T>
+__global__ void k_fitting(LevelView<T> L, const Scalars *sc, ModelParams mp) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= L.n || j >= L.m) return;
+    size_t o = (size_t)i * L.pitch + j;
+    double z = (double)L.z[o], c1 = sc->c1, c2 = sc->c2;
+    double F = mp.lambda1 * (z - c1) * (z - c1) - mp.lambda2 * (z - c2) * (z - c2);
+    if (mp.model == 0) F += mp.theta * (double)L.d[o];
+    L.F[o] = (T)F;
+}
+
+// phi^n <- phi^n + u, u <- 0 (start of a pseudo-time step on the finest grid).
+template <typename T>
+__global__ void k_fold(LevelView<T> L) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= L.n || j >= L.m) return;
+    size_t o = (size_t)i * L.pitch + j;
+    L.pn[o] = add_rn(L.pn[o], L.u[o]);
+    L.u[o] = T(0);
+}
+
+__device__ double block_sum_setup(double v, double *red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        double s = tid < (nt + 31) / 32 ? red[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (tid == 0) red[32] = s;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
+// Per-block partial sums over 32 x 32 tiles of: H z, H, (1-H) z, (1-H), u^2, pn^2 with
+// H = H_eps(pn + u) = 1/2 + atan((pn + u) / eps) / pi (Sec. 2.1).
+template <typename T>
+__global__ void __launch_bounds__(256) k_region_partials(LevelView<T> L, double eps, double *part) {
+    __shared__ double red[33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tid = threadIdx.y * 32 + threadIdx.x;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = tid; q < 1024; q += 256) {
+        int gi = i0 + q / 32, gj = j0 + q % 32;
+        if (gi >= L.n || gj >= L.m) continue;
+        size_t o = (size_t)gi * L.pitch + gj;
+        double pn = (double)L.pn[o], u = (double)L.u[o], z = (double)L.z[o];
+        double H = 0.5 + atan((pn + u) / eps) / M_PI;
+        s[0] += H * z; s[1] += H; s[2] += (1 - H) * z; s[3] += 1 - H; s[4] += u * u; s[5] += pn * pn;
+    }
+    const int b = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+    for (int k = 0; k < 6; ++k) {
+        double v = block_sum_setup(s[k], red);
+        if (tid == 0) part[(size_t)k * nb + b] = v;
+    }
+}
+
+__global__ void k_region_final(const double *part, int nb, Scalars *sc, int set_c) {
+    __shared__ double red[33];
+    double tot[6];
+    for (int k = 0; k < 6; ++k) {
+        double v = 0.0;
+        for (int q = threadIdx.x; q < nb; q += blockDim.x) v += part[(size_t)k * nb + q];
+        tot[k] = block_sum_setup(v, red);
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) sc->sums[k] = tot[k];
+        if (set_c) {
+            sc->c1 = tot[1] > 0 ? tot[0] / tot[1] : 0.0;
+            sc->c2 = tot[3] > 0 ? tot[2] / tot[3] : 0.0;
+        }
+    }
+}
+
+// Rada-Chen area term 2 nu (h^2 sum H(pn + uin) / (n0 m0) - A1 / (n0 m0)) of one grid.
+template <typename T>
+__global__ void __launch_bounds__(256) k_area_partials(LevelView<T> L, const T *uin, double eps, double *part) {
+    __shared__ double red[33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tid = threadIdx.y * 32 + threadIdx.x;
+    double s = 0.0;
+    for (int q = tid; q < 1024; q += 256) {
+        int gi = i0 + q / 32, gj = j0 + q % 32;
+        if (gi >= L.n || gj >= L.m) continue;
+        size_t o = (size_t)gi * L.pitch + gj;
+        s += 0.5 + atan(((double)L.pn[o] + (double)uin[o]) / eps) / M_PI;
+    }
+    double v = block_sum_setup(s, red);
+    if (tid == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
+__global__ void k_area_final(const double *part, int nb, double nu, double h2nm, const Scalars *sc,
+                             double *out) {
+    __shared__ double red[33];
+    double v = 0.0;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) v += part[q];
+    double s = block_sum_setup(v, red);
+    if (threadIdx.x == 0) *out = 2.0 * nu * (h2nm * s - sc->A1frac);
+}
+
+template <typename T>
+__global__ void k_mask(LevelView<T> L, uint8_t *mask) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= L.n || j >= L.m) return;
+    size_t o = (size_t)i * L.pitch + j;
+    mask[(size_t)i * L.m + j] = add_rn(L.pn[o], L.u[o]) > T(0) ? 1 : 0;
+}
+
+inline dim3 grid2(int n, int m) { return dim3((m + 31) / 32, (n + 7) / 8); }
+
+}  // namespace
+
+template <typename T>
+void launch_copy_in(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st) {
+    k_copy<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(src, m, dst, pitch, n, m);
+}
+template <typename T>
+void launch_copy_out(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st) {
+    k_copy<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(src, pitch, dst, m, n, m);
+}
+
+template <typename T>
+void launch_blur(const T *src, T *tmp, T *dst, int n, int m, int pitch_src, int pitch, const double *taps,
+                 int R, cudaStream_t st) {
+    Taps tp;
+    for (int t = 0; t <= 2 * R && t < 33; ++t) tp.w[t] = taps[t];
+    k_blur<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(src, tmp, n, m, pitch_src, pitch, tp, R, 0);
+    k_blur<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(tmp, dst, n, m, pitch, pitch, tp, R, 1);
+}
+
+template <typename T>
+void launch_edge_distance(const T *zb, T *w, T *d, int n, int m, int pitch, double beta_edge,
+                          const double *mk, int k, double sigma_d, int model, cudaStream_t st) {
+    k_edge_distance<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(zb, w, d, n, m, pitch, beta_edge, mk, k,
+                                                            sigma_d, model);
+}
+
+template <typename T>
+void launch_initial_phi(T *pn, T *u, int n, int m, int pitch, const double *hull, int nh, double cx,
+                        double cy, double r0, cudaStream_t st) {
+    k_initial_phi<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(pn, u, n, m, pitch, hull, nh, cx, cy, r0);
+}
+
+template <typename T>
+void launch_fitting(const LevelView<T> &L, const Scalars *sc, ModelParams mp, cudaStream_t st) {
+    k_fitting<T><<<grid2(L.n, L.m), dim3(32, 8), 0, st>>>(L, sc, mp);
+}
+
+template <typename T>
+void launch_fold(const LevelView<T> &L, cudaStream_t st) {
+    k_fold<T><<<grid2(L.n, L.m), dim3(32, 8), 0, st>>>(L);
+}
+
+template <typename T>
+void launch_region_sums(const LevelView<T> &L, double eps, double *partials, int npart, Scalars *sc,
+                        int finalize_c, cudaStream_t st) {
+    dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
+    k_region_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, eps, partials);
+    k_region_final<<<1, 1024, 0, st>>>(partials, npart, sc, finalize_c);
+}
+
+template <typename T>
+void launch_area(const LevelView<T> &L, const T *uin, double eps, double nu, double h2nm,
+                 double *partials, int npart, double *out, const Scalars *sc, cudaStream_t st) {
+    dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
+    k_area_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, uin, eps, partials);
+    k_area_final<<<1, 1024, 0, st>>>(partials, npart, nu, h2nm, sc, out);
+}
+
+template <typename T>
+void launch_mask(const LevelView<T> &L, uint8_t *mask, cudaStream_t st) {
+    k_mask<T><<<grid2(L.n, L.m), dim3(32, 8), 0, st>>>(L, mask);
+}
+
+#define INST(T)                                                                                      \
+    template void launch_copy_in<T>(const T *, T *, int, int, int, cudaStream_t);                    \
+    template void launch_copy_out<T>(const T *, T *, int, int, int, cudaStream_t);                   \
+    template void launch_blur<T>(const T *, T *, T *, int, int, int, int, const double *, int,        \
+                                 cudaStream_t);                                                       \
+    template void launch_edge_distance<T>(const T *, T *, T *, int, int, int, double, const double *, \
+                                          int, double, int, cudaStream_t);                            \
+    template void launch_initial_phi<T>(T *, T *, int, int, int, const double *, int, double, double, \
+                                        double, cudaStream_t);                                        \
+    template void launch_fitting<T>(const LevelView<T> &, const Scalars *, ModelParams, cudaStream_t); \
+    template void launch_fold<T>(const LevelView<T> &, cudaStream_t);                                \
+    template void launch_region_sums<T>(const LevelView<T> &, double, double *, int, Scalars *, int,  \
+                                        cudaStream_t);                                                \
+    template void launch_area<T>(const LevelView<T> &, const T *, double, double, double, double *,  \
+                                 int, double *, const Scalars *, cudaStream_t);                       \
+    template void launch_mask<T>(const LevelView<T> &, uint8_t *, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace segmg

@@ -1,0 +1,254 @@
+"""Python binding of the C ABI in include/segmg.h (argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``_build/libsegmg.so``; this module only
+converts torch tensors / numpy arrays to pointers and error codes to exceptions.  It raises
+``RuntimeError`` if the library has not been built (``paper_1807_02137_gb300.build()``) or if no
+CUDA device is present: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import buildlib as _build
+
+MG_F32, MG_F64 = 0, 1
+MG_MODEL_SC, MG_MODEL_RC = 0, 1
+MG_SMOOTH_FUSED, MG_SMOOTH_PHASED = 0, 1
+ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4: "MG_ERR_DIVERGED",
+          -5: "MG_ERR_TIMEOUT", -6: "MG_ERR_NOT_SPD", -7: "MG_ERR_NOMEM", -8: "MG_ERR_STATE"}
+EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
+           "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
+           "mg_get_level", "mg_get_stats", "mg_segment_host", "mg_get_stream", "mg_destroy",
+           "mg_strerror", "mg_last_error", "mg_time_kernels"]
+
+
+class Params(C.Structure):
+    """Mirror of mg_params."""
+
+    _fields_ = [
+        ("model", C.c_int), ("mu", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
+        ("theta", C.c_double), ("nu", C.c_double), ("eps", C.c_double), ("beta", C.c_double),
+        ("beta_edge", C.c_double), ("sigma_blur", C.c_double), ("sigma_d", C.c_double),
+        ("Sigma", C.c_double), ("tau", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
+        ("levels", C.c_int), ("precision", C.c_int), ("smoother", C.c_int),
+        ("coarse_maxit", C.c_int), ("coarse_tol", C.c_double), ("use_graph", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    """Mirror of mg_stats."""
+
+    _fields_ = [
+        ("n", C.c_int), ("m", C.c_int), ("levels", C.c_int), ("precision", C.c_int),
+        ("steps", C.c_int), ("cycles_step", C.c_int), ("cycles_total", C.c_int),
+        ("picard_last", C.c_int), ("rho", C.c_double), ("res0", C.c_double), ("eta", C.c_double),
+        ("c1", C.c_double), ("c2", C.c_double), ("A1", C.c_double), ("device_bytes", C.c_size_t),
+        ("launches", C.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SegmgError(RuntimeError):
+    def __init__(self, code, where, detail):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({detail})")
+
+
+_lib = None
+
+
+def lib():
+    """Loads the built library (no build here: a missing library is an error)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library not built: {_build.LIB} (run paper_1807_02137_gb300.build())")
+        L = C.CDLL(_build.LIB)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        P = C.POINTER(Params)
+        D = C.POINTER(C.c_double)
+        sig = {
+            "mg_default_params": ([P, i, i], i),
+            "mg_setup": ([C.POINTER(vp), vp, i, i, D, i, P, vp, vp], i),
+            "mg_reset": ([vp, vp, D, i], i),
+            "mg_begin_step": ([vp, D], i),
+            "mg_vcycle": ([vp, D], i),
+            "mg_end_step": ([vp, D], i),
+            "mg_solve_step": ([vp, d, i, C.POINTER(i), D], i),
+            "mg_solve": ([vp, d, i, d, i, C.POINTER(i)], i),
+            "mg_mask": ([vp, vp], i),
+            "mg_get_phi": ([vp, vp], i),
+            "mg_set_phi": ([vp, vp], i),
+            "mg_set_regions": ([vp, d, d], i),
+            "mg_get_level": ([vp, i, i, vp], i),
+            "mg_get_stats": ([vp, C.POINTER(Stats)], i),
+            "mg_segment_host": ([vp, i, i, D, i, P, d, i, d, i, vp, vp, C.POINTER(Stats)], i),
+            "mg_get_stream": ([vp], vp),
+            "mg_time_kernels": ([vp, i, i, D], i),
+            "mg_destroy": ([vp], None),
+            "mg_strerror": ([i], C.c_char_p),
+            "mg_last_error": ([], C.c_char_p),
+        }
+        for name, (a, r) in sig.items():
+            f = getattr(L, name)
+            f.argtypes, f.restype = a, r
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise SegmgError(rc, where, lib().mg_last_error().decode())
+
+
+def default_params(n, m, **kw) -> Params:
+    """mg_default_params plus overrides (for example precision=MG_F64, levels=5)."""
+    p = Params()
+    _check(lib().mg_default_params(C.byref(p), n, m), "mg_default_params")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _markers(mk):
+    a = np.ascontiguousarray(np.asarray(mk, dtype=np.float64).reshape(-1, 2))
+    return a, a.ctypes.data_as(C.POINTER(C.c_double)), len(a)
+
+
+class Solver:
+    """One image's solver (mg_setup ... mg_destroy).  `image` is a CUDA torch tensor of shape
+    (n, m), float32 for MG_F32 or float64 for MG_F64."""
+
+    def __init__(self, image, markers, params: Params, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the solver has no CPU path")
+        dt = torch.float64 if params.precision == MG_F64 else torch.float32
+        if not (image.is_cuda and image.dtype == dt and image.dim() == 2):
+            raise TypeError(f"image must be a 2-D CUDA tensor of {dt}")
+        self.image = image.contiguous()
+        self.n, self.m = self.image.shape
+        self.params = params
+        self.dtype = dt
+        self._mk, pm, k = _markers(markers)
+        torch.cuda.current_stream().synchronize()
+        h = C.c_void_p()
+        st = None if stream is None else C.c_void_p(stream)
+        _check(lib().mg_setup(C.byref(h), C.c_void_p(self.image.data_ptr()), self.n, self.m, pm, k,
+                              C.byref(params), None, st), "mg_setup")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream_ptr(self) -> int:
+        return lib().mg_get_stream(self._h) or 0
+
+    def reset(self, image, markers):
+        import torch
+        img = image.contiguous()
+        _, pm, k = _markers(markers)
+        torch.cuda.current_stream().synchronize()
+        _check(lib().mg_reset(self._h, C.c_void_p(img.data_ptr()), pm, k), "mg_reset")
+
+    def begin_step(self) -> float:
+        r = C.c_double()
+        _check(lib().mg_begin_step(self._h, C.byref(r)), "mg_begin_step")
+        return r.value
+
+    def vcycle(self) -> float:
+        r = C.c_double()
+        _check(lib().mg_vcycle(self._h, C.byref(r)), "mg_vcycle")
+        return r.value
+
+    def end_step(self) -> float:
+        e = C.c_double()
+        _check(lib().mg_end_step(self._h, C.byref(e)), "mg_end_step")
+        return e.value
+
+    def solve_step(self, tol, max_cycles=50, raise_on_cap=False):
+        """One pseudo-time step; returns (cycles, rho)."""
+        c, r = C.c_int(), C.c_double()
+        rc = lib().mg_solve_step(self._h, tol, max_cycles, C.byref(c), C.byref(r))
+        if rc != 0 and (rc != -5 or raise_on_cap):
+            _check(rc, "mg_solve_step")
+        return c.value, r.value
+
+    def solve(self, tol, max_cycles, eta_stop, max_steps) -> int:
+        s = C.c_int()
+        _check(lib().mg_solve(self._h, tol, max_cycles, eta_stop, max_steps, C.byref(s)), "mg_solve")
+        return s.value
+
+    def mask(self, out=None):
+        import torch
+        out = torch.empty((self.n, self.m), dtype=torch.uint8, device=self.image.device) if out is None else out
+        _check(lib().mg_mask(self._h, C.c_void_p(out.data_ptr())), "mg_mask")
+        return out
+
+    def phi(self):
+        import torch
+        out = torch.empty((self.n, self.m), dtype=self.dtype, device=self.image.device)
+        _check(lib().mg_get_phi(self._h, C.c_void_p(out.data_ptr())), "mg_get_phi")
+        return out
+
+    def set_phi(self, phi):
+        import torch
+        t = phi.to(device=self.image.device, dtype=self.dtype).contiguous()
+        torch.cuda.current_stream().synchronize()
+        _check(lib().mg_set_phi(self._h, C.c_void_p(t.data_ptr())), "mg_set_phi")
+
+    def set_regions(self, c1, c2):
+        _check(lib().mg_set_regions(self._h, float(c1), float(c2)), "mg_set_regions")
+
+    def level(self, l, field):
+        """field: 0 phi, 1 w, 2 z, 3 d, 4 F, 5 rhs."""
+        import torch
+        names = {"phi": 0, "w": 1, "z": 2, "d": 3, "F": 4, "rhs": 5}
+        f = names.get(field, field)
+        n, m = self.n >> l, self.m >> l
+        out = torch.empty((n, m), dtype=self.dtype, device=self.image.device)
+        _check(lib().mg_get_level(self._h, l, f, C.c_void_p(out.data_ptr())), "mg_get_level")
+        return out
+
+    def time_kernels(self, level=0, reps=3):
+        """Mean ms per launch of snapshot, sweeps A..D and residual on `level` (mg_time_kernels)."""
+        out = (C.c_double * 6)()
+        _check(lib().mg_time_kernels(self._h, level, reps, out), "mg_time_kernels")
+        return list(out)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().mg_get_stats(self._h, C.byref(s)), "mg_get_stats")
+        return s.as_dict()
+
+
+def segment_host(image, markers, params: Params, tol=1e-6, max_cycles=50, eta_stop=0.0,
+                 max_steps=1, want_phi=False):
+    """Whole pipeline from host buffers (mg_segment_host): returns (mask, phi or None, stats)."""
+    img = np.ascontiguousarray(image, dtype=np.float32)
+    n, m = img.shape
+    _, pm, k = _markers(markers)
+    mask = np.empty((n, m), dtype=np.uint8)
+    phi = np.empty((n, m), dtype=np.float32) if want_phi else None
+    st = Stats()
+    _check(lib().mg_segment_host(img.ctypes.data_as(C.c_void_p), n, m, pm, k, C.byref(params), tol,
+                                 max_cycles, eta_stop, max_steps, mask.ctypes.data_as(C.c_void_p),
+                                 phi.ctypes.data_as(C.c_void_p) if want_phi else None, C.byref(st)),
+           "mg_segment_host")
+    return mask, phi, st.as_dict()

@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a and exports every function include/segmg.h declares."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "segmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(mg_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1807_02137_gb300 import buildlib
+    return buildlib.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["mg_setup", "mg_vcycle", "mg_solve", "mg_mask", "mg_destroy", "mg_get_stats",
+                 "mg_strerror", "mg_segment_host", "mg_begin_step", "mg_end_step"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (mg_\w+)", out))
+    missing = set(declared_functions()) - exported
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_matches_struct_layouts(libpath):
+    import ctypes
+    from paper_1807_02137_gb300 import segmg
+    L = segmg.lib()
+    for name in declared_functions():
+        assert hasattr(L, name)
+    # sizes of the C structs, compiled with the host compiler from the header
+    code = ('#include <stdio.h>\n#include "segmg.h"\n'
+            'int main(){printf("%zu %zu %zu", sizeof(mg_params), sizeof(mg_stats), sizeof(mg_allocator));}')
+    exe = os.path.join(os.path.dirname(libpath), "abi_sizes")
+    subprocess.run(["gcc", "-x", "c", "-", "-I", os.path.join(ROOT, "include"), "-o", exe], input=code,
+                   text=True, check=True)
+    sizes = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    assert int(sizes[0]) == ctypes.sizeof(segmg.Params)
+    assert int(sizes[1]) == ctypes.sizeof(segmg.Stats)
+
+
+def test_host_only_calls_without_a_gpu(libpath):
+    from paper_1807_02137_gb300 import segmg
+    p = segmg.default_params(1024, 1024)
+    assert p.levels == 9 and p.tau == 1.0 and p.Sigma == 2.0 and abs(p.sigma_d - 51.2) < 1e-12
+    assert segmg.lib().mg_strerror(-6) == b"coarsest system not positive definite"
+    # a NULL handle is rejected before any CUDA call
+    assert segmg.lib().mg_vcycle(None, None) == -1

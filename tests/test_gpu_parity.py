@@ -1,0 +1,192 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1807_02137_gb300 import synth
+from tests.gpu_common import gpu_solver, need_gpu, oracle_params, relmax, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def segmg():
+    return need_gpu()
+
+
+def both(segmg, image, markers, **kw):
+    s, p = gpu_solver(segmg, image, markers, **kw)
+    o = O.Solver(np.asarray(image, dtype=np.float64), markers, oracle_params(*image.shape, p))
+    return s, o, p
+
+
+@pytest.mark.parametrize("shape", [(128, 128), (100, 77), (37, 53)])
+def test_setup_fields_fp64(segmg, shape):
+    n, m = shape
+    img, mk, _ = synth.disc_square(max(n, m), 0.05, 0)
+    img = img[:n, :m].copy()
+    mk = mk[(mk[:, 0] <= m - 1) & (mk[:, 1] <= n - 1)]
+    s, o, p = both(segmg, img, mk, precision=segmg.MG_F64, levels=3)
+    for l in range(3):
+        for f in ("w", "z", "d"):
+            assert relmax(s.level(l, f).cpu().numpy(), o.level(l, f)) < 1e-13, (l, f)
+    assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-13
+    st, so = s.stats(), o.scalars()
+    assert abs(st["c1"] - so["c1"]) < 1e-12 and abs(st["c2"] - so["c2"]) < 1e-12
+    assert abs(st["A1"] - so["A1"]) < 1e-9
+
+
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_vcycles_fp64_match_oracle(segmg, smoother):
+    W = synth.workload("disc128")
+    s, o, p = both(segmg, W.image, W.markers, precision=segmg.MG_F64, levels=W.levels,
+                   smoother=smoother)
+    r0g, r0o = s.begin_step(), o.begin_step()
+    assert abs(r0g - r0o) <= 1e-12 * r0o
+    for l in range(W.levels):   # fitting field minus phi^n / tau on every grid
+        Fg = s.level(l, "F").cpu().numpy() - s.level(l, "phi").cpu().numpy() / p.tau
+        assert relmax(Fg, o.level(l, "Fn")) < 1e-12, l
+    for c in range(3):
+        rg, ro = s.vcycle(), o.vcycle()
+        assert abs(rg - ro) <= 1e-8 * ro, (c, rg, ro)
+        assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-10, c
+
+
+def test_fp64_first_step_to_1e8_matches_oracle(segmg):
+    W = synth.workload("disc128")
+    s, o, p = both(segmg, W.image, W.markers, precision=segmg.MG_F64, levels=W.levels)
+    cyc, rho = s.solve_step(W.tol, 60)
+    hist = o.solve_step(W.tol, 60)
+    o.end_step()
+    assert rho <= W.tol and hist[-1] <= W.tol
+    assert abs(cyc - len(hist)) <= 1
+    assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-9
+    st, so = s.stats(), o.scalars()
+    assert abs(st["c1"] - so["c1"]) < 1e-10 and abs(st["c2"] - so["c2"]) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_fused_and_phased_smoothers_are_bitwise_equal(segmg, precision):
+    prec = segmg.MG_F64 if precision == "f64" else segmg.MG_F32
+    img, mk, _ = synth.ellipses(200, 170, 6, (20, 80), 6, 0.05, 7)
+    outs = []
+    for sm in (0, 1):
+        s, _ = gpu_solver(segmg, img, mk, precision=prec, levels=4, smoother=sm)
+        s.begin_step()
+        for _ in range(2):
+            s.vcycle()
+        outs.append(s.phi().cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_fp32_solution_matches_oracle_small(segmg):
+    img, mk, _ = synth.ellipses(256, 256, 12, (10, 60), 8, 0.05, 11)
+    s, o, p = both(segmg, img.astype(np.float32), mk, precision=segmg.MG_F32, levels=7)
+    cyc, rho = s.solve_step(1e-6, 60)
+    hist = o.solve_step(1e-9, 80)
+    assert rho <= 1e-6 and hist[-1] <= 1e-9
+    pg, po = s.phi().cpu().numpy(), o.phi
+    assert relmax(pg, po) < 1e-5
+    assert np.mean((pg > 0) != (po > 0)) <= 1e-4
+
+
+def test_rada_chen_fp64_matches_oracle(segmg):
+    img, mk, _ = synth.disc_square(96, 0.05, 2)
+    s, o, p = both(segmg, img, mk, precision=segmg.MG_F64, levels=4, model=segmg.MG_MODEL_RC)
+    s.begin_step(); o.begin_step()
+    for c in range(3):
+        rg, ro = s.vcycle(), o.vcycle()
+        assert abs(rg - ro) <= 1e-8 * ro
+    assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-10
+
+
+def test_multi_step_fp64_with_region_update(segmg):
+    W = synth.workload("disc128")
+    s, o, p = both(segmg, W.image, W.markers, precision=segmg.MG_F64, levels=W.levels)
+    for step in range(3):
+        s.begin_step(); o.begin_step()
+        for _ in range(4):
+            s.vcycle(); o.vcycle()
+        eg, eo = s.end_step(), o.end_step()
+        assert abs(eg - eo) <= 1e-9 * eo
+    assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-9
+    m = s.mask().cpu().numpy()
+    assert np.array_equal(m.astype(bool), o.phi > 0)
+
+
+@pytest.mark.parametrize("shape,levels", [((1, 1), 1), ((2, 3), 1), ((5, 4), 2), ((33, 65), 4)])
+def test_tiny_and_ragged_grids(segmg, shape, levels):
+    n, m = shape
+    rng = np.random.default_rng(n * 100 + m)
+    img = rng.uniform(0, 1, (n, m))
+    mk = np.array([[m // 2, n // 2]], dtype=float)
+    s, o, p = both(segmg, img, mk, precision=segmg.MG_F64, levels=levels)
+    s.begin_step(); o.begin_step()
+    for _ in range(2):
+        rg, ro = s.vcycle(), o.vcycle()
+    assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-10
+
+
+def test_degenerate_markers(segmg):
+    img, _, _ = synth.disc_square(64, 0.05, 3)
+    for mk in ([[20, 30]], [[10, 10], [20, 20], [30, 30]]):
+        s, o, p = both(segmg, img, np.array(mk, float), precision=segmg.MG_F64, levels=4)
+        assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-13
+        assert abs(s.stats()["A1"] - o.scalars()["A1"]) < 1e-9
+
+
+def test_repeated_runs_are_bitwise_identical(segmg):
+    img, mk, _ = synth.ellipses(192, 192, 8, (20, 80), 6, 0.05, 5)
+    outs = []
+    for _ in range(2):
+        s, _ = gpu_solver(segmg, img, mk, levels=6)
+        s.solve_step(1e-6, 40)
+        outs.append(s.phi().cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_graph_and_eager_launches_agree(segmg):
+    img, mk, _ = synth.ellipses(160, 160, 8, (20, 60), 6, 0.05, 9)
+    outs = []
+    for g in (0, 1):
+        s, _ = gpu_solver(segmg, img, mk, levels=6, use_graph=g)
+        s.begin_step()
+        for _ in range(3):
+            s.vcycle()
+        outs.append(s.phi().cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_host_pipeline_matches_device_pipeline(segmg):
+    img, mk, _ = synth.ellipses(256, 256, 10, (20, 80), 8, 0.05, 4)
+    p = segmg.default_params(256, 256)
+    mask_h, phi_h, st = segmg.segment_host(img, mk, p, 1e-6, 50, 0.0, 1, want_phi=True)
+    s, _ = gpu_solver(segmg, img, mk)
+    s.solve_step(1e-6, 50)
+    assert np.array_equal(phi_h, s.phi().cpu().numpy())
+    assert np.array_equal(mask_h, s.mask().cpu().numpy())
+    assert st["steps"] == 1 and st["rho"] <= 1e-6
+
+
+def test_errors_are_reported_not_raised_on_the_gpu(segmg):
+    img, mk, _ = synth.disc_square(64, 0.05, 0)
+    bad = img.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(segmg.SegmgError) as e:
+        gpu_solver(segmg, bad, mk, precision=segmg.MG_F64)
+    assert e.value.code == -2
+    with pytest.raises(segmg.SegmgError) as e:
+        gpu_solver(segmg, img, np.array([[70.0, 3.0]]), precision=segmg.MG_F64)
+    assert e.value.code == -1
+    with pytest.raises(segmg.SegmgError) as e:
+        gpu_solver(segmg, img, mk, precision=segmg.MG_F64, levels=4, Sigma=0.5)
+    assert e.value.code == -1
+    with pytest.raises(segmg.SegmgError) as e:      # coarsest grid too large for the direct solve
+        gpu_solver(segmg, np.zeros((256, 256)), mk, precision=segmg.MG_F64, levels=2)
+    assert e.value.code == -1
+    s, _ = gpu_solver(segmg, img, mk, precision=segmg.MG_F64, levels=4)
+    with pytest.raises(segmg.SegmgError) as e:
+        s.vcycle()
+    assert e.value.code == -8
+    s.begin_step()
+    s.vcycle()          # the handle is still usable after a rejected call
