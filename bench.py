@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: unknowns/s to residual 1e-6 of the GB300 multigrid segmentation solver.
+
+One step = one pass of the whole method on the 1024x1024 synthetic ellipse image (FP32, 9 grids,
+V(2,2), Hybrid Smoother 2): set-up from the image and markers (blur, edge detector, distance
+function, their restrictions, initial level set, c1/c2), one pseudo-time step solved by FAS
+V-cycles until ||L(phi)|| / ||L(phi^n)|| <= 1e-6 (norms accumulated in FP64), the end-of-step
+c1/c2 update and the mask.  value = n*m / seconds per step, summed over ranks (weak scaling:
+every rank solves its own image).  The L2 (129 MB) is flushed by writing 512 MB between timed
+steps, since the 1024^2 working set (~55 MB) would otherwise stay resident.
+
+--impl reference times the FP64 C oracle (the plain CPU restatement of the paper used by the
+tests) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "unknowns/sec to residual 1e-6 (FP64 check) and smoother HBM GB/s vs peak, 1 GB300"
+UNIT = "unknowns/s"
+WORKLOAD = "ellipse1024"
+TOL = 1e-6
+MAX_CYCLES = 60
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = [r.split(",") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    import torch
+    rank, lrank = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(lrank)
+    dist.init_process_group(backend)
+    return rank, ws, lrank, dist
+
+
+def oracle_sample(img, mk, cycles_needed=None, full=False):
+    """Times the oracle on the workload: set-up, begin_step and V-cycles.  Returns a dict."""
+    import oracle as O
+    n, m = img.shape
+    p = O.params(n, m, levels=9)
+    t0 = time.perf_counter()
+    s = O.Solver(img.astype(np.float64), mk, p)
+    t1 = time.perf_counter()
+    s.begin_step()
+    t2 = time.perf_counter()
+    ts, hist = [], []
+    limit = MAX_CYCLES if full else 2
+    for _ in range(limit):
+        a = time.perf_counter()
+        hist.append(s.vcycle())
+        ts.append(time.perf_counter() - a)
+        if hist[-1] <= TOL:
+            break
+    s.close()
+    return dict(setup=t1 - t0, begin=t2 - t1, cycle=float(np.mean(ts)), cycles_run=len(hist),
+                rho=hist[-1], converged=hist[-1] <= TOL)
+
+
+def run_reference(args):
+    rank, ws, _, dist = dist_init()
+    if rank != 0:
+        return
+    from paper_1807_02137_gb300 import synth
+    W = synth.workload(WORKLOAD)
+    img, mk = W.image, W.markers
+    n, m = img.shape
+    cycles_needed = None
+    for w in range(args.warmup):
+        r = oracle_sample(img, mk, full=(w == 0))
+        if w == 0:
+            cycles_needed = r["cycles_run"]
+    if cycles_needed is None:
+        cycles_needed = 13
+    per_step = []
+    for _ in range(args.steps):
+        r = oracle_sample(img, mk)
+        per_step.append(r["setup"] + r["begin"] + cycles_needed * r["cycle"])
+    sec = float(np.mean(per_step))
+    value = n * m / sec
+    sample = (f"FP64 C oracle, 1 host core: set-up + begin_step + 2 V-cycles of the {n}x{m} workload "
+              f"per step, scaled to the {cycles_needed} V-cycles the oracle needs to reach rho <= 1e-6 "
+              f"(measured in the first warm-up step)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{WORKLOAD}: {n}x{m} FP32 image, 12 ellipses, 8 markers, 9 grids, "
+                                   f"V(2,2), tau 1, one pseudo-time step to rho <= 1e-6",
+                       "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    rank, ws, lrank, dist = dist_init()
+    import torch
+    from paper_1807_02137_gb300 import buildlib, segmg, synth
+    W = synth.workload(WORKLOAD)
+    img_np, mk = W.image.astype(np.float32), W.markers
+    n, m = img_np.shape
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r = None
+        try:
+            r = oracle_sample(img_np, mk)     # before any GPU call
+        except Exception as e:  # the baseline is a report, never a reason to fail the bench
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+        if r:
+            cpu = r
+
+    buildlib.build()
+    torch.cuda.set_device(lrank)
+    dev = torch.device("cuda", lrank)
+    p = segmg.default_params(n, m)
+    img = torch.as_tensor(img_np, device=dev)
+    s = segmg.Solver(img, mk, p)
+    st = torch.cuda.ExternalStream(s.stream_ptr, device=dev)
+    mask = torch.empty((n, m), dtype=torch.uint8, device=dev)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MB > L2
+
+    def step():
+        s.reset(img, mk)
+        c, r = s.solve_step(TOL, MAX_CYCLES)
+        s.mask(out=mask)
+        return c, r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times, cycles, rhos = [], [], []
+    l0 = s.stats()["launches"]
+    with Clocks(lrank) as clk:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            with torch.cuda.stream(st):
+                flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            c, r = step()
+            b.record(st)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            cycles.append(c)
+            rhos.append(r)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    launches = s.stats()["launches"] - l0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = float(np.mean(times))
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * n * m / (ms_max * 1e-3)
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e_ms = []
+    for k in range(0 if args.no_e2e else max(1, min(args.steps, 5)) + 1):
+        t0 = time.perf_counter()
+        segmg.segment_host(img_np, mk, p, TOL, MAX_CYCLES, 0.0, 1)
+        if k > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms_max = float(np.mean(e2e_ms)) if e2e_ms else float("nan")
+    if dist:
+        t = torch.tensor([e2e_ms_max], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms_max = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel: the fused smoother sweep on the finest grid
+    hbm, peak_kind = peaks()
+    s.reset(img, mk)
+    s.begin_step()
+    kt = s.time_kernels(0, reps=5)
+    sweep_ms = float(np.mean(kt[1:5]))
+    bytes_per_cell = 17            # u, G, f (4 B each) + cls (1 B) read, u (4 B) written
+    achieved = bytes_per_cell * n * m / (sweep_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_sweep (fused Hybrid Smoother 2 sweep, finest grid)",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
+            "bytes_per_cell": bytes_per_cell, "ms_per_launch": sweep_ms,
+            "note": "1024^2 working set is L2-resident inside a step; see roofline_hbm for 8192^2"}
+    roof_big = None
+    if not args.no_hbm_roofline:
+        try:
+            img8, mk8, _ = synth.ellipses(8192, 8192, 96, (160, 1600), 8, 0.05, 1)
+            p8 = segmg.default_params(8192, 8192)
+            s8 = segmg.Solver(torch.as_tensor(img8, device=dev), mk8, p8)
+            s8.begin_step()
+            kt8 = s8.time_kernels(0, reps=3)
+            sw8 = float(np.mean(kt8[1:5]))
+            ach8 = bytes_per_cell * 8192 * 8192 / (sw8 * 1e-3) / 1e9
+            snap_bytes = 12 + 13     # pn, u, w, F (+ halo) read; G, f, cls written
+            res_bytes = 16           # pn, u, w, F read, r written (+ 0 rhs on the finest grid)
+            roof_big = {"bound": "hbm", "grid": "8192x8192 FP32", "unit": "GB/s", "peak": hbm,
+                        "sweep": {"ms": sw8, "achieved": ach8, "frac": ach8 / hbm},
+                        "snapshot": {"ms": kt8[0], "achieved": snap_bytes * 8192 ** 2 / (kt8[0] * 1e-3) / 1e9},
+                        "residual": {"ms": kt8[5], "achieved": res_bytes * 8192 ** 2 / (kt8[5] * 1e-3) / 1e9}}
+            for k in ("snapshot", "residual"):
+                roof_big[k]["frac"] = roof_big[k]["achieved"] / hbm
+            s8.close()
+        except Exception as e:
+            roof_big = {"error": str(e)}
+
+    cpu_line = None
+    if cpu and "setup" in cpu:
+        cyc = float(np.mean(cycles))
+        sec = cpu["setup"] + cpu["begin"] + cyc * cpu["cycle"]
+        cpu_line = {"value": n * m / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": (f"FP64 C oracle on 1 host core: set-up + begin_step + 2 V-cycles of the same "
+                               f"{n}x{m} workload ({cpu['setup'] + cpu['begin'] + 2 * cpu['cycle']:.1f} s), "
+                               f"scaled to the {cyc:.1f} V-cycles per step the GPU needed")}
+    elif cpu:
+        cpu_line = cpu
+
+    h2d = n * m * 4 + mk.size * 8
+    d2h = n * m
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {n}x{m} FP32 image, 12 ellipses, 8 markers, 9 grids, "
+                                   "V(2,2), tau 1, Spencer-Chen, one pseudo-time step to rho <= 1e-6",
+                       "l2": "flushed (512 MB write) between timed steps",
+                       "cycles_per_step": float(np.mean(cycles)), "rho_last": float(max(rhos)),
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": {"value": ws * n * m / (e2e_ms_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max,
+                    "path": "mg_segment_host (host image in, host mask out; allocation and set-up included)"},
+            "gpu_launches": int(launches),
+            "roofline": roof, "roofline_hbm": roof_big,
+            "cpu_baseline": cpu_line,
+            "clocks": clk.summary(),
+            "wall_s_timed_region": t_wall}
+    print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_profile_case(args):
+    """Small profiling case for ncu: an N x N ellipse image (N = --profile), one pseudo-time step
+    started and `--cycles` V-cycles run with eager launches (no graph), nothing timed."""
+    import torch
+    from paper_1807_02137_gb300 import buildlib, segmg, synth
+    buildlib.build()
+    N = args.profile
+    img, mk, _ = synth.ellipses(N, N, max(12, 12 * N // 1024), (20 * N / 1024, 200 * N / 1024), 8,
+                                0.05, 1)
+    p = segmg.default_params(N, N, use_graph=0)
+    s = segmg.Solver(torch.as_tensor(img, device="cuda"), mk, p)
+    s.begin_step()
+    for _ in range(args.cycles):
+        r = s.vcycle()
+    print(json.dumps({"profile_case": N, "cycles": args.cycles, "rho": r, **s.stats()}), flush=True)
+    s.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hbm-roofline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", type=int, default=0, help="run the N x N ncu profiling case instead")
+    ap.add_argument("--cycles", type=int, default=2)
+    args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
