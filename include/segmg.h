@@ -182,6 +182,24 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
  * [5] the residual kernel to ms[0..5].  Changes phi like real smoothing does.  Waits. */
 int mg_time_kernels(mg_handle h, int level, int reps, double *ms);
 
+/* Residual norm ||L(phi)||_2 of one grid function, with no device allocation.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory when they need the norm,
+ * such as code whose device memory is owned by a framework's pool or a running real-time loop
+ * that may not call cudaMalloc (it synchronises the device).  It computes the same quantity, with
+ * the same arithmetic and summation order, as the reference norm of mg_begin_step for a step
+ * starting at phi (zero increment, finest grid, spacing 1, no FAS right-hand side):
+ *   phi, w, F  device, n*m dense row-major arrays of float (MG_F32) or double (MG_F64): the level
+ *              set, the length weight w and the fitting field F (mg_get_level fields 0, 1, 4);
+ *   p          uses mu, beta, model and precision; only MG_MODEL_SC is accepted;
+ *   norm       host, receives the FP64-accumulated norm;  stream may be NULL (default stream).
+ * Its scratch is one file-scope device array sized for 65,536 tiles of 32 x 32 cells (for example
+ * 8192 x 8192); larger grids get MG_ERR_ARG.  The array's device address is looked up on the
+ * first call made on each device (with that device current), so make that first call before any
+ * stream capture.  Every call shares the array: calls that overlap on the GPU race on it.  The
+ * call waits for its stream.  Errors: MG_ERR_ARG, MG_ERR_CUDA (mg_last_error is not updated). */
+int mg_residual_norm_noalloc(const void *phi, const void *w, const void *F, int n, int m,
+                             const mg_params *p, double *norm, void *stream);
+
 /* The CUDA stream (cudaStream_t) the handle enqueues its work on: the caller's stream given
  * to mg_setup, or the library's own non-blocking stream when that was NULL. */
 void *mg_get_stream(mg_handle h);

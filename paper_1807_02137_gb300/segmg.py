@@ -22,7 +22,7 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
            "mg_get_level", "mg_get_stats", "mg_segment_host", "mg_get_stream", "mg_destroy",
-           "mg_strerror", "mg_last_error", "mg_time_kernels"]
+           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc"]
 
 
 class Params(C.Structure):
@@ -90,6 +90,7 @@ def lib():
             "mg_segment_host": ([vp, i, i, D, i, P, d, i, d, i, vp, vp, C.POINTER(Stats)], i),
             "mg_get_stream": ([vp], vp),
             "mg_time_kernels": ([vp, i, i, D], i),
+            "mg_residual_norm_noalloc": ([vp, vp, vp, i, i, P, D, vp], i),
             "mg_destroy": ([vp], None),
             "mg_strerror": ([i], C.c_char_p),
             "mg_last_error": ([], C.c_char_p),
@@ -236,6 +237,19 @@ class Solver:
         s = Stats()
         _check(lib().mg_get_stats(self._h, C.byref(s)), "mg_get_stats")
         return s.as_dict()
+
+
+def residual_norm_noalloc(phi, w, F, params: Params) -> float:
+    """mg_residual_norm_noalloc on dense CUDA tensors of the params' precision (no allocation
+    inside the library)."""
+    n, m = phi.shape
+    out = C.c_double()
+    rc = lib().mg_residual_norm_noalloc(C.c_void_p(phi.data_ptr()), C.c_void_p(w.data_ptr()),
+                                        C.c_void_p(F.data_ptr()), n, m, C.byref(params),
+                                        C.byref(out), None)
+    if rc != 0:
+        raise SegmgError(rc, "mg_residual_norm_noalloc", "see include/segmg.h")
+    return out.value
 
 
 def segment_host(image, markers, params: Params, tol=1e-6, max_cycles=50, eta_stop=0.0,
