@@ -33,13 +33,18 @@ __device__ __forceinline__ T face(T gc, T gn, bool has) {
 
 // G = w / |grad phi|_beta at a cell from the four neighbour values of pn and u (central
 // differences, spacing h; mirror ghosts are supplied by the caller as clamped neighbours).
+// FP32 uses the hardware reciprocal square root (about 2 ulp); FP64 the IEEE square root and
+// division.  Every kernel that forms G uses this one function, so G is the same everywhere.
+__device__ __forceinline__ float g_of(float w, float s) { return __fmul_rn(w, rsqrtf(s)); }
+__device__ __forceinline__ double g_of(double w, double s) { return __ddiv_rn(w, __dsqrt_rn(s)); }
+
 template <typename T>
 __device__ __forceinline__ T cell_G(T w, T pS, T pN, T pE, T pW, T uS, T uN, T uE, T uW, T inv_2h,
                                     T beta) {
     T gy = mul_rn(add_rn(sub_rn(pS, pN), sub_rn(uS, uN)), inv_2h);
     T gx = mul_rn(add_rn(sub_rn(pE, pW), sub_rn(uE, uW)), inv_2h);
     T s = fma_rn(gx, gx, fma_rn(gy, gy, beta));
-    return div_rn(w, sqrt_rn(s));
+    return g_of(w, s);
 }
 
 // GSLEX-I point update (eq. gslexrc) in increment form.  With the row divided by delta the
@@ -102,6 +107,12 @@ __device__ __forceinline__ void thomas_run(int len, T cdiff, T inv_tau, T endp, 
         put(t, x);
     }
 }
+
+// Sum of squares of the residual values a thread visits: accumulated in the storage precision
+// (a handful of values per thread), then widened to FP64 for the block and grid reductions.
+// FP64 arithmetic is slow on this GPU, so the per-cell work stays in FP32 on the FP32 path.
+template <typename T>
+__device__ __forceinline__ T add_square(T acc, T r) { return fma_rn(r, r, acc); }
 
 // Member mask of one 32-cell piece of a line from its star mask (bit t = position t):
 // starred cells, plus for every starred cell without a starred neighbour its next cell, or

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_residual(LevelView<T> L, const T *uin, 
     }
     __syncthreads();
     const T ar = area ? T(area[L.level]) : T(0);
-    double acc = 0.0;
+    T acc = T(0);
     for (int q = tid; q < 1024; q += 256) {
         int ti = q / 32, tj = q % 32, a = ti + 2, b = tj + 2;
         int gi = i0 + ti, gj = j0 + tj;
@@ -98,13 +98,13 @@ __global__ void __launch_bounds__(256) k_residual(LevelView<T> L, const T *uin, 
         if (mode == 0) {
             T r = L.has_rhs ? sub_rn(L.rhs[o], Lv) : -Lv;
             out[o] = r;
-            acc += (double)r * (double)r;
+            acc = add_square(acc, r);
         } else {
             out[o] = add_rn(out[o], Lv);
         }
     }
     if (mode == 0) {
-        double s = block_sum(acc, red);
+        double s = block_sum((double)acc, red);
         if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
     }
 }
@@ -188,9 +188,11 @@ __global__ void __launch_bounds__(256) k_interp_add(LevelView<T> Lf, LevelView<T
 // value by more than 1e-14 of the largest, or maxit steps.
 // ---------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse(LevelView<T> L, ModelParams mp, double A1frac,
-                                                 double h2nm, int maxit, double tol, double *scratch,
-                                                 Scalars *sc) {
+__global__ void __launch_bounds__(256) k_coarse(LevelView<T> L, ModelParams mp, double A1frac,
+                                                double h2nm, int maxit, double tol, double *scratch,
+                                                Scalars *sc) {
+    extern __shared__ double smem_coarse[];
+    if (!scratch) scratch = smem_coarse;          // small grids: everything in shared memory
     __shared__ double red[33];
     __shared__ int s_err;
     const int n = L.n, m = L.m, p = L.pitch, N = n * m;
@@ -374,11 +376,22 @@ void launch_interp_add(const LevelView<T> &Lf, const LevelView<T> &Lc, cudaStrea
     k_interp_add<T><<<grid, block, 0, st>>>(Lf, Lc);
 }
 
+constexpr size_t kCoarseSmemMax = 200 * 1024;
+
+void prepare_coarse_kernels() {
+    cudaFuncSetAttribute(k_coarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);
+    cudaFuncSetAttribute(k_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);
+}
+
 template <typename T>
 void launch_coarse_solve(const LevelView<T> &L, const double *, ModelParams mp, double A1frac,
                          double h2nm, int maxit, double tol, double *scratch, Scalars *sc,
                          cudaStream_t st) {
-    k_coarse<T><<<1, 1024, 0, st>>>(L, mp, A1frac, h2nm, maxit, tol, scratch, sc);
+    size_t bytes = coarse_scratch_doubles(L.n, L.m) * sizeof(double);
+    if (bytes <= kCoarseSmemMax)
+        k_coarse<T><<<1, 256, bytes, st>>>(L, mp, A1frac, h2nm, maxit, tol, nullptr, sc);
+    else
+        k_coarse<T><<<1, 256, 0, st>>>(L, mp, A1frac, h2nm, maxit, tol, scratch, sc);
 }
 
 #define INST(T)                                                                                    \

@@ -573,6 +573,7 @@ int mg_setup(mg_handle *out, const void *image, int n, int m, const double *mark
     if (!image) return fail(MG_ERR_ARG, "image is NULL");
     if ((rc = check_markers(markers_xy, k, n, m))) return rc;
     prepare_smoother_kernels();
+    prepare_coarse_kernels();
     SolverBase *s = nullptr;
     if (p->precision == MG_F32) {
         auto *t = new Solver<float>();

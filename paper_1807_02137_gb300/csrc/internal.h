@@ -106,5 +106,6 @@ void launch_coarse_solve(const LevelView<T> &L, const double *area_dummy, ModelP
                          double A1frac_times, double h2_over_nm, int maxit, double tol,
                          double *scratch, Scalars *sc, cudaStream_t st);
 size_t coarse_scratch_doubles(int n, int m);
+void prepare_coarse_kernels();
 
 }  // namespace segmg

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) k_residual_static(const T *phi, const T *
         sG[a][b] = g;
     }
     __syncthreads();
-    double acc = 0.0;
+    T acc = T(0);
     for (int q = tid; q < 1024; q += 256) {
         int ti = q / 32, tj = q % 32, a = ti + 2, b = tj + 2;
         int gi = i0 + ti, gj = j0 + tj;
@@ -93,9 +93,9 @@ __global__ void __launch_bounds__(256) k_residual_static(const T *phi, const T *
         fl = fma_rn(aW, add_rn(sub_rn(sP[a][b - 1], pc), z), fl);
         T Lv = fma_rn(cdiff, fl, -add_rn(F[(size_t)gi * m + gj], z));
         T r = -Lv;
-        acc += (double)r * (double)r;
+        acc = add_square(acc, r);
     }
-    double s = block_sum_na(acc, red);
+    double s = block_sum_na((double)acc, red);
     if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 

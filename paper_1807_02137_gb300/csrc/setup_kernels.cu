@@ -45,19 +45,20 @@ __global__ void k_blur(const T *src, T *dst, int n, int m, int ps, int pd, Taps 
 template <typename T>
 __global__ void k_edge_distance(const T *zb, T *w, T *d, int n, int m, int p, double beta_edge,
                                 const double *mk, int k, double sigma_d, int model) {
+    // arithmetic in the storage precision (FP32 exp for the FP32 path)
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
     if (i >= n || j >= m) return;
-    double zx = ((double)zb[(size_t)i * p + mirror(j + 1, m)] - (double)zb[(size_t)i * p + mirror(j - 1, m)]) * 0.5;
-    double zy = ((double)zb[(size_t)mirror(i + 1, n) * p + j] - (double)zb[(size_t)mirror(i - 1, n) * p + j]) * 0.5;
-    double g = 1.0 / (1.0 + beta_edge * (zx * zx + zy * zy));
-    double s2 = 2.0 * sigma_d * sigma_d, dd = 1.0;
+    T zx = (zb[(size_t)i * p + mirror(j + 1, m)] - zb[(size_t)i * p + mirror(j - 1, m)]) * T(0.5);
+    T zy = (zb[(size_t)mirror(i + 1, n) * p + j] - zb[(size_t)mirror(i - 1, n) * p + j]) * T(0.5);
+    T g = T(1) / (T(1) + T(beta_edge) * (zx * zx + zy * zy));
+    T inv_s2 = T(1.0 / (2.0 * sigma_d * sigma_d)), dd = T(1);
     for (int q = 0; q < k; ++q) {
-        double dx = mk[2 * q] - j, dy = mk[2 * q + 1] - i;
-        dd *= 1.0 - exp(-dx * dx / s2) * exp(-dy * dy / s2);
+        T dx = T(mk[2 * q]) - T(j), dy = T(mk[2 * q + 1]) - T(i);
+        dd *= T(1) - exp(-dx * dx * inv_s2) * exp(-dy * dy * inv_s2);
     }
     size_t o = (size_t)i * p + j;
-    d[o] = (T)dd;
-    w[o] = (T)(model == 1 ? dd * g : g);
+    d[o] = dd;
+    w[o] = model == 1 ? dd * g : g;
 }
 
 // Signed distance (px, positive inside) to the boundary of a convex polygon given counter-
@@ -67,26 +68,26 @@ __global__ void k_initial_phi(T *pn, T *u, int n, int m, int p, const double *hu
                               double cx, double cy, double r0) {
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
     if (i >= n || j >= m) return;
-    double px = j, py = i, val;
+    T px = T(j), py = T(i), val;
     if (nh == 0) {
-        val = r0 - sqrt((px - cx) * (px - cx) + (py - cy) * (py - cy));
+        val = T(r0) - sqrt((px - T(cx)) * (px - T(cx)) + (py - T(cy)) * (py - T(cy)));
     } else {
-        double dmin = 1e300;
+        T dmin = T(1e30);
         bool inside = true;
         for (int q = 0; q < nh; ++q) {
             int r = q + 1 == nh ? 0 : q + 1;
-            double ax = hull[2 * q], ay = hull[2 * q + 1], bx = hull[2 * r], by = hull[2 * r + 1];
-            double ex = bx - ax, ey = by - ay;
-            if (ex * (py - ay) - ey * (px - ax) < 0) inside = false;
-            double t = ((px - ax) * ex + (py - ay) * ey) / (ex * ex + ey * ey);
-            t = t < 0 ? 0 : (t > 1 ? 1 : t);
-            double dx = px - (ax + t * ex), dy = py - (ay + t * ey);
+            T ax = T(hull[2 * q]), ay = T(hull[2 * q + 1]), bx = T(hull[2 * r]), by = T(hull[2 * r + 1]);
+            T ex = bx - ax, ey = by - ay;
+            if (ex * (py - ay) - ey * (px - ax) < T(0)) inside = false;
+            T t = ((px - ax) * ex + (py - ay) * ey) / (ex * ex + ey * ey);
+            t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+            T dx = px - (ax + t * ex), dy = py - (ay + t * ey);
             dmin = fmin(dmin, sqrt(dx * dx + dy * dy));
         }
         val = inside ? dmin : -dmin;
     }
     size_t o = (size_t)i * p + j;
-    pn[o] = (T)val;
+    pn[o] = val;
     u[o] = T(0);
 }
 
@@ -135,18 +136,18 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_region_partials(LevelView<T> L, double eps, double *part) {
     __shared__ double red[33];
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tid = threadIdx.y * 32 + threadIdx.x;
-    double s[6] = {0, 0, 0, 0, 0, 0};
+    T s[6] = {0, 0, 0, 0, 0, 0};     // per-thread sums in the storage precision (4 cells)
     for (int q = tid; q < 1024; q += 256) {
         int gi = i0 + q / 32, gj = j0 + q % 32;
         if (gi >= L.n || gj >= L.m) continue;
         size_t o = (size_t)gi * L.pitch + gj;
-        double pn = (double)L.pn[o], u = (double)L.u[o], z = (double)L.z[o];
-        double H = 0.5 + atan((pn + u) / eps) / M_PI;
-        s[0] += H * z; s[1] += H; s[2] += (1 - H) * z; s[3] += 1 - H; s[4] += u * u; s[5] += pn * pn;
+        T pn = L.pn[o], u = L.u[o], z = L.z[o];
+        T H = T(0.5) + atan((pn + u) / T(eps)) * T(M_1_PI);
+        s[0] += H * z; s[1] += H; s[2] += (T(1) - H) * z; s[3] += T(1) - H; s[4] += u * u; s[5] += pn * pn;
     }
     const int b = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
     for (int k = 0; k < 6; ++k) {
-        double v = block_sum_setup(s[k], red);
+        double v = block_sum_setup((double)s[k], red);
         if (tid == 0) part[(size_t)k * nb + b] = v;
     }
 }
@@ -173,14 +174,14 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_area_partials(LevelView<T> L, const T *uin, double eps, double *part) {
     __shared__ double red[33];
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tid = threadIdx.y * 32 + threadIdx.x;
-    double s = 0.0;
+    T s = T(0);
     for (int q = tid; q < 1024; q += 256) {
         int gi = i0 + q / 32, gj = j0 + q % 32;
         if (gi >= L.n || gj >= L.m) continue;
         size_t o = (size_t)gi * L.pitch + gj;
-        s += 0.5 + atan(((double)L.pn[o] + (double)uin[o]) / eps) / M_PI;
+        s += T(0.5) + atan((L.pn[o] + uin[o]) / T(eps)) * T(M_1_PI);
     }
-    double v = block_sum_setup(s, red);
+    double v = block_sum_setup((double)s, red);
     if (tid == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = v;
 }
 

@@ -75,16 +75,12 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
             L.G[o] = gc;
             // jump set D (Sec. 4.1): max > Sigma * min over the faces inside the domain;
             // smallest coefficient with ties to the earlier of A, B, C, D (Sec. 4.1.3).
-            T v[4] = {aS, aN, aE, aW};
-            bool h[4] = {hS, hN, hE, hW};
-            T mx = T(-1), mn = T(0);
-            int am = -1, cnt = 0;
-            for (int k = 0; k < 4; ++k) {
-                if (!h[k]) continue;
-                if (cnt == 0 || v[k] < mn) { mn = v[k]; am = k; }
-                if (v[k] > mx) mx = v[k];
-                ++cnt;
-            }
+            const T big = T(3.0e38);
+            const T vS = hS ? aS : big, vN = hN ? aN : big, vE = hE ? aE : big, vW = hW ? aW : big;
+            const T mn = fmin(fmin(vS, vN), fmin(vE, vW));
+            const T mx = fmax(fmax(hS ? aS : T(-1), hN ? aN : T(-1)), fmax(hE ? aE : T(-1), hW ? aW : T(-1)));
+            const int am = vS == mn ? 0 : (vN == mn ? 1 : (vE == mn ? 2 : 3));
+            const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
             if (cnt >= 2 && mx > mul_rn(L.Sigma, mn))
                 star = (uint8_t)((1u << am) | kInD | (am << 5));
         }
@@ -177,140 +173,181 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
 }
 
 // ---------------------------------------------------------------------------------------
-// Fused path: one kernel per sweep
+// Fused path: one kernel per sweep.  A block owns a 32 x 64 output tile (aligned to the
+// 32-cell pieces of rows and columns) and loads it with a 4-cell halo: two checkerboard phases
+// and two zebra phases each consume one cell of halo across the line direction, and the
+// checkerboard phases one cell each along it.  Shared memory holds each field split by
+// checkerboard colour (cell (a, b) of the region at [(a + b) & 1][a][b >> 1]), so the cells a
+// warp updates in one colour phase, and their neighbours, are consecutive words.
 // ---------------------------------------------------------------------------------------
-constexpr int kOH = 32, kOW = 64, kH = 4, kRH = kOH + 2 * kH, kRW = kOW + 2 * kH, kRWp = kRW + 1;
+constexpr int kOH = 32, kOW = 64, kH = 4, kRH = kOH + 2 * kH, kRW = kOW + 2 * kH, kHW = kRW / 2;
+constexpr int kMaxTasks = 72;
+
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using type = float4; static constexpr int n = 4; };
+template <> struct VecOf<double> { using type = double2; static constexpr int n = 2; };
 
 template <typename T>
 struct FusedSmem {
-    T u[kRH][kRWp];
-    T G[kRH][kRWp];
-    T f[kRH][kRWp];
-    uint8_t c[kRH][kRWp + 3];
-    T endv[72][2];
-    uint32_t mask[72];
+    T u[2][kRH][kHW];
+    T G[2][kRH][kHW];
+    T f[2][kRH][kHW];
+    uint8_t c[2][kRH][kHW + 4];
+    T endv[kMaxTasks][2];
+    uint32_t mask[kMaxTasks];
 };
+
+#define SW_AT(arr, a, b) S.arr[((a) + (b)) & 1][a][(b) >> 1]
 
 template <typename T, int SWEEP>
 __global__ void __launch_bounds__(256) k_sweep(LevelView<T> L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FusedSmem<T> &S = *reinterpret_cast<FusedSmem<T> *>(smem_raw);
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n, NV = kRW / VN, NVO = kOW / VN;
     constexpr bool rowwise = SWEEP < 2, rev = (SWEEP & 1) != 0;
     const int i0 = blockIdx.y * kOH, j0 = blockIdx.x * kOW;
     const int n = L.n, m = L.m, p = L.pitch;
-    const int tid = threadIdx.x;
-    for (int q = tid; q < kRH * kRW; q += 256) {
-        int a = q / kRW, b = q % kRW;
-        int gi = i0 - kH + a, gj = j0 - kH + b;
-        T uu = T(0), gg = T(0), ff = T(0);
-        uint8_t cc = 0xff;
-        if (gi >= 0 && gi < n && gj >= 0 && gj < m) {
-            size_t o = (size_t)gi * p + gj;
-            uu = L.u[o]; gg = L.G[o]; ff = L.f[o]; cc = L.cls[o];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // ---- load u, G, f (vectors; the region starts 16-byte aligned) and the cls bytes
+    for (int q = tid; q < kRH * NV; q += 256) {
+        const int a = q / NV, b0 = (q % NV) * VN;
+        const int gi = i0 - kH + a, gj = j0 - kH + b0;
+        T uu[VN], gg[VN], ff[VN];
+        if (gi >= 0 && gi < n && gj >= 0 && gj < p) {
+            const size_t o = (size_t)gi * p + gj;
+            V x = *reinterpret_cast<const V *>(L.u + o);
+            V y = *reinterpret_cast<const V *>(L.G + o);
+            V z = *reinterpret_cast<const V *>(L.f + o);
+            memcpy(uu, &x, sizeof(V)); memcpy(gg, &y, sizeof(V)); memcpy(ff, &z, sizeof(V));
+        } else {
+            for (int e = 0; e < VN; ++e) uu[e] = gg[e] = ff[e] = T(0);
         }
-        S.u[a][b] = uu; S.G[a][b] = gg; S.f[a][b] = ff; S.c[a][b] = cc;
+        for (int e = 0; e < VN; ++e) {
+            SW_AT(u, a, b0 + e) = uu[e];
+            SW_AT(G, a, b0 + e) = gg[e];
+            SW_AT(f, a, b0 + e) = ff[e];
+        }
+    }
+    for (int q = tid; q < kRH * (kRW / 4); q += 256) {
+        const int a = q / (kRW / 4), b0 = (q % (kRW / 4)) * 4;
+        const int gi = i0 - kH + a, gj = j0 - kH + b0;
+        uint32_t w4 = 0xffffffffu;
+        if (gi >= 0 && gi < n && gj >= 0 && gj < p) w4 = *reinterpret_cast<const uint32_t *>(L.cls + (size_t)gi * p + gj);
+        for (int e = 0; e < 4; ++e) SW_AT(c, a, b0 + e) = (uint8_t)(w4 >> (8 * e));
     }
     __syncthreads();
-    // checkerboard phases: distance 3 then 2 from the output tile
+    // ---- checkerboard phases (distance 3 then 2 from the output tile)
+#pragma unroll
     for (int ph = 0; ph < 2; ++ph) {
-        const int colour = rev ? 1 - ph : ph, lo = 1 + ph;
-        const int hgt = kRH - 2 * lo, wid = kRW - 2 * lo;
-        for (int q = tid; q < hgt * wid; q += 256) {
-            int a = lo + q / wid, b = lo + q % wid;
-            int gi = i0 - kH + a, gj = j0 - kH + b;
-            if (gi < 0 || gi >= n || gj < 0 || gj >= m || ((gi + gj) & 1) != colour) continue;
-            if ((S.c[a][b] >> SWEEP) & 1u) continue;
-            bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
-            T gc = S.G[a][b];
-            T aS = face(gc, S.G[a + 1][b], hS), aN = face(gc, S.G[a - 1][b], hN);
-            T aE = face(gc, S.G[a][b + 1], hE), aW = face(gc, S.G[a][b - 1], hW);
-            S.u[a][b] = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, S.u[a + 1][b], S.u[a - 1][b],
-                                    S.u[a][b + 1], S.u[a][b - 1], S.f[a][b]);
+        const int colour = rev ? 1 - ph : ph, lo = 1 + ph, other = 1 - colour;
+        const int R = kRH - 2 * lo;
+        for (int q = tid; q < R * kHW; q += 256) {
+            const int a = lo + q / kHW, k = q % kHW;
+            const int x = (a + colour) & 1, b = 2 * k + x;
+            if (b < lo || b >= kRW - lo) continue;
+            const int gi = i0 - kH + a, gj = j0 - kH + b;
+            if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
+            if ((S.c[colour][a][k] >> SWEEP) & 1u) continue;
+            const bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
+            const T gc = S.G[colour][a][k];
+            const T aS = face(gc, S.G[other][a + 1][k], hS), aN = face(gc, S.G[other][a - 1][k], hN);
+            const T aE = face(gc, S.G[other][a][k + x], hE), aW = face(gc, S.G[other][a][k + x - 1], hW);
+            S.u[colour][a][k] = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, S.u[other][a + 1][k],
+                                            S.u[other][a - 1][k], S.u[other][a][k + x],
+                                            S.u[other][a][k + x - 1], S.f[colour][a][k]);
         }
         __syncthreads();
     }
-    // partial-line phases: lines at distance 1, then 0, of one parity each
+    // ---- partial-line phases: lines at distance 1, then 0, one parity each
+    constexpr int npc = rowwise ? 2 : 1;
+    const int len_lim = rowwise ? m : n, gl_lim = rowwise ? n : m;
+#pragma unroll
     for (int ph = 0; ph < 2; ++ph) {
         const int parity = rev ? 1 - ph : ph, dist = 1 - ph;
-        // tasks: (line, piece).  rowwise: lines = region rows, pieces = the two 32-column
-        // pieces of the output; colwise: lines = region columns, piece = the output rows.
         const int lfirst = kH - dist;
-        const int nlin = (rowwise ? kOH : kOW) + 2 * dist;
-        const int npc = rowwise ? 2 : 1;
-        const int ntask = nlin * npc;
-        // step a: member masks and the end values at the piece boundaries (pre-phase)
-        for (int t = tid; t < ntask; t += 256) {
-            int li = lfirst + t / npc, pc = t % npc;
-            int gline = rowwise ? i0 - kH + li : j0 - kH + li;
-            uint32_t mk = 0;
-            T e0 = T(0), e1 = T(0);
-            int gl_lim = rowwise ? n : m, len_lim = rowwise ? m : n;
-            int gstart = rowwise ? j0 + 32 * pc : i0;
-            if (gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim) {
-                int len = min(32, len_lim - gstart);
-                int s0 = kH + 32 * pc;                       // region index of the piece start
-                for (int s = 0; s < len; ++s) {
-                    uint8_t cc = rowwise ? S.c[li][s0 + s] : S.c[s0 + s][li];
-                    mk |= ((cc >> SWEEP) & 1u) << s;
-                }
+        const int ntask = ((rowwise ? kOH : kOW) + 2 * dist) * npc;
+        // step a: member masks by warp ballots, end values at the piece boundaries (pre-phase)
+        for (int t = warp; t < ntask; t += 8) {
+            const int li = lfirst + t / npc, pc = t % npc;
+            const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
+            const int gstart = rowwise ? j0 + 32 * pc : i0;
+            const int s0 = kH + 32 * pc;
+            const bool ok = gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim;
+            const int len = ok ? min(32, len_lim - gstart) : 0;
+            bool bit = false;
+            if (lane < len) bit = ((rowwise ? SW_AT(c, li, s0 + lane) : SW_AT(c, s0 + lane, li)) >> SWEEP) & 1u;
+            const uint32_t mk = __ballot_sync(0xffffffffu, bit);
+            if (lane == 0) {
+                T e0 = T(0), e1 = T(0);
                 if (mk) {
-                    if (gstart > 0) e0 = rowwise ? S.u[li][s0 - 1] : S.u[s0 - 1][li];
-                    if (gstart + len < len_lim) e1 = rowwise ? S.u[li][s0 + len] : S.u[s0 + len][li];
+                    if (gstart > 0) e0 = rowwise ? SW_AT(u, li, s0 - 1) : SW_AT(u, s0 - 1, li);
+                    if (gstart + len < len_lim) e1 = rowwise ? SW_AT(u, li, s0 + len) : SW_AT(u, s0 + len, li);
                 }
+                S.mask[t] = mk;
+                S.endv[t][0] = e0;
+                S.endv[t][1] = e1;
             }
-            S.mask[t] = mk;
-            S.endv[t][0] = e0;
-            S.endv[t][1] = e1;
         }
         __syncthreads();
-        // step b: solve every run of every task
+        // step b: every run of every task, one thread per task
         for (int t = tid; t < ntask; t += 256) {
-            uint32_t mk = S.mask[t];
+            const uint32_t mk = S.mask[t];
             if (!mk) continue;
-            int li = lfirst + t / npc, pc = t % npc;
-            int s0 = kH + 32 * pc;
-            int gline = rowwise ? i0 - kH + li : j0 - kH + li;
-            int gstart = rowwise ? j0 + 32 * pc : i0;
-            int len_lim = rowwise ? m : n;
-            int len = min(32, len_lim - gstart);
+            const int li = lfirst + t / npc, pc = t % npc;
+            const int s0 = kH + 32 * pc;
+            const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
+            const int gstart = rowwise ? j0 + 32 * pc : i0;
+            const int len = min(32, len_lim - gstart);
             int s = 0;
             while (s < len) {
                 if (!((mk >> s) & 1u)) { ++s; continue; }
-                int a0 = s;
+                const int a0 = s;
                 while (s < len && ((mk >> s) & 1u)) ++s;
-                int rl = s - a0;
-                T endp = a0 == 0 ? S.endv[t][0]
-                                 : (rowwise ? S.u[li][s0 + a0 - 1] : S.u[s0 + a0 - 1][li]);
-                T endn = (a0 + rl == len) ? S.endv[t][1]
-                                          : (rowwise ? S.u[li][s0 + a0 + rl] : S.u[s0 + a0 + rl][li]);
+                const int rl = s - a0;
+                const T endp = a0 == 0 ? S.endv[t][0] : (rowwise ? SW_AT(u, li, s0 + a0 - 1) : SW_AT(u, s0 + a0 - 1, li));
+                const T endn = (a0 + rl == len) ? S.endv[t][1] : (rowwise ? SW_AT(u, li, s0 + a0 + rl) : SW_AT(u, s0 + a0 + rl, li));
                 auto at = [&](int r) -> RunCell<T> {
-                    int pos = s0 + a0 + r;
-                    int a = rowwise ? li : pos, b = rowwise ? pos : li;
-                    int gi = rowwise ? gline : i0 - kH + pos, gj = rowwise ? j0 - kH + pos : gline;
-                    bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
-                    T gc = S.G[a][b];
-                    T aS = face(gc, S.G[a + 1][b], hS), aN = face(gc, S.G[a - 1][b], hN);
-                    T aE = face(gc, S.G[a][b + 1], hE), aW = face(gc, S.G[a][b - 1], hW);
+                    const int pos = s0 + a0 + r;
+                    const int a = rowwise ? li : pos, b = rowwise ? pos : li;
+                    const int gi = rowwise ? gline : i0 - kH + pos, gj = rowwise ? j0 - kH + pos : gline;
+                    const bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
+                    const T gc = SW_AT(G, a, b);
+                    const T aS = face(gc, SW_AT(G, a + 1, b), hS), aN = face(gc, SW_AT(G, a - 1, b), hN);
+                    const T aE = face(gc, SW_AT(G, a, b + 1), hE), aW = face(gc, SW_AT(G, a, b - 1), hW);
                     RunCell<T> c;
-                    if (rowwise) { c.ap = aW; c.an = aE; c.ax1 = aS; c.ax2 = aN; c.ux1 = S.u[a + 1][b]; c.ux2 = S.u[a - 1][b]; }
-                    else         { c.ap = aN; c.an = aS; c.ax1 = aE; c.ax2 = aW; c.ux1 = S.u[a][b + 1]; c.ux2 = S.u[a][b - 1]; }
-                    c.f = S.f[a][b];
+                    if (rowwise) {
+                        c.ap = aW; c.an = aE; c.ax1 = aS; c.ax2 = aN;
+                        c.ux1 = SW_AT(u, a + 1, b); c.ux2 = SW_AT(u, a - 1, b);
+                    } else {
+                        c.ap = aN; c.an = aS; c.ax1 = aE; c.ax2 = aW;
+                        c.ux1 = SW_AT(u, a, b + 1); c.ux2 = SW_AT(u, a, b - 1);
+                    }
+                    c.f = SW_AT(f, a, b);
                     return c;
                 };
-                thomas_run<T>(rl, L.cdiff, L.inv_tau, endp, endn, at, [&](int r, T x) {
-                    int pos = s0 + a0 + r;
-                    if (rowwise) S.u[li][pos] = x; else S.u[pos][li] = x;
+                thomas_run<T>(rl, L.cdiff, L.inv_tau, endp, endn, at, [&](int r, T xv) {
+                    const int pos = s0 + a0 + r;
+                    if (rowwise) SW_AT(u, li, pos) = xv; else SW_AT(u, pos, li) = xv;
                 });
             }
         }
         __syncthreads();
     }
-    for (int q = tid; q < kOH * kOW; q += 256) {
-        int a = kH + q / kOW, b = kH + q % kOW;
-        int gi = i0 + q / kOW, gj = j0 + q % kOW;
-        if (gi < n && gj < m) L.u[(size_t)gi * p + gj] = S.u[a][b];
+    // ---- write the output tile (vectors; padding columns keep their loaded values)
+    for (int q = tid; q < kOH * NVO; q += 256) {
+        const int a = kH + q / NVO, b0 = kH + (q % NVO) * VN;
+        const int gi = i0 + q / NVO, gj = j0 + (q % NVO) * VN;
+        if (gi >= n || gj >= p) continue;
+        T uu[VN];
+        for (int e = 0; e < VN; ++e) uu[e] = SW_AT(u, a, b0 + e);
+        V x;
+        memcpy(&x, uu, sizeof(V));
+        *reinterpret_cast<V *>(L.u + (size_t)gi * p + gj) = x;
     }
 }
+
+#undef SW_AT
 
 }  // namespace
 
