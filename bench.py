@@ -249,7 +249,7 @@ def run_ours(args):
     s.begin_step()
     kt = s.time_kernels(0, reps=5)
     sweep_ms = float(np.mean(kt[1:5]))
-    bytes_per_cell = 17            # u, G, f (4 B each) + cls (1 B) read, u (4 B) written
+    bytes_per_cell = 16.125        # u, G, f (4 B each) + member masks (1/8 B) read, u (4 B) written
     achieved = bytes_per_cell * n * m / (sweep_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": "k_sweep (fused Hybrid Smoother 2 sweep, finest grid)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -266,7 +266,7 @@ def run_ours(args):
             kt8 = s8.time_kernels(0, reps=3)
             sw8 = float(np.mean(kt8[1:5]))
             ach8 = bytes_per_cell * 8192 * 8192 / (sw8 * 1e-3) / 1e9
-            snap_bytes = 12 + 13     # pn, u, w, F (+ halo) read; G, f, cls written
+            snap_bytes = 24.25       # pn, u, w, F read; G, f and member masks (1/4 B) written
             res_bytes = 16           # pn, u, w, F read, r written (+ 0 rhs on the finest grid)
             roof_big = {"bound": "hbm", "grid": "8192x8192 FP32", "unit": "GB/s", "peak": hbm,
                         "sweep": {"ms": sw8, "achieved": ach8, "frac": ach8 / hbm},
@@ -331,6 +331,82 @@ def run_profile_case(args):
     s.close()
 
 
+def run_config3(args):
+    """Mixed precision at large size (w stored in BF16, smoothing FP32, FP64 norms and coarsest
+    solve): one pseudo-time step to rho <= 1e-6 on an N x N image from the ellipse recipe
+    (200 ellipses, axes 100-3000 px, 20 markers), the smoother roofline at that size, and the
+    error against the FP64 oracle on a 2048 x 2048 crop solved as a standalone problem."""
+    import torch
+    from paper_1807_02137_gb300 import buildlib, segmg, synth
+    import oracle as O
+    buildlib.build()
+    N = args.config3
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    img, mk = synth.ellipses_device(N, N, 200, (100 * N / 25000, 3000 * N / 25000), 20, 0.05, 2, dev)
+    gen_s = time.perf_counter() - t0
+    p = segmg.default_params(N, N, precision=segmg.MG_MIXED)
+    s = segmg.Solver(img, mk, p)
+    st = torch.cuda.ExternalStream(s.stream_ptr, device=dev)
+    s.solve_step(TOL, MAX_CYCLES)                 # warm-up (graph capture)
+    times, cyc = [], []
+    with Clocks(0) as clk:
+        for _ in range(max(1, args.steps)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            s.reset(img, mk)
+            c, r = s.solve_step(TOL, MAX_CYCLES)
+            b.record(st)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            cyc.append(c)
+    hbm, _ = peaks()
+    s.reset(img, mk)
+    s.begin_step()
+    kt = s.time_kernels(0, reps=2)
+    sw = float(np.mean(kt[1:5]))
+    stats = s.stats()
+    s.close()
+    # accuracy on a crop around the markers, solved standalone by the GPU (mixed and FP32) and
+    # by the FP64 oracle
+    C = min(2048, N)
+    cx, cy = float(np.mean(mk[:, 0])), float(np.mean(mk[:, 1]))
+    j0 = int(min(max(cx - C / 2, 0), N - C)); i0 = int(min(max(cy - C / 2, 0), N - C))
+    crop = img[i0:i0 + C, j0:j0 + C].float().cpu().numpy().copy()
+    cmk = mk - np.array([j0, i0])
+    cmk = cmk[(cmk[:, 0] >= 0) & (cmk[:, 0] <= C - 1) & (cmk[:, 1] >= 0) & (cmk[:, 1] <= C - 1)]
+    del img
+    torch.cuda.empty_cache()
+    out = {}
+    for name, prec in (("mixed", segmg.MG_MIXED), ("f32", segmg.MG_F32)):
+        pc = segmg.default_params(C, C, precision=prec)
+        sc = segmg.Solver(torch.as_tensor(crop, device=dev), cmk, pc)
+        sc.solve_step(TOL, MAX_CYCLES)
+        out[name] = sc.phi().double().cpu().numpy()
+        sc.close()
+    po = O.params(C, C, levels=segmg.default_params(C, C).levels)
+    t1 = time.perf_counter()
+    so = O.Solver(crop.astype(np.float64), cmk, po)
+    hist = so.solve_step(1e-9, 80)
+    ref = so.phi
+    oracle_s = time.perf_counter() - t1
+    acc = {}
+    for name, phi in out.items():
+        acc[name] = {"max_rel_err_phi": float(np.max(np.abs(phi - ref)) / np.max(np.abs(ref))),
+                     "mask_mismatch_frac": float(np.mean((phi > 0) != (ref > 0)))}
+    line = {"config": f"{N}x{N} mixed precision (w BF16, smoothing FP32, FP64 norms/coarsest)",
+            "levels": stats["levels"], "unknowns_per_s": N * N / (np.mean(times) * 1e-3),
+            "ms_per_step": float(np.mean(times)), "cycles_per_step": float(np.mean(cyc)),
+            "device_bytes": stats["device_bytes"], "generate_s": gen_s,
+            "roofline_sweep": {"ms": sw, "achieved_GBs": 16.125 * N * N / (sw * 1e-3) / 1e9, "peak": hbm,
+                               "frac": 16.125 * N * N / (sw * 1e-3) / 1e9 / hbm},
+            "kernel_ms": {"snapshot": kt[0], "sweeps": kt[1:5], "residual": kt[5]},
+            "crop": {"size": C, "origin": [i0, j0], "markers": int(len(cmk)), "oracle_cycles": len(hist),
+                     "oracle_rho": hist[-1], "oracle_s": oracle_s, **acc},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,8 +418,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", type=int, default=0, help="run the N x N ncu profiling case instead")
     ap.add_argument("--cycles", type=int, default=2)
+    ap.add_argument("--config3", type=int, default=0, help="run the mixed-precision N x N report")
     args = ap.parse_args()
-    if args.profile:
+    if args.config3:
+        run_config3(args)
+    elif args.profile:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -20,7 +20,8 @@
  *   - markers are k pairs (x, y) = (column, row) of doubles in HOST memory;
  *   - "device" pointers are CUDA device memory owned by the caller, "host" pointers are host
  *     memory owned by the caller; the library never frees caller memory;
- *   - the element type of an image / phi buffer is float for MG_F32 and double for MG_F64;
+ *   - the element type of an image / phi buffer is float for MG_F32 and MG_MIXED, double for
+ *     MG_F64;
  *   - every function returns MG_OK (0) or a negative MG_ERR_* code; mg_strerror() names it and
  *     mg_last_error() returns the detail text of the last failure on the calling thread;
  *   - work is enqueued on the handle's stream; only calls that return host values wait for it;
@@ -48,7 +49,8 @@ enum {
 };
 
 enum { MG_MODEL_SC = 0, MG_MODEL_RC = 1 };       /* Spencer-Chen / Rada-Chen (Sec. 2.2) */
-enum { MG_F32 = 0, MG_F64 = 1 };                 /* storage and smoothing precision */
+enum { MG_F32 = 0, MG_F64 = 1, MG_MIXED = 2 };  /* storage and smoothing precision; MG_MIXED = FP32
+                                                    with the image-derived weight w held in BF16 */
 enum { MG_SMOOTH_FUSED = 0, MG_SMOOTH_PHASED = 1 };   /* one kernel per sweep / per phase */
 
 typedef struct mg_handle_s *mg_handle;
@@ -71,7 +73,8 @@ typedef struct {
     double tau;            /* pseudo-time step (px^2-time units, > 0; 0 means infinity) */
     int nu1, nu2;          /* pre- and post-smoothing outer iterations (>= 0) */
     int levels;            /* number of grids, finest included (>= 1) */
-    int precision;         /* MG_F32 or MG_F64 */
+    int precision;         /* MG_F32, MG_F64 or MG_MIXED (norms, c1/c2 sums and the coarsest
+                              solve are FP64 in every mode) */
     int smoother;          /* MG_SMOOTH_FUSED or MG_SMOOTH_PHASED (same results) */
     int coarse_maxit;      /* Picard cap of the coarsest solve (>= 1) */
     double coarse_tol;     /* relative residual target of the coarsest solve */

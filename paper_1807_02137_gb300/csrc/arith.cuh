@@ -2,8 +2,9 @@
 //
 // The fused and the per-phase smoother kernels must produce bit-identical results (the fused
 // kernel only reorganises memory traffic).  Every operation of the relaxation formulas below
-// is therefore written with explicitly rounded intrinsics, which the compiler never contracts
-// or reorders, so both kernels execute the same sequence of IEEE operations.
+// is therefore written with explicitly rounded intrinsics (or one fixed hardware approximation),
+// which the compiler never contracts or reorders, so both kernels execute the same sequence of
+// operations.
 #pragma once
 
 #include <cstdint>
@@ -23,6 +24,11 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+
+// Division in the relaxation formulas: the hardware approximate quotient in FP32 (about 2 ulp,
+// deterministic), IEEE division in FP64.  Both smoother paths call this same function.
+__device__ __forceinline__ float div_relax(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_relax(double a, double b) { return __ddiv_rn(a, b); }
 
 // Face coefficient of a face that exists: the arithmetic mean of the two cell values of
 // G = w / |grad phi|_beta (Sec. 2.2, eq. abcdrc: G_{i+1/2,j}); a boundary face carries no flux.
@@ -60,7 +66,7 @@ __device__ __forceinline__ T point_relax(T cdiff, T inv_tau, T aS, T aN, T aE, T
     num = fma_rn(aE, uE, num);
     num = fma_rn(aW, uW, num);
     T den = add_rn(add_rn(aS, aN), add_rn(aE, aW));
-    return div_rn(fma_rn(cdiff, num, -f), fma_rn(cdiff, den, inv_tau));
+    return div_relax(fma_rn(cdiff, num, -f), fma_rn(cdiff, den, inv_tau));
 }
 
 // One cell of a partial-line run: face values along the line (previous / next cell) and across
@@ -92,7 +98,7 @@ __device__ __forceinline__ void thomas_run(int len, T cdiff, T inv_tau, T endp, 
         if (t == 0) rhs = fma_rn(-lo, endp, rhs);
         if (t == len - 1) rhs = fma_rn(-up, endn, rhs);
         if (t > 0) {
-            T wgt = div_rn(lo, cdi[t - 1]);
+            T wgt = div_relax(lo, cdi[t - 1]);
             di = fma_rn(-wgt, cup[t - 1], di);
             rhs = fma_rn(-wgt, crh[t - 1], rhs);
         }
@@ -100,13 +106,26 @@ __device__ __forceinline__ void thomas_run(int len, T cdiff, T inv_tau, T endp, 
         cdi[t] = di;
         crh[t] = rhs;
     }
-    T x = div_rn(crh[len - 1], cdi[len - 1]);
+    T x = div_relax(crh[len - 1], cdi[len - 1]);
     put(len - 1, x);
     for (int t = len - 2; t >= 0; --t) {
-        x = div_rn(fma_rn(-cup[t], x, crh[t]), cdi[t]);
+        x = div_relax(fma_rn(-cup[t], x, crh[t]), cdi[t]);
         put(t, x);
     }
 }
+
+// Asynchronous global -> shared copy of one element (4 or 8 bytes); zero-fill when !pred.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem, bool pred) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int sz = pred ? (int)sizeof(T) : 0;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(sz) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Sum of squares of the residual values a thread visits: accumulated in the storage precision
 // (a handful of values per thread), then widened to FP64 for the block and grid reductions.

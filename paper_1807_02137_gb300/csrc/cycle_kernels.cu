@@ -57,24 +57,40 @@ __global__ void __launch_bounds__(256) k_residual(LevelView<T> L, const T *uin, 
     __shared__ T sP[R][R + 1];
     __shared__ T sU[R][R + 1];
     __shared__ T sG[R][R + 1];
+    // FP32 stages w and F in shared memory too; FP64 reads them from global memory
+    constexpr bool kStage = sizeof(T) == 4;
+    constexpr int RW = kStage ? R : 1, FW = kStage ? 32 : 1;
+    __shared__ T sW[RW][RW + 1];
+    __shared__ T sF[FW][FW + 1];
     __shared__ double red[33];
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int n = L.n, m = L.m, p = L.pitch;
+    // stage pn, uin (mirror-clamped), w and F with asynchronous copies (all loads in flight)
     for (int q = tid; q < R * R; q += 256) {
         int a = q / R, b = q % R;
         int gi = clampi(i0 - 2 + a, 0, n - 1), gj = clampi(j0 - 2 + b, 0, m - 1);
-        sP[a][b] = L.pn[(size_t)gi * p + gj];
-        sU[a][b] = uin[(size_t)gi * p + gj];
+        cp_async_elem(&sP[a][b], L.pn + (size_t)gi * p + gj, true);
+        cp_async_elem(&sU[a][b], uin + (size_t)gi * p + gj, true);
+        if (kStage && a >= 1 && a < R - 1 && b >= 1 && b < R - 1 && !L.wb)
+            cp_async_elem(&sW[kStage ? a : 0][kStage ? b : 0], L.w + (size_t)gi * p + gj, true);
+        if (kStage && a >= 2 && a < R - 2 && b >= 2 && b < R - 2) {
+            int fi = min(i0 - 2 + a, n - 1), fj = min(j0 - 2 + b, m - 1);
+            cp_async_elem(&sF[kStage ? a - 2 : 0][kStage ? b - 2 : 0], L.F + (size_t)fi * p + fj, true);
+        }
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
     for (int q = tid; q < 34 * 34; q += 256) {
         int a = 1 + q / 34, b = 1 + q % 34;
         int gi = i0 - 2 + a, gj = j0 - 2 + b;
         T g = T(0);
         if (gi >= 0 && gi < n && gj >= 0 && gj < m)
-            g = cell_G(L.w[(size_t)gi * p + gj], sP[a + 1][b], sP[a - 1][b], sP[a][b + 1], sP[a][b - 1],
-                       sU[a + 1][b], sU[a - 1][b], sU[a][b + 1], sU[a][b - 1], L.inv_2h, L.beta);
+            g = cell_G((L.wb || !kStage) ? weight_at(L, (size_t)gi * p + gj) : sW[kStage ? a : 0][kStage ? b : 0],
+                       sP[a + 1][b], sP[a - 1][b],
+                       sP[a][b + 1], sP[a][b - 1], sU[a + 1][b], sU[a - 1][b], sU[a][b + 1], sU[a][b - 1],
+                       L.inv_2h, L.beta);
         sG[a][b] = g;
     }
     __syncthreads();
@@ -94,7 +110,8 @@ __global__ void __launch_bounds__(256) k_residual(LevelView<T> L, const T *uin, 
         fl = fma_rn(aE, add_rn(sub_rn(sP[a][b + 1], pc), sub_rn(sU[a][b + 1], uc)), fl);
         fl = fma_rn(aW, add_rn(sub_rn(sP[a][b - 1], pc), sub_rn(sU[a][b - 1], uc)), fl);
         size_t o = (size_t)gi * p + gj;
-        T Lv = sub_rn(fma_rn(L.cdiff, fl, -add_rn(L.F[o], ar)), mul_rn(L.inv_tau, uc));
+        T Fv = kStage ? sF[kStage ? ti : 0][kStage ? tj : 0] : L.F[o];
+        T Lv = sub_rn(fma_rn(L.cdiff, fl, -add_rn(Fv, ar)), mul_rn(L.inv_tau, uc));
         if (mode == 0) {
             T r = L.has_rhs ? sub_rn(L.rhs[o], Lv) : -Lv;
             out[o] = r;
@@ -224,7 +241,7 @@ __global__ void __launch_bounds__(256) k_coarse(LevelView<T> L, ModelParams mp, 
             int iS = min(i + 1, n - 1), iN = max(i - 1, 0), jE = min(j + 1, m - 1), jW = max(j - 1, 0);
             double gy = (x[idx(iS, j)] - x[idx(iN, j)]) * inv_2h;
             double gx = (x[idx(i, jE)] - x[idx(i, jW)]) * inv_2h;
-            G[idx(i, j)] = (double)L.w[(size_t)i * p + j] / sqrt(gx * gx + gy * gy + beta);
+            G[idx(i, j)] = (double)weight_at(L, (size_t)i * p + j) / sqrt(gx * gx + gy * gy + beta);
         }
         __syncthreads();
         return area;

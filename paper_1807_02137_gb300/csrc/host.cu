@@ -110,7 +110,8 @@ struct Level {
     double h = 1;
     T *pn = nullptr, *u = nullptr, *u0 = nullptr, *rhs = nullptr, *w = nullptr, *z = nullptr, *d = nullptr;
     T *F = nullptr, *G = nullptr, *f = nullptr, *r = nullptr, *upre = nullptr;
-    uint8_t *cls = nullptr;
+    uint32_t *mrow = nullptr, *mcol = nullptr;
+    __nv_bfloat16 *wb = nullptr;   // mixed precision only
 };
 
 template <typename T>
@@ -169,7 +170,9 @@ struct Solver final : SolverBase {
         v.inv_2h = (T)(1.0 / (2.0 * L.h));
         v.beta = (T)p.beta;
         v.pn = L.pn; v.u = L.u; v.u0 = L.u0; v.rhs = L.rhs; v.w = L.w; v.z = L.z; v.d = L.d;
-        v.F = L.F; v.G = L.G; v.f = L.f; v.r = L.r; v.upre = L.upre; v.cls = L.cls;
+        v.F = L.F; v.G = L.G; v.f = L.f; v.r = L.r; v.upre = L.upre;
+        v.mrow = L.mrow; v.mcol = L.mcol; v.npm = (L.m + 31) / 32; v.npn = (L.n + 31) / 32;
+        v.wb = L.wb;
         v.has_rhs = l > 0 ? 1 : 0;
         return v;
     }
@@ -198,7 +201,9 @@ struct Solver final : SolverBase {
                 plan.push_back({(void **)&L.rhs, take(fb)});
             }
             if (p.smoother == MG_SMOOTH_PHASED) plan.push_back({(void **)&L.upre, take(fb)});
-            plan.push_back({(void **)&L.cls, take((size_t)L.n * L.pitch)});
+            if (p.precision == MG_MIXED) plan.push_back({(void **)&L.wb, take((size_t)L.n * L.pitch * 2)});
+            plan.push_back({(void **)&L.mrow, take(sizeof(uint32_t) * 2 * (size_t)L.n * ((L.m + 31) / 32))});
+            plan.push_back({(void **)&L.mcol, take(sizeof(uint32_t) * 2 * (size_t)L.m * ((L.n + 31) / 32))});
             nn /= 2; mm /= 2;
         }
         npart = num_partials(n, m);
@@ -261,6 +266,9 @@ struct Solver final : SolverBase {
             launch_restrict<T>(Pf.z, Pf.n, Pf.m, Pf.pitch, Lc.z, nullptr, Lc.pitch, st);
             launch_restrict<T>(Pf.d, Pf.n, Pf.m, Pf.pitch, Lc.d, nullptr, Lc.pitch, st);
         }
+        if (p.precision == MG_MIXED)   // w in BF16 on every grid (restricted in FP32 first)
+            for (int l = 0; l < nlev; ++l)
+                launch_to_bf16((const float *)lv[l].w, lv[l].wb, lv[l].n, lv[l].m, lv[l].pitch, st);
         // initial level set: convex hull of the markers (Sec. 5)
         std::vector<double> hull = k >= 3 ? hull_of(mk, k) : std::vector<double>();
         int nh = (int)hull.size() / 2;
@@ -507,7 +515,8 @@ int check_params(const mg_params *p, int n, int m) {
     if (!p) return fail(MG_ERR_ARG, "params is NULL");
     if (n < 1 || m < 1) return fail(MG_ERR_ARG, "image size must be positive");
     if (p->model != MG_MODEL_SC && p->model != MG_MODEL_RC) return fail(MG_ERR_ARG, "model");
-    if (p->precision != MG_F32 && p->precision != MG_F64) return fail(MG_ERR_ARG, "precision");
+    if (p->precision != MG_F32 && p->precision != MG_F64 && p->precision != MG_MIXED)
+        return fail(MG_ERR_ARG, "precision");
     if (p->smoother != MG_SMOOTH_FUSED && p->smoother != MG_SMOOTH_PHASED) return fail(MG_ERR_ARG, "smoother");
     const double pos[] = {p->mu, p->eps, p->beta, p->sigma_blur, p->sigma_d};
     for (double v : pos)
@@ -575,7 +584,7 @@ int mg_setup(mg_handle *out, const void *image, int n, int m, const double *mark
     prepare_smoother_kernels();
     prepare_coarse_kernels();
     SolverBase *s = nullptr;
-    if (p->precision == MG_F32) {
+    if (p->precision != MG_F64) {
         auto *t = new Solver<float>();
         rc = t->init(n, m, *p, alloc, (cudaStream_t)stream, k);
         s = t;
@@ -662,7 +671,7 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
                     unsigned char *mask_host, float *phi_host, mg_stats *stats) {
     if (!image_host || !mask_host || !p) return fail(MG_ERR_ARG, "NULL argument");
     mg_params q = *p;
-    q.precision = MG_F32;
+    if (q.precision == MG_F64) q.precision = MG_F32;
     int rc = check_params(&q, n, m);
     if (rc) return rc;
     size_t N = (size_t)n * m;

@@ -10,6 +10,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace segmg {
@@ -19,9 +20,10 @@ constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarseCells = 4096;
 constexpr int kMaxCoarseBand = 64;
 
-// cls byte layout: bits 0..3 = member of a partial-line group in sweep A, B, C, D;
-// bit 4 = cell in the jump set D; bits 5..6 = index of its smallest coefficient.
-constexpr uint8_t kInD = 1u << 4;
+// Partial-line group membership is stored as one 32-bit mask per 32-cell piece of a line:
+// mrow[(k * n + i) * npm + (j >> 5)] bit (j & 31) for sweeps A (k = 0) and B (k = 1) along row
+// i, and mcol[(k * m + j) * npn + (i >> 5)] bit (i & 31) for sweeps C (k = 0) and D (k = 1)
+// along column j (npm = ceil(m / 32), npn = ceil(n / 32)).
 
 template <typename T>
 struct LevelView {
@@ -33,7 +35,9 @@ struct LevelView {
     T inv_2h;       // 1 / (2h), central differences
     T beta;
     T *pn, *u, *u0, *rhs, *w, *z, *d, *F, *G, *f, *r, *upre;
-    uint8_t *cls;
+    uint32_t *mrow, *mcol;     // member masks (see above)
+    int npm, npn;
+    const __nv_bfloat16 *wb;   // mixed precision: the length weight w stored in BF16 (else NULL)
     int has_rhs;    // 0 on the finest grid (zero right-hand side)
 };
 
@@ -54,6 +58,19 @@ struct ModelParams {
     int model;
     double mu, lambda1, lambda2, theta, nu, eps, beta;
 };
+
+// Member bit of cell (i, j) in sweep 0..3 (A, B, C, D).
+template <typename T>
+__device__ __forceinline__ bool member_bit(const LevelView<T> &L, int sweep, int i, int j) {
+    if (sweep < 2) return (L.mrow[((size_t)sweep * L.n + i) * L.npm + (j >> 5)] >> (j & 31)) & 1u;
+    return (L.mcol[((size_t)(sweep - 2) * L.m + j) * L.npn + (i >> 5)] >> (i & 31)) & 1u;
+}
+
+// The length weight w of cell o: BF16 storage in mixed precision, else the storage type.
+template <typename T>
+__device__ __forceinline__ T weight_at(const LevelView<T> &L, size_t o) {
+    return L.wb ? T(__bfloat162float(L.wb[o])) : L.w[o];
+}
 
 // ---- launchers (each enqueues on `st`) -------------------------------------------------
 
@@ -82,6 +99,7 @@ void launch_region_sums(const LevelView<T> &L, double eps, double *partials, int
                         Scalars *sc, int finalize_c, cudaStream_t st);
 template <typename T>
 void launch_mask(const LevelView<T> &L, uint8_t *mask, cudaStream_t st);
+void launch_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, int pitch, cudaStream_t st);
 template <typename T>
 void launch_area(const LevelView<T> &L, const T *uin, double eps, double nu, double h2_over_nm,
                  double *partials, int npart, double *out, const Scalars *sc, cudaStream_t st);

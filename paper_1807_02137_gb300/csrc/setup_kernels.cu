@@ -202,6 +202,11 @@ __global__ void k_mask(LevelView<T> L, uint8_t *mask) {
     mask[(size_t)i * L.m + j] = add_rn(L.pn[o], L.u[o]) > T(0) ? 1 : 0;
 }
 
+__global__ void k_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, int p) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    if (i < n && j < m) dst[(size_t)i * p + j] = __float2bfloat16_rn(src[(size_t)i * p + j]);
+}
+
 inline dim3 grid2(int n, int m) { return dim3((m + 31) / 32, (n + 7) / 8); }
 
 }  // namespace
@@ -266,6 +271,10 @@ void launch_area(const LevelView<T> &L, const T *uin, double eps, double nu, dou
 template <typename T>
 void launch_mask(const LevelView<T> &L, uint8_t *mask, cudaStream_t st) {
     k_mask<T><<<grid2(L.n, L.m), dim3(32, 8), 0, st>>>(L, mask);
+}
+
+void launch_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, int pitch, cudaStream_t st) {
+    k_to_bf16<<<grid2(n, m), dim3(32, 8), 0, st>>>(src, dst, n, m, pitch);
 }
 
 #define INST(T)                                                                                      \

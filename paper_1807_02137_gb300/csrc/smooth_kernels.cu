@@ -22,8 +22,8 @@ namespace {
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ---------------------------------------------------------------------------------------
-// Snapshot: G, f and the cls byte of every cell (32 x 32 tiles aligned to the 32-cell pieces
-// of rows and columns, so every piece of every line lies inside exactly one tile).
+// Snapshot: G and f of every cell and the member mask of every 32-cell piece of every row and
+// column (32 x 32 tiles aligned to the pieces, so each piece lies inside exactly one tile).
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *area) {
@@ -31,25 +31,45 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
     __shared__ T sP[R][R + 1];
     __shared__ T sU[R][R + 1];
     __shared__ T sG[R][R + 1];
+    // FP32 stages w, F and rhs in shared memory too; FP64 reads them from global memory (its
+    // static shared memory would otherwise exceed 48 KB)
+    constexpr bool kStage = sizeof(T) == 4;
+    constexpr int RW = kStage ? R : 1, FW = kStage ? 32 : 1;
+    __shared__ T sW[RW][RW + 1];
+    __shared__ T sF[FW][FW + 1];
+    __shared__ T sR[FW][FW + 1];
     __shared__ uint8_t sStar[32][33];
-    __shared__ uint8_t sMem[32][33];
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int n = L.n, m = L.m, p = L.pitch;
+    // stage pn, u (mirror-clamped, 36 x 36), w (34 x 34) and F, rhs (32 x 32) with asynchronous
+    // copies so that all of the tile's loads are in flight together
     for (int q = tid; q < R * R; q += 256) {
         int a = q / R, b = q % R;
         int gi = clampi(i0 - 2 + a, 0, n - 1), gj = clampi(j0 - 2 + b, 0, m - 1);
-        sP[a][b] = L.pn[(size_t)gi * p + gj];
-        sU[a][b] = L.u[(size_t)gi * p + gj];
+        cp_async_elem(&sP[a][b], L.pn + (size_t)gi * p + gj, true);
+        cp_async_elem(&sU[a][b], L.u + (size_t)gi * p + gj, true);
+        if (kStage && a >= 1 && a < R - 1 && b >= 1 && b < R - 1 && !L.wb)
+            cp_async_elem(&sW[kStage ? a : 0][kStage ? b : 0], L.w + (size_t)gi * p + gj, true);
+        if (kStage && a >= 2 && a < R - 2 && b >= 2 && b < R - 2) {
+            int fi = min(i0 - 2 + a, n - 1), fj = min(j0 - 2 + b, m - 1);
+            cp_async_elem(&sF[kStage ? a - 2 : 0][kStage ? b - 2 : 0], L.F + (size_t)fi * p + fj, true);
+            if (L.has_rhs)
+                cp_async_elem(&sR[kStage ? a - 2 : 0][kStage ? b - 2 : 0], L.rhs + (size_t)fi * p + fj, true);
+        }
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
     for (int q = tid; q < 34 * 34; q += 256) {
         int a = 1 + q / 34, b = 1 + q % 34;
         int gi = i0 - 2 + a, gj = j0 - 2 + b;
         T g = T(0);
         if (gi >= 0 && gi < n && gj >= 0 && gj < m)
-            g = cell_G(L.w[(size_t)gi * p + gj], sP[a + 1][b], sP[a - 1][b], sP[a][b + 1], sP[a][b - 1],
-                       sU[a + 1][b], sU[a - 1][b], sU[a][b + 1], sU[a][b - 1], L.inv_2h, L.beta);
+            g = cell_G((L.wb || !kStage) ? weight_at(L, (size_t)gi * p + gj) : sW[kStage ? a : 0][kStage ? b : 0],
+                       sP[a + 1][b], sP[a - 1][b],
+                       sP[a][b + 1], sP[a][b - 1], sU[a + 1][b], sU[a - 1][b], sU[a][b + 1], sU[a][b - 1],
+                       L.inv_2h, L.beta);
         sG[a][b] = g;
     }
     __syncthreads();
@@ -69,8 +89,8 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
             ds = fma_rn(aE, sub_rn(sP[a][b + 1], pc), ds);
             ds = fma_rn(aW, sub_rn(sP[a][b - 1], pc), ds);
             size_t o = (size_t)gi * p + gj;
-            T base = add_rn(L.F[o], ar);
-            if (L.has_rhs) base = add_rn(base, L.rhs[o]);
+            T base = add_rn(kStage ? sF[kStage ? ti : 0][kStage ? tj : 0] : L.F[o], ar);
+            if (L.has_rhs) base = add_rn(base, kStage ? sR[kStage ? ti : 0][kStage ? tj : 0] : L.rhs[o]);
             L.f[o] = fma_rn(-L.cdiff, ds, base);
             L.G[o] = gc;
             // jump set D (Sec. 4.1): max > Sigma * min over the faces inside the domain;
@@ -81,8 +101,7 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
             const T mx = fmax(fmax(hS ? aS : T(-1), hN ? aN : T(-1)), fmax(hE ? aE : T(-1), hW ? aW : T(-1)));
             const int am = vS == mn ? 0 : (vN == mn ? 1 : (vE == mn ? 2 : 3));
             const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
-            if (cnt >= 2 && mx > mul_rn(L.Sigma, mn))
-                star = (uint8_t)((1u << am) | kInD | (am << 5));
+            if (cnt >= 2 && mx > mul_rn(L.Sigma, mn)) star = (uint8_t)(1u << am);
         }
         sStar[ti][tj] = star;
     }
@@ -93,19 +112,19 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
         uint8_t s = sStar[r][lane];
         uint32_t mA = members_of(__ballot_sync(0xffffffffu, s & 1u), lenr);
         uint32_t mB = members_of(__ballot_sync(0xffffffffu, s & 2u), lenr);
-        sMem[r][lane] = (uint8_t)((s & 0xf0u) | ((mA >> lane) & 1u) | (((mB >> lane) & 1u) << 1));
+        if (lane == 0 && i0 + r < n) {
+            L.mrow[((size_t)0 * n + i0 + r) * L.npm + (j0 >> 5)] = mA;
+            L.mrow[((size_t)1 * n + i0 + r) * L.npm + (j0 >> 5)] = mB;
+        }
     }
-    __syncthreads();
     for (int c = warp; c < 32; c += 8) {             // column pieces: sweeps C, D
         uint8_t s = sStar[lane][c];
         uint32_t mC = members_of(__ballot_sync(0xffffffffu, s & 4u), lenc);
         uint32_t mD = members_of(__ballot_sync(0xffffffffu, s & 8u), lenc);
-        sMem[lane][c] |= (uint8_t)((((mC >> lane) & 1u) << 2) | (((mD >> lane) & 1u) << 3));
-    }
-    __syncthreads();
-    for (int q = tid; q < 1024; q += 256) {
-        int ti = q / 32, tj = q % 32, gi = i0 + ti, gj = j0 + tj;
-        if (gi < n && gj < m) L.cls[(size_t)gi * p + gj] = sMem[ti][tj];
+        if (lane == 0 && j0 + c < m) {
+            L.mcol[((size_t)0 * m + j0 + c) * L.npn + (i0 >> 5)] = mC;
+            L.mcol[((size_t)1 * m + j0 + c) * L.npn + (i0 >> 5)] = mD;
+        }
     }
 }
 
@@ -118,7 +137,7 @@ __global__ void __launch_bounds__(256) k_rb(LevelView<T> L, int colour, int swee
     const int n = L.n, m = L.m, p = L.pitch;
     if (i >= n || j >= m || ((i + j) & 1) != colour) return;
     size_t o = (size_t)i * p + j;
-    if ((L.cls[o] >> sweep) & 1u) return;
+    if (member_bit(L, sweep, i, j)) return;
     bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
     size_t oS = hS ? o + p : o, oN = hN ? o - p : o, oE = hE ? o + 1 : o, oW = hW ? o - 1 : o;
     T gc = L.G[o];
@@ -143,8 +162,8 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
     auto cell = [&](int t) -> size_t {
         return rowwise ? (size_t)line * p + (t0 + t) : (size_t)(t0 + t) * p + line;
     };
-    bool mbit = lane < len && ((L.cls[lane < len ? cell(lane) : cell(0)] >> sweep) & 1u);
-    uint32_t mask = __ballot_sync(0xffffffffu, mbit);
+    const uint32_t mask = rowwise ? L.mrow[((size_t)sweep * n + line) * L.npm + piece]
+                                  : L.mcol[((size_t)(sweep - 2) * m + line) * L.npn + piece];
     uint32_t starts = mask & ~(mask << 1);
     if (!((starts >> lane) & 1u)) return;
     uint32_t rest = ~(mask >> lane);
@@ -181,7 +200,10 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
 // warp updates in one colour phase, and their neighbours, are consecutive words.
 // ---------------------------------------------------------------------------------------
 constexpr int kOH = 32, kOW = 64, kH = 4, kRH = kOH + 2 * kH, kRW = kOW + 2 * kH, kHW = kRW / 2;
-constexpr int kMaxTasks = 72;
+constexpr int kThreads = 256;
+constexpr int kMaxTasks = 2 * (kOH > kOW ? kOH : kOW) + 8;
+// member-mask words held per region line: rows span 4 pieces (j0/32 - 1 .. j0/32 + 2), columns 3
+constexpr int kRowPieces = 4, kColPieces = 3;
 
 template <typename T> struct VecOf;
 template <> struct VecOf<float> { using type = float4; static constexpr int n = 4; };
@@ -192,15 +214,49 @@ struct FusedSmem {
     T u[2][kRH][kHW];
     T G[2][kRH][kHW];
     T f[2][kRH][kHW];
-    uint8_t c[2][kRH][kHW + 4];
+    uint32_t mk[kRW][kRowPieces];   // rowwise: [region row][piece]; colwise: [region column][piece]
     T endv[kMaxTasks][2];
-    uint32_t mask[kMaxTasks];
 };
 
 #define SW_AT(arr, a, b) S.arr[((a) + (b)) & 1][a][(b) >> 1]
 
+// Member bit of region cell (a, b) in the tile's sweep (masks staged in S.mk).
+template <typename T, bool ROWWISE>
+__device__ __forceinline__ bool tile_member(const FusedSmem<T> &S, int a, int b) {
+    if (ROWWISE) return (S.mk[a][(b + 28) >> 5] >> ((b - kH) & 31)) & 1u;
+    return (S.mk[b][(a + 28) >> 5] >> ((a - kH) & 31)) & 1u;
+}
+
+// One checkerboard phase over the region cells within distance 3 - ph of the output tile.
+// INTERIOR: the whole region lies inside the domain, so every updated cell has four faces.
+template <typename T, int SWEEP, bool INTERIOR>
+__device__ __forceinline__ void rb_phase(FusedSmem<T> &S, const LevelView<T> &L, int ph, int i0, int j0) {
+    constexpr bool rev = (SWEEP & 1) != 0;
+    const int colour = rev ? 1 - ph : ph, lo = 1 + ph, other = 1 - colour;
+    const int R = kRH - 2 * lo;
+    const int n = L.n, m = L.m;
+    for (int q = threadIdx.x; q < R * kHW; q += kThreads) {
+        const int a = lo + q / kHW, k = q % kHW;
+        const int x = (a + colour) & 1, b = 2 * k + x;
+        if (b < lo || b >= kRW - lo) continue;
+        bool hS = true, hN = true, hE = true, hW = true;
+        if (!INTERIOR) {
+            const int gi = i0 - kH + a, gj = j0 - kH + b;
+            if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
+            hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
+        }
+        if (tile_member<T, (SWEEP < 2)>(S, a, b)) continue;
+        const T gc = S.G[colour][a][k];
+        const T aS = face(gc, S.G[other][a + 1][k], hS), aN = face(gc, S.G[other][a - 1][k], hN);
+        const T aE = face(gc, S.G[other][a][k + x], hE), aW = face(gc, S.G[other][a][k + x - 1], hW);
+        S.u[colour][a][k] = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, S.u[other][a + 1][k],
+                                        S.u[other][a - 1][k], S.u[other][a][k + x],
+                                        S.u[other][a][k + x - 1], S.f[colour][a][k]);
+    }
+}
+
 template <typename T, int SWEEP>
-__global__ void __launch_bounds__(256) k_sweep(LevelView<T> L) {
+__global__ void __launch_bounds__(kThreads) k_sweep(LevelView<T> L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FusedSmem<T> &S = *reinterpret_cast<FusedSmem<T> *>(smem_raw);
     using V = typename VecOf<T>::type;
@@ -208,58 +264,74 @@ __global__ void __launch_bounds__(256) k_sweep(LevelView<T> L) {
     constexpr bool rowwise = SWEEP < 2, rev = (SWEEP & 1) != 0;
     const int i0 = blockIdx.y * kOH, j0 = blockIdx.x * kOW;
     const int n = L.n, m = L.m, p = L.pitch;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // ---- load u, G, f (vectors; the region starts 16-byte aligned) and the cls bytes
-    for (int q = tid; q < kRH * NV; q += 256) {
-        const int a = q / NV, b0 = (q % NV) * VN;
-        const int gi = i0 - kH + a, gj = j0 - kH + b0;
-        T uu[VN], gg[VN], ff[VN];
-        if (gi >= 0 && gi < n && gj >= 0 && gj < p) {
-            const size_t o = (size_t)gi * p + gj;
-            V x = *reinterpret_cast<const V *>(L.u + o);
-            V y = *reinterpret_cast<const V *>(L.G + o);
-            V z = *reinterpret_cast<const V *>(L.f + o);
-            memcpy(uu, &x, sizeof(V)); memcpy(gg, &y, sizeof(V)); memcpy(ff, &z, sizeof(V));
-        } else {
-            for (int e = 0; e < VN; ++e) uu[e] = gg[e] = ff[e] = T(0);
+    const int tid = threadIdx.x;
+    // ---- load u, G, f as vectors (the region starts 16-byte aligned): all loads of a batch are
+    // issued before any shared-memory store, so they are in flight together
+    constexpr int NVEC = kRH * NV, PER = (NVEC + kThreads - 1) / kThreads, BATCH = VN == 4 ? PER : 3;
+#pragma unroll
+    for (int k0 = 0; k0 < PER; k0 += BATCH) {
+        V x[BATCH][3];
+#pragma unroll
+        for (int k = 0; k < BATCH; ++k) {
+            const int q = tid + (k0 + k) * kThreads;
+            const int a = q / NV, b0 = (q % NV) * VN;
+            const int gi = i0 - kH + a, gj = j0 - kH + b0;
+            if (k0 + k < PER && q < NVEC && gi >= 0 && gi < n && gj >= 0 && gj < p) {
+                const size_t o = (size_t)gi * p + gj;
+                x[k][0] = __ldg(reinterpret_cast<const V *>(L.u + o));
+                x[k][1] = __ldg(reinterpret_cast<const V *>(L.G + o));
+                x[k][2] = __ldg(reinterpret_cast<const V *>(L.f + o));
+            } else {
+                memset(&x[k][0], 0, 3 * sizeof(V));
+            }
         }
-        for (int e = 0; e < VN; ++e) {
-            SW_AT(u, a, b0 + e) = uu[e];
-            SW_AT(G, a, b0 + e) = gg[e];
-            SW_AT(f, a, b0 + e) = ff[e];
+#pragma unroll
+        for (int k = 0; k < BATCH; ++k) {
+            const int q = tid + (k0 + k) * kThreads;
+            if (k0 + k >= PER || q >= NVEC) continue;
+            const int a = q / NV, b0 = (q % NV) * VN;
+            T e3[3][VN];
+            memcpy(e3, x[k], sizeof(e3));
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                SW_AT(u, a, b0 + e) = e3[0][e];
+                SW_AT(G, a, b0 + e) = e3[1][e];
+                SW_AT(f, a, b0 + e) = e3[2][e];
+            }
         }
     }
-    for (int q = tid; q < kRH * (kRW / 4); q += 256) {
-        const int a = q / (kRW / 4), b0 = (q % (kRW / 4)) * 4;
-        const int gi = i0 - kH + a, gj = j0 - kH + b0;
-        uint32_t w4 = 0xffffffffu;
-        if (gi >= 0 && gi < n && gj >= 0 && gj < p) w4 = *reinterpret_cast<const uint32_t *>(L.cls + (size_t)gi * p + gj);
-        for (int e = 0; e < 4; ++e) SW_AT(c, a, b0 + e) = (uint8_t)(w4 >> (8 * e));
+    // ---- member masks of every line piece that touches the region (zero outside the domain)
+    if (rowwise) {
+        for (int q = tid; q < kRH * kRowPieces; q += kThreads) {
+            const int a = q / kRowPieces, pc = q % kRowPieces;
+            const int gi = i0 - kH + a, piece = (j0 >> 5) - 1 + pc;
+            uint32_t w = 0;
+            if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm)
+                w = __ldg(L.mrow + ((size_t)SWEEP * n + gi) * L.npm + piece);
+            S.mk[a][pc] = w;
+        }
+    } else {
+        for (int q = tid; q < kRW * kColPieces; q += kThreads) {
+            const int b = q / kColPieces, pc = q % kColPieces;
+            const int gj = j0 - kH + b, piece = (i0 >> 5) - 1 + pc;
+            uint32_t w = 0;
+            if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn)
+                w = __ldg(L.mcol + ((size_t)(SWEEP - 2) * m + gj) * L.npn + piece);
+            S.mk[b][pc] = w;
+        }
     }
     __syncthreads();
     // ---- checkerboard phases (distance 3 then 2 from the output tile)
+    const bool interior = i0 - kH >= 0 && i0 - kH + kRH <= n && j0 - kH >= 0 && j0 - kH + kRW <= m;
 #pragma unroll
     for (int ph = 0; ph < 2; ++ph) {
-        const int colour = rev ? 1 - ph : ph, lo = 1 + ph, other = 1 - colour;
-        const int R = kRH - 2 * lo;
-        for (int q = tid; q < R * kHW; q += 256) {
-            const int a = lo + q / kHW, k = q % kHW;
-            const int x = (a + colour) & 1, b = 2 * k + x;
-            if (b < lo || b >= kRW - lo) continue;
-            const int gi = i0 - kH + a, gj = j0 - kH + b;
-            if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
-            if ((S.c[colour][a][k] >> SWEEP) & 1u) continue;
-            const bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
-            const T gc = S.G[colour][a][k];
-            const T aS = face(gc, S.G[other][a + 1][k], hS), aN = face(gc, S.G[other][a - 1][k], hN);
-            const T aE = face(gc, S.G[other][a][k + x], hE), aW = face(gc, S.G[other][a][k + x - 1], hW);
-            S.u[colour][a][k] = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, S.u[other][a + 1][k],
-                                            S.u[other][a - 1][k], S.u[other][a][k + x],
-                                            S.u[other][a][k + x - 1], S.f[colour][a][k]);
-        }
+        if (interior) rb_phase<T, SWEEP, true>(S, L, ph, i0, j0);
+        else rb_phase<T, SWEEP, false>(S, L, ph, i0, j0);
         __syncthreads();
     }
-    // ---- partial-line phases: lines at distance 1, then 0, one parity each
+    // ---- partial-line phases: lines at distance 1, then 0, one parity each.  A task is one
+    // piece of one line: rowwise the two 32-column pieces of the output (mask index 1, 2),
+    // colwise the 32-row piece of the output (mask index 1).
     constexpr int npc = rowwise ? 2 : 1;
     const int len_lim = rowwise ? m : n, gl_lim = rowwise ? n : m;
 #pragma unroll
@@ -267,37 +339,33 @@ __global__ void __launch_bounds__(256) k_sweep(LevelView<T> L) {
         const int parity = rev ? 1 - ph : ph, dist = 1 - ph;
         const int lfirst = kH - dist;
         const int ntask = ((rowwise ? kOH : kOW) + 2 * dist) * npc;
-        // step a: member masks by warp ballots, end values at the piece boundaries (pre-phase)
-        for (int t = warp; t < ntask; t += 8) {
+        // step a: the end values at the piece boundaries, read before any run is solved
+        for (int t = tid; t < ntask; t += kThreads) {
             const int li = lfirst + t / npc, pc = t % npc;
             const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
             const int gstart = rowwise ? j0 + 32 * pc : i0;
             const int s0 = kH + 32 * pc;
             const bool ok = gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim;
             const int len = ok ? min(32, len_lim - gstart) : 0;
-            bool bit = false;
-            if (lane < len) bit = ((rowwise ? SW_AT(c, li, s0 + lane) : SW_AT(c, s0 + lane, li)) >> SWEEP) & 1u;
-            const uint32_t mk = __ballot_sync(0xffffffffu, bit);
-            if (lane == 0) {
-                T e0 = T(0), e1 = T(0);
-                if (mk) {
-                    if (gstart > 0) e0 = rowwise ? SW_AT(u, li, s0 - 1) : SW_AT(u, s0 - 1, li);
-                    if (gstart + len < len_lim) e1 = rowwise ? SW_AT(u, li, s0 + len) : SW_AT(u, s0 + len, li);
-                }
-                S.mask[t] = mk;
-                S.endv[t][0] = e0;
-                S.endv[t][1] = e1;
+            const uint32_t mk = ok ? S.mk[li][1 + pc] : 0u;
+            T e0 = T(0), e1 = T(0);
+            if (mk) {
+                if (gstart > 0) e0 = rowwise ? SW_AT(u, li, s0 - 1) : SW_AT(u, s0 - 1, li);
+                if (gstart + len < len_lim) e1 = rowwise ? SW_AT(u, li, s0 + len) : SW_AT(u, s0 + len, li);
             }
+            S.endv[t][0] = e0;
+            S.endv[t][1] = e1;
         }
         __syncthreads();
         // step b: every run of every task, one thread per task
-        for (int t = tid; t < ntask; t += 256) {
-            const uint32_t mk = S.mask[t];
-            if (!mk) continue;
+        for (int t = tid; t < ntask; t += kThreads) {
             const int li = lfirst + t / npc, pc = t % npc;
-            const int s0 = kH + 32 * pc;
             const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
             const int gstart = rowwise ? j0 + 32 * pc : i0;
+            if (!(gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim)) continue;
+            const uint32_t mk = S.mk[li][1 + pc];
+            if (!mk) continue;
+            const int s0 = kH + 32 * pc;
             const int len = min(32, len_lim - gstart);
             int s = 0;
             while (s < len) {
@@ -335,15 +403,15 @@ __global__ void __launch_bounds__(256) k_sweep(LevelView<T> L) {
         __syncthreads();
     }
     // ---- write the output tile (vectors; padding columns keep their loaded values)
-    for (int q = tid; q < kOH * NVO; q += 256) {
+    for (int q = tid; q < kOH * NVO; q += kThreads) {
         const int a = kH + q / NVO, b0 = kH + (q % NVO) * VN;
         const int gi = i0 + q / NVO, gj = j0 + (q % NVO) * VN;
         if (gi >= n || gj >= p) continue;
         T uu[VN];
         for (int e = 0; e < VN; ++e) uu[e] = SW_AT(u, a, b0 + e);
-        V x;
-        memcpy(&x, uu, sizeof(V));
-        *reinterpret_cast<V *>(L.u + (size_t)gi * p + gj) = x;
+        V xv;
+        memcpy(&xv, uu, sizeof(V));
+        *reinterpret_cast<V *>(L.u + (size_t)gi * p + gj) = xv;
     }
 }
 
@@ -394,7 +462,7 @@ template <typename T, int SW>
 static void launch_fused_one(const LevelView<T> &L, cudaStream_t st) {
     size_t smem = sizeof(FusedSmem<T>);
     dim3 grid((L.m + kOW - 1) / kOW, (L.n + kOH - 1) / kOH);
-    k_sweep<T, SW><<<grid, 256, smem, st>>>(L);
+    k_sweep<T, SW><<<grid, kThreads, smem, st>>>(L);
 }
 
 template <typename T>

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import buildlib as _build
 
-MG_F32, MG_F64 = 0, 1
+MG_F32, MG_F64, MG_MIXED = 0, 1, 2
 MG_MODEL_SC, MG_MODEL_RC = 0, 1
 MG_SMOOTH_FUSED, MG_SMOOTH_PHASED = 0, 1
 ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4: "MG_ERR_DIVERGED",

@@ -14,7 +14,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["disc_square", "ellipses", "Workload", "workload"]
+__all__ = ["disc_square", "ellipses", "ellipses_device", "Workload", "workload"]
 
 
 def disc_square(n: int = 128, noise: float = 0.05, seed: int = 0, dtype=np.float64):
@@ -102,6 +102,61 @@ def ellipses(n: int, m: int | None = None, n_ellipses: int = 12, axes=(20.0, 200
     v = -(jj - cx) * np.sin(ang) + (ii - cy) * np.cos(ang)
     chosen_mask = (u / a) ** 2 + (v / b) ** 2 <= 1.0
     return img.astype(dtype), np.array(pts, dtype=np.float64), chosen_mask
+
+
+def ellipses_device(n: int, m: int | None = None, n_ellipses: int = 200, axes=(100.0, 3000.0),
+                    n_markers: int = 20, noise: float = 0.05, seed: int = 2, device="cuda"):
+    """The ellipse recipe of `ellipses` drawn with torch on `device`, for images too large for
+    host-side generation (25000 x 25000 and up).  Same distributions; the random stream is
+    torch's (not numpy's), so the pixels differ from `ellipses` with the same seed.
+    Returns (float32 tensor on device, markers as a numpy (k, 2) array)."""
+    import torch
+
+    m = n if m is None else m
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    u = lambda lo, hi: float(lo + (hi - lo) * torch.rand(1, generator=g, dtype=torch.float64))
+    psi = u(0, np.pi)
+    xs = torch.arange(m, device=device, dtype=torch.float32)
+    img = torch.empty((n, m), device=device, dtype=torch.float32)
+    step = 4096
+    for r0 in range(0, n, step):
+        rows = torch.arange(r0, min(n, r0 + step), device=device, dtype=torch.float32)
+        img[r0:r0 + len(rows)] = 0.1 + 0.2 * (xs[None, :] * np.cos(psi) + rows[:, None] * np.sin(psi)) / max(n, m)
+    params = []
+    for _ in range(n_ellipses):
+        cy, cx = u(0, n), u(0, m)
+        a, b = u(*axes) / 2.0, u(*axes) / 2.0
+        ang, val, s1, s2 = u(0, np.pi), u(0, 1), u(-0.1, 0.1), u(-0.1, 0.1)
+        params.append((cy, cx, a, b, ang, val, s1, s2))
+    for (cy, cx, a, b, ang, val, s1, s2) in params:
+        r = max(a, b) + 1
+        i0, i1 = max(int(cy - r), 0), min(int(cy + r) + 2, n)
+        j0, j1 = max(int(cx - r), 0), min(int(cx + r) + 2, m)
+        if i0 >= i1 or j0 >= j1:
+            continue
+        ii = torch.arange(i0, i1, device=device, dtype=torch.float32)[:, None]
+        jj = torch.arange(j0, j1, device=device, dtype=torch.float32)[None, :]
+        uu = (jj - cx) * np.cos(ang) + (ii - cy) * np.sin(ang)
+        vv = -(jj - cx) * np.sin(ang) + (ii - cy) * np.cos(ang)
+        inside = (uu / a) ** 2 + (vv / b) ** 2 <= 1.0
+        sub = img[i0:i1, j0:j1]
+        sub[inside] = (val + s1 * uu / a + s2 * vv / b)[inside]
+    if noise > 0:
+        gd = torch.Generator(device=device).manual_seed(seed)
+        for r0 in range(0, n, step):
+            blk = img[r0:r0 + step]
+            blk += noise * torch.randn(blk.shape, generator=gd, device=device, dtype=torch.float32)
+    cy, cx, a, b, ang, *_ = params[-1]
+    pts = []
+    while len(pts) < n_markers:
+        ru, rv = u(-1, 1), u(-1, 1)
+        if ru * ru + rv * rv > 1:
+            continue
+        x = cx + 0.8 * a * ru * np.cos(ang) - 0.8 * b * rv * np.sin(ang)
+        y = cy + 0.8 * a * ru * np.sin(ang) + 0.8 * b * rv * np.cos(ang)
+        if 0 <= x <= m - 1 and 0 <= y <= n - 1:
+            pts.append((round(x), round(y)))
+    return img, np.array(pts, dtype=np.float64)
 
 
 class Workload:
