@@ -407,6 +407,70 @@ def run_config3(args):
     print(json.dumps(line), flush=True)
 
 
+def run_config4(args):
+    """Batched uneven sizes: 64 images with sizes drawn from {256, 512, 768, 1024, 2048}^2, each
+    from the ellipse recipe with its own 4-16 markers (FP32).  One pseudo-time step of all images
+    to rho <= 1e-6 through the batch graph (one launch per V-cycle, converged images skipped on
+    the device), tile shapes from the autotuner, against the same images solved one by one."""
+    import torch
+    from paper_1807_02137_gb300 import buildlib, segmg, synth
+    buildlib.build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.Generator(np.random.PCG64(3))
+    sizes = rng.choice([256, 512, 768, 1024, 2048], size=args.config4)
+    imgs, mks, params = [], [], []
+    for q, n in enumerate(sizes):
+        k = int(rng.integers(4, 17))
+        img, mk = synth.ellipses_device(int(n), int(n), max(12, int(12 * n / 1024)),
+                                        (20 * n / 1024, 200 * n / 1024), k, 0.05, 100 + q, dev)
+        imgs.append(img)
+        mks.append(mk)
+        params.append(segmg.default_params(int(n), int(n)))
+    cells = int(sum(int(n) ** 2 for n in sizes))
+
+    def batch_run(tune):
+        b = segmg.Batch(imgs, mks, params)
+        shapes = None
+        if tune:
+            b.autotune(reps=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cyc, rho = b.solve_step(TOL, MAX_CYCLES)
+        dt = time.perf_counter() - t0
+        b.close()
+        return dt, cyc, rho
+
+    batch_run(True)                       # warm-up (graph build, autotune, caches)
+    tb = [batch_run(True) for _ in range(max(1, args.steps))]
+    tb_plain = [batch_run(False) for _ in range(max(1, args.steps))]
+    ts = []
+    for _ in range(max(1, args.steps)):
+        tot, cyc_s = 0.0, []
+        for q in range(len(imgs)):
+            s = segmg.Solver(imgs[q], mks[q], params[q])
+            s.solve_step(TOL, MAX_CYCLES)      # warm-up / graph capture of this image
+            s.reset(imgs[q], mks[q])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c, r = s.solve_step(TOL, MAX_CYCLES)
+            tot += time.perf_counter() - t0
+            cyc_s.append(c)
+            s.close()
+        ts.append(tot)
+    best_b = min(tb, key=lambda x: x[0])
+    line = {"config": f"batched: {len(sizes)} FP32 images, sizes {sorted(set(int(x) for x in sizes))}",
+            "size_counts": {int(k): int((sizes == k).sum()) for k in sorted(set(sizes))},
+            "cells": cells,
+            "batched_autotuned": {"s": best_b[0], "unknowns_per_s": cells / best_b[0],
+                                  "cycles_min_max": [min(best_b[1]), max(best_b[1])],
+                                  "rho_max": max(best_b[2])},
+            "batched_default_tiles": {"s": min(x[0] for x in tb_plain),
+                                      "unknowns_per_s": cells / min(x[0] for x in tb_plain)},
+            "one_by_one": {"s": min(ts), "unknowns_per_s": cells / min(ts)},
+            "speedup_batched_vs_one_by_one": min(ts) / best_b[0]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,8 +483,11 @@ def main():
     ap.add_argument("--profile", type=int, default=0, help="run the N x N ncu profiling case instead")
     ap.add_argument("--cycles", type=int, default=2)
     ap.add_argument("--config3", type=int, default=0, help="run the mixed-precision N x N report")
+    ap.add_argument("--config4", type=int, default=0, help="run the batched report with this many images")
     args = ap.parse_args()
-    if args.config3:
+    if args.config4:
+        run_config4(args)
+    elif args.config3:
         run_config3(args)
     elif args.profile:
         run_profile_case(args)

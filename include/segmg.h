@@ -179,6 +179,37 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
                     const mg_params *p, double tol, int max_cycles, double eta_stop,
                     int max_steps, unsigned char *mask_host, float *phi_host, mg_stats *stats);
 
+/* Tile-shape autotuner (a tuning step of this implementation; the paper has no counterpart):
+ * inside a pseudo-time step (after mg_begin_step), times one outer smoothing iteration of every
+ * grid but the coarsest with each fused-sweep tile shape (0 = 32x64, 1 = 32x32, 2 = 64x64
+ * cells) over `reps` repetitions and keeps the fastest per grid; writes the choices to
+ * shapes[0..levels-2] if not NULL.  The state is restored, and the results of later solves do
+ * not depend on the shapes (every shape computes the same values).  Waits. */
+int mg_autotune(mg_handle h, int reps, int *shapes);
+/* Sets the fused-sweep tile shape of grids 0..levels-2 (values 0..2 as above). */
+int mg_set_tile_shapes(mg_handle h, const int *shapes);
+
+/* Batches (BASELINE config 4 style workloads; no counterpart in the paper): `count` images of
+ * their own sizes solved together.  Each V-cycle of mg_batch_solve_step is one CUDA graph
+ * launch whose branches are the images' V-cycles; a branch is a conditional graph node that
+ * the device skips once that image's residual has reached the tolerance.
+ *   images[i]   device, n[i]*m[i] floats (read during the call);  markers[i] host, k[i] pairs;
+ *   params[i]   per-image parameters (MG_F32 or MG_MIXED), e.g. from mg_default_params;
+ *   stream      may be NULL (own non-blocking stream).
+ * Images' handles are owned by the batch: use mg_batch_handle(b, i) for mg_mask, mg_get_phi,
+ * mg_get_stats of image i, never mg_destroy.  Errors as mg_setup. */
+typedef struct mg_batch_s *mg_batch;
+int mg_batch_setup(mg_batch *out, int count, const void *const *images, const int *n, const int *m,
+                   const double *const *markers, const int *k, const mg_params *params, void *stream);
+/* One pseudo-time step of every image (begin, V-cycles until every rho <= tol or max_cycles
+ * launches, end).  cycles[i] / rho[i] (host, may be NULL) get each image's V-cycles and final
+ * rho.  MG_ERR_TIMEOUT when an image did not reach tol. */
+int mg_batch_solve_step(mg_batch b, double tol, int max_cycles, int *cycles, double *rho);
+/* mg_autotune for every image of the batch. */
+int mg_batch_autotune(mg_batch b, int reps);
+mg_handle mg_batch_handle(mg_batch b, int i);
+void mg_batch_destroy(mg_batch b);
+
 /* Diagnostic timing of the smoother kernels on grid `level` at the current state: runs `reps`
  * outer smoothing iterations eagerly with CUDA events on the handle's stream and writes the
  * mean milliseconds per launch of [0] the snapshot kernel, [1..4] the sweeps A, B, C, D,

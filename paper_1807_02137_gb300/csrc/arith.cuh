@@ -127,6 +127,104 @@ __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem, bool pred)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using type = float4; static constexpr int n = 4; };
+template <> struct VecOf<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ int clamp_idx(int v, int hi) { return v < 0 ? 0 : (v > hi ? hi : v); }
+
+// Loads rows i0-2 .. i0+33 and columns j0-2 .. j0+33 of one or two pitched grid functions into
+// dst[36][37] arrays, indices clamped into the domain (the mirror ghosts of the central
+// differences).  The 36 x 40 window from column j0-4 is read with 16-byte vector loads where it
+// lies inside the domain (per-element clamped loads at the edges); all of a thread's loads are
+// issued before its shared-memory stores.  256 threads.
+template <typename T>
+__device__ __forceinline__ void load_halo2(T (*dA)[37], const T *sA, T (*dB)[37], const T *sB, int i0, int j0,
+                                           int n, int m, int p, int tid) {
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n, NV = 40 / VN, NVEC = 36 * NV, PER = (NVEC + 255) / 256;
+    T xa[PER][VN], xb[PER][VN];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = tid + k * 256;
+        if (q >= NVEC) break;
+        const int a = q / NV, gi = i0 - 2 + a, gj = j0 - 4 + (q % NV) * VN;
+        if (gi >= 0 && gi < n && gj >= 0 && gj + VN <= m) {
+            const size_t o = (size_t)gi * p + gj;
+            V va = __ldg(reinterpret_cast<const V *>(sA + o));
+            memcpy(xa[k], &va, sizeof(V));
+            if (sB) {
+                V vb = __ldg(reinterpret_cast<const V *>(sB + o));
+                memcpy(xb[k], &vb, sizeof(V));
+            }
+        } else {
+            const size_t ro = (size_t)clamp_idx(gi, n - 1) * p;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const size_t o = ro + clamp_idx(gj + e, m - 1);
+                xa[k][e] = sA[o];
+                if (sB) xb[k][e] = sB[o];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = tid + k * 256;
+        if (q >= NVEC) break;
+        const int a = q / NV, b0 = (q % NV) * VN - 2;
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            const int b = b0 + e;
+            if (b >= 0 && b < 36) {
+                dA[a][b] = xa[k][e];
+                if (sB) dB[a][b] = xb[k][e];
+            }
+        }
+    }
+}
+
+// Loads the 32 x 32 tile at (i0, j0) of one or two pitched grid functions into dst[32][33]
+// (indices clamped into the domain; those values are never used), vector loads, 256 threads.
+template <typename T>
+__device__ __forceinline__ void load_tile32(T (*dA)[33], const T *sA, T (*dB)[33], const T *sB, int i0, int j0,
+                                            int n, int m, int p, int tid) {
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n, NV = 32 / VN, NVEC = 32 * NV, PER = (NVEC + 255) / 256;
+    T xa[PER][VN], xb[PER][VN];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = tid + k * 256;
+        const int a = q / NV, gi = i0 + a, gj = j0 + (q % NV) * VN;
+        if (gi < n && gj + VN <= m) {
+            const size_t o = (size_t)gi * p + gj;
+            V va = __ldg(reinterpret_cast<const V *>(sA + o));
+            memcpy(xa[k], &va, sizeof(V));
+            if (sB) {
+                V vb = __ldg(reinterpret_cast<const V *>(sB + o));
+                memcpy(xb[k], &vb, sizeof(V));
+            }
+        } else {
+            const size_t ro = (size_t)clamp_idx(gi, n - 1) * p;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const size_t o = ro + clamp_idx(gj + e, m - 1);
+                xa[k][e] = sA[o];
+                if (sB) xb[k][e] = sB[o];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = tid + k * 256;
+        const int a = q / NV, b0 = (q % NV) * VN;
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            dA[a][b0 + e] = xa[k][e];
+            if (sB) dB[a][b0 + e] = xb[k][e];
+        }
+    }
+}
+
 // Sum of squares of the residual values a thread visits: accumulated in the storage precision
 // (a handful of values per thread), then widened to FP64 for the block and grid reductions.
 // FP64 arithmetic is slow on this GPU, so the per-cell work stays in FP32 on the FP32 path.

@@ -6,8 +6,6 @@ namespace segmg {
 
 namespace {
 
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-
 // Sum of a per-thread double over the block (blockDim.x * blockDim.y <= 1024); the result is
 // returned to every thread.  Fixed reduction order: deterministic.
 __device__ double block_sum(double v, double *red) {
@@ -66,21 +64,12 @@ __global__ void __launch_bounds__(256) k_residual(LevelView<T> L, const T *uin, 
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int n = L.n, m = L.m, p = L.pitch;
-    // stage pn, uin (mirror-clamped), w and F with asynchronous copies (all loads in flight)
-    for (int q = tid; q < R * R; q += 256) {
-        int a = q / R, b = q % R;
-        int gi = clampi(i0 - 2 + a, 0, n - 1), gj = clampi(j0 - 2 + b, 0, m - 1);
-        cp_async_elem(&sP[a][b], L.pn + (size_t)gi * p + gj, true);
-        cp_async_elem(&sU[a][b], uin + (size_t)gi * p + gj, true);
-        if (kStage && a >= 1 && a < R - 1 && b >= 1 && b < R - 1 && !L.wb)
-            cp_async_elem(&sW[kStage ? a : 0][kStage ? b : 0], L.w + (size_t)gi * p + gj, true);
-        if (kStage && a >= 2 && a < R - 2 && b >= 2 && b < R - 2) {
-            int fi = min(i0 - 2 + a, n - 1), fj = min(j0 - 2 + b, m - 1);
-            cp_async_elem(&sF[kStage ? a - 2 : 0][kStage ? b - 2 : 0], L.F + (size_t)fi * p + fj, true);
-        }
+    // stage pn, uin (mirror-clamped), w and F (FP32 only) with vector loads
+    load_halo2<T>(sP, L.pn, sU, uin, i0, j0, n, m, p, tid);
+    if (kStage) {
+        if (!L.wb) load_halo2<T>(reinterpret_cast<T (*)[37]>(sW), L.w, nullptr, nullptr, i0, j0, n, m, p, tid);
+        load_tile32<T>(reinterpret_cast<T (*)[33]>(sF), L.F, nullptr, nullptr, i0, j0, n, m, p, tid);
     }
-    cp_async_commit();
-    cp_async_wait_all();
     __syncthreads();
     for (int q = tid; q < 34 * 34; q += 256) {
         int a = 1 + q / 34, b = 1 + q % 34;

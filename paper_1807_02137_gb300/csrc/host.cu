@@ -102,6 +102,8 @@ struct SolverBase {
     virtual int stats(mg_stats *s) = 0;
     virtual cudaStream_t stream() const = 0;
     virtual int time_kernels(int level, int reps, double *ms) = 0;
+    virtual int autotune(int reps, int *out) = 0;
+    virtual int set_shapes(const int *shapes) = 0;
 };
 
 template <typename T>
@@ -138,6 +140,7 @@ struct Solver final : SolverBase {
     bool in_step = false;
     cudaGraphExec_t gexec = nullptr;
     long long launches = 0, graph_nodes = 0;
+    int shape[kMaxLevels] = {};   // fused-sweep tile shape per grid (mg_autotune)
     ModelParams mp{};
 
     ~Solver() override { release(); }
@@ -319,6 +322,8 @@ struct Solver final : SolverBase {
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         res0 = std::sqrt(hsc->norm2_0);
+        // the last residual norm starts at the reference one (rho = 1 until a V-cycle runs)
+        CK(cudaMemcpyAsync(&dsc->norm2, &dsc->norm2_0, sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (!std::isfinite(res0)) return fail(MG_ERR_NAN, "non-finite initial residual");
         in_step = true;
         cycles_step = 0;
@@ -336,7 +341,7 @@ struct Solver final : SolverBase {
         launch_snapshot<T>(v, area_ptr(), st);
         for (int k = 0; k < 4; ++k) {
             if (p.smoother == MG_SMOOTH_PHASED) launch_sweep_phased<T>(v, k, st);
-            else launch_sweep_fused<T>(v, k, st);
+            else launch_sweep_fused<T>(v, k, shape[l], st);
         }
         launches += area_launches() + 1 + 4 * sweep_launches();
     }
@@ -363,12 +368,74 @@ struct Solver final : SolverBase {
         for (int t = 0; t < p.nu2; ++t) smooth(l);
     }
 
-    void enqueue_vcycle() {
+    void enqueue_vcycle(bool readback = true) {
         cycle(0);
         area_term(0, lv[0].u);
         launch_residual<T>(view(0), lv[0].u, area_ptr(), lv[0].r, 0, partials, npart, &dsc->norm2, st);
         launches += area_launches() + 2;
-        cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+        if (readback) cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+    }
+
+    // One V-cycle (ending with the finest residual norm on the device) captured into a graph,
+    // for composition into a batch graph.  Returns the graph and its kernel count.
+    int capture_vcycle(cudaGraph_t *g, long long *nodes) {
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        long long before = launches;
+        enqueue_vcycle(false);
+        *nodes = launches - before;
+        launches = before;
+        cudaError_t e = cudaStreamEndCapture(st, g);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        return MG_OK;
+    }
+
+    int set_shapes(const int *sh) override {
+        for (int l = 0; l < nlev - 1; ++l)
+            if (sh[l] < 0 || sh[l] >= kTileShapes) return fail(MG_ERR_ARG, "tile shape out of range");
+        for (int l = 0; l < nlev - 1; ++l) shape[l] = sh[l];
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        return MG_OK;
+    }
+
+    // Picks the fused-sweep tile shape of every grid by timing one outer smoothing iteration
+    // (snapshot + four sweeps, `reps` times) per shape; the state is restored afterwards.
+    int autotune(int reps, int *out) {
+        if (!in_step) return fail(MG_ERR_STATE, "mg_autotune outside a step");
+        if (p.smoother == MG_SMOOTH_PHASED) return fail(MG_ERR_ARG, "autotune applies to the fused smoother");
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int l = 0; l < nlev - 1; ++l) {
+            Level<T> &L = lv[l];
+            const size_t row = (size_t)L.m * sizeof(T), pitchb = (size_t)L.pitch * sizeof(T);
+            float best = 1e30f;
+            int arg = 0;
+            for (int sh = 0; sh < kTileShapes; ++sh) {
+                CK(cudaMemcpy2DAsync(L.r, pitchb, L.u, pitchb, row, L.n, cudaMemcpyDeviceToDevice, st));
+                LevelView<T> v = view(l);
+                float t = 0;
+                for (int warm = 0; warm < 2; ++warm) {
+                    CK(cudaEventRecord(e0, st));
+                    for (int r = 0; r < reps; ++r) {
+                        area_term(l, L.u);
+                        launch_snapshot<T>(v, area_ptr(), st);
+                        for (int k = 0; k < 4; ++k) launch_sweep_fused<T>(v, k, sh, st);
+                    }
+                    CK(cudaEventRecord(e1, st));
+                    CK(cudaEventSynchronize(e1));
+                    CK(cudaEventElapsedTime(&t, e0, e1));
+                }
+                CKL();
+                CK(cudaMemcpy2DAsync(L.u, pitchb, L.r, pitchb, row, L.n, cudaMemcpyDeviceToDevice, st));
+                if (t < best) { best = t; arg = sh; }
+            }
+            shape[l] = arg;
+            if (out) out[l] = arg;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }   // shapes are baked into graphs
+        return MG_OK;
     }
 
     int vcycle(double *rhoout) override {
@@ -491,7 +558,7 @@ struct Solver final : SolverBase {
             cudaEventRecord(ev[1], st);
             for (int k = 0; k < 4; ++k) {
                 if (p.smoother == MG_SMOOTH_PHASED) launch_sweep_phased<T>(v, k, st);
-                else launch_sweep_fused<T>(v, k, st);
+                else launch_sweep_fused<T>(v, k, shape[l], st);
                 cudaEventRecord(ev[2 + k], st);
             }
             launch_residual<T>(v, lv[l].u, area_ptr(), lv[l].r, 0, partials, 0, nullptr, st);
@@ -552,6 +619,160 @@ int check_markers(const double *mk, int k, int n, int m) {
 
 struct mg_handle_s {
     SolverBase *s;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Batched solves: many images, one CUDA graph per V-cycle whose branches are the images.
+// Each branch is a conditional node: a one-thread kernel sets its condition from the image's
+// last residual norm, so images that have reached the tolerance are skipped on the device.
+// ---------------------------------------------------------------------------------------
+__global__ void k_batch_cond(cudaGraphConditionalHandle h, const Scalars *sc, double tol2) {
+    const double n2 = sc->norm2, n0 = sc->norm2_0;
+    cudaGraphSetConditional(h, n2 > tol2 * n0 ? 1u : 0u);
+}
+
+__global__ void k_batch_gather(Scalars *const *sc, int count, double *out) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        out[3 * i] = sc[i]->norm2;
+        out[3 * i + 1] = sc[i]->norm2_0;
+        out[3 * i + 2] = (double)sc[i]->err;
+    }
+}
+
+struct Batch {
+    std::vector<Solver<float> *> s;
+    std::vector<mg_handle_s *> h;
+    std::vector<long long> nodes;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    Scalars **d_sc = nullptr;
+    double *d_out = nullptr, *h_out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double tol_baked = -1.0;
+
+    ~Batch() {
+        if (st) cudaStreamSynchronize(st);
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto *x : s) delete x;
+        for (auto *x : h) delete x;
+        if (d_sc) cudaFree(d_sc);
+        if (d_out) cudaFree(d_out);
+        if (h_out) cudaFreeHost(h_out);
+        if (own_stream && st) cudaStreamDestroy(st);
+    }
+
+    int build(double tol) {
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+        const int count = (int)s.size();
+        cudaGraph_t B;
+        CK(cudaGraphCreate(&B, 0));
+        std::vector<cudaGraphNode_t> ends;
+        nodes.assign(count, 0);
+        int rc = MG_OK;
+        double tol2 = tol * tol;
+        for (int i = 0; i < count && rc == MG_OK; ++i) {
+            cudaGraph_t gi;
+            if ((rc = s[i]->capture_vcycle(&gi, &nodes[i]))) break;
+            cudaGraphConditionalHandle hc;
+            cudaError_t e = cudaGraphConditionalHandleCreate(&hc, B, 0, cudaGraphCondAssignDefault);
+            cudaGraphNode_t kn = nullptr, cn = nullptr, child = nullptr;
+            if (e == cudaSuccess) {
+                const Scalars *sc = s[i]->dsc;
+                void *args[] = {&hc, (void *)&sc, &tol2};
+                cudaKernelNodeParams kp = {};
+                kp.func = (void *)k_batch_cond;
+                kp.gridDim = dim3(1);
+                kp.blockDim = dim3(1);
+                kp.kernelParams = args;
+                e = cudaGraphAddKernelNode(&kn, B, nullptr, 0, &kp);
+            }
+            if (e == cudaSuccess) {
+                cudaGraphNodeParams cp = {};
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = hc;
+                cp.conditional.type = cudaGraphCondTypeIf;
+                cp.conditional.size = 1;
+                e = cudaGraphAddNode(&cn, B, &kn, nullptr, 1, &cp);
+                if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, cp.conditional.phGraph_out[0], nullptr, 0, gi);
+            }
+            cudaGraphDestroy(gi);
+            if (e != cudaSuccess) rc = fail(MG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+            else ends.push_back(cn);
+        }
+        if (rc == MG_OK) {
+            cudaGraphNode_t gn, mn;
+            int cnt = count;
+            void *args[] = {(void *)&d_sc, &cnt, (void *)&d_out};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void *)k_batch_gather;
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(256);
+            kp.kernelParams = args;
+            cudaError_t e = cudaGraphAddKernelNode(&gn, B, ends.data(), ends.size(), &kp);
+            if (e == cudaSuccess)
+                e = cudaGraphAddMemcpyNode1D(&mn, B, &gn, 1, h_out, d_out, sizeof(double) * 3 * count, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, B, 0);
+            if (e != cudaSuccess) { exec = nullptr; rc = fail(MG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e)); }
+        }
+        cudaGraphDestroy(B);
+        if (rc == MG_OK) tol_baked = tol;
+        return rc;
+    }
+
+    int solve_step(double tol, int max_cycles, int *cycles, double *rho) {
+        const int count = (int)s.size();
+        for (int i = 0; i < count; ++i) {
+            int rc = s[i]->begin_step(nullptr);
+            if (rc) return rc;
+        }
+        if (!exec || tol != tol_baked) {
+            int rc = build(tol);
+            if (rc) return rc;
+        }
+        std::vector<int> cyc(count, 0);
+        std::vector<double> r(count, 1.0);
+        std::vector<char> active(count, 1);
+        int c = 0, rc = MG_OK;
+        for (; c < max_cycles; ++c) {
+            CK(cudaGraphLaunch(exec, st));
+            CK(cudaStreamSynchronize(st));
+            bool any = false;
+            for (int i = 0; i < count; ++i) {
+                const double n2 = h_out[3 * i], n0 = h_out[3 * i + 1];
+                if (active[i]) {
+                    ++cyc[i];
+                    s[i]->cycles_step = cyc[i];
+                    ++s[i]->cycles_total;
+                    s[i]->launches += nodes[i] + 1;
+                }
+                r[i] = n0 > 0 ? std::sqrt(n2) / std::sqrt(n0) : std::sqrt(n2);   // as mg_vcycle
+                s[i]->rho = r[i];
+                if (h_out[3 * i + 2] != 0.0 && rc == MG_OK) rc = fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
+                if (!std::isfinite(r[i]) && rc == MG_OK) rc = fail(MG_ERR_NAN, "non-finite residual");
+                active[i] = r[i] > tol;
+                any = any || active[i];
+            }
+            if (rc || !any) break;
+        }
+        if (cycles) for (int i = 0; i < count; ++i) cycles[i] = cyc[i];
+        if (rho) for (int i = 0; i < count; ++i) rho[i] = r[i];
+        if (rc) return rc;
+        for (int i = 0; i < count; ++i) {
+            int e = s[i]->end_step(nullptr);
+            if (e) return e;
+        }
+        for (int i = 0; i < count; ++i)
+            if (r[i] > tol) return fail(MG_ERR_TIMEOUT, "cycle cap reached before the tolerance");
+        return MG_OK;
+    }
+};
+
+}  // namespace
+
+struct mg_batch_s {
+    Batch b;
 };
 
 extern "C" {
@@ -708,6 +929,85 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
     g_err = keep;
     return rc;
 }
+
+int mg_autotune(mg_handle h, int reps, int *shapes) {
+    if (!h || reps < 1) return fail(MG_ERR_ARG, "NULL handle or reps < 1");
+    return h->s->autotune(reps, shapes);
+}
+
+int mg_set_tile_shapes(mg_handle h, const int *shapes) {
+    if (!h || !shapes) return fail(MG_ERR_ARG, "NULL argument");
+    return h->s->set_shapes(shapes);
+}
+
+int mg_batch_setup(mg_batch *out, int count, const void *const *images, const int *n, const int *m,
+                   const double *const *markers, const int *k, const mg_params *params, void *stream) {
+    if (!out) return fail(MG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !images || !n || !m || !markers || !k || !params) return fail(MG_ERR_ARG, "NULL argument or count < 1");
+    for (int i = 0; i < count; ++i) {
+        int rc = check_params(&params[i], n[i], m[i]);
+        if (rc) return rc;
+        if (params[i].precision == MG_F64) return fail(MG_ERR_ARG, "batches take MG_F32 or MG_MIXED images");
+        if (!images[i]) return fail(MG_ERR_ARG, "image is NULL");
+        if ((rc = check_markers(markers[i], k[i], n[i], m[i]))) return rc;
+    }
+    prepare_smoother_kernels();
+    prepare_coarse_kernels();
+    auto *B = new mg_batch_s();
+    Batch &b = B->b;
+    int rc = MG_OK;
+    if (stream) b.st = (cudaStream_t)stream;
+    else if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) == cudaSuccess) b.own_stream = true;
+    else rc = fail(MG_ERR_CUDA, "stream creation failed");
+    for (int i = 0; i < count && rc == MG_OK; ++i) {
+        auto *sv = new Solver<float>();
+        b.s.push_back(sv);
+        b.h.push_back(new mg_handle_s{sv});
+        rc = sv->init(n[i], m[i], params[i], nullptr, b.st, k[i]);
+        if (!rc) rc = sv->reset(images[i], markers[i], k[i]);
+    }
+    if (rc == MG_OK) {
+        std::vector<Scalars *> ptrs;
+        for (auto *x : b.s) ptrs.push_back(x->dsc);
+        cudaError_t e = cudaMalloc(&b.d_sc, sizeof(Scalars *) * count);
+        if (e == cudaSuccess) e = cudaMalloc(&b.d_out, sizeof(double) * 3 * count);
+        if (e == cudaSuccess) e = cudaMallocHost(&b.h_out, sizeof(double) * 3 * count);
+        if (e == cudaSuccess) e = cudaMemcpy(b.d_sc, ptrs.data(), sizeof(Scalars *) * count, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = fail(MG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (rc) {
+        std::string keep = g_err;
+        delete B;
+        g_err = keep;
+        return rc;
+    }
+    *out = B;
+    return MG_OK;
+}
+
+int mg_batch_solve_step(mg_batch b, double tol, int max_cycles, int *cycles, double *rho) {
+    if (!b || max_cycles < 1) return fail(MG_ERR_ARG, "NULL batch or max_cycles < 1");
+    return b->b.solve_step(tol, max_cycles, cycles, rho);
+}
+
+int mg_batch_autotune(mg_batch b, int reps) {
+    if (!b || reps < 1) return fail(MG_ERR_ARG, "NULL batch or reps < 1");
+    for (auto *x : b->b.s) {
+        int rc = x->begin_step(nullptr);
+        if (!rc) rc = x->autotune(reps, nullptr);
+        if (rc) return rc;
+    }
+    if (b->b.exec) { cudaGraphExecDestroy(b->b.exec); b->b.exec = nullptr; }
+    return MG_OK;
+}
+
+mg_handle mg_batch_handle(mg_batch b, int i) {
+    if (!b || i < 0 || i >= (int)b->b.h.size()) return nullptr;
+    return b->b.h[i];
+}
+
+void mg_batch_destroy(mg_batch b) { delete b; }
 
 void mg_destroy(mg_handle h) {
     if (!h) return;

@@ -11,15 +11,14 @@
 //      from the start of the phase.
 // Two implementations compute exactly the same sequence of IEEE operations per cell:
 //   - the phased path launches one kernel per phase (the reference implementation);
-//   - the fused path runs one kernel per sweep on 32 x 64 output tiles with a 4-cell halo,
-//     recomputing the halo redundantly so that no tile depends on another within a sweep.
+//   - the fused path runs one kernel per sweep on output tiles (32 x 64 by default; the shape
+//     is chosen per grid) with a 4-cell halo, recomputing the halo redundantly so that no tile
+//     depends on another within a sweep.
 #include "arith.cuh"
 
 namespace segmg {
 
 namespace {
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ---------------------------------------------------------------------------------------
 // Snapshot: G and f of every cell and the member mask of every 32-cell piece of every row and
@@ -42,24 +41,13 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int n = L.n, m = L.m, p = L.pitch;
-    // stage pn, u (mirror-clamped, 36 x 36), w (34 x 34) and F, rhs (32 x 32) with asynchronous
-    // copies so that all of the tile's loads are in flight together
-    for (int q = tid; q < R * R; q += 256) {
-        int a = q / R, b = q % R;
-        int gi = clampi(i0 - 2 + a, 0, n - 1), gj = clampi(j0 - 2 + b, 0, m - 1);
-        cp_async_elem(&sP[a][b], L.pn + (size_t)gi * p + gj, true);
-        cp_async_elem(&sU[a][b], L.u + (size_t)gi * p + gj, true);
-        if (kStage && a >= 1 && a < R - 1 && b >= 1 && b < R - 1 && !L.wb)
-            cp_async_elem(&sW[kStage ? a : 0][kStage ? b : 0], L.w + (size_t)gi * p + gj, true);
-        if (kStage && a >= 2 && a < R - 2 && b >= 2 && b < R - 2) {
-            int fi = min(i0 - 2 + a, n - 1), fj = min(j0 - 2 + b, m - 1);
-            cp_async_elem(&sF[kStage ? a - 2 : 0][kStage ? b - 2 : 0], L.F + (size_t)fi * p + fj, true);
-            if (L.has_rhs)
-                cp_async_elem(&sR[kStage ? a - 2 : 0][kStage ? b - 2 : 0], L.rhs + (size_t)fi * p + fj, true);
-        }
+    // stage pn, u (mirror-clamped, 36 x 36), w and F, rhs (FP32 only) with vector loads
+    load_halo2<T>(sP, L.pn, sU, L.u, i0, j0, n, m, p, tid);
+    if (kStage) {
+        if (!L.wb) load_halo2<T>(reinterpret_cast<T (*)[37]>(sW), L.w, nullptr, nullptr, i0, j0, n, m, p, tid);
+        load_tile32<T>(reinterpret_cast<T (*)[33]>(sF), L.F, reinterpret_cast<T (*)[33]>(sR),
+                       L.has_rhs ? L.rhs : nullptr, i0, j0, n, m, p, tid);
     }
-    cp_async_commit();
-    cp_async_wait_all();
     __syncthreads();
     for (int q = tid; q < 34 * 34; q += 256) {
         int a = 1 + q / 34, b = 1 + q % 34;
@@ -199,38 +187,47 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
 // checkerboard colour (cell (a, b) of the region at [(a + b) & 1][a][b >> 1]), so the cells a
 // warp updates in one colour phase, and their neighbours, are consecutive words.
 // ---------------------------------------------------------------------------------------
-constexpr int kOH = 32, kOW = 64, kH = 4, kRH = kOH + 2 * kH, kRW = kOW + 2 * kH, kHW = kRW / 2;
-constexpr int kThreads = 256;
-constexpr int kMaxTasks = 2 * (kOH > kOW ? kOH : kOW) + 8;
-// member-mask words held per region line: rows span 4 pieces (j0/32 - 1 .. j0/32 + 2), columns 3
-constexpr int kRowPieces = 4, kColPieces = 3;
+constexpr int kH = 4;
 
-template <typename T> struct VecOf;
-template <> struct VecOf<float> { using type = float4; static constexpr int n = 4; };
-template <> struct VecOf<double> { using type = double2; static constexpr int n = 2; };
+// Tile shapes of the fused sweep (output rows x columns, threads): both sides multiples of 32 so
+// that every 32-cell piece of a row or column lies wholly inside one tile.  The shape changes
+// only the memory traffic, never the results (tested); the autotuner picks one per grid.
+template <int OH_, int OW_, int NT_>
+struct TileShape {
+    static constexpr int OH = OH_, OW = OW_, NT = NT_;
+    static constexpr int RH = OH + 2 * kH, RW = OW + 2 * kH, HW = RW / 2;
+    static constexpr int MaxTasks = 2 * (OH > OW ? OH : OW) + 8;
+    // member-mask words per region line: OW/32 + 2 pieces along a row, OH/32 + 2 along a column
+    static constexpr int RowPieces = OW / 32 + 2, ColPieces = OH / 32 + 2;
+    static constexpr int MkLines = RH > RW ? RH : RW, MkPieces = RowPieces > ColPieces ? RowPieces : ColPieces;
+};
+using Tile0 = TileShape<32, 64, 256>;
+using Tile1 = TileShape<32, 32, 128>;
+using Tile2 = TileShape<64, 64, 512>;
 
-template <typename T>
+template <typename T, typename TS>
 struct FusedSmem {
-    T u[2][kRH][kHW];
-    T G[2][kRH][kHW];
-    T f[2][kRH][kHW];
-    uint32_t mk[kRW][kRowPieces];   // rowwise: [region row][piece]; colwise: [region column][piece]
-    T endv[kMaxTasks][2];
+    T u[2][TS::RH][TS::HW];
+    T G[2][TS::RH][TS::HW];
+    T f[2][TS::RH][TS::HW];
+    uint32_t mk[TS::MkLines][TS::MkPieces];   // rowwise: [region row][piece]; colwise: [region column][piece]
+    T endv[TS::MaxTasks][2];
 };
 
 #define SW_AT(arr, a, b) S.arr[((a) + (b)) & 1][a][(b) >> 1]
 
 // Member bit of region cell (a, b) in the tile's sweep (masks staged in S.mk).
-template <typename T, bool ROWWISE>
-__device__ __forceinline__ bool tile_member(const FusedSmem<T> &S, int a, int b) {
+template <typename T, typename TS, bool ROWWISE>
+__device__ __forceinline__ bool tile_member(const FusedSmem<T, TS> &S, int a, int b) {
     if (ROWWISE) return (S.mk[a][(b + 28) >> 5] >> ((b - kH) & 31)) & 1u;
     return (S.mk[b][(a + 28) >> 5] >> ((a - kH) & 31)) & 1u;
 }
 
 // One checkerboard phase over the region cells within distance 3 - ph of the output tile.
 // INTERIOR: the whole region lies inside the domain, so every updated cell has four faces.
-template <typename T, int SWEEP, bool INTERIOR>
-__device__ __forceinline__ void rb_phase(FusedSmem<T> &S, const LevelView<T> &L, int ph, int i0, int j0) {
+template <typename T, typename TS, int SWEEP, bool INTERIOR>
+__device__ __forceinline__ void rb_phase(FusedSmem<T, TS> &S, const LevelView<T> &L, int ph, int i0, int j0) {
+    constexpr int kRH = TS::RH, kRW = TS::RW, kHW = TS::HW, kThreads = TS::NT;
     constexpr bool rev = (SWEEP & 1) != 0;
     const int colour = rev ? 1 - ph : ph, lo = 1 + ph, other = 1 - colour;
     const int R = kRH - 2 * lo;
@@ -245,7 +242,7 @@ __device__ __forceinline__ void rb_phase(FusedSmem<T> &S, const LevelView<T> &L,
             if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
             hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
         }
-        if (tile_member<T, (SWEEP < 2)>(S, a, b)) continue;
+        if (tile_member<T, TS, (SWEEP < 2)>(S, a, b)) continue;
         const T gc = S.G[colour][a][k];
         const T aS = face(gc, S.G[other][a + 1][k], hS), aN = face(gc, S.G[other][a - 1][k], hN);
         const T aE = face(gc, S.G[other][a][k + x], hE), aW = face(gc, S.G[other][a][k + x - 1], hW);
@@ -255,10 +252,12 @@ __device__ __forceinline__ void rb_phase(FusedSmem<T> &S, const LevelView<T> &L,
     }
 }
 
-template <typename T, int SWEEP>
-__global__ void __launch_bounds__(kThreads) k_sweep(LevelView<T> L) {
+template <typename T, int SWEEP, typename TS>
+__global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
+    constexpr int kOH = TS::OH, kOW = TS::OW, kRH = TS::RH, kRW = TS::RW, kThreads = TS::NT;
+    constexpr int kRowPieces = TS::RowPieces, kColPieces = TS::ColPieces;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FusedSmem<T> &S = *reinterpret_cast<FusedSmem<T> *>(smem_raw);
+    FusedSmem<T, TS> &S = *reinterpret_cast<FusedSmem<T, TS> *>(smem_raw);
     using V = typename VecOf<T>::type;
     constexpr int VN = VecOf<T>::n, NV = kRW / VN, NVO = kOW / VN;
     constexpr bool rowwise = SWEEP < 2, rev = (SWEEP & 1) != 0;
@@ -325,14 +324,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep(LevelView<T> L) {
     const bool interior = i0 - kH >= 0 && i0 - kH + kRH <= n && j0 - kH >= 0 && j0 - kH + kRW <= m;
 #pragma unroll
     for (int ph = 0; ph < 2; ++ph) {
-        if (interior) rb_phase<T, SWEEP, true>(S, L, ph, i0, j0);
-        else rb_phase<T, SWEEP, false>(S, L, ph, i0, j0);
+        if (interior) rb_phase<T, TS, SWEEP, true>(S, L, ph, i0, j0);
+        else rb_phase<T, TS, SWEEP, false>(S, L, ph, i0, j0);
         __syncthreads();
     }
     // ---- partial-line phases: lines at distance 1, then 0, one parity each.  A task is one
-    // piece of one line: rowwise the two 32-column pieces of the output (mask index 1, 2),
-    // colwise the 32-row piece of the output (mask index 1).
-    constexpr int npc = rowwise ? 2 : 1;
+    // piece of one line: rowwise the 32-column pieces of the output, colwise its 32-row pieces
+    // (mask index 1 + pc: the region starts 4 cells before the first output piece).
+    constexpr int npc = rowwise ? kOW / 32 : kOH / 32;
     const int len_lim = rowwise ? m : n, gl_lim = rowwise ? n : m;
 #pragma unroll
     for (int ph = 0; ph < 2; ++ph) {
@@ -343,7 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(LevelView<T> L) {
         for (int t = tid; t < ntask; t += kThreads) {
             const int li = lfirst + t / npc, pc = t % npc;
             const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
-            const int gstart = rowwise ? j0 + 32 * pc : i0;
+            const int gstart = rowwise ? j0 + 32 * pc : i0 + 32 * pc;
             const int s0 = kH + 32 * pc;
             const bool ok = gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim;
             const int len = ok ? min(32, len_lim - gstart) : 0;
@@ -361,7 +360,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(LevelView<T> L) {
         for (int t = tid; t < ntask; t += kThreads) {
             const int li = lfirst + t / npc, pc = t % npc;
             const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
-            const int gstart = rowwise ? j0 + 32 * pc : i0;
+            const int gstart = rowwise ? j0 + 32 * pc : i0 + 32 * pc;
             if (!(gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim)) continue;
             const uint32_t mk = S.mk[li][1 + pc];
             if (!mk) continue;
@@ -445,41 +444,53 @@ void launch_sweep_phased(const LevelView<T> &L, int sweep, cudaStream_t st) {
     }
 }
 
-template <typename T, int SW>
+template <typename T, int SW, typename TS>
 static void set_fused_attr() {
-    cudaFuncSetAttribute(k_sweep<T, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(FusedSmem<T>));
+    cudaFuncSetAttribute(k_sweep<T, SW, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(FusedSmem<T, TS>));
+}
+
+template <typename T, typename TS>
+static void set_fused_attrs() {
+    set_fused_attr<T, 0, TS>(); set_fused_attr<T, 1, TS>(); set_fused_attr<T, 2, TS>(); set_fused_attr<T, 3, TS>();
 }
 
 // Raises the dynamic shared-memory limit of the fused sweep kernels on the current device
 // (called once per set-up, before any stream capture).
 void prepare_smoother_kernels() {
-    set_fused_attr<float, 0>(); set_fused_attr<float, 1>(); set_fused_attr<float, 2>(); set_fused_attr<float, 3>();
-    set_fused_attr<double, 0>(); set_fused_attr<double, 1>(); set_fused_attr<double, 2>(); set_fused_attr<double, 3>();
+    set_fused_attrs<float, Tile0>(); set_fused_attrs<float, Tile1>(); set_fused_attrs<float, Tile2>();
+    set_fused_attrs<double, Tile0>(); set_fused_attrs<double, Tile1>(); set_fused_attrs<double, Tile2>();
 }
 
-template <typename T, int SW>
+template <typename T, int SW, typename TS>
 static void launch_fused_one(const LevelView<T> &L, cudaStream_t st) {
-    size_t smem = sizeof(FusedSmem<T>);
-    dim3 grid((L.m + kOW - 1) / kOW, (L.n + kOH - 1) / kOH);
-    k_sweep<T, SW><<<grid, kThreads, smem, st>>>(L);
+    size_t smem = sizeof(FusedSmem<T, TS>);
+    dim3 grid((L.m + TS::OW - 1) / TS::OW, (L.n + TS::OH - 1) / TS::OH);
+    k_sweep<T, SW, TS><<<grid, TS::NT, smem, st>>>(L);
+}
+
+template <typename T, typename TS>
+static void launch_fused_shape(const LevelView<T> &L, int sweep, cudaStream_t st) {
+    switch (sweep) {
+        case 0: launch_fused_one<T, 0, TS>(L, st); break;
+        case 1: launch_fused_one<T, 1, TS>(L, st); break;
+        case 2: launch_fused_one<T, 2, TS>(L, st); break;
+        default: launch_fused_one<T, 3, TS>(L, st); break;
+    }
 }
 
 template <typename T>
-void launch_sweep_fused(const LevelView<T> &L, int sweep, cudaStream_t st) {
-    switch (sweep) {
-        case 0: launch_fused_one<T, 0>(L, st); break;
-        case 1: launch_fused_one<T, 1>(L, st); break;
-        case 2: launch_fused_one<T, 2>(L, st); break;
-        default: launch_fused_one<T, 3>(L, st); break;
-    }
+void launch_sweep_fused(const LevelView<T> &L, int sweep, int shape, cudaStream_t st) {
+    if (shape == 1) launch_fused_shape<T, Tile1>(L, sweep, st);
+    else if (shape == 2) launch_fused_shape<T, Tile2>(L, sweep, st);
+    else launch_fused_shape<T, Tile0>(L, sweep, st);
 }
 
 template void launch_snapshot<float>(const LevelView<float> &, const double *, cudaStream_t);
 template void launch_snapshot<double>(const LevelView<double> &, const double *, cudaStream_t);
 template void launch_sweep_phased<float>(const LevelView<float> &, int, cudaStream_t);
 template void launch_sweep_phased<double>(const LevelView<double> &, int, cudaStream_t);
-template void launch_sweep_fused<float>(const LevelView<float> &, int, cudaStream_t);
-template void launch_sweep_fused<double>(const LevelView<double> &, int, cudaStream_t);
+template void launch_sweep_fused<float>(const LevelView<float> &, int, int, cudaStream_t);
+template void launch_sweep_fused<double>(const LevelView<double> &, int, int, cudaStream_t);
 
 }  // namespace segmg

@@ -22,7 +22,9 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
            "mg_get_level", "mg_get_stats", "mg_segment_host", "mg_get_stream", "mg_destroy",
-           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc"]
+           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes",
+           "mg_batch_setup", "mg_batch_solve_step", "mg_batch_autotune", "mg_batch_handle",
+           "mg_batch_destroy"]
 
 
 class Params(C.Structure):
@@ -91,6 +93,14 @@ def lib():
             "mg_get_stream": ([vp], vp),
             "mg_time_kernels": ([vp, i, i, D], i),
             "mg_residual_norm_noalloc": ([vp, vp, vp, i, i, P, D, vp], i),
+            "mg_autotune": ([vp, i, C.POINTER(i)], i),
+            "mg_set_tile_shapes": ([vp, C.POINTER(i)], i),
+            "mg_batch_setup": ([C.POINTER(vp), i, C.POINTER(vp), C.POINTER(i), C.POINTER(i),
+                                C.POINTER(D), C.POINTER(i), P, vp], i),
+            "mg_batch_solve_step": ([vp, d, i, C.POINTER(i), D], i),
+            "mg_batch_autotune": ([vp, i], i),
+            "mg_batch_handle": ([vp, i], vp),
+            "mg_batch_destroy": ([vp], None),
             "mg_destroy": ([vp], None),
             "mg_strerror": ([i], C.c_char_p),
             "mg_last_error": ([], C.c_char_p),
@@ -199,13 +209,13 @@ class Solver:
     def mask(self, out=None):
         import torch
         out = torch.empty((self.n, self.m), dtype=torch.uint8, device=self.image.device) if out is None else out
-        _check(lib().mg_mask(self._h, C.c_void_p(out.data_ptr())), "mg_mask")
+        _check(lib().mg_mask(self._handle, C.c_void_p(out.data_ptr())), "mg_mask")
         return out
 
     def phi(self):
         import torch
         out = torch.empty((self.n, self.m), dtype=self.dtype, device=self.image.device)
-        _check(lib().mg_get_phi(self._h, C.c_void_p(out.data_ptr())), "mg_get_phi")
+        _check(lib().mg_get_phi(self._handle, C.c_void_p(out.data_ptr())), "mg_get_phi")
         return out
 
     def set_phi(self, phi):
@@ -227,6 +237,32 @@ class Solver:
         _check(lib().mg_get_level(self._h, l, f, C.c_void_p(out.data_ptr())), "mg_get_level")
         return out
 
+    @classmethod
+    def view(cls, handle, n, m, params, device):
+        """A non-owning Solver over a handle that belongs to a Batch."""
+        import torch
+        obj = cls.__new__(cls)
+        obj._h = None
+        obj._view = C.c_void_p(handle)
+        obj.n, obj.m, obj.params = n, m, params
+        obj.dtype = torch.float64 if params.precision == MG_F64 else torch.float32
+        obj.image = torch.empty(0, device=device)
+        return obj
+
+    @property
+    def _handle(self):
+        return self._h if self._h else self._view
+
+    def autotune(self, reps=2):
+        """mg_autotune inside the current step; returns the tile shape chosen per grid."""
+        out = (C.c_int * 16)()
+        _check(lib().mg_autotune(self._h, reps, out), "mg_autotune")
+        return list(out)[: self.params.levels - 1]
+
+    def set_tile_shapes(self, shapes):
+        arr = (C.c_int * 16)(*shapes)
+        _check(lib().mg_set_tile_shapes(self._h, arr), "mg_set_tile_shapes")
+
     def time_kernels(self, level=0, reps=3):
         """Mean ms per launch of snapshot, sweeps A..D and residual on `level` (mg_time_kernels)."""
         out = (C.c_double * 6)()
@@ -235,8 +271,60 @@ class Solver:
 
     def stats(self) -> dict:
         s = Stats()
-        _check(lib().mg_get_stats(self._h, C.byref(s)), "mg_get_stats")
+        _check(lib().mg_get_stats(self._handle, C.byref(s)), "mg_get_stats")
         return s.as_dict()
+
+
+class Batch:
+    """Many images solved together (mg_batch_*): one CUDA graph launch per V-cycle."""
+
+    def __init__(self, images, markers, params, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the solver has no CPU path")
+        self.images = [im.contiguous() for im in images]
+        cnt = len(self.images)
+        self._mks = [np.ascontiguousarray(np.asarray(mk, dtype=np.float64).reshape(-1, 2)) for mk in markers]
+        self.params = list(params)
+        imgs = (C.c_void_p * cnt)(*[im.data_ptr() for im in self.images])
+        ns = (C.c_int * cnt)(*[im.shape[0] for im in self.images])
+        ms = (C.c_int * cnt)(*[im.shape[1] for im in self.images])
+        mks = (C.POINTER(C.c_double) * cnt)(*[mk.ctypes.data_as(C.POINTER(C.c_double)) for mk in self._mks])
+        ks = (C.c_int * cnt)(*[len(mk) for mk in self._mks])
+        ps = (Params * cnt)(*self.params)
+        torch.cuda.current_stream().synchronize()
+        b = C.c_void_p()
+        _check(lib().mg_batch_setup(C.byref(b), cnt, imgs, ns, ms, mks, ks, ps,
+                                    None if stream is None else C.c_void_p(stream)), "mg_batch_setup")
+        self._b = b
+        self.count = cnt
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().mg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, reps=2):
+        _check(lib().mg_batch_autotune(self._b, reps), "mg_batch_autotune")
+
+    def solve_step(self, tol, max_cycles=60, raise_on_cap=False):
+        cyc = (C.c_int * self.count)()
+        rho = (C.c_double * self.count)()
+        rc = lib().mg_batch_solve_step(self._b, tol, max_cycles, cyc, rho)
+        if rc != 0 and (rc != -5 or raise_on_cap):
+            _check(rc, "mg_batch_solve_step")
+        return list(cyc), list(rho)
+
+    def solver(self, i) -> "Solver":
+        h = lib().mg_batch_handle(self._b, i)
+        n, m = self.images[i].shape
+        return Solver.view(h, n, m, self.params[i], self.images[i].device)
 
 
 def residual_norm_noalloc(phi, w, F, params: Params) -> float:

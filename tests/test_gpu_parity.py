@@ -218,3 +218,52 @@ def test_large_tiles_cover_boundary_and_interior(segmg):
             s.vcycle()
         outs.append(s.phi().cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_every_tile_shape_gives_the_same_result(segmg, precision):
+    prec = segmg.MG_F64 if precision == "f64" else segmg.MG_F32
+    img, mk, _ = synth.ellipses(233, 301, 10, (20, 120), 8, 0.05, 13)
+    outs = []
+    for sh in (0, 1, 2):
+        s, p = gpu_solver(segmg, img, mk, precision=prec, levels=5)
+        s.set_tile_shapes([sh] * (p.levels - 1))
+        s.begin_step()
+        for _ in range(2):
+            s.vcycle()
+        outs.append(s.phi().cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_autotune_keeps_the_state_and_the_results(segmg):
+    img, mk, _ = synth.ellipses(320, 320, 10, (20, 120), 8, 0.05, 14)
+    s1, _ = gpu_solver(segmg, img, mk)
+    s1.solve_step(1e-6, 50)
+    s2, p = gpu_solver(segmg, img, mk)
+    s2.begin_step()
+    shapes = s2.autotune(reps=1)
+    assert len(shapes) == p.levels - 1 and all(0 <= x <= 2 for x in shapes)
+    s2.end_step()          # the autotuner restored phi: this step changed nothing
+    s2.solve_step(1e-6, 50)
+    assert np.array_equal(s1.phi().cpu().numpy(), s2.phi().cpu().numpy())
+
+
+def test_batch_equals_individual_solves(segmg):
+    shapes = [(64, 64), (96, 80), (128, 128), (40, 200), (160, 160)]
+    imgs, mks, params = [], [], []
+    for q, (n, m) in enumerate(shapes):
+        img, mk, _ = synth.ellipses(n, m, 6, (10, min(n, m) / 2), 4 + q, 0.05, 30 + q)
+        imgs.append(img.astype(np.float32))
+        mks.append(mk)
+        params.append(segmg.default_params(n, m))
+    b = segmg.Batch([torch.as_tensor(x, device="cuda") for x in imgs], mks, params)
+    cyc, rho = b.solve_step(1e-6, 60)
+    for q in range(len(shapes)):
+        s, _ = gpu_solver(segmg, imgs[q], mks[q])
+        c, r = s.solve_step(1e-6, 60)
+        assert cyc[q] == c and rho[q] == r
+        v = b.solver(q)
+        assert np.array_equal(v.phi().cpu().numpy(), s.phi().cpu().numpy())
+        assert np.array_equal(v.mask().cpu().numpy(), s.mask().cpu().numpy())
+        assert v.stats()["steps"] == 1
+    b.close()
