@@ -297,13 +297,10 @@ __global__ void __launch_bounds__(256) k_coarse(LevelView<T> L, ModelParams mp, 
             const int last = min(k + bw, N - 1), cnt = last - k;
             for (int t = tid; t < cnt; t += nt) band[(size_t)(k + 1 + t) * bw1 + (1 + t)] /= lkk;
             __syncthreads();
-            const int pairs = cnt * (cnt + 1) / 2;
-            for (int t = tid; t < pairs; t += nt) {
-                // t -> (ii, jj) with 0 <= jj <= ii < cnt
-                int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-                while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-                while (ii * (ii + 1) / 2 > t) --ii;
-                int jj = t - ii * (ii + 1) / 2;
+            for (int t = tid; t < cnt * cnt; t += nt) {
+                // the trailing triangle: rows ii >= columns jj (integer indexing only)
+                const int ii = t / cnt, jj = t - ii * cnt;
+                if (jj > ii) continue;
                 int ri = k + 1 + ii, rj = k + 1 + jj;
                 band[(size_t)ri * bw1 + (ri - rj)] -= band[(size_t)ri * bw1 + (ri - k)] * band[(size_t)rj * bw1 + (rj - k)];
             }
