@@ -188,8 +188,16 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
 int mg_autotune(mg_handle h, int reps, int *shapes);
 /* Sets the fused-sweep tile shape of grids 0..levels-2 (values 0..2 as above). */
 int mg_set_tile_shapes(mg_handle h, const int *shapes);
+/* The bottom of the V-cycle in one block: with MG_F32 / MG_MIXED storage, the Spencer-Chen
+ * model and the fused smoother, the grids from the largest one whose whole sub-cycle (pn, u, w,
+ * F, rhs, G, f, u0, masks and the coarsest solve's scratch) fits in 200 KB of shared memory
+ * down to the coarsest run as one kernel of one 1024-thread block instead of one launch per
+ * grid and phase.  It performs the same operations per cell as the per-grid kernels, so the
+ * results are identical.  enable = 1 (the default at set-up) or 0; *first_level (may be NULL)
+ * gets the first grid it covers, -1 when it does not apply.  Errors: MG_ERR_ARG. */
+int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level);
 
-/* Batches (BASELINE config 4 style workloads; no counterpart in the paper): `count` images of
+/* Batches (many images at once; no counterpart in the paper): `count` images of
  * their own sizes solved together.  Each V-cycle of mg_batch_solve_step is one CUDA graph
  * launch whose branches are the images' V-cycles; a branch is a conditional graph node that
  * the device skips once that image's residual has reached the tolerance.

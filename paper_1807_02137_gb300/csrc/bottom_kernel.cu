@@ -1,0 +1,373 @@
+// bottom_kernel.cu -- the bottom of the FAS V-cycle (the small grids and the coarsest solve) in
+// one block.
+//
+// On the small grids (here at most 64 x 64 cells) every kernel of the V-cycle is latency-bound:
+// a launch costs far more than its few thousand cells of work.  This kernel runs the whole
+// sub-cycle from grid `lb` down to the coarsest and back in a single 1024-thread block, with
+// every grid resident in shared memory.  It executes, cell by cell, exactly the arithmetic of
+// the per-grid kernels (the snapshot, the per-phase smoother, the residual, the transfers and the
+// coarsest solve share their device functions), so the V-cycle's results do not change.
+// Used for the FP32 / mixed storage and the Spencer-Chen model when the grids fit in shared
+// memory; the host falls back to the per-grid kernels otherwise.
+#include "arith.cuh"
+#include "coarse_body.cuh"
+#include "reduce.cuh"
+
+#include <algorithm>
+
+namespace segmg {
+
+namespace {
+
+constexpr int kBT = kCoarseThreads;   // threads of the block (the coarsest solve uses them all)
+
+// One grid in shared memory (row pitch m).
+struct BGrid {
+    int n, m, npm, npn;
+    float cdiff, inv_tau, Sigma, inv_2h, beta;
+    float *pn, *u, *w, *F, *rhs, *G, *f, *u0;
+    uint32_t *mrow, *mcol;   // [2][n][npm], [2][m][npn]
+    int has_rhs;
+};
+
+__device__ __forceinline__ int cl(int v, int hi) { return v < 0 ? 0 : (v > hi ? hi : v); }
+
+// G = w / |grad phi|_beta of every cell at phi = pn + uu (mirror-clamped neighbours), as the
+// tile kernels form it.
+__device__ void b_G(const BGrid &B, const float *uu) {
+    const int n = B.n, m = B.m;
+    for (int q = threadIdx.x; q < n * m; q += kBT) {
+        const int i = q / m, j = q - (q / m) * m;
+        const int s = cl(i + 1, n - 1) * m + j, nn = cl(i - 1, n - 1) * m + j;
+        const int e = i * m + cl(j + 1, m - 1), w = i * m + cl(j - 1, m - 1);
+        B.G[q] = cell_G(B.w[q], B.pn[s], B.pn[nn], B.pn[e], B.pn[w], uu[s], uu[nn], uu[e], uu[w], B.inv_2h, B.beta);
+    }
+    __syncthreads();
+}
+
+// Snapshot (as k_snapshot): G, f, jump class and the member masks of every piece.
+__device__ void b_snapshot(const BGrid &B, uint8_t *star) {
+    const int n = B.n, m = B.m;
+    b_G(B, B.u);
+    for (int q = threadIdx.x; q < n * m; q += kBT) {
+        const int i = q / m, j = q - (q / m) * m;
+        const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
+        const float gc = B.G[q];
+        const float aS = face(gc, B.G[hS ? q + m : q], hS), aN = face(gc, B.G[hN ? q - m : q], hN);
+        const float aE = face(gc, B.G[hE ? q + 1 : q], hE), aW = face(gc, B.G[hW ? q - 1 : q], hW);
+        const float pc = B.pn[q];
+        float ds = mul_rn(aS, sub_rn(B.pn[cl(i + 1, n - 1) * m + j], pc));
+        ds = fma_rn(aN, sub_rn(B.pn[cl(i - 1, n - 1) * m + j], pc), ds);
+        ds = fma_rn(aE, sub_rn(B.pn[i * m + cl(j + 1, m - 1)], pc), ds);
+        ds = fma_rn(aW, sub_rn(B.pn[i * m + cl(j - 1, m - 1)], pc), ds);
+        float base = add_rn(B.F[q], 0.0f);
+        if (B.has_rhs) base = add_rn(base, B.rhs[q]);
+        B.f[q] = fma_rn(-B.cdiff, ds, base);
+        const float big = 3.0e38f;
+        const float vS = hS ? aS : big, vN = hN ? aN : big, vE = hE ? aE : big, vW = hW ? aW : big;
+        const float mn = fminf(fminf(vS, vN), fminf(vE, vW));
+        const float mx = fmaxf(fmaxf(hS ? aS : -1.f, hN ? aN : -1.f), fmaxf(hE ? aE : -1.f, hW ? aW : -1.f));
+        const int am = vS == mn ? 0 : (vN == mn ? 1 : (vE == mn ? 2 : 3));
+        const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
+        star[q] = (cnt >= 2 && mx > mul_rn(B.Sigma, mn)) ? (uint8_t)(1u << am) : (uint8_t)0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = warp; t < n * B.npm; t += kBT / 32) {          // row pieces: sweeps A, B
+        const int i = t / B.npm, pc = t - (t / B.npm) * B.npm;
+        const int j = pc * 32 + lane, len = min(32, m - pc * 32);
+        const uint8_t s = lane < len ? star[i * m + j] : 0;
+        const uint32_t mA = members_of(__ballot_sync(0xffffffffu, s & 1u), len);
+        const uint32_t mB = members_of(__ballot_sync(0xffffffffu, s & 2u), len);
+        if (lane == 0) {
+            B.mrow[(0 * n + i) * B.npm + pc] = mA;
+            B.mrow[(1 * n + i) * B.npm + pc] = mB;
+        }
+    }
+    for (int t = warp; t < m * B.npn; t += kBT / 32) {          // column pieces: sweeps C, D
+        const int j = t / B.npn, pc = t - (t / B.npn) * B.npn;
+        const int i = pc * 32 + lane, len = min(32, n - pc * 32);
+        const uint8_t s = lane < len ? star[i * m + j] : 0;
+        const uint32_t mC = members_of(__ballot_sync(0xffffffffu, s & 4u), len);
+        const uint32_t mD = members_of(__ballot_sync(0xffffffffu, s & 8u), len);
+        if (lane == 0) {
+            B.mcol[(0 * m + j) * B.npn + pc] = mC;
+            B.mcol[(1 * m + j) * B.npn + pc] = mD;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool b_member(const BGrid &B, int sweep, int i, int j) {
+    if (sweep < 2) return (B.mrow[(sweep * B.n + i) * B.npm + (j >> 5)] >> (j & 31)) & 1u;
+    return (B.mcol[((sweep - 2) * B.m + j) * B.npn + (i >> 5)] >> (i & 31)) & 1u;
+}
+
+// One directional sweep of Hybrid Smoother 2 in the parallel ordering (as k_rb + k_seg).
+__device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
+    const int n = B.n, m = B.m;
+    const bool rev = sweep & 1, rowwise = sweep < 2;
+    for (int ph = 0; ph < 2; ++ph) {
+        const int colour = rev ? 1 - ph : ph;
+        for (int q = threadIdx.x; q < n * m; q += kBT) {
+            const int i = q / m, j = q - (q / m) * m;
+            if (((i + j) & 1) != colour || b_member(B, sweep, i, j)) continue;
+            const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
+            const int oS = hS ? q + m : q, oN = hN ? q - m : q, oE = hE ? q + 1 : q, oW = hW ? q - 1 : q;
+            const float gc = B.G[q];
+            const float aS = face(gc, B.G[oS], hS), aN = face(gc, B.G[oN], hN);
+            const float aE = face(gc, B.G[oE], hE), aW = face(gc, B.G[oW], hW);
+            B.u[q] = point_relax(B.cdiff, B.inv_tau, aS, aN, aE, aW, B.u[oS], B.u[oN], B.u[oE], B.u[oW], B.f[q]);
+        }
+        __syncthreads();
+    }
+    const int nlines = rowwise ? n : m, llen = rowwise ? m : n, npieces = rowwise ? B.npm : B.npn;
+    for (int ph = 0; ph < 2; ++ph) {
+        const int parity = rev ? 1 - ph : ph;
+        const int nl = (nlines - parity + 1) / 2, ntask = nl * npieces;
+        auto cell = [&](int line, int t) { return rowwise ? line * m + t : t * m + line; };
+        // end values at the piece boundaries, read before any group of this phase is solved
+        for (int t = threadIdx.x; t < ntask; t += kBT) {
+            const int line = parity + 2 * (t / npieces), piece = t - (t / npieces) * npieces;
+            const int t0 = piece * 32, len = min(32, llen - t0);
+            endv[2 * t] = t0 > 0 ? B.u[cell(line, t0 - 1)] : 0.f;
+            endv[2 * t + 1] = t0 + len < llen ? B.u[cell(line, t0 + len)] : 0.f;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ntask; t += kBT) {
+            const int line = parity + 2 * (t / npieces), piece = t - (t / npieces) * npieces;
+            const int t0 = piece * 32, len = min(32, llen - t0);
+            const uint32_t mk = rowwise ? B.mrow[(sweep * n + line) * B.npm + piece]
+                                        : B.mcol[((sweep - 2) * m + line) * B.npn + piece];
+            int s = 0;
+            while (s < len) {
+                if (!((mk >> s) & 1u)) { ++s; continue; }
+                const int a0 = s;
+                while (s < len && ((mk >> s) & 1u)) ++s;
+                const int rl = s - a0;
+                const float endp = a0 == 0 ? endv[2 * t] : B.u[cell(line, t0 + a0 - 1)];
+                const float endn = (a0 + rl == len) ? endv[2 * t + 1] : B.u[cell(line, t0 + a0 + rl)];
+                auto at = [&](int r) -> RunCell<float> {
+                    const int tt = t0 + a0 + r, o = cell(line, tt);
+                    const int i = rowwise ? line : tt, j = rowwise ? tt : line;
+                    const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
+                    const int oS = hS ? o + m : o, oN = hN ? o - m : o, oE = hE ? o + 1 : o, oW = hW ? o - 1 : o;
+                    const float gc = B.G[o];
+                    const float aS = face(gc, B.G[oS], hS), aN = face(gc, B.G[oN], hN);
+                    const float aE = face(gc, B.G[oE], hE), aW = face(gc, B.G[oW], hW);
+                    RunCell<float> c;
+                    if (rowwise) { c.ap = aW; c.an = aE; c.ax1 = aS; c.ax2 = aN; c.ux1 = B.u[oS]; c.ux2 = B.u[oN]; }
+                    else         { c.ap = aN; c.an = aS; c.ax1 = aE; c.ax2 = aW; c.ux1 = B.u[oE]; c.ux2 = B.u[oW]; }
+                    c.f = B.f[o];
+                    return c;
+                };
+                thomas_run<float>(rl, B.cdiff, B.inv_tau, endp, endn, at,
+                                  [&](int r, float x) { B.u[cell(line, t0 + a0 + r)] = x; });
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// out = rhs - L(pn + uu) (mode 0) or out += L(pn + uu) (mode 1), as k_residual.
+__device__ void b_residual(const BGrid &B, const float *uu, float *out, int mode) {
+    const int n = B.n, m = B.m;
+    b_G(B, uu);
+    for (int q = threadIdx.x; q < n * m; q += kBT) {
+        const int i = q / m, j = q - (q / m) * m;
+        const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
+        const int s = cl(i + 1, n - 1) * m + j, nn = cl(i - 1, n - 1) * m + j;
+        const int e = i * m + cl(j + 1, m - 1), w = i * m + cl(j - 1, m - 1);
+        const float gc = B.G[q];
+        const float aS = face(gc, B.G[hS ? q + m : q], hS), aN = face(gc, B.G[hN ? q - m : q], hN);
+        const float aE = face(gc, B.G[hE ? q + 1 : q], hE), aW = face(gc, B.G[hW ? q - 1 : q], hW);
+        const float pc = B.pn[q], uc = uu[q];
+        float fl = mul_rn(aS, add_rn(sub_rn(B.pn[s], pc), sub_rn(uu[s], uc)));
+        fl = fma_rn(aN, add_rn(sub_rn(B.pn[nn], pc), sub_rn(uu[nn], uc)), fl);
+        fl = fma_rn(aE, add_rn(sub_rn(B.pn[e], pc), sub_rn(uu[e], uc)), fl);
+        fl = fma_rn(aW, add_rn(sub_rn(B.pn[w], pc), sub_rn(uu[w], uc)), fl);
+        const float Lv = sub_rn(fma_rn(B.cdiff, fl, -add_rn(B.F[q], 0.0f)), mul_rn(B.inv_tau, uc));
+        if (mode == 0) out[q] = B.has_rhs ? sub_rn(B.rhs[q], Lv) : -Lv;
+        else out[q] = add_rn(out[q], Lv);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int fw(int I, int n, int *idx, double *wt) {
+    const int q = 2 * I + 1;
+    if (q + 1 < n) { idx[0] = q - 1; idx[1] = q; idx[2] = q + 1; wt[0] = 0.25; wt[1] = 0.5; wt[2] = 0.25; return 3; }
+    idx[0] = q - 1; idx[1] = q; wt[0] = 0.5; wt[1] = 0.5;
+    return 2;
+}
+
+__device__ __forceinline__ int bl(int p, int nc, int *idx, double *wt) {
+    if (p & 1) { idx[0] = (p - 1) / 2; wt[0] = 1.0; return 1; }
+    if (p == 0) { idx[0] = 0; wt[0] = 1.0; return 1; }
+    const int I = p / 2 - 1;
+    if (I + 1 < nc) { idx[0] = I; idx[1] = I + 1; wt[0] = 0.5; wt[1] = 0.5; return 2; }
+    idx[0] = I; wt[0] = 1.0;
+    return 1;
+}
+
+// Full weighting of `src` (fine grid F) into dst (and dst2) on the coarse grid C, as k_restrict.
+__device__ void b_restrict(const BGrid &F, const float *src, const BGrid &C, float *dst, float *dst2) {
+    for (int q = threadIdx.x; q < C.n * C.m; q += kBT) {
+        const int I = q / C.m, J = q - (q / C.m) * C.m;
+        int ri[3], ci[3];
+        double rw[3], cw[3];
+        const int nr = fw(I, F.n, ri, rw), nk = fw(J, F.m, ci, cw);
+        float s = 0.f;
+        for (int a = 0; a < nr; ++a) {
+            float row = 0.f;
+            for (int b = 0; b < nk; ++b) row = fma_rn((float)cw[b], src[ri[a] * F.m + ci[b]], row);
+            s = fma_rn((float)rw[a], row, s);
+        }
+        dst[q] = s;
+        if (dst2) dst2[q] = s;
+    }
+    __syncthreads();
+}
+
+// fine.u += P (coarse.u - coarse.u0), as k_interp_add.
+__device__ void b_interp_add(const BGrid &F, const BGrid &C) {
+    for (int q = threadIdx.x; q < F.n * F.m; q += kBT) {
+        const int i = q / F.m, j = q - (q / F.m) * F.m;
+        int ri[2], ci[2];
+        double rw[2], cw[2];
+        const int nr = bl(i, C.n, ri, rw), nk = bl(j, C.m, ci, cw);
+        float s = 0.f;
+        for (int a = 0; a < nr; ++a)
+            for (int b = 0; b < nk; ++b) {
+                const int o = ri[a] * C.m + ci[b];
+                s = fma_rn((float)(rw[a] * cw[b]), sub_rn(C.u[o], C.u0[o]), s);
+            }
+        F.u[q] = add_rn(F.u[q], s);
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+// Shared-memory bytes the bottom kernel needs for grids lb .. L-1.
+size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L) {
+    size_t b = 0;
+    int maxN = 0, maxTask = 0;
+    for (int l = lb; l < L; ++l) {
+        const size_t N = (size_t)n[l] * m[l];
+        const int npm = (m[l] + 31) / 32, npn = (n[l] + 31) / 32;
+        b += 8 * N * sizeof(float);
+        b += sizeof(uint32_t) * (2 * (size_t)n[l] * npm + 2 * (size_t)m[l] * npn);
+        maxN = std::max(maxN, (int)N);
+        maxTask = std::max(maxTask, std::max((n[l] + 1) / 2 * npm, (m[l] + 1) / 2 * npn));
+    }
+    b += (size_t)maxN;                                   // star bytes
+    b = (b + 15) / 16 * 16;
+    b += sizeof(float) * 2 * (size_t)maxTask;           // end values
+    b = (b + 15) / 16 * 16;
+    b += sizeof(double) * coarse_scratch_doubles(n[L - 1], m[L - 1]);
+    return b;
+}
+
+__global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red[33];
+    __shared__ int s_err;
+    __shared__ BGrid Bs[kMaxLevels];
+    __shared__ size_t s_off[3];
+    // ---- carve shared memory (one thread), then load pn, w, F of every grid and u, rhs of grid lb
+    if (threadIdx.x == 0) {
+        size_t off = 0;
+        int maxN = 0, maxTask = 0;
+        for (int l = A.lb; l < A.L; ++l) {
+            const LevelView<float> &G = A.g[l];
+            BGrid &B = Bs[l];
+            B.n = G.n; B.m = G.m; B.npm = (G.m + 31) / 32; B.npn = (G.n + 31) / 32;
+            B.cdiff = G.cdiff; B.inv_tau = G.inv_tau; B.Sigma = G.Sigma; B.inv_2h = G.inv_2h; B.beta = G.beta;
+            B.has_rhs = G.has_rhs;
+            const int N = G.n * G.m;
+            float **arr[] = {&B.pn, &B.u, &B.w, &B.F, &B.rhs, &B.G, &B.f, &B.u0};
+            for (float **a : arr) { *a = reinterpret_cast<float *>(sm + off); off += sizeof(float) * N; }
+            B.mrow = reinterpret_cast<uint32_t *>(sm + off); off += sizeof(uint32_t) * 2 * (size_t)G.n * B.npm;
+            B.mcol = reinterpret_cast<uint32_t *>(sm + off); off += sizeof(uint32_t) * 2 * (size_t)G.m * B.npn;
+            maxN = max(maxN, N);
+            maxTask = max(maxTask, max((G.n + 1) / 2 * B.npm, (G.m + 1) / 2 * B.npn));
+        }
+        s_off[0] = off;                                 // star bytes
+        off += maxN;
+        off = (off + 15) / 16 * 16;
+        s_off[1] = off;                                 // end values
+        off += sizeof(float) * 2 * maxTask;
+        off = (off + 15) / 16 * 16;
+        s_off[2] = off;                                 // coarsest-solve scratch
+    }
+    __syncthreads();
+    for (int l = A.lb; l < A.L; ++l) {
+        const LevelView<float> &G = A.g[l];
+        const BGrid &B = Bs[l];
+        for (int q = threadIdx.x; q < B.n * B.m; q += kBT) {
+            const int i = q / B.m, j = q - (q / B.m) * B.m;
+            const size_t o = (size_t)i * G.pitch + j;
+            B.pn[q] = G.pn[o];
+            B.w[q] = weight_at(G, o);
+            B.F[q] = G.F[o];
+            if (l == A.lb) {
+                B.u[q] = G.u[o];
+                B.rhs[q] = G.has_rhs ? G.rhs[o] : 0.f;
+            }
+        }
+    }
+    uint8_t *star = sm + s_off[0];
+    float *endv = reinterpret_cast<float *>(sm + s_off[1]);
+    double *cscr = reinterpret_cast<double *>(sm + s_off[2]);
+    __syncthreads();
+    auto smooth = [&](int l) {
+        b_snapshot(Bs[l], star);
+        for (int k = 0; k < 4; ++k) b_sweep(Bs[l], k, endv);
+    };
+    // ---- down: smoothing, residual, restriction, coarse right-hand side (Algorithm 1)
+    for (int l = A.lb; l < A.L - 1; ++l) {
+        for (int t = 0; t < A.nu1; ++t) smooth(l);
+        b_residual(Bs[l], Bs[l].u, Bs[l].f, 0);
+        b_restrict(Bs[l], Bs[l].f, Bs[l + 1], Bs[l + 1].rhs, nullptr);
+        b_restrict(Bs[l], Bs[l].u, Bs[l + 1], Bs[l + 1].u, Bs[l + 1].u0);
+        b_residual(Bs[l + 1], Bs[l + 1].u0, Bs[l + 1].rhs, 1);
+    }
+    // ---- the coarsest solve
+    {
+        const BGrid &C = Bs[A.L - 1];
+        CoarseGrid<float> cg{C.n, C.m, C.m, C.pn, C.u, C.w, nullptr, C.F, C.rhs, C.has_rhs, C.inv_2h, C.inv_tau, C.beta};
+        int it;
+        double res;
+        coarse_solve_block<float>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol, cscr, red,
+                                  &s_err, &it, &res);
+        if (threadIdx.x == 0) {
+            A.sc->picard = it;
+            A.sc->coarse_res = res;
+            if (s_err) A.sc->err = 1;
+        }
+    }
+    // ---- up: interpolation and post-smoothing
+    for (int l = A.L - 2; l >= A.lb; --l) {
+        b_interp_add(Bs[l], Bs[l + 1]);
+        for (int t = 0; t < A.nu2; ++t) smooth(l);
+    }
+    // ---- grid lb's increment back to global memory
+    {
+        const LevelView<float> &G = A.g[A.lb];
+        const BGrid &B = Bs[A.lb];
+        for (int q = threadIdx.x; q < B.n * B.m; q += kBT) {
+            const int i = q / B.m, j = q - (q / B.m) * B.m;
+            G.u[(size_t)i * G.pitch + j] = B.u[q];
+        }
+    }
+}
+
+void prepare_bottom_kernel() {
+    cudaFuncSetAttribute(k_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBottomSmemMax);
+}
+
+void launch_bottom(const BottomArgs &A, size_t smem, cudaStream_t st) {
+    k_bottom<<<1, kBT, smem, st>>>(A);
+}
+
+}  // namespace segmg

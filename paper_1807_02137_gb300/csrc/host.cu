@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/segmg.h"
@@ -104,6 +105,7 @@ struct SolverBase {
     virtual int time_kernels(int level, int reps, double *ms) = 0;
     virtual int autotune(int reps, int *out) = 0;
     virtual int set_shapes(const int *shapes) = 0;
+    virtual int set_bottom(int enable) = 0;
 };
 
 template <typename T>
@@ -141,6 +143,8 @@ struct Solver final : SolverBase {
     cudaGraphExec_t gexec = nullptr;
     long long launches = 0, graph_nodes = 0;
     int shape[kMaxLevels] = {};   // fused-sweep tile shape per grid (mg_autotune)
+    int lb = -1;                  // first grid of the one-block bottom kernel (-1: not used)
+    size_t lb_smem = 0;
     ModelParams mp{};
 
     ~Solver() override { release(); }
@@ -232,7 +236,43 @@ struct Solver final : SolverBase {
         dmk = (double *)(base + o_mk);
         dhull = (double *)(base + o_hull);
         CK(cudaMallocHost(&hsc, sizeof(Scalars)));
+        set_bottom(1);
         return MG_OK;
+    }
+
+    // The bottom kernel runs grids lb .. nlev-1 in one block when the storage is FP32 (or mixed),
+    // the model is Spencer-Chen, the fused smoother is selected and at least two grids fit in
+    // its shared memory; lb is the largest grid that fits.
+    int set_bottom(int enable) override {
+        lb = -1;
+        lb_smem = 0;
+        if (enable && sizeof(T) == 4 && p.model == MG_MODEL_SC && p.smoother == MG_SMOOTH_FUSED) {
+            int ns[kMaxLevels], ms[kMaxLevels];
+            for (int l = 0; l < nlev; ++l) { ns[l] = lv[l].n; ms[l] = lv[l].m; }
+            for (int l = nlev - 2; l >= 0; --l) {
+                size_t b = bottom_smem_bytes(ns, ms, l, nlev);
+                if (b > kBottomSmemMax) break;
+                lb = l;
+                lb_smem = b;
+            }
+        }
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        return lb;
+    }
+
+    void launch_bottom_cycle() {
+        if constexpr (std::is_same<T, float>::value) {
+            BottomArgs a{};
+            a.lb = lb; a.L = nlev; a.nu1 = p.nu1; a.nu2 = p.nu2;
+            for (int l = lb; l < nlev; ++l) a.g[l] = view(l);
+            a.mp = mp;
+            a.A1frac = A1 / ((double)n * m);
+            a.h2nm_coarse = h2nm(nlev - 1);
+            a.coarse_tol = p.coarse_tol;
+            a.coarse_maxit = p.coarse_maxit;
+            a.sc = dsc;
+            launch_bottom(a, lb_smem, st);
+        }
     }
 
     int reset(const void *image, const double *mk, int k) override {
@@ -347,6 +387,11 @@ struct Solver final : SolverBase {
     }
 
     void cycle(int l) {
+        if (l == lb) {
+            launch_bottom_cycle();
+            ++launches;
+            return;
+        }
         if (l == nlev - 1) {
             launch_coarse_solve<T>(view(l), nullptr, mp, A1 / ((double)n * m), h2nm(l), p.coarse_maxit,
                                    p.coarse_tol, coarse, dsc, st);
@@ -804,6 +849,7 @@ int mg_setup(mg_handle *out, const void *image, int n, int m, const double *mark
     if ((rc = check_markers(markers_xy, k, n, m))) return rc;
     prepare_smoother_kernels();
     prepare_coarse_kernels();
+    prepare_bottom_kernel();
     SolverBase *s = nullptr;
     if (p->precision != MG_F64) {
         auto *t = new Solver<float>();
@@ -940,6 +986,13 @@ int mg_set_tile_shapes(mg_handle h, const int *shapes) {
     return h->s->set_shapes(shapes);
 }
 
+int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level) {
+    if (!h || (enable != 0 && enable != 1)) return fail(MG_ERR_ARG, "NULL handle or enable not 0/1");
+    int lb = h->s->set_bottom(enable);
+    if (first_level) *first_level = lb;
+    return MG_OK;
+}
+
 int mg_batch_setup(mg_batch *out, int count, const void *const *images, const int *n, const int *m,
                    const double *const *markers, const int *k, const mg_params *params, void *stream) {
     if (!out) return fail(MG_ERR_ARG, "out is NULL");
@@ -954,6 +1007,7 @@ int mg_batch_setup(mg_batch *out, int count, const void *const *images, const in
     }
     prepare_smoother_kernels();
     prepare_coarse_kernels();
+    prepare_bottom_kernel();
     auto *B = new mg_batch_s();
     Batch &b = B->b;
     int rc = MG_OK;

@@ -127,4 +127,18 @@ void launch_coarse_solve(const LevelView<T> &L, const double *area_dummy, ModelP
 size_t coarse_scratch_doubles(int n, int m);
 void prepare_coarse_kernels();
 
+// bottom_kernel.cu: grids lb .. L-1 of a V-cycle (FP32 storage, Spencer-Chen model) in one block
+struct BottomArgs {
+    int lb, L, nu1, nu2;
+    LevelView<float> g[kMaxLevels];
+    ModelParams mp;
+    double A1frac, h2nm_coarse, coarse_tol;
+    int coarse_maxit;
+    Scalars *sc;
+};
+constexpr size_t kBottomSmemMax = 200 * 1024;
+size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L);
+void prepare_bottom_kernel();
+void launch_bottom(const BottomArgs &A, size_t smem, cudaStream_t st);
+
 }  // namespace segmg

@@ -1,0 +1,42 @@
+// reduce.cuh -- deterministic block-wide FP64 reductions shared by the cycle kernels.
+#pragma once
+
+namespace segmg {
+
+// Sum of a per-thread double over the block (blockDim.x * blockDim.y <= 1024); the result is
+// returned to every thread.  Fixed reduction order: deterministic.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        double s = tid < (nt + 31) / 32 ? red[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (tid == 0) red[32] = s;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double *red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        double s = tid < (nt + 31) / 32 ? red[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+        if (tid == 0) red[32] = s;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace segmg

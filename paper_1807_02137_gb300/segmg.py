@@ -22,7 +22,7 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
            "mg_get_level", "mg_get_stats", "mg_segment_host", "mg_get_stream", "mg_destroy",
-           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes",
+           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel",
            "mg_batch_setup", "mg_batch_solve_step", "mg_batch_autotune", "mg_batch_handle",
            "mg_batch_destroy"]
 
@@ -95,6 +95,7 @@ def lib():
             "mg_residual_norm_noalloc": ([vp, vp, vp, i, i, P, D, vp], i),
             "mg_autotune": ([vp, i, C.POINTER(i)], i),
             "mg_set_tile_shapes": ([vp, C.POINTER(i)], i),
+            "mg_set_bottom_kernel": ([vp, i, C.POINTER(i)], i),
             "mg_batch_setup": ([C.POINTER(vp), i, C.POINTER(vp), C.POINTER(i), C.POINTER(i),
                                 C.POINTER(D), C.POINTER(i), P, vp], i),
             "mg_batch_solve_step": ([vp, d, i, C.POINTER(i), D], i),
@@ -262,6 +263,13 @@ class Solver:
     def set_tile_shapes(self, shapes):
         arr = (C.c_int * 16)(*shapes)
         _check(lib().mg_set_tile_shapes(self._h, arr), "mg_set_tile_shapes")
+
+    def set_bottom_kernel(self, enable=True):
+        """Switches the one-block bottom-of-cycle kernel (mg_set_bottom_kernel); returns the first
+        grid it covers, or -1 when it does not apply."""
+        lb = C.c_int(-1)
+        _check(lib().mg_set_bottom_kernel(self._h, 1 if enable else 0, C.byref(lb)), "mg_set_bottom_kernel")
+        return lb.value
 
     def time_kernels(self, level=0, reps=3):
         """Mean ms per launch of snapshot, sweeps A..D and residual on `level` (mg_time_kernels)."""

@@ -267,3 +267,36 @@ def test_batch_equals_individual_solves(segmg):
         assert np.array_equal(v.mask().cpu().numpy(), s.mask().cpu().numpy())
         assert v.stats()["steps"] == 1
     b.close()
+
+
+@pytest.mark.parametrize("shape,levels,nu", [((256, 256), 7, (2, 2)), ((200, 170), 6, (1, 3)),
+                                             ((61, 47), 4, (2, 2)), ((130, 97), 6, (3, 0))])
+@pytest.mark.parametrize("precision", ["f32", "mixed"])
+def test_bottom_kernel_equals_per_grid_kernels(segmg, shape, levels, nu, precision):
+    # the one-block bottom of the V-cycle performs the per-grid kernels' operations cell by cell
+    prec = segmg.MG_MIXED if precision == "mixed" else segmg.MG_F32
+    n, m = shape
+    img, mk, _ = synth.ellipses(n, m, 8, (8, min(n, m) / 2), 6, 0.05, 40 + n)
+    outs, firsts, stats = [], [], []
+    for on in (1, 0):
+        s, p = gpu_solver(segmg, img, mk, precision=prec, levels=levels, nu1=nu[0], nu2=nu[1])
+        firsts.append(s.set_bottom_kernel(bool(on)))
+        s.begin_step()
+        rhos = [s.vcycle() for _ in range(3)]
+        outs.append((s.phi().cpu().numpy(), rhos))
+        stats.append(s.stats())
+    assert firsts[0] >= 0 and firsts[1] == -1
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+    assert stats[0]["picard_last"] == stats[1]["picard_last"]
+
+
+def test_bottom_kernel_applies_only_where_it_is_exact(segmg):
+    img, mk, _ = synth.ellipses(128, 128, 6, (10, 60), 4, 0.05, 3)
+    for kw, expect in (({}, True), ({"precision": segmg.MG_F64}, False),
+                       ({"model": segmg.MG_MODEL_RC}, False), ({"smoother": 1}, False)):
+        s, p = gpu_solver(segmg, img, mk, levels=6, **kw)
+        lb = s.set_bottom_kernel(True)
+        assert (lb >= 0) == expect
+        if expect:
+            assert 0 <= lb <= p.levels - 2
