@@ -30,16 +30,35 @@ struct BGrid {
     int has_rhs;
 };
 
-__device__ __forceinline__ int cl(int v, int hi) { return v < 0 ? 0 : (v > hi ? hi : v); }
+
+// Thread layout over an array with `cols` columns: TX = the power of two >= cols (at most the
+// block size) threads along a row, kBT / TX rows at a time; no integer division per cell.
+struct Map2 {
+    int tx, ty, TX, TY;
+};
+__device__ __forceinline__ Map2 map_for(int cols) {
+    int lg = cols <= 1 ? 0 : 32 - __clz(cols - 1);
+    lg = min(lg, 10);
+    Map2 r;
+    r.TX = 1 << lg;
+    r.TY = kBT >> lg;
+    r.tx = threadIdx.x & (r.TX - 1);
+    r.ty = threadIdx.x >> lg;
+    return r;
+}
+#define FOR_CELLS(M, n, m, i, j)                                                              \
+    for (int i = (M).ty; i < (n); i += (M).TY)                                                \
+        for (int j = (M).tx; j < (m); j += (M).TX)
 
 // G = w / |grad phi|_beta of every cell at phi = pn + uu (mirror-clamped neighbours), as the
 // tile kernels form it.
 __device__ void b_G(const BGrid &B, const float *uu) {
     const int n = B.n, m = B.m;
-    for (int q = threadIdx.x; q < n * m; q += kBT) {
-        const int i = q / m, j = q - (q / m) * m;
-        const int s = cl(i + 1, n - 1) * m + j, nn = cl(i - 1, n - 1) * m + j;
-        const int e = i * m + cl(j + 1, m - 1), w = i * m + cl(j - 1, m - 1);
+    const Map2 M = map_for(m);
+    FOR_CELLS(M, n, m, i, j) {
+        const int q = i * m + j;
+        const int s = (i + 1 < n ? i + 1 : n - 1) * m + j, nn = (i > 0 ? i - 1 : 0) * m + j;
+        const int e = q + (j + 1 < m ? 1 : 0), w = q - (j > 0 ? 1 : 0);
         B.G[q] = cell_G(B.w[q], B.pn[s], B.pn[nn], B.pn[e], B.pn[w], uu[s], uu[nn], uu[e], uu[w], B.inv_2h, B.beta);
     }
     __syncthreads();
@@ -49,17 +68,19 @@ __device__ void b_G(const BGrid &B, const float *uu) {
 __device__ void b_snapshot(const BGrid &B, uint8_t *star) {
     const int n = B.n, m = B.m;
     b_G(B, B.u);
-    for (int q = threadIdx.x; q < n * m; q += kBT) {
-        const int i = q / m, j = q - (q / m) * m;
+    const Map2 M = map_for(m);
+    FOR_CELLS(M, n, m, i, j) {
+        const int q = i * m + j;
         const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
+        const int oS = hS ? q + m : q, oN = hN ? q - m : q, oE = hE ? q + 1 : q, oW = hW ? q - 1 : q;
         const float gc = B.G[q];
-        const float aS = face(gc, B.G[hS ? q + m : q], hS), aN = face(gc, B.G[hN ? q - m : q], hN);
-        const float aE = face(gc, B.G[hE ? q + 1 : q], hE), aW = face(gc, B.G[hW ? q - 1 : q], hW);
+        const float aS = face(gc, B.G[oS], hS), aN = face(gc, B.G[oN], hN);
+        const float aE = face(gc, B.G[oE], hE), aW = face(gc, B.G[oW], hW);
         const float pc = B.pn[q];
-        float ds = mul_rn(aS, sub_rn(B.pn[cl(i + 1, n - 1) * m + j], pc));
-        ds = fma_rn(aN, sub_rn(B.pn[cl(i - 1, n - 1) * m + j], pc), ds);
-        ds = fma_rn(aE, sub_rn(B.pn[i * m + cl(j + 1, m - 1)], pc), ds);
-        ds = fma_rn(aW, sub_rn(B.pn[i * m + cl(j - 1, m - 1)], pc), ds);
+        float ds = mul_rn(aS, sub_rn(B.pn[oS], pc));
+        ds = fma_rn(aN, sub_rn(B.pn[oN], pc), ds);
+        ds = fma_rn(aE, sub_rn(B.pn[oE], pc), ds);
+        ds = fma_rn(aW, sub_rn(B.pn[oW], pc), ds);
         float base = add_rn(B.F[q], 0.0f);
         if (B.has_rhs) base = add_rn(base, B.rhs[q]);
         B.f[q] = fma_rn(-B.cdiff, ds, base);
@@ -73,28 +94,28 @@ __device__ void b_snapshot(const BGrid &B, uint8_t *star) {
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int t = warp; t < n * B.npm; t += kBT / 32) {          // row pieces: sweeps A, B
-        const int i = t / B.npm, pc = t - (t / B.npm) * B.npm;
-        const int j = pc * 32 + lane, len = min(32, m - pc * 32);
-        const uint8_t s = lane < len ? star[i * m + j] : 0;
-        const uint32_t mA = members_of(__ballot_sync(0xffffffffu, s & 1u), len);
-        const uint32_t mB = members_of(__ballot_sync(0xffffffffu, s & 2u), len);
-        if (lane == 0) {
-            B.mrow[(0 * n + i) * B.npm + pc] = mA;
-            B.mrow[(1 * n + i) * B.npm + pc] = mB;
+    for (int i = warp; i < n; i += kBT / 32)                  // row pieces: sweeps A, B
+        for (int pc = 0; pc < B.npm; ++pc) {
+            const int j = pc * 32 + lane, len = min(32, m - pc * 32);
+            const uint8_t s = lane < len ? star[i * m + j] : 0;
+            const uint32_t mA = members_of(__ballot_sync(0xffffffffu, s & 1u), len);
+            const uint32_t mB = members_of(__ballot_sync(0xffffffffu, s & 2u), len);
+            if (lane == 0) {
+                B.mrow[(0 * n + i) * B.npm + pc] = mA;
+                B.mrow[(1 * n + i) * B.npm + pc] = mB;
+            }
         }
-    }
-    for (int t = warp; t < m * B.npn; t += kBT / 32) {          // column pieces: sweeps C, D
-        const int j = t / B.npn, pc = t - (t / B.npn) * B.npn;
-        const int i = pc * 32 + lane, len = min(32, n - pc * 32);
-        const uint8_t s = lane < len ? star[i * m + j] : 0;
-        const uint32_t mC = members_of(__ballot_sync(0xffffffffu, s & 4u), len);
-        const uint32_t mD = members_of(__ballot_sync(0xffffffffu, s & 8u), len);
-        if (lane == 0) {
-            B.mcol[(0 * m + j) * B.npn + pc] = mC;
-            B.mcol[(1 * m + j) * B.npn + pc] = mD;
+    for (int j = warp; j < m; j += kBT / 32)                  // column pieces: sweeps C, D
+        for (int pc = 0; pc < B.npn; ++pc) {
+            const int i = pc * 32 + lane, len = min(32, n - pc * 32);
+            const uint8_t s = lane < len ? star[i * m + j] : 0;
+            const uint32_t mC = members_of(__ballot_sync(0xffffffffu, s & 4u), len);
+            const uint32_t mD = members_of(__ballot_sync(0xffffffffu, s & 8u), len);
+            if (lane == 0) {
+                B.mcol[(0 * m + j) * B.npn + pc] = mC;
+                B.mcol[(1 * m + j) * B.npn + pc] = mD;
+            }
         }
-    }
     __syncthreads();
 }
 
@@ -107,11 +128,15 @@ __device__ __forceinline__ bool b_member(const BGrid &B, int sweep, int i, int j
 __device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
     const int n = B.n, m = B.m;
     const bool rev = sweep & 1, rowwise = sweep < 2;
+    // checkerboard phases: the cells of one colour, two per row pair of threads' columns
+    const int mh = (m + 1) >> 1;
+    const Map2 MH = map_for(mh);
     for (int ph = 0; ph < 2; ++ph) {
         const int colour = rev ? 1 - ph : ph;
-        for (int q = threadIdx.x; q < n * m; q += kBT) {
-            const int i = q / m, j = q - (q / m) * m;
-            if (((i + j) & 1) != colour || b_member(B, sweep, i, j)) continue;
+        FOR_CELLS(MH, n, mh, i, k) {
+            const int j = 2 * k + ((i + colour) & 1);
+            if (j >= m || b_member(B, sweep, i, j)) continue;
+            const int q = i * m + j;
             const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
             const int oS = hS ? q + m : q, oN = hN ? q - m : q, oE = hE ? q + 1 : q, oW = hW ? q - 1 : q;
             const float gc = B.G[q];
@@ -121,34 +146,38 @@ __device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
         }
         __syncthreads();
     }
+    // partial-line phases: one warp per line of the phase's parity.  Lines of one parity do not
+    // interact, and the cells just outside a piece lie on the same line, so a warp reads the
+    // end values of all its pieces before it solves any run: no block-wide barrier is needed.
     const int nlines = rowwise ? n : m, llen = rowwise ? m : n, npieces = rowwise ? B.npm : B.npn;
+    const int step = rowwise ? 1 : m;                 // stride along a line
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int ph = 0; ph < 2; ++ph) {
         const int parity = rev ? 1 - ph : ph;
-        const int nl = (nlines - parity + 1) / 2, ntask = nl * npieces;
-        auto cell = [&](int line, int t) { return rowwise ? line * m + t : t * m + line; };
-        // end values at the piece boundaries, read before any group of this phase is solved
-        for (int t = threadIdx.x; t < ntask; t += kBT) {
-            const int line = parity + 2 * (t / npieces), piece = t - (t / npieces) * npieces;
-            const int t0 = piece * 32, len = min(32, llen - t0);
-            endv[2 * t] = t0 > 0 ? B.u[cell(line, t0 - 1)] : 0.f;
-            endv[2 * t + 1] = t0 + len < llen ? B.u[cell(line, t0 + len)] : 0.f;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < ntask; t += kBT) {
-            const int line = parity + 2 * (t / npieces), piece = t - (t / npieces) * npieces;
-            const int t0 = piece * 32, len = min(32, llen - t0);
-            const uint32_t mk = rowwise ? B.mrow[(sweep * n + line) * B.npm + piece]
-                                        : B.mcol[((sweep - 2) * m + line) * B.npn + piece];
-            int s = 0;
-            while (s < len) {
-                if (!((mk >> s) & 1u)) { ++s; continue; }
-                const int a0 = s;
-                while (s < len && ((mk >> s) & 1u)) ++s;
-                const int rl = s - a0;
-                const float endp = a0 == 0 ? endv[2 * t] : B.u[cell(line, t0 + a0 - 1)];
-                const float endn = (a0 + rl == len) ? endv[2 * t + 1] : B.u[cell(line, t0 + a0 + rl)];
+        const int nl = (nlines - parity + 1) / 2;
+        for (int li = warp; li < nl; li += kBT / 32) {
+            const int line = parity + 2 * li;
+            const int base = rowwise ? line * m : line;   // cell of position 0 on the line
+            const uint32_t *mks = rowwise ? B.mrow + (sweep * n + line) * B.npm
+                                          : B.mcol + ((sweep - 2) * m + line) * B.npn;
+            float *ev = endv + 2 * li * npieces;
+            for (int pc = lane; pc < npieces; pc += 32) {
+                const int t0 = pc * 32, len = min(32, llen - t0);
+                ev[2 * pc] = t0 > 0 ? B.u[base + (t0 - 1) * step] : 0.f;
+                ev[2 * pc + 1] = t0 + len < llen ? B.u[base + (t0 + len) * step] : 0.f;
+            }
+            __syncwarp();
+            for (int pc = 0; pc < npieces; ++pc) {
+                const uint32_t mk = mks[pc];
+                const uint32_t starts = mk & ~(mk << 1);
+                if (!((starts >> lane) & 1u)) continue;
+                const int t0 = pc * 32, len = min(32, llen - t0);
+                const uint32_t rest = ~(mk >> lane);
+                const int a0 = lane, rl = rest ? __ffs(rest) - 1 : 32 - lane;
+                const float endp = a0 == 0 ? ev[2 * pc] : B.u[base + (t0 + a0 - 1) * step];
+                const float endn = (a0 + rl == len) ? ev[2 * pc + 1] : B.u[base + (t0 + a0 + rl) * step];
                 auto at = [&](int r) -> RunCell<float> {
-                    const int tt = t0 + a0 + r, o = cell(line, tt);
+                    const int tt = t0 + a0 + r, o = base + tt * step;
                     const int i = rowwise ? line : tt, j = rowwise ? tt : line;
                     const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
                     const int oS = hS ? o + m : o, oN = hN ? o - m : o, oE = hE ? o + 1 : o, oW = hW ? o - 1 : o;
@@ -162,8 +191,9 @@ __device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
                     return c;
                 };
                 thomas_run<float>(rl, B.cdiff, B.inv_tau, endp, endn, at,
-                                  [&](int r, float x) { B.u[cell(line, t0 + a0 + r)] = x; });
+                                  [&](int r, float x) { B.u[base + (t0 + a0 + r) * step] = x; });
             }
+            __syncwarp();
         }
         __syncthreads();
     }
@@ -173,19 +203,19 @@ __device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
 __device__ void b_residual(const BGrid &B, const float *uu, float *out, int mode) {
     const int n = B.n, m = B.m;
     b_G(B, uu);
-    for (int q = threadIdx.x; q < n * m; q += kBT) {
-        const int i = q / m, j = q - (q / m) * m;
+    const Map2 M = map_for(m);
+    FOR_CELLS(M, n, m, i, j) {
+        const int q = i * m + j;
         const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
-        const int s = cl(i + 1, n - 1) * m + j, nn = cl(i - 1, n - 1) * m + j;
-        const int e = i * m + cl(j + 1, m - 1), w = i * m + cl(j - 1, m - 1);
+        const int oS = hS ? q + m : q, oN = hN ? q - m : q, oE = hE ? q + 1 : q, oW = hW ? q - 1 : q;
         const float gc = B.G[q];
-        const float aS = face(gc, B.G[hS ? q + m : q], hS), aN = face(gc, B.G[hN ? q - m : q], hN);
-        const float aE = face(gc, B.G[hE ? q + 1 : q], hE), aW = face(gc, B.G[hW ? q - 1 : q], hW);
+        const float aS = face(gc, B.G[oS], hS), aN = face(gc, B.G[oN], hN);
+        const float aE = face(gc, B.G[oE], hE), aW = face(gc, B.G[oW], hW);
         const float pc = B.pn[q], uc = uu[q];
-        float fl = mul_rn(aS, add_rn(sub_rn(B.pn[s], pc), sub_rn(uu[s], uc)));
-        fl = fma_rn(aN, add_rn(sub_rn(B.pn[nn], pc), sub_rn(uu[nn], uc)), fl);
-        fl = fma_rn(aE, add_rn(sub_rn(B.pn[e], pc), sub_rn(uu[e], uc)), fl);
-        fl = fma_rn(aW, add_rn(sub_rn(B.pn[w], pc), sub_rn(uu[w], uc)), fl);
+        float fl = mul_rn(aS, add_rn(sub_rn(B.pn[oS], pc), sub_rn(uu[oS], uc)));
+        fl = fma_rn(aN, add_rn(sub_rn(B.pn[oN], pc), sub_rn(uu[oN], uc)), fl);
+        fl = fma_rn(aE, add_rn(sub_rn(B.pn[oE], pc), sub_rn(uu[oE], uc)), fl);
+        fl = fma_rn(aW, add_rn(sub_rn(B.pn[oW], pc), sub_rn(uu[oW], uc)), fl);
         const float Lv = sub_rn(fma_rn(B.cdiff, fl, -add_rn(B.F[q], 0.0f)), mul_rn(B.inv_tau, uc));
         if (mode == 0) out[q] = B.has_rhs ? sub_rn(B.rhs[q], Lv) : -Lv;
         else out[q] = add_rn(out[q], Lv);
@@ -211,8 +241,8 @@ __device__ __forceinline__ int bl(int p, int nc, int *idx, double *wt) {
 
 // Full weighting of `src` (fine grid F) into dst (and dst2) on the coarse grid C, as k_restrict.
 __device__ void b_restrict(const BGrid &F, const float *src, const BGrid &C, float *dst, float *dst2) {
-    for (int q = threadIdx.x; q < C.n * C.m; q += kBT) {
-        const int I = q / C.m, J = q - (q / C.m) * C.m;
+    const Map2 M = map_for(C.m);
+    FOR_CELLS(M, C.n, C.m, I, J) {
         int ri[3], ci[3];
         double rw[3], cw[3];
         const int nr = fw(I, F.n, ri, rw), nk = fw(J, F.m, ci, cw);
@@ -222,6 +252,7 @@ __device__ void b_restrict(const BGrid &F, const float *src, const BGrid &C, flo
             for (int b = 0; b < nk; ++b) row = fma_rn((float)cw[b], src[ri[a] * F.m + ci[b]], row);
             s = fma_rn((float)rw[a], row, s);
         }
+        const int q = I * C.m + J;
         dst[q] = s;
         if (dst2) dst2[q] = s;
     }
@@ -230,8 +261,8 @@ __device__ void b_restrict(const BGrid &F, const float *src, const BGrid &C, flo
 
 // fine.u += P (coarse.u - coarse.u0), as k_interp_add.
 __device__ void b_interp_add(const BGrid &F, const BGrid &C) {
-    for (int q = threadIdx.x; q < F.n * F.m; q += kBT) {
-        const int i = q / F.m, j = q - (q / F.m) * F.m;
+    const Map2 M = map_for(F.m);
+    FOR_CELLS(M, F.n, F.m, i, j) {
         int ri[2], ci[2];
         double rw[2], cw[2];
         const int nr = bl(i, C.n, ri, rw), nk = bl(j, C.m, ci, cw);
@@ -241,6 +272,7 @@ __device__ void b_interp_add(const BGrid &F, const BGrid &C) {
                 const int o = ri[a] * C.m + ci[b];
                 s = fma_rn((float)(rw[a] * cw[b]), sub_rn(C.u[o], C.u0[o]), s);
             }
+        const int q = i * F.m + j;
         F.u[q] = add_rn(F.u[q], s);
     }
     __syncthreads();
@@ -264,7 +296,7 @@ size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L) {
     b = (b + 15) / 16 * 16;
     b += sizeof(float) * 2 * (size_t)maxTask;           // end values
     b = (b + 15) / 16 * 16;
-    b += sizeof(double) * coarse_scratch_doubles(n[L - 1], m[L - 1]);
+    b += sizeof(float) * coarse_scratch_elems(n[L - 1], m[L - 1]);
     return b;
 }
 
@@ -304,8 +336,9 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
     for (int l = A.lb; l < A.L; ++l) {
         const LevelView<float> &G = A.g[l];
         const BGrid &B = Bs[l];
-        for (int q = threadIdx.x; q < B.n * B.m; q += kBT) {
-            const int i = q / B.m, j = q - (q / B.m) * B.m;
+        const Map2 M = map_for(B.m);
+        FOR_CELLS(M, B.n, B.m, i, j) {
+            const int q = i * B.m + j;
             const size_t o = (size_t)i * G.pitch + j;
             B.pn[q] = G.pn[o];
             B.w[q] = weight_at(G, o);
@@ -318,7 +351,7 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
     }
     uint8_t *star = sm + s_off[0];
     float *endv = reinterpret_cast<float *>(sm + s_off[1]);
-    double *cscr = reinterpret_cast<double *>(sm + s_off[2]);
+    float *cscr = reinterpret_cast<float *>(sm + s_off[2]);
     __syncthreads();
     auto smooth = [&](int l) {
         b_snapshot(Bs[l], star);
@@ -355,10 +388,8 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
     {
         const LevelView<float> &G = A.g[A.lb];
         const BGrid &B = Bs[A.lb];
-        for (int q = threadIdx.x; q < B.n * B.m; q += kBT) {
-            const int i = q / B.m, j = q - (q / B.m) * B.m;
-            G.u[(size_t)i * G.pitch + j] = B.u[q];
-        }
+        const Map2 M = map_for(B.m);
+        FOR_CELLS(M, B.n, B.m, i, j) G.u[(size_t)i * G.pitch + j] = B.u[i * B.m + j];
     }
 }
 

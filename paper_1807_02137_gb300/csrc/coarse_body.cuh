@@ -8,6 +8,34 @@
 namespace segmg {
 
 constexpr int kCoarseThreads = 1024;
+constexpr int kWarpCoarseMax = 256;   // grids of at most this many cells are solved by one warp
+
+// The threads that run the coarsest solve: one warp (no block barriers) or the whole block.
+template <int NT>
+struct Team {
+    static __device__ __forceinline__ void sync() {
+        if constexpr (NT == 32) __syncwarp();
+        else __syncthreads();
+    }
+    template <typename C>
+    static __device__ __forceinline__ C sum(C v, double *red) {
+        if constexpr (NT != 32) {
+            return block_sum_t<C>(v, red);
+        } else {
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            return v;
+        }
+    }
+    template <typename C>
+    static __device__ __forceinline__ C max(C v, double *red) {
+        if constexpr (NT != 32) {
+            return block_max_t<C>(v, red);
+        } else {
+            for (int o = 16; o > 0; o >>= 1) v = max_t<C>(v, __shfl_xor_sync(0xffffffffu, v, o));
+            return v;
+        }
+    }
+};
 
 // A grid the coarsest solve reads (pn, w, F, rhs) and updates (u), row pitch `pitch`.
 template <typename T>
@@ -23,89 +51,115 @@ struct CoarseGrid {
 };
 
 // ---------------------------------------------------------------------------------------
-// Coarsest solve (Algorithm 1, "compute the exact solution"), one block, FP64.
-// Picard on the frozen coefficients: each step solves
-//   (mu/h^2 sum_X G_X + 1/tau) phi - mu/h^2 sum_X G_X phi_X = -(F - pn/tau + area + rhs)
-// (symmetric positive definite) by banded Cholesky with cells ordered along the shorter side,
-// until the nonlinear residual falls below tol times its initial value, a step changes no
-// value by more than 1e-14 of the largest, or maxit steps.
+// Coarsest solve (Algorithm 1, "compute the exact solution"), one block, in the storage
+// precision.  The unknown is the increment u of phi = pn + u.  Picard on the frozen
+// coefficients G (at phi): each step solves the symmetric positive definite system
+//   (mu/h^2 sum_X G_X + 1/tau) u - mu/h^2 sum_X G_X u_X = mu/h^2 sum_X G_X (pn_X - pn) - F - area - rhs
+// by banded Cholesky with cells ordered along the shorter side.  It stops when the nonlinear
+// residual falls below tol times its initial value, when a step changes no value by more than
+// kStat times max(1, max |phi|) (1e-14 in FP64, 1e-6 in FP32: rounding level), when in FP32 a
+// step no longer reduces the residual by 10% (it has reached the rounding floor), or after
+// maxit steps.
 // ---------------------------------------------------------------------------------------
-// All threads of the block must call it; scratch holds coarse_scratch_doubles(n, m) doubles.
-template <typename T>
-__device__ void coarse_solve_block(const CoarseGrid<T> &L, ModelParams mp, double A1frac, double h2nm,
-                                   int maxit, double tol, double *scratch, double *red, int *s_err,
-                                   int *it_out, double *res_out) {
+template <typename C>
+__device__ __forceinline__ C rsqrt_of(C s);
+template <>
+__device__ __forceinline__ float rsqrt_of<float>(float s) { return rsqrtf(s); }
+template <>
+__device__ __forceinline__ double rsqrt_of<double>(double s) { return 1.0 / sqrt(s); }
+
+// Run by the NT threads of a team (NT = 32: warp 0; else the whole block); scratch holds
+// coarse_scratch_elems(n, m) values of T.
+template <typename T, int NT>
+__device__ void coarse_solve_team(const CoarseGrid<T> &L, ModelParams mp, double A1frac, double h2nm,
+                                  int maxit, double tol, T *scratch, double *red, int *s_err,
+                                  int *it_out, double *res_out) {
+    using C = T;
+    using TM = Team<NT>;
+    constexpr bool kF32 = sizeof(T) == 4;
+    constexpr C kStat = kF32 ? C(1e-6) : C(1e-14);
     const int n = L.n, m = L.m, p = L.pitch, N = n * m;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = NT;
     const bool colmajor = m > n;
     const int bw = colmajor ? n : m, bw1 = bw + 1;
-    double *x = scratch, *G = x + N, *b = G + N, *y = b + N, *band = y + N;
-    const double hinv = 2.0 * (double)L.inv_2h;
-    const double cdiff = mp.mu * hinv * hinv;
-    const double inv_tau = (double)L.inv_tau, inv_2h = (double)L.inv_2h, beta = (double)L.beta;
+    C *x = scratch, *G = x + N, *b = G + N, *y = b + N, *band = y + N;
+    const C hinv = C(2) * L.inv_2h;
+    const C cdiff = C(mp.mu) * hinv * hinv;
+    const C inv_tau = L.inv_tau, inv_2h = L.inv_2h, beta = L.beta;
     auto idx = [&](int i, int j) { return colmajor ? j * n + i : i * m + j; };
+    auto pn_at = [&](int i, int j) { return (C)L.pn[(size_t)i * p + j]; };
     if (tid == 0) *s_err = 0;
     for (int q = tid; q < N; q += nt) {
         int i = q / m, j = q % m;
-        x[idx(i, j)] = (double)L.pn[(size_t)i * p + j] + (double)L.u[(size_t)i * p + j];
+        x[idx(i, j)] = (C)L.u[(size_t)i * p + j];
     }
-    __syncthreads();
-    // G at x and the Rada-Chen area term; returns the area term
-    auto coeffs = [&]() -> double {
-        double area = 0.0;
+    TM::sync();
+    // G at phi = pn + x and the Rada-Chen area term; returns the area term
+    auto coeffs = [&]() -> C {
+        C area = C(0);
         if (mp.model == 1) {
             double hs = 0.0;
-            for (int q = tid; q < N; q += nt) hs += 0.5 + atan(x[q] / mp.eps) / M_PI;
-            hs = block_sum(hs, red);
-            area = 2.0 * mp.nu * (h2nm * hs - A1frac);
+            for (int q = tid; q < N; q += nt) {
+                int i = q / m, j = q % m;
+                hs += 0.5 + atan(((double)pn_at(i, j) + (double)x[idx(i, j)]) / mp.eps) / M_PI;
+            }
+            hs = TM::template sum<double>(hs, red);
+            area = (C)(2.0 * mp.nu * (h2nm * hs - A1frac));
         }
         for (int q = tid; q < N; q += nt) {
             int i = q / m, j = q % m;
             int iS = min(i + 1, n - 1), iN = max(i - 1, 0), jE = min(j + 1, m - 1), jW = max(j - 1, 0);
-            double gy = (x[idx(iS, j)] - x[idx(iN, j)]) * inv_2h;
-            double gx = (x[idx(i, jE)] - x[idx(i, jW)]) * inv_2h;
-            G[idx(i, j)] = (double)(L.wb ? T(__bfloat162float(L.wb[(size_t)i * p + j])) : L.w[(size_t)i * p + j]) / sqrt(gx * gx + gy * gy + beta);
+            C gy = ((pn_at(iS, j) - pn_at(iN, j)) + (x[idx(iS, j)] - x[idx(iN, j)])) * inv_2h;
+            C gx = ((pn_at(i, jE) - pn_at(i, jW)) + (x[idx(i, jE)] - x[idx(i, jW)])) * inv_2h;
+            C w = L.wb ? C(__bfloat162float(L.wb[(size_t)i * p + j])) : (C)L.w[(size_t)i * p + j];
+            G[idx(i, j)] = w * rsqrt_of<C>(gx * gx + gy * gy + beta);
         }
-        __syncthreads();
+        TM::sync();
         return area;
     };
-    auto faceG = [&](int i, int j, int i2, int j2) { return 0.5 * (G[idx(i, j)] + G[idx(i2, j2)]); };
+    auto faceG = [&](int i, int j, int i2, int j2) { return C(0.5) * (G[idx(i, j)] + G[idx(i2, j2)]); };
     auto resnorm = [&]() -> double {
-        double area = coeffs();
-        double acc = 0.0;
+        C area = coeffs();
+        C acc = C(0);
         for (int q = tid; q < N; q += nt) {
             int i = q / m, j = q % m;
-            double xc = x[idx(i, j)], fl = 0.0;
-            if (i + 1 < n) fl += faceG(i, j, i + 1, j) * (x[idx(i + 1, j)] - xc);
-            if (i > 0) fl += faceG(i, j, i - 1, j) * (x[idx(i - 1, j)] - xc);
-            if (j + 1 < m) fl += faceG(i, j, i, j + 1) * (x[idx(i, j + 1)] - xc);
-            if (j > 0) fl += faceG(i, j, i, j - 1) * (x[idx(i, j - 1)] - xc);
+            const C xc = x[idx(i, j)], pc = pn_at(i, j);
+            C fl = C(0);
+            auto add = [&](int i2, int j2) { fl += faceG(i, j, i2, j2) * ((pn_at(i2, j2) - pc) + (x[idx(i2, j2)] - xc)); };
+            if (i + 1 < n) add(i + 1, j);
+            if (i > 0) add(i - 1, j);
+            if (j + 1 < m) add(i, j + 1);
+            if (j > 0) add(i, j - 1);
             size_t o = (size_t)i * p + j;
-            double pn = (double)L.pn[o];
-            double Lv = cdiff * fl - (double)L.F[o] - area - inv_tau * (xc - pn);
-            double r = (L.has_rhs ? (double)L.rhs[o] : 0.0) - Lv;
+            C Lv = cdiff * fl - (C)L.F[o] - area - inv_tau * xc;
+            C r = (L.has_rhs ? (C)L.rhs[o] : C(0)) - Lv;
             acc += r * r;
         }
-        return sqrt(block_sum(acc, red));
+        return sqrt((double)TM::template sum<C>(acc, red));
     };
     const double r0 = resnorm();
-    double res = r0;
+    double res = r0, res_prev = r0;
     int it = 0;
     while (it < maxit) {
         if (it > 0) {
             res = resnorm();
             if (res <= tol * r0 || res == 0.0) break;
+            if (kF32 && res > 0.9 * res_prev) break;
+            res_prev = res;
         }
         if (r0 == 0.0) break;
-        double area = coeffs();
-        for (int q = tid; q < N * bw1; q += nt) band[q] = 0.0;
-        __syncthreads();
+        C area = coeffs();
+        for (int q = tid; q < N * bw1; q += nt) band[q] = C(0);
+        TM::sync();
         for (int q = tid; q < N; q += nt) {
             int i = q / m, j = q % m, r = idx(i, j);
-            double diag = 0.0;
+            const C pc = pn_at(i, j);
+            C diag = C(0), pflux = C(0);
             auto off = [&](int i2, int j2) {
-                double a = cdiff * faceG(i, j, i2, j2);
+                C g = faceG(i, j, i2, j2);
+                C a = cdiff * g;
                 diag += a;
+                pflux += g * (pn_at(i2, j2) - pc);
                 int c = idx(i2, j2);
                 if (c < r) band[(size_t)r * bw1 + (r - c)] = -a;
             };
@@ -115,22 +169,23 @@ __device__ void coarse_solve_block(const CoarseGrid<T> &L, ModelParams mp, doubl
             if (j > 0) off(i, j - 1);
             band[(size_t)r * bw1] = diag + inv_tau;
             size_t o = (size_t)i * p + j;
-            b[r] = -((double)L.F[o] - inv_tau * (double)L.pn[o] + area + (L.has_rhs ? (double)L.rhs[o] : 0.0));
+            b[r] = cdiff * pflux - (C)L.F[o] - area - (L.has_rhs ? (C)L.rhs[o] : C(0));
         }
-        __syncthreads();
-        // right-looking banded Cholesky: band[r*bw1 + (r-c)] = L(r, c)
+        TM::sync();
+        // right-looking banded Cholesky: band[r*bw1 + (r-c)] = L(r, c); the diagonal entry
+        // keeps 1 / L(k, k) once column k is done
         for (int k = 0; k < N && !(*s_err); ++k) {
             if (tid == 0) {
-                double d = band[(size_t)k * bw1];
-                if (!(d > 0.0)) (*s_err) = 1;
-                else band[(size_t)k * bw1] = sqrt(d);
+                C d = band[(size_t)k * bw1];
+                if (!(d > C(0))) (*s_err) = 1;
+                else band[(size_t)k * bw1] = rsqrt_of<C>(d);
             }
-            __syncthreads();
+            TM::sync();
             if ((*s_err)) break;
-            const double lkk = band[(size_t)k * bw1];
+            const C rkk = band[(size_t)k * bw1];
             const int last = min(k + bw, N - 1), cnt = last - k;
-            for (int t = tid; t < cnt; t += nt) band[(size_t)(k + 1 + t) * bw1 + (1 + t)] /= lkk;
-            __syncthreads();
+            for (int t = tid; t < cnt; t += nt) band[(size_t)(k + 1 + t) * bw1 + (1 + t)] *= rkk;
+            TM::sync();
             for (int t = tid; t < cnt * cnt; t += nt) {
                 // the trailing triangle: rows ii >= columns jj (integer indexing only)
                 const int ii = t / cnt, jj = t - ii * cnt;
@@ -138,48 +193,63 @@ __device__ void coarse_solve_block(const CoarseGrid<T> &L, ModelParams mp, doubl
                 int ri = k + 1 + ii, rj = k + 1 + jj;
                 band[(size_t)ri * bw1 + (ri - rj)] -= band[(size_t)ri * bw1 + (ri - k)] * band[(size_t)rj * bw1 + (rj - k)];
             }
-            __syncthreads();
+            TM::sync();
         }
         if ((*s_err)) break;
         // forward and backward substitution by warp 0
         if (tid < 32) {
             for (int r = 0; r < N; ++r) {
-                double s = 0.0;
+                C s = C(0);
                 for (int c = max(0, r - bw) + tid; c < r; c += 32) s += band[(size_t)r * bw1 + (r - c)] * y[c];
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-                if (tid == 0) y[r] = (b[r] - s) / band[(size_t)r * bw1];
+                if (tid == 0) y[r] = (b[r] - s) * band[(size_t)r * bw1];
                 __syncwarp();
             }
             for (int r = N - 1; r >= 0; --r) {
-                double s = 0.0;
+                C s = C(0);
                 int c1 = min(N - 1, r + bw);
                 for (int c = r + 1 + tid; c <= c1; c += 32) s += band[(size_t)c * bw1 + (c - r)] * b[c];
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-                if (tid == 0) b[r] = (y[r] - s) / band[(size_t)r * bw1];
+                if (tid == 0) b[r] = (y[r] - s) * band[(size_t)r * bw1];
                 __syncwarp();
             }
         }
-        __syncthreads();
-        double dmax = 0.0, pmax = 1.0;
+        TM::sync();
+        C dmax = C(0), pmax = C(1);
         for (int q = tid; q < N; q += nt) {
-            dmax = fmax(dmax, fabs(b[q] - x[q]));
-            pmax = fmax(pmax, fabs(b[q]));
+            const int i = colmajor ? q % n : q / m, j = colmajor ? q / n : q % m;
+            dmax = max_t<C>(dmax, abs_t<C>(b[q] - x[q]));
+            pmax = max_t<C>(pmax, abs_t<C>(pn_at(i, j) + b[q]));
         }
-        dmax = block_max(dmax, red);
-        pmax = block_max(pmax, red);
+        dmax = TM::template max<C>(dmax, red);
+        pmax = TM::template max<C>(pmax, red);
         for (int q = tid; q < N; q += nt) x[q] = b[q];
-        __syncthreads();
+        TM::sync();
         ++it;
-        if (dmax <= 1e-14 * pmax) break;
+        if (dmax <= kStat * pmax) break;
     }
     for (int q = tid; q < N; q += nt) {
         int i = q / m, j = q % m;
-        size_t o = (size_t)i * p + j;
-        L.u[o] = (T)(x[idx(i, j)] - (double)L.pn[o]);
+        L.u[(size_t)i * p + j] = (T)x[idx(i, j)];
     }
     *it_out = it;
     *res_out = res;
-    __syncthreads();
+    TM::sync();
+}
+
+// The coarsest solve; all threads of the (kCoarseThreads) block call it.  it_out / res_out are
+// valid in thread 0.
+template <typename T>
+__device__ void coarse_solve_block(const CoarseGrid<T> &L, ModelParams mp, double A1frac, double h2nm,
+                                   int maxit, double tol, T *scratch, double *red, int *s_err,
+                                   int *it_out, double *res_out) {
+    if (L.n * L.m <= kWarpCoarseMax) {
+        if (threadIdx.x < 32)
+            coarse_solve_team<T, 32>(L, mp, A1frac, h2nm, maxit, tol, scratch, red, s_err, it_out, res_out);
+        __syncthreads();
+    } else {
+        coarse_solve_team<T, kCoarseThreads>(L, mp, A1frac, h2nm, maxit, tol, scratch, red, s_err, it_out, res_out);
+    }
 }
 
 

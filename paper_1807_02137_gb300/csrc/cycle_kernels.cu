@@ -11,7 +11,8 @@ namespace {
 // ---------------------------------------------------------------------------------------
 // Residual of L (the row-scaled operator of one pseudo-time step) on 32 x 32 tiles:
 //   L(phi) = mu/h^2 sum_X G_X ((pn_X - pn) + (u_X - u)) - F - area - u / tau,
-// mode 0: out = rhs - L(pn + uin) and a per-block FP64 partial of sum out^2;
+// mode 0: out = rhs - L(pn + uin) and, if partials is not NULL, a per-block FP64 partial of
+// sum out^2;
 // mode 1: out += L(pn + uin)   (the FAS right-hand side f^{2h} = N^{2h} phi^{2h} + r^{2h}).
 // ---------------------------------------------------------------------------------------
 template <typename T>
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(256) k_residual(LevelView<T> L, const T *uin, 
             out[o] = add_rn(out[o], Lv);
         }
     }
-    if (mode == 0) {
+    if (mode == 0 && partials) {
         double s = block_sum((double)acc, red);
         if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
     }
@@ -154,10 +155,10 @@ __global__ void __launch_bounds__(256) k_interp_add(LevelView<T> Lf, LevelView<T
 // The coarsest solve (coarse_body.cuh) as its own one-block kernel.
 template <typename T>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse(LevelView<T> L, ModelParams mp, double A1frac,
-                                                           double h2nm, int maxit, double tol, double *scratch,
+                                                           double h2nm, int maxit, double tol, T *scratch,
                                                            Scalars *sc) {
-    extern __shared__ double smem_coarse[];
-    if (!scratch) scratch = smem_coarse;          // small grids: everything in shared memory
+    extern __shared__ __align__(16) unsigned char smem_coarse[];
+    if (!scratch) scratch = reinterpret_cast<T *>(smem_coarse);   // small grids: all in shared memory
     __shared__ double red[33];
     __shared__ int s_err;
     CoarseGrid<T> g{L.n, L.m, L.pitch, L.pn, L.u, L.w, L.wb, L.F, L.rhs, L.has_rhs, L.inv_2h, L.inv_tau, L.beta};
@@ -175,16 +176,13 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(LevelView<T> L, Model
 
 int num_partials(int n, int m) { return ((m + 31) / 32) * ((n + 31) / 32); }
 
-size_t coarse_scratch_doubles(int n, int m) {
-    size_t N = (size_t)n * m, bw = (size_t)(m > n ? n : m);
-    return 4 * N + N * (bw + 1);
-}
 
 template <typename T>
 void launch_residual(const LevelView<T> &L, const T *uin, const double *area, T *out, int mode,
                      double *partials, int npart, double *norm_out, cudaStream_t st) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, 8);
-    k_residual<T><<<grid, block, 0, st>>>(L, uin, area, out, mode, partials);
+    // the per-block partial sums (FP64, slow on this GPU) only when the norm is wanted
+    k_residual<T><<<grid, block, 0, st>>>(L, uin, area, out, mode, norm_out ? partials : nullptr);
     if (mode == 0 && norm_out) k_sum_partials<<<1, 1024, 0, st>>>(partials, npart, norm_out);
 }
 
@@ -211,11 +209,11 @@ template <typename T>
 void launch_coarse_solve(const LevelView<T> &L, const double *, ModelParams mp, double A1frac,
                          double h2nm, int maxit, double tol, double *scratch, Scalars *sc,
                          cudaStream_t st) {
-    size_t bytes = coarse_scratch_doubles(L.n, L.m) * sizeof(double);
+    size_t bytes = coarse_scratch_elems(L.n, L.m) * sizeof(T);
     if (bytes <= kCoarseSmemMax)
         k_coarse<T><<<1, kCoarseThreads, bytes, st>>>(L, mp, A1frac, h2nm, maxit, tol, nullptr, sc);
     else
-        k_coarse<T><<<1, kCoarseThreads, 0, st>>>(L, mp, A1frac, h2nm, maxit, tol, scratch, sc);
+        k_coarse<T><<<1, kCoarseThreads, 0, st>>>(L, mp, A1frac, h2nm, maxit, tol, reinterpret_cast<T *>(scratch), sc);
 }
 
 #define INST(T)                                                                                    \

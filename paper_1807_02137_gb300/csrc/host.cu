@@ -217,7 +217,7 @@ struct Solver final : SolverBase {
         kcap = std::max(k, 16);
         size_t o_sc = take(sizeof(Scalars));
         size_t o_part = take(sizeof(double) * 8 * (size_t)npart);
-        size_t o_coarse = take(sizeof(double) * coarse_scratch_doubles(lv[nlev - 1].n, lv[nlev - 1].m));
+        size_t o_coarse = take(sizeof(T) * coarse_scratch_elems(lv[nlev - 1].n, lv[nlev - 1].m));
         size_t o_mk = take(sizeof(double) * 2 * kcap);
         size_t o_hull = take(sizeof(double) * (4 * kcap + 8));
         pool_bytes = off;

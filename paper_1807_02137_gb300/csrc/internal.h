@@ -124,8 +124,13 @@ template <typename T>
 void launch_coarse_solve(const LevelView<T> &L, const double *area_dummy, ModelParams mp,
                          double A1frac_times, double h2_over_nm, int maxit, double tol,
                          double *scratch, Scalars *sc, cudaStream_t st);
-size_t coarse_scratch_doubles(int n, int m);
 void prepare_coarse_kernels();
+
+// Scratch elements (of the storage type) of the coarsest solve on an n x m grid.
+__host__ __device__ inline size_t coarse_scratch_elems(int n, int m) {
+    size_t N = (size_t)n * m, bw = (size_t)(m > n ? n : m);
+    return 4 * N + N * (bw + 1);
+}
 
 // bottom_kernel.cu: grids lb .. L-1 of a V-cycle (FP32 storage, Spencer-Chen model) in one block
 struct BottomArgs {

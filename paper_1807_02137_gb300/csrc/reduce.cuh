@@ -39,4 +39,49 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     return r;
 }
 
+template <typename C>
+__device__ __forceinline__ C max_t(C a, C b) { return a > b ? a : (b > a ? b : a); }
+template <typename C>
+__device__ __forceinline__ C abs_t(C a) { return a < C(0) ? -a : a; }
+
+// The same reductions in the type C (FP32 sums stay in FP32); `red` holds 33 doubles.
+template <typename C>
+__device__ __forceinline__ C block_sum_t(C v, double *red) {
+    if (sizeof(C) == 8) return (C)block_sum((double)v, red);
+    C *rf = reinterpret_cast<C *>(red);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((tid & 31) == 0) rf[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        C s = tid < (nt + 31) / 32 ? rf[tid] : C(0);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (tid == 0) rf[32] = s;
+    }
+    __syncthreads();
+    C r = rf[32];
+    __syncthreads();
+    return r;
+}
+
+template <typename C>
+__device__ __forceinline__ C block_max_t(C v, double *red) {
+    C *rf = reinterpret_cast<C *>(red);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) v = max_t<C>(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((tid & 31) == 0) rf[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        C s = tid < (nt + 31) / 32 ? rf[tid] : C(0);
+        for (int o = 16; o > 0; o >>= 1) s = max_t<C>(s, __shfl_down_sync(0xffffffffu, s, o));
+        if (tid == 0) rf[32] = s;
+    }
+    __syncthreads();
+    C r = rf[32];
+    __syncthreads();
+    return r;
+}
+
 }  // namespace segmg

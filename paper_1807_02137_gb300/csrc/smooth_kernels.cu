@@ -366,12 +366,11 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
             if (!mk) continue;
             const int s0 = kH + 32 * pc;
             const int len = min(32, len_lim - gstart);
-            int s = 0;
-            while (s < len) {
-                if (!((mk >> s) & 1u)) { ++s; continue; }
-                const int a0 = s;
-                while (s < len && ((mk >> s) & 1u)) ++s;
-                const int rl = s - a0;
+            // runs in order of their first cell, found with bit operations on the mask
+            for (uint32_t starts = mk & ~(mk << 1); starts; starts &= starts - 1) {
+                const int a0 = __ffs(starts) - 1;
+                const uint32_t rest = ~(mk >> a0);
+                const int rl = rest ? __ffs(rest) - 1 : 32 - a0;
                 const T endp = a0 == 0 ? S.endv[t][0] : (rowwise ? SW_AT(u, li, s0 + a0 - 1) : SW_AT(u, s0 + a0 - 1, li));
                 const T endn = (a0 + rl == len) ? S.endv[t][1] : (rowwise ? SW_AT(u, li, s0 + a0 + rl) : SW_AT(u, s0 + a0 + rl, li));
                 auto at = [&](int r) -> RunCell<T> {
