@@ -281,7 +281,7 @@ __device__ void b_interp_add(const BGrid &F, const BGrid &C) {
 }  // namespace
 
 // Shared-memory bytes the bottom kernel needs for grids lb .. L-1.
-size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L) {
+size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L, int coarse_fp64) {
     size_t b = 0;
     int maxN = 0, maxTask = 0;
     for (int l = lb; l < L; ++l) {
@@ -296,7 +296,7 @@ size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L) {
     b = (b + 15) / 16 * 16;
     b += sizeof(float) * 2 * (size_t)maxTask;           // end values
     b = (b + 15) / 16 * 16;
-    b += sizeof(float) * coarse_scratch_elems(n[L - 1], m[L - 1]);
+    b += (coarse_fp64 ? sizeof(double) : sizeof(float)) * coarse_scratch_elems(n[L - 1], m[L - 1]);
     return b;
 }
 
@@ -351,7 +351,6 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
     }
     uint8_t *star = sm + s_off[0];
     float *endv = reinterpret_cast<float *>(sm + s_off[1]);
-    float *cscr = reinterpret_cast<float *>(sm + s_off[2]);
     __syncthreads();
     auto smooth = [&](int l) {
         b_snapshot(Bs[l], star);
@@ -371,8 +370,12 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
         CoarseGrid<float> cg{C.n, C.m, C.m, C.pn, C.u, C.w, nullptr, C.F, C.rhs, C.has_rhs, C.inv_2h, C.inv_tau, C.beta};
         int it;
         double res;
-        coarse_solve_block<float>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol, cscr, red,
-                                  &s_err, &it, &res);
+        if (A.coarse_fp64)
+            coarse_solve_block<float, double>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
+                                              reinterpret_cast<double *>(sm + s_off[2]), red, &s_err, &it, &res);
+        else
+            coarse_solve_block<float, float>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
+                                             reinterpret_cast<float *>(sm + s_off[2]), red, &s_err, &it, &res);
         if (threadIdx.x == 0) {
             A.sc->picard = it;
             A.sc->coarse_res = res;

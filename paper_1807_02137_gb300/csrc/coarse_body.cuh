@@ -51,8 +51,9 @@ struct CoarseGrid {
 };
 
 // ---------------------------------------------------------------------------------------
-// Coarsest solve (Algorithm 1, "compute the exact solution"), one block, in the storage
-// precision.  The unknown is the increment u of phi = pn + u.  Picard on the frozen
+// Coarsest solve (Algorithm 1, "compute the exact solution"), one block, in the arithmetic
+// precision of the path (FP32 for FP32 storage, FP64 for FP64 and mixed storage).  The unknown
+// is the increment u of phi = pn + u.  Picard on the frozen
 // coefficients G (at phi): each step solves the symmetric positive definite system
 //   (mu/h^2 sum_X G_X + 1/tau) u - mu/h^2 sum_X G_X u_X = mu/h^2 sum_X G_X (pn_X - pn) - F - area - rhs
 // by banded Cholesky with cells ordered along the shorter side.  It stops when the nonlinear
@@ -68,24 +69,23 @@ __device__ __forceinline__ float rsqrt_of<float>(float s) { return rsqrtf(s); }
 template <>
 __device__ __forceinline__ double rsqrt_of<double>(double s) { return 1.0 / sqrt(s); }
 
-// Run by the NT threads of a team (NT = 32: warp 0; else the whole block); scratch holds
-// coarse_scratch_elems(n, m) values of T.
-template <typename T, int NT>
+// Run by the NT threads of a team (NT = 32: warp 0; else the whole block) in the arithmetic
+// type C (storage T); scratch holds coarse_scratch_elems(n, m) values of C.
+template <typename T, typename C, int NT>
 __device__ void coarse_solve_team(const CoarseGrid<T> &L, ModelParams mp, double A1frac, double h2nm,
-                                  int maxit, double tol, T *scratch, double *red, int *s_err,
+                                  int maxit, double tol, C *scratch, double *red, int *s_err,
                                   int *it_out, double *res_out) {
-    using C = T;
     using TM = Team<NT>;
-    constexpr bool kF32 = sizeof(T) == 4;
+    constexpr bool kF32 = sizeof(C) == 4;
     constexpr C kStat = kF32 ? C(1e-6) : C(1e-14);
     const int n = L.n, m = L.m, p = L.pitch, N = n * m;
     const int tid = threadIdx.x, nt = NT;
     const bool colmajor = m > n;
     const int bw = colmajor ? n : m, bw1 = bw + 1;
     C *x = scratch, *G = x + N, *b = G + N, *y = b + N, *band = y + N;
-    const C hinv = C(2) * L.inv_2h;
+    const C hinv = C(2) * (C)L.inv_2h;
     const C cdiff = C(mp.mu) * hinv * hinv;
-    const C inv_tau = L.inv_tau, inv_2h = L.inv_2h, beta = L.beta;
+    const C inv_tau = (C)L.inv_tau, inv_2h = (C)L.inv_2h, beta = (C)L.beta;
     auto idx = [&](int i, int j) { return colmajor ? j * n + i : i * m + j; };
     auto pn_at = [&](int i, int j) { return (C)L.pn[(size_t)i * p + j]; };
     if (tid == 0) *s_err = 0;
@@ -237,18 +237,19 @@ __device__ void coarse_solve_team(const CoarseGrid<T> &L, ModelParams mp, double
     TM::sync();
 }
 
-// The coarsest solve; all threads of the (kCoarseThreads) block call it.  it_out / res_out are
-// valid in thread 0.
-template <typename T>
+// The coarsest solve in the arithmetic type C; all threads of the (kCoarseThreads) block call
+// it.  it_out / res_out are valid in thread 0.
+template <typename T, typename C>
 __device__ void coarse_solve_block(const CoarseGrid<T> &L, ModelParams mp, double A1frac, double h2nm,
-                                   int maxit, double tol, T *scratch, double *red, int *s_err,
+                                   int maxit, double tol, C *scratch, double *red, int *s_err,
                                    int *it_out, double *res_out) {
     if (L.n * L.m <= kWarpCoarseMax) {
         if (threadIdx.x < 32)
-            coarse_solve_team<T, 32>(L, mp, A1frac, h2nm, maxit, tol, scratch, red, s_err, it_out, res_out);
+            coarse_solve_team<T, C, 32>(L, mp, A1frac, h2nm, maxit, tol, scratch, red, s_err, it_out, res_out);
         __syncthreads();
     } else {
-        coarse_solve_team<T, kCoarseThreads>(L, mp, A1frac, h2nm, maxit, tol, scratch, red, s_err, it_out, res_out);
+        coarse_solve_team<T, C, kCoarseThreads>(L, mp, A1frac, h2nm, maxit, tol, scratch, red, s_err, it_out,
+                                                res_out);
     }
 }
 

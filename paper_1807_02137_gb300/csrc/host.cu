@@ -113,7 +113,7 @@ struct Level {
     int n = 0, m = 0, pitch = 0;
     double h = 1;
     T *pn = nullptr, *u = nullptr, *u0 = nullptr, *rhs = nullptr, *w = nullptr, *z = nullptr, *d = nullptr;
-    T *F = nullptr, *G = nullptr, *f = nullptr, *r = nullptr, *upre = nullptr;
+    T *F = nullptr, *G = nullptr, *f = nullptr, *r = nullptr, *upre = nullptr, *t = nullptr;
     uint32_t *mrow = nullptr, *mcol = nullptr;
     __nv_bfloat16 *wb = nullptr;   // mixed precision only
 };
@@ -177,7 +177,7 @@ struct Solver final : SolverBase {
         v.inv_2h = (T)(1.0 / (2.0 * L.h));
         v.beta = (T)p.beta;
         v.pn = L.pn; v.u = L.u; v.u0 = L.u0; v.rhs = L.rhs; v.w = L.w; v.z = L.z; v.d = L.d;
-        v.F = L.F; v.G = L.G; v.f = L.f; v.r = L.r; v.upre = L.upre;
+        v.F = L.F; v.G = L.G; v.f = L.f; v.r = L.r; v.upre = L.upre; v.t = L.t;
         v.mrow = L.mrow; v.mcol = L.mcol; v.npm = (L.m + 31) / 32; v.npn = (L.n + 31) / 32;
         v.wb = L.wb;
         v.has_rhs = l > 0 ? 1 : 0;
@@ -201,7 +201,7 @@ struct Solver final : SolverBase {
             Level<T> &L = lv[l];
             L.n = nn; L.m = mm; L.pitch = (mm + 31) / 32 * 32; L.h = std::ldexp(1.0, l);
             size_t fb = (size_t)L.n * L.pitch * sizeof(T);
-            T **fields[] = {&L.pn, &L.u, &L.w, &L.z, &L.d, &L.F, &L.G, &L.f, &L.r};
+            T **fields[] = {&L.pn, &L.u, &L.w, &L.z, &L.d, &L.F, &L.G, &L.f, &L.r, &L.t};
             for (T **f : fields) plan.push_back({(void **)f, take(fb)});
             if (l > 0) {
                 plan.push_back({(void **)&L.u0, take(fb)});
@@ -217,7 +217,7 @@ struct Solver final : SolverBase {
         kcap = std::max(k, 16);
         size_t o_sc = take(sizeof(Scalars));
         size_t o_part = take(sizeof(double) * 8 * (size_t)npart);
-        size_t o_coarse = take(sizeof(T) * coarse_scratch_elems(lv[nlev - 1].n, lv[nlev - 1].m));
+        size_t o_coarse = take(sizeof(double) * coarse_scratch_elems(lv[nlev - 1].n, lv[nlev - 1].m));
         size_t o_mk = take(sizeof(double) * 2 * kcap);
         size_t o_hull = take(sizeof(double) * (4 * kcap + 8));
         pool_bytes = off;
@@ -250,7 +250,7 @@ struct Solver final : SolverBase {
             int ns[kMaxLevels], ms[kMaxLevels];
             for (int l = 0; l < nlev; ++l) { ns[l] = lv[l].n; ms[l] = lv[l].m; }
             for (int l = nlev - 2; l >= 0; --l) {
-                size_t b = bottom_smem_bytes(ns, ms, l, nlev);
+                size_t b = bottom_smem_bytes(ns, ms, l, nlev, p.precision == MG_MIXED);
                 if (b > kBottomSmemMax) break;
                 lb = l;
                 lb_smem = b;
@@ -264,6 +264,7 @@ struct Solver final : SolverBase {
         if constexpr (std::is_same<T, float>::value) {
             BottomArgs a{};
             a.lb = lb; a.L = nlev; a.nu1 = p.nu1; a.nu2 = p.nu2;
+            a.coarse_fp64 = p.precision == MG_MIXED;
             for (int l = lb; l < nlev; ++l) a.g[l] = view(l);
             a.mp = mp;
             a.A1frac = A1 / ((double)n * m);
@@ -393,8 +394,8 @@ struct Solver final : SolverBase {
             return;
         }
         if (l == nlev - 1) {
-            launch_coarse_solve<T>(view(l), nullptr, mp, A1 / ((double)n * m), h2nm(l), p.coarse_maxit,
-                                   p.coarse_tol, coarse, dsc, st);
+            launch_coarse_solve<T>(view(l), p.precision == MG_MIXED, mp, A1 / ((double)n * m), h2nm(l),
+                                   p.coarse_maxit, p.coarse_tol, coarse, dsc, st);
             ++launches;
             return;
         }

@@ -35,6 +35,8 @@ struct LevelView {
     T inv_2h;       // 1 / (2h), central differences
     T beta;
     T *pn, *u, *u0, *rhs, *w, *z, *d, *F, *G, *f, *r, *upre;
+    T *t;                      // the fused sweeps' second buffer: A and C read u and write t,
+                               // B and D read t and write u (a sweep never reads what it writes)
     uint32_t *mrow, *mcol;     // member masks (see above)
     int npm, npn;
     const __nv_bfloat16 *wb;   // mixed precision: the length weight w stored in BF16 (else NULL)
@@ -121,9 +123,9 @@ void launch_residual(const LevelView<T> &L, const T *uin, const double *area, T 
 template <typename T>
 void launch_interp_add(const LevelView<T> &Lf, const LevelView<T> &Lc, cudaStream_t st);
 template <typename T>
-void launch_coarse_solve(const LevelView<T> &L, const double *area_dummy, ModelParams mp,
-                         double A1frac_times, double h2_over_nm, int maxit, double tol,
-                         double *scratch, Scalars *sc, cudaStream_t st);
+void launch_coarse_solve(const LevelView<T> &L, int fp64, ModelParams mp, double A1frac,
+                         double h2_over_nm, int maxit, double tol, double *scratch, Scalars *sc,
+                         cudaStream_t st);   // fp64: FP64 arithmetic for FP32 storage
 void prepare_coarse_kernels();
 
 // Scratch elements (of the storage type) of the coarsest solve on an n x m grid.
@@ -135,6 +137,7 @@ __host__ __device__ inline size_t coarse_scratch_elems(int n, int m) {
 // bottom_kernel.cu: grids lb .. L-1 of a V-cycle (FP32 storage, Spencer-Chen model) in one block
 struct BottomArgs {
     int lb, L, nu1, nu2;
+    int coarse_fp64;   // the coarsest solve in FP64 arithmetic (mixed precision) or FP32
     LevelView<float> g[kMaxLevels];
     ModelParams mp;
     double A1frac, h2nm_coarse, coarse_tol;
@@ -142,7 +145,7 @@ struct BottomArgs {
     Scalars *sc;
 };
 constexpr size_t kBottomSmemMax = 200 * 1024;
-size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L);
+size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L, int coarse_fp64);
 void prepare_bottom_kernel();
 void launch_bottom(const BottomArgs &A, size_t smem, cudaStream_t st);
 

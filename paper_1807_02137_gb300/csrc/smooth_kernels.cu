@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
 }
 
 // ---------------------------------------------------------------------------------------
-// Fused path: one kernel per sweep.  A block owns a 32 x 64 output tile (aligned to the
+// Fused path: one kernel per sweep, reading u from one buffer and writing the other (sweeps A
+// and C: u -> t, B and D: t -> u).  A block owns a 32 x 64 output tile (aligned to the
 // 32-cell pieces of rows and columns) and loads it with a 4-cell halo: two checkerboard phases
 // and two zebra phases each consume one cell of halo across the line direction, and the
 // checkerboard phases one cell each along it.  Shared memory holds each field split by
@@ -264,6 +265,10 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
     const int i0 = blockIdx.y * kOH, j0 = blockIdx.x * kOW;
     const int n = L.n, m = L.m, p = L.pitch;
     const int tid = threadIdx.x;
+    // ping-pong: tiles read their halo from one buffer and write their output to the other, so
+    // no tile can read a neighbour's already updated cells
+    const T *uin = (SWEEP & 1) ? L.t : L.u;
+    T *uout = (SWEEP & 1) ? L.u : L.t;
     // ---- load u, G, f as vectors (the region starts 16-byte aligned): all loads of a batch are
     // issued before any shared-memory store, so they are in flight together
     constexpr int NVEC = kRH * NV, PER = (NVEC + kThreads - 1) / kThreads, BATCH = VN == 4 ? PER : 3;
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
             const int gi = i0 - kH + a, gj = j0 - kH + b0;
             if (k0 + k < PER && q < NVEC && gi >= 0 && gi < n && gj >= 0 && gj < p) {
                 const size_t o = (size_t)gi * p + gj;
-                x[k][0] = __ldg(reinterpret_cast<const V *>(L.u + o));
+                x[k][0] = __ldg(reinterpret_cast<const V *>(uin + o));
                 x[k][1] = __ldg(reinterpret_cast<const V *>(L.G + o));
                 x[k][2] = __ldg(reinterpret_cast<const V *>(L.f + o));
             } else {
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
         for (int e = 0; e < VN; ++e) uu[e] = SW_AT(u, a, b0 + e);
         V xv;
         memcpy(&xv, uu, sizeof(V));
-        *reinterpret_cast<V *>(L.u + (size_t)gi * p + gj) = xv;
+        *reinterpret_cast<V *>(uout + (size_t)gi * p + gj) = xv;
     }
 }
 

@@ -300,3 +300,19 @@ def test_bottom_kernel_applies_only_where_it_is_exact(segmg):
         assert (lb >= 0) == expect
         if expect:
             assert 0 <= lb <= p.levels - 2
+
+
+def test_fused_sweep_is_scheduling_independent_on_multi_wave_grids(segmg):
+    # 2048^2 needs several waves of 32 x 64 tiles: a tile must never see a neighbour's updated
+    # cells, so the fused sweep equals the per-phase path bitwise and runs repeat bitwise
+    img, mk, _ = synth.ellipses(2048, 2048, 24, (40, 400), 8, 0.05, 21)
+    outs = []
+    for sm in (0, 0, 1):
+        s, _ = gpu_solver(segmg, img, mk, precision=segmg.MG_F32, levels=10, smoother=sm)
+        s.begin_step()
+        for _ in range(2):
+            s.vcycle()
+        outs.append(s.phi().cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
