@@ -51,7 +51,10 @@ enum {
 enum { MG_MODEL_SC = 0, MG_MODEL_RC = 1 };       /* Spencer-Chen / Rada-Chen (Sec. 2.2) */
 enum { MG_F32 = 0, MG_F64 = 1, MG_MIXED = 2 };  /* storage and smoothing precision; MG_MIXED = FP32
                                                     with the image-derived weight w held in BF16 */
-enum { MG_SMOOTH_FUSED = 0, MG_SMOOTH_PHASED = 1 };   /* one kernel per sweep / per phase */
+/* Hybrid Smoother 2 kernels (same results): one kernel per sweep with tiles staged by the
+ * Tensor Memory Accelerator (FP64 storage: by vector loads), one kernel per phase, or one kernel
+ * per sweep with vector loads. */
+enum { MG_SMOOTH_FUSED = 0, MG_SMOOTH_PHASED = 1, MG_SMOOTH_FUSED_VEC = 2 };
 
 typedef struct mg_handle_s *mg_handle;
 
@@ -73,9 +76,9 @@ typedef struct {
     double tau;            /* pseudo-time step (px^2-time units, > 0; 0 means infinity) */
     int nu1, nu2;          /* pre- and post-smoothing outer iterations (>= 0) */
     int levels;            /* number of grids, finest included (>= 1) */
-    int precision;         /* MG_F32, MG_F64 or MG_MIXED (norms, c1/c2 sums and the coarsest
-                              solve are FP64 in every mode) */
-    int smoother;          /* MG_SMOOTH_FUSED or MG_SMOOTH_PHASED (same results) */
+    int precision;         /* MG_F32, MG_F64 or MG_MIXED (norms and c1/c2 sums are FP64 in every
+                              mode; the coarsest solve is FP32 with MG_F32, else FP64) */
+    int smoother;          /* MG_SMOOTH_FUSED, MG_SMOOTH_PHASED or MG_SMOOTH_FUSED_VEC */
     int coarse_maxit;      /* Picard cap of the coarsest solve (>= 1) */
     double coarse_tol;     /* relative residual target of the coarsest solve */
     int use_graph;         /* 1: replay each V-cycle as a captured CUDA graph */

@@ -116,6 +116,7 @@ struct Level {
     T *F = nullptr, *G = nullptr, *f = nullptr, *r = nullptr, *upre = nullptr, *t = nullptr;
     uint32_t *mrow = nullptr, *mcol = nullptr;
     __nv_bfloat16 *wb = nullptr;   // mixed precision only
+    SweepMaps maps[kTileShapes];   // FP32 storage: tensor maps of the TMA sweep, per tile shape
 };
 
 template <typename T>
@@ -236,6 +237,13 @@ struct Solver final : SolverBase {
         dmk = (double *)(base + o_mk);
         dhull = (double *)(base + o_hull);
         CK(cudaMallocHost(&hsc, sizeof(Scalars)));
+        if constexpr (std::is_same<T, float>::value) {
+            if (p.smoother == MG_SMOOTH_FUSED)
+                for (int l = 0; l < nlev; ++l)
+                    for (int sh = 0; sh < kTileShapes; ++sh)
+                        if (!encode_sweep_maps(view(l), sh, &lv[l].maps[sh]))
+                            return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a grid");
+        }
         set_bottom(1);
         return MG_OK;
     }
@@ -246,7 +254,7 @@ struct Solver final : SolverBase {
     int set_bottom(int enable) override {
         lb = -1;
         lb_smem = 0;
-        if (enable && sizeof(T) == 4 && p.model == MG_MODEL_SC && p.smoother == MG_SMOOTH_FUSED) {
+        if (enable && sizeof(T) == 4 && p.model == MG_MODEL_SC && p.smoother != MG_SMOOTH_PHASED) {
             int ns[kMaxLevels], ms[kMaxLevels];
             for (int l = 0; l < nlev; ++l) { ns[l] = lv[l].n; ms[l] = lv[l].m; }
             for (int l = nlev - 2; l >= 0; --l) {
@@ -376,14 +384,23 @@ struct Solver final : SolverBase {
     int area_launches() const { return p.model == MG_MODEL_RC ? 2 : 0; }
     int sweep_launches() const { return p.smoother == MG_SMOOTH_PHASED ? 4 : 1; }
 
+    // One directional sweep k of grid l with tile shape sh.
+    void sweep(int l, const LevelView<T> &v, int k, int sh) {
+        if (p.smoother == MG_SMOOTH_PHASED) {
+            launch_sweep_phased<T>(v, k, st);
+        } else if (p.smoother == MG_SMOOTH_FUSED_VEC) {
+            launch_sweep_fused<T>(v, k, sh, st);
+        } else {
+            if constexpr (std::is_same<T, float>::value) launch_sweep_tma(v, k, sh, lv[l].maps[sh], &dsc->err, st);
+            else launch_sweep_fused<T>(v, k, sh, st);
+        }
+    }
+
     void smooth(int l) {
         area_term(l, lv[l].u);
         LevelView<T> v = view(l);
         launch_snapshot<T>(v, area_ptr(), st);
-        for (int k = 0; k < 4; ++k) {
-            if (p.smoother == MG_SMOOTH_PHASED) launch_sweep_phased<T>(v, k, st);
-            else launch_sweep_fused<T>(v, k, shape[l], st);
-        }
+        for (int k = 0; k < 4; ++k) sweep(l, v, k, shape[l]);
         launches += area_launches() + 1 + 4 * sweep_launches();
     }
 
@@ -465,7 +482,7 @@ struct Solver final : SolverBase {
                     for (int r = 0; r < reps; ++r) {
                         area_term(l, L.u);
                         launch_snapshot<T>(v, area_ptr(), st);
-                        for (int k = 0; k < 4; ++k) launch_sweep_fused<T>(v, k, sh, st);
+                        for (int k = 0; k < 4; ++k) sweep(l, v, k, sh);
                     }
                     CK(cudaEventRecord(e1, st));
                     CK(cudaEventSynchronize(e1));
@@ -512,6 +529,7 @@ struct Solver final : SolverBase {
         rho = res0 > 0 ? std::sqrt(hsc->norm2) / res0 : std::sqrt(hsc->norm2);
         if (rhoout) *rhoout = rho;
         if (hsc->err & 1) return fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
+        if (hsc->err & 4) return fail(MG_ERR_CUDA, "a tile copy into shared memory did not complete in time");
         if (!std::isfinite(rho)) return fail(MG_ERR_NAN, "non-finite residual");
         if (rho > 1e3) return fail(MG_ERR_DIVERGED, "residual grew by more than 1e3");
         return MG_OK;
@@ -603,8 +621,7 @@ struct Solver final : SolverBase {
             launch_snapshot<T>(v, area_ptr(), st);
             cudaEventRecord(ev[1], st);
             for (int k = 0; k < 4; ++k) {
-                if (p.smoother == MG_SMOOTH_PHASED) launch_sweep_phased<T>(v, k, st);
-                else launch_sweep_fused<T>(v, k, shape[l], st);
+                sweep(l, v, k, shape[l]);
                 cudaEventRecord(ev[2 + k], st);
             }
             launch_residual<T>(v, lv[l].u, area_ptr(), lv[l].r, 0, partials, 0, nullptr, st);
@@ -630,7 +647,8 @@ int check_params(const mg_params *p, int n, int m) {
     if (p->model != MG_MODEL_SC && p->model != MG_MODEL_RC) return fail(MG_ERR_ARG, "model");
     if (p->precision != MG_F32 && p->precision != MG_F64 && p->precision != MG_MIXED)
         return fail(MG_ERR_ARG, "precision");
-    if (p->smoother != MG_SMOOTH_FUSED && p->smoother != MG_SMOOTH_PHASED) return fail(MG_ERR_ARG, "smoother");
+    if (p->smoother != MG_SMOOTH_FUSED && p->smoother != MG_SMOOTH_PHASED && p->smoother != MG_SMOOTH_FUSED_VEC)
+        return fail(MG_ERR_ARG, "smoother");
     const double pos[] = {p->mu, p->eps, p->beta, p->sigma_blur, p->sigma_d};
     for (double v : pos)
         if (!(v > 0) || !std::isfinite(v)) return fail(MG_ERR_ARG, "mu, eps, beta, sigma_blur, sigma_d must be > 0");
@@ -851,6 +869,7 @@ int mg_setup(mg_handle *out, const void *image, int n, int m, const double *mark
     prepare_smoother_kernels();
     prepare_coarse_kernels();
     prepare_bottom_kernel();
+    prepare_sweep_tma();
     SolverBase *s = nullptr;
     if (p->precision != MG_F64) {
         auto *t = new Solver<float>();
@@ -1009,6 +1028,7 @@ int mg_batch_setup(mg_batch *out, int count, const void *const *images, const in
     prepare_smoother_kernels();
     prepare_coarse_kernels();
     prepare_bottom_kernel();
+    prepare_sweep_tma();
     auto *B = new mg_batch_s();
     Batch &b = B->b;
     int rc = MG_OK;

@@ -116,6 +116,19 @@ void launch_sweep_fused(const LevelView<T> &L, int sweep, int shape, cudaStream_
 template <typename T>
 void launch_sweep_phased(const LevelView<T> &L, int sweep, cudaStream_t st);
 
+// sweep_tma.cu: the fused sweep for FP32 storage with TMA-staged tiles.  A SweepMaps holds the
+// tensor maps (CUtensorMap, 128 bytes each) of u, t, G and f of one grid for one tile shape.
+struct SweepMaps {
+    alignas(64) unsigned char u[128];
+    alignas(64) unsigned char t[128];
+    alignas(64) unsigned char G[128];
+    alignas(64) unsigned char f[128];
+};
+void prepare_sweep_tma();
+bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M);
+void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const SweepMaps &M, int *err,
+                      cudaStream_t st);
+
 // cycle_kernels.cu
 template <typename T>
 void launch_residual(const LevelView<T> &L, const T *uin, const double *area, T *out, int mode,

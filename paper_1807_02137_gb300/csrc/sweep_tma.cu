@@ -1,0 +1,389 @@
+// sweep_tma.cu -- the fused Hybrid Smoother 2 sweep (Sec. 4.3) for FP32 storage, with the tiles
+// staged into shared memory by the Tensor Memory Accelerator.
+//
+// Same sweep, same tiles and the same per-cell operations as k_sweep in smooth_kernels.cu (the
+// results are bitwise identical); what changes is how tiles reach shared memory:
+//   - persistent blocks: each block walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...;
+//   - the u, G and f boxes of a tile (output tile plus a 4-cell halo, zero outside the grid)
+//     are copied by three cp.async.bulk.tensor loads issued by one thread, completing on an
+//     mbarrier;
+//   - two stages: while a block smooths one tile, the next tile's boxes are in flight.
+// Shared memory holds the boxes dense (row-major, as TMA writes them).  The checkerboard phases
+// interleave two rows across the lanes of a warp (lane 2k: row a, lane 2k+1: row a+1), so the
+// 32 cells a warp updates fall in 32 different banks without the colour-split layout the
+// vector-load kernel uses.
+//
+// Every wait on an mbarrier is bounded.  On time-out the block records bit 4 in the handle's
+// error word, waits (bounded) for its copies still in flight and returns; the host reports it.
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "arith.cuh"
+
+namespace segmg {
+
+namespace {
+
+constexpr int kH = 4;
+constexpr long kWaitLimit = 1L << 22;   // try_wait rounds before a wait gives up
+
+template <int OH_, int OW_, int NT_>
+struct TShape {
+    static constexpr int OH = OH_, OW = OW_, NT = NT_;
+    static constexpr int RH = OH + 2 * kH, RW = OW + 2 * kH;
+    static constexpr int MaxTasks = 2 * (OH > OW ? OH : OW) + 8;
+    static constexpr int RowPieces = OW / 32 + 2, ColPieces = OH / 32 + 2;
+    static constexpr int MkLines = RH > RW ? RH : RW, MkPieces = RowPieces > ColPieces ? RowPieces : ColPieces;
+    static constexpr int BoxBytes = RH * RW * 4;
+};
+using TT0 = TShape<32, 64, 256>;
+using TT1 = TShape<32, 32, 128>;
+using TT2 = TShape<64, 64, 512>;
+
+template <typename TS>
+struct TmaSmem {
+    float box[2][3][TS::RH][TS::RW];           // [stage][u, G, f][row][column]
+    uint32_t mk[TS::MkLines][TS::MkPieces];    // member masks of the tile (as k_sweep)
+    float endv[TS::MaxTasks][2];
+    unsigned long long bar[2];                 // one mbarrier per stage
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the completion of phase `parity`; false on time-out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    for (long it = 0; it < kWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 2-D tiled TMA load of the box at column x, row y (elements; x * 4 bytes is a multiple of 16)
+// into dst, completing on bar.
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+template <typename TS, bool ROWWISE>
+__device__ __forceinline__ bool member(const TmaSmem<TS> &S, int a, int b) {
+    if (ROWWISE) return (S.mk[a][(b + 28) >> 5] >> ((b - kH) & 31)) & 1u;
+    return (S.mk[b][(a + 28) >> 5] >> ((a - kH) & 31)) & 1u;
+}
+
+// One checkerboard phase over the box cells within distance 3 - ph of the output tile (the
+// cells and the operations of rb_phase in smooth_kernels.cu).
+template <typename TS, int SWEEP, bool INTERIOR>
+__device__ __forceinline__ void rb_phase(TmaSmem<TS> &S, int st, const LevelView<float> &L, int ph, int i0, int j0) {
+    constexpr int kRH = TS::RH, kRW = TS::RW;
+    constexpr bool rev = (SWEEP & 1) != 0;
+    float (*u)[kRW] = S.box[st][0];
+    const float (*G)[kRW] = S.box[st][1];
+    const float (*f)[kRW] = S.box[st][2];
+    const int colour = rev ? 1 - ph : ph, lo = 1 + ph;
+    const int n = L.n, m = L.m;
+    for (int q = threadIdx.x; q < (kRH / 2) * kRW; q += TS::NT) {
+        const int pr = q / kRW, e = q - pr * kRW;
+        const int a = 2 * pr + (e & 1), b = (e & ~1) + ((a + colour) & 1);
+        if (a < lo || a >= kRH - lo || b < lo || b >= kRW - lo) continue;
+        bool hS = true, hN = true, hE = true, hW = true;
+        if (!INTERIOR) {
+            const int gi = i0 - kH + a, gj = j0 - kH + b;
+            if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
+            hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
+        }
+        if (member<TS, (SWEEP < 2)>(S, a, b)) continue;
+        const float gc = G[a][b];
+        const float aS = face(gc, G[a + 1][b], hS), aN = face(gc, G[a - 1][b], hN);
+        const float aE = face(gc, G[a][b + 1], hE), aW = face(gc, G[a][b - 1], hW);
+        u[a][b] = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, u[a + 1][b], u[a - 1][b], u[a][b + 1],
+                              u[a][b - 1], f[a][b]);
+    }
+}
+
+template <int SWEEP, typename TS>
+__global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const __grid_constant__ CUtensorMap tin,
+                                                      const __grid_constant__ CUtensorMap tG,
+                                                      const __grid_constant__ CUtensorMap tf, int *err) {
+    constexpr int kOH = TS::OH, kOW = TS::OW, kRH = TS::RH, kRW = TS::RW;
+    constexpr int kRowPieces = TS::RowPieces, kColPieces = TS::ColPieces;
+    constexpr bool rowwise = SWEEP < 2, rev = (SWEEP & 1) != 0;
+    extern __shared__ unsigned char smem_raw[];
+    TmaSmem<TS> &S = *reinterpret_cast<TmaSmem<TS> *>(
+        smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));   // boxes 128-byte aligned
+    const int n = L.n, m = L.m, p = L.pitch;
+    const int tid = threadIdx.x;
+    const int ntx = (m + kOW - 1) / kOW, ntiles = ntx * ((n + kOH - 1) / kOH);
+    float *uout = (SWEEP & 1) ? L.u : L.t;   // ping-pong (see k_sweep)
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int tile, int stage) {   // one thread
+        const int ty = tile / ntx, tx = tile - ty * ntx;
+        const int x = tx * kOW - kH, y = ty * kOH - kH;
+        fence_proxy_async();
+        mbar_expect_tx(&S.bar[stage], 3u * TS::BoxBytes);
+        tma_load(&S.box[stage][0][0][0], &tin, x, y, &S.bar[stage]);
+        tma_load(&S.box[stage][1][0][0], &tG, x, y, &S.bar[stage]);
+        tma_load(&S.box[stage][2][0][0], &tf, x, y, &S.bar[stage]);
+    };
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) issue(tile, 0);
+    for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+        const int st = k & 1;
+        const int next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles) issue(next, st ^ 1);
+        const int ty = tile / ntx, tx = tile - ty * ntx;
+        const int i0 = ty * kOH, j0 = tx * kOW;
+        // member masks of every line piece that touches the box (zero outside the grid)
+        if (rowwise) {
+            for (int q = tid; q < kRH * kRowPieces; q += TS::NT) {
+                const int a = q / kRowPieces, pc = q % kRowPieces;
+                const int gi = i0 - kH + a, piece = (j0 >> 5) - 1 + pc;
+                uint32_t w = 0;
+                if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm)
+                    w = __ldg(L.mrow + ((size_t)SWEEP * n + gi) * L.npm + piece);
+                S.mk[a][pc] = w;
+            }
+        } else {
+            for (int q = tid; q < kRW * kColPieces; q += TS::NT) {
+                const int b = q / kColPieces, pc = q % kColPieces;
+                const int gj = j0 - kH + b, piece = (i0 >> 5) - 1 + pc;
+                uint32_t w = 0;
+                if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn)
+                    w = __ldg(L.mcol + ((size_t)(SWEEP - 2) * m + gj) * L.npn + piece);
+                S.mk[b][pc] = w;
+            }
+        }
+        const bool ok = mbar_wait(&S.bar[st], (unsigned)((k >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: report, let the prefetch (if any) land, and stop
+            if (tid == 0) {
+                atomicOr(err, 4);
+                if (next < ntiles) mbar_wait(&S.bar[st ^ 1], (unsigned)(((k + 1) >> 1) & 1));
+            }
+            __syncthreads();
+            return;
+        }
+        float (*u)[kRW] = S.box[st][0];
+        const float (*G)[kRW] = S.box[st][1];
+        const float (*f)[kRW] = S.box[st][2];
+        // ---- checkerboard phases (distance 3 then 2 from the output tile)
+        const bool interior = i0 - kH >= 0 && i0 - kH + kRH <= n && j0 - kH >= 0 && j0 - kH + kRW <= m;
+#pragma unroll
+        for (int ph = 0; ph < 2; ++ph) {
+            if (interior) rb_phase<TS, SWEEP, true>(S, st, L, ph, i0, j0);
+            else rb_phase<TS, SWEEP, false>(S, st, L, ph, i0, j0);
+            __syncthreads();
+        }
+        // ---- partial-line phases (as k_sweep): lines at distance 1, then 0, one parity each
+        constexpr int npc = rowwise ? kOW / 32 : kOH / 32;
+        const int len_lim = rowwise ? m : n, gl_lim = rowwise ? n : m;
+#pragma unroll
+        for (int ph = 0; ph < 2; ++ph) {
+            const int parity = rev ? 1 - ph : ph, dist = 1 - ph;
+            const int lfirst = kH - dist;
+            const int ntask = ((rowwise ? kOH : kOW) + 2 * dist) * npc;
+            for (int t = tid; t < ntask; t += TS::NT) {
+                const int li = lfirst + t / npc, pc = t % npc;
+                const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
+                const int gstart = rowwise ? j0 + 32 * pc : i0 + 32 * pc;
+                const int s0 = kH + 32 * pc;
+                const bool okl = gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim;
+                const int len = okl ? min(32, len_lim - gstart) : 0;
+                const uint32_t mk = okl ? S.mk[li][1 + pc] : 0u;
+                float e0 = 0.f, e1 = 0.f;
+                if (mk) {
+                    if (gstart > 0) e0 = rowwise ? u[li][s0 - 1] : u[s0 - 1][li];
+                    if (gstart + len < len_lim) e1 = rowwise ? u[li][s0 + len] : u[s0 + len][li];
+                }
+                S.endv[t][0] = e0;
+                S.endv[t][1] = e1;
+            }
+            __syncthreads();
+            for (int t = tid; t < ntask; t += TS::NT) {
+                const int li = lfirst + t / npc, pc = t % npc;
+                const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
+                const int gstart = rowwise ? j0 + 32 * pc : i0 + 32 * pc;
+                if (!(gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim)) continue;
+                const uint32_t mk = S.mk[li][1 + pc];
+                if (!mk) continue;
+                const int s0 = kH + 32 * pc;
+                const int len = min(32, len_lim - gstart);
+                for (uint32_t starts = mk & ~(mk << 1); starts; starts &= starts - 1) {
+                    const int a0 = __ffs(starts) - 1;
+                    const uint32_t rest = ~(mk >> a0);
+                    const int rl = rest ? __ffs(rest) - 1 : 32 - a0;
+                    const float endp = a0 == 0 ? S.endv[t][0] : (rowwise ? u[li][s0 + a0 - 1] : u[s0 + a0 - 1][li]);
+                    const float endn = (a0 + rl == len) ? S.endv[t][1] : (rowwise ? u[li][s0 + a0 + rl] : u[s0 + a0 + rl][li]);
+                    auto at = [&](int r) -> RunCell<float> {
+                        const int pos = s0 + a0 + r;
+                        const int a = rowwise ? li : pos, b = rowwise ? pos : li;
+                        const int gi = rowwise ? gline : i0 - kH + pos, gj = rowwise ? j0 - kH + pos : gline;
+                        const bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
+                        const float gc = G[a][b];
+                        const float aS = face(gc, G[a + 1][b], hS), aN = face(gc, G[a - 1][b], hN);
+                        const float aE = face(gc, G[a][b + 1], hE), aW = face(gc, G[a][b - 1], hW);
+                        RunCell<float> c;
+                        if (rowwise) {
+                            c.ap = aW; c.an = aE; c.ax1 = aS; c.ax2 = aN;
+                            c.ux1 = u[a + 1][b]; c.ux2 = u[a - 1][b];
+                        } else {
+                            c.ap = aN; c.an = aS; c.ax1 = aE; c.ax2 = aW;
+                            c.ux1 = u[a][b + 1]; c.ux2 = u[a][b - 1];
+                        }
+                        c.f = f[a][b];
+                        return c;
+                    };
+                    thomas_run<float>(rl, L.cdiff, L.inv_tau, endp, endn, at, [&](int r, float xv) {
+                        const int pos = s0 + a0 + r;
+                        if (rowwise) u[li][pos] = xv; else u[pos][li] = xv;
+                    });
+                }
+            }
+            __syncthreads();
+        }
+        // ---- the output tile to uout (16-byte vectors; padding columns keep their box values)
+        constexpr int NVO = kOW / 4;
+        for (int q = tid; q < kOH * NVO; q += TS::NT) {
+            const int a = kH + q / NVO, b0 = kH + (q % NVO) * 4;
+            const int gi = i0 + q / NVO, gj = j0 + (q % NVO) * 4;
+            if (gi >= n || gj >= p) continue;
+            *reinterpret_cast<float4 *>(uout + (size_t)gi * p + gj) = *reinterpret_cast<const float4 *>(&u[a][b0]);
+        }
+        __syncthreads();   // the stage is free for the copy issued at the next iteration
+    }
+}
+
+template <int SW, typename TS>
+size_t tma_smem() { return sizeof(TmaSmem<TS>) + 128; }
+
+// Resident blocks per SM of each instantiation (measured once at set-up, outside any capture).
+template <int SW, typename TS>
+int &tma_blocks_per_sm() {
+    static int b = 1;
+    return b;
+}
+
+template <int SW, typename TS>
+void set_attr() {
+    cudaFuncSetAttribute(k_sweep_tma<SW, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<SW, TS>());
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_sweep_tma<SW, TS>, TS::NT, tma_smem<SW, TS>()) !=
+            cudaSuccess || v < 1)
+        v = 1;
+    tma_blocks_per_sm<SW, TS>() = v;
+}
+
+template <typename TS>
+void set_attrs() { set_attr<0, TS>(); set_attr<1, TS>(); set_attr<2, TS>(); set_attr<3, TS>(); }
+
+template <int SW, typename TS>
+void launch_one(const LevelView<float> &L, const SweepMaps &M, int sms, int *err, cudaStream_t st) {
+    const int ntiles = ((L.m + TS::OW - 1) / TS::OW) * ((L.n + TS::OH - 1) / TS::OH);
+    const int grid = std::min(ntiles, sms * tma_blocks_per_sm<SW, TS>());
+    const CUtensorMap *in = reinterpret_cast<const CUtensorMap *>((SW & 1) ? M.t : M.u);
+    k_sweep_tma<SW, TS><<<grid, TS::NT, tma_smem<SW, TS>(), st>>>(
+        L, *in, *reinterpret_cast<const CUtensorMap *>(M.G), *reinterpret_cast<const CUtensorMap *>(M.f), err);
+}
+
+template <typename TS>
+void launch_shape(const LevelView<float> &L, int sweep, const SweepMaps &M, int sms, int *err, cudaStream_t st) {
+    switch (sweep) {
+        case 0: launch_one<0, TS>(L, M, sms, err, st); break;
+        case 1: launch_one<1, TS>(L, M, sms, err, st); break;
+        case 2: launch_one<2, TS>(L, M, sms, err, st); break;
+        default: launch_one<3, TS>(L, M, sms, err, st); break;
+    }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+    static EncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+// One FP32 n x m grid function with row pitch `pitch` (elements) as a 2-D tensor, box RW x RH,
+// zero fill outside.
+bool encode(void *out, float *base, int n, int m, int pitch, int RH, int RW) {
+    EncodeFn fn = encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)RW, (cuuint32_t)RH};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(reinterpret_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename TS>
+bool encode_shape(const LevelView<float> &L, SweepMaps &M) {
+    return encode(M.u, L.u, L.n, L.m, L.pitch, TS::RH, TS::RW) && encode(M.t, L.t, L.n, L.m, L.pitch, TS::RH, TS::RW) &&
+           encode(M.G, L.G, L.n, L.m, L.pitch, TS::RH, TS::RW) && encode(M.f, L.f, L.n, L.m, L.pitch, TS::RH, TS::RW);
+}
+
+int g_sms = 0;
+
+}  // namespace
+
+void prepare_sweep_tma() {
+    set_attrs<TT0>(); set_attrs<TT1>(); set_attrs<TT2>();
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms < 1) g_sms = 1;
+}
+
+bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M) {
+    if (shape == 1) return encode_shape<TT1>(L, *M);
+    if (shape == 2) return encode_shape<TT2>(L, *M);
+    return encode_shape<TT0>(L, *M);
+}
+
+void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const SweepMaps &M, int *err, cudaStream_t st) {
+    if (shape == 1) launch_shape<TT1>(L, sweep, M, g_sms, err, st);
+    else if (shape == 2) launch_shape<TT2>(L, sweep, M, g_sms, err, st);
+    else launch_shape<TT0>(L, sweep, M, g_sms, err, st);
+}
+
+}  // namespace segmg

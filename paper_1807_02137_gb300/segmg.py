@@ -16,7 +16,7 @@ from . import buildlib as _build
 
 MG_F32, MG_F64, MG_MIXED = 0, 1, 2
 MG_MODEL_SC, MG_MODEL_RC = 0, 1
-MG_SMOOTH_FUSED, MG_SMOOTH_PHASED = 0, 1
+MG_SMOOTH_FUSED, MG_SMOOTH_PHASED, MG_SMOOTH_FUSED_VEC = 0, 1, 2
 ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4: "MG_ERR_DIVERGED",
           -5: "MG_ERR_TIMEOUT", -6: "MG_ERR_NOT_SPD", -7: "MG_ERR_NOMEM", -8: "MG_ERR_STATE"}
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",

@@ -70,13 +70,13 @@ def test_fused_and_phased_smoothers_are_bitwise_equal(segmg, precision):
     prec = segmg.MG_F64 if precision == "f64" else segmg.MG_F32
     img, mk, _ = synth.ellipses(200, 170, 6, (20, 80), 6, 0.05, 7)
     outs = []
-    for sm in (0, 1):
+    for sm in (0, 1, 2):   # TMA-staged fused sweep (FP32) / per-phase kernels / vector-load fused sweep
         s, _ = gpu_solver(segmg, img, mk, precision=prec, levels=4, smoother=sm)
         s.begin_step()
         for _ in range(2):
             s.vcycle()
         outs.append(s.phi().cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
 def test_fp32_solution_matches_oracle_small(segmg):
@@ -307,7 +307,7 @@ def test_fused_sweep_is_scheduling_independent_on_multi_wave_grids(segmg):
     # cells, so the fused sweep equals the per-phase path bitwise and runs repeat bitwise
     img, mk, _ = synth.ellipses(2048, 2048, 24, (40, 400), 8, 0.05, 21)
     outs = []
-    for sm in (0, 0, 1):
+    for sm in (0, 0, 1, 2):
         s, _ = gpu_solver(segmg, img, mk, precision=segmg.MG_F32, levels=10, smoother=sm)
         s.begin_step()
         for _ in range(2):
@@ -315,4 +315,4 @@ def test_fused_sweep_is_scheduling_independent_on_multi_wave_grids(segmg):
         outs.append(s.phi().cpu().numpy())
         s.close()
     assert np.array_equal(outs[0], outs[1])
-    assert np.array_equal(outs[0], outs[2])
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[0], outs[3])
