@@ -94,6 +94,8 @@ def lib():
                 "or_frozen_coeffs": ([D, D, D, D, C.c_int, C.c_int, C.c_double, P, C.c_double, C.c_double, D], None),
                 "or_smooth_given": ([D, C.c_int, C.c_int, C.c_double, C.c_int, D], None),
                 "or_members": ([D, C.c_int, C.c_int, C.c_double, C.c_int, I], None),
+                "or_energy": ([D, D, D, D, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P], C.c_double),
+                "or_solver_energy": ([C.c_void_p], C.c_double),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -142,6 +144,16 @@ def initial_phi(n, m, markers, r0=None):
     r0 = 0.05 * max(n, m) if r0 is None else r0
     h = lib().or_initial_phi(n, m, px, py, len(mk), r0, _d(out)[1], _d(area)[1])
     return out, float(area[0]), h
+
+
+def energy(phi, z, w, d, c1, c2, A1, p: Params):
+    """Level-set energy of eq. scfunc / rcfunc on one grid in pixel units (or_energy)."""
+    phi, pp = _d(phi)
+    z, pz = _d(z)
+    w, pw = _d(w)
+    d, pd = _d(d)
+    n, m = phi.shape
+    return float(lib().or_energy(pp, pz, pw, pd, n, m, c1, c2, A1, C.byref(p)))
 
 
 def region_means(phi, z, eps=1.0):
@@ -304,6 +316,10 @@ class Solver:
 
     def set_c(self, c1, c2):
         lib().or_set_c(self._h, c1, c2)
+
+    def energy(self) -> float:
+        """Energy of the current finest-grid phi with the current c1, c2 (or_solver_energy)."""
+        return float(lib().or_solver_energy(self._h))
 
     def solve_step(self, tol, max_cycles=50):
         """One pseudo-time step: V-cycles until rho <= tol.  Returns list of rho."""

@@ -43,8 +43,12 @@ typedef struct {
     double inv_tau;       /* 1/tau of the implicit pseudo-time step (0 = steady equation) */
     int nu1, nu2;         /* pre/post smoothing outer iterations */
     int levels;           /* number of grids (finest = level 0) */
-    int smoother;         /* 0 = Hybrid Smoother 2, parallel ordering; 1 = Hybrid Smoother 2,
-                             lexicographic ordering of Fig. 4; 2 = GSLINE-I (Algorithm 1) */
+    int smoother;         /* 0 = Hybrid Smoother 2, parallel ordering (Algorithm 3 on the GPU);
+                             1 = Hybrid Smoother 2, lexicographic ordering of Fig. 4;
+                             2 = GSLINE-I, columns left to right (Algorithm 1);
+                             3 = GSLINE-I, even then odd columns;
+                             4 = Hybrid Smoother 1, lexicographic (Algorithm 2);
+                             5 = Hybrid Smoother 1, parallel ordering */
     int coarse_maxit;     /* Picard iterations cap of the coarsest solve */
     double coarse_tol;    /* relative nonlinear-residual target of the coarsest solve */
 } or_params;
@@ -661,6 +665,94 @@ static void gsline_columns(const or_coeffs *k, double *phi)
     for (int j = 0; j < k->m; ++j) solve_run(k, phi, phi, 0, j, 0, k->n - 1);
 }
 
+/* GSLINE-I in the zebra ordering (Algorithm 1's smoother restated for parallel hardware): all
+ * even columns, each solved exactly as in gsline_columns, then all odd columns.  Columns of one
+ * parity are not neighbours, so solving them one after another equals solving them together
+ * from the values at the start of the phase.  Pinned by: the block definition. */
+static void gsline_zebra(const or_coeffs *k, double *phi)
+{
+    for (int par = 0; par < 2; ++par)
+        for (int j = par; j < k->m; j += 2) solve_run(k, phi, phi, 0, j, 0, k->n - 1);
+}
+
+/* Hybrid Smoother 1 block (Sec. 4.2, the schemes with A, B, C or D lagged, eqs. caseAlagged to
+ * caseDlagged) at a cell P of the set D whose smallest coefficient is `lag` (0..3 = A..D): P and
+ * its neighbours other than the lagged one are updated together by solving their own equations
+ * exactly, every other value (the lagged neighbour included) at its current value.  The
+ * neighbours are not neighbours of each other, so the system is an arrow matrix; the leaves are
+ * eliminated into P's row.  (The paper prints the couplings of the leaf rows with P's
+ * coefficients; the rows here keep their own coefficients, A of the north neighbour for its
+ * coupling to P and so on, which after division of each row by its delta are the same numbers.)
+ * A neighbour outside the grid is not part of the block.  Pinned by: the block definition. */
+static void hs1_block(const or_coeffs *k, double *phi, int i, int j, int lag)
+{
+    int n = k->n, m = k->m;
+    size_t q = (size_t)i * m + j;
+    /* neighbour offsets and existence in A, B, C, D order */
+    int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+    const double *cP[4] = {k->A, k->B, k->C, k->D};
+    /* the coefficient of a leaf's row for its neighbour in the opposite direction (P) */
+    int opp[4] = {1, 0, 3, 2};
+    double rP = k->f[q], num = 0.0, den = -k->S[q];
+    double rl[4], cl[4], Sl[4];
+    int has[4];
+    for (int t = 0; t < 4; ++t) {
+        int ii = i + di[t], jj = j + dj[t];
+        has[t] = ii >= 0 && ii < n && jj >= 0 && jj < m;
+        if (!has[t]) continue;
+        size_t ql = (size_t)ii * m + jj;
+        if (t == lag) { rP -= cP[t][q] * phi[ql]; has[t] = 0; continue; }
+        /* leaf row: c_lP x_P - S_l x_l = f_l - sum over its other neighbours */
+        double r = k->f[ql];
+        for (int u = 0; u < 4; ++u) {
+            if (u == opp[t]) continue;
+            int i2 = ii + di[u], j2 = jj + dj[u];
+            if (i2 < 0 || i2 >= n || j2 < 0 || j2 >= m) continue;
+            r -= cP[u][ql] * phi[(size_t)i2 * m + j2];
+        }
+        rl[t] = r;
+        cl[t] = cP[opp[t]][ql];
+        Sl[t] = k->S[ql];
+        /* x_l = (c_lP x_P - r_l) / S_l substituted into P's row */
+        num += cP[t][q] * r / Sl[t];
+        den += cP[t][q] * cl[t] / Sl[t];
+    }
+    double xP = (rP + num) / den;
+    phi[q] = xP;
+    for (int t = 0; t < 4; ++t) {
+        if (!has[t]) continue;
+        size_t ql = (size_t)(i + di[t]) * m + (j + dj[t]);
+        phi[ql] = (cl[t] * xP - rl[t]) / Sl[t];
+    }
+}
+
+/* Hybrid Smoother 1 as Algorithm 2 runs it (Sec. 4.2, steps I-II): GSLINE-I on all columns, then
+ * the block of every cell of D in lexicographic order (rows top to bottom, left to right). */
+static void hs1_lexicographic(const or_coeffs *k, double Sigma, double *phi)
+{
+    gsline_columns(k, phi);
+    for (int i = 0; i < k->n; ++i)
+        for (int j = 0; j < k->m; ++j) {
+            int c = cell_class(k, i, j, Sigma);
+            if (c >= 0) hs1_block(k, phi, i, j, c);
+        }
+}
+
+/* Hybrid Smoother 1 in the parallel ordering used on the GPU: GSLINE-I zebra, then the blocks of
+ * D in 16 classes (i mod 4, j mod 4), class by class.  Two blocks of one class have centres at
+ * least 4 cells apart (Manhattan), so neither reads a cell the other writes: solving a class's
+ * blocks one after another equals solving them together.  Pinned by: the block definition. */
+static void hs1_parallel(const or_coeffs *k, double Sigma, double *phi)
+{
+    gsline_zebra(k, phi);
+    for (int c = 0; c < 16; ++c)
+        for (int i = c / 4; i < k->n; i += 4)
+            for (int j = c % 4; j < k->m; j += 4) {
+                int cls = cell_class(k, i, j, Sigma);
+                if (cls >= 0) hs1_block(k, phi, i, j, cls);
+            }
+}
+
 /* ------------------------------------------------------------------------------------- */
 /* Coarsest-grid solve (Algorithm 1, "compute the exact solution")                        */
 /* ------------------------------------------------------------------------------------- */
@@ -780,6 +872,19 @@ typedef struct {
     int picard_last;
 } or_solver;
 
+/* One outer iteration of smoother `kind` with frozen coefficients k. */
+static void run_smoother(const or_coeffs *k, double Sigma, int kind, double *phi)
+{
+    switch (kind) {
+        case 0: hs2_parallel(k, Sigma, phi); break;
+        case 1: hs2_lexicographic(k, Sigma, phi); break;
+        case 2: gsline_columns(k, phi); break;
+        case 3: gsline_zebra(k, phi); break;
+        case 4: hs1_lexicographic(k, Sigma, phi); break;
+        default: hs1_parallel(k, Sigma, phi); break;
+    }
+}
+
 /* One outer iteration of the selected smoother on level l (Algorithm 1, "Smoother"). */
 static void smooth(or_solver *s, int l)
 {
@@ -787,9 +892,7 @@ static void smooth(or_solver *s, int l)
     or_coeffs k;
     coeffs_alloc(&k, L->n, L->m);
     frozen_coeffs(L->phi, L->w, L->Fn, L->rhs, L->n, L->m, L->h, &s->p, s->n0m0, s->A1, &k);
-    if (s->p.smoother == 0) hs2_parallel(&k, s->p.Sigma, L->phi);
-    else if (s->p.smoother == 1) hs2_lexicographic(&k, s->p.Sigma, L->phi);
-    else gsline_columns(&k, L->phi);
+    run_smoother(&k, s->p.Sigma, s->p.smoother, L->phi);
     coeffs_free(&k);
 }
 
@@ -935,6 +1038,49 @@ double or_end_step(or_solver *s)
     return pn > 0 ? sqrt(dn / pn) : sqrt(dn);
 }
 
+/* Energy of a level set on the finest grid (the functionals of Sec. 2.2: eq. scfunc for
+ * Spencer-Chen, eq. rcfunc for Rada-Chen; Table 7 reports it after each cycle), in pixel units
+ * (h = 1, areas summed over cells):
+ *   E = sum_ij [ mu w |grad H_eps(phi)| + lambda1 (z - c1)^2 H + lambda2 (z - c2)^2 (1 - H) ]
+ *       + theta sum_ij d H                               (Spencer-Chen)
+ *       + nu n m (sum_ij H / (n m) - A1 / (n m))^2       (Rada-Chen)
+ * with H = H_eps(phi), |grad H_eps(phi)| = delta_eps(phi) |grad phi|_beta (central differences,
+ * mirror ghosts, as in the coefficients), w = g (Spencer-Chen) or d g (Rada-Chen).  Reading:
+ * the two squared area terms of eq. rcfunc are one term, since |Omega_2| - A2 = -(|Omega_1| - A1);
+ * it is written with area fractions and scaled so that its first variation is the area term
+ * 2 nu (sum H / (n m) - A1 / (n m)) of the equation solved (the factor of 2 absorbed in nu, as
+ * there).  Pinned by: the co-area formula (a straight and a circular contour give mu times
+ * their length), the fitting terms of a sharp two-region level set against region variances,
+ * the distance term and the area term of a sharp level set against their closed forms. */
+double or_energy(const double *phi, const double *z, const double *w, const double *d, int n, int m,
+                 double c1, double c2, double A1, const or_params *p)
+{
+    double E = 0.0, sH = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < m; ++j) {
+            size_t q = (size_t)i * m + j;
+            double H = heaviside(phi[q], p->eps);
+            double len = dirac(phi[q], p->eps) * grad_norm(phi, n, m, 1.0, p->beta, i, j);
+            double e = p->mu * w[q] * len + p->lambda1 * (z[q] - c1) * (z[q] - c1) * H
+                     + p->lambda2 * (z[q] - c2) * (z[q] - c2) * (1.0 - H);
+            if (p->model == 0) e += p->theta * d[q] * H;
+            E += e;
+            sH += H;
+        }
+    if (p->model == 1) {
+        double nm = (double)n * m, a = sH / nm - A1 / nm;
+        E += p->nu * nm * a * a;
+    }
+    return E;
+}
+
+/* The energy of the solver's current finest-grid phi with its current c1, c2. */
+double or_solver_energy(const or_solver *s)
+{
+    const or_level *F = &s->lv[0];
+    return or_energy(F->phi, F->z, F->w, F->d, F->n, F->m, s->c1, s->c2, s->A1, &s->p);
+}
+
 /* Accessors used by the tests. */
 void or_get_phi(const or_solver *s, double *out)
 {
@@ -974,8 +1120,7 @@ void or_frozen_coeffs(const double *phi, const double *w, const double *Fn, cons
 }
 
 /* One outer smoothing iteration with given frozen coefficients (A..D, S, f as above), for the
- * tests: kind 0 = parallel Hybrid Smoother 2, 1 = lexicographic Hybrid Smoother 2,
- * 2 = GSLINE-I. */
+ * tests: kind as or_params.smoother. */
 void or_smooth_given(const double *coef, int n, int m, double Sigma, int kind, double *phi)
 {
     size_t N = (size_t)n * m;
@@ -984,9 +1129,7 @@ void or_smooth_given(const double *coef, int n, int m, double Sigma, int kind, d
     k.A = (double *)coef; k.B = (double *)coef + N; k.C = (double *)coef + 2 * N;
     k.D = (double *)coef + 3 * N; k.S = (double *)coef + 4 * N; k.f = (double *)coef + 5 * N;
     k.delta = NULL;
-    if (kind == 0) hs2_parallel(&k, Sigma, phi);
-    else if (kind == 1) hs2_lexicographic(&k, Sigma, phi);
-    else gsline_columns(&k, phi);
+    run_smoother(&k, Sigma, kind, phi);
 }
 
 /* Member flags of the four sweeps (parallel ordering) for given coefficients: out[k*N + q]. */

@@ -155,11 +155,62 @@ def test_gsline_matches_block_definition():
     assert np.allclose(T, block_matrix(assemble(K), phases, n * m), atol=1e-12)
 
 
+def _zebra_phases(n, m):
+    return [[[i * m + j for i in range(n)] for j in range(par, m, 2)] for par in (0, 1)]
+
+
+def _hs1_block(K, i, j, lag, Sigma=2.0):
+    n, m = K["S"].shape
+    cells = [i * m + j]
+    for t, (di, dj) in enumerate(((1, 0), (-1, 0), (0, 1), (0, -1))):
+        ii, jj = i + di, j + dj
+        if t != lag and 0 <= ii < n and 0 <= jj < m:
+            cells.append(ii * m + jj)
+    return cells
+
+
+def _cls(K, i, j, Sigma=2.0):
+    n, m = K["S"].shape
+    return O.classify(K["A"][i, j], K["B"][i, j], K["C"][i, j], K["D"][i, j],
+                      (i + 1 < n, i > 0, j + 1 < m, j > 0), Sigma)
+
+
+def test_gsline_zebra_matches_block_definition():
+    n, m = 7, 9
+    K = rand_coef(n, m, 15)
+    T = oracle_matrix(K, 3)
+    assert np.allclose(T, block_matrix(assemble(K), _zebra_phases(n, m), n * m), atol=1e-12)
+
+
+@pytest.mark.parametrize("n,m,seed", [(7, 8, 16), (9, 6, 17)])
+def test_hybrid_smoother_1_lexicographic_matches_block_definition(n, m, seed):
+    K = rand_coef(n, m, seed)
+    D = [(i, j, _cls(K, i, j)) for i in range(n) for j in range(m) if _cls(K, i, j) >= 0]
+    assert len(D) > 5
+    phases = [[[i * m + j for i in range(n)]] for j in range(m)]
+    phases += [[_hs1_block(K, i, j, c)] for i, j, c in D]
+    T = oracle_matrix(K, 4)
+    assert np.allclose(T, block_matrix(assemble(K), phases, n * m), atol=1e-11)
+
+
+@pytest.mark.parametrize("n,m,seed", [(9, 10, 18), (11, 7, 19)])
+def test_hybrid_smoother_1_parallel_matches_block_definition(n, m, seed):
+    K = rand_coef(n, m, seed)
+    phases = _zebra_phases(n, m)
+    for c in range(16):
+        blocks = [_hs1_block(K, i, j, _cls(K, i, j)) for i in range(c // 4, n, 4)
+                  for j in range(c % 4, m, 4) if _cls(K, i, j) >= 0]
+        phases.append(blocks)
+    assert sum(len(b) for b in phases[2:]) > 5
+    T = oracle_matrix(K, 5)
+    assert np.allclose(T, block_matrix(assemble(K), phases, n * m), atol=1e-11)
+
+
 def test_smoothers_converge_to_the_direct_solution():
     K = rand_coef(12, 10, 6, spread=2.0, extra=0.5)
     M = assemble(K)
     x = solve(M, K["f"].ravel())                     # M phi = f
-    for kind in (0, 1, 2):
+    for kind in (0, 1, 2, 3, 4, 5):
         phi = np.zeros((12, 10))
         for _ in range(200):
             phi = O.smooth_given(K, phi, 2.0, kind)

@@ -119,13 +119,14 @@ def test_rada_chen_fas_converges():
 
 
 def test_paper_orderings_converge_too():
-    # The lexicographic Hybrid Smoother 2 (the paper's Algorithm 3) and GSLINE-I (Algorithm 1)
-    # drive the same first step to the same solution.
+    # Both orderings of Hybrid Smoother 2 (Algorithm 3), of GSLINE-I (Algorithm 1) and of Hybrid
+    # Smoother 1 (Algorithm 2) drive the same first step to the same solution.
     img, mk, _ = synth.disc_square(64, 0.05, 6)
     sols = []
-    for sm in (0, 1, 2):
+    for sm in (0, 1, 2, 3, 4, 5):
         s = O.Solver(img, mk, O.params(64, 64, levels=4, smoother=sm))
         hist = s.solve_step(1e-10, 80)
         assert hist[-1] <= 1e-10
         sols.append(s.phi)
-    assert np.allclose(sols[0], sols[1], atol=1e-8) and np.allclose(sols[0], sols[2], atol=1e-8)
+    for x in sols[1:]:
+        assert np.allclose(sols[0], x, atol=1e-8)
