@@ -51,10 +51,19 @@ enum {
 enum { MG_MODEL_SC = 0, MG_MODEL_RC = 1 };       /* Spencer-Chen / Rada-Chen (Sec. 2.2) */
 enum { MG_F32 = 0, MG_F64 = 1, MG_MIXED = 2 };  /* storage and smoothing precision; MG_MIXED = FP32
                                                     with the image-derived weight w held in BF16 */
-/* Hybrid Smoother 2 kernels (same results): one kernel per sweep with tiles staged by the
- * Tensor Memory Accelerator (FP64 storage: by vector loads), one kernel per phase, or one kernel
- * per sweep with vector loads. */
-enum { MG_SMOOTH_FUSED = 0, MG_SMOOTH_PHASED = 1, MG_SMOOTH_FUSED_VEC = 2 };
+/* Smoothers.  Hybrid Smoother 2 (Sec. 4.3, the paper's Algorithm 3), three kernel variants with
+ * the same results: one kernel per sweep with tiles staged by the Tensor Memory Accelerator
+ * (FP64 storage: by vector loads), one kernel per phase, or one kernel per sweep with vector
+ * loads.  The paper's other smoothers, in parallel orderings: GSLINE-I (Sec. 3.2, Algorithm 1;
+ * even columns, then odd columns) and Hybrid Smoother 1 (Sec. 4.2, Algorithm 2; GSLINE-I, then
+ * the arrow-system blocks of the set D in 16 classes (i mod 4, j mod 4)). */
+enum {
+    MG_SMOOTH_FUSED = 0,
+    MG_SMOOTH_PHASED = 1,
+    MG_SMOOTH_FUSED_VEC = 2,
+    MG_SMOOTH_GSLINE = 3,
+    MG_SMOOTH_HS1 = 4
+};
 
 typedef struct mg_handle_s *mg_handle;
 
@@ -78,7 +87,7 @@ typedef struct {
     int levels;            /* number of grids, finest included (>= 1) */
     int precision;         /* MG_F32, MG_F64 or MG_MIXED (norms and c1/c2 sums are FP64 in every
                               mode; the coarsest solve is FP32 with MG_F32, else FP64) */
-    int smoother;          /* MG_SMOOTH_FUSED, MG_SMOOTH_PHASED or MG_SMOOTH_FUSED_VEC */
+    int smoother;          /* MG_SMOOTH_* */
     int coarse_maxit;      /* Picard cap of the coarsest solve (>= 1) */
     double coarse_tol;     /* relative residual target of the coarsest solve */
     int use_graph;         /* 1: replay each V-cycle as a captured CUDA graph */
@@ -191,6 +200,16 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
 int mg_autotune(mg_handle h, int reps, int *shapes);
 /* Sets the fused-sweep tile shape of grids 0..levels-2 (values 0..2 as above). */
 int mg_set_tile_shapes(mg_handle h, const int *shapes);
+/* Energy of the current level set (Sec. 2.2: eq. scfunc for Spencer-Chen, eq. rcfunc for
+ * Rada-Chen; the diagnostic the paper reports after each cycle in Table 7), on the finest grid
+ * in pixel units, with the current c1, c2:
+ *   E = sum_ij [mu w delta_eps(phi) |grad phi|_beta + lambda1 (z - c1)^2 H + lambda2 (z - c2)^2 (1 - H)]
+ *       + theta sum_ij d H                      (Spencer-Chen; w = g)
+ *       + nu n m (sum_ij H / (n m) - A1 / (n m))^2   (Rada-Chen; w = d g)
+ * with H = H_eps(phi) and central differences with mirror ghosts.  Sums are FP64.  *E (host)
+ * receives it; waits for the handle's stream.  Errors: MG_ERR_ARG (NULL), MG_ERR_CUDA. */
+int mg_energy(mg_handle h, double *E);
+
 /* The bottom of the V-cycle in one block: with MG_F32 / MG_MIXED storage, the Spencer-Chen
  * model and the fused smoother, the grids from the largest one whose whole sub-cycle (pn, u, w,
  * F, rhs, G, f, u0, masks and the coarsest solve's scratch) fits in 200 KB of shared memory

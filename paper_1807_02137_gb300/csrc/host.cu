@@ -106,6 +106,7 @@ struct SolverBase {
     virtual int autotune(int reps, int *out) = 0;
     virtual int set_shapes(const int *shapes) = 0;
     virtual int set_bottom(int enable) = 0;
+    virtual int energy(double *E) = 0;
 };
 
 template <typename T>
@@ -116,6 +117,7 @@ struct Level {
     T *F = nullptr, *G = nullptr, *f = nullptr, *r = nullptr, *upre = nullptr, *t = nullptr;
     uint32_t *mrow = nullptr, *mcol = nullptr;
     __nv_bfloat16 *wb = nullptr;   // mixed precision only
+    uint8_t *cls = nullptr;        // Hybrid Smoother 1 only
     SweepMaps maps[kTileShapes];   // FP32 storage: tensor maps of the TMA sweep, per tile shape
 };
 
@@ -181,6 +183,7 @@ struct Solver final : SolverBase {
         v.F = L.F; v.G = L.G; v.f = L.f; v.r = L.r; v.upre = L.upre; v.t = L.t;
         v.mrow = L.mrow; v.mcol = L.mcol; v.npm = (L.m + 31) / 32; v.npn = (L.n + 31) / 32;
         v.wb = L.wb;
+        v.cls = L.cls;
         v.has_rhs = l > 0 ? 1 : 0;
         return v;
     }
@@ -210,6 +213,7 @@ struct Solver final : SolverBase {
             }
             if (p.smoother == MG_SMOOTH_PHASED) plan.push_back({(void **)&L.upre, take(fb)});
             if (p.precision == MG_MIXED) plan.push_back({(void **)&L.wb, take((size_t)L.n * L.pitch * 2)});
+            if (p.smoother == MG_SMOOTH_HS1) plan.push_back({(void **)&L.cls, take((size_t)L.n * L.pitch)});
             plan.push_back({(void **)&L.mrow, take(sizeof(uint32_t) * 2 * (size_t)L.n * ((L.m + 31) / 32))});
             plan.push_back({(void **)&L.mcol, take(sizeof(uint32_t) * 2 * (size_t)L.m * ((L.n + 31) / 32))});
             nn /= 2; mm /= 2;
@@ -254,7 +258,7 @@ struct Solver final : SolverBase {
     int set_bottom(int enable) override {
         lb = -1;
         lb_smem = 0;
-        if (enable && sizeof(T) == 4 && p.model == MG_MODEL_SC && p.smoother != MG_SMOOTH_PHASED) {
+        if (enable && sizeof(T) == 4 && p.model == MG_MODEL_SC && fused()) {
             int ns[kMaxLevels], ms[kMaxLevels];
             for (int l = 0; l < nlev; ++l) { ns[l] = lv[l].n; ms[l] = lv[l].m; }
             for (int l = nlev - 2; l >= 0; --l) {
@@ -266,6 +270,15 @@ struct Solver final : SolverBase {
         }
         if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
         return lb;
+    }
+
+    int energy(double *E) override {
+        launch_energy<T>(view(0), mp, partials, npart, dsc, &dsc->sums[7], st);
+        ++launches;
+        CKL();
+        CK(cudaMemcpyAsync(E, &dsc->sums[7], sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return MG_OK;
     }
 
     void launch_bottom_cycle() {
@@ -382,7 +395,17 @@ struct Solver final : SolverBase {
 
     // kernels per call of each enqueue helper (for the launch counter)
     int area_launches() const { return p.model == MG_MODEL_RC ? 2 : 0; }
-    int sweep_launches() const { return p.smoother == MG_SMOOTH_PHASED ? 4 : 1; }
+    bool fused() const { return p.smoother == MG_SMOOTH_FUSED || p.smoother == MG_SMOOTH_FUSED_VEC; }
+    // kernels of one outer smoothing iteration after the snapshot on grid l
+    int smoother_launches(int l) const {
+        if (p.smoother == MG_SMOOTH_PHASED) return 16;
+        if (fused()) return 4;
+        int k = 0;
+        for (int par = 0; par < 2; ++par) k += (lv[l].m - par + 1) / 2 > 0;
+        if (p.smoother == MG_SMOOTH_HS1)
+            for (int c = 0; c < 16; ++c) k += (lv[l].n - c / 4 + 3) / 4 > 0 && (lv[l].m - c % 4 + 3) / 4 > 0;
+        return k;
+    }
 
     // One directional sweep k of grid l with tile shape sh.
     void sweep(int l, const LevelView<T> &v, int k, int sh) {
@@ -396,12 +419,23 @@ struct Solver final : SolverBase {
         }
     }
 
+    // The smoother after the snapshot: four directional sweeps of Hybrid Smoother 2, or GSLINE-I
+    // (and the Hybrid Smoother 1 blocks).
+    void relax(int l, const LevelView<T> &v, int sh) {
+        if (p.smoother == MG_SMOOTH_GSLINE || p.smoother == MG_SMOOTH_HS1) {
+            launch_gsline<T>(v, st);
+            if (p.smoother == MG_SMOOTH_HS1) launch_hs1_blocks<T>(v, st);
+        } else {
+            for (int k = 0; k < 4; ++k) sweep(l, v, k, sh);
+        }
+    }
+
     void smooth(int l) {
         area_term(l, lv[l].u);
         LevelView<T> v = view(l);
         launch_snapshot<T>(v, area_ptr(), st);
-        for (int k = 0; k < 4; ++k) sweep(l, v, k, shape[l]);
-        launches += area_launches() + 1 + 4 * sweep_launches();
+        relax(l, v, shape[l]);
+        launches += area_launches() + 1 + smoother_launches(l);
     }
 
     void cycle(int l) {
@@ -464,7 +498,7 @@ struct Solver final : SolverBase {
     // (snapshot + four sweeps, `reps` times) per shape; the state is restored afterwards.
     int autotune(int reps, int *out) {
         if (!in_step) return fail(MG_ERR_STATE, "mg_autotune outside a step");
-        if (p.smoother == MG_SMOOTH_PHASED) return fail(MG_ERR_ARG, "autotune applies to the fused smoother");
+        if (!fused()) return fail(MG_ERR_ARG, "autotune applies to the fused Hybrid Smoother 2");
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
@@ -620,13 +654,18 @@ struct Solver final : SolverBase {
             cudaEventRecord(ev[0], st);
             launch_snapshot<T>(v, area_ptr(), st);
             cudaEventRecord(ev[1], st);
-            for (int k = 0; k < 4; ++k) {
-                sweep(l, v, k, shape[l]);
-                cudaEventRecord(ev[2 + k], st);
+            if (p.smoother == MG_SMOOTH_GSLINE || p.smoother == MG_SMOOTH_HS1) {
+                relax(l, v, shape[l]);        // the whole smoother in the first slot
+                for (int k = 0; k < 4; ++k) cudaEventRecord(ev[2 + k], st);
+            } else {
+                for (int k = 0; k < 4; ++k) {
+                    sweep(l, v, k, shape[l]);
+                    cudaEventRecord(ev[2 + k], st);
+                }
             }
             launch_residual<T>(v, lv[l].u, area_ptr(), lv[l].r, 0, partials, 0, nullptr, st);
             cudaEventRecord(ev[6], st);
-            launches += area_launches() + 2 + 4 * sweep_launches();
+            launches += area_launches() + 2 + smoother_launches(l);
             CKL();
             CK(cudaEventSynchronize(ev[6]));
             for (int k = 0; k < 6; ++k) {
@@ -647,8 +686,7 @@ int check_params(const mg_params *p, int n, int m) {
     if (p->model != MG_MODEL_SC && p->model != MG_MODEL_RC) return fail(MG_ERR_ARG, "model");
     if (p->precision != MG_F32 && p->precision != MG_F64 && p->precision != MG_MIXED)
         return fail(MG_ERR_ARG, "precision");
-    if (p->smoother != MG_SMOOTH_FUSED && p->smoother != MG_SMOOTH_PHASED && p->smoother != MG_SMOOTH_FUSED_VEC)
-        return fail(MG_ERR_ARG, "smoother");
+    if (p->smoother < MG_SMOOTH_FUSED || p->smoother > MG_SMOOTH_HS1) return fail(MG_ERR_ARG, "smoother");
     const double pos[] = {p->mu, p->eps, p->beta, p->sigma_blur, p->sigma_d};
     for (double v : pos)
         if (!(v > 0) || !std::isfinite(v)) return fail(MG_ERR_ARG, "mu, eps, beta, sigma_blur, sigma_d must be > 0");
@@ -1004,6 +1042,11 @@ int mg_autotune(mg_handle h, int reps, int *shapes) {
 int mg_set_tile_shapes(mg_handle h, const int *shapes) {
     if (!h || !shapes) return fail(MG_ERR_ARG, "NULL argument");
     return h->s->set_shapes(shapes);
+}
+
+int mg_energy(mg_handle h, double *E) {
+    if (!h || !E) return fail(MG_ERR_ARG, "NULL argument");
+    return h->s->energy(E);
 }
 
 int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level) {

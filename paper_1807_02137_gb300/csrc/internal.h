@@ -40,6 +40,8 @@ struct LevelView {
     uint32_t *mrow, *mcol;     // member masks (see above)
     int npm, npn;
     const __nv_bfloat16 *wb;   // mixed precision: the length weight w stored in BF16 (else NULL)
+    uint8_t *cls;              // Hybrid Smoother 1 only: per cell 1 << (index of the smallest of
+                               // A..D) if the cell is in D, else 0 (else NULL)
     int has_rhs;    // 0 on the finest grid (zero right-hand side)
 };
 
@@ -105,6 +107,9 @@ void launch_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, int pitc
 template <typename T>
 void launch_area(const LevelView<T> &L, const T *uin, double eps, double nu, double h2_over_nm,
                  double *partials, int npart, double *out, const Scalars *sc, cudaStream_t st);
+template <typename T>
+void launch_energy(const LevelView<T> &L, ModelParams mp, double *partials, int npart, const Scalars *sc,
+                   double *out, cudaStream_t st);
 int num_partials(int n, int m);
 
 // smooth_kernels.cu
@@ -115,6 +120,12 @@ template <typename T>
 void launch_sweep_fused(const LevelView<T> &L, int sweep, int shape, cudaStream_t st);
 template <typename T>
 void launch_sweep_phased(const LevelView<T> &L, int sweep, cudaStream_t st);
+
+// line_smoothers.cu: GSLINE-I (zebra columns) and the Hybrid Smoother 1 blocks
+template <typename T>
+void launch_gsline(const LevelView<T> &L, cudaStream_t st);
+template <typename T>
+void launch_hs1_blocks(const LevelView<T> &L, cudaStream_t st);
 
 // sweep_tma.cu: the fused sweep for FP32 storage with TMA-staged tiles.  A SweepMaps holds the
 // tensor maps (CUtensorMap, 128 bytes each) of u, t, G and f of one grid for one tile shape.

@@ -169,6 +169,69 @@ __global__ void k_region_final(const double *part, int nb, Scalars *sc, int set_
     }
 }
 
+// Level-set energy (Sec. 2.2, eqs. scfunc / rcfunc) of the finest grid, pixel units: per 32 x 32
+// tile the sums of the cell energy
+//   mu w delta(phi) |grad phi|_beta + lambda1 (z - c1)^2 H + lambda2 (z - c2)^2 (1 - H) [+ theta d H]
+// and of H, with phi = pn + u, H = H_eps(phi), delta = delta_eps(phi) and |grad phi|_beta by
+// central differences with mirror ghosts (clamped neighbours).
+template <typename T>
+__global__ void __launch_bounds__(256) k_energy_partials(LevelView<T> L, ModelParams mp, const Scalars *sc,
+                                                         double *part) {
+    __shared__ double red[33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tid = threadIdx.y * 32 + threadIdx.x;
+    const int n = L.n, m = L.m, p = L.pitch;
+    const T c1 = T(sc->c1), c2 = T(sc->c2), eps = T(mp.eps), beta = T(mp.beta);
+    double se = 0.0, sh = 0.0;
+    for (int q = tid; q < 1024; q += 256) {
+        const int gi = i0 + q / 32, gj = j0 + q % 32;
+        if (gi >= n || gj >= m) continue;
+        const size_t o = (size_t)gi * p + gj;
+        auto phi = [&](int i, int j) {
+            const size_t r = (size_t)(i < 0 ? 0 : (i >= n ? n - 1 : i)) * p + (j < 0 ? 0 : (j >= m ? m - 1 : j));
+            return L.pn[r] + L.u[r];
+        };
+        const T ph = phi(gi, gj);
+        const T gx = (phi(gi, gj + 1) - phi(gi, gj - 1)) * T(0.5);
+        const T gy = (phi(gi + 1, gj) - phi(gi - 1, gj)) * T(0.5);
+        const T H = T(0.5) + atan(ph / eps) * T(M_1_PI);
+        const T dl = eps * T(M_1_PI) / (eps * eps + ph * ph);
+        const T z = L.z[o];
+        T e = T(mp.mu) * weight_at(L, o) * dl * sqrt(gx * gx + gy * gy + beta) +
+              T(mp.lambda1) * (z - c1) * (z - c1) * H + T(mp.lambda2) * (z - c2) * (z - c2) * (T(1) - H);
+        if (mp.model == 0) e += T(mp.theta) * L.d[o] * H;
+        se += (double)e;
+        sh += (double)H;
+    }
+    const int b = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+    const double ve = block_sum_setup(se, red);
+    const double vh = block_sum_setup(sh, red);
+    if (tid == 0) {
+        part[b] = ve;
+        part[(size_t)nb + b] = vh;
+    }
+}
+
+// E = sum of the cell energies + (Rada-Chen) nu n m (sum H / (n m) - A1 / (n m))^2, into *out.
+__global__ void k_energy_final(const double *part, int nb, ModelParams mp, double nm, const Scalars *sc,
+                               double *out) {
+    __shared__ double red[33];
+    double ve = 0.0, vh = 0.0;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+        ve += part[q];
+        vh += part[(size_t)nb + q];
+    }
+    ve = block_sum_setup(ve, red);
+    vh = block_sum_setup(vh, red);
+    if (threadIdx.x == 0) {
+        double E = ve;
+        if (mp.model == 1) {
+            const double a = vh / nm - sc->A1frac;
+            E += mp.nu * nm * a * a;
+        }
+        *out = E;
+    }
+}
+
 // Rada-Chen area term 2 nu (h^2 sum H(pn + uin) / (n0 m0) - A1 / (n0 m0)) of one grid.
 template <typename T>
 __global__ void __launch_bounds__(256) k_area_partials(LevelView<T> L, const T *uin, double eps, double *part) {
@@ -210,6 +273,15 @@ __global__ void k_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, in
 inline dim3 grid2(int n, int m) { return dim3((m + 31) / 32, (n + 7) / 8); }
 
 }  // namespace
+
+template <typename T>
+void launch_energy(const LevelView<T> &L, ModelParams mp, double *partials, int npart, const Scalars *sc,
+                   double *out, cudaStream_t st) {
+    dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
+    k_energy_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, mp, sc, partials);
+    k_energy_final<<<1, 1024, 0, st>>>(partials, npart, mp, (double)L.n * L.m, sc, out);
+}
+
 
 template <typename T>
 void launch_copy_in(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st) {
@@ -292,7 +364,9 @@ void launch_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, int pitc
                                         cudaStream_t);                                                \
     template void launch_area<T>(const LevelView<T> &, const T *, double, double, double, double *,  \
                                  int, double *, const Scalars *, cudaStream_t);                       \
-    template void launch_mask<T>(const LevelView<T> &, uint8_t *, cudaStream_t);
+    template void launch_mask<T>(const LevelView<T> &, uint8_t *, cudaStream_t);                    \
+    template void launch_energy<T>(const LevelView<T> &, ModelParams, double *, int, const Scalars *, \
+                                   double *, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
             if (cnt >= 2 && mx > mul_rn(L.Sigma, mn)) star = (uint8_t)(1u << am);
         }
         sStar[ti][tj] = star;
+        if (L.cls && gi < n && gj < m) L.cls[(size_t)gi * p + gj] = star;
     }
     __syncthreads();
     const int warp = tid / 32, lane = tid % 32;

@@ -14,6 +14,11 @@ def need_gpu():
     return segmg
 
 
+# the oracle's smoother with the GPU smoother's ordering: Hybrid Smoother 2 parallel (all three
+# kernel variants), GSLINE-I zebra, Hybrid Smoother 1 parallel
+ORACLE_SMOOTHER = {0: 0, 1: 0, 2: 0, 3: 3, 4: 5}
+
+
 def oracle_params(n, m, gp):
     """Oracle parameters equal to the GPU parameters `gp` (a segmg.Params)."""
     import oracle as O
@@ -21,7 +26,7 @@ def oracle_params(n, m, gp):
                     theta=gp.theta, nu=gp.nu, eps=gp.eps, beta=gp.beta, beta_edge=gp.beta_edge,
                     sigma_blur=gp.sigma_blur, sigma_d=gp.sigma_d, Sigma=gp.Sigma,
                     inv_tau=(1.0 / gp.tau if gp.tau > 0 else 0.0), nu1=gp.nu1, nu2=gp.nu2,
-                    levels=gp.levels, smoother=0, coarse_maxit=gp.coarse_maxit,
+                    levels=gp.levels, smoother=ORACLE_SMOOTHER[gp.smoother], coarse_maxit=gp.coarse_maxit,
                     coarse_tol=gp.coarse_tol)
 
 

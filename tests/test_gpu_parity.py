@@ -316,3 +316,42 @@ def test_fused_sweep_is_scheduling_independent_on_multi_wave_grids(segmg):
         s.close()
     assert np.array_equal(outs[0], outs[1])
     assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[0], outs[3])
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_energy_matches_oracle(segmg, model):
+    # the energy of the level set (Table 7's diagnostic) after set-up, after V-cycles and after
+    # the end-of-step c1/c2 update, FP64 and FP32
+    img, mk, _ = synth.ellipses(150, 131, 6, (20, 70), 5, 0.05, 17)
+    for prec, tol in ((segmg.MG_F64, 1e-10), (segmg.MG_F32, 2e-5)):
+        s, o, p = both(segmg, img.astype(np.float32) if prec == segmg.MG_F32 else img, mk,
+                       precision=prec, levels=4, model=model)
+        assert abs(s.energy() - o.energy()) <= tol * abs(o.energy())
+        s.begin_step(); o.begin_step()
+        for _ in range(3):
+            s.vcycle(); o.vcycle()
+        assert abs(s.energy() - o.energy()) <= tol * abs(o.energy())
+        s.end_step(); o.end_step()
+        assert abs(s.energy() - o.energy()) <= tol * abs(o.energy())
+        s.close()
+
+
+@pytest.mark.parametrize("smoother", [3, 4])
+def test_gsline_and_hybrid_smoother_1_match_oracle(segmg, smoother):
+    # Algorithm 1 (GSLINE-I, zebra columns) and Algorithm 2 (Hybrid Smoother 1, parallel
+    # ordering) against the oracle's same orderings: FP64 per V-cycle, FP32 to the solution
+    img, mk, _ = synth.ellipses(140, 117, 6, (20, 70), 5, 0.05, 23)
+    s, o, p = both(segmg, img, mk, precision=segmg.MG_F64, levels=4, smoother=smoother)
+    s.begin_step(); o.begin_step()
+    for _ in range(3):
+        rg, ro = s.vcycle(), o.vcycle()
+        assert abs(rg - ro) <= 1e-8 * ro
+    assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-10
+    s.close(); o.close()
+    s32, o2, _ = both(segmg, img.astype(np.float32), mk, precision=segmg.MG_F32, levels=4, smoother=smoother)
+    cyc, rho = s32.solve_step(1e-6, 80)
+    hist = o2.solve_step(1e-9, 120)
+    assert rho <= 1e-6 and hist[-1] <= 1e-9
+    pg, po = s32.phi().cpu().numpy(), o2.phi
+    assert relmax(pg, po) < 1e-5
+    assert np.mean((pg > 0) != (po > 0)) <= 1e-4
