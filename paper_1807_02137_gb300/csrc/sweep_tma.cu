@@ -41,12 +41,12 @@ using TT0 = TShape<32, 64, 256>;
 using TT1 = TShape<32, 32, 128>;
 using TT2 = TShape<64, 64, 512>;
 
-template <typename TS>
+template <typename TS, int STAGES>
 struct TmaSmem {
-    float box[2][3][TS::RH][TS::RW];           // [stage][u, G, f][row][column]
+    float box[STAGES][3][TS::RH][TS::RW];      // [stage][u, G, f][row][column]
     uint32_t mk[TS::MkLines][TS::MkPieces];    // member masks of the tile (as k_sweep)
     float endv[TS::MaxTasks][2];
-    unsigned long long bar[2];                 // one mbarrier per stage
+    unsigned long long bar[STAGES];            // one mbarrier per stage
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -90,16 +90,17 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
-template <typename TS, bool ROWWISE>
-__device__ __forceinline__ bool member(const TmaSmem<TS> &S, int a, int b) {
+template <typename TS, int STAGES, bool ROWWISE>
+__device__ __forceinline__ bool member(const TmaSmem<TS, STAGES> &S, int a, int b) {
     if (ROWWISE) return (S.mk[a][(b + 28) >> 5] >> ((b - kH) & 31)) & 1u;
     return (S.mk[b][(a + 28) >> 5] >> ((a - kH) & 31)) & 1u;
 }
 
 // One checkerboard phase over the box cells within distance 3 - ph of the output tile (the
 // cells and the operations of rb_phase in smooth_kernels.cu).
-template <typename TS, int SWEEP, bool INTERIOR>
-__device__ __forceinline__ void rb_phase(TmaSmem<TS> &S, int st, const LevelView<float> &L, int ph, int i0, int j0) {
+template <typename TS, int STAGES, int SWEEP, bool INTERIOR>
+__device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const LevelView<float> &L, int ph, int i0,
+                                         int j0) {
     constexpr int kRH = TS::RH, kRW = TS::RW;
     constexpr bool rev = (SWEEP & 1) != 0;
     float (*u)[kRW] = S.box[st][0];
@@ -117,7 +118,7 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS> &S, int st, const LevelView
             if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
             hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
         }
-        if (member<TS, (SWEEP < 2)>(S, a, b)) continue;
+        if (member<TS, STAGES, (SWEEP < 2)>(S, a, b)) continue;
         const float gc = G[a][b];
         const float aS = face(gc, G[a + 1][b], hS), aN = face(gc, G[a - 1][b], hN);
         const float aE = face(gc, G[a][b + 1], hE), aW = face(gc, G[a][b - 1], hW);
@@ -126,7 +127,10 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS> &S, int st, const LevelView
     }
 }
 
-template <int SWEEP, typename TS>
+// STAGES = 2: persistent blocks, the next tile's copies in flight while a tile is smoothed;
+// STAGES = 1: one box set per block (half the shared memory, more blocks per SM), used when every
+// tile of the grid gets its own resident block.
+template <int SWEEP, typename TS, int STAGES>
 __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const __grid_constant__ CUtensorMap tin,
                                                       const __grid_constant__ CUtensorMap tG,
                                                       const __grid_constant__ CUtensorMap tf, int *err) {
@@ -134,15 +138,14 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
     constexpr int kRowPieces = TS::RowPieces, kColPieces = TS::ColPieces;
     constexpr bool rowwise = SWEEP < 2, rev = (SWEEP & 1) != 0;
     extern __shared__ unsigned char smem_raw[];
-    TmaSmem<TS> &S = *reinterpret_cast<TmaSmem<TS> *>(
+    TmaSmem<TS, STAGES> &S = *reinterpret_cast<TmaSmem<TS, STAGES> *>(
         smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));   // boxes 128-byte aligned
     const int n = L.n, m = L.m, p = L.pitch;
     const int tid = threadIdx.x;
     const int ntx = (m + kOW - 1) / kOW, ntiles = ntx * ((n + kOH - 1) / kOH);
     float *uout = (SWEEP & 1) ? L.u : L.t;   // ping-pong (see k_sweep)
     if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
+        for (int k = 0; k < STAGES; ++k) mbar_init(&S.bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -158,9 +161,10 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
     int tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) issue(tile, 0);
     for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
-        const int st = k & 1;
+        const int st = STAGES == 2 ? (k & 1) : 0;
+        const unsigned parity = STAGES == 2 ? (unsigned)((k >> 1) & 1) : (unsigned)(k & 1);
         const int next = tile + gridDim.x;
-        if (tid == 0 && next < ntiles) issue(next, st ^ 1);
+        if (STAGES == 2 && tid == 0 && next < ntiles) issue(next, st ^ 1);
         const int ty = tile / ntx, tx = tile - ty * ntx;
         const int i0 = ty * kOH, j0 = tx * kOW;
         // member masks of every line piece that touches the box (zero outside the grid)
@@ -183,12 +187,13 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
                 S.mk[b][pc] = w;
             }
         }
-        const bool ok = mbar_wait(&S.bar[st], (unsigned)((k >> 1) & 1));
+        const bool ok = mbar_wait(&S.bar[st], parity);
         if (__syncthreads_or(!ok)) {
-            // a copy never completed: report, let the prefetch (if any) land, and stop
+            // a copy never completed: report, give the copies in flight a last bounded wait, stop
             if (tid == 0) {
                 atomicOr(err, 4);
-                if (next < ntiles) mbar_wait(&S.bar[st ^ 1], (unsigned)(((k + 1) >> 1) & 1));
+                mbar_wait(&S.bar[st], parity);
+                if (STAGES == 2 && next < ntiles) mbar_wait(&S.bar[st ^ 1], (unsigned)(((k + 1) >> 1) & 1));
             }
             __syncthreads();
             return;
@@ -200,8 +205,8 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
         const bool interior = i0 - kH >= 0 && i0 - kH + kRH <= n && j0 - kH >= 0 && j0 - kH + kRW <= m;
 #pragma unroll
         for (int ph = 0; ph < 2; ++ph) {
-            if (interior) rb_phase<TS, SWEEP, true>(S, st, L, ph, i0, j0);
-            else rb_phase<TS, SWEEP, false>(S, st, L, ph, i0, j0);
+            if (interior) rb_phase<TS, STAGES, SWEEP, true>(S, st, L, ph, i0, j0);
+            else rb_phase<TS, STAGES, SWEEP, false>(S, st, L, ph, i0, j0);
             __syncthreads();
         }
         // ---- partial-line phases (as k_sweep): lines at distance 1, then 0, one parity each
@@ -279,40 +284,52 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
             if (gi >= n || gj >= p) continue;
             *reinterpret_cast<float4 *>(uout + (size_t)gi * p + gj) = *reinterpret_cast<const float4 *>(&u[a][b0]);
         }
-        __syncthreads();   // the stage is free for the copy issued at the next iteration
+        __syncthreads();   // the stage is free for the next copy into it
+        if (STAGES == 1 && tid == 0 && next < ntiles) issue(next, 0);
     }
 }
 
-template <int SW, typename TS>
-size_t tma_smem() { return sizeof(TmaSmem<TS>) + 128; }
+template <int SW, typename TS, int STAGES>
+size_t tma_smem() { return sizeof(TmaSmem<TS, STAGES>) + 128; }
 
 // Resident blocks per SM of each instantiation (measured once at set-up, outside any capture).
-template <int SW, typename TS>
+template <int SW, typename TS, int STAGES>
 int &tma_blocks_per_sm() {
     static int b = 1;
     return b;
 }
 
-template <int SW, typename TS>
+template <int SW, typename TS, int STAGES>
 void set_attr() {
-    cudaFuncSetAttribute(k_sweep_tma<SW, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<SW, TS>());
+    cudaFuncSetAttribute(k_sweep_tma<SW, TS, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tma_smem<SW, TS, STAGES>());
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_sweep_tma<SW, TS>, TS::NT, tma_smem<SW, TS>()) !=
-            cudaSuccess || v < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_sweep_tma<SW, TS, STAGES>, TS::NT,
+                                                      tma_smem<SW, TS, STAGES>()) != cudaSuccess || v < 1)
         v = 1;
-    tma_blocks_per_sm<SW, TS>() = v;
+    tma_blocks_per_sm<SW, TS, STAGES>() = v;
 }
 
 template <typename TS>
-void set_attrs() { set_attr<0, TS>(); set_attr<1, TS>(); set_attr<2, TS>(); set_attr<3, TS>(); }
+void set_attrs() {
+    set_attr<0, TS, 1>(); set_attr<1, TS, 1>(); set_attr<2, TS, 1>(); set_attr<3, TS, 1>();
+    set_attr<0, TS, 2>(); set_attr<1, TS, 2>(); set_attr<2, TS, 2>(); set_attr<3, TS, 2>();
+}
 
+// One tile per block when every tile gets a resident block with one stage; else persistent
+// double-buffered blocks, as many as fit.
 template <int SW, typename TS>
 void launch_one(const LevelView<float> &L, const SweepMaps &M, int sms, int *err, cudaStream_t st) {
     const int ntiles = ((L.m + TS::OW - 1) / TS::OW) * ((L.n + TS::OH - 1) / TS::OH);
-    const int grid = std::min(ntiles, sms * tma_blocks_per_sm<SW, TS>());
     const CUtensorMap *in = reinterpret_cast<const CUtensorMap *>((SW & 1) ? M.t : M.u);
-    k_sweep_tma<SW, TS><<<grid, TS::NT, tma_smem<SW, TS>(), st>>>(
-        L, *in, *reinterpret_cast<const CUtensorMap *>(M.G), *reinterpret_cast<const CUtensorMap *>(M.f), err);
+    const CUtensorMap &mG = *reinterpret_cast<const CUtensorMap *>(M.G);
+    const CUtensorMap &mf = *reinterpret_cast<const CUtensorMap *>(M.f);
+    if (ntiles <= sms * tma_blocks_per_sm<SW, TS, 1>()) {
+        k_sweep_tma<SW, TS, 1><<<ntiles, TS::NT, tma_smem<SW, TS, 1>(), st>>>(L, *in, mG, mf, err);
+    } else {
+        const int grid = std::min(ntiles, sms * tma_blocks_per_sm<SW, TS, 2>());
+        k_sweep_tma<SW, TS, 2><<<grid, TS::NT, tma_smem<SW, TS, 2>(), st>>>(L, *in, mG, mf, err);
+    }
 }
 
 template <typename TS>
