@@ -42,7 +42,7 @@ class Params(C.Structure):
         ("beta_edge", C.c_double), ("sigma_blur", C.c_double), ("sigma_d", C.c_double),
         ("Sigma", C.c_double), ("inv_tau", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
         ("levels", C.c_int), ("smoother", C.c_int), ("coarse_maxit", C.c_int),
-        ("coarse_tol", C.c_double),
+        ("coarse_tol", C.c_double), ("coarse_solver", C.c_int), ("aos_dt", C.c_double),
     ]
 
 
@@ -53,7 +53,8 @@ def params(n=None, m=None, **kw) -> Params:
     sd = 0.05 * max(n or 128, m or n or 128)
     d = dict(model=0, mu=1.0, lambda1=10.0, lambda2=10.0, theta=1.0, nu=1.0, eps=1.0, beta=1e-6,
              beta_edge=1.0, sigma_blur=1.0, sigma_d=sd, Sigma=2.0, inv_tau=1.0, nu1=2,
-             nu2=2, levels=5, smoother=0, coarse_maxit=100, coarse_tol=1e-13)
+             nu2=2, levels=5, smoother=0, coarse_maxit=100, coarse_tol=1e-13, coarse_solver=0,
+             aos_dt=10.0)
     if "tau" in kw:
         t = kw.pop("tau")
         kw["inv_tau"] = 0.0 if t is None or t == float("inf") else 1.0 / t
@@ -94,6 +95,9 @@ def lib():
                 "or_frozen_coeffs": ([D, D, D, D, C.c_int, C.c_int, C.c_double, P, C.c_double, C.c_double, D], None),
                 "or_smooth_given": ([D, C.c_int, C.c_int, C.c_double, C.c_int, D], None),
                 "or_members": ([D, C.c_int, C.c_int, C.c_double, C.c_int, I], None),
+                "or_aos_iteration": ([D, D, D, D, C.c_int, C.c_int, C.c_double, P, C.c_double, C.c_double,
+                                      C.c_double], None),
+                "or_solver_aos": ([C.c_void_p, C.c_double, C.c_int, C.c_double, D], C.c_int),
                 "or_energy": ([D, D, D, D, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P], C.c_double),
                 "or_solver_energy": ([C.c_void_p], C.c_double),
             }
@@ -144,6 +148,20 @@ def initial_phi(n, m, markers, r0=None):
     r0 = 0.05 * max(n, m) if r0 is None else r0
     h = lib().or_initial_phi(n, m, px, py, len(mk), r0, _d(out)[1], _d(area)[1])
     return out, float(area[0]), h
+
+
+def aos_iteration(phi, w, Fn, rhs, h=1.0, p=None, n0m0=None, A1=0.0, dt=1.0):
+    """One AOS iteration of the pseudo-time-step problem L(phi) = rhs (or_aos_iteration)."""
+    phi, _ = _d(phi)
+    out, po = _d(phi.copy())
+    n, m = phi.shape
+    p = p or params(n, m)
+    w, pw = _d(w)
+    Fn, pf = _d(Fn)
+    rhs, pr = _d(rhs) if rhs is not None else (None, None)
+    lib().or_aos_iteration(po, pw, pf, pr, n, m, h, C.byref(p),
+                           float(n * m if n0m0 is None else n0m0), A1, dt)
+    return out
 
 
 def energy(phi, z, w, d, c1, c2, A1, p: Params):
@@ -316,6 +334,13 @@ class Solver:
 
     def set_c(self, c1, c2):
         lib().or_set_c(self._h, c1, c2)
+
+    def aos(self, dt, max_iter, eta):
+        """AOS iterations on the finest grid until the relative change < eta (or_solver_aos).
+        Returns (iterations, rho)."""
+        r = np.zeros(1)
+        it = lib().or_solver_aos(self._h, dt, max_iter, eta, _d(r)[1])
+        return it, float(r[0])
 
     def energy(self) -> float:
         """Energy of the current finest-grid phi with the current c1, c2 (or_solver_energy)."""

@@ -49,8 +49,10 @@ typedef struct {
                              3 = GSLINE-I, even then odd columns;
                              4 = Hybrid Smoother 1, lexicographic (Algorithm 2);
                              5 = Hybrid Smoother 1, parallel ordering */
-    int coarse_maxit;     /* Picard iterations cap of the coarsest solve */
+    int coarse_maxit;     /* Picard iterations cap of the coarsest solve (AOS: its iterations) */
     double coarse_tol;    /* relative nonlinear-residual target of the coarsest solve */
+    int coarse_solver;    /* 0 = Picard + banded Cholesky; 1 = AOS time marching */
+    double aos_dt;        /* AOS artificial time step */
 } or_params;
 
 /* ------------------------------------------------------------------------------------- */
@@ -853,6 +855,76 @@ int or_coarse_solve(double *phi, const double *w, const double *Fn, const double
 }
 
 /* ------------------------------------------------------------------------------------- */
+/* AOS time marching (Algorithm 1, "using e.g. time-marching or AOS"; Sec. 5: 100 AOS      */
+/* iterations on the coarsest grid, and the baseline of Table 6)                          */
+/* ------------------------------------------------------------------------------------- */
+
+/* One AOS iteration (additive operator splitting, Weickert, ter Haar Romeny and Viergever,
+ * 1998) for the artificial evolution d phi / ds = L(phi) - rhs of one pseudo-time step, with
+ * the coefficients frozen at the current phi:
+ *   L(phi) - rhs = A_x phi + A_y phi - phi / tau + c,   c = -(Fn + area + rhs)
+ * where A_x couples each cell to its east / west neighbours (C, D over delta) and A_y to its
+ * south / north neighbours (A, B over delta), and Fn already holds -phi^n / tau.  The reaction
+ * term is split evenly between the two directions and kept implicit:
+ *   phi <- 1/2 sum_l (I (1 + dt / tau) - 2 dt A_l)^{-1} (phi + dt c),
+ * each inverse a set of tridiagonal solves along rows (l = x) or columns (l = y).
+ * Pinned by: consistency with L (the step over dt tends to L(phi) - rhs as dt -> 0, with an
+ * O(dt) error), the closed form of the reaction-only problem (mu = 0), convergence of the
+ * iteration to a fixed point whose residual shrinks with dt. */
+void or_aos_iteration(double *phi, const double *w, const double *Fn, const double *rhs, int n, int m,
+                      double h, const or_params *p, double n0m0, double A1, double dt)
+{
+    size_t N = (size_t)n * m;
+    or_coeffs k;
+    coeffs_alloc(&k, n, m);
+    frozen_coeffs(phi, w, Fn, rhs, n, m, h, p, n0m0, A1, &k);
+    double area = area_term(phi, n, m, h, p, n0m0, A1);
+    double *src = malloc(sizeof(double) * N), *yx = malloc(sizeof(double) * N);
+    int L = n > m ? n : m;
+    double *lo = malloc(sizeof(double) * L), *di = malloc(sizeof(double) * L);
+    double *up = malloc(sizeof(double) * L), *r = malloc(sizeof(double) * L);
+    for (size_t q = 0; q < N; ++q) src[q] = phi[q] - dt * (Fn[q] + area + (rhs ? rhs[q] : 0.0));
+    const double diag0 = 1.0 + dt * p->inv_tau;
+    for (int dir = 0; dir < 2; ++dir) {           /* 0: rows (A_x), 1: columns (A_y) */
+        int nl = dir == 0 ? n : m, len = dir == 0 ? m : n;
+        for (int line = 0; line < nl; ++line) {
+            for (int t = 0; t < len; ++t) {
+                int i = dir == 0 ? line : t, j = dir == 0 ? t : line;
+                size_t q = (size_t)i * m + j;
+                double cp = (dir == 0 ? k.D[q] : k.B[q]) / k.delta[q];   /* previous cell */
+                double cn = (dir == 0 ? k.C[q] : k.A[q]) / k.delta[q];   /* next cell */
+                lo[t] = -2.0 * dt * cp;
+                up[t] = -2.0 * dt * cn;
+                di[t] = diag0 + 2.0 * dt * (cp + cn);
+                r[t] = src[q];
+            }
+            for (int t = 1; t < len; ++t) {
+                double wgt = lo[t] / di[t - 1];
+                di[t] -= wgt * up[t - 1];
+                r[t] -= wgt * r[t - 1];
+            }
+            double x = r[len - 1] / di[len - 1];
+            for (int t = len - 1; t >= 0; --t) {
+                if (t < len - 1) x = (r[t] - up[t] * x) / di[t];
+                int i = dir == 0 ? line : t, j = dir == 0 ? t : line;
+                size_t q = (size_t)i * m + j;
+                if (dir == 0) yx[q] = x;
+                else phi[q] = 0.5 * (yx[q] + x);
+            }
+        }
+    }
+    free(src); free(yx); free(lo); free(di); free(up); free(r);
+    coeffs_free(&k);
+}
+
+/* The coarsest solve by `iters` AOS iterations (the paper's choice: 100). */
+static void or_aos_solve(double *phi, const double *w, const double *Fn, const double *rhs, int n, int m,
+                         double h, const or_params *p, double n0m0, double A1, int iters, double dt)
+{
+    for (int it = 0; it < iters; ++it) or_aos_iteration(phi, w, Fn, rhs, n, m, h, p, n0m0, A1, dt);
+}
+
+/* ------------------------------------------------------------------------------------- */
 /* FAS multigrid (Sec. 3.1, Algorithm 1) and the outer driver (Sec. 5)                    */
 /* ------------------------------------------------------------------------------------- */
 
@@ -909,8 +981,14 @@ static void fas_vcycle(or_solver *s, int l)
 {
     or_level *L = &s->lv[l];
     if (l == s->nlev - 1) {
-        s->picard_last = or_coarse_solve(L->phi, L->w, L->Fn, L->rhs, L->n, L->m, L->h, &s->p,
+if (s->p.coarse_solver == 1) {
+            or_aos_solve(L->phi, L->w, L->Fn, L->rhs, L->n, L->m, L->h, &s->p, s->n0m0, s->A1,
+                         s->p.coarse_maxit, s->p.aos_dt);
+            s->picard_last = s->p.coarse_maxit;
+        } else {
+            s->picard_last = or_coarse_solve(L->phi, L->w, L->Fn, L->rhs, L->n, L->m, L->h, &s->p,
                                          s->n0m0, s->A1);
+        }
         return;
     }
     or_level *Cg = &s->lv[l + 1];
@@ -1036,6 +1114,33 @@ double or_end_step(or_solver *s)
         pn += s->phin[q] * s->phin[q];
     }
     return pn > 0 ? sqrt(dn / pn) : sqrt(dn);
+}
+
+/* AOS on the finest grid for the current pseudo-time step (the AOS method of Table 6): up to
+ * max_iter iterations with step dt until the relative change ||phi^{k+1} - phi^k|| / ||phi^k||
+ * falls below eta.  Returns the iterations run; *rho gets ||L(phi) - rhs|| / ||L(phi^n)||. */
+int or_solver_aos(or_solver *s, double dt, int max_iter, double eta, double *rho)
+{
+    or_level *F = &s->lv[0];
+    size_t N = (size_t)F->n * F->m;
+    double *prev = malloc(sizeof(double) * N);
+    int it = 0;
+    while (it < max_iter) {
+        memcpy(prev, F->phi, sizeof(double) * N);
+        or_aos_iteration(F->phi, F->w, F->Fn, F->rhs, F->n, F->m, F->h, &s->p, s->n0m0, s->A1, dt);
+        ++it;
+        double dn = 0, pn = 0;
+        for (size_t q = 0; q < N; ++q) {
+            dn += (F->phi[q] - prev[q]) * (F->phi[q] - prev[q]);
+            pn += prev[q] * prev[q];
+        }
+        if (sqrt(dn) <= eta * sqrt(pn)) break;
+    }
+    free(prev);
+    residual(s, 0);
+    double r = norm2(F->tmp, N);
+    if (rho) *rho = s->res0 > 0 ? r / s->res0 : r;
+    return it;
 }
 
 /* Energy of a level set on the finest grid (the functionals of Sec. 2.2: eq. scfunc for
