@@ -65,6 +65,8 @@ enum {
     MG_SMOOTH_HS1 = 4
 };
 
+enum { MG_COARSE_PICARD = 0, MG_COARSE_AOS = 1 };   /* coarsest-grid solver */
+
 typedef struct mg_handle_s *mg_handle;
 
 /* Parameters.  Model weights follow Sec. 2.2 (eqs. rcfunc, scfunc); the smoother and cycle
@@ -91,6 +93,9 @@ typedef struct {
     int coarse_maxit;      /* Picard cap of the coarsest solve (>= 1) */
     double coarse_tol;     /* relative residual target of the coarsest solve */
     int use_graph;         /* 1: replay each V-cycle as a captured CUDA graph */
+    int coarse_solver;     /* MG_COARSE_PICARD, or MG_COARSE_AOS: coarse_maxit AOS iterations of
+                              step aos_dt (Algorithm 1 "time-marching or AOS"; Sec. 5 uses 100) */
+    double aos_dt;         /* AOS artificial time step (> 0) */
 } mg_params;
 
 /* Counters and scalars of the current state (mg_get_stats). */
@@ -200,6 +205,16 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
 int mg_autotune(mg_handle h, int reps, int *shapes);
 /* Sets the fused-sweep tile shape of grids 0..levels-2 (values 0..2 as above). */
 int mg_set_tile_shapes(mg_handle h, const int *shapes);
+/* AOS time marching on the finest grid for the current pseudo-time step: the AOS method the
+ * paper compares against in Table 6 (additive operator splitting of d phi / ds = L(phi) - rhs,
+ * coefficients frozen per iteration, the 1/tau term split evenly between rows and columns):
+ *   phi <- 1/2 sum_{l = rows, columns} ((1 + dt/tau) I - 2 dt A_l)^{-1} (phi + dt c).
+ * Runs up to max_iter iterations of step dt (> 0), stopping when the relative change
+ * ||phi^{k+1} - phi^k|| / ||phi^k|| is at most eta (the paper's stopping test).  *iters and
+ * *rho (host, may be NULL) get the iterations run and ||L(phi)|| / ||L(phi^n)||.  Call between
+ * mg_begin_step and mg_end_step; waits.  Errors: MG_ERR_ARG, MG_ERR_STATE, MG_ERR_CUDA. */
+int mg_aos(mg_handle h, double dt, int max_iter, double eta, int *iters, double *rho);
+
 /* Energy of the current level set (Sec. 2.2: eq. scfunc for Spencer-Chen, eq. rcfunc for
  * Rada-Chen; the diagnostic the paper reports after each cycle in Table 7), on the finest grid
  * in pixel units, with the current c1, c2:

@@ -372,10 +372,12 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
         double res;
         if (A.coarse_fp64)
             coarse_solve_block<float, double>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
-                                              reinterpret_cast<double *>(sm + s_off[2]), red, &s_err, &it, &res);
+                                              reinterpret_cast<double *>(sm + s_off[2]), red, &s_err, &it, &res,
+                                              A.coarse_aos, A.aos_dt);
         else
             coarse_solve_block<float, float>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
-                                             reinterpret_cast<float *>(sm + s_off[2]), red, &s_err, &it, &res);
+                                             reinterpret_cast<float *>(sm + s_off[2]), red, &s_err, &it, &res,
+                                             A.coarse_aos, A.aos_dt);
         if (threadIdx.x == 0) {
             A.sc->picard = it;
             A.sc->coarse_res = res;

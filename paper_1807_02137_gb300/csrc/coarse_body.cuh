@@ -237,12 +237,112 @@ __device__ void coarse_solve_team(const CoarseGrid<T> &L, ModelParams mp, double
     TM::sync();
 }
 
+// ---------------------------------------------------------------------------------------
+// The coarsest solve by AOS time marching (Algorithm 1, "using e.g. time-marching or AOS";
+// Sec. 5: 100 iterations on the coarsest grid), `iters` iterations of step dt.  One iteration
+// (additive operator splitting of d phi / ds = L(phi) - rhs, coefficients frozen at phi, the
+// 1/tau term split evenly between rows and columns), in increment form: for l = rows, columns
+//   ((1 + dt/tau) I - 2 dt A_l) y_l = u + dt (2 A_l pn - F - area - rhs),   u <- (y_x + y_y) / 2
+// with A_l the mu/h^2-weighted face-G differences along l (the same step as the FP64 oracle's
+// total-phi form, rewritten for phi = pn + u).  Scratch: 5 N values of C.
+// ---------------------------------------------------------------------------------------
+template <typename T, typename C, int NT>
+__device__ void aos_solve_team(const CoarseGrid<T> &L, ModelParams mp, double A1frac, double h2nm, int iters,
+                               double dt_, C *scratch, double *red) {
+    using TM = Team<NT>;
+    const int n = L.n, m = L.m, p = L.pitch, N = n * m;
+    const int tid = threadIdx.x;
+    C *x = scratch, *G = x + N, *yx = G + N, *dd = yx + N, *rr = dd + N;
+    const C hinv = C(2) * (C)L.inv_2h;
+    const C cdiff = C(mp.mu) * hinv * hinv;
+    const C inv_tau = (C)L.inv_tau, inv_2h = (C)L.inv_2h, beta = (C)L.beta, dt = (C)dt_;
+    auto pn_at = [&](int i, int j) { return (C)L.pn[(size_t)i * p + j]; };
+    for (int q = tid; q < N; q += NT) x[q] = (C)L.u[(size_t)(q / m) * p + (q % m)];
+    TM::sync();
+    for (int it = 0; it < iters; ++it) {
+        C area = C(0);
+        if (mp.model == 1) {
+            double hs = 0.0;
+            for (int q = tid; q < N; q += NT)
+                hs += 0.5 + atan(((double)pn_at(q / m, q % m) + (double)x[q]) / mp.eps) / M_PI;
+            hs = TM::template sum<double>(hs, red);
+            area = (C)(2.0 * mp.nu * (h2nm * hs - A1frac));
+        }
+        for (int q = tid; q < N; q += NT) {
+            const int i = q / m, j = q % m;
+            const int iS = min(i + 1, n - 1), iN = max(i - 1, 0), jE = min(j + 1, m - 1), jW = max(j - 1, 0);
+            const C gy = ((pn_at(iS, j) - pn_at(iN, j)) + (x[iS * m + j] - x[iN * m + j])) * inv_2h;
+            const C gx = ((pn_at(i, jE) - pn_at(i, jW)) + (x[i * m + jE] - x[i * m + jW])) * inv_2h;
+            const C w = L.wb ? C(__bfloat162float(L.wb[(size_t)i * p + j])) : (C)L.w[(size_t)i * p + j];
+            G[q] = w * rsqrt_of<C>(gx * gx + gy * gy + beta);
+        }
+        TM::sync();
+        // rows (dir 0) into yx, then columns (dir 1) into x = (yx + y) / 2
+        for (int dir = 0; dir < 2; ++dir) {
+            const int nl = dir == 0 ? n : m, len = dir == 0 ? m : n, stp = dir == 0 ? 1 : m;
+            for (int line = tid; line < nl; line += NT) {
+                const int q0 = dir == 0 ? line * m : line;
+                C cup = C(0), cdi = C(1), crh = C(0);
+                for (int t = 0; t < len; ++t) {
+                    const int q = q0 + t * stp;
+                    const int i = q / m, j = q % m;
+                    const C cp = t > 0 ? cdiff * C(0.5) * (G[q] + G[q - stp]) : C(0);
+                    const C cn = t + 1 < len ? cdiff * C(0.5) * (G[q] + G[q + stp]) : C(0);
+                    const C pc = pn_at(i, j);
+                    C Apn = C(0);
+                    if (t > 0) Apn += cp * (pn_at((q - stp) / m, (q - stp) % m) - pc);
+                    if (t + 1 < len) Apn += cn * (pn_at((q + stp) / m, (q + stp) % m) - pc);
+                    const size_t o = (size_t)i * p + j;
+                    const C rhs = (L.has_rhs ? (C)L.rhs[o] : C(0));
+                    C di = C(1) + dt * inv_tau + C(2) * dt * (cp + cn);
+                    C r = x[q] + dt * (C(2) * Apn - (C)L.F[o] - area - rhs);
+                    if (t > 0) {
+                        const C wgt = (-C(2) * dt * cp) / cdi;
+                        di -= wgt * cup;
+                        r -= wgt * crh;
+                    }
+                    dd[q] = di;
+                    rr[q] = r;
+                    cup = -C(2) * dt * cn;
+                    cdi = di;
+                    crh = r;
+                }
+                C y = crh / cdi;
+                for (int t = len - 1; t >= 0; --t) {
+                    const int q = q0 + t * stp;
+                    if (t < len - 1) {
+                        const C cn = cdiff * C(0.5) * (G[q] + G[q + stp]);
+                        y = (rr[q] + C(2) * dt * cn * y) / dd[q];
+                    }
+                    if (dir == 0) yx[q] = y;
+                    else x[q] = C(0.5) * (yx[q] + y);
+                }
+            }
+            TM::sync();
+        }
+    }
+    for (int q = tid; q < N; q += NT) L.u[(size_t)(q / m) * p + (q % m)] = (T)x[q];
+    TM::sync();
+}
+
 // The coarsest solve in the arithmetic type C; all threads of the (kCoarseThreads) block call
 // it.  it_out / res_out are valid in thread 0.
 template <typename T, typename C>
 __device__ void coarse_solve_block(const CoarseGrid<T> &L, ModelParams mp, double A1frac, double h2nm,
                                    int maxit, double tol, C *scratch, double *red, int *s_err,
-                                   int *it_out, double *res_out) {
+                                   int *it_out, double *res_out, int aos = 0, double aos_dt = 0.0) {
+    if (aos) {
+        if (threadIdx.x == 0) *s_err = 0;
+        if (L.n * L.m <= kWarpCoarseMax) {
+            if (threadIdx.x < 32) aos_solve_team<T, C, 32>(L, mp, A1frac, h2nm, maxit, aos_dt, scratch, red);
+            __syncthreads();
+        } else {
+            aos_solve_team<T, C, kCoarseThreads>(L, mp, A1frac, h2nm, maxit, aos_dt, scratch, red);
+        }
+        *it_out = maxit;
+        *res_out = 0.0;
+        return;
+    }
     if (L.n * L.m <= kWarpCoarseMax) {
         if (threadIdx.x < 32)
             coarse_solve_team<T, C, 32>(L, mp, A1frac, h2nm, maxit, tol, scratch, red, s_err, it_out, res_out);

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_interp_add(LevelView<T> Lf, LevelView<T
 template <typename T, typename C>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse(LevelView<T> L, ModelParams mp, double A1frac,
                                                            double h2nm, int maxit, double tol, C *scratch,
-                                                           Scalars *sc) {
+                                                           Scalars *sc, int aos, double aos_dt) {
     extern __shared__ __align__(16) unsigned char smem_coarse[];
     if (!scratch) scratch = reinterpret_cast<C *>(smem_coarse);   // small grids: all in shared memory
     __shared__ double red[33];
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(LevelView<T> L, Model
     CoarseGrid<T> g{L.n, L.m, L.pitch, L.pn, L.u, L.w, L.wb, L.F, L.rhs, L.has_rhs, L.inv_2h, L.inv_tau, L.beta};
     int it;
     double res;
-    coarse_solve_block<T, C>(g, mp, A1frac, h2nm, maxit, tol, scratch, red, &s_err, &it, &res);
+    coarse_solve_block<T, C>(g, mp, A1frac, h2nm, maxit, tol, scratch, red, &s_err, &it, &res, aos, aos_dt);
     if (threadIdx.x == 0) {
         sc->picard = it;
         sc->coarse_res = res;
@@ -208,20 +208,21 @@ void prepare_coarse_kernels() {
 
 template <typename T, typename C>
 static void coarse_launch(const LevelView<T> &L, ModelParams mp, double A1frac, double h2nm, int maxit,
-                          double tol, double *scratch, Scalars *sc, cudaStream_t st) {
+                          double tol, double *scratch, Scalars *sc, int aos, double aos_dt, cudaStream_t st) {
     size_t bytes = coarse_scratch_elems(L.n, L.m) * sizeof(C);
     if (bytes <= kCoarseSmemMax)
-        k_coarse<T, C><<<1, kCoarseThreads, bytes, st>>>(L, mp, A1frac, h2nm, maxit, tol, nullptr, sc);
+        k_coarse<T, C><<<1, kCoarseThreads, bytes, st>>>(L, mp, A1frac, h2nm, maxit, tol, nullptr, sc, aos, aos_dt);
     else
-        k_coarse<T, C><<<1, kCoarseThreads, 0, st>>>(L, mp, A1frac, h2nm, maxit, tol, reinterpret_cast<C *>(scratch), sc);
+        k_coarse<T, C><<<1, kCoarseThreads, 0, st>>>(L, mp, A1frac, h2nm, maxit, tol, reinterpret_cast<C *>(scratch),
+                                                     sc, aos, aos_dt);
 }
 
 template <typename T>
 void launch_coarse_solve(const LevelView<T> &L, int fp64, ModelParams mp, double A1frac,
                          double h2nm, int maxit, double tol, double *scratch, Scalars *sc,
-                         cudaStream_t st) {
-    if (sizeof(T) == 8 || fp64) coarse_launch<T, double>(L, mp, A1frac, h2nm, maxit, tol, scratch, sc, st);
-    else coarse_launch<T, float>(L, mp, A1frac, h2nm, maxit, tol, scratch, sc, st);
+                         int aos, double aos_dt, cudaStream_t st) {
+    if (sizeof(T) == 8 || fp64) coarse_launch<T, double>(L, mp, A1frac, h2nm, maxit, tol, scratch, sc, aos, aos_dt, st);
+    else coarse_launch<T, float>(L, mp, A1frac, h2nm, maxit, tol, scratch, sc, aos, aos_dt, st);
 }
 
 #define INST(T)                                                                                    \
@@ -230,7 +231,8 @@ void launch_coarse_solve(const LevelView<T> &L, int fp64, ModelParams mp, double
     template void launch_restrict<T>(const T *, int, int, int, T *, T *, int, cudaStream_t);       \
     template void launch_interp_add<T>(const LevelView<T> &, const LevelView<T> &, cudaStream_t);  \
     template void launch_coarse_solve<T>(const LevelView<T> &, int, ModelParams, double,            \
-                                         double, int, double, double *, Scalars *, cudaStream_t);
+                                         double, int, double, double *, Scalars *, int, double,     \
+                                         cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -107,6 +107,7 @@ struct SolverBase {
     virtual int set_shapes(const int *shapes) = 0;
     virtual int set_bottom(int enable) = 0;
     virtual int energy(double *E) = 0;
+    virtual int aos(double dt, int max_iter, double eta, int *iters, double *rho) = 0;
 };
 
 template <typename T>
@@ -272,6 +273,35 @@ struct Solver final : SolverBase {
         return lb;
     }
 
+    int aos(double dt, int max_iter, double eta_stop, int *iters, double *rhoout) override {
+        if (!in_step) return fail(MG_ERR_STATE, "mg_aos outside a step");
+        if (!(dt > 0) || max_iter < 1) return fail(MG_ERR_ARG, "dt <= 0 or max_iter < 1");
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        int it = 0;
+        while (it < max_iter) {
+            area_term(0, lv[0].u);
+            launch_snapshot<T>(view(0), area_ptr(), st);
+            launch_aos_iteration<T>(view(0), area_ptr(), dt, partials, dsc->aos, st);
+            launches += area_launches() + 4;
+            ++it;
+            CKL();
+            double s2[2];
+            CK(cudaMemcpyAsync(s2, dsc->aos, sizeof(s2), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (!std::isfinite(s2[0])) return fail(MG_ERR_NAN, "non-finite AOS iterate");
+            if (std::sqrt(s2[0]) <= eta_stop * std::sqrt(s2[1])) break;
+        }
+        area_term(0, lv[0].u);
+        launch_residual<T>(view(0), lv[0].u, area_ptr(), lv[0].r, 0, partials, npart, &dsc->norm2, st);
+        launches += area_launches() + 2;
+        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        rho = res0 > 0 ? std::sqrt(hsc->norm2) / res0 : std::sqrt(hsc->norm2);
+        if (iters) *iters = it;
+        if (rhoout) *rhoout = rho;
+        return MG_OK;
+    }
+
     int energy(double *E) override {
         launch_energy<T>(view(0), mp, partials, npart, dsc, &dsc->sums[7], st);
         ++launches;
@@ -286,6 +316,8 @@ struct Solver final : SolverBase {
             BottomArgs a{};
             a.lb = lb; a.L = nlev; a.nu1 = p.nu1; a.nu2 = p.nu2;
             a.coarse_fp64 = p.precision == MG_MIXED;
+            a.coarse_aos = p.coarse_solver == MG_COARSE_AOS;
+            a.aos_dt = p.aos_dt;
             for (int l = lb; l < nlev; ++l) a.g[l] = view(l);
             a.mp = mp;
             a.A1frac = A1 / ((double)n * m);
@@ -446,7 +478,8 @@ struct Solver final : SolverBase {
         }
         if (l == nlev - 1) {
             launch_coarse_solve<T>(view(l), p.precision == MG_MIXED, mp, A1 / ((double)n * m), h2nm(l),
-                                   p.coarse_maxit, p.coarse_tol, coarse, dsc, st);
+                                   p.coarse_maxit, p.coarse_tol, coarse, dsc, p.coarse_solver == MG_COARSE_AOS,
+                                   p.aos_dt, st);
             ++launches;
             return;
         }
@@ -687,6 +720,8 @@ int check_params(const mg_params *p, int n, int m) {
     if (p->precision != MG_F32 && p->precision != MG_F64 && p->precision != MG_MIXED)
         return fail(MG_ERR_ARG, "precision");
     if (p->smoother < MG_SMOOTH_FUSED || p->smoother > MG_SMOOTH_HS1) return fail(MG_ERR_ARG, "smoother");
+    if (p->coarse_solver != MG_COARSE_PICARD && p->coarse_solver != MG_COARSE_AOS) return fail(MG_ERR_ARG, "coarse_solver");
+    if (p->coarse_solver == MG_COARSE_AOS && !(p->aos_dt > 0)) return fail(MG_ERR_ARG, "aos_dt <= 0");
     const double pos[] = {p->mu, p->eps, p->beta, p->sigma_blur, p->sigma_d};
     for (double v : pos)
         if (!(v > 0) || !std::isfinite(v)) return fail(MG_ERR_ARG, "mu, eps, beta, sigma_blur, sigma_d must be > 0");
@@ -893,6 +928,7 @@ int mg_default_params(mg_params *p, int n, int m) {
     p->levels = lev;
     p->precision = MG_F32; p->smoother = MG_SMOOTH_FUSED;
     p->coarse_maxit = 100; p->coarse_tol = 1e-13; p->use_graph = 1;
+    p->coarse_solver = MG_COARSE_PICARD; p->aos_dt = 10.0;
     return MG_OK;
 }
 
@@ -1042,6 +1078,11 @@ int mg_autotune(mg_handle h, int reps, int *shapes) {
 int mg_set_tile_shapes(mg_handle h, const int *shapes) {
     if (!h || !shapes) return fail(MG_ERR_ARG, "NULL argument");
     return h->s->set_shapes(shapes);
+}
+
+int mg_aos(mg_handle h, double dt, int max_iter, double eta, int *iters, double *rho) {
+    if (!h) return fail(MG_ERR_ARG, "NULL handle");
+    return h->s->aos(dt, max_iter, eta, iters, rho);
 }
 
 int mg_energy(mg_handle h, double *E) {

@@ -54,6 +54,7 @@ struct Scalars {
     double norm2_0;          // sum r^2 of L(phi^n)
     double sums[8];          // sum H z, sum H, sum (1-H) z, sum (1-H), sum u^2, sum phi_n^2
     double coarse_res;       // last coarsest nonlinear residual
+    double aos[2];           // AOS on the finest grid: sum (u_new - u)^2, sum (pn + u)^2
     int picard;              // Picard iterations of the last coarsest solve
     int err;                 // 1 = non-positive Cholesky pivot
 };
@@ -149,7 +150,11 @@ void launch_interp_add(const LevelView<T> &Lf, const LevelView<T> &Lc, cudaStrea
 template <typename T>
 void launch_coarse_solve(const LevelView<T> &L, int fp64, ModelParams mp, double A1frac,
                          double h2_over_nm, int maxit, double tol, double *scratch, Scalars *sc,
-                         cudaStream_t st);   // fp64: FP64 arithmetic for FP32 storage
+                         int aos, double aos_dt, cudaStream_t st);   // fp64: FP64 arithmetic for FP32
+                                                                    // storage; aos: AOS iterations
+template <typename T>
+void launch_aos_iteration(const LevelView<T> &L, const double *area, double dt, double *partials, double *sums,
+                          cudaStream_t st);
 void prepare_coarse_kernels();
 
 // Scratch elements (of the storage type) of the coarsest solve on an n x m grid.
@@ -162,6 +167,8 @@ __host__ __device__ inline size_t coarse_scratch_elems(int n, int m) {
 struct BottomArgs {
     int lb, L, nu1, nu2;
     int coarse_fp64;   // the coarsest solve in FP64 arithmetic (mixed precision) or FP32
+    int coarse_aos;    // the coarsest solve by AOS iterations (step aos_dt)
+    double aos_dt;
     LevelView<float> g[kMaxLevels];
     ModelParams mp;
     double A1frac, h2nm_coarse, coarse_tol;

@@ -17,12 +17,13 @@ from . import buildlib as _build
 MG_F32, MG_F64, MG_MIXED = 0, 1, 2
 MG_MODEL_SC, MG_MODEL_RC = 0, 1
 MG_SMOOTH_FUSED, MG_SMOOTH_PHASED, MG_SMOOTH_FUSED_VEC, MG_SMOOTH_GSLINE, MG_SMOOTH_HS1 = 0, 1, 2, 3, 4
+MG_COARSE_PICARD, MG_COARSE_AOS = 0, 1
 ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4: "MG_ERR_DIVERGED",
           -5: "MG_ERR_TIMEOUT", -6: "MG_ERR_NOT_SPD", -7: "MG_ERR_NOMEM", -8: "MG_ERR_STATE"}
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
            "mg_get_level", "mg_get_stats", "mg_segment_host", "mg_get_stream", "mg_destroy",
-           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_energy",
+           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_energy", "mg_aos",
            "mg_batch_setup", "mg_batch_solve_step", "mg_batch_autotune", "mg_batch_handle",
            "mg_batch_destroy"]
 
@@ -37,6 +38,7 @@ class Params(C.Structure):
         ("Sigma", C.c_double), ("tau", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
         ("levels", C.c_int), ("precision", C.c_int), ("smoother", C.c_int),
         ("coarse_maxit", C.c_int), ("coarse_tol", C.c_double), ("use_graph", C.c_int),
+        ("coarse_solver", C.c_int), ("aos_dt", C.c_double),
     ]
 
 
@@ -97,6 +99,7 @@ def lib():
             "mg_set_tile_shapes": ([vp, C.POINTER(i)], i),
             "mg_set_bottom_kernel": ([vp, i, C.POINTER(i)], i),
             "mg_energy": ([vp, C.POINTER(C.c_double)], i),
+            "mg_aos": ([vp, C.c_double, i, C.c_double, C.POINTER(i), C.POINTER(C.c_double)], i),
             "mg_batch_setup": ([C.POINTER(vp), i, C.POINTER(vp), C.POINTER(i), C.POINTER(i),
                                 C.POINTER(D), C.POINTER(i), P, vp], i),
             "mg_batch_solve_step": ([vp, d, i, C.POINTER(i), D], i),
@@ -264,6 +267,12 @@ class Solver:
     def set_tile_shapes(self, shapes):
         arr = (C.c_int * 16)(*shapes)
         _check(lib().mg_set_tile_shapes(self._h, arr), "mg_set_tile_shapes")
+
+    def aos(self, dt, max_iter, eta):
+        """AOS time marching on the finest grid (mg_aos); returns (iterations, rho)."""
+        it, r = C.c_int(), C.c_double()
+        _check(lib().mg_aos(self._h, dt, max_iter, eta, C.byref(it), C.byref(r)), "mg_aos")
+        return it.value, r.value
 
     def energy(self) -> float:
         """Level-set energy of the current phi with the current c1, c2 (mg_energy)."""

@@ -27,7 +27,7 @@ def oracle_params(n, m, gp):
                     sigma_blur=gp.sigma_blur, sigma_d=gp.sigma_d, Sigma=gp.Sigma,
                     inv_tau=(1.0 / gp.tau if gp.tau > 0 else 0.0), nu1=gp.nu1, nu2=gp.nu2,
                     levels=gp.levels, smoother=ORACLE_SMOOTHER[gp.smoother], coarse_maxit=gp.coarse_maxit,
-                    coarse_tol=gp.coarse_tol)
+                    coarse_tol=gp.coarse_tol, coarse_solver=gp.coarse_solver, aos_dt=gp.aos_dt)
 
 
 def gpu_solver(segmg, image, markers, **kw):

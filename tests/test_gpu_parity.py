@@ -355,3 +355,46 @@ def test_gsline_and_hybrid_smoother_1_match_oracle(segmg, smoother):
     pg, po = s32.phi().cpu().numpy(), o2.phi
     assert relmax(pg, po) < 1e-5
     assert np.mean((pg > 0) != (po > 0)) <= 1e-4
+
+
+def test_aos_coarsest_solver_matches_oracle(segmg):
+    # V-cycles whose coarsest solve is 100 AOS iterations (Sec. 5), FP64 against the oracle
+    img, mk, _ = synth.ellipses(160, 144, 6, (20, 70), 5, 0.05, 27)
+    s, o, p = both(segmg, img, mk, precision=segmg.MG_F64, levels=5, coarse_solver=segmg.MG_COARSE_AOS,
+                   aos_dt=10.0)
+    s.begin_step(); o.begin_step()
+    for _ in range(3):
+        rg, ro = s.vcycle(), o.vcycle()
+        assert abs(rg - ro) <= 1e-8 * ro
+    assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-10
+    # FP32: the one-block bottom kernel runs the same AOS coarsest solve (bitwise)
+    outs = []
+    for on in (1, 0):
+        s32, _ = gpu_solver(segmg, img, mk, precision=segmg.MG_F32, levels=5,
+                            coarse_solver=segmg.MG_COARSE_AOS, aos_dt=10.0)
+        s32.set_bottom_kernel(bool(on))
+        c, r = s32.solve_step(1e-6, 60)
+        assert r <= 1e-6
+        outs.append(s32.phi().cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_finest_grid_aos_matches_oracle(segmg, model):
+    # the AOS method of Table 6 on the finest grid, FP64 and FP32
+    img, mk, _ = synth.ellipses(120, 136, 5, (20, 60), 5, 0.05, 29)
+    for prec, tol in ((segmg.MG_F64, 1e-10), (segmg.MG_F32, 1e-5)):
+        s, o, p = both(segmg, img.astype(np.float32) if prec == segmg.MG_F32 else img, mk,
+                       precision=prec, levels=4, model=model)
+        s.begin_step(); o.begin_step()
+        ig, rg = s.aos(0.5, 12, 0.0)
+        io, ro = o.aos(0.5, 12, 0.0)
+        assert ig == io == 12
+        assert abs(rg - ro) <= 100 * tol * ro
+        assert relmax(s.phi().cpu().numpy(), o.phi) < tol
+        # the relative-change stop ends both at the same iteration
+        s.begin_step(); o.begin_step()
+        ig, _ = s.aos(0.5, 200, 1e-4)
+        io, _ = o.aos(0.5, 200, 1e-4)
+        assert abs(ig - io) <= (0 if prec == segmg.MG_F64 else 1)
+        s.close()
