@@ -262,9 +262,12 @@ def run_ours(args):
     sweep_ms = float(np.mean(kt[1:5]))
     bytes_per_cell = 16.125        # u, G, f (4 B each) + member masks (1/8 B) read, u (4 B) written
     achieved = bytes_per_cell * n * m / (sweep_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_sweep (fused Hybrid Smoother 2 sweep, finest grid)",
+    # DRAM bytes of one finest-grid sweep launch from an ncu capture of this kernel on this grid
+    # (profiles/k_sweep_tma_traffic_ellipse1024.txt): u, G, f read once, u written to L2
+    traffic = 12.74e6
+    roof = {"bound": "hbm", "kernel": "k_sweep_tma (TMA-staged fused Hybrid Smoother 2 sweep, finest grid)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
+            "traffic": traffic, "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
             "bytes_per_cell": bytes_per_cell, "ms_per_launch": sweep_ms,
             "note": "1024^2 working set is L2-resident inside a step; see roofline_hbm for 8192^2"}
     roof_big = None
