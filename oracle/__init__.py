@@ -98,6 +98,8 @@ def lib():
                 "or_aos_iteration": ([D, D, D, D, C.c_int, C.c_int, C.c_double, P, C.c_double, C.c_double,
                                       C.c_double], None),
                 "or_solver_aos": ([C.c_void_p, C.c_double, C.c_int, C.c_double, D], C.c_int),
+                "or_set_omega": ([C.c_void_p, C.c_int, D], None),
+                "or_smooth_given_omega": ([D, D, C.c_int, C.c_int, C.c_double, C.c_int, D], None),
                 "or_energy": ([D, D, D, D, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P], C.c_double),
                 "or_solver_energy": ([C.c_void_p], C.c_double),
             }
@@ -246,6 +248,17 @@ def smooth_given(coef, phi, Sigma=2.0, kind=0):
     return out
 
 
+def smooth_given_omega(coef, omega, phi, Sigma=2.0, kind=0):
+    """smooth_given with per-cell relaxation weights of the point updates."""
+    if isinstance(coef, dict):
+        coef = np.stack([coef[k] for k in "A B C D S f".split()])
+    coef, pc = _d(coef)
+    om, po_ = _d(omega)
+    out, po = _d(np.array(phi, dtype=np.float64, copy=True))
+    lib().or_smooth_given_omega(pc, po_, phi.shape[0], phi.shape[1], Sigma, kind, po)
+    return out
+
+
 def members(coef, Sigma=2.0, piece=32):
     """Member flags (4, n, m) of the four sweeps; piece <= 0 means whole lines."""
     if isinstance(coef, dict):
@@ -341,6 +354,14 @@ class Solver:
         r = np.zeros(1)
         it = lib().or_solver_aos(self._h, dt, max_iter, eta, _d(r)[1])
         return it, float(r[0])
+
+    def set_omega(self, l, omega):
+        """Relaxation weights of the point updates on grid l (None: plain smoother)."""
+        if omega is None:
+            lib().or_set_omega(self._h, l, None)
+        else:
+            w, pw = _d(omega)
+            lib().or_set_omega(self._h, l, pw)
 
     def energy(self) -> float:
         """Energy of the current finest-grid phi with the current c1, c2 (or_solver_energy)."""

@@ -338,6 +338,7 @@ static double grad_norm(const double *phi, int n, int m, double h, double beta, 
 typedef struct {
     int n, m;
     double *A, *B, *C, *D, *S, *f, *delta;
+    const double *omega;   /* per-cell relaxation weights of the point updates (NULL = 1) */
 } or_coeffs;
 
 static void coeffs_alloc(or_coeffs *k, int n, int m)
@@ -348,6 +349,7 @@ static void coeffs_alloc(or_coeffs *k, int n, int m)
     k->C = calloc(N, sizeof(double)); k->D = calloc(N, sizeof(double));
     k->S = calloc(N, sizeof(double)); k->f = calloc(N, sizeof(double));
     k->delta = calloc(N, sizeof(double));
+    k->omega = NULL;
 }
 static void coeffs_free(or_coeffs *k)
 {
@@ -596,8 +598,12 @@ static void hs2_parallel(const or_coeffs *k, double Sigma, double *phi)
             int colour = rev ? 1 - c : c;
             for (int i = 0; i < n; ++i)
                 for (int j = 0; j < m; ++j)
-                    if ((i + j) % 2 == colour && !member[(size_t)i * m + j])
-                        phi[(size_t)i * m + j] = point_update(k, phi, i, j);
+                    if ((i + j) % 2 == colour && !member[(size_t)i * m + j]) {
+                        size_t q = (size_t)i * m + j;
+                        double g = point_update(k, phi, i, j);
+                        /* relaxation weight (SURVEY NEXT-2 reading): phi += omega (g - phi) */
+                        phi[q] = k->omega ? phi[q] + k->omega[q] * (g - phi[q]) : g;
+                    }
         }
         int nl = rowwise ? n : m, len = rowwise ? m : n;
         for (int c = 0; c < 2; ++c) {
@@ -932,6 +938,7 @@ typedef struct {
     int n, m;
     double h;
     double *phi, *phi0, *rhs, *w, *z, *d, *Fn, *tmp;
+    double *omega;          /* relaxation weights of the point updates on this grid (NULL = 1) */
 } or_level;
 
 typedef struct {
@@ -964,6 +971,7 @@ static void smooth(or_solver *s, int l)
     or_coeffs k;
     coeffs_alloc(&k, L->n, L->m);
     frozen_coeffs(L->phi, L->w, L->Fn, L->rhs, L->n, L->m, L->h, &s->p, s->n0m0, s->A1, &k);
+    k.omega = L->omega;
     run_smoother(&k, s->p.Sigma, s->p.smoother, L->phi);
     coeffs_free(&k);
 }
@@ -1062,7 +1070,7 @@ void or_destroy(or_solver *s)
     for (int l = 0; l < s->nlev; ++l) {
         or_level *L = &s->lv[l];
         free(L->phi); free(L->phi0); free(L->rhs); free(L->w); free(L->z); free(L->d);
-        free(L->Fn); free(L->tmp);
+        free(L->Fn); free(L->tmp); free(L->omega);
     }
     free(s->lv); free(s->phin); free(s);
 }
@@ -1208,6 +1216,17 @@ void or_get_scalars(const or_solver *s, double *out /* c1, c2, A1, res0, picard_
 }
 void or_set_c(or_solver *s, double c1, double c2) { s->c1 = c1; s->c2 = c2; }
 
+/* Per-cell relaxation weights of the point updates of the parallel Hybrid Smoother 2 on grid l
+ * (NULL: back to 1).  Used with learned weights. */
+void or_set_omega(or_solver *s, int l, const double *w)
+{
+    or_level *L = &s->lv[l];
+    size_t N = (size_t)L->n * L->m;
+    if (!w) { free(L->omega); L->omega = NULL; return; }
+    if (!L->omega) L->omega = malloc(sizeof(double) * N);
+    memcpy(L->omega, w, sizeof(double) * N);
+}
+
 /* Frozen coefficients of an arbitrary grid function, for the tests (A, B, C, D, S, f, delta
  * each n*m, in that order in out). */
 void or_frozen_coeffs(const double *phi, const double *w, const double *Fn, const double *rhs,
@@ -1234,6 +1253,21 @@ void or_smooth_given(const double *coef, int n, int m, double Sigma, int kind, d
     k.A = (double *)coef; k.B = (double *)coef + N; k.C = (double *)coef + 2 * N;
     k.D = (double *)coef + 3 * N; k.S = (double *)coef + 4 * N; k.f = (double *)coef + 5 * N;
     k.delta = NULL;
+    k.omega = NULL;
+    run_smoother(&k, Sigma, kind, phi);
+}
+
+/* As or_smooth_given, with per-cell relaxation weights of the point updates. */
+void or_smooth_given_omega(const double *coef, const double *omega, int n, int m, double Sigma, int kind,
+                           double *phi)
+{
+    size_t N = (size_t)n * m;
+    or_coeffs k;
+    k.n = n; k.m = m;
+    k.A = (double *)coef; k.B = (double *)coef + N; k.C = (double *)coef + 2 * N;
+    k.D = (double *)coef + 3 * N; k.S = (double *)coef + 4 * N; k.f = (double *)coef + 5 * N;
+    k.delta = NULL;
+    k.omega = omega;
     run_smoother(&k, Sigma, kind, phi);
 }
 
@@ -1244,7 +1278,7 @@ void or_members(const double *coef, int n, int m, double Sigma, int piece, int *
     or_coeffs k;
     k.n = n; k.m = m;
     k.A = (double *)coef; k.B = (double *)coef + N; k.C = (double *)coef + 2 * N;
-    k.D = (double *)coef + 3 * N; k.S = NULL; k.f = NULL; k.delta = NULL;
+    k.D = (double *)coef + 3 * N; k.S = NULL; k.f = NULL; k.delta = NULL; k.omega = NULL;
     int *star = malloc(sizeof(int) * N);
     for (int sweep = 0; sweep < 4; ++sweep) {
         star_flags(&k, Sigma, sweep, star);
