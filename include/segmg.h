@@ -112,6 +112,8 @@ typedef struct {
     double A1;             /* area of the initial polygon (px^2) */
     size_t device_bytes;   /* device memory held by the handle */
     long long launches;    /* kernels launched by the handle so far (graph nodes included) */
+    long long learned_accepted;   /* V-cycles run with learned relaxation weights and kept */
+    long long learned_rejected;   /* ... and rejected (rerun with the plain smoother) */
 } mg_stats;
 
 /* Optional device allocator (for example a framework's caching allocator).  alloc returns a
@@ -183,7 +185,8 @@ int mg_set_regions(mg_handle h, double c1, double c2);
 
 /* Copies one internal field of grid `level` (device, n_l*m_l elements of the precision's type;
  * n_l = n >> level): field 0 = phi, 1 = w, 2 = z, 3 = d, 4 = F (fitting field of the step),
- * 5 = FAS right-hand side.  For tests and diagnostics. */
+ * 5 = FAS right-hand side, 6 = G of the last coefficient snapshot, 7 = the relaxation weights
+ * (mg_set_learned / mg_set_omega).  For tests and diagnostics. */
 int mg_get_level(mg_handle h, int level, int field, void *out);
 
 int mg_get_stats(mg_handle h, mg_stats *s);
@@ -214,6 +217,53 @@ int mg_set_tile_shapes(mg_handle h, const int *shapes);
  * *rho (host, may be NULL) get the iterations run and ||L(phi)|| / ||L(phi^n)||.  Call between
  * mg_begin_step and mg_end_step; waits.  Errors: MG_ERR_ARG, MG_ERR_STATE, MG_ERR_CUDA. */
 int mg_aos(mg_handle h, double dt, int max_iter, double eta, int *iters, double *rho);
+
+/* Learned relaxation weights (an extension in the spirit of Sec. 4, which designs the smoother
+ * cell by cell from the local coefficients).  Every non-member point update of Hybrid Smoother 2
+ * becomes phi += omega (g - phi), with omega = 2 sigmoid(z) in (0, 2) and z from a network of
+ * three 3x3 convolutions.  The network is 5 -> 16 (ReLU) -> 16 (ReLU) -> 1 channels with zero
+ * padding at the grid boundary.  Its input per cell is its four face values of G (S, N, E, W;
+ * zero on a boundary face) divided by their sum, and log(max / min of the existing faces) / 8.
+ * Inference stores weights and activations in BF16 and accumulates in FP32.  The weights apply
+ * on the grids the per-grid kernels smooth; the one-block bottom kernel smooths without them.
+ *   theta    host, mg_learned_nparam() floats (3201): W1 (16,5,3,3), b1 (16), W2 (16,16,3,3),
+ *            b2 (16), W3 (1,16,3,3), b3; NULL keeps the current parameters;
+ *   mode     0 off; 1 every V-cycle after the first of a step runs with the weights and is kept
+ *            only if its residual falls at least as fast as the last plain V-cycle's, else the
+ *            state is restored and the V-cycle rerun plain; 2 always with the weights;
+ *   refresh  V-cycles between two inferences (>= 1); the weights are computed from the first
+ *            snapshot of each grid in a V-cycle that infers.
+ * Requires MG_SMOOTH_FUSED or MG_SMOOTH_FUSED_VEC.  Errors: MG_ERR_ARG, MG_ERR_NOMEM. */
+int mg_set_learned(mg_handle h, const float *theta, int mode, int refresh);
+int mg_learned_nparam(void);
+/* Fixed relaxation weights of grid `level` (host, n_l x m_l values of the storage type, row
+ * major), used by every following V-cycle; NULL switches them off.  Grids the bottom kernel
+ * smooths are refused (MG_ERR_ARG). */
+int mg_set_omega(mg_handle h, int level, const void *omega);
+
+/* Training of the learned weights on crops of 24 x 24 cells recorded from solves.  A crop record
+ * holds 7 planes of 24 x 24 floats: the row-scaled coefficients c_S, c_N, c_E, c_W
+ * (mu/h^2 times the face values of G), the snapshot right-hand side f, the increment u, and in
+ * the last plane [0] = 1/tau, [1] = (i0 + j0) mod 2 of the crop origin.  Loss of a crop: one
+ * red and one black weighted point update on the cells at least one cell inside, then 1/2 the
+ * mean of r^2 = (f - (sum_X c_X u_X - S u))^2 over the cells at least two inside,
+ * S = sum_X c_X + 1/tau.  Gradients by reverse mode in FP32; Adam (lr, 0.9, 0.999, 1e-8). */
+typedef struct mg_trainer_s *mg_trainer;
+/* capacity crops, batches of at most batch_max; theta0 host (NULL: He-normal hidden layers
+ * from `seed`, zero output layer: omega = 1, the plain smoother). */
+int mg_trainer_create(mg_trainer *out, int capacity, int batch_max, unsigned long long seed, const float *theta0);
+/* Appends `count` crops of h's finest grid at seeded random origins (the current increment and
+ * the last snapshot's coefficients and f); stops at capacity.  Waits. */
+int mg_trainer_record(mg_trainer t, mg_handle h, int count);
+/* Appends `count` crop records from host memory. */
+int mg_trainer_load(mg_trainer t, const float *records, int count);
+int mg_trainer_count(mg_trainer t);
+/* Mean loss and gradient over the crops idx[0..batch-1] (host) without a step. */
+int mg_trainer_grad(mg_trainer t, const int *idx, int batch, float *grad, double *loss);
+/* `iters` Adam steps on random batches; *loss gets the last batch's mean loss.  Waits. */
+int mg_trainer_train(mg_trainer t, int iters, int batch, double lr, double *loss);
+int mg_trainer_get(mg_trainer t, float *theta);
+void mg_trainer_destroy(mg_trainer t);
 
 /* Energy of the current level set (Sec. 2.2: eq. scfunc for Spencer-Chen, eq. rcfunc for
  * Rada-Chen; the diagnostic the paper reports after each cycle in Table 7), on the finest grid

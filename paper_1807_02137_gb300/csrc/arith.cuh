@@ -69,6 +69,12 @@ __device__ __forceinline__ T point_relax(T cdiff, T inv_tau, T aS, T aN, T aE, T
     return div_relax(fma_rn(cdiff, num, -f), fma_rn(cdiff, den, inv_tau));
 }
 
+// A point update with a relaxation weight: u_old + omega (g - u_old).
+template <typename T>
+__device__ __forceinline__ T relax_weighted(T omega, T g, T u_old) {
+    return fma_rn(omega, sub_rn(g, u_old), u_old);
+}
+
 // One cell of a partial-line run: face values along the line (previous / next cell) and across
 // it (two sides), the two across-line neighbour values and f.
 template <typename T>

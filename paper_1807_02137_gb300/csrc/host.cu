@@ -5,6 +5,7 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <random>
 #include <vector>
 
 #include "../../include/segmg.h"
@@ -108,6 +109,9 @@ struct SolverBase {
     virtual int set_bottom(int enable) = 0;
     virtual int energy(double *E) = 0;
     virtual int aos(double dt, int max_iter, double eta, int *iters, double *rho) = 0;
+    virtual int set_learned(const float *theta, int mode, int refresh) = 0;
+    virtual int set_omega(int l, const void *w) = 0;
+    virtual int record_crops(float *data, int first, int count, unsigned long long seed) = 0;
 };
 
 template <typename T>
@@ -148,15 +152,40 @@ struct Solver final : SolverBase {
     long long launches = 0, graph_nodes = 0;
     int shape[kMaxLevels] = {};   // fused-sweep tile shape per grid (mg_autotune)
     int lb = -1;                  // first grid of the one-block bottom kernel (-1: not used)
+    // learned relaxation weights of the point updates (learned.cu)
+    int learn_mode = 0;           // 0 off; 1 per V-cycle acceptance; 2 always; 3 fixed weights
+    int learn_refresh = 4;        // V-cycles between inferences
+    int learn_since = 0;          // V-cycles since the last inference
+    bool use_omega = false;       // view() hands out the weight grids
+    bool infer_pending[kMaxLevels] = {};
+    __nv_bfloat16 *net = nullptr; // BF16 parameters
+    T *omega_buf[kMaxLevels] = {};
+    bool omega_valid[kMaxLevels] = {};   // the grid's weights are set (fixed) or inferred
+    T *ubak = nullptr;            // finest-grid increment saved before a learned V-cycle
+    cudaGraphExec_t gexec_l = nullptr, gexec_li = nullptr;   // learned V-cycle; with inference
+    long long nodes_l = 0, nodes_li = 0;
+    double plain_rate = -1.0;     // contraction of the last plain V-cycle of the step
+    long long learned_acc = 0, learned_rej = 0;
     size_t lb_smem = 0;
     ModelParams mp{};
 
     ~Solver() override { release(); }
 
+    void drop_graphs() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (gexec_l) cudaGraphExecDestroy(gexec_l);
+        if (gexec_li) cudaGraphExecDestroy(gexec_li);
+        gexec = gexec_l = gexec_li = nullptr;
+    }
+
     void release() {
         if (st) cudaStreamSynchronize(st);
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
+        drop_graphs();
+        for (auto &b : omega_buf) { if (b) cudaFree(b); b = nullptr; }
+        if (ubak) cudaFree(ubak);
+        if (net) cudaFree(net);
+        ubak = nullptr;
+        net = nullptr;
         if (pool) {
             if (use_al) al.free(pool, pool_bytes, st, al.ctx);
             else cudaFreeAsync(pool, st);
@@ -185,6 +214,7 @@ struct Solver final : SolverBase {
         v.mrow = L.mrow; v.mcol = L.mcol; v.npm = (L.m + 31) / 32; v.npn = (L.n + 31) / 32;
         v.wb = L.wb;
         v.cls = L.cls;
+        v.omega = use_omega && omega_valid[l] ? omega_buf[l] : nullptr;
         v.has_rhs = l > 0 ? 1 : 0;
         return v;
     }
@@ -269,14 +299,14 @@ struct Solver final : SolverBase {
                 lb_smem = b;
             }
         }
-        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        drop_graphs();
         return lb;
     }
 
     int aos(double dt, int max_iter, double eta_stop, int *iters, double *rhoout) override {
         if (!in_step) return fail(MG_ERR_STATE, "mg_aos outside a step");
         if (!(dt > 0) || max_iter < 1) return fail(MG_ERR_ARG, "dt <= 0 or max_iter < 1");
-        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        drop_graphs();
         int it = 0;
         while (it < max_iter) {
             area_term(0, lv[0].u);
@@ -331,7 +361,7 @@ struct Solver final : SolverBase {
 
     int reset(const void *image, const double *mk, int k) override {
         if (k > kcap) return fail(MG_ERR_ARG, "more markers than at set-up");
-        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }   // A1 is baked into the graph
+        drop_graphs();   // A1 is baked into the graphs
         in_step = false;
         steps = cycles_step = cycles_total = 0;
         rho = eta = res0 = 0;
@@ -416,6 +446,9 @@ struct Solver final : SolverBase {
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         res0 = std::sqrt(hsc->norm2_0);
+        rho = 1.0;
+        plain_rate = -1.0;
+        learn_since = 0;
         // the last residual norm starts at the reference one (rho = 1 until a V-cycle runs)
         CK(cudaMemcpyAsync(&dsc->norm2, &dsc->norm2_0, sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (!std::isfinite(res0)) return fail(MG_ERR_NAN, "non-finite initial residual");
@@ -466,6 +499,11 @@ struct Solver final : SolverBase {
         area_term(l, lv[l].u);
         LevelView<T> v = view(l);
         launch_snapshot<T>(v, area_ptr(), st);
+        if (use_omega && infer_pending[l] && omega_buf[l]) {
+            launch_omega_infer<T>(v, net, omega_buf[l], st);   // weights from this snapshot's G
+            infer_pending[l] = false;
+            ++launches;
+        }
         relax(l, v, shape[l]);
         launches += area_launches() + 1 + smoother_launches(l);
     }
@@ -523,7 +561,7 @@ struct Solver final : SolverBase {
         for (int l = 0; l < nlev - 1; ++l)
             if (sh[l] < 0 || sh[l] >= kTileShapes) return fail(MG_ERR_ARG, "tile shape out of range");
         for (int l = 0; l < nlev - 1; ++l) shape[l] = sh[l];
-        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        drop_graphs();
         return MG_OK;
     }
 
@@ -564,41 +602,180 @@ struct Solver final : SolverBase {
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }   // shapes are baked into graphs
+        drop_graphs();   // shapes are baked into the graphs
         return MG_OK;
     }
 
-    int vcycle(double *rhoout) override {
-        if (!in_step) return fail(MG_ERR_STATE, "mg_vcycle before mg_begin_step");
+    // Enqueues one V-cycle, replayed from a graph captured once per kind (plain, learned,
+    // learned with inference).
+    int run_cycle(cudaGraphExec_t &ge, long long &nodes) {
         if (p.use_graph) {
-            if (!gexec) {
+            if (!ge) {
                 cudaGraph_t g;
+                bool pend[kMaxLevels];
+                std::copy(std::begin(infer_pending), std::end(infer_pending), pend);
                 CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
                 long long before = launches;
                 enqueue_vcycle();
-                graph_nodes = launches - before;
+                nodes = launches - before;
                 launches = before;
+                std::copy(std::begin(pend), std::end(pend), infer_pending);
                 cudaError_t e = cudaStreamEndCapture(st, &g);
                 if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
-                e = cudaGraphInstantiate(&gexec, g, 0);
+                e = cudaGraphInstantiate(&ge, g, 0);
                 cudaGraphDestroy(g);
-                if (e != cudaSuccess) { gexec = nullptr; return fail(MG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+                if (e != cudaSuccess) { ge = nullptr; return fail(MG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
             }
-            CK(cudaGraphLaunch(gexec, st));
-            launches += graph_nodes;
+            CK(cudaGraphLaunch(ge, st));
+            launches += nodes;
         } else {
             enqueue_vcycle();
             CKL();
         }
         CK(cudaStreamSynchronize(st));
+        return MG_OK;
+    }
+
+    int cycle_plain() {
+        use_omega = (learn_mode == 3);
+        std::fill(std::begin(infer_pending), std::end(infer_pending), false);
+        int rc = learn_mode == 3 ? run_cycle(gexec_l, nodes_l) : run_cycle(gexec, graph_nodes);
+        use_omega = false;
+        return rc;
+    }
+
+    int cycle_learned() {
+        const bool infer = learn_since == 0 || learn_since >= learn_refresh;
+        use_omega = true;
+        for (int l = 0; l < nlev; ++l) infer_pending[l] = infer && omega_buf[l] != nullptr;
+        int rc = infer ? run_cycle(gexec_li, nodes_li) : run_cycle(gexec_l, nodes_l);
+        use_omega = false;
+        std::fill(std::begin(infer_pending), std::end(infer_pending), false);
+        learn_since = infer ? 1 : learn_since + 1;
+        return rc;
+    }
+
+    double current_rho() const { return res0 > 0 ? std::sqrt(hsc->norm2) / res0 : std::sqrt(hsc->norm2); }
+
+    int vcycle(double *rhoout) override {
+        if (!in_step) return fail(MG_ERR_STATE, "mg_vcycle before mg_begin_step");
+        const double rho_prev = rho > 0 ? rho : 1.0;
+        int rc;
+        if (learn_mode == 0 || learn_mode == 3) {
+            rc = cycle_plain();
+        } else if (learn_mode == 2) {
+            rc = cycle_learned();
+        } else if (plain_rate < 0) {
+            rc = cycle_plain();                 // first V-cycle of the step: the reference rate
+            if (!rc) plain_rate = current_rho() / rho_prev;
+        } else {
+            // learned V-cycle, kept only if it contracts at least as fast as the last plain one
+            Level<T> &F = lv[0];
+            const size_t row = (size_t)F.m * sizeof(T), pb = (size_t)F.pitch * sizeof(T);
+            CK(cudaMemcpy2DAsync(ubak, pb, F.u, pb, row, F.n, cudaMemcpyDeviceToDevice, st));
+            rc = cycle_learned();
+            if (!rc) {
+                const double r = current_rho();
+                if (std::isfinite(r) && r / rho_prev <= plain_rate) {
+                    ++learned_acc;
+                } else {
+                    ++learned_rej;
+                    CK(cudaMemcpy2DAsync(F.u, pb, ubak, pb, row, F.n, cudaMemcpyDeviceToDevice, st));
+                    rc = cycle_plain();
+                    if (!rc) plain_rate = current_rho() / rho_prev;
+                }
+            }
+        }
+        if (rc) return rc;
         ++cycles_step;
         ++cycles_total;
-        rho = res0 > 0 ? std::sqrt(hsc->norm2) / res0 : std::sqrt(hsc->norm2);
+        rho = current_rho();
         if (rhoout) *rhoout = rho;
         if (hsc->err & 1) return fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
         if (hsc->err & 4) return fail(MG_ERR_CUDA, "a tile copy into shared memory did not complete in time");
         if (!std::isfinite(rho)) return fail(MG_ERR_NAN, "non-finite residual");
         if (rho > 1e3) return fail(MG_ERR_DIVERGED, "residual grew by more than 1e3");
+        return MG_OK;
+    }
+
+    // Learned relaxation weights: parameters (host FP32, NULL keeps the current ones), mode and
+    // inference interval.  Weight grids exist on the grids the per-grid kernels smooth.
+    int set_learned(const float *theta, int mode, int refresh) override {
+        if (mode < 0 || mode > 2 || refresh < 1) return fail(MG_ERR_ARG, "mode must be 0..2, refresh >= 1");
+        if (mode > 0 && !fused()) return fail(MG_ERR_ARG, "learned weights apply to the fused Hybrid Smoother 2");
+        if (theta) {
+            const int np = learned_nparam();
+            std::vector<__nv_bfloat16> hb(np);
+            for (int k = 0; k < np; ++k) hb[k] = __float2bfloat16(theta[k]);
+            if (!net) CK(cudaMalloc(&net, sizeof(__nv_bfloat16) * np));
+            CK(cudaMemcpy(net, hb.data(), sizeof(__nv_bfloat16) * np, cudaMemcpyHostToDevice));
+        }
+        if (mode > 0 && !net) return fail(MG_ERR_ARG, "no parameters given");
+        if (mode > 0) {
+            int rc = alloc_omega();
+            if (rc) return rc;
+            for (int l = 0; l < nlev; ++l) omega_valid[l] = omega_buf[l] != nullptr;   // inferred before use
+        }
+        learn_mode = mode;
+        learn_refresh = refresh;
+        learn_since = 0;
+        plain_rate = -1.0;
+        drop_graphs();
+        return MG_OK;
+    }
+
+    int alloc_omega() {
+        const int top = lb >= 0 ? lb : nlev - 1;
+        for (int l = 0; l < top; ++l)
+            if (!omega_buf[l]) CK(cudaMalloc(&omega_buf[l], sizeof(T) * (size_t)lv[l].n * lv[l].pitch));
+        if (!ubak) CK(cudaMalloc(&ubak, sizeof(T) * (size_t)lv[0].n * lv[0].pitch));
+        return MG_OK;
+    }
+
+    // Training crops of the finest grid's current frozen system (coefficients and f of the last
+    // snapshot, the current increment u) at seeded random origins.
+    int record_crops(float *data, int first, int count, unsigned long long seed) override {
+        const int c = learned_crop();
+        const Level<T> &L = lv[0];
+        if (L.n < c || L.m < c) return fail(MG_ERR_ARG, "finest grid smaller than a crop");
+        std::mt19937_64 rng(seed);
+        std::vector<int> org(2 * count);
+        for (int k = 0; k < count; ++k) {
+            org[2 * k] = (int)(rng() % (unsigned long long)(L.n - c + 1));
+            org[2 * k + 1] = (int)(rng() % (unsigned long long)(L.m - c + 1));
+        }
+        int *d = nullptr;
+        CK(cudaMallocAsync(&d, sizeof(int) * 2 * count, st));
+        CK(cudaMemcpyAsync(d, org.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice, st));
+        launch_record_crops<T>(view(0), d, count, data, first, st);
+        ++launches;
+        CKL();
+        CK(cudaFreeAsync(d, st));
+        CK(cudaStreamSynchronize(st));
+        return MG_OK;
+    }
+
+    // Fixed relaxation weights of grid l (host, n_l x m_l of the storage type; NULL: none).
+    int set_omega(int l, const void *w) override {
+        if (l < 0 || l >= nlev - 1) return fail(MG_ERR_ARG, "level");
+        if (lb >= 0 && l >= lb) return fail(MG_ERR_ARG, "grid smoothed by the bottom kernel (disable it first)");
+        if (!fused()) return fail(MG_ERR_ARG, "weights apply to the fused Hybrid Smoother 2");
+        int rc = alloc_omega();
+        if (rc) return rc;
+        if (w) {
+            const Level<T> &L = lv[l];
+            CK(cudaMemcpy2D(omega_buf[l], (size_t)L.pitch * sizeof(T), w, (size_t)L.m * sizeof(T),
+                            (size_t)L.m * sizeof(T), L.n, cudaMemcpyHostToDevice));
+            if (learn_mode != 3) std::fill(std::begin(omega_valid), std::end(omega_valid), false);
+            omega_valid[l] = true;
+            learn_mode = 3;
+        } else {
+            omega_valid[l] = false;
+            bool any = false;
+            for (bool b : omega_valid) any = any || b;
+            if (!any && learn_mode == 3) learn_mode = 0;
+        }
+        drop_graphs();
         return MG_OK;
     }
 
@@ -647,13 +824,14 @@ struct Solver final : SolverBase {
     }
 
     int get_level(int l, int field, void *out) override {
-        if (l < 0 || l >= nlev || field < 0 || field > 5) return fail(MG_ERR_ARG, "level / field out of range");
+        if (l < 0 || l >= nlev || field < 0 || field > 7) return fail(MG_ERR_ARG, "level / field out of range");
         Level<T> &L = lv[l];
         if (field == 0) {
             dim3 grid((L.m + 31) / 32, (L.n + 7) / 8);
             k_phi_out<T><<<grid, dim3(32, 8), 0, st>>>(L.pn, L.u, L.n, L.m, L.pitch, (T *)out);
         } else {
-            const T *src = field == 1 ? L.w : field == 2 ? L.z : field == 3 ? L.d : field == 4 ? L.F : L.rhs;
+            const T *src = field == 1 ? L.w : field == 2 ? L.z : field == 3 ? L.d : field == 4 ? L.F
+                         : field == 5 ? L.rhs : field == 6 ? L.G : omega_buf[l];
             if (!src) return fail(MG_ERR_ARG, "field not stored on this level");
             launch_copy_out<T>(src, (T *)out, L.n, L.m, L.pitch, st);
         }
@@ -672,6 +850,8 @@ struct Solver final : SolverBase {
         s->c1 = hsc->c1; s->c2 = hsc->c2; s->A1 = A1;
         s->device_bytes = pool_bytes;
         s->launches = launches;
+        s->learned_accepted = learned_acc;
+        s->learned_rejected = learned_rej;
         return MG_OK;
     }
 
@@ -944,6 +1124,7 @@ int mg_setup(mg_handle *out, const void *image, int n, int m, const double *mark
     prepare_coarse_kernels();
     prepare_bottom_kernel();
     prepare_sweep_tma();
+    prepare_learned_kernels();
     SolverBase *s = nullptr;
     if (p->precision != MG_F64) {
         auto *t = new Solver<float>();
@@ -1085,6 +1266,150 @@ int mg_aos(mg_handle h, double dt, int max_iter, double eta, int *iters, double 
     return h->s->aos(dt, max_iter, eta, iters, rho);
 }
 
+int mg_set_learned(mg_handle h, const float *theta, int mode, int refresh) {
+    if (!h) return fail(MG_ERR_ARG, "NULL handle");
+    return h->s->set_learned(theta, mode, refresh);
+}
+
+int mg_set_omega(mg_handle h, int level, const void *omega) {
+    if (!h) return fail(MG_ERR_ARG, "NULL handle");
+    return h->s->set_omega(level, omega);
+}
+
+int mg_learned_nparam(void) { return learned_nparam(); }
+
+}  // extern "C"
+
+struct mg_trainer_s {
+    int cap = 0, count = 0, batch_max = 0, step = 0;
+    unsigned long long seed = 0;
+    cudaStream_t st = nullptr;
+    float *data = nullptr, *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr, *loss = nullptr;
+    float *gmean = nullptr, *lmean = nullptr;
+    int *idx = nullptr;
+    std::mt19937_64 rng;
+    ~mg_trainer_s() {
+        if (st) cudaStreamSynchronize(st);
+        for (void *q : {(void *)data, (void *)theta, (void *)mom, (void *)vel, (void *)grad, (void *)loss,
+                        (void *)gmean, (void *)lmean, (void *)idx})
+            if (q) cudaFree(q);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
+extern "C" {
+
+int mg_trainer_create(mg_trainer *out, int capacity, int batch_max, unsigned long long seed, const float *theta0) {
+    if (!out || capacity < 1 || batch_max < 1) return fail(MG_ERR_ARG, "NULL out, capacity < 1 or batch_max < 1");
+    *out = nullptr;
+    prepare_learned_kernels();
+    auto *t = new mg_trainer_s();
+    t->cap = capacity; t->batch_max = batch_max; t->seed = seed; t->rng.seed(seed);
+    const int np = learned_nparam();
+    const size_t rec = learned_record_floats();
+    cudaError_t e = cudaStreamCreateWithFlags(&t->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&t->data, sizeof(float) * rec * capacity);
+    if (e == cudaSuccess) e = cudaMalloc(&t->theta, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&t->mom, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&t->vel, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&t->grad, sizeof(float) * np * (size_t)batch_max);
+    if (e == cudaSuccess) e = cudaMalloc(&t->loss, sizeof(float) * batch_max);
+    if (e == cudaSuccess) e = cudaMalloc(&t->gmean, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMalloc(&t->lmean, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&t->idx, sizeof(int) * batch_max);
+    if (e == cudaSuccess) e = cudaMemset(t->mom, 0, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaMemset(t->vel, 0, sizeof(float) * np);
+    if (e != cudaSuccess) {
+        delete t;
+        return fail(e == cudaErrorMemoryAllocation ? MG_ERR_NOMEM : MG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    std::vector<float> th(np, 0.f);
+    if (theta0) {
+        std::copy(theta0, theta0 + np, th.begin());
+    } else {
+        // He-normal hidden layers, zero output layer and biases: omega = 2 sigmoid(0) = 1 at the
+        // start, the plain smoother
+        std::normal_distribution<float> nd(0.f, 1.f);
+        const float s1 = std::sqrt(2.f / 45.f), s2 = std::sqrt(2.f / 144.f);
+        for (int k = 0; k < 720; ++k) th[k] = s1 * nd(t->rng);
+        for (int k = 736; k < 3040; ++k) th[k] = s2 * nd(t->rng);
+    }
+    if (cudaMemcpy(t->theta, th.data(), sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess) {
+        delete t;
+        return fail(MG_ERR_CUDA, "parameter upload");
+    }
+    *out = t;
+    return MG_OK;
+}
+
+int mg_trainer_record(mg_trainer t, mg_handle h, int count) {
+    if (!t || !h || count < 1) return fail(MG_ERR_ARG, "NULL argument or count < 1");
+    count = std::min(count, t->cap - t->count);
+    if (count <= 0) return MG_OK;
+    int rc = h->s->record_crops(t->data, t->count, count, t->rng());
+    if (!rc) t->count += count;
+    return rc;
+}
+
+int mg_trainer_load(mg_trainer t, const float *records, int count) {
+    if (!t || !records || count < 1 || t->count + count > t->cap) return fail(MG_ERR_ARG, "NULL argument or capacity");
+    const size_t rec = learned_record_floats();
+    cudaError_t e = cudaMemcpy(t->data + rec * t->count, records, sizeof(float) * rec * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, cudaGetErrorString(e));
+    t->count += count;
+    return MG_OK;
+}
+
+int mg_trainer_count(mg_trainer t) { return t ? t->count : 0; }
+
+// One batch: mean loss and gradient over the given crops; with lr > 0 also the Adam step.
+static int trainer_batch(mg_trainer t, const int *idx, int batch, double lr, double *loss_out, float *grad_out) {
+    if (cudaMemcpyAsync(t->idx, idx, sizeof(int) * batch, cudaMemcpyHostToDevice, t->st) != cudaSuccess)
+        return fail(MG_ERR_CUDA, "index upload");
+    if (lr > 0) ++t->step;
+    launch_train_step(t->theta, t->mom, t->vel, t->data, t->idx, batch, t->grad, t->loss, t->gmean, t->lmean,
+                      (float)lr, lr > 0 ? t->step : 0, t->st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, cudaGetErrorString(e));
+    float l = 0.f;
+    e = cudaMemcpyAsync(&l, t->lmean, sizeof(float), cudaMemcpyDeviceToHost, t->st);
+    if (e == cudaSuccess && grad_out)
+        e = cudaMemcpyAsync(grad_out, t->gmean, sizeof(float) * learned_nparam(), cudaMemcpyDeviceToHost, t->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, cudaGetErrorString(e));
+    if (loss_out) *loss_out = l;
+    return MG_OK;
+}
+
+int mg_trainer_grad(mg_trainer t, const int *idx, int batch, float *grad, double *loss) {
+    if (!t || !idx || batch < 1 || batch > t->batch_max) return fail(MG_ERR_ARG, "NULL argument or batch");
+    for (int k = 0; k < batch; ++k)
+        if (idx[k] < 0 || idx[k] >= t->count) return fail(MG_ERR_ARG, "crop index out of range");
+    return trainer_batch(t, idx, batch, 0.0, loss, grad);
+}
+
+int mg_trainer_train(mg_trainer t, int iters, int batch, double lr, double *loss) {
+    if (!t || iters < 1 || batch < 1 || batch > t->batch_max || !(lr > 0) || t->count < 1)
+        return fail(MG_ERR_ARG, "NULL trainer, iters / batch / lr out of range or no crops");
+    std::vector<int> idx(batch);
+    double l = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        for (int k = 0; k < batch; ++k) idx[k] = (int)(t->rng() % (unsigned long long)t->count);
+        int rc = trainer_batch(t, idx.data(), batch, lr, &l, nullptr);
+        if (rc) return rc;
+    }
+    if (loss) *loss = l;
+    return MG_OK;
+}
+
+int mg_trainer_get(mg_trainer t, float *theta) {
+    if (!t || !theta) return fail(MG_ERR_ARG, "NULL argument");
+    cudaError_t e = cudaMemcpy(theta, t->theta, sizeof(float) * learned_nparam(), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MG_OK : fail(MG_ERR_CUDA, cudaGetErrorString(e));
+}
+
+void mg_trainer_destroy(mg_trainer t) { delete t; }
+
 int mg_energy(mg_handle h, double *E) {
     if (!h || !E) return fail(MG_ERR_ARG, "NULL argument");
     return h->s->energy(E);
@@ -1113,6 +1438,7 @@ int mg_batch_setup(mg_batch *out, int count, const void *const *images, const in
     prepare_coarse_kernels();
     prepare_bottom_kernel();
     prepare_sweep_tma();
+    prepare_learned_kernels();
     auto *B = new mg_batch_s();
     Batch &b = B->b;
     int rc = MG_OK;

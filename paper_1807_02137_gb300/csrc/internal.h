@@ -42,6 +42,8 @@ struct LevelView {
     const __nv_bfloat16 *wb;   // mixed precision: the length weight w stored in BF16 (else NULL)
     uint8_t *cls;              // Hybrid Smoother 1 only: per cell 1 << (index of the smallest of
                                // A..D) if the cell is in D, else 0 (else NULL)
+    const T *omega;            // relaxation weights of the Hybrid Smoother 2 point updates
+                               // (phi += omega (g - phi)); NULL: plain updates
     int has_rhs;    // 0 on the finest grid (zero right-hand side)
 };
 
@@ -140,6 +142,19 @@ void prepare_sweep_tma();
 bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M);
 void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const SweepMaps &M, int *err,
                       cudaStream_t st);
+
+// learned.cu: learned relaxation weights (inference and training)
+int learned_nparam();
+int learned_crop();
+size_t learned_record_floats();
+void prepare_learned_kernels();
+template <typename T>
+void launch_omega_infer(const LevelView<T> &L, const __nv_bfloat16 *net, T *omega, cudaStream_t st);
+template <typename T>
+void launch_record_crops(const LevelView<T> &L, const int *origins, int count, float *data, int first,
+                         cudaStream_t st);
+void launch_train_step(float *theta, float *mom, float *vel, const float *data, const int *idx, int batch,
+                       float *grad, float *loss, float *gmean, float *lmean, float lr, int step, cudaStream_t st);
 
 // cycle_kernels.cu
 template <typename T>

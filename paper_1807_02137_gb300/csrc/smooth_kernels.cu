@@ -132,7 +132,9 @@ __global__ void __launch_bounds__(256) k_rb(LevelView<T> L, int colour, int swee
     T gc = L.G[o];
     T aS = face(gc, L.G[oS], hS), aN = face(gc, L.G[oN], hN);
     T aE = face(gc, L.G[oE], hE), aW = face(gc, L.G[oW], hW);
-    L.u[o] = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, L.u[oS], L.u[oN], L.u[oE], L.u[oW], L.f[o]);
+    T v = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, L.u[oS], L.u[oN], L.u[oE], L.u[oW], L.f[o]);
+    if (L.omega) v = relax_weighted(L.omega[o], v, L.u[o]);
+    L.u[o] = v;
 }
 
 // One warp per (line, 32-cell piece); groups are read from upre (the values at the start of
@@ -239,8 +241,8 @@ __device__ __forceinline__ void rb_phase(FusedSmem<T, TS> &S, const LevelView<T>
         const int x = (a + colour) & 1, b = 2 * k + x;
         if (b < lo || b >= kRW - lo) continue;
         bool hS = true, hN = true, hE = true, hW = true;
+        const int gi = i0 - kH + a, gj = j0 - kH + b;
         if (!INTERIOR) {
-            const int gi = i0 - kH + a, gj = j0 - kH + b;
             if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
             hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
         }
@@ -248,9 +250,10 @@ __device__ __forceinline__ void rb_phase(FusedSmem<T, TS> &S, const LevelView<T>
         const T gc = S.G[colour][a][k];
         const T aS = face(gc, S.G[other][a + 1][k], hS), aN = face(gc, S.G[other][a - 1][k], hN);
         const T aE = face(gc, S.G[other][a][k + x], hE), aW = face(gc, S.G[other][a][k + x - 1], hW);
-        S.u[colour][a][k] = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, S.u[other][a + 1][k],
-                                        S.u[other][a - 1][k], S.u[other][a][k + x],
-                                        S.u[other][a][k + x - 1], S.f[colour][a][k]);
+        T v = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, S.u[other][a + 1][k], S.u[other][a - 1][k],
+                          S.u[other][a][k + x], S.u[other][a][k + x - 1], S.f[colour][a][k]);
+        if (L.omega) v = relax_weighted(__ldg(L.omega + (size_t)gi * L.pitch + gj), v, S.u[colour][a][k]);
+        S.u[colour][a][k] = v;
     }
 }
 

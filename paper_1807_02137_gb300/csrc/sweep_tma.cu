@@ -113,8 +113,8 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
         const int a = 2 * pr + (e & 1), b = (e & ~1) + ((a + colour) & 1);
         if (a < lo || a >= kRH - lo || b < lo || b >= kRW - lo) continue;
         bool hS = true, hN = true, hE = true, hW = true;
+        const int gi = i0 - kH + a, gj = j0 - kH + b;
         if (!INTERIOR) {
-            const int gi = i0 - kH + a, gj = j0 - kH + b;
             if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
             hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
         }
@@ -122,8 +122,10 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
         const float gc = G[a][b];
         const float aS = face(gc, G[a + 1][b], hS), aN = face(gc, G[a - 1][b], hN);
         const float aE = face(gc, G[a][b + 1], hE), aW = face(gc, G[a][b - 1], hW);
-        u[a][b] = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, u[a + 1][b], u[a - 1][b], u[a][b + 1],
+        float v = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, u[a + 1][b], u[a - 1][b], u[a][b + 1],
                               u[a][b - 1], f[a][b]);
+        if (L.omega) v = relax_weighted(__ldg(L.omega + (size_t)gi * L.pitch + gj), v, u[a][b]);
+        u[a][b] = v;
     }
 }
 

@@ -23,7 +23,9 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
            "mg_get_level", "mg_get_stats", "mg_segment_host", "mg_get_stream", "mg_destroy",
-           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_energy", "mg_aos",
+           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
+           "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_grad",
+           "mg_trainer_train", "mg_trainer_get", "mg_trainer_destroy",
            "mg_batch_setup", "mg_batch_solve_step", "mg_batch_autotune", "mg_batch_handle",
            "mg_batch_destroy"]
 
@@ -50,7 +52,7 @@ class Stats(C.Structure):
         ("steps", C.c_int), ("cycles_step", C.c_int), ("cycles_total", C.c_int),
         ("picard_last", C.c_int), ("rho", C.c_double), ("res0", C.c_double), ("eta", C.c_double),
         ("c1", C.c_double), ("c2", C.c_double), ("A1", C.c_double), ("device_bytes", C.c_size_t),
-        ("launches", C.c_longlong),
+        ("launches", C.c_longlong), ("learned_accepted", C.c_longlong), ("learned_rejected", C.c_longlong),
     ]
 
     def as_dict(self):
@@ -100,6 +102,17 @@ def lib():
             "mg_set_bottom_kernel": ([vp, i, C.POINTER(i)], i),
             "mg_energy": ([vp, C.POINTER(C.c_double)], i),
             "mg_aos": ([vp, C.c_double, i, C.c_double, C.POINTER(i), C.POINTER(C.c_double)], i),
+            "mg_set_learned": ([vp, C.POINTER(C.c_float), i, i], i),
+            "mg_set_omega": ([vp, i, vp], i),
+            "mg_learned_nparam": ([], i),
+            "mg_trainer_create": ([C.POINTER(vp), i, i, C.c_ulonglong, C.POINTER(C.c_float)], i),
+            "mg_trainer_record": ([vp, vp, i], i),
+            "mg_trainer_load": ([vp, C.POINTER(C.c_float), i], i),
+            "mg_trainer_count": ([vp], i),
+            "mg_trainer_grad": ([vp, C.POINTER(i), i, C.POINTER(C.c_float), C.POINTER(C.c_double)], i),
+            "mg_trainer_train": ([vp, i, i, C.c_double, C.POINTER(C.c_double)], i),
+            "mg_trainer_get": ([vp, C.POINTER(C.c_float)], i),
+            "mg_trainer_destroy": ([vp], None),
             "mg_batch_setup": ([C.POINTER(vp), i, C.POINTER(vp), C.POINTER(i), C.POINTER(i),
                                 C.POINTER(D), C.POINTER(i), P, vp], i),
             "mg_batch_solve_step": ([vp, d, i, C.POINTER(i), D], i),
@@ -233,9 +246,9 @@ class Solver:
         _check(lib().mg_set_regions(self._h, float(c1), float(c2)), "mg_set_regions")
 
     def level(self, l, field):
-        """field: 0 phi, 1 w, 2 z, 3 d, 4 F, 5 rhs."""
+        """field: 0 phi, 1 w, 2 z, 3 d, 4 F, 5 rhs, 6 G, 7 omega."""
         import torch
-        names = {"phi": 0, "w": 1, "z": 2, "d": 3, "F": 4, "rhs": 5}
+        names = {"phi": 0, "w": 1, "z": 2, "d": 3, "F": 4, "rhs": 5, "G": 6, "omega": 7}
         f = names.get(field, field)
         n, m = self.n >> l, self.m >> l
         out = torch.empty((n, m), dtype=self.dtype, device=self.image.device)
@@ -273,6 +286,26 @@ class Solver:
         it, r = C.c_int(), C.c_double()
         _check(lib().mg_aos(self._h, dt, max_iter, eta, C.byref(it), C.byref(r)), "mg_aos")
         return it.value, r.value
+
+    def set_learned(self, theta=None, mode=1, refresh=4):
+        """Learned relaxation weights (mg_set_learned): theta (3201 floats) or None."""
+        import numpy as np
+        ptr = None
+        if theta is not None:
+            th = np.ascontiguousarray(theta, dtype=np.float32)
+            assert th.size == lib().mg_learned_nparam()
+            ptr = th.ctypes.data_as(C.POINTER(C.c_float))
+        _check(lib().mg_set_learned(self._h, ptr, mode, refresh), "mg_set_learned")
+
+    def set_omega(self, level, omega):
+        """Fixed relaxation weights of one grid (mg_set_omega); None switches them off."""
+        import numpy as np
+        if omega is None:
+            _check(lib().mg_set_omega(self._h, level, None), "mg_set_omega")
+            return
+        dt = np.float64 if str(self.dtype) == "torch.float64" else np.float32
+        w = np.ascontiguousarray(omega, dtype=dt)
+        _check(lib().mg_set_omega(self._h, level, C.c_void_p(w.ctypes.data)), "mg_set_omega")
 
     def energy(self) -> float:
         """Level-set energy of the current phi with the current c1, c2 (mg_energy)."""
@@ -378,3 +411,60 @@ def segment_host(image, markers, params: Params, tol=1e-6, max_cycles=50, eta_st
                                  phi.ctypes.data_as(C.c_void_p) if want_phi else None, C.byref(st)),
            "mg_segment_host")
     return mask, phi, st.as_dict()
+
+
+class Trainer:
+    """Training of the learned relaxation weights (mg_trainer_*)."""
+
+    def __init__(self, capacity, batch_max=64, seed=0, theta0=None):
+        import numpy as np
+        h = C.c_void_p()
+        ptr = None
+        if theta0 is not None:
+            self._t0 = np.ascontiguousarray(theta0, dtype=np.float32)
+            ptr = self._t0.ctypes.data_as(C.POINTER(C.c_float))
+        _check(lib().mg_trainer_create(C.byref(h), capacity, batch_max, seed, ptr), "mg_trainer_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mg_trainer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def record(self, solver, count):
+        _check(lib().mg_trainer_record(self._h, solver._handle, count), "mg_trainer_record")
+
+    def load(self, records):
+        import numpy as np
+        r = np.ascontiguousarray(records, dtype=np.float32)
+        _check(lib().mg_trainer_load(self._h, r.ctypes.data_as(C.POINTER(C.c_float)), r.shape[0]), "mg_trainer_load")
+
+    @property
+    def count(self):
+        return lib().mg_trainer_count(self._h)
+
+    def grad(self, idx):
+        import numpy as np
+        ix = np.ascontiguousarray(idx, dtype=np.int32)
+        g = np.zeros(lib().mg_learned_nparam(), dtype=np.float32)
+        loss = C.c_double()
+        _check(lib().mg_trainer_grad(self._h, ix.ctypes.data_as(C.POINTER(C.c_int)), ix.size,
+                                     g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)), "mg_trainer_grad")
+        return loss.value, g
+
+    def train(self, iters, batch, lr):
+        loss = C.c_double()
+        _check(lib().mg_trainer_train(self._h, iters, batch, lr, C.byref(loss)), "mg_trainer_train")
+        return loss.value
+
+    def theta(self):
+        import numpy as np
+        out = np.zeros(lib().mg_learned_nparam(), dtype=np.float32)
+        _check(lib().mg_trainer_get(self._h, out.ctypes.data_as(C.POINTER(C.c_float))), "mg_trainer_get")
+        return out
