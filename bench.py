@@ -549,6 +549,73 @@ def run_algorithms(args):
     print(json.dumps({"algorithms": N, "tol": TOL, "rows": rows}), flush=True)
 
 
+def run_learned(args):
+    """Learned relaxation weights (the config-5 form): train on states recorded from 200 plain
+    solves of 1024^2 ellipse images (seeds 100-299), then time one pseudo-time step to
+    rho <= 1e-6 at the given sizes with the plain smoother and with the learned weights kept per
+    V-cycle only when they beat the plain smoother's rate (mode 1)."""
+    import torch
+    from paper_1807_02137_gb300 import buildlib, segmg, synth
+    buildlib.build()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    tr = segmg.Trainer(capacity=200 * 24, batch_max=64, seed=5)
+    for k in range(200):
+        img, mk, _ = synth.ellipses(1024, 1024, 12, (20, 200), 8, 0.05, 100 + k)
+        s = segmg.Solver(torch.as_tensor(img.astype(np.float32), device=dev), mk, segmg.default_params(1024, 1024))
+        s.begin_step()
+        for c in range(6):
+            s.vcycle()
+            if c in (0, 2, 5):
+                tr.record(s, 8)
+        s.close()
+    t_rec = time.perf_counter() - t0
+    loss0 = tr.grad(list(range(64)))[0]
+    t1 = time.perf_counter()
+    loss = tr.train(args.train_iters, 64, 3e-3)
+    t_train = time.perf_counter() - t1
+    loss1 = tr.grad(list(range(64)))[0]
+    theta = tr.theta()
+    rows = []
+    for N in args.learned:
+        # the config-3 image recipe scaled to N (200 ellipses, axes 100-3000 px at 25000^2, the
+        # device-side generator of the config-3 run)
+        img, mk = synth.ellipses_device(N, N, 200, (100 * N / 25000, 3000 * N / 25000), 20, 0.05, 2, dev)
+        img = img.float().cpu().numpy() if hasattr(img, "cpu") else img
+        levels, sz = 1, N
+        while sz // 2 >= 4 and levels < 12:
+            sz //= 2
+            levels += 1
+        W = synth.Workload(f"ellipses200_{N}", img, mk, levels, TOL, "f32", "config-3 recipe")
+        timg = torch.as_tensor(W.image.astype(np.float32), device=dev)
+        for mode in (0, 1):
+            p = segmg.default_params(N, N, levels=W.levels)
+            s = segmg.Solver(timg, W.markers, p)
+            if mode:
+                s.set_learned(theta, mode=1, refresh=args.refresh)
+            st = torch.cuda.ExternalStream(s.stream_ptr)
+            for rep in range(2):                    # the second run is timed
+                s.reset(timg, W.markers)
+                a0 = s.stats()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                cyc, rho = s.solve_step(TOL, MAX_CYCLES)
+                b.record(st)
+                b.synchronize()
+            stt = s.stats()
+            rows.append({"n": N, "mode": "learned (per V-cycle acceptance)" if mode else "plain",
+                         "cycles": cyc, "rho": rho, "converged": rho <= TOL, "ms": a.elapsed_time(b),
+                         "unknowns_per_s": N * N / (a.elapsed_time(b) * 1e-3),
+                         "learned_accepted": stt["learned_accepted"] - a0["learned_accepted"],
+                         "learned_rejected": stt["learned_rejected"] - a0["learned_rejected"]})
+            s.close()
+    print(json.dumps({"learned": {"crops": tr.count, "record_s": t_rec, "train_iters": args.train_iters,
+                                  "train_s": t_train, "loss_before": loss0, "loss_after": loss1,
+                                  "last_batch_loss": loss, "refresh": args.refresh},
+                      "rows": rows}), flush=True)
+    tr.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -564,8 +631,16 @@ def main():
     ap.add_argument("--config3", type=int, default=0, help="run the mixed-precision N x N report")
     ap.add_argument("--config4", type=int, default=0, help="run the batched report with this many images")
     ap.add_argument("--algorithms", type=int, default=0, help="compare Algorithms 1-3 on an N x N image")
+    ap.add_argument("--learned", type=int, nargs="*", default=None,
+                    help="train the learned relaxation weights, then compare at these sizes")
+    ap.add_argument("--train-iters", type=int, default=1000)
+    ap.add_argument("--refresh", type=int, default=4)
     args = ap.parse_args()
-    if args.algorithms:
+    if args.learned is not None:
+        if not args.learned:
+            args.learned = [4096, 8192]
+        run_learned(args)
+    elif args.algorithms:
         run_algorithms(args)
     elif args.config4:
         run_config4(args)

@@ -230,7 +230,8 @@ int mg_aos(mg_handle h, double dt, int max_iter, double eta, int *iters, double 
  *            b2 (16), W3 (1,16,3,3), b3; NULL keeps the current parameters;
  *   mode     0 off; 1 every V-cycle after the first of a step runs with the weights and is kept
  *            only if its residual falls at least as fast as the last plain V-cycle's, else the
- *            state is restored and the V-cycle rerun plain; 2 always with the weights;
+ *            state is restored and the V-cycle rerun plain, and the next 1, 2, 4 or 8 V-cycles
+ *            (doubling with consecutive rejections) run plain; 2 always with the weights;
  *   refresh  V-cycles between two inferences (>= 1); the weights are computed from the first
  *            snapshot of each grid in a V-cycle that infers.
  * Requires MG_SMOOTH_FUSED or MG_SMOOTH_FUSED_VEC.  Errors: MG_ERR_ARG, MG_ERR_NOMEM. */

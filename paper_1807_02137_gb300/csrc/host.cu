@@ -165,6 +165,7 @@ struct Solver final : SolverBase {
     cudaGraphExec_t gexec_l = nullptr, gexec_li = nullptr;   // learned V-cycle; with inference
     long long nodes_l = 0, nodes_li = 0;
     double plain_rate = -1.0;     // contraction of the last plain V-cycle of the step
+    int learn_skip = 0, learn_backoff = 1;   // plain V-cycles left before the next learned try
     long long learned_acc = 0, learned_rej = 0;
     size_t lb_smem = 0;
     ModelParams mp{};
@@ -449,6 +450,8 @@ struct Solver final : SolverBase {
         rho = 1.0;
         plain_rate = -1.0;
         learn_since = 0;
+        learn_skip = 0;
+        learn_backoff = 1;
         // the last residual norm starts at the reference one (rho = 1 until a V-cycle runs)
         CK(cudaMemcpyAsync(&dsc->norm2, &dsc->norm2_0, sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (!std::isfinite(res0)) return fail(MG_ERR_NAN, "non-finite initial residual");
@@ -665,9 +668,12 @@ struct Solver final : SolverBase {
             rc = cycle_plain();
         } else if (learn_mode == 2) {
             rc = cycle_learned();
-        } else if (plain_rate < 0) {
-            rc = cycle_plain();                 // first V-cycle of the step: the reference rate
+        } else if (plain_rate < 0 || learn_skip > 0) {
+            // the first V-cycle of the step, or a back-off after a rejected learned V-cycle:
+            // plain, and its rate is the reference
+            rc = cycle_plain();
             if (!rc) plain_rate = current_rho() / rho_prev;
+            if (learn_skip > 0) --learn_skip;
         } else {
             // learned V-cycle, kept only if it contracts at least as fast as the last plain one
             Level<T> &F = lv[0];
@@ -678,8 +684,11 @@ struct Solver final : SolverBase {
                 const double r = current_rho();
                 if (std::isfinite(r) && r / rho_prev <= plain_rate) {
                     ++learned_acc;
+                    learn_backoff = 1;
                 } else {
                     ++learned_rej;
+                    learn_skip = learn_backoff;                  // plain for a while, doubling
+                    learn_backoff = std::min(2 * learn_backoff, 8);
                     CK(cudaMemcpy2DAsync(F.u, pb, ubak, pb, row, F.n, cudaMemcpyDeviceToDevice, st));
                     rc = cycle_plain();
                     if (!rc) plain_rate = current_rho() / rho_prev;

@@ -119,8 +119,8 @@ def test_training_loss_and_gradient_match_oracle(segmg):
 
 
 def test_learned_mode_keeps_the_solution(segmg):
-    # per-V-cycle acceptance: the step still converges to the oracle's solution, and every
-    # V-cycle after the first is counted as accepted or rejected
+    # per-V-cycle acceptance: the step still converges to the oracle's solution; learned V-cycles
+    # are tried after the first (plain) one, with plain back-off after a rejection
     img, mk, _ = synth.ellipses(256, 256, 12, (10, 60), 8, 0.05, 11)   # converges plain to 1e-6
     s, p = gpu_solver(segmg, img.astype(np.float32), mk, precision=segmg.MG_F32, levels=7)
     t = segmg.Trainer(capacity=64, batch_max=16, seed=3)
@@ -128,7 +128,7 @@ def test_learned_mode_keeps_the_solution(segmg):
     cyc, rho = s.solve_step(1e-6, 60)
     st = s.stats()
     assert rho <= 1e-6
-    assert st["learned_accepted"] + st["learned_rejected"] == cyc - 1
+    assert 1 <= st["learned_accepted"] + st["learned_rejected"] <= cyc - 1
     o = O.Solver(img.astype(np.float32).astype(np.float64), mk, oracle_params(256, 256, p))
     hist = o.solve_step(1e-9, 80)
     assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-5
