@@ -229,7 +229,7 @@ __device__ __forceinline__ bool tile_member(const FusedSmem<T, TS> &S, int a, in
 
 // One checkerboard phase over the region cells within distance 3 - ph of the output tile.
 // INTERIOR: the whole region lies inside the domain, so every updated cell has four faces.
-template <typename T, typename TS, int SWEEP, bool INTERIOR>
+template <typename T, typename TS, int SWEEP, bool INTERIOR, bool WEIGHTED>
 __device__ __forceinline__ void rb_phase(FusedSmem<T, TS> &S, const LevelView<T> &L, int ph, int i0, int j0) {
     constexpr int kRH = TS::RH, kRW = TS::RW, kHW = TS::HW, kThreads = TS::NT;
     constexpr bool rev = (SWEEP & 1) != 0;
@@ -241,8 +241,8 @@ __device__ __forceinline__ void rb_phase(FusedSmem<T, TS> &S, const LevelView<T>
         const int x = (a + colour) & 1, b = 2 * k + x;
         if (b < lo || b >= kRW - lo) continue;
         bool hS = true, hN = true, hE = true, hW = true;
-        const int gi = i0 - kH + a, gj = j0 - kH + b;
         if (!INTERIOR) {
+            const int gi = i0 - kH + a, gj = j0 - kH + b;
             if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
             hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
         }
@@ -252,7 +252,10 @@ __device__ __forceinline__ void rb_phase(FusedSmem<T, TS> &S, const LevelView<T>
         const T aE = face(gc, S.G[other][a][k + x], hE), aW = face(gc, S.G[other][a][k + x - 1], hW);
         T v = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, S.u[other][a + 1][k], S.u[other][a - 1][k],
                           S.u[other][a][k + x], S.u[other][a][k + x - 1], S.f[colour][a][k]);
-        if (L.omega) v = relax_weighted(__ldg(L.omega + (size_t)gi * L.pitch + gj), v, S.u[colour][a][k]);
+        if (WEIGHTED) {
+            const size_t o = (size_t)(i0 - kH + a) * L.pitch + (j0 - kH + b);
+            v = relax_weighted(__ldg(L.omega + o), v, S.u[colour][a][k]);
+        }
         S.u[colour][a][k] = v;
     }
 }
@@ -333,8 +336,13 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
     const bool interior = i0 - kH >= 0 && i0 - kH + kRH <= n && j0 - kH >= 0 && j0 - kH + kRW <= m;
 #pragma unroll
     for (int ph = 0; ph < 2; ++ph) {
-        if (interior) rb_phase<T, TS, SWEEP, true>(S, L, ph, i0, j0);
-        else rb_phase<T, TS, SWEEP, false>(S, L, ph, i0, j0);
+        if (L.omega) {
+            if (interior) rb_phase<T, TS, SWEEP, true, true>(S, L, ph, i0, j0);
+            else rb_phase<T, TS, SWEEP, false, true>(S, L, ph, i0, j0);
+        } else {
+            if (interior) rb_phase<T, TS, SWEEP, true, false>(S, L, ph, i0, j0);
+            else rb_phase<T, TS, SWEEP, false, false>(S, L, ph, i0, j0);
+        }
         __syncthreads();
     }
     // ---- partial-line phases: lines at distance 1, then 0, one parity each.  A task is one

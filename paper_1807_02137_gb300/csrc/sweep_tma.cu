@@ -98,7 +98,7 @@ __device__ __forceinline__ bool member(const TmaSmem<TS, STAGES> &S, int a, int 
 
 // One checkerboard phase over the box cells within distance 3 - ph of the output tile (the
 // cells and the operations of rb_phase in smooth_kernels.cu).
-template <typename TS, int STAGES, int SWEEP, bool INTERIOR>
+template <typename TS, int STAGES, int SWEEP, bool INTERIOR, bool WEIGHTED>
 __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const LevelView<float> &L, int ph, int i0,
                                          int j0) {
     constexpr int kRH = TS::RH, kRW = TS::RW;
@@ -113,8 +113,8 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
         const int a = 2 * pr + (e & 1), b = (e & ~1) + ((a + colour) & 1);
         if (a < lo || a >= kRH - lo || b < lo || b >= kRW - lo) continue;
         bool hS = true, hN = true, hE = true, hW = true;
-        const int gi = i0 - kH + a, gj = j0 - kH + b;
         if (!INTERIOR) {
+            const int gi = i0 - kH + a, gj = j0 - kH + b;
             if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
             hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
         }
@@ -124,7 +124,10 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
         const float aE = face(gc, G[a][b + 1], hE), aW = face(gc, G[a][b - 1], hW);
         float v = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, u[a + 1][b], u[a - 1][b], u[a][b + 1],
                               u[a][b - 1], f[a][b]);
-        if (L.omega) v = relax_weighted(__ldg(L.omega + (size_t)gi * L.pitch + gj), v, u[a][b]);
+        if (WEIGHTED) {
+            const size_t o = (size_t)(i0 - kH + a) * L.pitch + (j0 - kH + b);
+            v = relax_weighted(__ldg(L.omega + o), v, u[a][b]);
+        }
         u[a][b] = v;
     }
 }
@@ -207,8 +210,13 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
         const bool interior = i0 - kH >= 0 && i0 - kH + kRH <= n && j0 - kH >= 0 && j0 - kH + kRW <= m;
 #pragma unroll
         for (int ph = 0; ph < 2; ++ph) {
-            if (interior) rb_phase<TS, STAGES, SWEEP, true>(S, st, L, ph, i0, j0);
-            else rb_phase<TS, STAGES, SWEEP, false>(S, st, L, ph, i0, j0);
+            if (L.omega) {
+                if (interior) rb_phase<TS, STAGES, SWEEP, true, true>(S, st, L, ph, i0, j0);
+                else rb_phase<TS, STAGES, SWEEP, false, true>(S, st, L, ph, i0, j0);
+            } else {
+                if (interior) rb_phase<TS, STAGES, SWEEP, true, false>(S, st, L, ph, i0, j0);
+                else rb_phase<TS, STAGES, SWEEP, false, false>(S, st, L, ph, i0, j0);
+            }
             __syncthreads();
         }
         // ---- partial-line phases (as k_sweep): lines at distance 1, then 0, one parity each
