@@ -264,7 +264,7 @@ def run_ours(args):
     achieved = bytes_per_cell * n * m / (sweep_ms * 1e-3) / 1e9
     # DRAM bytes of one finest-grid sweep launch from an ncu capture of this kernel on this grid
     # (profiles/k_sweep_tma_traffic_ellipse1024.txt): u, G, f read once, u written to L2
-    traffic = 12.74e6
+    traffic = 12.75e6
     roof = {"bound": "hbm", "kernel": "k_sweep_tma (TMA-staged fused Hybrid Smoother 2 sweep, finest grid)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic, "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
