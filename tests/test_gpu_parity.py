@@ -398,3 +398,52 @@ def test_finest_grid_aos_matches_oracle(segmg, model):
         io, _ = o.aos(0.5, 200, 1e-4)
         assert abs(ig - io) <= (0 if prec == segmg.MG_F64 else 1)
         s.close()
+
+
+def test_bench_workload_full_size_matches_oracle(segmg):
+    # the bench's 1024^2 FP32 workload in the bench's launch configuration (TMA sweeps, bottom
+    # kernel, graphs, autotuned tiles) against the FP64 oracle's converged solution
+    W = synth.workload("ellipse1024")
+    s, p = gpu_solver(segmg, W.image.astype(np.float32), W.markers, levels=W.levels)
+    s.begin_step()
+    s.autotune(reps=1)
+    s.end_step()
+    s.reset(torch.as_tensor(W.image.astype(np.float32), device="cuda"), W.markers)
+    cyc, rho = s.solve_step(1e-6, 60)
+    assert rho <= 1e-6
+    o = O.Solver(W.image.astype(np.float32).astype(np.float64), W.markers, oracle_params(1024, 1024, p))
+    hist = o.solve_step(1e-9, 80)
+    assert hist[-1] <= 1e-9
+    pg, po = s.phi().cpu().numpy(), o.phi
+    assert relmax(pg, po) < 1e-5
+    assert np.mean((pg > 0) != (po > 0)) <= 1e-4
+    o.close()
+
+
+def test_mixed_precision_large_grid_properties_and_crop(segmg):
+    # 8192^2 mixed precision (w in BF16): properties that hold at any size (monotone residual,
+    # rho <= 1e-6, a mask with both regions), and a 512^2 crop solved standalone against the oracle
+    dev = torch.device("cuda", 0)
+    img, mk = synth.ellipses_device(8192, 8192, 200, (100 * 8192 / 25000, 3000 * 8192 / 25000), 20, 0.05, 2, dev)
+    p = segmg.default_params(8192, 8192, precision=segmg.MG_MIXED)
+    s = segmg.Solver(img, mk, p)
+    s.begin_step()
+    hist = []
+    for _ in range(40):
+        hist.append(s.vcycle())
+        if hist[-1] <= 1e-6:
+            break
+    assert hist[-1] <= 1e-6
+    assert all(b < a for a, b in zip(hist, hist[1:]))
+    frac = float(s.mask().float().mean())
+    assert 0.0 < frac < 0.5            # the selected object: present, a small part of the image
+    s.close()
+    crop = img[3000:3512, 1000:1512].float().cpu().numpy()
+    cm = np.array([[256.0 + 20 * np.cos(t), 256.0 + 20 * np.sin(t)] for t in np.linspace(0, 6, 6)])
+    s2, o2, p2 = both(segmg, crop, cm, precision=segmg.MG_MIXED, levels=7)
+    c2, r2 = s2.solve_step(1e-6, 60)
+    h2 = o2.solve_step(1e-9, 80)
+    assert r2 <= 1e-6 and h2[-1] <= 1e-9
+    pg, po = s2.phi().cpu().numpy(), o2.phi
+    assert relmax(pg, po) < 1e-4
+    assert np.mean((pg > 0) != (po > 0)) <= 1e-3
