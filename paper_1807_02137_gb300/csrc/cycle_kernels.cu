@@ -82,6 +82,126 @@ __global__ void __launch_bounds__(256) k_residual(LevelView<T> L, const T *uin, 
     }
 }
 
+__device__ __forceinline__ int fw_taps(int I, int n, int *idx, double *wt);
+
+// Loads the window dst[a][b] = src[clamp(r0 + a)][clamp(c0 + b)], a < ROWS, b < COLS, of one or
+// two pitched FP32 grid functions (indices clamped into the grid: the mirror ghosts), with
+// 16-byte vector loads where the window lies inside; c0 mod 4 == OFF.  NT threads.
+template <int ROWS, int COLS, int OFF, int NT>
+__device__ __forceinline__ void load_window(float (*dA)[COLS + 1], const float *sA, float (*dB)[COLS + 1],
+                                            const float *sB, int r0, int c0, int n, int m, int p, int tid) {
+    constexpr int NV = (COLS + OFF + 3) / 4, NVEC = ROWS * NV;
+    for (int q = tid; q < NVEC; q += NT) {
+        const int a = q / NV, k = q % NV, gi = r0 + a, gj = c0 - OFF + 4 * k;
+        float xa[4], xb[4];
+        if (gi >= 0 && gi < n && gj >= 0 && gj + 4 <= m) {
+            const size_t o = (size_t)gi * p + gj;
+            const float4 va = __ldg(reinterpret_cast<const float4 *>(sA + o));
+            xa[0] = va.x; xa[1] = va.y; xa[2] = va.z; xa[3] = va.w;
+            if (sB) {
+                const float4 vb = __ldg(reinterpret_cast<const float4 *>(sB + o));
+                xb[0] = vb.x; xb[1] = vb.y; xb[2] = vb.z; xb[3] = vb.w;
+            }
+        } else {
+            const size_t ro = (size_t)clamp_idx(gi, n - 1) * p;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const size_t o = ro + clamp_idx(gj + e, m - 1);
+                xa[e] = sA[o];
+                if (sB) xb[e] = sB[o];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int b = 4 * k - OFF + e;
+            if (b >= 0 && b < COLS) {
+                dA[a][b] = xa[e];
+                if (sB) dB[a][b] = xb[e];
+            }
+        }
+    }
+}
+
+// The end of a pre-smoothing on an FP32 grid in one kernel: the residual r = rhs - L(pn + u)
+// (the arithmetic of k_residual, mode 0) on the 32 x 32 fine tile plus one row and column,
+// then the full weighting of r and of u onto the 16 x 16 coarse cells of the tile (the
+// arithmetic of k_restrict): coarse rhs, u and u0.  r itself is not stored.
+struct ResRestrictSmem {
+    float P[37][38], U[37][38], W[37][38];   // rows i0-2 .. i0+34, columns j0-2 .. j0+34
+    float G[35][36];                         // rows i0-1 .. i0+33
+    float F[33][34], RH[33][34];             // rows i0 .. i0+32
+    float R[33][34];
+};
+
+__global__ void __launch_bounds__(256) k_residual_restrict(LevelView<float> L, LevelView<float> C, const double *area) {
+    extern __shared__ __align__(16) unsigned char smem_rr[];
+    ResRestrictSmem &S = *reinterpret_cast<ResRestrictSmem *>(smem_rr);
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tid = threadIdx.y * 32 + threadIdx.x;
+    const int n = L.n, m = L.m, p = L.pitch;
+    load_window<37, 37, 2, 256>(S.P, L.pn, S.U, L.u, i0 - 2, j0 - 2, n, m, p, tid);
+    if (!L.wb) load_window<37, 37, 2, 256>(S.W, L.w, nullptr, nullptr, i0 - 2, j0 - 2, n, m, p, tid);
+    load_window<33, 33, 0, 256>(S.F, L.F, L.has_rhs ? S.RH : nullptr, L.has_rhs ? L.rhs : nullptr, i0, j0, n, m, p,
+                                tid);
+    __syncthreads();
+    for (int q = tid; q < 35 * 35; q += 256) {
+        const int a = q / 35, b = q % 35, gi = i0 - 1 + a, gj = j0 - 1 + b;
+        float g = 0.f;
+        if (gi >= 0 && gi < n && gj >= 0 && gj < m) {
+            const int A = a + 1, B = b + 1;
+            const float w = L.wb ? weight_at(L, (size_t)gi * p + gj) : S.W[A][B];
+            g = cell_G(w, S.P[A + 1][B], S.P[A - 1][B], S.P[A][B + 1], S.P[A][B - 1], S.U[A + 1][B], S.U[A - 1][B],
+                       S.U[A][B + 1], S.U[A][B - 1], L.inv_2h, L.beta);
+        }
+        S.G[a][b] = g;
+    }
+    __syncthreads();
+    const float ar = area ? float(area[L.level]) : 0.f;
+    for (int q = tid; q < 33 * 33; q += 256) {
+        const int ti = q / 33, tj = q % 33, gi = i0 + ti, gj = j0 + tj;
+        float r = 0.f;
+        if (gi < n && gj < m) {
+            const int a = ti + 1, b = tj + 1;        // in G
+            const int A = ti + 2, B = tj + 2;        // in P, U
+            const bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
+            const float gc = S.G[a][b];
+            const float aS = face(gc, S.G[a + 1][b], hS), aN = face(gc, S.G[a - 1][b], hN);
+            const float aE = face(gc, S.G[a][b + 1], hE), aW = face(gc, S.G[a][b - 1], hW);
+            const float pc = S.P[A][B], uc = S.U[A][B];
+            float fl = mul_rn(aS, add_rn(sub_rn(S.P[A + 1][B], pc), sub_rn(S.U[A + 1][B], uc)));
+            fl = fma_rn(aN, add_rn(sub_rn(S.P[A - 1][B], pc), sub_rn(S.U[A - 1][B], uc)), fl);
+            fl = fma_rn(aE, add_rn(sub_rn(S.P[A][B + 1], pc), sub_rn(S.U[A][B + 1], uc)), fl);
+            fl = fma_rn(aW, add_rn(sub_rn(S.P[A][B - 1], pc), sub_rn(S.U[A][B - 1], uc)), fl);
+            const float Lv = sub_rn(fma_rn(L.cdiff, fl, -add_rn(S.F[ti][tj], ar)), mul_rn(L.inv_tau, uc));
+            r = L.has_rhs ? sub_rn(S.RH[ti][tj], Lv) : -Lv;
+        }
+        S.R[ti][tj] = r;
+    }
+    __syncthreads();
+    // full weighting onto the coarse cells of this tile: one thread per coarse cell
+    {
+        const int I = blockIdx.y * 16 + tid / 16, J = blockIdx.x * 16 + tid % 16;
+        if (I < C.n && J < C.m) {
+            int ri[3], ci[3];
+            double rw[3], cw[3];
+            const int nr = fw_taps(I, n, ri, rw), nk = fw_taps(J, m, ci, cw);
+            float sr = 0.f, su = 0.f;
+            for (int a = 0; a < nr; ++a) {
+                float rowr = 0.f, rowu = 0.f;
+                for (int b = 0; b < nk; ++b) {
+                    rowr = fma_rn(float(cw[b]), S.R[ri[a] - i0][ci[b] - j0], rowr);
+                    rowu = fma_rn(float(cw[b]), S.U[ri[a] - i0 + 2][ci[b] - j0 + 2], rowu);
+                }
+                sr = fma_rn(float(rw[a]), rowr, sr);
+                su = fma_rn(float(rw[a]), rowu, su);
+            }
+            const size_t o = (size_t)I * C.pitch + J;
+            C.rhs[o] = sr;
+            C.u[o] = su;
+            C.u0[o] = su;
+        }
+    }
+}
+
 // Sums `np` partials in a fixed order into *out.
 __global__ void k_sum_partials(const double *partials, int np, double *out) {
     __shared__ double red[33];
@@ -200,7 +320,14 @@ void launch_interp_add(const LevelView<T> &Lf, const LevelView<T> &Lc, cudaStrea
 
 constexpr size_t kCoarseSmemMax = 200 * 1024;
 
+void launch_residual_restrict(const LevelView<float> &L, const LevelView<float> &C, const double *area,
+                              cudaStream_t st) {
+    dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, 8);
+    k_residual_restrict<<<grid, block, sizeof(ResRestrictSmem), st>>>(L, C, area);
+}
+
 void prepare_coarse_kernels() {
+    cudaFuncSetAttribute(k_residual_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ResRestrictSmem));
     cudaFuncSetAttribute(k_coarse<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);
     cudaFuncSetAttribute(k_coarse<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);
     cudaFuncSetAttribute(k_coarse<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);

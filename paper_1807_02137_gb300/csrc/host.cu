@@ -527,12 +527,18 @@ struct Solver final : SolverBase {
         for (int t = 0; t < p.nu1; ++t) smooth(l);
         Level<T> &L = lv[l], &C = lv[l + 1];
         area_term(l, L.u);
-        launch_residual<T>(view(l), L.u, area_ptr(), L.r, 0, partials, 0, nullptr, st);
-        launch_restrict<T>(L.r, L.n, L.m, L.pitch, C.rhs, nullptr, C.pitch, st);
-        launch_restrict<T>(L.u, L.n, L.m, L.pitch, C.u, C.u0, C.pitch, st);
+        if constexpr (std::is_same<T, float>::value) {
+            launch_residual_restrict(view(l), view(l + 1), area_ptr(), st);
+            launches += 1;
+        } else {
+            launch_residual<T>(view(l), L.u, area_ptr(), L.r, 0, partials, 0, nullptr, st);
+            launch_restrict<T>(L.r, L.n, L.m, L.pitch, C.rhs, nullptr, C.pitch, st);
+            launch_restrict<T>(L.u, L.n, L.m, L.pitch, C.u, C.u0, C.pitch, st);
+            launches += 3;
+        }
         area_term(l + 1, C.u0);
         launch_residual<T>(view(l + 1), C.u0, area_ptr(), C.rhs, 1, partials, 0, nullptr, st);
-        launches += 2 * area_launches() + 4;
+        launches += 2 * area_launches() + 1;
         cycle(l + 1);
         launch_interp_add<T>(view(l), view(l + 1), st);
         ++launches;

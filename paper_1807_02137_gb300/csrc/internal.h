@@ -171,6 +171,9 @@ template <typename T>
 void launch_aos_iteration(const LevelView<T> &L, const double *area, double dt, double *partials, double *sums,
                           cudaStream_t st);
 void prepare_coarse_kernels();
+// FP32 grids: the residual and the full weighting of r and u onto the coarse grid in one kernel
+void launch_residual_restrict(const LevelView<float> &L, const LevelView<float> &C, const double *area,
+                              cudaStream_t st);
 
 // Scratch elements (of the storage type) of the coarsest solve on an n x m grid.
 __host__ __device__ inline size_t coarse_scratch_elems(int n, int m) {
