@@ -40,6 +40,8 @@ struct TShape {
 using TT0 = TShape<32, 64, 256>;
 using TT1 = TShape<32, 32, 128>;
 using TT2 = TShape<64, 64, 512>;
+using TT3 = TShape<32, 64, 512>;
+using TT4 = TShape<32, 32, 256>;
 
 template <typename TS, int STAGES>
 struct TmaSmem {
@@ -395,7 +397,7 @@ int g_sms = 0;
 }  // namespace
 
 void prepare_sweep_tma() {
-    set_attrs<TT0>(); set_attrs<TT1>(); set_attrs<TT2>();
+    set_attrs<TT0>(); set_attrs<TT1>(); set_attrs<TT2>(); set_attrs<TT3>(); set_attrs<TT4>();
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_sms < 1) g_sms = 1;
@@ -404,12 +406,16 @@ void prepare_sweep_tma() {
 bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M) {
     if (shape == 1) return encode_shape<TT1>(L, *M);
     if (shape == 2) return encode_shape<TT2>(L, *M);
+    if (shape == 3) return encode_shape<TT3>(L, *M);
+    if (shape == 4) return encode_shape<TT4>(L, *M);
     return encode_shape<TT0>(L, *M);
 }
 
 void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const SweepMaps &M, int *err, cudaStream_t st) {
     if (shape == 1) launch_shape<TT1>(L, sweep, M, g_sms, err, st);
     else if (shape == 2) launch_shape<TT2>(L, sweep, M, g_sms, err, st);
+    else if (shape == 3) launch_shape<TT3>(L, sweep, M, g_sms, err, st);
+    else if (shape == 4) launch_shape<TT4>(L, sweep, M, g_sms, err, st);
     else launch_shape<TT0>(L, sweep, M, g_sms, err, st);
 }
 
