@@ -202,12 +202,12 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
 /* Tile-shape autotuner (a tuning step of this implementation; the paper has no counterpart):
  * inside a pseudo-time step (after mg_begin_step), times one outer smoothing iteration of every
  * grid but the coarsest with each fused-sweep tile shape (rows x columns of cells, threads per
- * tile: 0 = 32x64/256, 1 = 32x32/128, 2 = 64x64/512, 3 = 32x64/512, 4 = 32x32/256) over `reps`
- * repetitions and keeps the fastest per grid; writes the choices to
+ * tile: 0 = 32x64/256, 1 = 32x32/128, 2 = 64x64/512, 3 = 32x64/512, 4 = 32x32/256, 5 = 32x32/512) over
+ * `reps` repetitions and keeps the fastest per grid; writes the choices to
  * shapes[0..levels-2] if not NULL.  The state is restored, and the results of later solves do
  * not depend on the shapes (every shape computes the same values).  Waits. */
 int mg_autotune(mg_handle h, int reps, int *shapes);
-/* Sets the fused-sweep tile shape of grids 0..levels-2 (values 0..4 as above). */
+/* Sets the fused-sweep tile shape of grids 0..levels-2 (values 0..5 as above). */
 int mg_set_tile_shapes(mg_handle h, const int *shapes);
 /* AOS time marching on the finest grid for the current pseudo-time step: the AOS method the
  * paper compares against in Table 6 (additive operator splitting of d phi / ds = L(phi) - rhs,

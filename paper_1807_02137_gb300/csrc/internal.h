@@ -118,8 +118,8 @@ int num_partials(int n, int m);
 // smooth_kernels.cu
 template <typename T>
 void launch_snapshot(const LevelView<T> &L, const double *area, cudaStream_t st);
-constexpr int kTileShapes = 5;   // fused-sweep tile shapes (rows x columns, threads): 32x64 256, 32x32 128,
-                                 // 64x64 512, 32x64 512, 32x32 256 (see smooth_kernels.cu)
+constexpr int kTileShapes = 6;   // fused-sweep tile shapes (rows x columns, threads): 32x64 256, 32x32 128,
+                                 // 64x64 512, 32x64 512, 32x32 256, 32x32 512 (see smooth_kernels.cu)
 template <typename T>
 void launch_sweep_fused(const LevelView<T> &L, int sweep, int shape, cudaStream_t st);
 template <typename T>

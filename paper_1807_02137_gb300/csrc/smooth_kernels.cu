@@ -210,6 +210,7 @@ using Tile1 = TileShape<32, 32, 128>;
 using Tile2 = TileShape<64, 64, 512>;
 using Tile3 = TileShape<32, 64, 512>;   // more threads per tile: fewer cells per thread per phase
 using Tile4 = TileShape<32, 32, 256>;
+using Tile5 = TileShape<32, 32, 512>;   // one cell per thread per checkerboard phase
 
 template <typename T, typename TS>
 struct FusedSmem {
@@ -477,9 +478,9 @@ static void set_fused_attrs() {
 // (called once per set-up, before any stream capture).
 void prepare_smoother_kernels() {
     set_fused_attrs<float, Tile0>(); set_fused_attrs<float, Tile1>(); set_fused_attrs<float, Tile2>();
-    set_fused_attrs<float, Tile3>(); set_fused_attrs<float, Tile4>();
+    set_fused_attrs<float, Tile3>(); set_fused_attrs<float, Tile4>(); set_fused_attrs<float, Tile5>();
     set_fused_attrs<double, Tile0>(); set_fused_attrs<double, Tile1>(); set_fused_attrs<double, Tile2>();
-    set_fused_attrs<double, Tile3>(); set_fused_attrs<double, Tile4>();
+    set_fused_attrs<double, Tile3>(); set_fused_attrs<double, Tile4>(); set_fused_attrs<double, Tile5>();
 }
 
 template <typename T, int SW, typename TS>
@@ -505,6 +506,7 @@ void launch_sweep_fused(const LevelView<T> &L, int sweep, int shape, cudaStream_
     else if (shape == 2) launch_fused_shape<T, Tile2>(L, sweep, st);
     else if (shape == 3) launch_fused_shape<T, Tile3>(L, sweep, st);
     else if (shape == 4) launch_fused_shape<T, Tile4>(L, sweep, st);
+    else if (shape == 5) launch_fused_shape<T, Tile5>(L, sweep, st);
     else launch_fused_shape<T, Tile0>(L, sweep, st);
 }
 

@@ -42,6 +42,7 @@ using TT1 = TShape<32, 32, 128>;
 using TT2 = TShape<64, 64, 512>;
 using TT3 = TShape<32, 64, 512>;
 using TT4 = TShape<32, 32, 256>;
+using TT5 = TShape<32, 32, 512>;
 
 template <typename TS, int STAGES>
 struct TmaSmem {
@@ -397,7 +398,7 @@ int g_sms = 0;
 }  // namespace
 
 void prepare_sweep_tma() {
-    set_attrs<TT0>(); set_attrs<TT1>(); set_attrs<TT2>(); set_attrs<TT3>(); set_attrs<TT4>();
+    set_attrs<TT0>(); set_attrs<TT1>(); set_attrs<TT2>(); set_attrs<TT3>(); set_attrs<TT4>(); set_attrs<TT5>();
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_sms < 1) g_sms = 1;
@@ -408,6 +409,7 @@ bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M) {
     if (shape == 2) return encode_shape<TT2>(L, *M);
     if (shape == 3) return encode_shape<TT3>(L, *M);
     if (shape == 4) return encode_shape<TT4>(L, *M);
+    if (shape == 5) return encode_shape<TT5>(L, *M);
     return encode_shape<TT0>(L, *M);
 }
 
@@ -416,6 +418,7 @@ void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const Swe
     else if (shape == 2) launch_shape<TT2>(L, sweep, M, g_sms, err, st);
     else if (shape == 3) launch_shape<TT3>(L, sweep, M, g_sms, err, st);
     else if (shape == 4) launch_shape<TT4>(L, sweep, M, g_sms, err, st);
+    else if (shape == 5) launch_shape<TT5>(L, sweep, M, g_sms, err, st);
     else launch_shape<TT0>(L, sweep, M, g_sms, err, st);
 }
 
