@@ -84,40 +84,58 @@ struct RunCell {
     T f;
 };
 
-// Partial-line update (Sec. 4.3, step III): the rows of one run of cells on a line, coupled
-// through the in-line coefficients, solved exactly by the Thomas algorithm (the system is
-// diagonally dominant, Sec. 3.2).  at(t) returns the RunCell of run position t; endp / endn
-// are the values just before / after the run (their coefficients are zero at a domain edge).
-// The solution is written through put(t, value).
-template <typename T, typename At, typename Put>
-__device__ __forceinline__ void thomas_run(int len, T cdiff, T inv_tau, T endp, T endn, At at,
-                                           Put put) {
-    T cup[kChunk], cdi[kChunk], crh[kChunk];
-    for (int t = 0; t < len; ++t) {
-        RunCell<T> c = at(t);
-        T lo = mul_rn(cdiff, c.ap);
-        T up = mul_rn(cdiff, c.an);
-        T sum = add_rn(add_rn(c.ap, c.an), add_rn(c.ax1, c.ax2));
-        T di = -fma_rn(cdiff, sum, inv_tau);
-        T across = fma_rn(c.ax2, c.ux2, mul_rn(c.ax1, c.ux1));
-        T rhs = fma_rn(-cdiff, across, c.f);
-        if (t == 0) rhs = fma_rn(-lo, endp, rhs);
-        if (t == len - 1) rhs = fma_rn(-up, endn, rhs);
-        if (t > 0) {
-            T wgt = div_relax(lo, cdi[t - 1]);
-            di = fma_rn(-wgt, cup[t - 1], di);
-            rhs = fma_rn(-wgt, crh[t - 1], rhs);
-        }
-        cup[t] = up;
-        cdi[t] = di;
-        crh[t] = rhs;
+// Partial-line update (Sec. 4.3, step III) of one 32-cell piece of a line, by a whole warp
+// (lane t: piece position t).  Each run of member cells (bit t of mk) is a tridiagonal system
+// coupled through the in-line coefficients, with the values just outside the run fixed; the
+// system is diagonally dominant (Sec. 3.2).  Every other lane carries an identity row, so the
+// runs decouple and one parallel cyclic reduction solves all of them at once: each doubling
+// step s = 1, 2, 4, 8, 16 eliminates the couplings to positions t - s and t + s, and the loop
+// stops as soon as no coupling is left (after ceil(log2(longest run)) steps; the remaining
+// steps would change no value).
+//   own         this lane's value at the start of the phase (0 for lanes >= len);
+//   endp, endn  the values just before / after the piece (their coefficients are zero at a
+//               domain edge);  at(t) the RunCell of position t (called for member lanes only).
+// Returns true on member lanes, with the new value in x.  All 32 lanes must call it together,
+// with the same mk, len, endp and endn.
+template <typename T, typename At>
+__device__ __forceinline__ bool pcr_piece(uint32_t mk, int len, T cdiff, T inv_tau, T own, T endp, T endn, At at,
+                                          T &x) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool mem = (mk >> lane) & 1u;
+    T prevv = __shfl_up_sync(kFull, own, 1), nextv = __shfl_down_sync(kFull, own, 1);
+    if (lane == 0) prevv = endp;
+    if (lane == len - 1) nextv = endn;
+    T a = T(0), b = T(1), c = T(0), d = T(0);
+    if (mem) {
+        const RunCell<T> cc = at(lane);
+        const T lo = mul_rn(cdiff, cc.ap), up = mul_rn(cdiff, cc.an);
+        const T sum = add_rn(add_rn(cc.ap, cc.an), add_rn(cc.ax1, cc.ax2));
+        b = -fma_rn(cdiff, sum, inv_tau);
+        const T across = fma_rn(cc.ax2, cc.ux2, mul_rn(cc.ax1, cc.ux1));
+        d = fma_rn(-cdiff, across, cc.f);
+        const bool pm = lane > 0 && ((mk >> (lane - 1)) & 1u);
+        const bool nm = lane < 31 && lane + 1 < len && ((mk >> (lane + 1)) & 1u);
+        if (pm) a = lo; else d = fma_rn(-lo, prevv, d);
+        if (nm) c = up; else d = fma_rn(-up, nextv, d);
     }
-    T x = div_relax(crh[len - 1], cdi[len - 1]);
-    put(len - 1, x);
-    for (int t = len - 2; t >= 0; --t) {
-        x = div_relax(fma_rn(-cup[t], x, crh[t]), cdi[t]);
-        put(t, x);
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        if (!__any_sync(kFull, a != T(0) || c != T(0))) break;
+        T am = __shfl_up_sync(kFull, a, s), bm = __shfl_up_sync(kFull, b, s);
+        T cm = __shfl_up_sync(kFull, c, s), dm = __shfl_up_sync(kFull, d, s);
+        T ap = __shfl_down_sync(kFull, a, s), bp = __shfl_down_sync(kFull, b, s);
+        T cp = __shfl_down_sync(kFull, c, s), dp = __shfl_down_sync(kFull, d, s);
+        if (lane < s) { am = T(0); bm = T(1); cm = T(0); dm = T(0); }
+        if (lane + s > 31) { ap = T(0); bp = T(1); cp = T(0); dp = T(0); }
+        const T al = div_relax(-a, bm), ga = div_relax(-c, bp);
+        b = fma_rn(ga, ap, fma_rn(al, cm, b));
+        d = fma_rn(ga, dp, fma_rn(al, dm, d));
+        a = mul_rn(al, am);
+        c = mul_rn(ga, cp);
     }
+    x = div_relax(d, b);
+    return mem;
 }
 
 // Asynchronous global -> shared copy of one element (4 or 8 bytes); zero-fill when !pred.

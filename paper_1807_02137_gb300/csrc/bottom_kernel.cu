@@ -169,16 +169,12 @@ __device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
             __syncwarp();
             for (int pc = 0; pc < npieces; ++pc) {
                 const uint32_t mk = mks[pc];
-                const uint32_t starts = mk & ~(mk << 1);
-                if (!((starts >> lane) & 1u)) continue;
-                const int t0 = pc * 32, len = min(32, llen - t0);
-                const uint32_t rest = ~(mk >> lane);
-                const int a0 = lane, rl = rest ? __ffs(rest) - 1 : 32 - lane;
-                const float endp = a0 == 0 ? ev[2 * pc] : B.u[base + (t0 + a0 - 1) * step];
-                const float endn = (a0 + rl == len) ? ev[2 * pc + 1] : B.u[base + (t0 + a0 + rl) * step];
+                if (!mk) continue;   // the whole warp
+                const int t0 = pc * 32, len = min(32, llen - t0), tt = t0 + lane;
+                const float own = lane < len ? B.u[base + tt * step] : 0.f;
                 auto at = [&](int r) -> RunCell<float> {
-                    const int tt = t0 + a0 + r, o = base + tt * step;
-                    const int i = rowwise ? line : tt, j = rowwise ? tt : line;
+                    const int o = base + (t0 + r) * step;
+                    const int i = rowwise ? line : t0 + r, j = rowwise ? t0 + r : line;
                     const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
                     const int oS = hS ? o + m : o, oN = hN ? o - m : o, oE = hE ? o + 1 : o, oW = hW ? o - 1 : o;
                     const float gc = B.G[o];
@@ -190,8 +186,9 @@ __device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
                     c.f = B.f[o];
                     return c;
                 };
-                thomas_run<float>(rl, B.cdiff, B.inv_tau, endp, endn, at,
-                                  [&](int r, float x) { B.u[base + (t0 + a0 + r) * step] = x; });
+                float x;
+                if (pcr_piece<float>(mk, len, B.cdiff, B.inv_tau, own, ev[2 * pc], ev[2 * pc + 1], at, x))
+                    B.u[base + tt * step] = x;
             }
             __syncwarp();
         }

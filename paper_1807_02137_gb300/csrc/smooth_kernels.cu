@@ -15,6 +15,7 @@
 //     is chosen per grid) with a 4-cell halo, recomputing the halo redundantly so that no tile
 //     depends on another within a sweep.
 #include "arith.cuh"
+#include "line_phase.cuh"
 
 namespace segmg {
 
@@ -137,8 +138,8 @@ __global__ void __launch_bounds__(256) k_rb(LevelView<T> L, int colour, int swee
     L.u[o] = v;
 }
 
-// One warp per (line, 32-cell piece); groups are read from upre (the values at the start of
-// the phase) and written to u.
+// One warp per (line, 32-cell piece), solved together by pcr_piece; groups are read from upre
+// (the values at the start of the phase) and written to u.
 template <typename T>
 __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int parity) {
     const int n = L.n, m = L.m, p = L.pitch;
@@ -155,13 +156,9 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
     };
     const uint32_t mask = rowwise ? L.mrow[((size_t)sweep * n + line) * L.npm + piece]
                                   : L.mcol[((size_t)(sweep - 2) * m + line) * L.npn + piece];
-    uint32_t starts = mask & ~(mask << 1);
-    if (!((starts >> lane) & 1u)) return;
-    uint32_t rest = ~(mask >> lane);
-    int rl = rest ? __ffs(rest) - 1 : 32 - lane;
+    if (!mask) return;   // the whole warp
     const T *up = L.upre;
-    auto at = [&](int s) -> RunCell<T> {
-        int t = lane + s;
+    auto at = [&](int t) -> RunCell<T> {
         int i = rowwise ? line : t0 + t, j = rowwise ? t0 + t : line;
         size_t o = cell(t);
         bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
@@ -175,11 +172,12 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
         c.f = L.f[o];
         return c;
     };
-    int ta = t0 + lane, tb = t0 + lane + rl - 1;      // first / last position along the line
+    const T own = lane < len ? up[cell(lane)] : T(0);
     T endp = T(0), endn = T(0);
-    if (ta > 0) endp = up[rowwise ? (size_t)line * p + ta - 1 : (size_t)(ta - 1) * p + line];
-    if (tb + 1 < llen) endn = up[rowwise ? (size_t)line * p + tb + 1 : (size_t)(tb + 1) * p + line];
-    thomas_run<T>(rl, L.cdiff, L.inv_tau, endp, endn, at, [&](int s, T x) { L.u[cell(lane + s)] = x; });
+    if (t0 > 0) endp = up[rowwise ? (size_t)line * p + t0 - 1 : (size_t)(t0 - 1) * p + line];
+    if (t0 + len < llen) endn = up[rowwise ? (size_t)line * p + t0 + len : (size_t)(t0 + len) * p + line];
+    T x;
+    if (pcr_piece<T>(mask, len, L.cdiff, L.inv_tau, own, endp, endn, at, x)) L.u[cell(lane)] = x;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -200,7 +198,6 @@ template <int OH_, int OW_, int NT_>
 struct TileShape {
     static constexpr int OH = OH_, OW = OW_, NT = NT_;
     static constexpr int RH = OH + 2 * kH, RW = OW + 2 * kH, HW = RW / 2;
-    static constexpr int MaxTasks = 2 * (OH > OW ? OH : OW) + 8;
     // member-mask words per region line: OW/32 + 2 pieces along a row, OH/32 + 2 along a column
     static constexpr int RowPieces = OW / 32 + 2, ColPieces = OH / 32 + 2;
     static constexpr int MkLines = RH > RW ? RH : RW, MkPieces = RowPieces > ColPieces ? RowPieces : ColPieces;
@@ -218,7 +215,6 @@ struct FusedSmem {
     T G[2][TS::RH][TS::HW];
     T f[2][TS::RH][TS::HW];
     uint32_t mk[TS::MkLines][TS::MkPieces];   // rowwise: [region row][piece]; colwise: [region column][piece]
-    T endv[TS::MaxTasks][2];
 };
 
 #define SW_AT(arr, a, b) S.arr[((a) + (b)) & 1][a][(b) >> 1]
@@ -315,6 +311,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
         }
     }
     // ---- member masks of every line piece that touches the region (zero outside the domain)
+    bool lm = false;   // a piece the line phases solve has a member
     if (rowwise) {
         for (int q = tid; q < kRH * kRowPieces; q += kThreads) {
             const int a = q / kRowPieces, pc = q % kRowPieces;
@@ -323,6 +320,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
             if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm)
                 w = __ldg(L.mrow + ((size_t)SWEEP * n + gi) * L.npm + piece);
             S.mk[a][pc] = w;
+            lm |= solves_word<kH, kOH, kOW, true>(a, pc, w);
         }
     } else {
         for (int q = tid; q < kRW * kColPieces; q += kThreads) {
@@ -332,9 +330,10 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
             if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn)
                 w = __ldg(L.mcol + ((size_t)(SWEEP - 2) * m + gj) * L.npn + piece);
             S.mk[b][pc] = w;
+            lm |= solves_word<kH, kOH, kOW, false>(b, pc, w);
         }
     }
-    __syncthreads();
+    const bool lines = __syncthreads_or(lm);
     // ---- checkerboard phases (distance 3 then 2 from the output tile)
     const bool interior = i0 - kH >= 0 && i0 - kH + kRH <= n && j0 - kH >= 0 && j0 - kH + kRW <= m;
 #pragma unroll
@@ -348,78 +347,12 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
         }
         __syncthreads();
     }
-    // ---- partial-line phases: lines at distance 1, then 0, one parity each.  A task is one
-    // piece of one line: rowwise the 32-column pieces of the output, colwise its 32-row pieces
-    // (mask index 1 + pc: the region starts 4 cells before the first output piece).
-    constexpr int npc = rowwise ? kOW / 32 : kOH / 32;
-    const int len_lim = rowwise ? m : n, gl_lim = rowwise ? n : m;
-#pragma unroll
-    for (int ph = 0; ph < 2; ++ph) {
-        const int parity = rev ? 1 - ph : ph, dist = 1 - ph;
-        const int lfirst = kH - dist;
-        const int ntask = ((rowwise ? kOH : kOW) + 2 * dist) * npc;
-        // step a: the end values at the piece boundaries, read before any run is solved
-        for (int t = tid; t < ntask; t += kThreads) {
-            const int li = lfirst + t / npc, pc = t % npc;
-            const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
-            const int gstart = rowwise ? j0 + 32 * pc : i0 + 32 * pc;
-            const int s0 = kH + 32 * pc;
-            const bool ok = gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim;
-            const int len = ok ? min(32, len_lim - gstart) : 0;
-            const uint32_t mk = ok ? S.mk[li][1 + pc] : 0u;
-            T e0 = T(0), e1 = T(0);
-            if (mk) {
-                if (gstart > 0) e0 = rowwise ? SW_AT(u, li, s0 - 1) : SW_AT(u, s0 - 1, li);
-                if (gstart + len < len_lim) e1 = rowwise ? SW_AT(u, li, s0 + len) : SW_AT(u, s0 + len, li);
-            }
-            S.endv[t][0] = e0;
-            S.endv[t][1] = e1;
-        }
-        __syncthreads();
-        // step b: every run of every task, one thread per task
-        for (int t = tid; t < ntask; t += kThreads) {
-            const int li = lfirst + t / npc, pc = t % npc;
-            const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
-            const int gstart = rowwise ? j0 + 32 * pc : i0 + 32 * pc;
-            if (!(gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim)) continue;
-            const uint32_t mk = S.mk[li][1 + pc];
-            if (!mk) continue;
-            const int s0 = kH + 32 * pc;
-            const int len = min(32, len_lim - gstart);
-            // runs in order of their first cell, found with bit operations on the mask
-            for (uint32_t starts = mk & ~(mk << 1); starts; starts &= starts - 1) {
-                const int a0 = __ffs(starts) - 1;
-                const uint32_t rest = ~(mk >> a0);
-                const int rl = rest ? __ffs(rest) - 1 : 32 - a0;
-                const T endp = a0 == 0 ? S.endv[t][0] : (rowwise ? SW_AT(u, li, s0 + a0 - 1) : SW_AT(u, s0 + a0 - 1, li));
-                const T endn = (a0 + rl == len) ? S.endv[t][1] : (rowwise ? SW_AT(u, li, s0 + a0 + rl) : SW_AT(u, s0 + a0 + rl, li));
-                auto at = [&](int r) -> RunCell<T> {
-                    const int pos = s0 + a0 + r;
-                    const int a = rowwise ? li : pos, b = rowwise ? pos : li;
-                    const int gi = rowwise ? gline : i0 - kH + pos, gj = rowwise ? j0 - kH + pos : gline;
-                    const bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
-                    const T gc = SW_AT(G, a, b);
-                    const T aS = face(gc, SW_AT(G, a + 1, b), hS), aN = face(gc, SW_AT(G, a - 1, b), hN);
-                    const T aE = face(gc, SW_AT(G, a, b + 1), hE), aW = face(gc, SW_AT(G, a, b - 1), hW);
-                    RunCell<T> c;
-                    if (rowwise) {
-                        c.ap = aW; c.an = aE; c.ax1 = aS; c.ax2 = aN;
-                        c.ux1 = SW_AT(u, a + 1, b); c.ux2 = SW_AT(u, a - 1, b);
-                    } else {
-                        c.ap = aN; c.an = aS; c.ax1 = aE; c.ax2 = aW;
-                        c.ux1 = SW_AT(u, a, b + 1); c.ux2 = SW_AT(u, a, b - 1);
-                    }
-                    c.f = SW_AT(f, a, b);
-                    return c;
-                };
-                thomas_run<T>(rl, L.cdiff, L.inv_tau, endp, endn, at, [&](int r, T xv) {
-                    const int pos = s0 + a0 + r;
-                    if (rowwise) SW_AT(u, li, pos) = xv; else SW_AT(u, pos, li) = xv;
-                });
-            }
-        }
-        __syncthreads();
-    }
+    // ---- partial-line phases (line_phase.cuh), skipped when no piece of the tile has a member
+    if (lines)
+        tile_line_phases<T, kH, kOH, kOW, kThreads, rowwise, rev>(
+            [&](int a, int b) -> T & { return SW_AT(u, a, b); }, [&](int a, int b) { return SW_AT(G, a, b); },
+            [&](int a, int b) { return SW_AT(f, a, b); }, [&](int li, int pc) { return S.mk[li][1 + pc]; }, i0, j0,
+            n, m, L.cdiff, L.inv_tau);
     // ---- write the output tile (vectors; padding columns keep their loaded values)
     for (int q = tid; q < kOH * NVO; q += kThreads) {
         const int a = kH + q / NVO, b0 = kH + (q % NVO) * VN;

@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "arith.cuh"
+#include "line_phase.cuh"
 
 namespace segmg {
 
@@ -32,7 +33,6 @@ template <int OH_, int OW_, int NT_>
 struct TShape {
     static constexpr int OH = OH_, OW = OW_, NT = NT_;
     static constexpr int RH = OH + 2 * kH, RW = OW + 2 * kH;
-    static constexpr int MaxTasks = 2 * (OH > OW ? OH : OW) + 8;
     static constexpr int RowPieces = OW / 32 + 2, ColPieces = OH / 32 + 2;
     static constexpr int MkLines = RH > RW ? RH : RW, MkPieces = RowPieces > ColPieces ? RowPieces : ColPieces;
     static constexpr int BoxBytes = RH * RW * 4;
@@ -48,7 +48,6 @@ template <typename TS, int STAGES>
 struct TmaSmem {
     float box[STAGES][3][TS::RH][TS::RW];      // [stage][u, G, f][row][column]
     uint32_t mk[TS::MkLines][TS::MkPieces];    // member masks of the tile (as k_sweep)
-    float endv[TS::MaxTasks][2];
     unsigned long long bar[STAGES];            // one mbarrier per stage
 };
 
@@ -176,6 +175,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
         const int ty = tile / ntx, tx = tile - ty * ntx;
         const int i0 = ty * kOH, j0 = tx * kOW;
         // member masks of every line piece that touches the box (zero outside the grid)
+        bool lm = false;   // a piece the line phases solve has a member
         if (rowwise) {
             for (int q = tid; q < kRH * kRowPieces; q += TS::NT) {
                 const int a = q / kRowPieces, pc = q % kRowPieces;
@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
                 if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm)
                     w = __ldg(L.mrow + ((size_t)SWEEP * n + gi) * L.npm + piece);
                 S.mk[a][pc] = w;
+                lm |= solves_word<kH, kOH, kOW, true>(a, pc, w);
             }
         } else {
             for (int q = tid; q < kRW * kColPieces; q += TS::NT) {
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
                 if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn)
                     w = __ldg(L.mcol + ((size_t)(SWEEP - 2) * m + gj) * L.npn + piece);
                 S.mk[b][pc] = w;
+                lm |= solves_word<kH, kOH, kOW, false>(b, pc, w);
             }
         }
         const bool ok = mbar_wait(&S.bar[st], parity);
@@ -206,6 +208,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
             __syncthreads();
             return;
         }
+        const bool lines = __syncthreads_or(lm);
         float (*u)[kRW] = S.box[st][0];
         const float (*G)[kRW] = S.box[st][1];
         const float (*f)[kRW] = S.box[st][2];
@@ -222,73 +225,12 @@ __global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const 
             }
             __syncthreads();
         }
-        // ---- partial-line phases (as k_sweep): lines at distance 1, then 0, one parity each
-        constexpr int npc = rowwise ? kOW / 32 : kOH / 32;
-        const int len_lim = rowwise ? m : n, gl_lim = rowwise ? n : m;
-#pragma unroll
-        for (int ph = 0; ph < 2; ++ph) {
-            const int parity = rev ? 1 - ph : ph, dist = 1 - ph;
-            const int lfirst = kH - dist;
-            const int ntask = ((rowwise ? kOH : kOW) + 2 * dist) * npc;
-            for (int t = tid; t < ntask; t += TS::NT) {
-                const int li = lfirst + t / npc, pc = t % npc;
-                const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
-                const int gstart = rowwise ? j0 + 32 * pc : i0 + 32 * pc;
-                const int s0 = kH + 32 * pc;
-                const bool okl = gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim;
-                const int len = okl ? min(32, len_lim - gstart) : 0;
-                const uint32_t mk = okl ? S.mk[li][1 + pc] : 0u;
-                float e0 = 0.f, e1 = 0.f;
-                if (mk) {
-                    if (gstart > 0) e0 = rowwise ? u[li][s0 - 1] : u[s0 - 1][li];
-                    if (gstart + len < len_lim) e1 = rowwise ? u[li][s0 + len] : u[s0 + len][li];
-                }
-                S.endv[t][0] = e0;
-                S.endv[t][1] = e1;
-            }
-            __syncthreads();
-            for (int t = tid; t < ntask; t += TS::NT) {
-                const int li = lfirst + t / npc, pc = t % npc;
-                const int gline = rowwise ? i0 - kH + li : j0 - kH + li;
-                const int gstart = rowwise ? j0 + 32 * pc : i0 + 32 * pc;
-                if (!(gline >= 0 && gline < gl_lim && (gline & 1) == parity && gstart < len_lim)) continue;
-                const uint32_t mk = S.mk[li][1 + pc];
-                if (!mk) continue;
-                const int s0 = kH + 32 * pc;
-                const int len = min(32, len_lim - gstart);
-                for (uint32_t starts = mk & ~(mk << 1); starts; starts &= starts - 1) {
-                    const int a0 = __ffs(starts) - 1;
-                    const uint32_t rest = ~(mk >> a0);
-                    const int rl = rest ? __ffs(rest) - 1 : 32 - a0;
-                    const float endp = a0 == 0 ? S.endv[t][0] : (rowwise ? u[li][s0 + a0 - 1] : u[s0 + a0 - 1][li]);
-                    const float endn = (a0 + rl == len) ? S.endv[t][1] : (rowwise ? u[li][s0 + a0 + rl] : u[s0 + a0 + rl][li]);
-                    auto at = [&](int r) -> RunCell<float> {
-                        const int pos = s0 + a0 + r;
-                        const int a = rowwise ? li : pos, b = rowwise ? pos : li;
-                        const int gi = rowwise ? gline : i0 - kH + pos, gj = rowwise ? j0 - kH + pos : gline;
-                        const bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
-                        const float gc = G[a][b];
-                        const float aS = face(gc, G[a + 1][b], hS), aN = face(gc, G[a - 1][b], hN);
-                        const float aE = face(gc, G[a][b + 1], hE), aW = face(gc, G[a][b - 1], hW);
-                        RunCell<float> c;
-                        if (rowwise) {
-                            c.ap = aW; c.an = aE; c.ax1 = aS; c.ax2 = aN;
-                            c.ux1 = u[a + 1][b]; c.ux2 = u[a - 1][b];
-                        } else {
-                            c.ap = aN; c.an = aS; c.ax1 = aE; c.ax2 = aW;
-                            c.ux1 = u[a][b + 1]; c.ux2 = u[a][b - 1];
-                        }
-                        c.f = f[a][b];
-                        return c;
-                    };
-                    thomas_run<float>(rl, L.cdiff, L.inv_tau, endp, endn, at, [&](int r, float xv) {
-                        const int pos = s0 + a0 + r;
-                        if (rowwise) u[li][pos] = xv; else u[pos][li] = xv;
-                    });
-                }
-            }
-            __syncthreads();
-        }
+        // ---- partial-line phases (line_phase.cuh), skipped when no piece of the tile has a member
+        if (lines)
+            tile_line_phases<float, kH, kOH, kOW, TS::NT, rowwise, rev>(
+                [&](int a, int b) -> float & { return u[a][b]; }, [&](int a, int b) { return G[a][b]; },
+                [&](int a, int b) { return f[a][b]; }, [&](int li, int pc) { return S.mk[li][1 + pc]; }, i0, j0, n,
+                m, L.cdiff, L.inv_tau);
         // ---- the output tile to uout (16-byte vectors; padding columns keep their box values)
         constexpr int NVO = kOW / 4;
         for (int q = tid; q < kOH * NVO; q += TS::NT) {
