@@ -50,25 +50,39 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
                        L.has_rhs ? L.rhs : nullptr, i0, j0, n, m, p, tid);
     }
     __syncthreads();
-    for (int q = tid; q < 34 * 34; q += 256) {
-        int a = 1 + q / 34, b = 1 + q % 34;
-        int gi = i0 - 2 + a, gj = j0 - 2 + b;
+    // Lane = tile column, warp row wy handles tile rows wy, wy + 8, wy + 16, wy + 24.  Interior
+    // tiles (every cell with four faces, the G ring inside the grid) skip the bounds tests.
+    const int lane = threadIdx.x, wy = threadIdx.y;
+    const bool interior = i0 >= 1 && j0 >= 1 && i0 + 33 <= n && j0 + 33 <= m;
+    auto g_at = [&](int a, int b, bool check) {   // G of box cell (a, b), 1 <= a, b <= 34
+        const int gi = i0 - 2 + a, gj = j0 - 2 + b;
         T g = T(0);
-        if (gi >= 0 && gi < n && gj >= 0 && gj < m)
+        if (!check || (gi >= 0 && gi < n && gj >= 0 && gj < m))
             g = cell_G((L.wb || !kStage) ? weight_at(L, (size_t)gi * p + gj) : sW[kStage ? a : 0][kStage ? b : 0],
-                       sP[a + 1][b], sP[a - 1][b],
-                       sP[a][b + 1], sP[a][b - 1], sU[a + 1][b], sU[a - 1][b], sU[a][b + 1], sU[a][b - 1],
-                       L.inv_2h, L.beta);
+                       sP[a + 1][b], sP[a - 1][b], sP[a][b + 1], sP[a][b - 1], sU[a + 1][b], sU[a - 1][b],
+                       sU[a][b + 1], sU[a][b - 1], L.inv_2h, L.beta);
         sG[a][b] = g;
+    };
+    // G on the 34 x 34 box rows / columns 1..34: the 32 tile columns by lane, then the two ring
+    // columns (68 cells) packed into whole warps
+    if (interior) {
+        for (int a = 1 + wy; a <= 34; a += 8) g_at(a, lane + 2, false);
+        if (tid < 68) g_at(1 + (tid >> 1), (tid & 1) ? 34 : 1, false);
+    } else {
+        for (int a = 1 + wy; a <= 34; a += 8) g_at(a, lane + 2, true);
+        if (tid < 68) g_at(1 + (tid >> 1), (tid & 1) ? 34 : 1, true);
     }
     __syncthreads();
     const T ar = area ? T(area[L.level]) : T(0);
-    for (int q = tid; q < 1024; q += 256) {
-        int ti = q / 32, tj = q % 32, a = ti + 2, b = tj + 2;
-        int gi = i0 + ti, gj = j0 + tj;
+    const int gj = j0 + lane, b = lane + 2;
+    const int lenr = min(32, m - j0), lenc = min(32, n - i0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ti = wy + 8 * k, a = ti + 2, gi = i0 + ti;
         uint8_t star = 0;
-        if (gi < n && gj < m) {
-            bool hS = gi + 1 < n, hN = gi > 0, hE = gj + 1 < m, hW = gj > 0;
+        if (interior || (gi < n && gj < m)) {
+            const bool hS = interior || gi + 1 < n, hN = interior || gi > 0;
+            const bool hE = interior || gj + 1 < m, hW = interior || gj > 0;
             T gc = sG[a][b];
             T aS = face(gc, sG[a + 1][b], hS), aN = face(gc, sG[a - 1][b], hN);
             T aE = face(gc, sG[a][b + 1], hE), aW = face(gc, sG[a][b - 1], hW);
@@ -78,8 +92,8 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
             ds = fma_rn(aE, sub_rn(sP[a][b + 1], pc), ds);
             ds = fma_rn(aW, sub_rn(sP[a][b - 1], pc), ds);
             size_t o = (size_t)gi * p + gj;
-            T base = add_rn(kStage ? sF[kStage ? ti : 0][kStage ? tj : 0] : L.F[o], ar);
-            if (L.has_rhs) base = add_rn(base, kStage ? sR[kStage ? ti : 0][kStage ? tj : 0] : L.rhs[o]);
+            T base = add_rn(kStage ? sF[kStage ? ti : 0][kStage ? lane : 0] : L.F[o], ar);
+            if (L.has_rhs) base = add_rn(base, kStage ? sR[kStage ? ti : 0][kStage ? lane : 0] : L.rhs[o]);
             L.f[o] = fma_rn(-L.cdiff, ds, base);
             L.G[o] = gc;
             // jump set D (Sec. 4.1): max > Sigma * min over the faces inside the domain;
@@ -91,30 +105,22 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
             const int am = vS == mn ? 0 : (vN == mn ? 1 : (vE == mn ? 2 : 3));
             const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
             if (cnt >= 2 && mx > mul_rn(L.Sigma, mn)) star = (uint8_t)(1u << am);
+            if (L.cls) L.cls[o] = star;
         }
-        sStar[ti][tj] = star;
-        if (L.cls && gi < n && gj < m) L.cls[(size_t)gi * p + gj] = star;
+        sStar[ti][lane] = star;
+        // the row piece of this warp row: sweeps A (bit 0) and B (bit 1); lane 0 / 1 store
+        const uint32_t mA = members_of(__ballot_sync(0xffffffffu, star & 1u), lenr);
+        const uint32_t mB = members_of(__ballot_sync(0xffffffffu, star & 2u), lenr);
+        if (lane < 2 && gi < n) L.mrow[((size_t)lane * n + gi) * L.npm + (j0 >> 5)] = lane ? mB : mA;
     }
     __syncthreads();
-    const int warp = tid / 32, lane = tid % 32;
-    const int lenr = min(32, m - j0), lenc = min(32, n - i0);
-    for (int r = warp; r < 32; r += 8) {             // row pieces: sweeps A, B
-        uint8_t s = sStar[r][lane];
-        uint32_t mA = members_of(__ballot_sync(0xffffffffu, s & 1u), lenr);
-        uint32_t mB = members_of(__ballot_sync(0xffffffffu, s & 2u), lenr);
-        if (lane == 0 && i0 + r < n) {
-            L.mrow[((size_t)0 * n + i0 + r) * L.npm + (j0 >> 5)] = mA;
-            L.mrow[((size_t)1 * n + i0 + r) * L.npm + (j0 >> 5)] = mB;
-        }
-    }
-    for (int c = warp; c < 32; c += 8) {             // column pieces: sweeps C, D
-        uint8_t s = sStar[lane][c];
-        uint32_t mC = members_of(__ballot_sync(0xffffffffu, s & 4u), lenc);
-        uint32_t mD = members_of(__ballot_sync(0xffffffffu, s & 8u), lenc);
-        if (lane == 0 && j0 + c < m) {
-            L.mcol[((size_t)0 * m + j0 + c) * L.npn + (i0 >> 5)] = mC;
-            L.mcol[((size_t)1 * m + j0 + c) * L.npn + (i0 >> 5)] = mD;
-        }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {                   // column pieces: sweeps C, D
+        const int c = wy + 8 * k;
+        const uint8_t sc = sStar[lane][c];
+        const uint32_t mC = members_of(__ballot_sync(0xffffffffu, sc & 4u), lenc);
+        const uint32_t mD = members_of(__ballot_sync(0xffffffffu, sc & 8u), lenc);
+        if (lane < 2 && j0 + c < m) L.mcol[((size_t)lane * m + j0 + c) * L.npn + (i0 >> 5)] = lane ? mD : mC;
     }
 }
 
