@@ -76,6 +76,10 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
     const T ar = area ? T(area[L.level]) : T(0);
     const int gj = j0 + lane, b = lane + 2;
     const int lenr = min(32, m - j0), lenc = min(32, n - i0);
+    // The 16 pieces of this warp (rows wy + 8k: sweeps A, B; columns wy + 8k: sweeps C, D) are
+    // collected as ballots into lanes 0..15 and finished by one members_of: lane 2k + s holds
+    // row wy + 8k, sweep A (s = 0) or B (s = 1); lane 8 + 2k + s column wy + 8k, C or D.
+    uint32_t bits = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int ti = wy + 8 * k, a = ti + 2, gi = i0 + ti;
@@ -108,19 +112,26 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
             if (L.cls) L.cls[o] = star;
         }
         sStar[ti][lane] = star;
-        // the row piece of this warp row: sweeps A (bit 0) and B (bit 1); lane 0 / 1 store
-        const uint32_t mA = members_of(__ballot_sync(0xffffffffu, star & 1u), lenr);
-        const uint32_t mB = members_of(__ballot_sync(0xffffffffu, star & 2u), lenr);
-        if (lane < 2 && gi < n) L.mrow[((size_t)lane * n + gi) * L.npm + (j0 >> 5)] = lane ? mB : mA;
+        const uint32_t bA = __ballot_sync(0xffffffffu, star & 1u), bB = __ballot_sync(0xffffffffu, star & 2u);
+        if (lane == 2 * k) bits = bA;
+        if (lane == 2 * k + 1) bits = bB;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {                   // column pieces: sweeps C, D
-        const int c = wy + 8 * k;
-        const uint8_t sc = sStar[lane][c];
-        const uint32_t mC = members_of(__ballot_sync(0xffffffffu, sc & 4u), lenc);
-        const uint32_t mD = members_of(__ballot_sync(0xffffffffu, sc & 8u), lenc);
-        if (lane < 2 && j0 + c < m) L.mcol[((size_t)lane * m + j0 + c) * L.npn + (i0 >> 5)] = lane ? mD : mC;
+    for (int k = 0; k < 4; ++k) {
+        const uint8_t sc = sStar[lane][wy + 8 * k];
+        const uint32_t bC = __ballot_sync(0xffffffffu, sc & 4u), bD = __ballot_sync(0xffffffffu, sc & 8u);
+        if (lane == 8 + 2 * k) bits = bC;
+        if (lane == 9 + 2 * k) bits = bD;
+    }
+    if (lane < 16) {
+        const int line = wy + 8 * ((lane >> 1) & 3), s = lane & 1;
+        const uint32_t mk = members_of(bits, lane < 8 ? lenr : lenc);
+        if (lane < 8) {
+            if (i0 + line < n) L.mrow[((size_t)s * n + i0 + line) * L.npm + (j0 >> 5)] = mk;
+        } else if (j0 + line < m) {
+            L.mcol[((size_t)s * m + j0 + line) * L.npn + (i0 >> 5)] = mk;
+        }
     }
 }
 
