@@ -189,10 +189,11 @@ def run_ours(args):
     mask = torch.empty((n, m), dtype=torch.uint8, device=dev)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MB > L2
 
-    # fused-sweep tile shapes: measured once per grid before timing (mg_autotune; the shapes never
-    # change results, only speed)
+    # fused-sweep tile shapes and the first grid of the bottom kernel: measured once before timing
+    # (mg_autotune; they never change results, only speed)
     s.begin_step()
     shapes = s.autotune(reps=3)
+    bottom_level = s.stats()["bottom_level"]
     s.end_step()
 
     def step():
@@ -311,7 +312,7 @@ def run_ours(args):
             "config": {"workload": f"{WORKLOAD}: {n}x{m} FP32 image, 12 ellipses, 8 markers, 9 grids, "
                                    "V(2,2), tau 1, Spencer-Chen, one pseudo-time step to rho <= 1e-6",
                        "l2": "flushed (512 MB write) between timed steps",
-                       "tile_shapes": shapes,
+                       "tile_shapes": shapes, "bottom_kernel_from_grid": bottom_level,
                        "cycles_per_step": float(np.mean(cycles)), "rho_last": float(max(rhos)),
                        "parallelism": f"replicas x{ws}"},
             "e2e": {"value": ws * n * m / (e2e_ms_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -114,6 +114,7 @@ typedef struct {
     long long launches;    /* kernels launched by the handle so far (graph nodes included) */
     long long learned_accepted;   /* V-cycles run with learned relaxation weights and kept */
     long long learned_rejected;   /* ... and rejected (rerun with the plain smoother) */
+    int bottom_level;      /* first grid of the one-block bottom kernel, -1 when it is not used */
 } mg_stats;
 
 /* Optional device allocator (for example a framework's caching allocator).  alloc returns a
@@ -202,10 +203,13 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
 /* Tile-shape autotuner (a tuning step of this implementation; the paper has no counterpart):
  * inside a pseudo-time step (after mg_begin_step), times one outer smoothing iteration of every
  * grid but the coarsest with each fused-sweep tile shape (rows x columns of cells, threads per
- * tile: 0 = 32x64/256, 1 = 32x32/128, 2 = 64x64/512, 3 = 32x64/512, 4 = 32x32/256, 5 = 32x32/512) over
- * `reps` repetitions and keeps the fastest per grid; writes the choices to
- * shapes[0..levels-2] if not NULL.  The state is restored, and the results of later solves do
- * not depend on the shapes (every shape computes the same values).  Waits. */
+ * tile: 0 = 32x64/256, 1 = 32x32/128, 2 = 64x64/512, 3 = 32x64/512, 4 = 32x32/256,
+ * 5 = 32x32/512) over `reps` repetitions and keeps the fastest per grid; writes the choices to
+ * shapes[0..levels-2] if not NULL.  Then, when the bottom kernel is in use, it times `reps`
+ * V-cycles with the bottom kernel starting at the largest grid that fits and at the next two
+ * coarser grids, and keeps the fastest (mg_stats.bottom_level).  The state is restored, and the
+ * results of later solves do not depend on these choices (every choice computes the same
+ * values).  Waits. */
 int mg_autotune(mg_handle h, int reps, int *shapes);
 /* Sets the fused-sweep tile shape of grids 0..levels-2 (values 0..5 as above). */
 int mg_set_tile_shapes(mg_handle h, const int *shapes);
@@ -285,6 +289,13 @@ int mg_energy(mg_handle h, double *E);
  * results are identical.  enable = 1 (the default at set-up) or 0; *first_level (may be NULL)
  * gets the first grid it covers, -1 when it does not apply.  Errors: MG_ERR_ARG. */
 int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level);
+/* Sets the first grid of the one-block bottom kernel (a tuning step of this implementation; the
+ * paper has no counterpart): `level` from the largest grid that fits (the first_level that
+ * mg_set_bottom_kernel(h, 1, ...) reports) to levels - 2, or -1 for none.  A later start runs
+ * more grids through the per-grid kernels; the results are the same either way.  mg_autotune
+ * also chooses it (mg_stats.bottom_level).  Errors: MG_ERR_ARG (level out of that range, or the
+ * bottom kernel does not apply). */
+int mg_set_bottom_level(mg_handle h, int level);
 
 /* Batches (many images at once; no counterpart in the paper): `count` images of
  * their own sizes solved together.  Each V-cycle of mg_batch_solve_step is one CUDA graph

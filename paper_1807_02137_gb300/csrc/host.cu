@@ -107,6 +107,7 @@ struct SolverBase {
     virtual int autotune(int reps, int *out) = 0;
     virtual int set_shapes(const int *shapes) = 0;
     virtual int set_bottom(int enable) = 0;
+    virtual int set_bottom_level(int level) = 0;
     virtual int energy(double *E) = 0;
     virtual int aos(double dt, int max_iter, double eta, int *iters, double *rho) = 0;
     virtual int set_learned(const float *theta, int mode, int refresh) = 0;
@@ -152,6 +153,7 @@ struct Solver final : SolverBase {
     long long launches = 0, graph_nodes = 0;
     int shape[kMaxLevels] = {};   // fused-sweep tile shape per grid (mg_autotune)
     int lb = -1;                  // first grid of the one-block bottom kernel (-1: not used)
+    int lb_first = -1;            // the largest grid it can start at (-1: it does not apply)
     // learned relaxation weights of the point updates (learned.cu)
     int learn_mode = 0;           // 0 off; 1 per V-cycle acceptance; 2 always; 3 fixed weights
     int learn_refresh = 4;        // V-cycles between inferences
@@ -161,7 +163,8 @@ struct Solver final : SolverBase {
     __nv_bfloat16 *net = nullptr; // BF16 parameters
     T *omega_buf[kMaxLevels] = {};
     bool omega_valid[kMaxLevels] = {};   // the grid's weights are set (fixed) or inferred
-    T *ubak = nullptr;            // finest-grid increment saved before a learned V-cycle
+    T *ubak = nullptr;            // finest-grid increment saved before a learned V-cycle (and
+                                  // while mg_autotune times V-cycles)
     cudaGraphExec_t gexec_l = nullptr, gexec_li = nullptr;   // learned V-cycle; with inference
     long long nodes_l = 0, nodes_li = 0;
     double plain_rate = -1.0;     // contraction of the last plain V-cycle of the step
@@ -288,20 +291,35 @@ struct Solver final : SolverBase {
     // the model is Spencer-Chen, the fused smoother is selected and at least two grids fit in
     // its shared memory; lb is the largest grid that fits.
     int set_bottom(int enable) override {
-        lb = -1;
+        lb = lb_first = -1;
         lb_smem = 0;
-        if (enable && sizeof(T) == 4 && p.model == MG_MODEL_SC && fused()) {
+        if (sizeof(T) == 4 && p.model == MG_MODEL_SC && fused()) {
             int ns[kMaxLevels], ms[kMaxLevels];
             for (int l = 0; l < nlev; ++l) { ns[l] = lv[l].n; ms[l] = lv[l].m; }
             for (int l = nlev - 2; l >= 0; --l) {
                 size_t b = bottom_smem_bytes(ns, ms, l, nlev, p.precision == MG_MIXED);
                 if (b > kBottomSmemMax) break;
-                lb = l;
-                lb_smem = b;
+                lb_first = l;
             }
         }
+        if (enable && lb_first >= 0) use_bottom_from(lb_first);
         drop_graphs();
         return lb;
+    }
+
+    void use_bottom_from(int l) {
+        int ns[kMaxLevels], ms[kMaxLevels];
+        for (int k = 0; k < nlev; ++k) { ns[k] = lv[k].n; ms[k] = lv[k].m; }
+        lb = l;
+        lb_smem = l >= 0 ? bottom_smem_bytes(ns, ms, l, nlev, p.precision == MG_MIXED) : 0;
+    }
+
+    int set_bottom_level(int level) override {
+        if (level != -1 && (lb_first < 0 || level < lb_first || level > nlev - 2))
+            return fail(MG_ERR_ARG, "bottom level out of range (or the bottom kernel does not apply)");
+        use_bottom_from(level);
+        drop_graphs();
+        return MG_OK;
     }
 
     int aos(double dt, int max_iter, double eta_stop, int *iters, double *rhoout) override {
@@ -609,9 +627,50 @@ struct Solver final : SolverBase {
             shape[l] = arg;
             if (out) out[l] = arg;
         }
+        drop_graphs();   // shapes are baked into the graphs
+        int rc = MG_OK;
+        if (lb >= 0 && (learn_mode == 0 || learn_mode == 3)) rc = tune_bottom(reps, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        drop_graphs();   // shapes are baked into the graphs
+        return rc;
+    }
+
+    // Times `reps` V-cycles (after one untimed) with the bottom kernel starting at lb_first,
+    // lb_first + 1 and lb_first + 2 and keeps the fastest; the finest increment (saved in ubak:
+    // a V-cycle writes every other finest-grid scratch field) and the device scalars are
+    // restored after each candidate (the coarse grids are rebuilt by every V-cycle).
+    int tune_bottom(int reps, cudaEvent_t e0, cudaEvent_t e1) {
+        Level<T> &L = lv[0];
+        const size_t row = (size_t)L.m * sizeof(T), pitchb = (size_t)L.pitch * sizeof(T);
+        if (!ubak) CK(cudaMalloc(&ubak, sizeof(T) * (size_t)L.n * L.pitch));
+        Scalars saved;
+        CK(cudaMemcpyAsync(&saved, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const long long launches0 = launches;
+        float best = 1e30f;
+        int arg = lb;
+        for (int cand = lb_first; cand <= std::min(lb_first + 2, nlev - 2); ++cand) {
+            use_bottom_from(cand);
+            drop_graphs();
+            CK(cudaMemcpy2DAsync(ubak, pitchb, L.u, pitchb, row, L.n, cudaMemcpyDeviceToDevice, st));
+            int rc = cycle_plain();   // captures this candidate's graph
+            float t = 0;
+            if (rc == MG_OK) {
+                CK(cudaEventRecord(e0, st));
+                for (int r = 0; r < reps && rc == MG_OK; ++r) rc = cycle_plain();
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                CK(cudaEventElapsedTime(&t, e0, e1));
+            }
+            CK(cudaMemcpy2DAsync(L.u, pitchb, ubak, pitchb, row, L.n, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(dsc, &saved, sizeof(Scalars), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));
+            if (rc != MG_OK) return rc;
+            if (t < best) { best = t; arg = cand; }
+        }
+        launches = launches0;
+        use_bottom_from(arg);
+        drop_graphs();
         return MG_OK;
     }
 
@@ -867,6 +926,7 @@ struct Solver final : SolverBase {
         s->launches = launches;
         s->learned_accepted = learned_acc;
         s->learned_rejected = learned_rej;
+        s->bottom_level = lb;
         return MG_OK;
     }
 
@@ -1435,6 +1495,11 @@ int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level) {
     int lb = h->s->set_bottom(enable);
     if (first_level) *first_level = lb;
     return MG_OK;
+}
+
+int mg_set_bottom_level(mg_handle h, int level) {
+    if (!h) return fail(MG_ERR_ARG, "NULL handle");
+    return h->s->set_bottom_level(level);
 }
 
 int mg_batch_setup(mg_batch *out, int count, const void *const *images, const int *n, const int *m,

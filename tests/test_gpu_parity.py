@@ -244,6 +244,8 @@ def test_autotune_keeps_the_state_and_the_results(segmg):
     s2.begin_step()
     shapes = s2.autotune(reps=1)
     assert len(shapes) == p.levels - 1 and all(0 <= x <= 5 for x in shapes)
+    lb = s2.stats()["bottom_level"]
+    assert lb >= 0 and lb <= p.levels - 2
     s2.end_step()          # the autotuner restored phi: this step changed nothing
     s2.solve_step(1e-6, 50)
     assert np.array_equal(s1.phi().cpu().numpy(), s2.phi().cpu().numpy())
@@ -290,6 +292,33 @@ def test_bottom_kernel_equals_per_grid_kernels(segmg, shape, levels, nu, precisi
     assert np.array_equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1]
     assert stats[0]["picard_last"] == stats[1]["picard_last"]
+
+
+@pytest.mark.parametrize("precision", ["f32", "mixed"])
+def test_every_bottom_level_gives_the_same_result(segmg, precision):
+    # where the one-block bottom kernel starts changes only which kernels run the small grids
+    prec = segmg.MG_MIXED if precision == "mixed" else segmg.MG_F32
+    img, mk, _ = synth.ellipses(256, 256, 8, (8, 128), 6, 0.05, 77)
+    outs = []
+    s, p = gpu_solver(segmg, img, mk, precision=prec, levels=7)
+    first = s.set_bottom_kernel(True)
+    assert first >= 0
+    s.close()
+    for lb in [first, first + 1, first + 2, -1]:
+        s, p = gpu_solver(segmg, img, mk, precision=prec, levels=7)
+        s.set_bottom_level(lb)
+        assert s.stats()["bottom_level"] == lb
+        s.begin_step()
+        rhos = [s.vcycle() for _ in range(3)]
+        outs.append((s.phi().cpu().numpy(), rhos))
+        s.close()
+    for x in outs[1:]:
+        assert np.array_equal(outs[0][0], x[0]) and outs[0][1] == x[1]
+    s, p = gpu_solver(segmg, img, mk, precision=prec, levels=7)
+    for bad in (first - 1, p.levels - 1):
+        with pytest.raises(segmg.SegmgError):
+            s.set_bottom_level(bad)
+    s.close()
 
 
 def test_bottom_kernel_applies_only_where_it_is_exact(segmg):
