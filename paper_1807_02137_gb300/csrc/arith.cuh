@@ -161,16 +161,16 @@ __device__ __forceinline__ int clamp_idx(int v, int hi) { return v < 0 ? 0 : (v 
 // dst[36][37] arrays, indices clamped into the domain (the mirror ghosts of the central
 // differences).  The 36 x 40 window from column j0-4 is read with 16-byte vector loads where it
 // lies inside the domain (per-element clamped loads at the edges); all of a thread's loads are
-// issued before its shared-memory stores.  256 threads.
-template <typename T>
+// issued before its shared-memory stores.  NT threads (tid < NT).
+template <typename T, int NT = 256>
 __device__ __forceinline__ void load_halo2(T (*dA)[37], const T *sA, T (*dB)[37], const T *sB, int i0, int j0,
                                            int n, int m, int p, int tid) {
     using V = typename VecOf<T>::type;
-    constexpr int VN = VecOf<T>::n, NV = 40 / VN, NVEC = 36 * NV, PER = (NVEC + 255) / 256;
+    constexpr int VN = VecOf<T>::n, NV = 40 / VN, NVEC = 36 * NV, PER = (NVEC + NT - 1) / NT;
     T xa[PER][VN], xb[PER][VN];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int q = tid + k * 256;
+        const int q = tid + k * NT;
         if (q >= NVEC) break;
         const int a = q / NV, gi = i0 - 2 + a, gj = j0 - 4 + (q % NV) * VN;
         if (gi >= 0 && gi < n && gj >= 0 && gj + VN <= m) {
@@ -193,7 +193,7 @@ __device__ __forceinline__ void load_halo2(T (*dA)[37], const T *sA, T (*dB)[37]
     }
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int q = tid + k * 256;
+        const int q = tid + k * NT;
         if (q >= NVEC) break;
         const int a = q / NV, b0 = (q % NV) * VN - 2;
 #pragma unroll
@@ -208,16 +208,17 @@ __device__ __forceinline__ void load_halo2(T (*dA)[37], const T *sA, T (*dB)[37]
 }
 
 // Loads the 32 x 32 tile at (i0, j0) of one or two pitched grid functions into dst[32][33]
-// (indices clamped into the domain; those values are never used), vector loads, 256 threads.
-template <typename T>
+// (indices clamped into the domain; those values are never used), vector loads, NT threads.
+template <typename T, int NT = 256>
 __device__ __forceinline__ void load_tile32(T (*dA)[33], const T *sA, T (*dB)[33], const T *sB, int i0, int j0,
                                             int n, int m, int p, int tid) {
     using V = typename VecOf<T>::type;
-    constexpr int VN = VecOf<T>::n, NV = 32 / VN, NVEC = 32 * NV, PER = (NVEC + 255) / 256;
+    constexpr int VN = VecOf<T>::n, NV = 32 / VN, NVEC = 32 * NV, PER = (NVEC + NT - 1) / NT;
     T xa[PER][VN], xb[PER][VN];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int q = tid + k * 256;
+        const int q = tid + k * NT;
+        if (q >= NVEC) break;
         const int a = q / NV, gi = i0 + a, gj = j0 + (q % NV) * VN;
         if (gi < n && gj + VN <= m) {
             const size_t o = (size_t)gi * p + gj;
@@ -239,7 +240,8 @@ __device__ __forceinline__ void load_tile32(T (*dA)[33], const T *sA, T (*dB)[33
     }
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int q = tid + k * 256;
+        const int q = tid + k * NT;
+        if (q >= NVEC) break;
         const int a = q / NV, b0 = (q % NV) * VN;
 #pragma unroll
         for (int e = 0; e < VN; ++e) {

@@ -25,9 +25,11 @@ namespace {
 // Snapshot: G and f of every cell and the member mask of every 32-cell piece of every row and
 // column (32 x 32 tiles aligned to the pieces, so each piece lies inside exactly one tile).
 // ---------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *area) {
-    constexpr int R = 36;
+// WARPS warps per tile (8, 16 or 32): more threads per tile shorten each thread's chain of work
+// on small grids, where a launch is latency-bound; large grids use 8 (more tiles per SM).
+template <typename T, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_snapshot(LevelView<T> L, const double *area) {
+    constexpr int R = 36, NT = 32 * WARPS, RPW = 32 / WARPS;   // threads; tile rows per warp
     __shared__ T sP[R][R + 1];
     __shared__ T sU[R][R + 1];
     __shared__ T sG[R][R + 1];
@@ -43,14 +45,14 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int n = L.n, m = L.m, p = L.pitch;
     // stage pn, u (mirror-clamped, 36 x 36), w and F, rhs (FP32 only) with vector loads
-    load_halo2<T>(sP, L.pn, sU, L.u, i0, j0, n, m, p, tid);
+    load_halo2<T, NT>(sP, L.pn, sU, L.u, i0, j0, n, m, p, tid);
     if (kStage) {
-        if (!L.wb) load_halo2<T>(reinterpret_cast<T (*)[37]>(sW), L.w, nullptr, nullptr, i0, j0, n, m, p, tid);
-        load_tile32<T>(reinterpret_cast<T (*)[33]>(sF), L.F, reinterpret_cast<T (*)[33]>(sR),
-                       L.has_rhs ? L.rhs : nullptr, i0, j0, n, m, p, tid);
+        if (!L.wb) load_halo2<T, NT>(reinterpret_cast<T (*)[37]>(sW), L.w, nullptr, nullptr, i0, j0, n, m, p, tid);
+        load_tile32<T, NT>(reinterpret_cast<T (*)[33]>(sF), L.F, reinterpret_cast<T (*)[33]>(sR),
+                           L.has_rhs ? L.rhs : nullptr, i0, j0, n, m, p, tid);
     }
     __syncthreads();
-    // Lane = tile column, warp row wy handles tile rows wy, wy + 8, wy + 16, wy + 24.  Interior
+    // Lane = tile column, warp row wy handles tile rows wy, wy + WARPS, ....  Interior
     // tiles (every cell with four faces, the G ring inside the grid) skip the bounds tests.
     const int lane = threadIdx.x, wy = threadIdx.y;
     const bool interior = i0 >= 1 && j0 >= 1 && i0 + 33 <= n && j0 + 33 <= m;
@@ -66,23 +68,24 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
     // G on the 34 x 34 box rows / columns 1..34: the 32 tile columns by lane, then the two ring
     // columns (68 cells) packed into whole warps
     if (interior) {
-        for (int a = 1 + wy; a <= 34; a += 8) g_at(a, lane + 2, false);
+        for (int a = 1 + wy; a <= 34; a += WARPS) g_at(a, lane + 2, false);
         if (tid < 68) g_at(1 + (tid >> 1), (tid & 1) ? 34 : 1, false);
     } else {
-        for (int a = 1 + wy; a <= 34; a += 8) g_at(a, lane + 2, true);
+        for (int a = 1 + wy; a <= 34; a += WARPS) g_at(a, lane + 2, true);
         if (tid < 68) g_at(1 + (tid >> 1), (tid & 1) ? 34 : 1, true);
     }
     __syncthreads();
     const T ar = area ? T(area[L.level]) : T(0);
     const int gj = j0 + lane, b = lane + 2;
     const int lenr = min(32, m - j0), lenc = min(32, n - i0);
-    // The 16 pieces of this warp (rows wy + 8k: sweeps A, B; columns wy + 8k: sweeps C, D) are
-    // collected as ballots into lanes 0..15 and finished by one members_of: lane 2k + s holds
-    // row wy + 8k, sweep A (s = 0) or B (s = 1); lane 8 + 2k + s column wy + 8k, C or D.
+    // The 4 RPW pieces of this warp (rows wy + WARPS k: sweeps A, B; columns wy + WARPS k:
+    // sweeps C, D) are collected as ballots into lanes 0 .. 4 RPW - 1 and finished by one
+    // members_of: lane 2k + s holds row wy + WARPS k, sweep A (s = 0) or B (s = 1); lane
+    // 2 RPW + 2k + s column wy + WARPS k, sweep C or D.
     uint32_t bits = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int ti = wy + 8 * k, a = ti + 2, gi = i0 + ti;
+    for (int k = 0; k < RPW; ++k) {
+        const int ti = wy + WARPS * k, a = ti + 2, gi = i0 + ti;
         uint8_t star = 0;
         if (interior || (gi < n && gj < m)) {
             const bool hS = interior || gi + 1 < n, hN = interior || gi > 0;
@@ -118,16 +121,17 @@ __global__ void __launch_bounds__(256) k_snapshot(LevelView<T> L, const double *
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint8_t sc = sStar[lane][wy + 8 * k];
+    for (int k = 0; k < RPW; ++k) {
+        const uint8_t sc = sStar[lane][wy + WARPS * k];
         const uint32_t bC = __ballot_sync(0xffffffffu, sc & 4u), bD = __ballot_sync(0xffffffffu, sc & 8u);
-        if (lane == 8 + 2 * k) bits = bC;
-        if (lane == 9 + 2 * k) bits = bD;
+        if (lane == 2 * RPW + 2 * k) bits = bC;
+        if (lane == 2 * RPW + 2 * k + 1) bits = bD;
     }
-    if (lane < 16) {
-        const int line = wy + 8 * ((lane >> 1) & 3), s = lane & 1;
-        const uint32_t mk = members_of(bits, lane < 8 ? lenr : lenc);
-        if (lane < 8) {
+    if (lane < 4 * RPW) {
+        const bool row = lane < 2 * RPW;
+        const int line = wy + WARPS * ((lane >> 1) % RPW), s = lane & 1;
+        const uint32_t mk = members_of(bits, row ? lenr : lenc);
+        if (row) {
             if (i0 + line < n) L.mrow[((size_t)s * n + i0 + line) * L.npm + (j0 >> 5)] = mk;
         } else if (j0 + line < m) {
             L.mcol[((size_t)s * m + j0 + line) * L.npn + (i0 >> 5)] = mk;
@@ -387,10 +391,40 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
 
 }  // namespace
 
+// Resident snapshot blocks per SM for 8, 16, 32 warps per tile (measured once, outside any
+// capture) and the SM count.
+template <typename T>
+struct SnapOcc {
+    int per_sm[3] = {1, 1, 1}, sms = 1;
+    SnapOcc() {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot<T, 8>, 256, 0) == cudaSuccess && v > 0) per_sm[0] = v;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot<T, 16>, 512, 0) == cudaSuccess && v > 0) per_sm[1] = v;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot<T, 32>, 1024, 0) == cudaSuccess && v > 0) per_sm[2] = v;
+    }
+};
+
+template <typename T>
+const SnapOcc<T> &snap_occ() {
+    static const SnapOcc<T> o;
+    return o;
+}
+
+// The most threads per tile with which every tile of the grid still gets a resident block.
 template <typename T>
 void launch_snapshot(const LevelView<T> &L, const double *area, cudaStream_t st) {
-    dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, 8);
-    k_snapshot<T><<<grid, block, 0, st>>>(L, area);
+    dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
+    const long tiles = (long)grid.x * grid.y;
+    const SnapOcc<T> &o = snap_occ<T>();
+    if (tiles <= (long)o.sms * o.per_sm[2])
+        k_snapshot<T, 32><<<grid, dim3(32, 32), 0, st>>>(L, area);
+    else if (tiles <= (long)o.sms * o.per_sm[1])
+        k_snapshot<T, 16><<<grid, dim3(32, 16), 0, st>>>(L, area);
+    else
+        k_snapshot<T, 8><<<grid, dim3(32, 8), 0, st>>>(L, area);
 }
 
 template <typename T>
@@ -424,13 +458,15 @@ static void set_fused_attrs() {
     set_fused_attr<T, 0, TS>(); set_fused_attr<T, 1, TS>(); set_fused_attr<T, 2, TS>(); set_fused_attr<T, 3, TS>();
 }
 
-// Raises the dynamic shared-memory limit of the fused sweep kernels on the current device
-// (called once per set-up, before any stream capture).
+// Raises the dynamic shared-memory limit of the fused sweep kernels on the current device and
+// measures the snapshot's occupancy (called once per set-up, before any stream capture).
 void prepare_smoother_kernels() {
     set_fused_attrs<float, Tile0>(); set_fused_attrs<float, Tile1>(); set_fused_attrs<float, Tile2>();
     set_fused_attrs<float, Tile3>(); set_fused_attrs<float, Tile4>(); set_fused_attrs<float, Tile5>();
     set_fused_attrs<double, Tile0>(); set_fused_attrs<double, Tile1>(); set_fused_attrs<double, Tile2>();
     set_fused_attrs<double, Tile3>(); set_fused_attrs<double, Tile4>(); set_fused_attrs<double, Tile5>();
+    (void)snap_occ<float>();   // snapshot occupancy, measured here rather than inside a capture
+    (void)snap_occ<double>();
 }
 
 template <typename T, int SW, typename TS>
