@@ -593,7 +593,8 @@ struct Solver final : SolverBase {
     }
 
     // Picks the fused-sweep tile shape of every grid by timing one outer smoothing iteration
-    // (snapshot + four sweeps, `reps` times) per shape; the state is restored afterwards.
+    // (snapshot + four sweeps, `reps` times, replayed as a graph when the solver uses graphs)
+    // per shape; the state is restored afterwards.
     int autotune(int reps, int *out) {
         if (!in_step) return fail(MG_ERR_STATE, "mg_autotune outside a step");
         if (!fused()) return fail(MG_ERR_ARG, "autotune applies to the fused Hybrid Smoother 2");
@@ -608,18 +609,36 @@ struct Solver final : SolverBase {
             for (int sh = 0; sh < kTileShapes; ++sh) {
                 CK(cudaMemcpy2DAsync(L.r, pitchb, L.u, pitchb, row, L.n, cudaMemcpyDeviceToDevice, st));
                 LevelView<T> v = view(l);
-                float t = 0;
-                for (int warm = 0; warm < 2; ++warm) {
-                    CK(cudaEventRecord(e0, st));
+                auto enqueue = [&]() {
                     for (int r = 0; r < reps; ++r) {
                         area_term(l, L.u);
                         launch_snapshot<T>(v, area_ptr(), st);
                         for (int k = 0; k < 4; ++k) sweep(l, v, k, sh);
                     }
+                };
+                // With graphs, time a captured graph of the iterations: eager launches would
+                // measure the host's launch rate on the small grids, not the kernels.
+                cudaGraphExec_t ge = nullptr;
+                if (p.use_graph) {
+                    cudaGraph_t g;
+                    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                    enqueue();
+                    cudaError_t e = cudaStreamEndCapture(st, &g);
+                    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+                    e = cudaGraphInstantiate(&ge, g, 0);
+                    cudaGraphDestroy(g);
+                    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+                }
+                float t = 0;
+                for (int warm = 0; warm < 2; ++warm) {
+                    CK(cudaEventRecord(e0, st));
+                    if (ge) CK(cudaGraphLaunch(ge, st));
+                    else enqueue();
                     CK(cudaEventRecord(e1, st));
                     CK(cudaEventSynchronize(e1));
                     CK(cudaEventElapsedTime(&t, e0, e1));
                 }
+                if (ge) cudaGraphExecDestroy(ge);
                 CKL();
                 CK(cudaMemcpy2DAsync(L.u, pitchb, L.r, pitchb, row, L.n, cudaMemcpyDeviceToDevice, st));
                 if (t < best) { best = t; arg = sh; }
