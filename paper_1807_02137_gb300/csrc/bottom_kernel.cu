@@ -124,31 +124,13 @@ __device__ __forceinline__ bool b_member(const BGrid &B, int sweep, int i, int j
     return (B.mcol[((sweep - 2) * B.m + j) * B.npn + (i >> 5)] >> (i & 31)) & 1u;
 }
 
-// One directional sweep of Hybrid Smoother 2 in the parallel ordering (as k_rb + k_seg).
-__device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
+// The two partial-line phases of one directional sweep (as k_seg): one warp per line of the
+// phase's parity.  Lines of one parity do not interact, and the cells just outside a piece lie
+// on the same line, so a warp reads the end values of all its pieces before it solves any run:
+// no block-wide barrier is needed within a phase.
+__device__ void b_lines(const BGrid &B, int sweep, float *endv) {
     const int n = B.n, m = B.m;
     const bool rev = sweep & 1, rowwise = sweep < 2;
-    // checkerboard phases: the cells of one colour, two per row pair of threads' columns
-    const int mh = (m + 1) >> 1;
-    const Map2 MH = map_for(mh);
-    for (int ph = 0; ph < 2; ++ph) {
-        const int colour = rev ? 1 - ph : ph;
-        FOR_CELLS(MH, n, mh, i, k) {
-            const int j = 2 * k + ((i + colour) & 1);
-            if (j >= m || b_member(B, sweep, i, j)) continue;
-            const int q = i * m + j;
-            const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
-            const int oS = hS ? q + m : q, oN = hN ? q - m : q, oE = hE ? q + 1 : q, oW = hW ? q - 1 : q;
-            const float gc = B.G[q];
-            const float aS = face(gc, B.G[oS], hS), aN = face(gc, B.G[oN], hN);
-            const float aE = face(gc, B.G[oE], hE), aW = face(gc, B.G[oW], hW);
-            B.u[q] = point_relax(B.cdiff, B.inv_tau, aS, aN, aE, aW, B.u[oS], B.u[oN], B.u[oE], B.u[oW], B.f[q]);
-        }
-        __syncthreads();
-    }
-    // partial-line phases: one warp per line of the phase's parity.  Lines of one parity do not
-    // interact, and the cells just outside a piece lie on the same line, so a warp reads the
-    // end values of all its pieces before it solves any run: no block-wide barrier is needed.
     const int nlines = rowwise ? n : m, llen = rowwise ? m : n, npieces = rowwise ? B.npm : B.npn;
     const int step = rowwise ? 1 : m;                 // stride along a line
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,6 +175,78 @@ __device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
             __syncwarp();
         }
         __syncthreads();
+    }
+}
+
+// One directional sweep of Hybrid Smoother 2 in the parallel ordering (as k_rb + k_seg).
+__device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
+    const int n = B.n, m = B.m;
+    const bool rev = sweep & 1;
+    // checkerboard phases: the cells of one colour, two per row pair of threads' columns
+    const int mh = (m + 1) >> 1;
+    const Map2 MH = map_for(mh);
+    for (int ph = 0; ph < 2; ++ph) {
+        const int colour = rev ? 1 - ph : ph;
+        FOR_CELLS(MH, n, mh, i, k) {
+            const int j = 2 * k + ((i + colour) & 1);
+            if (j >= m || b_member(B, sweep, i, j)) continue;
+            const int q = i * m + j;
+            const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
+            const int oS = hS ? q + m : q, oN = hN ? q - m : q, oE = hE ? q + 1 : q, oW = hW ? q - 1 : q;
+            const float gc = B.G[q];
+            const float aS = face(gc, B.G[oS], hS), aN = face(gc, B.G[oN], hN);
+            const float aE = face(gc, B.G[oE], hE), aW = face(gc, B.G[oW], hW);
+            B.u[q] = point_relax(B.cdiff, B.inv_tau, aS, aN, aE, aW, B.u[oS], B.u[oN], B.u[oE], B.u[oW], B.f[q]);
+        }
+        __syncthreads();
+    }
+    b_lines(B, sweep, endv);
+}
+
+// One outer smoothing iteration (snapshot and four sweeps) of a grid with at most one cell per
+// thread.  The cell's four face values, the denominator of its point update, f and its member
+// bits are formed once after the snapshot and kept in registers, so a checkerboard phase reads
+// only the four neighbouring values of u from shared memory.  The update is point_relax's
+// sequence of operations, so the results equal those of b_snapshot and four b_sweep calls; a
+// sweep with no member cell on the grid skips its (empty) line phases.
+__device__ void b_smooth_small(const BGrid &B, uint8_t *star, float *endv) {
+    __shared__ unsigned s_any;   // bit k: sweep k has a member cell somewhere on the grid
+    if (threadIdx.x == 0) s_any = 0;
+    b_snapshot(B, star);         // ends with a barrier
+    const int n = B.n, m = B.m, q = threadIdx.x;
+    const bool own = q < n * m;
+    float aS = 0.f, aN = 0.f, aE = 0.f, aW = 0.f, dv = 1.f, fq = 0.f;
+    int oS = q, oN = q, oE = q, oW = q, colour = 0;
+    unsigned mem = 0;
+    if (own) {
+        const int i = q / m, j = q - i * m;
+        const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
+        oS = hS ? q + m : q; oN = hN ? q - m : q; oE = hE ? q + 1 : q; oW = hW ? q - 1 : q;
+        const float gc = B.G[q];
+        aS = face(gc, B.G[oS], hS); aN = face(gc, B.G[oN], hN);
+        aE = face(gc, B.G[oE], hE); aW = face(gc, B.G[oW], hW);
+        dv = fma_rn(B.cdiff, add_rn(add_rn(aS, aN), add_rn(aE, aW)), B.inv_tau);
+        fq = B.f[q];
+        colour = (i + j) & 1;
+        for (int k = 0; k < 4; ++k) mem |= (unsigned)b_member(B, k, i, j) << k;
+    }
+    const unsigned wm = __reduce_or_sync(0xffffffffu, mem);
+    if ((threadIdx.x & 31) == 0 && wm) atomicOr(&s_any, wm);
+    __syncthreads();
+    const unsigned any = s_any;
+    for (int k = 0; k < 4; ++k) {
+        const bool rev = k & 1;
+        for (int ph = 0; ph < 2; ++ph) {
+            if (own && colour == (rev ? 1 - ph : ph) && !((mem >> k) & 1u)) {
+                float num = mul_rn(aS, B.u[oS]);
+                num = fma_rn(aN, B.u[oN], num);
+                num = fma_rn(aE, B.u[oE], num);
+                num = fma_rn(aW, B.u[oW], num);
+                B.u[q] = div_relax(fma_rn(B.cdiff, num, -fq), dv);
+            }
+            __syncthreads();
+        }
+        if ((any >> k) & 1u) b_lines(B, k, endv);
     }
 }
 
@@ -350,8 +404,12 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
     float *endv = reinterpret_cast<float *>(sm + s_off[1]);
     __syncthreads();
     auto smooth = [&](int l) {
-        b_snapshot(Bs[l], star);
-        for (int k = 0; k < 4; ++k) b_sweep(Bs[l], k, endv);
+        if (Bs[l].n * Bs[l].m <= kBT) {
+            b_smooth_small(Bs[l], star, endv);
+        } else {
+            b_snapshot(Bs[l], star);
+            for (int k = 0; k < 4; ++k) b_sweep(Bs[l], k, endv);
+        }
     };
     // ---- down: smoothing, residual, restriction, coarse right-hand side (Algorithm 1)
     for (int l = A.lb; l < A.L - 1; ++l) {
