@@ -193,7 +193,7 @@ def run_ours(args):
     # (mg_autotune; they never change results, only speed)
     s.begin_step()
     shapes = s.autotune(reps=3)
-    bottom_level = s.stats()["bottom_level"]
+    bottom_level, cluster_level = s.stats()["bottom_level"], s.stats()["cluster_level"]
     s.end_step()
 
     def step():
@@ -313,6 +313,7 @@ def run_ours(args):
                                    "V(2,2), tau 1, Spencer-Chen, one pseudo-time step to rho <= 1e-6",
                        "l2": "flushed (512 MB write) between timed steps",
                        "tile_shapes": shapes, "bottom_kernel_from_grid": bottom_level,
+                       "cluster_bottom_from_grid": cluster_level,
                        "cycles_per_step": float(np.mean(cycles)), "rho_last": float(max(rhos)),
                        "parallelism": f"replicas x{ws}"},
             "e2e": {"value": ws * n * m / (e2e_ms_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,

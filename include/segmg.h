@@ -115,6 +115,7 @@ typedef struct {
     long long learned_accepted;   /* V-cycles run with learned relaxation weights and kept */
     long long learned_rejected;   /* ... and rejected (rerun with the plain smoother) */
     int bottom_level;      /* first grid of the one-block bottom kernel, -1 when it is not used */
+    int cluster_level;     /* first grid of the cluster bottom kernel, -1 when it is not used */
 } mg_stats;
 
 /* Optional device allocator (for example a framework's caching allocator).  alloc returns a
@@ -206,8 +207,10 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
  * tile: 0 = 32x64/256, 1 = 32x32/128, 2 = 64x64/512, 3 = 32x64/512, 4 = 32x32/256,
  * 5 = 32x32/512) over `reps` repetitions and keeps the fastest per grid; writes the choices to
  * shapes[0..levels-2] if not NULL.  Then, when the bottom kernel is in use, it times `reps`
- * V-cycles with the bottom kernel starting at the largest grid that fits and at the next two
- * coarser grids, and keeps the fastest (mg_stats.bottom_level).  The state is restored, and the
+ * V-cycles with the one-block bottom kernel starting at the largest grid that fits and at the next
+ * two coarser grids, and with the cluster bottom kernel (mg_set_cluster_level) from the grid before
+ * and from that largest grid where such a cluster fits, and keeps the fastest
+ * (mg_stats.bottom_level, mg_stats.cluster_level).  The state is restored, and the
  * results of later solves do not depend on these choices (every choice computes the same
  * values).  Waits. */
 int mg_autotune(mg_handle h, int reps, int *shapes);
@@ -296,6 +299,15 @@ int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level);
  * also chooses it (mg_stats.bottom_level).  Errors: MG_ERR_ARG (level out of that range, or the
  * bottom kernel does not apply). */
 int mg_set_bottom_level(mg_handle h, int level);
+/* Runs the bottom of the V-cycle from grid `level` as one thread-block cluster (a tuning step of
+ * this implementation; the paper has no counterpart): one 1024-thread CTA per 32 x 32 tile of
+ * that grid, neighbours exchanged through distributed shared memory, and CTA 0 running the
+ * coarser grids like the one-block kernel.  `level` from the grid before the largest one the
+ * one-block kernel can start at, to levels - 2, with at most 16 tiles; -1 switches it off (the
+ * one-block kernel, if on, then takes over).  The results are the same either way.  mg_autotune
+ * also chooses it (mg_stats.cluster_level).  Errors: MG_ERR_ARG (out of range, or no such cluster
+ * fits the GPU). */
+int mg_set_cluster_level(mg_handle h, int level);
 
 /* Batches (many images at once; no counterpart in the paper): `count` images of
  * their own sizes solved together.  Each V-cycle of mg_batch_solve_step is one CUDA graph

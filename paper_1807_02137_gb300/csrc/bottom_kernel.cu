@@ -9,6 +9,8 @@
 // coarsest solve share their device functions), so the V-cycle's results do not change.
 // Used for the FP32 / mixed storage and the Spencer-Chen model when the grids fit in shared
 // memory; the host falls back to the per-grid kernels otherwise.
+#include <cooperative_groups.h>
+
 #include "arith.cuh"
 #include "coarse_body.cuh"
 #include "reduce.cuh"
@@ -351,17 +353,62 @@ size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L, int coarse_f
     return b;
 }
 
-__global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ double red[33];
-    __shared__ int s_err;
-    __shared__ BGrid Bs[kMaxLevels];
-    __shared__ size_t s_off[3];
-    // ---- carve shared memory (one thread), then load pn, w, F of every grid and u, rhs of grid lb
+// The sub-cycle from grid lb (its u and rhs already in shared memory) down to the coarsest and
+// back, run by the whole block: smoothing, residual, restriction, coarse right-hand side, the
+// coarsest solve, interpolation, post-smoothing (Algorithm 1).
+__device__ void bottom_subcycle(const BottomArgs &A, BGrid *Bs, int lb, uint8_t *star, float *endv,
+                                unsigned char *scratch, double *red, int *s_err) {
+    auto smooth = [&](int l) {
+        if (Bs[l].n * Bs[l].m <= kBT) {
+            b_smooth_small(Bs[l], star, endv);
+        } else {
+            b_snapshot(Bs[l], star);
+            for (int k = 0; k < 4; ++k) b_sweep(Bs[l], k, endv);
+        }
+    };
+    // ---- down: smoothing, residual, restriction, coarse right-hand side (Algorithm 1)
+    for (int l = lb; l < A.L - 1; ++l) {
+        for (int t = 0; t < A.nu1; ++t) smooth(l);
+        b_residual(Bs[l], Bs[l].u, Bs[l].f, 0);
+        b_restrict(Bs[l], Bs[l].f, Bs[l + 1], Bs[l + 1].rhs, nullptr);
+        b_restrict(Bs[l], Bs[l].u, Bs[l + 1], Bs[l + 1].u, Bs[l + 1].u0);
+        b_residual(Bs[l + 1], Bs[l + 1].u0, Bs[l + 1].rhs, 1);
+    }
+    // ---- the coarsest solve
+    {
+        const BGrid &C = Bs[A.L - 1];
+        CoarseGrid<float> cg{C.n, C.m, C.m, C.pn, C.u, C.w, nullptr, C.F, C.rhs, C.has_rhs, C.inv_2h, C.inv_tau, C.beta};
+        int it;
+        double res;
+        if (A.coarse_fp64)
+            coarse_solve_block<float, double>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
+                                              reinterpret_cast<double *>(scratch), red, s_err, &it, &res,
+                                              A.coarse_aos, A.aos_dt);
+        else
+            coarse_solve_block<float, float>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
+                                             reinterpret_cast<float *>(scratch), red, s_err, &it, &res,
+                                             A.coarse_aos, A.aos_dt);
+        if (threadIdx.x == 0) {
+            A.sc->picard = it;
+            A.sc->coarse_res = res;
+            if (*s_err) A.sc->err = 1;
+        }
+    }
+    // ---- up: interpolation and post-smoothing
+    for (int l = A.L - 2; l >= lb; --l) {
+        b_interp_add(Bs[l], Bs[l + 1]);
+        for (int t = 0; t < A.nu2; ++t) smooth(l);
+    }
+}
+
+// Carves the shared memory of grids lb .. L-1 (thread 0) and loads pn, w and F of every grid and,
+// when load_first, u and rhs of grid lb.  s_off: star bytes, end values, coarsest-solve scratch.
+__device__ void bottom_setup(const BottomArgs &A, BGrid *Bs, int lb, bool load_first, unsigned char *sm,
+                             size_t *s_off) {
     if (threadIdx.x == 0) {
         size_t off = 0;
         int maxN = 0, maxTask = 0;
-        for (int l = A.lb; l < A.L; ++l) {
+        for (int l = lb; l < A.L; ++l) {
             const LevelView<float> &G = A.g[l];
             BGrid &B = Bs[l];
             B.n = G.n; B.m = G.m; B.npm = (G.m + 31) / 32; B.npn = (G.n + 31) / 32;
@@ -384,7 +431,7 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
         s_off[2] = off;                                 // coarsest-solve scratch
     }
     __syncthreads();
-    for (int l = A.lb; l < A.L; ++l) {
+    for (int l = lb; l < A.L; ++l) {
         const LevelView<float> &G = A.g[l];
         const BGrid &B = Bs[l];
         const Map2 M = map_for(B.m);
@@ -394,56 +441,26 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
             B.pn[q] = G.pn[o];
             B.w[q] = weight_at(G, o);
             B.F[q] = G.F[o];
-            if (l == A.lb) {
+            if (load_first && l == lb) {
                 B.u[q] = G.u[o];
                 B.rhs[q] = G.has_rhs ? G.rhs[o] : 0.f;
             }
         }
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red[33];
+    __shared__ int s_err;
+    __shared__ BGrid Bs[kMaxLevels];
+    __shared__ size_t s_off[3];
+    bottom_setup(A, Bs, A.lb, true, sm, s_off);
     uint8_t *star = sm + s_off[0];
     float *endv = reinterpret_cast<float *>(sm + s_off[1]);
     __syncthreads();
-    auto smooth = [&](int l) {
-        if (Bs[l].n * Bs[l].m <= kBT) {
-            b_smooth_small(Bs[l], star, endv);
-        } else {
-            b_snapshot(Bs[l], star);
-            for (int k = 0; k < 4; ++k) b_sweep(Bs[l], k, endv);
-        }
-    };
-    // ---- down: smoothing, residual, restriction, coarse right-hand side (Algorithm 1)
-    for (int l = A.lb; l < A.L - 1; ++l) {
-        for (int t = 0; t < A.nu1; ++t) smooth(l);
-        b_residual(Bs[l], Bs[l].u, Bs[l].f, 0);
-        b_restrict(Bs[l], Bs[l].f, Bs[l + 1], Bs[l + 1].rhs, nullptr);
-        b_restrict(Bs[l], Bs[l].u, Bs[l + 1], Bs[l + 1].u, Bs[l + 1].u0);
-        b_residual(Bs[l + 1], Bs[l + 1].u0, Bs[l + 1].rhs, 1);
-    }
-    // ---- the coarsest solve
-    {
-        const BGrid &C = Bs[A.L - 1];
-        CoarseGrid<float> cg{C.n, C.m, C.m, C.pn, C.u, C.w, nullptr, C.F, C.rhs, C.has_rhs, C.inv_2h, C.inv_tau, C.beta};
-        int it;
-        double res;
-        if (A.coarse_fp64)
-            coarse_solve_block<float, double>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
-                                              reinterpret_cast<double *>(sm + s_off[2]), red, &s_err, &it, &res,
-                                              A.coarse_aos, A.aos_dt);
-        else
-            coarse_solve_block<float, float>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
-                                             reinterpret_cast<float *>(sm + s_off[2]), red, &s_err, &it, &res,
-                                             A.coarse_aos, A.aos_dt);
-        if (threadIdx.x == 0) {
-            A.sc->picard = it;
-            A.sc->coarse_res = res;
-            if (s_err) A.sc->err = 1;
-        }
-    }
-    // ---- up: interpolation and post-smoothing
-    for (int l = A.L - 2; l >= A.lb; --l) {
-        b_interp_add(Bs[l], Bs[l + 1]);
-        for (int t = 0; t < A.nu2; ++t) smooth(l);
-    }
+    bottom_subcycle(A, Bs, A.lb, star, endv, sm + s_off[2], red, &s_err);
     // ---- grid lb's increment back to global memory
     {
         const LevelView<float> &G = A.g[A.lb];
@@ -453,12 +470,336 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// The bottom of the V-cycle from a grid spread over a thread-block cluster.  On grids of about
+// 64^2 every per-grid launch is latency-bound (a V-cycle spends about 23 launches per grid) while
+// one block is too little for the grid.  Here one 1024-thread CTA owns each 32 x 32 tile of grid
+// lc (one cell per thread, at most 16 tiles: one cluster) in its shared memory, pn, u and G with
+// a ring of the neighbouring tiles' edge cells.  After each phase a cluster barrier, then the
+// ring is copied from the neighbours' shared memory (distributed shared memory), so every phase
+// computes from local shared memory.  A checkerboard phase needs one barrier: a neighbour that
+// copies a ring cell after this CTA has already overwritten it (next colour) copies it again
+// before using it.  A partial-line phase writes cells whose start-of-phase values neighbours use
+// as end values, so it waits for every copy to finish first.  CTA 0 also holds grids
+// lc+1 .. L-1 and runs their sub-cycle (bottom_subcycle) between the restriction and the
+// interpolation.  Every cell performs the per-grid kernels' operations, so the results are the
+// same.
+// ---------------------------------------------------------------------------------------
+constexpr int kHP = 34;   // the 32 x 32 tile and its ring
+
+struct CTile {
+    float P[kHP][kHP], U[kHP][kHP], G[kHP][kHP];            // pn, u, G; tile cell (a, b) at [a + 1][b + 1]
+    float W[32][32], F[32][32], R[32][32], Fv[32][32], Res[32][32];   // w, F, rhs, f, residual
+    uint32_t mrow[2][32];   // sweeps A, B: the piece of tile row r
+    uint32_t mcol[2][32];   // sweeps C, D: the piece of tile column c
+    uint8_t star[32][33];
+    unsigned any;           // bit k: a member cell of sweep k in this tile
+};
+constexpr size_t kTileBytes = (sizeof(CTile) + 127) / 128 * 128;
+
+__global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
+    namespace cgc = cooperative_groups;
+    cgc::cluster_group cl = cgc::this_cluster();
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red[33];
+    __shared__ int s_err;
+    __shared__ BGrid Bs[kMaxLevels];
+    __shared__ size_t s_off[3];
+    __shared__ CTile *tp[16];
+    CTile &T = *reinterpret_cast<CTile *>(sm);
+    const int lc = A.lb;
+    const LevelView<float> &Lg = A.g[lc];
+    const int n = Lg.n, m = Lg.m, TX = (m + 31) / 32;
+    const float cdiff = Lg.cdiff, inv_tau = Lg.inv_tau, Sigma = Lg.Sigma, inv_2h = Lg.inv_2h, beta = Lg.beta;
+    const bool has_rhs = Lg.has_rhs != 0;
+    const int rank = (int)cl.block_rank();
+    const int ty = rank / TX, tx = rank - ty * TX, i0 = ty * 32, j0 = tx * 32;
+    const int q = threadIdx.x, ti = q >> 5, lane = q & 31;
+    const int i = i0 + ti, j = j0 + lane;
+    const bool own = i < n && j < m;
+    if (q < (int)cl.num_blocks()) tp[q] = cl.map_shared_rank(&T, q);
+    // padded row / column of grid row / column a, clamped into the grid (the mirror ghosts)
+    auto pr = [&](int a) { return min(max(a, 0), n - 1) - i0 + 1; };
+    auto pc = [&](int b) { return min(max(b, 0), m - 1) - j0 + 1; };
+    const int r0 = ti + 1, c0 = lane + 1, rS = pr(i + 1), rN = pr(i - 1), cE = pc(j + 1), cW = pc(j - 1);
+    // the ring of field f (0: pn, 1: u, 2: G) from the neighbouring tiles (after a cluster barrier)
+    auto field = [&](CTile *t, int f) -> float (*)[kHP] { return f == 0 ? t->P : (f == 1 ? t->U : t->G); };
+    auto ring = [&](int f) {
+        if (q < 128) {
+            const int side = q >> 5, k = q & 31;
+            float (*X)[kHP] = field(&T, f);
+            if (side == 0) {
+                if (i0 > 0 && j0 + k < m) X[0][k + 1] = field(tp[rank - TX], f)[32][k + 1];
+            } else if (side == 1) {
+                if (i0 + 32 < n && j0 + k < m) X[33][k + 1] = field(tp[rank + TX], f)[1][k + 1];
+            } else if (side == 2) {
+                if (j0 > 0 && i0 + k < n) X[k + 1][0] = field(tp[rank - 1], f)[k + 1][32];
+            } else {
+                if (j0 + 32 < m && i0 + k < n) X[k + 1][33] = field(tp[rank + 1], f)[k + 1][1];
+            }
+        }
+    };
+    if (own) {
+        const size_t o = (size_t)i * Lg.pitch + j;
+        T.P[r0][c0] = Lg.pn[o];
+        T.U[r0][c0] = Lg.u[o];
+        T.W[ti][lane] = weight_at(Lg, o);
+        T.F[ti][lane] = Lg.F[o];
+        T.R[ti][lane] = has_rhs ? Lg.rhs[o] : 0.f;
+    }
+    // grids lc+1 .. L-1: every CTA carves the same offsets (CTA 0's arrays are then reached by
+    // mapping this CTA's addresses); their pn, w, F are loaded
+    bottom_setup(A, Bs, lc + 1, false, sm + kTileBytes, s_off);
+    cl.sync();
+    ring(0);
+    ring(1);
+    __syncthreads();
+    auto g_phase = [&]() {   // G at pn + u of the own cell, then its ring
+        if (own)
+            T.G[r0][c0] = cell_G(T.W[ti][lane], T.P[rS][c0], T.P[rN][c0], T.P[r0][cE], T.P[r0][cW], T.U[rS][c0],
+                                 T.U[rN][c0], T.U[r0][cE], T.U[r0][cW], inv_2h, beta);
+        cl.sync();
+        ring(2);
+        __syncthreads();
+    };
+    const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
+    const int colour = (i + j) & 1;
+    // ---- one outer smoothing iteration (snapshot and four sweeps)
+    auto smooth = [&]() {
+        g_phase();
+        float aS = 0.f, aN = 0.f, aE = 0.f, aW = 0.f, dv = 1.f, fq = 0.f;
+        uint32_t star = 0;
+        if (own) {
+            const float gc = T.G[r0][c0];
+            aS = face(gc, T.G[rS][c0], hS); aN = face(gc, T.G[rN][c0], hN);
+            aE = face(gc, T.G[r0][cE], hE); aW = face(gc, T.G[r0][cW], hW);
+            const float pcv = T.P[r0][c0];
+            float ds = mul_rn(aS, sub_rn(T.P[rS][c0], pcv));
+            ds = fma_rn(aN, sub_rn(T.P[rN][c0], pcv), ds);
+            ds = fma_rn(aE, sub_rn(T.P[r0][cE], pcv), ds);
+            ds = fma_rn(aW, sub_rn(T.P[r0][cW], pcv), ds);
+            float base = add_rn(T.F[ti][lane], 0.0f);
+            if (has_rhs) base = add_rn(base, T.R[ti][lane]);
+            fq = fma_rn(-cdiff, ds, base);
+            T.Fv[ti][lane] = fq;
+            const float big = 3.0e38f;
+            const float vS = hS ? aS : big, vN = hN ? aN : big, vE = hE ? aE : big, vW = hW ? aW : big;
+            const float mn = fminf(fminf(vS, vN), fminf(vE, vW));
+            const float mx = fmaxf(fmaxf(hS ? aS : -1.f, hN ? aN : -1.f), fmaxf(hE ? aE : -1.f, hW ? aW : -1.f));
+            const int am = vS == mn ? 0 : (vN == mn ? 1 : (vE == mn ? 2 : 3));
+            const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
+            star = (cnt >= 2 && mx > mul_rn(Sigma, mn)) ? (1u << am) : 0u;
+            dv = fma_rn(cdiff, add_rn(add_rn(aS, aN), add_rn(aE, aW)), inv_tau);
+        }
+        // member masks of the tile's pieces: row ti (this warp) and column ti
+        T.star[ti][lane] = (uint8_t)star;
+        const int lenr = min(32, m - j0), lenc = min(32, n - i0);
+        const uint32_t mA = members_of(__ballot_sync(0xffffffffu, star & 1u), lenr);
+        const uint32_t mB = members_of(__ballot_sync(0xffffffffu, star & 2u), lenr);
+        if (lane == 0) { T.mrow[0][ti] = mA; T.mrow[1][ti] = mB; }
+        __syncthreads();
+        const uint8_t sc = T.star[lane][ti];
+        const uint32_t mC = members_of(__ballot_sync(0xffffffffu, sc & 4u), lenc);
+        const uint32_t mD = members_of(__ballot_sync(0xffffffffu, sc & 8u), lenc);
+        if (lane == 0) { T.mcol[0][ti] = mC; T.mcol[1][ti] = mD; }
+        __syncthreads();
+        unsigned mem = 0;
+        if (own) {
+            mem |= (T.mrow[0][ti] >> lane) & 1u;
+            mem |= ((T.mrow[1][ti] >> lane) & 1u) << 1;
+            mem |= ((T.mcol[0][lane] >> ti) & 1u) << 2;
+            mem |= ((T.mcol[1][lane] >> ti) & 1u) << 3;
+        }
+        if (q < 32) {
+            const unsigned a = (T.mrow[0][q] ? 1u : 0u) | (T.mrow[1][q] ? 2u : 0u) | (T.mcol[0][q] ? 4u : 0u) |
+                               (T.mcol[1][q] ? 8u : 0u);
+            const unsigned r = __reduce_or_sync(0xffffffffu, a);
+            if (q == 0) T.any = r;
+        }
+        unsigned any = 0;   // every tile's bits, read after the first checkerboard phase's barrier
+        for (int k = 0; k < 4; ++k) {
+            const bool rev = k & 1, rowwise = k < 2;
+            for (int ph = 0; ph < 2; ++ph) {
+                if (own && colour == (rev ? 1 - ph : ph) && !((mem >> k) & 1u)) {
+                    float num = mul_rn(aS, T.U[rS][c0]);
+                    num = fma_rn(aN, T.U[rN][c0], num);
+                    num = fma_rn(aE, T.U[r0][cE], num);
+                    num = fma_rn(aW, T.U[r0][cW], num);
+                    T.U[r0][c0] = div_relax(fma_rn(cdiff, num, -fq), dv);
+                }
+                cl.sync();
+                if (k == 0 && ph == 0)
+                    for (int r = 0; r < (int)cl.num_blocks(); ++r) any |= tp[r]->any;
+                ring(1);
+                __syncthreads();
+            }
+            if (!((any >> k) & 1u)) continue;
+            // partial-line phases: warp ti owns tile row ti (rowwise) or tile column ti
+            for (int ph = 0; ph < 2; ++ph) {
+                cl.sync();   // every neighbour has copied this tile's ring cells
+                const int parity = rev ? 1 - ph : ph;
+                const int gl = (rowwise ? i0 : j0) + ti, llen = rowwise ? m : n, t0 = rowwise ? j0 : i0;
+                const int len = min(32, llen - t0);
+                const bool ok = gl < (rowwise ? n : m) && (gl & 1) == parity;
+                const uint32_t mk = ok ? (rowwise ? T.mrow[k][ti] : T.mcol[k - 2][ti]) : 0u;
+                if (mk) {
+                    float e0 = 0.f, e1 = 0.f, ownv = 0.f;
+                    if (t0 > 0) e0 = rowwise ? T.U[r0][0] : T.U[0][r0];
+                    if (t0 + len < llen) e1 = rowwise ? T.U[r0][len + 1] : T.U[len + 1][r0];
+                    if (lane < len) ownv = rowwise ? T.U[r0][lane + 1] : T.U[lane + 1][r0];
+                    __syncwarp();
+                    auto at = [&](int r) -> RunCell<float> {
+                        const int ci = rowwise ? gl : t0 + r, cj = rowwise ? t0 + r : gl;
+                        const int a = ci - i0 + 1, b = cj - j0 + 1;
+                        const int aS2 = pr(ci + 1), aN2 = pr(ci - 1), bE2 = pc(cj + 1), bW2 = pc(cj - 1);
+                        const bool cS = ci + 1 < n, cN = ci > 0, cE2 = cj + 1 < m, cW2 = cj > 0;
+                        const float gc = T.G[a][b];
+                        const float bS = face(gc, T.G[aS2][b], cS), bN = face(gc, T.G[aN2][b], cN);
+                        const float bE = face(gc, T.G[a][bE2], cE2), bW = face(gc, T.G[a][bW2], cW2);
+                        RunCell<float> c;
+                        if (rowwise) { c.ap = bW; c.an = bE; c.ax1 = bS; c.ax2 = bN; c.ux1 = T.U[aS2][b]; c.ux2 = T.U[aN2][b]; }
+                        else         { c.ap = bN; c.an = bS; c.ax1 = bE; c.ax2 = bW; c.ux1 = T.U[a][bE2]; c.ux2 = T.U[a][bW2]; }
+                        c.f = T.Fv[a - 1][b - 1];
+                        return c;
+                    };
+                    float x;
+                    if (pcr_piece<float>(mk, len, cdiff, inv_tau, ownv, e0, e1, at, x)) {
+                        if (rowwise) T.U[r0][lane + 1] = x;
+                        else T.U[lane + 1][r0] = x;
+                    }
+                }
+                cl.sync();
+                ring(1);
+                __syncthreads();
+            }
+        }
+    };
+    for (int t = 0; t < A.nu1; ++t) smooth();
+    // ---- residual r = rhs - L(pn + u) of the own cell (as b_residual, mode 0)
+    g_phase();
+    if (own) {
+        const float gc = T.G[r0][c0];
+        const float aS = face(gc, T.G[rS][c0], hS), aN = face(gc, T.G[rN][c0], hN);
+        const float aE = face(gc, T.G[r0][cE], hE), aW = face(gc, T.G[r0][cW], hW);
+        const float pcv = T.P[r0][c0], uc = T.U[r0][c0];
+        float fl = mul_rn(aS, add_rn(sub_rn(T.P[rS][c0], pcv), sub_rn(T.U[rS][c0], uc)));
+        fl = fma_rn(aN, add_rn(sub_rn(T.P[rN][c0], pcv), sub_rn(T.U[rN][c0], uc)), fl);
+        fl = fma_rn(aE, add_rn(sub_rn(T.P[r0][cE], pcv), sub_rn(T.U[r0][cE], uc)), fl);
+        fl = fma_rn(aW, add_rn(sub_rn(T.P[r0][cW], pcv), sub_rn(T.U[r0][cW], uc)), fl);
+        const float Lv = sub_rn(fma_rn(cdiff, fl, -add_rn(T.F[ti][lane], 0.0f)), mul_rn(inv_tau, uc));
+        T.Res[ti][lane] = has_rhs ? sub_rn(T.R[ti][lane], Lv) : -Lv;
+    }
+    cl.sync();
+    // ---- CTA 0: restriction of the residual and of u (as b_restrict), the coarse right-hand
+    // side, and the sub-cycle of grids lc+1 .. L-1
+    if (rank == 0) {
+        const BGrid &C = Bs[lc + 1];
+        auto fine = [&](bool res, int a, int b) -> float {   // a fine cell inside the grid
+            const CTile *t = tp[(a >> 5) * TX + (b >> 5)];
+            return res ? t->Res[a & 31][b & 31] : t->U[(a & 31) + 1][(b & 31) + 1];
+        };
+        const Map2 M = map_for(C.m);
+        FOR_CELLS(M, C.n, C.m, I, J) {
+            int ri[3], ci[3];
+            double rw[3], cw[3];
+            const int nr = fw(I, n, ri, rw), nk = fw(J, m, ci, cw);
+            float sr = 0.f, su = 0.f;
+            for (int a = 0; a < nr; ++a) {
+                float rr = 0.f, ru = 0.f;
+                for (int b = 0; b < nk; ++b) {
+                    rr = fma_rn((float)cw[b], fine(true, ri[a], ci[b]), rr);
+                    ru = fma_rn((float)cw[b], fine(false, ri[a], ci[b]), ru);
+                }
+                sr = fma_rn((float)rw[a], rr, sr);
+                su = fma_rn((float)rw[a], ru, su);
+            }
+            const int o = I * C.m + J;
+            C.rhs[o] = sr;
+            C.u[o] = su;
+            C.u0[o] = su;
+        }
+        __syncthreads();
+        b_residual(C, C.u0, C.rhs, 1);
+        bottom_subcycle(A, Bs, lc + 1, sm + kTileBytes + s_off[0],
+                        reinterpret_cast<float *>(sm + kTileBytes + s_off[1]), sm + kTileBytes + s_off[2], red,
+                        &s_err);
+    }
+    cl.sync();
+    // ---- interpolation of CTA 0's coarse correction (as b_interp_add)
+    {
+        const BGrid &C = Bs[lc + 1];
+        const float *Cu = cl.map_shared_rank(C.u, 0), *Cu0 = cl.map_shared_rank(C.u0, 0);
+        if (own) {
+            int ri[2], ci[2];
+            double rw[2], cw[2];
+            const int nr = bl(i, C.n, ri, rw), nk = bl(j, C.m, ci, cw);
+            float sum = 0.f;
+            for (int a = 0; a < nr; ++a)
+                for (int b = 0; b < nk; ++b) {
+                    const int o = ri[a] * C.m + ci[b];
+                    sum = fma_rn((float)(rw[a] * cw[b]), sub_rn(Cu[o], Cu0[o]), sum);
+                }
+            T.U[r0][c0] = add_rn(T.U[r0][c0], sum);
+        }
+    }
+    cl.sync();
+    ring(1);
+    __syncthreads();
+    for (int t = 0; t < A.nu2; ++t) smooth();
+    if (own) Lg.u[(size_t)i * Lg.pitch + j] = T.U[r0][c0];
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
 void prepare_bottom_kernel() {
     cudaFuncSetAttribute(k_bottom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBottomSmemMax);
+    // a refused attribute leaves the cluster kernel unusable: cluster_fits then reports no fit
+    if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax) != cudaSuccess ||
+        cudaFuncSetAttribute(k_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
 }
 
 void launch_bottom(const BottomArgs &A, size_t smem, cudaStream_t st) {
     k_bottom<<<1, kBT, smem, st>>>(A);
+}
+
+size_t cluster_smem_bytes(size_t bottom_bytes) { return kTileBytes + bottom_bytes; }
+
+int cluster_fits(int tiles, size_t smem) {
+    if (tiles < 1 || tiles > kClusterMaxTiles || smem > kClusterSmemMax) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = tiles;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, k_cluster, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // the query's error is reported through the return value
+        return -(int)e;
+    }
+    return nc;
+}
+
+void launch_cluster(const BottomArgs &A, int tiles, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = tiles;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_cluster, A);
 }
 
 }  // namespace segmg

@@ -108,6 +108,7 @@ struct SolverBase {
     virtual int set_shapes(const int *shapes) = 0;
     virtual int set_bottom(int enable) = 0;
     virtual int set_bottom_level(int level) = 0;
+    virtual int set_cluster_level(int level) = 0;
     virtual int energy(double *E) = 0;
     virtual int aos(double dt, int max_iter, double eta, int *iters, double *rho) = 0;
     virtual int set_learned(const float *theta, int mode, int refresh) = 0;
@@ -154,6 +155,10 @@ struct Solver final : SolverBase {
     int shape[kMaxLevels] = {};   // fused-sweep tile shape per grid (mg_autotune)
     int lb = -1;                  // first grid of the one-block bottom kernel (-1: not used)
     int lb_first = -1;            // the largest grid it can start at (-1: it does not apply)
+    int lc = -1;                  // first grid of the cluster bottom kernel (-1: not used); it runs
+                                  // grids lc .. nlev-1 (lb is then unused)
+    int lc_tiles = 0;
+    size_t lc_smem = 0;
     // learned relaxation weights of the point updates (learned.cu)
     int learn_mode = 0;           // 0 off; 1 per V-cycle acceptance; 2 always; 3 fixed weights
     int learn_refresh = 4;        // V-cycles between inferences
@@ -314,6 +319,33 @@ struct Solver final : SolverBase {
         lb_smem = l >= 0 ? bottom_smem_bytes(ns, ms, l, nlev, p.precision == MG_MIXED) : 0;
     }
 
+    // The cluster bottom kernel from grid `level`: grids level+1 .. nlev-1 must fit the one-block
+    // kernel's shared memory beside the tile, and grid `level` must have at most
+    // kClusterMaxTiles tiles of 32 x 32.
+    int set_cluster_level(int level) override {
+        if (level == -1) {
+            lc = -1;
+            drop_graphs();
+            return MG_OK;
+        }
+        if (lb_first < 0 || level < lb_first - 1 || level > nlev - 2)
+            return fail(MG_ERR_ARG, "cluster level out of range (or the bottom kernel does not apply)");
+        int ns[kMaxLevels], ms[kMaxLevels];
+        for (int k = 0; k < nlev; ++k) { ns[k] = lv[k].n; ms[k] = lv[k].m; }
+        const int tiles = ((lv[level].n + 31) / 32) * ((lv[level].m + 31) / 32);
+        const size_t bytes = cluster_smem_bytes(bottom_smem_bytes(ns, ms, level + 1, nlev, p.precision == MG_MIXED));
+        const int fits = cluster_fits(tiles, bytes);
+        if (fits < 1)
+            return fail(MG_ERR_ARG, "the grid does not fit one thread-block cluster (" + std::to_string(tiles) +
+                                        " CTAs, " + std::to_string(bytes) + " bytes of shared memory each: " +
+                                        std::to_string(fits) + ")");
+        lc = level;
+        lc_tiles = tiles;
+        lc_smem = bytes;
+        drop_graphs();
+        return MG_OK;
+    }
+
     int set_bottom_level(int level) override {
         if (level != -1 && (lb_first < 0 || level < lb_first || level > nlev - 2))
             return fail(MG_ERR_ARG, "bottom level out of range (or the bottom kernel does not apply)");
@@ -360,21 +392,23 @@ struct Solver final : SolverBase {
         return MG_OK;
     }
 
-    void launch_bottom_cycle() {
+    void launch_bottom_cycle(bool cluster = false) {
         if constexpr (std::is_same<T, float>::value) {
+            const int first = cluster ? lc : lb;
             BottomArgs a{};
-            a.lb = lb; a.L = nlev; a.nu1 = p.nu1; a.nu2 = p.nu2;
+            a.lb = first; a.L = nlev; a.nu1 = p.nu1; a.nu2 = p.nu2;
             a.coarse_fp64 = p.precision == MG_MIXED;
             a.coarse_aos = p.coarse_solver == MG_COARSE_AOS;
             a.aos_dt = p.aos_dt;
-            for (int l = lb; l < nlev; ++l) a.g[l] = view(l);
+            for (int l = first; l < nlev; ++l) a.g[l] = view(l);
             a.mp = mp;
             a.A1frac = A1 / ((double)n * m);
             a.h2nm_coarse = h2nm(nlev - 1);
             a.coarse_tol = p.coarse_tol;
             a.coarse_maxit = p.coarse_maxit;
             a.sc = dsc;
-            launch_bottom(a, lb_smem, st);
+            if (cluster) launch_cluster(a, lc_tiles, lc_smem, st);
+            else launch_bottom(a, lb_smem, st);
         }
     }
 
@@ -530,6 +564,11 @@ struct Solver final : SolverBase {
     }
 
     void cycle(int l) {
+        if (l == lc) {
+            launch_bottom_cycle(true);
+            ++launches;
+            return;
+        }
         if (l == lb) {
             launch_bottom_cycle();
             ++launches;
@@ -654,10 +693,11 @@ struct Solver final : SolverBase {
         return rc;
     }
 
-    // Times `reps` V-cycles (after one untimed) with the bottom kernel starting at lb_first,
-    // lb_first + 1 and lb_first + 2 and keeps the fastest; the finest increment (saved in ubak:
-    // a V-cycle writes every other finest-grid scratch field) and the device scalars are
-    // restored after each candidate (the coarse grids are rebuilt by every V-cycle).
+    // Times `reps` V-cycles (after one untimed) for each way of running the bottom of the V-cycle:
+    // the one-block kernel from lb_first, lb_first + 1, lb_first + 2, and the cluster kernel from
+    // lb_first - 1 and lb_first where such a cluster fits; keeps the fastest.  The finest increment
+    // (saved in ubak: a V-cycle writes every other finest-grid scratch field) and the device
+    // scalars are restored after each candidate (the coarse grids are rebuilt by every V-cycle).
     int tune_bottom(int reps, cudaEvent_t e0, cudaEvent_t e1) {
         Level<T> &L = lv[0];
         const size_t row = (size_t)L.m * sizeof(T), pitchb = (size_t)L.pitch * sizeof(T);
@@ -667,10 +707,20 @@ struct Solver final : SolverBase {
         CK(cudaStreamSynchronize(st));
         const long long launches0 = launches;
         float best = 1e30f;
-        int arg = lb;
-        for (int cand = lb_first; cand <= std::min(lb_first + 2, nlev - 2); ++cand) {
-            use_bottom_from(cand);
-            drop_graphs();
+        int best_lb = lb, best_lc = lc;
+        struct Cand { bool cluster; int level; };
+        Cand cands[5];
+        int nc = 0;
+        for (int c = lb_first; c <= std::min(lb_first + 2, nlev - 2); ++c) cands[nc++] = {false, c};
+        for (int c = std::max(lb_first - 1, 0); c <= std::min(lb_first, nlev - 2); ++c) cands[nc++] = {true, c};
+        for (int k = 0; k < nc; ++k) {
+            if (cands[k].cluster) {
+                if (set_cluster_level(cands[k].level) != MG_OK) continue;   // no such cluster fits
+            } else {
+                lc = -1;
+                use_bottom_from(cands[k].level);
+                drop_graphs();
+            }
             CK(cudaMemcpy2DAsync(ubak, pitchb, L.u, pitchb, row, L.n, cudaMemcpyDeviceToDevice, st));
             int rc = cycle_plain();   // captures this candidate's graph
             float t = 0;
@@ -685,10 +735,16 @@ struct Solver final : SolverBase {
             CK(cudaMemcpyAsync(dsc, &saved, sizeof(Scalars), cudaMemcpyHostToDevice, st));
             CK(cudaStreamSynchronize(st));
             if (rc != MG_OK) return rc;
-            if (t < best) { best = t; arg = cand; }
+            if (t < best) {
+                best = t;
+                best_lb = lb;
+                best_lc = lc;
+            }
         }
         launches = launches0;
-        use_bottom_from(arg);
+        use_bottom_from(best_lb);
+        lc = -1;
+        if (best_lc >= 0) set_cluster_level(best_lc);
         drop_graphs();
         return MG_OK;
     }
@@ -945,7 +1001,8 @@ struct Solver final : SolverBase {
         s->launches = launches;
         s->learned_accepted = learned_acc;
         s->learned_rejected = learned_rej;
-        s->bottom_level = lb;
+        s->bottom_level = lc >= 0 ? -1 : lb;
+        s->cluster_level = lc;
         return MG_OK;
     }
 
@@ -1519,6 +1576,11 @@ int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level) {
 int mg_set_bottom_level(mg_handle h, int level) {
     if (!h) return fail(MG_ERR_ARG, "NULL handle");
     return h->s->set_bottom_level(level);
+}
+
+int mg_set_cluster_level(mg_handle h, int level) {
+    if (!h) return fail(MG_ERR_ARG, "NULL handle");
+    return h->s->set_cluster_level(level);
 }
 
 int mg_batch_setup(mg_batch *out, int count, const void *const *images, const int *n, const int *m,

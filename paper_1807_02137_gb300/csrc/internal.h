@@ -198,5 +198,14 @@ constexpr size_t kBottomSmemMax = 200 * 1024;
 size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L, int coarse_fp64);
 void prepare_bottom_kernel();
 void launch_bottom(const BottomArgs &A, size_t smem, cudaStream_t st);
+// The bottom of the V-cycle from grid A.lb spread over a cluster of `tiles` CTAs (one per 32 x 32
+// tile, at most kClusterMaxTiles), CTA 0 holding grids A.lb+1 .. L-1.  smem = cluster_smem_bytes
+// of the shared memory of grids A.lb+1 .. L-1; cluster_fits returns how many such clusters can
+// be resident (0: none or out of range; negative: minus the CUDA error of the query).
+constexpr int kClusterMaxTiles = 16;
+constexpr size_t kClusterSmemMax = 220 * 1024;   // dynamic, beside the kernel's static shared memory
+size_t cluster_smem_bytes(size_t bottom_bytes);
+int cluster_fits(int tiles, size_t smem);
+void launch_cluster(const BottomArgs &A, int tiles, size_t smem, cudaStream_t st);
 
 }  // namespace segmg

@@ -23,7 +23,7 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
            "mg_get_level", "mg_get_stats", "mg_segment_host", "mg_get_stream", "mg_destroy",
-           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
+           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_set_cluster_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
            "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_grad",
            "mg_trainer_train", "mg_trainer_get", "mg_trainer_destroy",
            "mg_batch_setup", "mg_batch_solve_step", "mg_batch_autotune", "mg_batch_handle",
@@ -53,7 +53,7 @@ class Stats(C.Structure):
         ("picard_last", C.c_int), ("rho", C.c_double), ("res0", C.c_double), ("eta", C.c_double),
         ("c1", C.c_double), ("c2", C.c_double), ("A1", C.c_double), ("device_bytes", C.c_size_t),
         ("launches", C.c_longlong), ("learned_accepted", C.c_longlong), ("learned_rejected", C.c_longlong),
-        ("bottom_level", C.c_int),
+        ("bottom_level", C.c_int), ("cluster_level", C.c_int),
     ]
 
     def as_dict(self):
@@ -102,6 +102,7 @@ def lib():
             "mg_set_tile_shapes": ([vp, C.POINTER(i)], i),
             "mg_set_bottom_kernel": ([vp, i, C.POINTER(i)], i),
             "mg_set_bottom_level": ([vp, i], i),
+            "mg_set_cluster_level": ([vp, i], i),
             "mg_energy": ([vp, C.POINTER(C.c_double)], i),
             "mg_aos": ([vp, C.c_double, i, C.c_double, C.POINTER(i), C.POINTER(C.c_double)], i),
             "mg_set_learned": ([vp, C.POINTER(C.c_float), i, i], i),
@@ -325,6 +326,10 @@ class Solver:
     def set_bottom_level(self, level):
         """First grid of the bottom kernel (mg_set_bottom_level); -1 for none."""
         _check(lib().mg_set_bottom_level(self._h, int(level)), "mg_set_bottom_level")
+
+    def set_cluster_level(self, level):
+        """First grid of the cluster bottom kernel (mg_set_cluster_level); -1 for none."""
+        _check(lib().mg_set_cluster_level(self._h, int(level)), "mg_set_cluster_level")
 
     def time_kernels(self, level=0, reps=3):
         """Mean ms per launch of snapshot, sweeps A..D and residual on `level` (mg_time_kernels)."""

@@ -244,8 +244,8 @@ def test_autotune_keeps_the_state_and_the_results(segmg):
     s2.begin_step()
     shapes = s2.autotune(reps=1)
     assert len(shapes) == p.levels - 1 and all(0 <= x <= 5 for x in shapes)
-    lb = s2.stats()["bottom_level"]
-    assert lb >= 0 and lb <= p.levels - 2
+    lb, lc = s2.stats()["bottom_level"], s2.stats()["cluster_level"]
+    assert (0 <= lb <= p.levels - 2) != (0 <= lc <= p.levels - 2)
     s2.end_step()          # the autotuner restored phi: this step changed nothing
     s2.solve_step(1e-6, 50)
     assert np.array_equal(s1.phi().cpu().numpy(), s2.phi().cpu().numpy())
@@ -318,6 +318,46 @@ def test_every_bottom_level_gives_the_same_result(segmg, precision):
     for bad in (first - 1, p.levels - 1):
         with pytest.raises(segmg.SegmgError):
             s.set_bottom_level(bad)
+    s.close()
+
+
+@pytest.mark.parametrize("shape,levels", [((256, 256), 7), ((200, 170), 6)])
+@pytest.mark.parametrize("precision", ["f32", "mixed"])
+def test_cluster_bottom_equals_one_block_and_per_grid(segmg, shape, levels, precision):
+    # the bottom of the V-cycle spread over a thread-block cluster (one CTA per 32 x 32 tile,
+    # ragged tiles included) performs the same operations cell by cell
+    prec = segmg.MG_MIXED if precision == "mixed" else segmg.MG_F32
+    n, m = shape
+    img, mk, _ = synth.ellipses(n, m, 14, (6, min(n, m) / 2), 6, 0.1, 91 + n)
+    s, p = gpu_solver(segmg, img, mk, precision=prec, levels=levels)
+    first = s.set_bottom_kernel(True)
+    s.close()
+    # the grid the one-block kernel starts at always fits a cluster here; the grid above it may
+    # not (its cluster needs one SM per tile within one GPC), and is then refused
+    runs = [("one-block", None), ("none", None), ("cluster", first), ("cluster", first - 1)]
+    outs = []
+    for kind, lc in runs:
+        s, p = gpu_solver(segmg, img, mk, precision=prec, levels=levels)
+        if kind == "none":
+            s.set_bottom_kernel(False)
+        elif kind == "cluster":
+            try:
+                s.set_cluster_level(lc)
+            except segmg.SegmgError:
+                assert lc == first - 1
+                s.close()
+                continue
+            assert s.stats()["cluster_level"] == lc
+        s.begin_step()
+        rhos = [s.vcycle() for _ in range(3)]
+        outs.append((s.phi().cpu().numpy(), rhos, s.stats()["picard_last"]))
+        s.close()
+    for x in outs[1:]:
+        assert np.array_equal(outs[0][0], x[0]) and outs[0][1] == x[1] and outs[0][2] == x[2]
+    s, p = gpu_solver(segmg, img, mk, precision=prec, levels=levels)
+    for bad in (first - 2, p.levels - 1):
+        with pytest.raises(segmg.SegmgError):
+            s.set_cluster_level(bad)
     s.close()
 
 
