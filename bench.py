@@ -265,7 +265,7 @@ def run_ours(args):
     achieved = bytes_per_cell * n * m / (sweep_ms * 1e-3) / 1e9
     # DRAM bytes of one finest-grid sweep launch from an ncu capture of this kernel on this grid
     # (profiles/k_sweep_tma_traffic_ellipse1024.txt): u, G, f read once, u written to L2
-    traffic = 12.75e6
+    traffic = 12.76e6
     roof = {"bound": "hbm", "kernel": "k_sweep_tma (TMA-staged fused Hybrid Smoother 2 sweep, finest grid)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic, "peak_kind": peak_kind + " (hbm_gbs, burst copy)",
@@ -341,6 +341,8 @@ def run_profile_case(args):
                                 0.05, 1)
     p = segmg.default_params(N, N, use_graph=0)
     s = segmg.Solver(torch.as_tensor(img, device="cuda"), mk, p)
+    if args.tile_shape >= 0:
+        s.set_tile_shapes([args.tile_shape] * (p.levels - 1))
     s.begin_step()
     for _ in range(args.cycles):
         r = s.vcycle()
@@ -630,6 +632,7 @@ def main():
     ap.add_argument("--sample-cycles", type=int, default=2, help="V-cycles per reference-arm sample")
     ap.add_argument("--profile", type=int, default=0, help="run the N x N ncu profiling case instead")
     ap.add_argument("--cycles", type=int, default=2)
+    ap.add_argument("--tile-shape", type=int, default=-1, help="profiling case: this tile shape on every grid")
     ap.add_argument("--config3", type=int, default=0, help="run the mixed-precision N x N report")
     ap.add_argument("--config4", type=int, default=0, help="run the batched report with this many images")
     ap.add_argument("--algorithms", type=int, default=0, help="compare Algorithms 1-3 on an N x N image")
