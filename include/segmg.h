@@ -285,16 +285,19 @@ void mg_trainer_destroy(mg_trainer t);
 int mg_energy(mg_handle h, double *E);
 
 /* The bottom of the V-cycle in one block: with MG_F32 / MG_MIXED storage, the Spencer-Chen
- * model and the fused smoother, the grids from the largest one whose whole sub-cycle (pn, u, w,
- * F, rhs, G, f, u0, masks and the coarsest solve's scratch) fits in 200 KB of shared memory
- * down to the coarsest run as one kernel of one 1024-thread block instead of one launch per
- * grid and phase.  It performs the same operations per cell as the per-grid kernels, so the
- * results are identical.  enable = 1 (the default at set-up) or 0; *first_level (may be NULL)
- * gets the first grid it covers, -1 when it does not apply.  Errors: MG_ERR_ARG. */
+ * model and the fused smoother, the grids from a first one down to the coarsest run as one
+ * kernel of one 1024-thread block instead of one launch per grid and phase.  The first grid is
+ * one whose whole sub-cycle (pn, u, w, F, rhs, G, f, u0, masks and the coarsest solve's scratch)
+ * fits in 200 KB of shared memory: by default the first such grid with at most 1024 cells (one
+ * per thread; larger grids run faster as per-grid launches), else the largest such grid;
+ * mg_set_bottom_level and mg_autotune change it.  It performs the same operations per cell as
+ * the per-grid kernels, so the results are identical.  enable = 1 (the default at set-up) or 0;
+ * *first_level (may be NULL) gets the first grid it covers, -1 when it does not apply.
+ * Errors: MG_ERR_ARG. */
 int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level);
 /* Sets the first grid of the one-block bottom kernel (a tuning step of this implementation; the
- * paper has no counterpart): `level` from the largest grid that fits (the first_level that
- * mg_set_bottom_kernel(h, 1, ...) reports) to levels - 2, or -1 for none.  A later start runs
+ * paper has no counterpart): `level` from the largest grid whose sub-cycle fits the kernel's
+ * shared memory (see mg_set_bottom_kernel) to levels - 2, or -1 for none.  A later start runs
  * more grids through the per-grid kernels; the results are the same either way.  mg_autotune
  * also chooses it (mg_stats.bottom_level).  Errors: MG_ERR_ARG (level out of that range, or the
  * bottom kernel does not apply). */

@@ -22,6 +22,7 @@ namespace segmg {
 namespace {
 
 constexpr int kBT = kCoarseThreads;   // threads of the block (the coarsest solve uses them all)
+static_assert(kBT == kBottomThreads, "the host's default first grid assumes this block size");
 
 // One grid in shared memory (row pitch m).
 struct BGrid {

@@ -288,13 +288,18 @@ struct Solver final : SolverBase {
                         if (!encode_sweep_maps(view(l), sh, &lv[l].maps[sh]))
                             return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a grid");
         }
+        // default tile shapes (what mg_autotune chooses on most grids): 32 x 32 tiles, 256 threads
+        // on the finest grid, 512 below
+        for (int l = 0; l < nlev - 1; ++l) shape[l] = l == 0 ? 4 : 5;
         set_bottom(1);
         return MG_OK;
     }
 
     // The bottom kernel runs grids lb .. nlev-1 in one block when the storage is FP32 (or mixed),
     // the model is Spencer-Chen, the fused smoother is selected and at least two grids fit in
-    // its shared memory; lb is the largest grid that fits.
+    // its shared memory (lb_first: the largest grid that fits).  By default it starts at the
+    // first of those grids with at most one cell per thread (the block's fast path; larger grids
+    // run faster as per-grid launches), or at lb_first when there is none.
     int set_bottom(int enable) override {
         lb = lb_first = -1;
         lb_smem = 0;
@@ -307,7 +312,11 @@ struct Solver final : SolverBase {
                 lb_first = l;
             }
         }
-        if (enable && lb_first >= 0) use_bottom_from(lb_first);
+        if (enable && lb_first >= 0) {
+            int l = lb_first;
+            while (l < nlev - 2 && lv[l].n * lv[l].m > kBottomThreads) ++l;
+            use_bottom_from(lv[l].n * lv[l].m <= kBottomThreads ? l : lb_first);
+        }
         drop_graphs();
         return lb;
     }

@@ -195,6 +195,7 @@ struct BottomArgs {
     Scalars *sc;
 };
 constexpr size_t kBottomSmemMax = 200 * 1024;
+constexpr int kBottomThreads = 1024;   // threads of the bottom kernels' blocks
 size_t bottom_smem_bytes(const int *n, const int *m, int lb, int L, int coarse_fp64);
 void prepare_bottom_kernel();
 void launch_bottom(const BottomArgs &A, size_t smem, cudaStream_t st);

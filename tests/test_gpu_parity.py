@@ -294,6 +294,17 @@ def test_bottom_kernel_equals_per_grid_kernels(segmg, shape, levels, nu, precisi
     assert stats[0]["picard_last"] == stats[1]["picard_last"]
 
 
+def largest_fitting_bottom(s, levels):
+    """The largest grid the one-block bottom kernel can start at (the first level accepted)."""
+    for lb in range(levels - 1):
+        try:
+            s.set_bottom_level(lb)
+            return lb
+        except Exception:
+            continue
+    return -1
+
+
 @pytest.mark.parametrize("precision", ["f32", "mixed"])
 def test_every_bottom_level_gives_the_same_result(segmg, precision):
     # where the one-block bottom kernel starts changes only which kernels run the small grids
@@ -301,8 +312,9 @@ def test_every_bottom_level_gives_the_same_result(segmg, precision):
     img, mk, _ = synth.ellipses(256, 256, 8, (8, 128), 6, 0.05, 77)
     outs = []
     s, p = gpu_solver(segmg, img, mk, precision=prec, levels=7)
-    first = s.set_bottom_kernel(True)
-    assert first >= 0
+    default = s.set_bottom_kernel(True)
+    first = largest_fitting_bottom(s, p.levels)
+    assert 0 <= first <= default
     s.close()
     for lb in [first, first + 1, first + 2, -1]:
         s, p = gpu_solver(segmg, img, mk, precision=prec, levels=7)
@@ -330,9 +342,10 @@ def test_cluster_bottom_equals_one_block_and_per_grid(segmg, shape, levels, prec
     n, m = shape
     img, mk, _ = synth.ellipses(n, m, 14, (6, min(n, m) / 2), 6, 0.1, 91 + n)
     s, p = gpu_solver(segmg, img, mk, precision=prec, levels=levels)
-    first = s.set_bottom_kernel(True)
+    first = largest_fitting_bottom(s, p.levels)
+    assert first >= 0
     s.close()
-    # the grid the one-block kernel starts at always fits a cluster here; the grid above it may
+    # the largest grid the one-block kernel can start at always fits a cluster here; the grid above it may
     # not (its cluster needs one SM per tile within one GPC), and is then refused
     runs = [("one-block", None), ("none", None), ("cluster", first), ("cluster", first - 1)]
     outs = []
