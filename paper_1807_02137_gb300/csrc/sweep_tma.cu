@@ -29,9 +29,10 @@ namespace {
 constexpr int kH = 4;
 constexpr long kWaitLimit = 1L << 22;   // try_wait rounds before a wait gives up
 
-template <int OH_, int OW_, int NT_>
+template <int OH_, int OW_, int NT_, int MINB_ = 1>
 struct TShape {
     static constexpr int OH = OH_, OW = OW_, NT = NT_;
+    static constexpr int MinBlocks = MINB_;   // resident blocks per SM asked of the compiler
     static constexpr int RH = OH + 2 * kH, RW = OW + 2 * kH;
     static constexpr int RowPieces = OW / 32 + 2, ColPieces = OH / 32 + 2;
     static constexpr int MkLines = RH > RW ? RH : RW, MkPieces = RowPieces > ColPieces ? RowPieces : ColPieces;
@@ -41,7 +42,9 @@ using TT0 = TShape<32, 64, 256>;
 using TT1 = TShape<32, 32, 128>;
 using TT2 = TShape<64, 64, 512>;
 using TT3 = TShape<32, 64, 512>;
-using TT4 = TShape<32, 32, 256>;
+// 8 blocks of 256 threads per SM (at most 32 registers): every 32 x 32 tile of a 1024^2 grid
+// then has its own resident block, one stage and no persistent loop
+using TT4 = TShape<32, 32, 256, 8>;
 using TT5 = TShape<32, 32, 512>;
 
 template <typename TS, int STAGES>
@@ -138,7 +141,7 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
 // STAGES = 1: one box set per block (half the shared memory, more blocks per SM), used when every
 // tile of the grid gets its own resident block.
 template <int SWEEP, typename TS, int STAGES>
-__global__ void __launch_bounds__(TS::NT) k_sweep_tma(LevelView<float> L, const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<float> L, const __grid_constant__ CUtensorMap tin,
                                                       const __grid_constant__ CUtensorMap tG,
                                                       const __grid_constant__ CUtensorMap tf, int *err) {
     constexpr int kOH = TS::OH, kOW = TS::OW, kRH = TS::RH, kRW = TS::RW;
