@@ -15,9 +15,10 @@ namespace {
 // sum out^2;
 // mode 1: out += L(pn + uin)   (the FAS right-hand side f^{2h} = N^{2h} phi^{2h} + r^{2h}).
 // ---------------------------------------------------------------------------------------
+// (FP32: at most 32 registers, so that 8 blocks share an SM and a 1024^2 grid's tiles fit one wave)
 template <typename T>
-__global__ void __launch_bounds__(256) k_residual(LevelView<T> L, const T *uin, const double *area,
-                                                  T *out, int mode, double *partials) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 1)
+    k_residual(LevelView<T> L, const T *uin, const double *area, T *out, int mode, double *partials) {
     constexpr int R = 36;
     __shared__ T sP[R][R + 1];
     __shared__ T sU[R][R + 1];

@@ -27,8 +27,11 @@ namespace {
 // ---------------------------------------------------------------------------------------
 // WARPS warps per tile (8, 16 or 32): more threads per tile shorten each thread's chain of work
 // on small grids, where a launch is latency-bound; large grids use 8 (more tiles per SM).
+// (FP32 with 8 warps: at most 32 registers, so that 7 blocks share an SM and a 1024^2 grid's
+// tiles fit one wave)
 template <typename T, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_snapshot(LevelView<T> L, const double *area) {
+__global__ void __launch_bounds__(32 * WARPS, (WARPS == 8 && sizeof(T) == 4) ? 7 : 1)
+    k_snapshot(LevelView<T> L, const double *area) {
     constexpr int R = 36, NT = 32 * WARPS, RPW = 32 / WARPS;   // threads; tile rows per warp
     __shared__ T sP[R][R + 1];
     __shared__ T sU[R][R + 1];
