@@ -15,9 +15,10 @@ namespace {
 // sum out^2;
 // mode 1: out += L(pn + uin)   (the FAS right-hand side f^{2h} = N^{2h} phi^{2h} + r^{2h}).
 // ---------------------------------------------------------------------------------------
-// (FP32: at most 32 registers, so that 8 blocks share an SM and a 1024^2 grid's tiles fit one wave)
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 1)
+// MINB > 1 asks the compiler for that many resident blocks per SM (FP32, fewer registers): used
+// when it lets every tile of the grid be resident at once (a 1024^2 grid)
+template <typename T, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB)
     k_residual(LevelView<T> L, const T *uin, const double *area, T *out, int mode, double *partials) {
     constexpr int R = 36;
     __shared__ T sP[R][R + 1];
@@ -298,12 +299,36 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(LevelView<T> L, Model
 int num_partials(int n, int m) { return ((m + 31) / 32) * ((n + 31) / 32); }
 
 
+// Resident blocks per SM of the FP32 residual held to 8 blocks per SM, and the SM count
+// (measured once at set-up, outside any capture).
+struct ResOcc {
+    int per_sm = 0, sms = 1;
+    ResOcc() {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residual<float, 8>, 256, 0) != cudaSuccess)
+            per_sm = 0;
+    }
+};
+const ResOcc &res_occ() {
+    static const ResOcc o;
+    return o;
+}
+
 template <typename T>
 void launch_residual(const LevelView<T> &L, const T *uin, const double *area, T *out, int mode,
                      double *partials, int npart, double *norm_out, cudaStream_t st) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, 8);
-    // the per-block partial sums (FP64, slow on this GPU) only when the norm is wanted
-    k_residual<T><<<grid, block, 0, st>>>(L, uin, area, out, mode, norm_out ? partials : nullptr);
+    // the per-block partial sums (FP64, slow on this GPU) only when the norm is wanted; the
+    // register-limited FP32 variant when it makes every tile resident at once (same operations,
+    // same order)
+    const ResOcc &o = res_occ();
+    if (sizeof(T) == 4 && (long)grid.x * grid.y <= (long)o.sms * o.per_sm)
+        k_residual<T, sizeof(T) == 4 ? 8 : 1><<<grid, block, 0, st>>>(L, uin, area, out, mode,
+                                                                      norm_out ? partials : nullptr);
+    else
+        k_residual<T><<<grid, block, 0, st>>>(L, uin, area, out, mode, norm_out ? partials : nullptr);
     if (mode == 0 && norm_out) k_sum_partials<<<1, 1024, 0, st>>>(partials, npart, norm_out);
 }
 
@@ -328,6 +353,7 @@ void launch_residual_restrict(const LevelView<float> &L, const LevelView<float> 
 }
 
 void prepare_coarse_kernels() {
+    (void)res_occ();
     cudaFuncSetAttribute(k_residual_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ResRestrictSmem));
     cudaFuncSetAttribute(k_coarse<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);
     cudaFuncSetAttribute(k_coarse<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemMax);

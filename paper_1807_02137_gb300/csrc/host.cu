@@ -288,9 +288,17 @@ struct Solver final : SolverBase {
                         if (!encode_sweep_maps(view(l), sh, &lv[l].maps[sh]))
                             return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a grid");
         }
-        // default tile shapes (what mg_autotune chooses on most grids): 32 x 32 tiles, 256 threads
-        // on the finest grid, 512 below
-        for (int l = 0; l < nlev - 1; ++l) shape[l] = l == 0 ? 4 : 5;
+        // default tile shapes (what mg_autotune chooses on grids up to 1024^2): 32 x 32 tiles (256
+        // threads on the finest grid, 512 below) where they all fit one wave of 8 blocks per SM;
+        // 32 x 64 tiles on larger grids, where the smaller halo share counts
+        {
+            int dev = 0, sms = 1;
+            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            for (int l = 0; l < nlev - 1; ++l) {
+                const long tiles = (long)((lv[l].n + 31) / 32) * ((lv[l].m + 31) / 32);
+                shape[l] = tiles <= 8L * std::max(sms, 1) ? (l == 0 ? 4 : 5) : 0;
+            }
+        }
         set_bottom(1);
         return MG_OK;
     }

@@ -27,11 +27,10 @@ namespace {
 // ---------------------------------------------------------------------------------------
 // WARPS warps per tile (8, 16 or 32): more threads per tile shorten each thread's chain of work
 // on small grids, where a launch is latency-bound; large grids use 8 (more tiles per SM).
-// (FP32 with 8 warps: at most 32 registers, so that 7 blocks share an SM and a 1024^2 grid's
-// tiles fit one wave)
-template <typename T, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS, (WARPS == 8 && sizeof(T) == 4) ? 7 : 1)
-    k_snapshot(LevelView<T> L, const double *area) {
+// MINB > 1 asks the compiler for that many resident blocks per SM (fewer registers): used when
+// it lets every tile of the grid be resident at once (a 1024^2 grid with 8 warps per tile)
+template <typename T, int WARPS, int MINB = 1>
+__global__ void __launch_bounds__(32 * WARPS, MINB) k_snapshot(LevelView<T> L, const double *area) {
     constexpr int R = 36, NT = 32 * WARPS, RPW = 32 / WARPS;   // threads; tile rows per warp
     __shared__ T sP[R][R + 1];
     __shared__ T sU[R][R + 1];
@@ -394,11 +393,11 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
 
 }  // namespace
 
-// Resident snapshot blocks per SM for 8, 16, 32 warps per tile (measured once, outside any
-// capture) and the SM count.
+// Resident snapshot blocks per SM for 8, 16, 32 warps per tile and for 8 warps held to 7
+// blocks per SM (FP32) (measured once, outside any capture), and the SM count.
 template <typename T>
 struct SnapOcc {
-    int per_sm[3] = {1, 1, 1}, sms = 1;
+    int per_sm[4] = {1, 1, 1, 0}, sms = 1;
     SnapOcc() {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -407,6 +406,8 @@ struct SnapOcc {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot<T, 8>, 256, 0) == cudaSuccess && v > 0) per_sm[0] = v;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot<T, 16>, 512, 0) == cudaSuccess && v > 0) per_sm[1] = v;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot<T, 32>, 1024, 0) == cudaSuccess && v > 0) per_sm[2] = v;
+        if constexpr (sizeof(T) == 4)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot<T, 8, 7>, 256, 0) == cudaSuccess) per_sm[3] = v;
     }
 };
 
@@ -426,6 +427,8 @@ void launch_snapshot(const LevelView<T> &L, const double *area, cudaStream_t st)
         k_snapshot<T, 32><<<grid, dim3(32, 32), 0, st>>>(L, area);
     else if (tiles <= (long)o.sms * o.per_sm[1])
         k_snapshot<T, 16><<<grid, dim3(32, 16), 0, st>>>(L, area);
+    else if (sizeof(T) == 4 && tiles <= (long)o.sms * o.per_sm[3])
+        k_snapshot<T, 8, sizeof(T) == 4 ? 7 : 1><<<grid, dim3(32, 8), 0, st>>>(L, area);
     else
         k_snapshot<T, 8><<<grid, dim3(32, 8), 0, st>>>(L, area);
 }
