@@ -9,6 +9,8 @@ namespace segmg {
 
 constexpr int kCoarseThreads = 1024;
 constexpr int kWarpCoarseMax = 256;   // grids of at most this many cells are solved by one warp
+constexpr int kRegBand = 8;           // one warp keeps the band factor in registers up to this width
+                                      // (and at most 32 unknowns: one row per lane)
 
 // The threads that run the coarsest solve: one warp (no block barriers) or the whole block.
 template <int NT>
@@ -68,6 +70,70 @@ template <>
 __device__ __forceinline__ float rsqrt_of<float>(float s) { return rsqrtf(s); }
 template <>
 __device__ __forceinline__ double rsqrt_of<double>(double s) { return 1.0 / sqrt(s); }
+
+// Banded Cholesky factorisation and solve of A x = b by one warp for N <= 32 unknowns and band
+// width bw <= kRegBand: lane r holds row r of the band (Lr[d] = A(r, r - d), then L(r, r - d);
+// Lr[0] keeps 1 / L(r, r)).  Column k's pivot and entries reach the other lanes by shuffles;
+// every element receives the same updates, in the same order, as in the shared-memory
+// factorisation.  The substitutions accumulate column by column.  Returns false (on every lane)
+// when a pivot is not positive; else lane r < N holds x(r) in xr.
+template <typename C>
+__device__ __forceinline__ bool warp_band_solve(const C *band, const C *b, int N, int bw, C &xr) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int r = threadIdx.x & 31, bw1 = bw + 1;
+    C Lr[kRegBand + 1];
+#pragma unroll
+    for (int d = 0; d <= kRegBand; ++d) Lr[d] = (r < N && d <= bw && d <= r) ? band[(size_t)r * bw1 + d] : C(0);
+    for (int k = 0; k < N; ++k) {
+        const C piv = __shfl_sync(kFull, Lr[0], k);
+        if (!(piv > C(0))) return false;
+        const C rkk = rsqrt_of<C>(piv);
+        if (r == k) Lr[0] = rkk;
+        const int dk = r - k;
+        C lk = C(0);   // L(r, k) once column k is scaled
+#pragma unroll
+        for (int d = 1; d <= kRegBand; ++d)
+            if (d == dk && d <= bw) {
+                Lr[d] *= rkk;
+                lk = Lr[d];
+            }
+        // trailing update: L(r, c) -= L(r, k) L(c, k) for k < c <= r <= k + bw
+#pragma unroll
+        for (int j = 1; j <= kRegBand; ++j) {
+            if (j > bw) break;
+            const C lck = __shfl_sync(kFull, lk, min(k + j, 31));
+            const int idx = dk - j;   // r - c
+#pragma unroll
+            for (int d = 0; d < kRegBand; ++d)
+                if (d == idx && dk <= bw && r < N) Lr[d] -= lk * lck;
+        }
+    }
+    // forward: y = L^-1 b
+    const C br = r < N ? b[r] : C(0);
+    C acc = C(0), y = C(0);
+    for (int c = 0; c < N; ++c) {
+        const C yc = __shfl_sync(kFull, (br - acc) * Lr[0], c);
+        if (r == c) y = yc;
+        const int dc = r - c;
+#pragma unroll
+        for (int d = 1; d <= kRegBand; ++d)
+            if (d == dc && d <= bw) acc += Lr[d] * yc;
+    }
+    // backward: x = L^-T y
+    C acc2 = C(0);
+    xr = C(0);
+    for (int c = N - 1; c >= 0; --c) {
+        const C xc = __shfl_sync(kFull, (y - acc2) * Lr[0], c);
+        if (r == c) xr = xc;
+#pragma unroll
+        for (int d = 1; d <= kRegBand; ++d) {
+            if (d > bw) break;
+            const C lcd = __shfl_sync(kFull, Lr[d], c);   // L(c, c - d)
+            if (r == c - d) acc2 += lcd * xc;
+        }
+    }
+    return true;
+}
 
 // Run by the NT threads of a team (NT = 32: warp 0; else the whole block) in the arithmetic
 // type C (storage T); scratch holds coarse_scratch_elems(n, m) values of C.
@@ -172,46 +238,61 @@ __device__ void coarse_solve_team(const CoarseGrid<T> &L, ModelParams mp, double
             b[r] = cdiff * pflux - (C)L.F[o] - area - (L.has_rhs ? (C)L.rhs[o] : C(0));
         }
         TM::sync();
-        // right-looking banded Cholesky: band[r*bw1 + (r-c)] = L(r, c); the diagonal entry
-        // keeps 1 / L(k, k) once column k is done
-        for (int k = 0; k < N && !(*s_err); ++k) {
-            if (tid == 0) {
-                C d = band[(size_t)k * bw1];
-                if (!(d > C(0))) (*s_err) = 1;
-                else band[(size_t)k * bw1] = rsqrt_of<C>(d);
-            }
+        bool in_regs = false;
+        if constexpr (NT == 32) in_regs = N <= 32 && bw <= kRegBand;
+        if (in_regs) {
+            // the tiny coarsest grids: the band factor in registers, one row per lane
+            C xr;
+            const bool ok = warp_band_solve<C>(band, b, N, bw, xr);
             TM::sync();
+            if (!ok) {
+                if (tid == 0) *s_err = 1;
+                TM::sync();
+                break;
+            }
+            if (tid < N) b[tid] = xr;
+        } else {
+            // right-looking banded Cholesky: band[r*bw1 + (r-c)] = L(r, c); the diagonal entry
+            // keeps 1 / L(k, k) once column k is done
+            for (int k = 0; k < N && !(*s_err); ++k) {
+                if (tid == 0) {
+                    C d = band[(size_t)k * bw1];
+                    if (!(d > C(0))) (*s_err) = 1;
+                    else band[(size_t)k * bw1] = rsqrt_of<C>(d);
+                }
+                TM::sync();
+                if ((*s_err)) break;
+                const C rkk = band[(size_t)k * bw1];
+                const int last = min(k + bw, N - 1), cnt = last - k;
+                for (int t = tid; t < cnt; t += nt) band[(size_t)(k + 1 + t) * bw1 + (1 + t)] *= rkk;
+                TM::sync();
+                for (int t = tid; t < cnt * cnt; t += nt) {
+                    // the trailing triangle: rows ii >= columns jj (integer indexing only)
+                    const int ii = t / cnt, jj = t - ii * cnt;
+                    if (jj > ii) continue;
+                    int ri = k + 1 + ii, rj = k + 1 + jj;
+                    band[(size_t)ri * bw1 + (ri - rj)] -= band[(size_t)ri * bw1 + (ri - k)] * band[(size_t)rj * bw1 + (rj - k)];
+                }
+                TM::sync();
+            }
             if ((*s_err)) break;
-            const C rkk = band[(size_t)k * bw1];
-            const int last = min(k + bw, N - 1), cnt = last - k;
-            for (int t = tid; t < cnt; t += nt) band[(size_t)(k + 1 + t) * bw1 + (1 + t)] *= rkk;
-            TM::sync();
-            for (int t = tid; t < cnt * cnt; t += nt) {
-                // the trailing triangle: rows ii >= columns jj (integer indexing only)
-                const int ii = t / cnt, jj = t - ii * cnt;
-                if (jj > ii) continue;
-                int ri = k + 1 + ii, rj = k + 1 + jj;
-                band[(size_t)ri * bw1 + (ri - rj)] -= band[(size_t)ri * bw1 + (ri - k)] * band[(size_t)rj * bw1 + (rj - k)];
-            }
-            TM::sync();
-        }
-        if ((*s_err)) break;
-        // forward and backward substitution by warp 0
-        if (tid < 32) {
-            for (int r = 0; r < N; ++r) {
-                C s = C(0);
-                for (int c = max(0, r - bw) + tid; c < r; c += 32) s += band[(size_t)r * bw1 + (r - c)] * y[c];
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-                if (tid == 0) y[r] = (b[r] - s) * band[(size_t)r * bw1];
-                __syncwarp();
-            }
-            for (int r = N - 1; r >= 0; --r) {
-                C s = C(0);
-                int c1 = min(N - 1, r + bw);
-                for (int c = r + 1 + tid; c <= c1; c += 32) s += band[(size_t)c * bw1 + (c - r)] * b[c];
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-                if (tid == 0) b[r] = (y[r] - s) * band[(size_t)r * bw1];
-                __syncwarp();
+            // forward and backward substitution by warp 0
+            if (tid < 32) {
+                for (int r = 0; r < N; ++r) {
+                    C s = C(0);
+                    for (int c = max(0, r - bw) + tid; c < r; c += 32) s += band[(size_t)r * bw1 + (r - c)] * y[c];
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+                    if (tid == 0) y[r] = (b[r] - s) * band[(size_t)r * bw1];
+                    __syncwarp();
+                }
+                for (int r = N - 1; r >= 0; --r) {
+                    C s = C(0);
+                    int c1 = min(N - 1, r + bw);
+                    for (int c = r + 1 + tid; c <= c1; c += 32) s += band[(size_t)c * bw1 + (c - r)] * b[c];
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+                    if (tid == 0) b[r] = (y[r] - s) * band[(size_t)r * bw1];
+                    __syncwarp();
+                }
             }
         }
         TM::sync();
