@@ -42,7 +42,8 @@ enum {
     MG_ERR_NAN = -2,        /* NaN or Inf in the input image or in a residual norm */
     MG_ERR_CUDA = -3,       /* a CUDA runtime call failed (detail in mg_last_error) */
     MG_ERR_DIVERGED = -4,   /* residual grew by more than 1e3 over its initial value */
-    MG_ERR_TIMEOUT = -5,    /* an iteration cap was reached without meeting the tolerance */
+    MG_ERR_TIMEOUT = -5,    /* an iteration cap was reached without meeting the tolerance, or a
+                               bounded wait on the device gave up (mg_set_wait_limit) */
     MG_ERR_NOT_SPD = -6,    /* coarsest-grid Cholesky met a non-positive pivot */
     MG_ERR_NOMEM = -7,      /* device allocation failed */
     MG_ERR_STATE = -8       /* call out of order (e.g. mg_vcycle before mg_begin_step) */
@@ -96,6 +97,13 @@ typedef struct {
     int coarse_solver;     /* MG_COARSE_PICARD, or MG_COARSE_AOS: coarse_maxit AOS iterations of
                               step aos_dt (Algorithm 1 "time-marching or AOS"; Sec. 5 uses 100) */
     double aos_dt;         /* AOS artificial time step (> 0) */
+    double stall_ratio;    /* pseudo-time step control of mg_solve_step / mg_solve / the batch: an
+                              attempt at a step is rejected when, from its 4th V-cycle on,
+                              rho_j > stall_ratio * rho_{j-2}, when a V-cycle diverges or returns a
+                              non-finite residual, or when the cycle cap is reached; phi is then
+                              restored to phi^n and the step is retried with tau / 2.  0 switches
+                              the control off (0 <= stall_ratio < 1; default 0.6) */
+    int max_halvings;      /* rejected attempts allowed per step (>= 0; default 10) */
 } mg_params;
 
 /* Counters and scalars of the current state (mg_get_stats). */
@@ -116,6 +124,8 @@ typedef struct {
     long long learned_rejected;   /* ... and rejected (rerun with the plain smoother) */
     int bottom_level;      /* first grid of the one-block bottom kernel, -1 when it is not used */
     int cluster_level;     /* first grid of the cluster bottom kernel, -1 when it is not used */
+    double tau;            /* pseudo-time step of the next / current step (halved by the control) */
+    int attempts_rejected; /* step attempts rejected by the step control so far */
 } mg_stats;
 
 /* Optional device allocator (for example a framework's caching allocator).  alloc returns a
@@ -130,7 +140,8 @@ typedef struct {
 /* Fills *p with the defaults: Spencer-Chen, mu = 1, lambda1 = lambda2 = 10, theta = 1,
  * nu = 1, eps = 1, beta = 1e-6, beta_edge = 1, sigma_blur = 1, sigma_d = 0.05 max(n, m),
  * Sigma = 2, tau = 1, V(2,2), levels = as many halvings as keep min(n, m) >= 4 (at most 12),
- * MG_F32, fused smoother, coarse_maxit = 100, coarse_tol = 1e-13, use_graph = 1. */
+ * MG_F32, fused smoother, coarse_maxit = 100, coarse_tol = 1e-13, use_graph = 1,
+ * stall_ratio = 0.6, max_halvings = 10. */
 int mg_default_params(mg_params *p, int n, int m);
 
 /* Builds a solver for one n x m image (Sec. 2.2 data, Sec. 5 initialisation):
@@ -167,8 +178,14 @@ int mg_vcycle(mg_handle h, double *rho);
  * eta = ||phi - phi^n|| / ||phi^n|| (to *eta if not NULL; waits). */
 int mg_end_step(mg_handle h, double *eta);
 
-/* mg_begin_step, then V-cycles until rho <= tol or max_cycles, then mg_end_step.  Returns
- * MG_ERR_TIMEOUT (state still valid) when max_cycles is reached first. */
+/* mg_begin_step, then V-cycles until rho <= tol or max_cycles, then mg_end_step.
+ * With the step control on (params.stall_ratio > 0) an attempt that stalls, diverges or reaches
+ * max_cycles is rejected: phi is restored to phi^n, tau is halved (it stays halved for the
+ * following steps) and the step starts again, up to params.max_halvings times.  The paper solves
+ * the stationary equation and stops on the relative change (Sec. 5), so it has no rule for the
+ * pseudo-time steps; this is the reading this library takes for them.
+ * *cycles (may be NULL) gets the V-cycles of all attempts, *rho the last residual ratio.
+ * Returns MG_ERR_TIMEOUT (state still valid: the last attempt's phi) when no attempt reached tol. */
 int mg_solve_step(mg_handle h, double tol, int max_cycles, int *cycles, double *rho);
 
 /* Pseudo-time steps (each by mg_solve_step) until eta < eta_stop or max_steps; *steps gets
@@ -192,6 +209,15 @@ int mg_set_regions(mg_handle h, double c1, double c2);
 int mg_get_level(mg_handle h, int level, int field, void *out);
 
 int mg_get_stats(mg_handle h, mg_stats *s);
+
+/* Bound of the device-side waits of the FP32 fused sweep (the Tensor Memory Accelerator copies of
+ * a tile into shared memory complete on an mbarrier; each wait polls it at most `rounds` times,
+ * default 4,194,304).  When a wait gives up, the block records it, waits once more (with the
+ * default bound) for the copies it has in flight, and ends; the next mg_vcycle / mg_solve_step
+ * returns MG_ERR_TIMEOUT and the handle stays usable.  rounds = 0 makes every such wait give up at
+ * once (for tests of that path).  A diagnostic setting of this implementation; the paper has no
+ * counterpart.  Errors: MG_ERR_ARG (rounds < 0). */
+int mg_set_wait_limit(mg_handle h, long long rounds);
 
 /* Whole pipeline through host buffers: copies the float image to the device, runs mg_setup,
  * then mg_solve(tol, max_cycles, eta_stop, max_steps) with the given parameters (precision
@@ -342,18 +368,22 @@ int mg_time_kernels(mg_handle h, int level, int reps, double *ms);
 /* Residual norm ||L(phi)||_2 of one grid function, with no device allocation.  The paper has no
  * counterpart: this serves callers that cannot allocate device memory when they need the norm,
  * such as code whose device memory is owned by a framework's pool or a running real-time loop
- * that may not call cudaMalloc (it synchronises the device).  It computes the same quantity, with
- * the same arithmetic and summation order, as the reference norm of mg_begin_step for a step
- * starting at phi (zero increment, finest grid, spacing 1, no FAS right-hand side):
+ * that may not call cudaMalloc (it synchronises the device).  It computes the same quantity as the
+ * reference norm of mg_begin_step for a step starting at phi (zero increment, finest grid,
+ * spacing 1, no FAS right-hand side), and agrees with it to about 1e-12 relative (the per-tile
+ * partial sums may be added in another order):
  *   phi, w, F  device, n*m dense row-major arrays of float (MG_F32) or double (MG_F64): the level
  *              set, the length weight w and the fitting field F (mg_get_level fields 0, 1, 4);
  *   p          uses mu, beta, model and precision; only MG_MODEL_SC is accepted;
  *   norm       host, receives the FP64-accumulated norm;  stream may be NULL (default stream).
  * Its scratch is one file-scope device array sized for 65,536 tiles of 32 x 32 cells (for example
- * 8192 x 8192); larger grids get MG_ERR_ARG.  The array's device address is looked up on the
- * first call made on each device (with that device current), so make that first call before any
- * stream capture.  Every call shares the array: calls that overlap on the GPU race on it.  The
- * call waits for its stream.  Errors: MG_ERR_ARG, MG_ERR_CUDA (mg_last_error is not updated). */
+ * 8192 x 8192); larger grids, and grids of more than 65,535 tile rows, get MG_ERR_ARG before any
+ * device access.  The array's device address is looked up on the first call made on each device
+ * (with that device current) and kept for the life of the process, so make that first call before
+ * any stream capture; after cudaDeviceReset on a device the kept address is no longer valid, and
+ * this entry point must not be called on that device again.  Every call shares the array: calls
+ * that overlap on the GPU race on it.  The call waits for its stream.  Errors: MG_ERR_ARG,
+ * MG_ERR_CUDA (mg_last_error is not updated). */
 int mg_residual_norm_noalloc(const void *phi, const void *w, const void *F, int n, int m,
                              const mg_params *p, double *norm, void *stream);
 

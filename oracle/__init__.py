@@ -92,6 +92,7 @@ def lib():
                 "or_get_level": ([C.c_void_p, C.c_int, C.c_int, D], None),
                 "or_get_scalars": ([C.c_void_p, D], None),
                 "or_set_c": ([C.c_void_p, C.c_double, C.c_double], None),
+                "or_set_inv_tau": ([C.c_void_p, C.c_double], None),
                 "or_frozen_coeffs": ([D, D, D, D, C.c_int, C.c_int, C.c_double, P, C.c_double, C.c_double, D], None),
                 "or_smooth_given": ([D, C.c_int, C.c_int, C.c_double, C.c_int, D], None),
                 "or_members": ([D, C.c_int, C.c_int, C.c_double, C.c_int, I], None),
@@ -377,3 +378,48 @@ class Solver:
             if r <= tol:
                 break
         return hist
+
+    def set_tau(self, tau):
+        """tau of the following pseudo-time steps (None or inf: the stationary equation)."""
+        lib().or_set_inv_tau(self._h, 0.0 if tau is None or tau == float("inf") else 1.0 / tau)
+
+    def solve_step_controlled(self, tau, tol, max_cycles=40, stall_ratio=0.6, max_halvings=10):
+        """One pseudo-time step under the step-size control of the outer driver.
+
+        The implicit step with pseudo-time tau is a nonlinear problem of its own; its lagged-
+        coefficient V-cycles (Algorithm 1 with the Sec. 4 smoother) contract well for small
+        enough tau and can stall for larger tau once the level set has flat parts, where the
+        coefficients w / |grad phi|_beta become very large.  The paper solves the stationary
+        equation and stops on the relative change only (Sec. 5), so it has no rule for this;
+        the reading taken here:
+          - an attempt runs V-cycles j = 1, 2, ... until rho_j <= tol (the step is accepted);
+          - it is rejected when j >= 4 and rho_j > stall_ratio * rho_{j-2} (less than a factor
+            1/stall_ratio gained in two V-cycles), when rho_j is not finite or above 1e3, or when
+            max_cycles V-cycles did not reach tol;
+          - a rejected attempt restores phi = phi^n and the step is tried again with tau / 2, at
+            most max_halvings times.
+        Returns (tau, attempts): the tau of the accepted step (the next step starts from it),
+        and per attempt (tau, list of rho).  Raises RuntimeError when no attempt was accepted."""
+        phin = self.phi
+        attempts = []
+        for _ in range(max_halvings + 1):
+            self.set_tau(tau)
+            self.begin_step()
+            hist = []
+            ok = False
+            for j in range(1, max_cycles + 1):
+                r = self.vcycle()
+                hist.append(r)
+                if r <= tol:
+                    ok = True
+                    break
+                if not np.isfinite(r) or r > 1e3:
+                    break
+                if j >= 4 and r > stall_ratio * hist[-3]:
+                    break
+            attempts.append((tau, hist))
+            if ok:
+                return tau, attempts
+            self.phi = phin
+            tau = tau / 2.0
+        raise RuntimeError(f"no pseudo-time step reached rho <= {tol}: {attempts}")

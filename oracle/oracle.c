@@ -601,7 +601,7 @@ static void hs2_parallel(const or_coeffs *k, double Sigma, double *phi)
                     if ((i + j) % 2 == colour && !member[(size_t)i * m + j]) {
                         size_t q = (size_t)i * m + j;
                         double g = point_update(k, phi, i, j);
-                        /* relaxation weight (SURVEY NEXT-2 reading): phi += omega (g - phi) */
+                        /* per-cell relaxation weight of the learned-weights extension: phi += omega (g - phi) */
                         phi[q] = k->omega ? phi[q] + k->omega[q] * (g - phi[q]) : g;
                     }
         }
@@ -1216,8 +1216,13 @@ void or_get_scalars(const or_solver *s, double *out /* c1, c2, A1, res0, picard_
 }
 void or_set_c(or_solver *s, double c1, double c2) { s->c1 = c1; s->c2 = c2; }
 
+/* Sets 1/tau of the following pseudo-time steps (the step-size control of the outer driver
+ * halves tau when a step stops contracting; the next or_begin_step folds the new value into
+ * the fitting field's -phi^n / tau term). */
+void or_set_inv_tau(or_solver *s, double inv_tau) { s->p.inv_tau = inv_tau; }
+
 /* Per-cell relaxation weights of the point updates of the parallel Hybrid Smoother 2 on grid l
- * (NULL: back to 1).  Used with learned weights. */
+ * (NULL: back to 1).  Used by the learned relaxation-weights extension. */
 void or_set_omega(or_solver *s, int l, const double *w)
 {
     or_level *L = &s->lv[l];

@@ -114,6 +114,12 @@ struct SolverBase {
     virtual int set_learned(const float *theta, int mode, int refresh) = 0;
     virtual int set_omega(int l, const void *w) = 0;
     virtual int record_crops(float *data, int first, int count, unsigned long long seed) = 0;
+    // pseudo-time step control (mg_solve_step): the parameters, a restart of the current step
+    // from phi^n with a new tau, and the bookkeeping of the step's V-cycles
+    virtual const mg_params &params() const = 0;
+    virtual int restart_step(double tau) = 0;
+    virtual void set_cycles_step(int c) = 0;
+    virtual int set_wait_limit(long long rounds) = 0;
 };
 
 template <typename T>
@@ -149,6 +155,8 @@ struct Solver final : SolverBase {
     int kcap = 0;
     double A1 = 0, res0 = 0, rho = 0, eta = 0;
     int steps = 0, cycles_step = 0, cycles_total = 0;
+    int rejected = 0;             // step attempts rejected by the step control
+    long long wait_limit = kDefaultWaitLimit;   // try_wait rounds of the TMA sweep's bounded waits
     bool in_step = false;
     cudaGraphExec_t gexec = nullptr;
     long long launches = 0, graph_nodes = 0;
@@ -523,6 +531,7 @@ struct Solver final : SolverBase {
         learn_backoff = 1;
         // the last residual norm starts at the reference one (rho = 1 until a V-cycle runs)
         CK(cudaMemcpyAsync(&dsc->norm2, &dsc->norm2_0, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(&dsc->halt, 0, sizeof(int), st));
         if (!std::isfinite(res0)) return fail(MG_ERR_NAN, "non-finite initial residual");
         in_step = true;
         cycles_step = 0;
@@ -551,7 +560,8 @@ struct Solver final : SolverBase {
         } else if (p.smoother == MG_SMOOTH_FUSED_VEC) {
             launch_sweep_fused<T>(v, k, sh, st);
         } else {
-            if constexpr (std::is_same<T, float>::value) launch_sweep_tma(v, k, sh, lv[l].maps[sh], &dsc->err, st);
+            if constexpr (std::is_same<T, float>::value)
+                launch_sweep_tma(v, k, sh, lv[l].maps[sh], &dsc->err, wait_limit, st);
             else launch_sweep_fused<T>(v, k, sh, st);
         }
     }
@@ -858,7 +868,11 @@ struct Solver final : SolverBase {
         rho = current_rho();
         if (rhoout) *rhoout = rho;
         if (hsc->err & 1) return fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
-        if (hsc->err & 4) return fail(MG_ERR_CUDA, "a tile copy into shared memory did not complete in time");
+        if (hsc->err & 4) {   // reported once: the word is cleared so the handle stays usable
+            CK(cudaMemsetAsync(&dsc->err, 0, sizeof(int), st));
+            CK(cudaStreamSynchronize(st));
+            return fail(MG_ERR_TIMEOUT, "a tile copy into shared memory did not complete within the wait limit");
+        }
         if (!std::isfinite(rho)) return fail(MG_ERR_NAN, "non-finite residual");
         if (rho > 1e3) return fail(MG_ERR_DIVERGED, "residual grew by more than 1e3");
         return MG_OK;
@@ -945,6 +959,30 @@ struct Solver final : SolverBase {
         return MG_OK;
     }
 
+    const mg_params &params() const override { return p; }
+
+    int set_wait_limit(long long rounds) override {
+        if (rounds < 0) return fail(MG_ERR_ARG, "wait limit < 0");
+        wait_limit = rounds;
+        drop_graphs();   // the limit is a launch argument baked into the graphs
+        return MG_OK;
+    }
+    void set_cycles_step(int c) override { cycles_step = c; }
+
+    // Rejects the current attempt at a step: phi = phi^n again (the increment u of the finest
+    // grid is zeroed; the coarse grids are rebuilt by every V-cycle) and the following attempts
+    // and steps use `tau` (the graphs, which hold 1/tau, are captured again).
+    int restart_step(double tau) override {
+        if (!in_step) return fail(MG_ERR_STATE, "restart outside a step");
+        Level<T> &F = lv[0];
+        CK(cudaMemset2DAsync(F.u, (size_t)F.pitch * sizeof(T), 0, (size_t)F.m * sizeof(T), F.n, st));
+        p.tau = tau;
+        ++rejected;
+        drop_graphs();
+        in_step = false;
+        return MG_OK;
+    }
+
     int end_step(double *etaout) override {
         if (!in_step) return fail(MG_ERR_STATE, "mg_end_step before mg_begin_step");
         launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
@@ -1020,6 +1058,8 @@ struct Solver final : SolverBase {
         s->learned_rejected = learned_rej;
         s->bottom_level = lc >= 0 ? -1 : lb;
         s->cluster_level = lc;
+        s->tau = p.tau;
+        s->attempts_rejected = rejected;
         return MG_OK;
     }
 
@@ -1087,7 +1127,56 @@ int check_params(const mg_params *p, int n, int m) {
     if (p->coarse_maxit < 1 || !(p->coarse_tol >= 0)) return fail(MG_ERR_ARG, "coarse_maxit / coarse_tol");
     if (p->model == MG_MODEL_SC && p->tau == 0 && p->lambda1 == 0 && p->lambda2 == 0 && p->theta == 0)
         return fail(MG_ERR_ARG, "degenerate model");
+    if (!(p->stall_ratio >= 0 && p->stall_ratio < 1) || p->max_halvings < 0 || p->max_halvings > 60)
+        return fail(MG_ERR_ARG, "stall_ratio must be in [0, 1) and max_halvings in [0, 60]");
     return MG_OK;
+}
+
+// The step control's test on the residual history of one attempt (rho[0..j-1] after V-cycle j):
+// reject from the 4th V-cycle on when two V-cycles gained less than a factor 1 / stall_ratio.
+bool attempt_stalled(const std::vector<double> &rho, double stall_ratio) {
+    const size_t j = rho.size();
+    return stall_ratio > 0 && j >= 4 && rho[j - 1] > stall_ratio * rho[j - 3];
+}
+
+// One pseudo-time step under the step control (mg_solve_step): attempts from phi^n with tau,
+// tau / 2, ... until one reaches tol.  A rejected attempt restores phi^n.
+int solve_step_controlled(SolverBase *s, double tol, int max_cycles, int *cycles, double *rho) {
+    const bool control = s->params().stall_ratio > 0;
+    int total = 0, rc = MG_OK;
+    double r = 1.0;
+    bool ok = false;
+    for (int attempt = 0;; ++attempt) {
+        if ((rc = s->begin_step(nullptr))) return rc;
+        std::vector<double> hist;
+        bool bad = false;   // diverged or non-finite: the state is not kept
+        for (int j = 1; j <= max_cycles; ++j) {
+            rc = s->vcycle(&r);
+            ++total;
+            if (rc == MG_ERR_DIVERGED || rc == MG_ERR_NAN) {
+                if (!control) return rc;
+                bad = true;
+                break;
+            }
+            if (rc) return rc;
+            hist.push_back(r);
+            if (r <= tol) { ok = true; break; }
+            if (control && attempt_stalled(hist, s->params().stall_ratio)) break;
+        }
+        if (ok || !control) break;
+        const double tau = s->params().tau;
+        if (attempt >= s->params().max_halvings || !(tau > 0)) {
+            if (bad && (rc = s->restart_step(tau))) return rc;   // keep phi^n, not a diverged state
+            if (bad && (rc = s->begin_step(nullptr))) return rc;
+            break;
+        }
+        if ((rc = s->restart_step(0.5 * tau))) return rc;
+    }
+    s->set_cycles_step(total);
+    if (cycles) *cycles = total;
+    if (rho) *rho = r;
+    if ((rc = s->end_step(nullptr))) return rc;
+    return ok ? MG_OK : fail(MG_ERR_TIMEOUT, "no attempt at the step reached the tolerance");
 }
 
 int check_markers(const double *mk, int k, int n, int m) {
@@ -1115,7 +1204,7 @@ namespace {
 // ---------------------------------------------------------------------------------------
 __global__ void k_batch_cond(cudaGraphConditionalHandle h, const Scalars *sc, double tol2) {
     const double n2 = sc->norm2, n0 = sc->norm2_0;
-    cudaGraphSetConditional(h, n2 > tol2 * n0 ? 1u : 0u);
+    cudaGraphSetConditional(h, (n2 > tol2 * n0 && sc->halt == 0) ? 1u : 0u);
 }
 
 __global__ void k_batch_gather(Scalars *const *sc, int count, double *out) {
@@ -1206,6 +1295,10 @@ struct Batch {
         return rc;
     }
 
+    // One pseudo-time step of every image.  Each graph launch runs one V-cycle of every image
+    // that has not reached tol.  The step control of mg_solve_step applies per image: an image
+    // whose attempt stalls, diverges or reaches max_cycles V-cycles is restarted from its phi^n
+    // with tau / 2 (its graph branch is captured again).
     int solve_step(double tol, int max_cycles, int *cycles, double *rho) {
         const int count = (int)s.size();
         for (int i = 0; i < count; ++i) {
@@ -1216,30 +1309,62 @@ struct Batch {
             int rc = build(tol);
             if (rc) return rc;
         }
-        std::vector<int> cyc(count, 0);
+        std::vector<int> cyc(count, 0), halvings(count, 0);
         std::vector<double> r(count, 1.0);
-        std::vector<char> active(count, 1);
-        int c = 0, rc = MG_OK;
-        for (; c < max_cycles; ++c) {
+        std::vector<std::vector<double>> hist(count);
+        std::vector<char> active(count, 1), failed(count, 0);
+        int rc = MG_OK;
+        for (int launch = 0; rc == MG_OK; ++launch) {
             CK(cudaGraphLaunch(exec, st));
             CK(cudaStreamSynchronize(st));
-            bool any = false;
+            bool any = false, rebuild = false;
             for (int i = 0; i < count; ++i) {
+                if (!active[i]) continue;
                 const double n2 = h_out[3 * i], n0 = h_out[3 * i + 1];
-                if (active[i]) {
-                    ++cyc[i];
-                    s[i]->cycles_step = cyc[i];
-                    ++s[i]->cycles_total;
-                    s[i]->launches += nodes[i] + 1;
-                }
+                ++cyc[i];
+                s[i]->cycles_step = cyc[i];
+                ++s[i]->cycles_total;
+                s[i]->launches += nodes[i] + 1;
                 r[i] = n0 > 0 ? std::sqrt(n2) / std::sqrt(n0) : std::sqrt(n2);   // as mg_vcycle
                 s[i]->rho = r[i];
-                if (h_out[3 * i + 2] != 0.0 && rc == MG_OK) rc = fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
-                if (!std::isfinite(r[i]) && rc == MG_OK) rc = fail(MG_ERR_NAN, "non-finite residual");
-                active[i] = r[i] > tol;
+                const int err = (int)h_out[3 * i + 2];
+                if ((err & 1) && rc == MG_OK) rc = fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
+                if ((err & 4) && rc == MG_OK) {
+                    CK(cudaMemsetAsync(&s[i]->dsc->err, 0, sizeof(int), st));
+                    rc = fail(MG_ERR_TIMEOUT, "a tile copy into shared memory did not complete within the wait limit");
+                }
+                hist[i].push_back(r[i]);
+                if (r[i] <= tol) { active[i] = 0; continue; }
+                const mg_params &pi = s[i]->p;
+                const bool control = pi.stall_ratio > 0;
+                const bool bad = !std::isfinite(r[i]) || r[i] > 1e3;
+                const bool stop = bad || (int)hist[i].size() >= max_cycles || attempt_stalled(hist[i], pi.stall_ratio);
+                if (!control) {
+                    if (!std::isfinite(r[i]) && rc == MG_OK) rc = fail(MG_ERR_NAN, "non-finite residual");
+                    if ((int)hist[i].size() >= max_cycles) {
+                        active[i] = 0;
+                        failed[i] = 1;
+                        CK(cudaMemsetAsync(&s[i]->dsc->halt, 1, sizeof(int), st));
+                        continue;
+                    }
+                } else if (stop) {
+                    if (halvings[i] >= pi.max_halvings) {
+                        active[i] = 0;
+                        failed[i] = 1;
+                        if (bad && rc == MG_OK && !(rc = s[i]->restart_step(pi.tau))) rc = s[i]->begin_step(nullptr);
+                        CK(cudaMemsetAsync(&s[i]->dsc->halt, 1, sizeof(int), st));
+                        continue;
+                    }
+                    ++halvings[i];
+                    hist[i].clear();
+                    if (rc == MG_OK) rc = s[i]->restart_step(0.5 * pi.tau);
+                    if (rc == MG_OK) rc = s[i]->begin_step(nullptr);
+                    rebuild = true;
+                }
                 any = any || active[i];
             }
             if (rc || !any) break;
+            if (rebuild && (rc = build(tol))) break;
         }
         if (cycles) for (int i = 0; i < count; ++i) cycles[i] = cyc[i];
         if (rho) for (int i = 0; i < count; ++i) rho[i] = r[i];
@@ -1249,7 +1374,7 @@ struct Batch {
             if (e) return e;
         }
         for (int i = 0; i < count; ++i)
-            if (r[i] > tol) return fail(MG_ERR_TIMEOUT, "cycle cap reached before the tolerance");
+            if (failed[i]) return fail(MG_ERR_TIMEOUT, "an image reached no tolerance within its attempts");
         return MG_OK;
     }
 };
@@ -1277,6 +1402,7 @@ int mg_default_params(mg_params *p, int n, int m) {
     p->precision = MG_F32; p->smoother = MG_SMOOTH_FUSED;
     p->coarse_maxit = 100; p->coarse_tol = 1e-13; p->use_graph = 1;
     p->coarse_solver = MG_COARSE_PICARD; p->aos_dt = 10.0;
+    p->stall_ratio = 0.6; p->max_halvings = 10;
     return MG_OK;
 }
 
@@ -1329,21 +1455,7 @@ int mg_end_step(mg_handle h, double *eta) { return h ? h->s->end_step(eta) : fai
 
 int mg_solve_step(mg_handle h, double tol, int max_cycles, int *cycles, double *rho) {
     if (!h || max_cycles < 1) return fail(MG_ERR_ARG, "NULL handle or max_cycles < 1");
-    int rc = h->s->begin_step(nullptr);
-    if (rc) return rc;
-    double r = 1.0;
-    int c = 0;
-    while (c < max_cycles) {
-        rc = h->s->vcycle(&r);
-        ++c;
-        if (rc) return rc;
-        if (r <= tol) break;
-    }
-    if (cycles) *cycles = c;
-    if (rho) *rho = r;
-    rc = h->s->end_step(nullptr);
-    if (rc) return rc;
-    return r <= tol ? MG_OK : fail(MG_ERR_TIMEOUT, "cycle cap reached before the tolerance");
+    return solve_step_controlled(h->s, tol, max_cycles, cycles, rho);
 }
 
 int mg_solve(mg_handle h, double tol, int max_cycles, double eta_stop, int max_steps, int *steps) {
@@ -1375,6 +1487,9 @@ int mg_get_level(mg_handle h, int level, int field, void *out) {
     return (h && out) ? h->s->get_level(level, field, out) : fail(MG_ERR_ARG, "NULL argument");
 }
 int mg_get_stats(mg_handle h, mg_stats *s) { return (h && s) ? h->s->stats(s) : fail(MG_ERR_ARG, "NULL argument"); }
+int mg_set_wait_limit(mg_handle h, long long rounds) {
+    return h ? h->s->set_wait_limit(rounds) : fail(MG_ERR_ARG, "NULL handle");
+}
 
 int mg_segment_host(const float *image_host, int n, int m, const double *markers_xy, int k,
                     const mg_params *p, double tol, int max_cycles, double eta_stop, int max_steps,

@@ -59,6 +59,8 @@ struct Scalars {
     double aos[2];           // AOS on the finest grid: sum (u_new - u)^2, sum (pn + u)^2
     int picard;              // Picard iterations of the last coarsest solve
     int err;                 // 1 = non-positive Cholesky pivot
+    int halt;                // nonzero: a batch skips this image's V-cycles (set by the host when
+                             // the image gives up a step; cleared by every step's start)
 };
 
 struct ModelParams {
@@ -141,8 +143,9 @@ struct SweepMaps {
 };
 void prepare_sweep_tma();
 bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M);
+constexpr long long kDefaultWaitLimit = 1LL << 22;   // try_wait rounds before a TMA wait gives up
 void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const SweepMaps &M, int *err,
-                      cudaStream_t st);
+                      long long wait_limit, cudaStream_t st);
 
 // learned.cu: learned relaxation weights (inference and training)
 int learned_nparam();

@@ -133,6 +133,8 @@ extern "C" int mg_residual_norm_noalloc(const void *phi, const void *w, const vo
     long tiles = (long)((m + 31) / 32) * ((n + 31) / 32);
     if (tiles > kNoAllocMaxTiles)
         return err(MG_ERR_ARG, "grid exceeds the static scratch (at most 65536 tiles of 32 x 32 cells)");
+    if ((n + 31) / 32 > 65535)   // the tile rows are the launch's grid.y
+        return err(MG_ERR_ARG, "more than 65535 rows of 32 x 32 tiles");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return err(MG_ERR_CUDA, "no current CUDA device");
@@ -151,6 +153,7 @@ extern "C" int mg_residual_norm_noalloc(const void *phi, const void *w, const vo
         scratch = g_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)stream;
+    (void)cudaGetLastError();   // a pending error of earlier, unrelated work is not this call's
     int rc = p->precision == MG_F32 ? run<float>(phi, w, F, n, m, p, scratch, st)
                                     : run<double>(phi, w, F, n, m, p, scratch, st);
     if (rc) return rc;

@@ -13,8 +13,10 @@
 // 32 cells a warp updates fall in 32 different banks without the colour-split layout the
 // vector-load kernel uses.
 //
-// Every wait on an mbarrier is bounded.  On time-out the block records bit 4 in the handle's
-// error word, waits (bounded) for its copies still in flight and returns; the host reports it.
+// Every wait on an mbarrier is bounded (wait_limit try_wait rounds, a launch argument: the
+// handle's mg_set_wait_limit, default kDefaultWaitLimit).  On time-out the block records bit 4 in
+// the handle's error word, waits (bounded by kDrainLimit) for its copies still in flight and
+// returns; the host reports it.
 #include <cuda.h>
 
 #include <algorithm>
@@ -27,7 +29,7 @@ namespace segmg {
 namespace {
 
 constexpr int kH = 4;
-constexpr long kWaitLimit = 1L << 22;   // try_wait rounds before a wait gives up
+constexpr long long kDrainLimit = 1LL << 22;   // try_wait rounds of the last wait for copies in flight
 
 template <int OH_, int OW_, int NT_, int MINB_ = 1>
 struct TShape {
@@ -65,10 +67,11 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
                  : "memory");
 }
 
-// Bounded wait for the completion of phase `parity`; false on time-out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// Bounded wait for the completion of phase `parity` (at most `limit` try_wait rounds); false on
+// time-out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
     const unsigned a = smem_u32(bar);
-    for (long it = 0; it < kWaitLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         unsigned done;
         asm volatile(
             "{\n.reg .pred p;\n"
@@ -143,7 +146,8 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
 template <int SWEEP, typename TS, int STAGES>
 __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<float> L, const __grid_constant__ CUtensorMap tin,
                                                       const __grid_constant__ CUtensorMap tG,
-                                                      const __grid_constant__ CUtensorMap tf, int *err) {
+                                                      const __grid_constant__ CUtensorMap tf, int *err,
+                                                      long long wait_limit) {
     constexpr int kOH = TS::OH, kOW = TS::OW, kRH = TS::RH, kRW = TS::RW;
     constexpr int kRowPieces = TS::RowPieces, kColPieces = TS::ColPieces;
     constexpr bool rowwise = SWEEP < 2, rev = (SWEEP & 1) != 0;
@@ -200,13 +204,15 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
                 lm |= solves_word<kH, kOH, kOW, false>(b, pc, w);
             }
         }
-        const bool ok = mbar_wait(&S.bar[st], parity);
+        const bool ok = mbar_wait(&S.bar[st], parity, wait_limit);
         if (__syncthreads_or(!ok)) {
-            // a copy never completed: report, give the copies in flight a last bounded wait, stop
+            // a copy did not complete within wait_limit rounds: report, give the copies in flight a
+            // last bounded wait (kDrainLimit rounds, so that none still writes into shared memory
+            // once the block has ended), stop
             if (tid == 0) {
                 atomicOr(err, 4);
-                mbar_wait(&S.bar[st], parity);
-                if (STAGES == 2 && next < ntiles) mbar_wait(&S.bar[st ^ 1], (unsigned)(((k + 1) >> 1) & 1));
+                mbar_wait(&S.bar[st], parity, kDrainLimit);
+                if (STAGES == 2 && next < ntiles) mbar_wait(&S.bar[st ^ 1], (unsigned)(((k + 1) >> 1) & 1), kDrainLimit);
             }
             __syncthreads();
             return;
@@ -277,26 +283,27 @@ void set_attrs() {
 // One tile per block when every tile gets a resident block with one stage; else persistent
 // double-buffered blocks, as many as fit.
 template <int SW, typename TS>
-void launch_one(const LevelView<float> &L, const SweepMaps &M, int sms, int *err, cudaStream_t st) {
+void launch_one(const LevelView<float> &L, const SweepMaps &M, int sms, int *err, long long wl, cudaStream_t st) {
     const int ntiles = ((L.m + TS::OW - 1) / TS::OW) * ((L.n + TS::OH - 1) / TS::OH);
     const CUtensorMap *in = reinterpret_cast<const CUtensorMap *>((SW & 1) ? M.t : M.u);
     const CUtensorMap &mG = *reinterpret_cast<const CUtensorMap *>(M.G);
     const CUtensorMap &mf = *reinterpret_cast<const CUtensorMap *>(M.f);
     if (ntiles <= sms * tma_blocks_per_sm<SW, TS, 1>()) {
-        k_sweep_tma<SW, TS, 1><<<ntiles, TS::NT, tma_smem<SW, TS, 1>(), st>>>(L, *in, mG, mf, err);
+        k_sweep_tma<SW, TS, 1><<<ntiles, TS::NT, tma_smem<SW, TS, 1>(), st>>>(L, *in, mG, mf, err, wl);
     } else {
         const int grid = std::min(ntiles, sms * tma_blocks_per_sm<SW, TS, 2>());
-        k_sweep_tma<SW, TS, 2><<<grid, TS::NT, tma_smem<SW, TS, 2>(), st>>>(L, *in, mG, mf, err);
+        k_sweep_tma<SW, TS, 2><<<grid, TS::NT, tma_smem<SW, TS, 2>(), st>>>(L, *in, mG, mf, err, wl);
     }
 }
 
 template <typename TS>
-void launch_shape(const LevelView<float> &L, int sweep, const SweepMaps &M, int sms, int *err, cudaStream_t st) {
+void launch_shape(const LevelView<float> &L, int sweep, const SweepMaps &M, int sms, int *err, long long wl,
+                  cudaStream_t st) {
     switch (sweep) {
-        case 0: launch_one<0, TS>(L, M, sms, err, st); break;
-        case 1: launch_one<1, TS>(L, M, sms, err, st); break;
-        case 2: launch_one<2, TS>(L, M, sms, err, st); break;
-        default: launch_one<3, TS>(L, M, sms, err, st); break;
+        case 0: launch_one<0, TS>(L, M, sms, err, wl, st); break;
+        case 1: launch_one<1, TS>(L, M, sms, err, wl, st); break;
+        case 2: launch_one<2, TS>(L, M, sms, err, wl, st); break;
+        default: launch_one<3, TS>(L, M, sms, err, wl, st); break;
     }
 }
 
@@ -358,13 +365,15 @@ bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M) {
     return encode_shape<TT0>(L, *M);
 }
 
-void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const SweepMaps &M, int *err, cudaStream_t st) {
-    if (shape == 1) launch_shape<TT1>(L, sweep, M, g_sms, err, st);
-    else if (shape == 2) launch_shape<TT2>(L, sweep, M, g_sms, err, st);
-    else if (shape == 3) launch_shape<TT3>(L, sweep, M, g_sms, err, st);
-    else if (shape == 4) launch_shape<TT4>(L, sweep, M, g_sms, err, st);
-    else if (shape == 5) launch_shape<TT5>(L, sweep, M, g_sms, err, st);
-    else launch_shape<TT0>(L, sweep, M, g_sms, err, st);
+void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const SweepMaps &M, int *err,
+                      long long wait_limit, cudaStream_t st) {
+    const long long wl = wait_limit;
+    if (shape == 1) launch_shape<TT1>(L, sweep, M, g_sms, err, wl, st);
+    else if (shape == 2) launch_shape<TT2>(L, sweep, M, g_sms, err, wl, st);
+    else if (shape == 3) launch_shape<TT3>(L, sweep, M, g_sms, err, wl, st);
+    else if (shape == 4) launch_shape<TT4>(L, sweep, M, g_sms, err, wl, st);
+    else if (shape == 5) launch_shape<TT5>(L, sweep, M, g_sms, err, wl, st);
+    else launch_shape<TT0>(L, sweep, M, g_sms, err, wl, st);
 }
 
 }  // namespace segmg

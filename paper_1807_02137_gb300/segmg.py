@@ -22,7 +22,7 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
           -5: "MG_ERR_TIMEOUT", -6: "MG_ERR_NOT_SPD", -7: "MG_ERR_NOMEM", -8: "MG_ERR_STATE"}
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
-           "mg_get_level", "mg_get_stats", "mg_segment_host", "mg_get_stream", "mg_destroy",
+           "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_segment_host", "mg_get_stream", "mg_destroy",
            "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_set_cluster_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
            "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_grad",
            "mg_trainer_train", "mg_trainer_get", "mg_trainer_destroy",
@@ -40,7 +40,8 @@ class Params(C.Structure):
         ("Sigma", C.c_double), ("tau", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
         ("levels", C.c_int), ("precision", C.c_int), ("smoother", C.c_int),
         ("coarse_maxit", C.c_int), ("coarse_tol", C.c_double), ("use_graph", C.c_int),
-        ("coarse_solver", C.c_int), ("aos_dt", C.c_double),
+        ("coarse_solver", C.c_int), ("aos_dt", C.c_double), ("stall_ratio", C.c_double),
+        ("max_halvings", C.c_int),
     ]
 
 
@@ -53,7 +54,8 @@ class Stats(C.Structure):
         ("picard_last", C.c_int), ("rho", C.c_double), ("res0", C.c_double), ("eta", C.c_double),
         ("c1", C.c_double), ("c2", C.c_double), ("A1", C.c_double), ("device_bytes", C.c_size_t),
         ("launches", C.c_longlong), ("learned_accepted", C.c_longlong), ("learned_rejected", C.c_longlong),
-        ("bottom_level", C.c_int), ("cluster_level", C.c_int),
+        ("bottom_level", C.c_int), ("cluster_level", C.c_int), ("tau", C.c_double),
+        ("attempts_rejected", C.c_int),
     ]
 
     def as_dict(self):
@@ -94,6 +96,7 @@ def lib():
             "mg_set_regions": ([vp, d, d], i),
             "mg_get_level": ([vp, i, i, vp], i),
             "mg_get_stats": ([vp, C.POINTER(Stats)], i),
+            "mg_set_wait_limit": ([vp, C.c_longlong], i),
             "mg_segment_host": ([vp, i, i, D, i, P, d, i, d, i, vp, vp, C.POINTER(Stats)], i),
             "mg_get_stream": ([vp], vp),
             "mg_time_kernels": ([vp, i, i, D], i),
@@ -337,6 +340,10 @@ class Solver:
         _check(lib().mg_time_kernels(self._h, level, reps, out), "mg_time_kernels")
         return list(out)
 
+    def set_wait_limit(self, rounds):
+        """Bound of the fused sweep's device-side waits (mg_set_wait_limit); 0 gives up at once."""
+        _check(lib().mg_set_wait_limit(self._h, int(rounds)), "mg_set_wait_limit")
+
     def stats(self) -> dict:
         s = Stats()
         _check(lib().mg_get_stats(self._handle, C.byref(s)), "mg_get_stats")
@@ -397,7 +404,24 @@ class Batch:
 
 def residual_norm_noalloc(phi, w, F, params: Params) -> float:
     """mg_residual_norm_noalloc on dense CUDA tensors of the params' precision (no allocation
-    inside the library)."""
+    inside the library).  The three tensors must be 2-D of one shape, of the dtype the precision
+    implies (float64 for MG_F64, else float32), contiguous and on a CUDA device: anything else is
+    refused here, before the library reads any of them."""
+    import torch
+    want = torch.float64 if params.precision == MG_F64 else torch.float32
+    ts = {"phi": phi, "w": w, "F": F}
+    for name, t in ts.items():
+        if not isinstance(t, torch.Tensor) or t.dim() != 2 or tuple(t.shape) != tuple(phi.shape):
+            raise TypeError(f"{name} must be a 2-D tensor of phi's shape {tuple(phi.shape)}")
+    for name, t in ts.items():
+        if t.dtype != want:
+            raise TypeError(f"{name} is {t.dtype}; the params' precision needs {want}")
+    for name, t in ts.items():
+        if not t.is_contiguous():
+            raise TypeError(f"{name} must be contiguous (dense row-major)")
+    for name, t in ts.items():
+        if not t.is_cuda:
+            raise TypeError(f"{name} must be on a CUDA device")
     n, m = phi.shape
     out = C.c_double()
     rc = lib().mg_residual_norm_noalloc(C.c_void_p(phi.data_ptr()), C.c_void_p(w.data_ptr()),

@@ -59,3 +59,21 @@ def test_host_only_calls_without_a_gpu(libpath):
     assert segmg.lib().mg_strerror(-6) == b"coarsest system not positive definite"
     # a NULL handle is rejected before any CUDA call
     assert segmg.lib().mg_vcycle(None, None) == -1
+
+
+def test_noalloc_binding_refuses_mismatched_tensors_before_any_call(libpath):
+    # float32 tensors with FP64 params would make the kernel read twice the buffers' bytes: the
+    # binding refuses them (and non-CUDA, strided or mis-shaped tensors) before the library runs
+    import torch
+    from paper_1807_02137_gb300 import segmg
+    p = segmg.default_params(8, 8, precision=segmg.MG_F64)
+    f32 = torch.zeros(8, 8, dtype=torch.float32)
+    with pytest.raises(TypeError, match="precision"):
+        segmg.residual_norm_noalloc(f32, f32, f32, p)
+    f64 = torch.zeros(8, 8, dtype=torch.float64)
+    with pytest.raises(TypeError, match="shape"):
+        segmg.residual_norm_noalloc(f64, f64, torch.zeros(8, 9, dtype=torch.float64), p)
+    with pytest.raises(TypeError, match="contiguous"):
+        segmg.residual_norm_noalloc(f64, f64, torch.zeros(8, 16, dtype=torch.float64)[:, ::2], p)
+    with pytest.raises(TypeError, match="CUDA"):
+        segmg.residual_norm_noalloc(f64, f64, f64, p)

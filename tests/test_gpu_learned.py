@@ -130,6 +130,7 @@ def test_learned_mode_keeps_the_solution(segmg):
     assert rho <= 1e-6
     assert 1 <= st["learned_accepted"] + st["learned_rejected"] <= cyc - 1
     o = O.Solver(img.astype(np.float32).astype(np.float64), mk, oracle_params(256, 256, p))
+    o.set_tau(st["tau"])
     hist = o.solve_step(1e-9, 80)
     assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-5
     # recording crops from the solver's state

@@ -130,3 +130,50 @@ def test_paper_orderings_converge_too():
         sols.append(s.phi)
     for x in sols[1:]:
         assert np.allclose(sols[0], x, atol=1e-8)
+
+
+def _ellipse_solver(n, seed, tau=1.0):
+    img, mk, _ = synth.ellipses(n, n, 12, (20 * n / 256, 200 * n / 256), 8, 0.05, seed, dtype=np.float64)
+    lev = 1
+    s = n
+    while s // 2 >= 4:
+        s //= 2
+        lev += 1
+    return O.Solver(img, mk, O.params(n, n, levels=lev, tau=tau)), img, mk, lev
+
+
+def test_step_control_rejects_a_stalled_attempt_and_restarts_from_phi_n():
+    # 64^2 ellipses, seed 1: the first step's attempt with tau = 1 stalls (two V-cycles gain less
+    # than a factor 1 / 0.6); the step is retried from phi^n with tau = 1/2 and converges
+    o, img, mk, lev = _ellipse_solver(64, 1)
+    phin = o.phi
+    tau, att = o.solve_step_controlled(1.0, 1e-6, stall_ratio=0.6)
+    assert len(att) >= 2 and tau == 0.5 ** (len(att) - 1)
+    for k, (t, h) in enumerate(att[:-1]):
+        assert t == 0.5 ** k
+        stalled = len(h) >= 4 and h[-1] > 0.6 * h[-3]
+        assert stalled or len(h) == 40 or not np.isfinite(h[-1]) or h[-1] > 1e3
+        assert h[-1] > 1e-6
+    assert att[-1][1][-1] <= 1e-6
+    got = o.phi
+    # the accepted attempt started from phi^n: the same step solved directly with the accepted
+    # tau gives the same phi, bitwise
+    o2, *_ = _ellipse_solver(64, 1, tau=tau)
+    assert np.array_equal(o2.phi, phin)
+    h2 = o2.solve_step(1e-6, 40)
+    assert h2 == att[-1][1]
+    assert np.array_equal(o2.phi, got)
+
+
+@pytest.mark.parametrize("n,seed", [(48, 2), (64, 3)])
+def test_every_controlled_step_reaches_the_tolerance(n, seed):
+    # with tau fixed at 1, the later steps of these images stall (rho ~ 1e-3); under the step
+    # control every step reaches rho <= 1e-6 and tau never grows
+    o, *_ = _ellipse_solver(n, seed)
+    tau, taus = 1.0, []
+    for _ in range(3):
+        tau, att = o.solve_step_controlled(tau, 1e-6)
+        o.end_step()
+        assert att[-1][1][-1] <= 1e-6
+        taus.append(tau)
+    assert all(b <= a for a, b in zip(taus, taus[1:]))
