@@ -219,6 +219,13 @@ int mg_get_stats(mg_handle h, mg_stats *s);
  * counterpart.  Errors: MG_ERR_ARG (rounds < 0). */
 int mg_set_wait_limit(mg_handle h, long long rounds);
 
+/* Host-side fault injection for tests of the error paths (no counterpart in the paper): the
+ * `cycle`-th V-cycle (1-based, counted from the start of the current or next step attempt) run
+ * after this call reports a residual ratio of 1e9, as a diverged V-cycle would; mg_vcycle then
+ * returns MG_ERR_DIVERGED and the step control of mg_solve_step rejects the attempt.  It fires
+ * once; 0 cancels it.  The device state is left as the V-cycle computed it.  Errors: MG_ERR_ARG. */
+int mg_inject_divergence(mg_handle h, int cycle);
+
 /* Whole pipeline through host buffers: copies the float image to the device, runs mg_setup,
  * then mg_solve(tol, max_cycles, eta_stop, max_steps) with the given parameters (precision
  * forced to MG_F32), and copies the mask (and phi if phi_host is not NULL) back.  All host

@@ -120,6 +120,7 @@ struct SolverBase {
     virtual int restart_step(double tau) = 0;
     virtual void set_cycles_step(int c) = 0;
     virtual int set_wait_limit(long long rounds) = 0;
+    virtual int inject_divergence(int cycle) = 0;
 };
 
 template <typename T>
@@ -157,6 +158,8 @@ struct Solver final : SolverBase {
     int steps = 0, cycles_step = 0, cycles_total = 0;
     int rejected = 0;             // step attempts rejected by the step control
     long long wait_limit = kDefaultWaitLimit;   // try_wait rounds of the TMA sweep's bounded waits
+    int inject_cycle = 0;         // mg_inject_divergence: V-cycle (of a step attempt) that reports
+                                  // a diverged residual once; 0 = none
     bool in_step = false;
     cudaGraphExec_t gexec = nullptr;
     long long launches = 0, graph_nodes = 0;
@@ -866,6 +869,10 @@ struct Solver final : SolverBase {
         ++cycles_step;
         ++cycles_total;
         rho = current_rho();
+        if (inject_cycle > 0 && cycles_step == inject_cycle) {   // host-side fault injection
+            inject_cycle = 0;
+            rho = 1e9;
+        }
         if (rhoout) *rhoout = rho;
         if (hsc->err & 1) return fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
         if (hsc->err & 4) {   // reported once: the word is cleared so the handle stays usable
@@ -960,6 +967,12 @@ struct Solver final : SolverBase {
     }
 
     const mg_params &params() const override { return p; }
+
+    int inject_divergence(int cycle) override {
+        if (cycle < 0) return fail(MG_ERR_ARG, "cycle < 0");
+        inject_cycle = cycle;
+        return MG_OK;
+    }
 
     int set_wait_limit(long long rounds) override {
         if (rounds < 0) return fail(MG_ERR_ARG, "wait limit < 0");
@@ -1487,6 +1500,9 @@ int mg_get_level(mg_handle h, int level, int field, void *out) {
     return (h && out) ? h->s->get_level(level, field, out) : fail(MG_ERR_ARG, "NULL argument");
 }
 int mg_get_stats(mg_handle h, mg_stats *s) { return (h && s) ? h->s->stats(s) : fail(MG_ERR_ARG, "NULL argument"); }
+int mg_inject_divergence(mg_handle h, int cycle) {
+    return h ? h->s->inject_divergence(cycle) : fail(MG_ERR_ARG, "NULL handle");
+}
 int mg_set_wait_limit(mg_handle h, long long rounds) {
     return h ? h->s->set_wait_limit(rounds) : fail(MG_ERR_ARG, "NULL handle");
 }

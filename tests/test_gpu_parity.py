@@ -594,31 +594,31 @@ def test_batch_members_match_the_oracle(segmg):
     b.close()
 
 
-def test_divergence_is_reported_and_the_step_control_restores_phi_n(segmg):
-    # tau = inf (the paper's stationary equation) has no bounded solution on this image: the
-    # residual grows by ~1e19 within three V-cycles.  Without the step control mg_vcycle reports
-    # MG_ERR_DIVERGED; with it, the step gives up (tau cannot be halved) and phi is phi^n again.
-    W = synth.workload("disc128")
-    s, p = gpu_solver(segmg, W.image, W.markers, precision=segmg.MG_F64, levels=W.levels, tau=0.0,
-                      stall_ratio=0.0)
-    phi0 = s.phi().cpu().numpy()
+def test_divergence_is_reported_and_the_step_control_restarts_from_phi_n(segmg):
+    # a diverged V-cycle, injected on the host (the third V-cycle of the step reports a residual
+    # ratio of 1e9): without the step control mg_vcycle returns MG_ERR_DIVERGED; with it the
+    # attempt is rejected, phi^n restored and the step solved with tau / 2, which gives bitwise
+    # the solution of that step solved directly with tau / 2
+    img, mk, _ = synth.ellipses(192, 192, 8, (10, 80), 6, 0.05, 19)
+    img = img.astype(np.float32)
+    s, p = gpu_solver(segmg, img, mk, stall_ratio=0.0)
     s.begin_step()
-    codes = []
-    for _ in range(8):
-        try:
-            s.vcycle()
-        except segmg.SegmgError as e:
-            codes.append(e.code)
-            break
-    assert codes == [-4]
-    s.close()
-    s, p = gpu_solver(segmg, W.image, W.markers, precision=segmg.MG_F64, levels=W.levels, tau=0.0)
+    s.inject_divergence(3)
+    s.vcycle(); s.vcycle()
     with pytest.raises(segmg.SegmgError) as e:
-        s.solve_step(1e-8, 20, raise_on_cap=True)
-    assert e.value.code == -5
-    assert np.array_equal(s.phi().cpu().numpy(), phi0)
-    assert s.stats()["attempts_rejected"] >= 1
+        s.vcycle()
+    assert e.value.code == -4
     s.close()
+    s, p = gpu_solver(segmg, img, mk)
+    s.inject_divergence(3)
+    c, rho = s.solve_step(1e-6, 40)
+    st = s.stats()
+    assert rho <= 1e-6 and st["attempts_rejected"] == 1 and st["tau"] == 0.5 * p.tau
+    ref, _ = gpu_solver(segmg, img, mk, tau=0.5 * p.tau)
+    c2, rho2 = ref.solve_step(1e-6, 40)
+    assert c == c2 + 3 and rho == rho2
+    assert np.array_equal(s.phi().cpu().numpy(), ref.phi().cpu().numpy())
+    s.close(); ref.close()
 
 
 def test_sweep_wait_limit_time_out_is_reported_and_the_handle_recovers(segmg):
