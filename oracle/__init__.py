@@ -5,7 +5,10 @@ FAS V-cycle and outer driver (``oracle.c``), plus the Local Fourier Analysis too
 (``lfa.py``).  It is the independent checker of the CUDA library: it shares no code with it,
 and only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg may use it.
 
-``build()`` compiles ``oracle.c`` with gcc into ``oracle/_build/liboracle.so``.
+``build()`` compiles ``oracle.c`` with gcc into ``oracle/_build/liboracle.so`` (the checker, one
+core).  ``build(openmp=True)`` compiles the same file with ``-fopenmp`` into ``liboracle_omp.so``:
+its loops marked independent run on all host cores with bitwise the same results.  It is used only
+to time the oracle on all cores (``Solver(..., openmp=True)``).
 """
 from __future__ import annotations
 
@@ -19,18 +22,23 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 _lock = threading.Lock()
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (plain C, -O2, no fast-math)."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-    return _OUT
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle shared library (plain C, -O2, no fast-math; -fopenmp for the all-core
+    timing build)."""
+    out = _OUT_OMP if openmp else _OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
+        flags = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *flags, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class Params(C.Structure):
@@ -62,11 +70,11 @@ def params(n=None, m=None, **kw) -> Params:
     return Params(**d)
 
 
-def lib():
-    global _lib
+def lib(openmp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if (_lib_omp if openmp else _lib) is None:
+            L = C.CDLL(build(openmp=openmp))
             D = C.POINTER(C.c_double)
             I = C.POINTER(C.c_int)
             P = C.POINTER(Params)
@@ -108,8 +116,11 @@ def lib():
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = res
-            _lib = L
-    return _lib
+            if openmp:
+                _lib_omp = L
+            else:
+                _lib = L
+    return _lib_omp if openmp else _lib
 
 
 def _d(a):
@@ -290,18 +301,19 @@ def coarse_solve(phi, w, Fn, rhs, h=1.0, p=None, n0m0=None, A1=0.0):
 class Solver:
     """The oracle's FAS solver over one image (create / begin_step / vcycle / end_step)."""
 
-    def __init__(self, image, markers, p: Params):
+    def __init__(self, image, markers, p: Params, openmp: bool = False):
         img, pi = _d(image)
         mk = np.asarray(markers, dtype=np.float64).reshape(-1, 2)
         self._mx, px = _d(mk[:, 0].copy())
         self._my, py = _d(mk[:, 1].copy())
         self.n, self.m = img.shape
         self.p = p
-        self._h = lib().or_create(pi, self.n, self.m, px, py, len(mk), C.byref(p))
+        self._L = lib(openmp)
+        self._h = self._L.or_create(pi, self.n, self.m, px, py, len(mk), C.byref(p))
 
     def close(self):
         if self._h:
-            lib().or_destroy(self._h)
+            self._L.or_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -311,25 +323,25 @@ class Solver:
             pass
 
     def begin_step(self) -> float:
-        return lib().or_begin_step(self._h)
+        return self._L.or_begin_step(self._h)
 
     def vcycle(self) -> float:
-        return lib().or_vcycle(self._h)
+        return self._L.or_vcycle(self._h)
 
     def end_step(self) -> float:
-        return lib().or_end_step(self._h)
+        return self._L.or_end_step(self._h)
 
     @property
     def phi(self):
         out = np.empty((self.n, self.m))
-        lib().or_get_phi(self._h, _d(out)[1])
+        self._L.or_get_phi(self._h, _d(out)[1])
         return out
 
     @phi.setter
     def phi(self, v):
         v, p = _d(v)
         assert v.shape == (self.n, self.m)
-        lib().or_set_phi(self._h, p)
+        self._L.or_set_phi(self._h, p)
 
     def level(self, l, which):
         names = ["phi", "w", "z", "d", "Fn", "rhs", "tmp"]
@@ -338,35 +350,35 @@ class Solver:
         for _ in range(l):
             n, m = n // 2, m // 2
         out = np.empty((n, m))
-        lib().or_get_level(self._h, l, idx, _d(out)[1])
+        self._L.or_get_level(self._h, l, idx, _d(out)[1])
         return out
 
     def scalars(self):
         out = np.zeros(5)
-        lib().or_get_scalars(self._h, _d(out)[1])
+        self._L.or_get_scalars(self._h, _d(out)[1])
         return dict(c1=out[0], c2=out[1], A1=out[2], res0=out[3], picard=int(out[4]))
 
     def set_c(self, c1, c2):
-        lib().or_set_c(self._h, c1, c2)
+        self._L.or_set_c(self._h, c1, c2)
 
     def aos(self, dt, max_iter, eta):
         """AOS iterations on the finest grid until the relative change < eta (or_solver_aos).
         Returns (iterations, rho)."""
         r = np.zeros(1)
-        it = lib().or_solver_aos(self._h, dt, max_iter, eta, _d(r)[1])
+        it = self._L.or_solver_aos(self._h, dt, max_iter, eta, _d(r)[1])
         return it, float(r[0])
 
     def set_omega(self, l, omega):
         """Relaxation weights of the point updates on grid l (None: plain smoother)."""
         if omega is None:
-            lib().or_set_omega(self._h, l, None)
+            self._L.or_set_omega(self._h, l, None)
         else:
             w, pw = _d(omega)
-            lib().or_set_omega(self._h, l, pw)
+            self._L.or_set_omega(self._h, l, pw)
 
     def energy(self) -> float:
         """Energy of the current finest-grid phi with the current c1, c2 (or_solver_energy)."""
-        return float(lib().or_solver_energy(self._h))
+        return float(self._L.or_solver_energy(self._h))
 
     def solve_step(self, tol, max_cycles=50):
         """One pseudo-time step: V-cycles until rho <= tol.  Returns list of rho."""
@@ -381,7 +393,7 @@ class Solver:
 
     def set_tau(self, tau):
         """tau of the following pseudo-time steps (None or inf: the stationary equation)."""
-        lib().or_set_inv_tau(self._h, 0.0 if tau is None or tau == float("inf") else 1.0 / tau)
+        self._L.or_set_inv_tau(self._h, 0.0 if tau is None or tau == float("inf") else 1.0 / tau)
 
     def solve_step_controlled(self, tau, tol, max_cycles=40, stall_ratio=0.6, max_halvings=10):
         """One pseudo-time step under the step-size control of the outer driver.

@@ -19,6 +19,11 @@
  *
  * Parity status of each function is recorded next to it ("pinned by" lists the independent
  * checks in tests/test_oracle_*.py).
+ *
+ * The "#pragma omp parallel for" lines mark loops whose iterations are independent (each writes
+ * its own cells and reads nothing another iteration writes).  The checker is built without
+ * OpenMP, where they do nothing; the same file built with -fopenmp is the all-core timing
+ * baseline, and gives bitwise the same results (tested).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -82,12 +87,14 @@ void or_gauss_blur(const double *z, int n, int m, double sigma, double *out)
     for (int t = -R; t <= R; ++t) { wt[t + R] = exp(-(double)(t * t) / (2 * sigma * sigma)); s += wt[t + R]; }
     for (int t = 0; t <= 2 * R; ++t) wt[t] /= s;
     double *tmp = malloc(sizeof(double) * (size_t)n * m);
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < m; ++j) {
             double a = 0;
             for (int t = -R; t <= R; ++t) a += wt[t + R] * z[(size_t)i * m + mirror(j + t, m)];
             tmp[(size_t)i * m + j] = a;
         }
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < m; ++j) {
             double a = 0;
@@ -103,6 +110,7 @@ void or_gauss_blur(const double *z, int n, int m, double sigma, double *out)
  * Pinned by: g = 1 on a constant image; closed form on a linear ramp. */
 void or_edge_detector(const double *zb, int n, int m, double beta_edge, double *g)
 {
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < m; ++j) {
             double zx = (zb[(size_t)i * m + mirror(j + 1, m)] - zb[(size_t)i * m + mirror(j - 1, m)]) / 2.0;
@@ -116,6 +124,7 @@ void or_edge_detector(const double *zb, int n, int m, double beta_edge, double *
  * away, product structure for two markers. */
 void or_distance(int n, int m, const double *mx, const double *my, int k, double sigma_d, double *d)
 {
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < m; ++j) {
             double p = 1.0;
@@ -180,6 +189,7 @@ int or_initial_phi(int n, int m, const double *mx, const double *my, int k, doub
         double cx = 0, cy = 0;
         for (int q = 0; q < k; ++q) { cx += mx[q]; cy += my[q]; }
         cx /= k; cy /= k;
+        #pragma omp parallel for
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < m; ++j)
                 phi[(size_t)i * m + j] = r0 - sqrt((j - cx) * (j - cx) + (i - cy) * (i - cy));
@@ -187,6 +197,7 @@ int or_initial_phi(int n, int m, const double *mx, const double *my, int k, doub
         free(hull);
         return 0;
     }
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < m; ++j) {
             double px = j, py = i, dmin = INFINITY;
@@ -262,6 +273,7 @@ static int fw_taps(int I, int n, int *idx, double *wt)
 void or_restrict(const double *f, int n, int m, double *c)
 {
     int nc = n / 2, mc = m / 2;
+    #pragma omp parallel for
     for (int I = 0; I < nc; ++I) {
         int ri[3], ci[3];
         double rw[3], cw[3];
@@ -295,6 +307,7 @@ static int bl_taps(int p, int nc, int *idx, double *wt)
  * interior, constants everywhere; P = 4 R^T away from the boundary. */
 void or_interpolate_add(const double *e, int nc, int mc, double *f, int n, int m)
 {
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i) {
         int ri[2], ci[2];
         double rw[2], cw[2];
@@ -373,10 +386,12 @@ static void frozen_coeffs(const double *phi, const double *w, const double *Fn, 
 {
     size_t N = (size_t)n * m;
     double *G = malloc(sizeof(double) * N);
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < m; ++j)
             G[(size_t)i * m + j] = w[(size_t)i * m + j] / grad_norm(phi, n, m, h, p->beta, i, j);
     double area = area_term(phi, n, m, h, p, n0m0, A1);
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < m; ++j) {
             size_t q = (size_t)i * m + j;
@@ -408,6 +423,7 @@ void or_apply_L(const double *phi, const double *w, const double *Fn, int n, int
     coeffs_alloc(&k, n, m);
     frozen_coeffs(phi, w, Fn, NULL, n, m, h, p, n0m0, A1, &k);
     double area = area_term(phi, n, m, h, p, n0m0, A1);
+    #pragma omp parallel for
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < m; ++j) {
             size_t q = (size_t)i * m + j;
@@ -426,6 +442,7 @@ void or_apply_L(const double *phi, const double *w, const double *Fn, int n, int
 void or_fitting(const double *z, const double *d, const double *phin, int n, int m,
                 double c1, double c2, const or_params *p, double *Fn)
 {
+    #pragma omp parallel for
     for (size_t q = 0; q < (size_t)n * m; ++q) {
         double F = p->lambda1 * (z[q] - c1) * (z[q] - c1) - p->lambda2 * (z[q] - c2) * (z[q] - c2);
         if (p->model == 0) F += p->theta * d[q];
@@ -549,6 +566,7 @@ static void solve_run(const or_coeffs *k, const double *src, double *dst, int ro
  * coefficient is k (Sec. 4.3, step I). */
 static void star_flags(const or_coeffs *k, double Sigma, int sweep, int *star)
 {
+    #pragma omp parallel for
     for (int i = 0; i < k->n; ++i)
         for (int j = 0; j < k->m; ++j)
             star[(size_t)i * k->m + j] = cell_class(k, i, j, Sigma) == sweep;
@@ -560,16 +578,17 @@ static void sweep_members(const or_coeffs *k, const int *star, int sweep, int pi
 {
     int n = k->n, m = k->m, rowwise = sweep < 2;
     int nl = rowwise ? n : m, len = rowwise ? m : n;
-    int *sl = malloc(sizeof(int) * len), *ml = malloc(sizeof(int) * len);
+    #pragma omp parallel for
     for (int l = 0; l < nl; ++l) {
+        int *sl = malloc(sizeof(int) * len), *ml = malloc(sizeof(int) * len);
         for (int t = 0; t < len; ++t) sl[t] = star[rowwise ? (size_t)l * m + t : (size_t)t * m + l];
         for (int lo = 0; lo < len; lo += piece) {
             int hi = lo + piece < len ? lo + piece : len;
             line_members(sl, lo, hi, ml);
         }
         for (int t = 0; t < len; ++t) member[rowwise ? (size_t)l * m + t : (size_t)t * m + l] = ml[t];
+        free(sl); free(ml);
     }
-    free(sl); free(ml);
 }
 
 /* Hybrid Smoother 2 in the parallel ordering (the ordering the GPU runs, restated plainly).
@@ -596,6 +615,7 @@ static void hs2_parallel(const or_coeffs *k, double Sigma, double *phi)
         sweep_members(k, star, sweep, OR_CHUNK, member);
         for (int c = 0; c < 2; ++c) {
             int colour = rev ? 1 - c : c;
+            #pragma omp parallel for
             for (int i = 0; i < n; ++i)
                 for (int j = 0; j < m; ++j)
                     if ((i + j) % 2 == colour && !member[(size_t)i * m + j]) {
@@ -609,6 +629,7 @@ static void hs2_parallel(const or_coeffs *k, double Sigma, double *phi)
         for (int c = 0; c < 2; ++c) {
             int parity = rev ? 1 - c : c;
             memcpy(pre, phi, sizeof(double) * N);
+            #pragma omp parallel for
             for (int l = parity; l < nl; l += 2)
                 for (int lo = 0; lo < len; lo += OR_CHUNK) {
                     int hi = lo + OR_CHUNK < len ? lo + OR_CHUNK : len;
@@ -981,6 +1002,7 @@ static void residual(or_solver *s, int l)
 {
     or_level *L = &s->lv[l];
     or_apply_L(L->phi, L->w, L->Fn, L->n, L->m, L->h, &s->p, s->n0m0, s->A1, L->tmp);
+    #pragma omp parallel for
     for (size_t q = 0; q < (size_t)L->n * L->m; ++q) L->tmp[q] = L->rhs[q] - L->tmp[q];
 }
 

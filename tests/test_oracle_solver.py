@@ -177,3 +177,18 @@ def test_every_controlled_step_reaches_the_tolerance(n, seed):
         assert att[-1][1][-1] <= 1e-6
         taus.append(tau)
     assert all(b <= a for a, b in zip(taus, taus[1:]))
+
+
+def test_all_core_build_gives_bitwise_the_serial_results():
+    # the -fopenmp build (the all-core timing baseline) runs the independent loops in parallel;
+    # every V-cycle equals the serial checker's bitwise
+    img, mk, _ = synth.ellipses(96, 80, 8, (10, 50), 6, 0.05, 4, dtype=np.float64)
+    out = []
+    for omp in (False, True):
+        s = O.Solver(img, mk, O.params(96, 80, levels=5), openmp=omp)
+        s.begin_step()
+        rhos = [s.vcycle() for _ in range(3)]
+        out.append((rhos, s.phi))
+        s.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
