@@ -97,14 +97,44 @@ def dist_init():
     return rank, ws, lrank, dist
 
 
-def oracle_sample(img, mk, cycles_needed=None, full=False, sample_cycles=2):
+def host_info():
+    """The host the CPU baseline runs on: logical cores, CPU model and RAM."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            model = None
+    ram = None
+    try:
+        with open("/proc/meminfo") as f:
+            ram = round(int(f.readline().split()[1]) / 1024 ** 2, 1)
+    except Exception:
+        pass
+    return {"logical_cores": os.cpu_count(), "cpu_model": model, "ram_gib": ram}
+
+
+def oracle_sample(img, mk, cycles_needed=None, full=False, sample_cycles=2, openmp=False):
     """Times the oracle on the workload: set-up, begin_step and `sample_cycles` V-cycles (all
-    V-cycles to rho <= 1e-6 when `full`).  Returns a dict."""
+    V-cycles to rho <= 1e-6 when `full`).  openmp: the all-core build of the oracle (its
+    independent loops on every host core; bitwise the serial results).  Returns a dict."""
     import oracle as O
     n, m = img.shape
     p = O.params(n, m, levels=9)
     t0 = time.perf_counter()
-    s = O.Solver(img.astype(np.float64), mk, p)
+    s = O.Solver(img.astype(np.float64), mk, p, openmp=openmp)
     t1 = time.perf_counter()
     s.begin_step()
     t2 = time.perf_counter()
@@ -122,6 +152,10 @@ def oracle_sample(img, mk, cycles_needed=None, full=False, sample_cycles=2):
 
 
 def run_reference(args):
+    """The oracle arm: the FP64 C oracle (its all-core OpenMP build, the parallel ordering of the
+    smoother) on the host cores.  Each step is the whole step of the bench workload (set-up,
+    V-cycles until rho <= 1e-6, end of step), unless --sample-cycles N > 0 asks for a sample of
+    N V-cycles scaled to the V-cycles the first warm-up step needed."""
     rank, ws, _, dist = dist_init()
     if rank != 0:
         if dist:
@@ -131,22 +165,34 @@ def run_reference(args):
     W = synth.workload(WORKLOAD)
     img, mk = W.image, W.markers
     n, m = img.shape
+    full = args.sample_cycles <= 0
     cycles_needed = None
     for w in range(args.warmup):
-        r = oracle_sample(img, mk, full=(w == 0 and args.sample_cycles >= 2))
-        if w == 0 and args.sample_cycles >= 2:
+        r = oracle_sample(img, mk, full=(w == 0 or full), openmp=True)
+        if w == 0:
             cycles_needed = r["cycles_run"]
     if cycles_needed is None:
         cycles_needed = 13
-    per_step = []
+    per_step, measured = [], []
     for _ in range(args.steps):
-        r = oracle_sample(img, mk, sample_cycles=args.sample_cycles)
-        per_step.append(r["setup"] + r["begin"] + cycles_needed * r["cycle"])
+        if full:
+            r = oracle_sample(img, mk, full=True, openmp=True)
+            t = r["setup"] + r["begin"] + r["cycles_run"] * r["cycle"]
+            per_step.append(t)
+            measured.append(t)
+        else:
+            r = oracle_sample(img, mk, sample_cycles=args.sample_cycles, openmp=True)
+            per_step.append(r["setup"] + r["begin"] + cycles_needed * r["cycle"])
+            measured.append(r["setup"] + r["begin"] + args.sample_cycles * r["cycle"])
     sec = float(np.mean(per_step))
     value = n * m / sec
-    sample = (f"FP64 C oracle, 1 host core: set-up + begin_step + {args.sample_cycles} V-cycles of the {n}x{m} workload "
-              f"per step, scaled to the {cycles_needed} V-cycles the oracle needs to reach rho <= 1e-6 "
-              f"(measured in the first warm-up step)")
+    hi = host_info()
+    if full:
+        sample = (f"FP64 C oracle (all-core OpenMP build, {hi['logical_cores']} threads): the whole step of the "
+                  f"{n}x{m} workload per timed step (set-up, {cycles_needed} V-cycles to rho <= 1e-6)")
+    else:
+        sample = (f"FP64 C oracle (all-core OpenMP build): set-up + begin_step + {args.sample_cycles} V-cycles per "
+                  f"step, extrapolated to the {cycles_needed} V-cycles the oracle needs (first warm-up step)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -154,7 +200,9 @@ def run_reference(args):
             "config": {"workload": f"{WORKLOAD}: {n}x{m} FP32 image, 12 ellipses, 8 markers, 9 grids, "
                                    f"V(2,2), tau 1, one pseudo-time step to rho <= 1e-6",
                        "l2": "n/a (host)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": hi["logical_cores"], "kind": "oracle",
+                             "sample": sample, "extrapolated": not full, "host": hi,
+                             "measured_s_per_step": float(np.mean(measured))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     if dist:
@@ -171,13 +219,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        r = None
-        try:
-            r = oracle_sample(img_np, mk)     # before any GPU call
+        try:   # before any GPU call: the whole step on all host cores, and 2 V-cycles on one core
+            cpu = {"all": oracle_sample(img_np, mk, full=True, openmp=True),
+                   "one": oracle_sample(img_np, mk, sample_cycles=2)}
         except Exception as e:  # the baseline is a report, never a reason to fail the bench
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
-        if r:
-            cpu = r
+            cpu = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
 
     buildlib.build()
     torch.cuda.set_device(lrank)
@@ -278,12 +324,14 @@ def run_ours(args):
             p8 = segmg.default_params(8192, 8192)
             s8 = segmg.Solver(torch.as_tensor(img8, device=dev), mk8, p8)
             s8.begin_step()
+            shapes8 = s8.autotune(reps=1)
             kt8 = s8.time_kernels(0, reps=3)
             sw8 = float(np.mean(kt8[1:5]))
             ach8 = bytes_per_cell * 8192 * 8192 / (sw8 * 1e-3) / 1e9
             snap_bytes = 24.25       # pn, u, w, F read; G, f and member masks (1/4 B) written
             res_bytes = 16           # pn, u, w, F read, r written (+ 0 rhs on the finest grid)
             roof_big = {"bound": "hbm", "grid": "8192x8192 FP32", "unit": "GB/s", "peak": hbm,
+                        "tile_shape": shapes8[0],
                         "sweep": {"ms": sw8, "achieved": ach8, "frac": ach8 / hbm},
                         "snapshot": {"ms": kt8[0], "achieved": snap_bytes * 8192 ** 2 / (kt8[0] * 1e-3) / 1e9},
                         "residual": {"ms": kt8[5], "achieved": res_bytes * 8192 ** 2 / (kt8[5] * 1e-3) / 1e9}}
@@ -294,15 +342,36 @@ def run_ours(args):
             roof_big = {"error": str(e)}
 
     cpu_line = None
-    if cpu and "setup" in cpu:
-        cyc = float(np.mean(cycles))
-        sec = cpu["setup"] + cpu["begin"] + cyc * cpu["cycle"]
-        cpu_line = {"value": n * m / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-                    "sample": (f"FP64 C oracle on 1 host core: set-up + begin_step + 2 V-cycles of the same "
-                               f"{n}x{m} workload ({cpu['setup'] + cpu['begin'] + 2 * cpu['cycle']:.1f} s), "
-                               f"scaled to the {cyc:.1f} V-cycles per step the GPU needed")}
+    if cpu and "all" in cpu:
+        a, o1 = cpu["all"], cpu["one"]
+        hi = host_info()
+        sec = a["setup"] + a["begin"] + a["cycles_run"] * a["cycle"]
+        sec1 = o1["setup"] + o1["begin"] + a["cycles_run"] * o1["cycle"]
+        cpu_line = {"value": n * m / sec, "unit": UNIT, "cores": hi["logical_cores"], "kind": "oracle",
+                    "sample": (f"FP64 C oracle, all-core OpenMP build ({hi['logical_cores']} threads): the whole step "
+                               f"of the same {n}x{m} workload ({a['cycles_run']} V-cycles to rho <= 1e-6, "
+                               f"{sec:.1f} s), measured, not extrapolated"),
+                    "host": hi,
+                    "one_core": {"value": n * m / sec1, "cores": 1,
+                                 "sample": (f"serial build: set-up + begin_step + 2 V-cycles "
+                                            f"({o1['setup'] + o1['begin'] + 2 * o1['cycle']:.1f} s), extrapolated "
+                                            f"to the {a['cycles_run']} V-cycles of the step")}}
     elif cpu:
         cpu_line = cpu
+
+    # the other configurations, measured in the same run (extra keys of this line): 25000^2 mixed
+    # precision with its error against the oracle on a 2048^2 crop, and the 64-image batch
+    extra = {}
+    if not args.no_extra:
+        for key, fn in (("config3_mixed_25000", lambda: config3_report(25000, 1, 2048, lrank)),
+                        ("config4_batch_64", lambda: config4_report(64, 1, lrank))):
+            try:
+                t0 = time.perf_counter()
+                extra[key] = fn()
+                extra[key]["wall_s"] = time.perf_counter() - t0
+            except Exception as e:   # a report, never a reason to lose the headline line
+                extra[key] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
 
     h2d = n * m * 4 + mk.size * 8
     d2h = n * m
@@ -323,7 +392,7 @@ def run_ours(args):
             "roofline": roof, "roofline_hbm": roof_big,
             "cpu_baseline": cpu_line,
             "clocks": clk.summary(),
-            "wall_s_timed_region": t_wall}
+            "wall_s_timed_region": t_wall, **extra}
     print(json.dumps(line), flush=True)
     s.close()
     if dist:
@@ -351,16 +420,20 @@ def run_profile_case(args):
 
 
 def run_config3(args):
+    print(json.dumps(config3_report(args.config3, args.steps)), flush=True)
+
+
+def config3_report(N, steps, crop_size=2048, dev_index=0):
     """Mixed precision at large size (w stored in BF16, smoothing FP32, FP64 norms and coarsest
     solve): one pseudo-time step to rho <= 1e-6 on an N x N image from the ellipse recipe
     (200 ellipses, axes 100-3000 px, 20 markers), the smoother roofline at that size, and the
-    error against the FP64 oracle on a 2048 x 2048 crop solved as a standalone problem."""
+    error against the FP64 oracle (its all-core build) on a crop_size^2 crop solved as a
+    standalone problem.  Returns a dict."""
     import torch
     from paper_1807_02137_gb300 import buildlib, segmg, synth
     import oracle as O
     buildlib.build()
-    N = args.config3
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", dev_index)
     t0 = time.perf_counter()
     img, mk = synth.ellipses_device(N, N, 200, (100 * N / 25000, 3000 * N / 25000), 20, 0.05, 2, dev)
     gen_s = time.perf_counter() - t0
@@ -369,8 +442,8 @@ def run_config3(args):
     st = torch.cuda.ExternalStream(s.stream_ptr, device=dev)
     s.solve_step(TOL, MAX_CYCLES)                 # warm-up (graph capture)
     times, cyc = [], []
-    with Clocks(0) as clk:
-        for _ in range(max(1, args.steps)):
+    with Clocks(dev_index) as clk:
+        for _ in range(max(1, steps)):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
             s.reset(img, mk)
@@ -388,7 +461,7 @@ def run_config3(args):
     s.close()
     # accuracy on a crop around the markers, solved standalone by the GPU (mixed and FP32) and
     # by the FP64 oracle
-    C = min(2048, N)
+    C = min(crop_size, N)
     cx, cy = float(np.mean(mk[:, 0])), float(np.mean(mk[:, 1]))
     j0 = int(min(max(cx - C / 2, 0), N - C)); i0 = int(min(max(cy - C / 2, 0), N - C))
     crop = img[i0:i0 + C, j0:j0 + C].float().cpu().numpy().copy()
@@ -396,47 +469,60 @@ def run_config3(args):
     cmk = cmk[(cmk[:, 0] >= 0) & (cmk[:, 0] <= C - 1) & (cmk[:, 1] >= 0) & (cmk[:, 1] <= C - 1)]
     del img
     torch.cuda.empty_cache()
-    out = {}
+    out, taus = {}, {}
     for name, prec in (("mixed", segmg.MG_MIXED), ("f32", segmg.MG_F32)):
         pc = segmg.default_params(C, C, precision=prec)
         sc = segmg.Solver(torch.as_tensor(crop, device=dev), cmk, pc)
         sc.solve_step(TOL, MAX_CYCLES)
         out[name] = sc.phi().double().cpu().numpy()
+        taus[name] = sc.stats()["tau"]
         sc.close()
-    po = O.params(C, C, levels=segmg.default_params(C, C).levels)
+    # the oracle solves the same step with the tau each GPU solve's step control accepted
+    refs, hist = {}, None
     t1 = time.perf_counter()
-    so = O.Solver(crop.astype(np.float64), cmk, po)
-    hist = so.solve_step(1e-9, 80)
-    ref = so.phi
+    for tau in sorted(set(taus.values())):
+        po = O.params(C, C, levels=segmg.default_params(C, C).levels, tau=tau)
+        so = O.Solver(crop.astype(np.float64), cmk, po, openmp=True)
+        hist = so.solve_step(1e-9, 80)
+        refs[tau] = so.phi
+        so.close()
     oracle_s = time.perf_counter() - t1
     acc = {}
     for name, phi in out.items():
+        ref = refs[taus[name]]
         acc[name] = {"max_rel_err_phi": float(np.max(np.abs(phi - ref)) / np.max(np.abs(ref))),
                      "mask_mismatch_frac": float(np.mean((phi > 0) != (ref > 0)))}
-    line = {"config": f"{N}x{N} mixed precision (w BF16, smoothing FP32, FP64 norms/coarsest)",
+    bytes_sweep = 16.125 * N * N
+    return {"config": f"{N}x{N} mixed precision (w BF16, smoothing FP32, FP64 norms/coarsest)",
             "levels": stats["levels"], "unknowns_per_s": N * N / (np.mean(times) * 1e-3),
             "ms_per_step": float(np.mean(times)), "cycles_per_step": float(np.mean(cyc)),
+            "tau": stats["tau"], "rho": float(r),
             "device_bytes": stats["device_bytes"], "generate_s": gen_s,
-            "roofline_sweep": {"ms": sw, "achieved_GBs": 16.125 * N * N / (sw * 1e-3) / 1e9, "peak": hbm,
-                               "frac": 16.125 * N * N / (sw * 1e-3) / 1e9 / hbm},
+            "roofline_sweep": {"ms": sw, "achieved_GBs": bytes_sweep / (sw * 1e-3) / 1e9, "peak": hbm,
+                               "frac": bytes_sweep / (sw * 1e-3) / 1e9 / hbm},
             "kernel_ms": {"snapshot": kt[0], "sweeps": kt[1:5], "residual": kt[5]},
-            "crop": {"size": C, "origin": [i0, j0], "markers": int(len(cmk)), "oracle_cycles": len(hist),
-                     "oracle_rho": hist[-1], "oracle_s": oracle_s, **acc},
+            "crop": {"size": C, "origin": [i0, j0], "markers": int(len(cmk)), "tau": taus,
+                     "oracle_cycles": len(hist), "oracle_rho": hist[-1], "oracle_s": oracle_s,
+                     "oracle_build": "all-core OpenMP (bitwise the serial checker)", **acc},
             "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
 
 
 def run_config4(args):
-    """Batched uneven sizes: 64 images with sizes drawn from {256, 512, 768, 1024, 2048}^2, each
-    from the ellipse recipe with its own 4-16 markers (FP32).  One pseudo-time step of all images
-    to rho <= 1e-6 through the batch graph (one launch per V-cycle, converged images skipped on
-    the device), tile shapes from the autotuner, against the same images solved one by one."""
+    print(json.dumps(config4_report(args.config4, args.steps)), flush=True)
+
+
+def config4_report(count, steps, dev_index=0):
+    """Batched uneven sizes: `count` images with sizes drawn from {256, 512, 768, 1024, 2048}^2,
+    each from the ellipse recipe with its own 4-16 markers (FP32).  One pseudo-time step of all
+    images to rho <= 1e-6 through the batch graph (one launch per V-cycle, converged images skipped
+    on the device), tile shapes from the autotuner, against the same images solved one by one.
+    Returns a dict."""
     import torch
     from paper_1807_02137_gb300 import buildlib, segmg, synth
     buildlib.build()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", dev_index)
     rng = np.random.Generator(np.random.PCG64(3))
-    sizes = rng.choice([256, 512, 768, 1024, 2048], size=args.config4)
+    sizes = rng.choice([256, 512, 768, 1024, 2048], size=count)
     imgs, mks, params = [], [], []
     for q, n in enumerate(sizes):
         k = int(rng.integers(4, 17))
@@ -460,10 +546,10 @@ def run_config4(args):
         return dt, cyc, rho
 
     batch_run(True)                       # warm-up (graph build, autotune, caches)
-    tb = [batch_run(True) for _ in range(max(1, args.steps))]
-    tb_plain = [batch_run(False) for _ in range(max(1, args.steps))]
+    tb = [batch_run(True) for _ in range(max(1, steps))]
+    tb_plain = [batch_run(False) for _ in range(max(1, steps))]
     ts = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, steps)):
         tot, cyc_s = 0.0, []
         for q in range(len(imgs)):
             s = segmg.Solver(imgs[q], mks[q], params[q])
@@ -477,17 +563,17 @@ def run_config4(args):
             s.close()
         ts.append(tot)
     best_b = min(tb, key=lambda x: x[0])
-    line = {"config": f"batched: {len(sizes)} FP32 images, sizes {sorted(set(int(x) for x in sizes))}",
+    return {"config": f"batched: {len(sizes)} FP32 images, sizes {sorted(set(int(x) for x in sizes))}",
             "size_counts": {int(k): int((sizes == k).sum()) for k in sorted(set(sizes))},
             "cells": cells,
             "batched_autotuned": {"s": best_b[0], "unknowns_per_s": cells / best_b[0],
                                   "cycles_min_max": [min(best_b[1]), max(best_b[1])],
                                   "rho_max": max(best_b[2])},
             "batched_default_tiles": {"s": min(x[0] for x in tb_plain),
-                                      "unknowns_per_s": cells / min(x[0] for x in tb_plain)},
+                                      "unknowns_per_s": cells / min(x[0] for x in tb_plain),
+                                      "rho_max": max(max(x[2]) for x in tb_plain)},
             "one_by_one": {"s": min(ts), "unknowns_per_s": cells / min(ts)},
             "speedup_batched_vs_one_by_one": min(ts) / best_b[0]}
-    print(json.dumps(line), flush=True)
 
 
 def run_algorithms(args):
@@ -629,7 +715,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-roofline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--sample-cycles", type=int, default=2, help="V-cycles per reference-arm sample")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 25000^2 and 64-image reports")
+    ap.add_argument("--sample-cycles", type=int, default=0,
+                    help="reference arm: V-cycles per sample (0: the whole step is timed)")
     ap.add_argument("--profile", type=int, default=0, help="run the N x N ncu profiling case instead")
     ap.add_argument("--cycles", type=int, default=2)
     ap.add_argument("--tile-shape", type=int, default=-1, help="profiling case: this tile shape on every grid")

@@ -1,12 +1,16 @@
 // host.cu -- driver of the FAS V-cycle and the C ABI declared in include/segmg.h.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <type_traits>
 #include <random>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/segmg.h"
 #include "internal.h"
@@ -20,6 +24,25 @@ namespace {
 using namespace segmg;
 
 thread_local std::string g_err;
+
+// NVTX range for profilers (no cost without one).  The ranges mark host-side work: per level in
+// eager mode (use_graph = 0); with graphs, the V-cycle range encloses the graph launch.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
+// Per-V-cycle log of the step control (JSON lines appended to the file named by the SEGMG_LOG
+// environment variable; nothing when it is unset).
+void log_cycle(int step, int attempt, int cycle, double rho, double tau, double ms) {
+    static const char *path = std::getenv("SEGMG_LOG");
+    if (!path || !*path) return;
+    if (FILE *f = std::fopen(path, "a")) {
+        std::fprintf(f, "{\"step\": %d, \"attempt\": %d, \"cycle\": %d, \"rho\": %.17g, \"tau\": %.17g, \"ms\": %.4f}\n",
+                     step, attempt, cycle, rho, tau, ms);
+        std::fclose(f);
+    }
+}
 
 int fail(int code, const std::string &msg) {
     g_err = msg;
@@ -515,6 +538,7 @@ struct Solver final : SolverBase {
     const double *area_ptr() const { return p.model == MG_MODEL_RC ? dsc->area : nullptr; }
 
     int begin_step(double *r0out) override {
+        Range range("begin step");
         launch_fold<T>(view(0), st);
         for (int l = 1; l < nlev; ++l) {
             Level<T> &Pf = lv[l - 1], &Lc = lv[l];
@@ -581,6 +605,7 @@ struct Solver final : SolverBase {
     }
 
     void smooth(int l) {
+        Range range("smoothing iteration");
         area_term(l, lv[l].u);
         LevelView<T> v = view(l);
         launch_snapshot<T>(v, area_ptr(), st);
@@ -594,6 +619,10 @@ struct Solver final : SolverBase {
     }
 
     void cycle(int l) {
+        static const char *kLevelNames[kMaxLevels] = {"grid 0", "grid 1", "grid 2", "grid 3", "grid 4", "grid 5",
+                                                      "grid 6", "grid 7", "grid 8", "grid 9", "grid 10", "grid 11",
+                                                      "grid 12", "grid 13", "grid 14", "grid 15"};
+        Range range(kLevelNames[l]);
         if (l == lc) {
             launch_bottom_cycle(true);
             ++launches;
@@ -831,6 +860,7 @@ struct Solver final : SolverBase {
     double current_rho() const { return res0 > 0 ? std::sqrt(hsc->norm2) / res0 : std::sqrt(hsc->norm2); }
 
     int vcycle(double *rhoout) override {
+        Range range("V-cycle");
         if (!in_step) return fail(MG_ERR_STATE, "mg_vcycle before mg_begin_step");
         const double rho_prev = rho > 0 ? rho : 1.0;
         int rc;
@@ -997,6 +1027,7 @@ struct Solver final : SolverBase {
     }
 
     int end_step(double *etaout) override {
+        Range range("end step");
         if (!in_step) return fail(MG_ERR_STATE, "mg_end_step before mg_begin_step");
         launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
         CKL();
@@ -1155,17 +1186,23 @@ bool attempt_stalled(const std::vector<double> &rho, double stall_ratio) {
 // One pseudo-time step under the step control (mg_solve_step): attempts from phi^n with tau,
 // tau / 2, ... until one reaches tol.  A rejected attempt restores phi^n.
 int solve_step_controlled(SolverBase *s, double tol, int max_cycles, int *cycles, double *rho) {
+    Range range("pseudo-time step");
     const bool control = s->params().stall_ratio > 0;
     int total = 0, rc = MG_OK;
     double r = 1.0;
     bool ok = false;
+    mg_stats st0;
+    s->stats(&st0);
     for (int attempt = 0;; ++attempt) {
         if ((rc = s->begin_step(nullptr))) return rc;
         std::vector<double> hist;
         bool bad = false;   // diverged or non-finite: the state is not kept
         for (int j = 1; j <= max_cycles; ++j) {
+            const auto t0 = std::chrono::steady_clock::now();
             rc = s->vcycle(&r);
             ++total;
+            log_cycle(st0.steps, attempt, j, r, s->params().tau,
+                      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
             if (rc == MG_ERR_DIVERGED || rc == MG_ERR_NAN) {
                 if (!control) return rc;
                 bad = true;

@@ -33,7 +33,7 @@ def test_reference_arm_under_two_ranks():
     assert len(lines) == 1                       # rank 0 alone prints
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
-    assert d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["cores"] == os.cpu_count()
 
 
 def _worker(rank, world, port, q):
