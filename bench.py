@@ -533,21 +533,25 @@ def config4_report(count, steps, dev_index=0):
         params.append(segmg.default_params(int(n), int(n)))
     cells = int(sum(int(n) ** 2 for n in sizes))
 
-    def batch_run(tune):
+    def batch_run(tune, reps):
+        # one untimed step (graph build, and the tuning when asked), then `reps` timed steps from
+        # the same images (mg_reset of every image: tau back to its parameter, graphs kept)
         b = segmg.Batch(imgs, mks, params)
-        shapes = None
         if tune:
             b.autotune(reps=1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        cyc, rho = b.solve_step(TOL, MAX_CYCLES)
-        dt = time.perf_counter() - t0
+        b.solve_step(TOL, MAX_CYCLES)
+        out = []
+        for _ in range(reps):
+            b.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cyc, rho = b.solve_step(TOL, MAX_CYCLES)
+            out.append((time.perf_counter() - t0, cyc, rho))
         b.close()
-        return dt, cyc, rho
+        return out
 
-    batch_run(True)                       # warm-up (graph build, autotune, caches)
-    tb = [batch_run(True) for _ in range(max(1, steps))]
-    tb_plain = [batch_run(False) for _ in range(max(1, steps))]
+    tb = batch_run(True, max(1, steps))
+    tb_plain = batch_run(False, max(1, steps))
     ts = []
     for _ in range(max(1, steps)):
         tot, cyc_s = 0.0, []

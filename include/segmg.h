@@ -219,6 +219,13 @@ int mg_get_stats(mg_handle h, mg_stats *s);
  * counterpart.  Errors: MG_ERR_ARG (rounds < 0). */
 int mg_set_wait_limit(mg_handle h, long long rounds);
 
+/* Which kernel forms the coefficient snapshot (a tuning step of this implementation; the paper
+ * has no counterpart): 1 = 32 x 32 tiles staged in shared memory (short critical path, for
+ * small grids), 2 = one warp per tile walking down its rows with register windows (fewer
+ * instructions per cell, for large HBM-bound grids), 0 = chosen per grid by its size (the
+ * default).  All give bitwise the same results.  Errors: MG_ERR_ARG. */
+int mg_set_snapshot_kernel(mg_handle h, int kind);
+
 /* Host-side fault injection for tests of the error paths (no counterpart in the paper): the
  * `cycle`-th V-cycle (1-based, counted from the start of the current or next step attempt) run
  * after this call reports a residual ratio of 1e9, as a diverged V-cycle would; mg_vcycle then
@@ -357,11 +364,18 @@ int mg_set_cluster_level(mg_handle h, int level);
 typedef struct mg_batch_s *mg_batch;
 int mg_batch_setup(mg_batch *out, int count, const void *const *images, const int *n, const int *m,
                    const double *const *markers, const int *k, const mg_params *params, void *stream);
-/* One pseudo-time step of every image (begin, V-cycles until every rho <= tol or max_cycles
- * launches, end).  cycles[i] / rho[i] (host, may be NULL) get each image's V-cycles and final
- * rho.  MG_ERR_TIMEOUT when an image did not reach tol. */
+/* One pseudo-time step of every image (begin, V-cycles until every rho <= tol, end), with the
+ * step control of mg_solve_step per image: an attempt that stalls, diverges or reaches max_cycles
+ * V-cycles halts that image; when no image is left running, the halted ones restart together
+ * from their phi^n with tau / 2 (at most params.max_halvings times each).  The results equal
+ * those of mg_solve_step on each image alone.  cycles[i] / rho[i] (host, may be NULL) get each
+ * image's V-cycles (all attempts) and final rho.  MG_ERR_TIMEOUT when an image did not reach
+ * tol.  To solve new images of the same sizes, call mg_reset on mg_batch_handle(b, i). */
 int mg_batch_solve_step(mg_batch b, double tol, int max_cycles, int *cycles, double *rho);
-/* mg_autotune for every image of the batch. */
+/* Tile shapes for the batch as a whole: runs mg_autotune on every image, then times `reps`
+ * launches of the batch graph (every image running) with those per-image choices and with each
+ * single tile shape on every grid of every image, and keeps the fastest.  The images' phi is
+ * restored; results of later steps do not depend on the choice.  Waits. */
 int mg_batch_autotune(mg_batch b, int reps);
 mg_handle mg_batch_handle(mg_batch b, int i);
 void mg_batch_destroy(mg_batch b);

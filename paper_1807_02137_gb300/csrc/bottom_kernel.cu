@@ -382,11 +382,11 @@ __device__ void bottom_subcycle(const BottomArgs &A, BGrid *Bs, int lb, uint8_t 
         int it;
         double res;
         if (A.coarse_fp64)
-            coarse_solve_block<float, double>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
+            coarse_solve_block<float, double>(cg, A.mp, A.sc->A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
                                               reinterpret_cast<double *>(scratch), red, s_err, &it, &res,
                                               A.coarse_aos, A.aos_dt);
         else
-            coarse_solve_block<float, float>(cg, A.mp, A.A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
+            coarse_solve_block<float, float>(cg, A.mp, A.sc->A1frac, A.h2nm_coarse, A.coarse_maxit, A.coarse_tol,
                                              reinterpret_cast<float *>(scratch), red, s_err, &it, &res,
                                              A.coarse_aos, A.aos_dt);
         if (threadIdx.x == 0) {

@@ -286,7 +286,9 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(LevelView<T> L, Model
     CoarseGrid<T> g{L.n, L.m, L.pitch, L.pn, L.u, L.w, L.wb, L.F, L.rhs, L.has_rhs, L.inv_2h, L.inv_tau, L.beta};
     int it;
     double res;
-    coarse_solve_block<T, C>(g, mp, A1frac, h2nm, maxit, tol, scratch, red, &s_err, &it, &res, aos, aos_dt);
+    (void)A1frac;   // the area of the initial contour is read from the device scalars (set by each reset,
+                    // so a captured graph stays valid across resets)
+    coarse_solve_block<T, C>(g, mp, sc->A1frac, h2nm, maxit, tol, scratch, red, &s_err, &it, &res, aos, aos_dt);
     if (threadIdx.x == 0) {
         sc->picard = it;
         sc->coarse_res = res;

@@ -144,6 +144,7 @@ struct SolverBase {
     virtual void set_cycles_step(int c) = 0;
     virtual int set_wait_limit(long long rounds) = 0;
     virtual int inject_divergence(int cycle) = 0;
+    virtual int set_snapshot_kernel(int kind) = 0;
 };
 
 template <typename T>
@@ -180,7 +181,10 @@ struct Solver final : SolverBase {
     double A1 = 0, res0 = 0, rho = 0, eta = 0;
     int steps = 0, cycles_step = 0, cycles_total = 0;
     int rejected = 0;             // step attempts rejected by the step control
+    double tau0 = 1.0;            // tau of the parameters (the step control halves p.tau)
+    long long graph_epoch = 0;    // counts drop_graphs(): a batch rebuilds its graph when it changed
     long long wait_limit = kDefaultWaitLimit;   // try_wait rounds of the TMA sweep's bounded waits
+    int snap_kind = 0;            // mg_set_snapshot_kernel: 0 by grid size, 1 tiles, 2 register windows
     int inject_cycle = 0;         // mg_inject_divergence: V-cycle (of a step attempt) that reports
                                   // a diverged residual once; 0 = none
     bool in_step = false;
@@ -215,6 +219,7 @@ struct Solver final : SolverBase {
     ~Solver() override { release(); }
 
     void drop_graphs() {
+        ++graph_epoch;
         if (gexec) cudaGraphExecDestroy(gexec);
         if (gexec_l) cudaGraphExecDestroy(gexec_l);
         if (gexec_li) cudaGraphExecDestroy(gexec_li);
@@ -266,6 +271,7 @@ struct Solver final : SolverBase {
 
     int init(int n_, int m_, const mg_params &p_, const mg_allocator *a, cudaStream_t s, int k) {
         p = p_; n = n_; m = m_; nlev = p.levels;
+        tau0 = p.tau;
         mp = ModelParams{p.model, p.mu, p.lambda1, p.lambda2, p.theta, p.nu, p.eps, p.beta};
         if (s) st = s;
         else { CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)); own_stream = true; }
@@ -412,7 +418,7 @@ struct Solver final : SolverBase {
         int it = 0;
         while (it < max_iter) {
             area_term(0, lv[0].u);
-            launch_snapshot<T>(view(0), area_ptr(), st);
+            launch_snapshot<T>(view(0), area_ptr(), snap_kind, st);
             launch_aos_iteration<T>(view(0), area_ptr(), dt, partials, dsc->aos, st);
             launches += area_launches() + 4;
             ++it;
@@ -465,8 +471,14 @@ struct Solver final : SolverBase {
 
     int reset(const void *image, const double *mk, int k) override {
         if (k > kcap) return fail(MG_ERR_ARG, "more markers than at set-up");
-        drop_graphs();   // A1 is baked into the graphs
+        // the kernels read the initial contour's area from the device scalars, so the captured
+        // graphs stay valid; only a tau changed by the step control is restored (and they go)
+        if (p.tau != tau0) {
+            p.tau = tau0;
+            drop_graphs();
+        }
         in_step = false;
+        rejected = 0;
         steps = cycles_step = cycles_total = 0;
         rho = eta = res0 = 0;
         Level<T> &L0 = lv[0];
@@ -608,7 +620,7 @@ struct Solver final : SolverBase {
         Range range("smoothing iteration");
         area_term(l, lv[l].u);
         LevelView<T> v = view(l);
-        launch_snapshot<T>(v, area_ptr(), st);
+        launch_snapshot<T>(v, area_ptr(), snap_kind, st);
         if (use_omega && infer_pending[l] && omega_buf[l]) {
             launch_omega_infer<T>(v, net, omega_buf[l], st);   // weights from this snapshot's G
             infer_pending[l] = false;
@@ -710,7 +722,7 @@ struct Solver final : SolverBase {
                 auto enqueue = [&]() {
                     for (int r = 0; r < reps; ++r) {
                         area_term(l, L.u);
-                        launch_snapshot<T>(v, area_ptr(), st);
+                        launch_snapshot<T>(v, area_ptr(), snap_kind, st);
                         for (int k = 0; k < 4; ++k) sweep(l, v, k, sh);
                     }
                 };
@@ -998,9 +1010,23 @@ struct Solver final : SolverBase {
 
     const mg_params &params() const override { return p; }
 
+    // phi = phi^n again on the finest grid (the increment zeroed), nothing else changed
+    int zero_increment() {
+        Level<T> &F = lv[0];
+        CK(cudaMemset2DAsync(F.u, (size_t)F.pitch * sizeof(T), 0, (size_t)F.m * sizeof(T), F.n, st));
+        return MG_OK;
+    }
+
     int inject_divergence(int cycle) override {
         if (cycle < 0) return fail(MG_ERR_ARG, "cycle < 0");
         inject_cycle = cycle;
+        return MG_OK;
+    }
+
+    int set_snapshot_kernel(int kind) override {
+        if (kind < 0 || kind > 2) return fail(MG_ERR_ARG, "snapshot kernel kind must be 0, 1 or 2");
+        snap_kind = kind;
+        drop_graphs();
         return MG_OK;
     }
 
@@ -1117,7 +1143,7 @@ struct Solver final : SolverBase {
         for (int r = 0; r < reps; ++r) {
             area_term(l, lv[l].u);
             cudaEventRecord(ev[0], st);
-            launch_snapshot<T>(v, area_ptr(), st);
+            launch_snapshot<T>(v, area_ptr(), snap_kind, st);
             cudaEventRecord(ev[1], st);
             if (p.smoother == MG_SMOOTH_GSLINE || p.smoother == MG_SMOOTH_HS1) {
                 relax(l, v, shape[l]);        // the whole smoother in the first slot
@@ -1275,6 +1301,8 @@ struct Batch {
     double *d_out = nullptr, *h_out = nullptr;
     cudaGraphExec_t exec = nullptr;
     double tol_baked = -1.0;
+    std::vector<long long> epochs;   // each image's graph_epoch when the batch graph was built
+    int tuned_shape = -2;            // mg_batch_autotune: -1 per-image shapes, 0..5 one shape, -2 not run
 
     ~Batch() {
         if (st) cudaStreamSynchronize(st);
@@ -1341,80 +1369,144 @@ struct Batch {
             if (e != cudaSuccess) { exec = nullptr; rc = fail(MG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e)); }
         }
         cudaGraphDestroy(B);
-        if (rc == MG_OK) tol_baked = tol;
+        if (rc == MG_OK) {
+            tol_baked = tol;
+            epochs.resize(count);
+            for (int i = 0; i < count; ++i) epochs[i] = s[i]->graph_epoch;
+        }
+        return rc;
+    }
+
+    // Tile shapes for the batch as a whole: the per-image choices of mg_autotune, and each tile
+    // shape on every grid of every image, each timed as `reps` launches of the batch graph (every
+    // image running: tolerance 0) from the images' phi^n; keeps the fastest.  The images' state
+    // is restored (phi = phi^n); a step is left begun, as after mg_autotune.
+    int autotune(int reps) {
+        const int count = (int)s.size();
+        std::vector<std::vector<int>> own(count);
+        for (int i = 0; i < count; ++i) {
+            int rc = s[i]->begin_step(nullptr);
+            if (!rc) rc = s[i]->autotune(reps, nullptr);
+            if (rc) return rc;
+            own[i].assign(s[i]->shape, s[i]->shape + kMaxLevels);
+        }
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_c = -1;
+        int rc = MG_OK;
+        for (int c = -1; c < kTileShapes && rc == MG_OK; ++c) {   // -1: the per-image choices
+            for (int i = 0; i < count && rc == MG_OK; ++i) {
+                std::vector<int> sh(kMaxLevels, c);
+                rc = s[i]->set_shapes(c < 0 ? own[i].data() : sh.data());
+                if (!rc) rc = s[i]->begin_step(nullptr);
+            }
+            if (rc || (rc = build(0.0))) break;
+            float t = 0;
+            for (int warm = 0; warm < 2 && rc == MG_OK; ++warm) {
+                if (cudaEventRecord(e0, st) != cudaSuccess) rc = fail(MG_ERR_CUDA, "event");
+                for (int r = 0; r < reps && rc == MG_OK; ++r)
+                    if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = fail(MG_ERR_CUDA, "graph launch");
+                if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                    rc = fail(MG_ERR_CUDA, "event");
+                cudaEventElapsedTime(&t, e0, e1);
+            }
+            for (int i = 0; i < count && rc == MG_OK; ++i) rc = s[i]->zero_increment();
+            if (rc == MG_OK && t < best) { best = t; best_c = c; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        for (int i = 0; i < count && rc == MG_OK; ++i) {
+            std::vector<int> sh(kMaxLevels, best_c);
+            rc = s[i]->set_shapes(best_c < 0 ? own[i].data() : sh.data());
+            if (!rc) rc = s[i]->begin_step(nullptr);
+        }
+        tuned_shape = best_c;
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
         return rc;
     }
 
     // One pseudo-time step of every image.  Each graph launch runs one V-cycle of every image
-    // that has not reached tol.  The step control of mg_solve_step applies per image: an image
-    // whose attempt stalls, diverges or reaches max_cycles V-cycles is restarted from its phi^n
-    // with tau / 2 (its graph branch is captured again).
+    // that has not reached tol.  The step control of mg_solve_step applies per image, in rounds:
+    // an image whose attempt stalls, diverges or reaches max_cycles V-cycles is halted on the
+    // device; once no image is left running, the halted ones restart from their phi^n with
+    // tau / 2 together (one rebuild of the batch graph per round).
     int solve_step(double tol, int max_cycles, int *cycles, double *rho) {
         const int count = (int)s.size();
         for (int i = 0; i < count; ++i) {
             int rc = s[i]->begin_step(nullptr);
             if (rc) return rc;
         }
-        if (!exec || tol != tol_baked) {
+        bool stale = !exec || tol != tol_baked || (int)epochs.size() != count;
+        for (int i = 0; i < count && !stale; ++i) stale = s[i]->graph_epoch != epochs[i];
+        if (stale) {
             int rc = build(tol);
             if (rc) return rc;
         }
         std::vector<int> cyc(count, 0), halvings(count, 0);
         std::vector<double> r(count, 1.0);
         std::vector<std::vector<double>> hist(count);
-        std::vector<char> active(count, 1), failed(count, 0);
+        std::vector<char> active(count, 1), failed(count, 0), restart(count, 0);
         int rc = MG_OK;
-        for (int launch = 0; rc == MG_OK; ++launch) {
-            CK(cudaGraphLaunch(exec, st));
-            CK(cudaStreamSynchronize(st));
-            bool any = false, rebuild = false;
-            for (int i = 0; i < count; ++i) {
-                if (!active[i]) continue;
-                const double n2 = h_out[3 * i], n0 = h_out[3 * i + 1];
-                ++cyc[i];
-                s[i]->cycles_step = cyc[i];
-                ++s[i]->cycles_total;
-                s[i]->launches += nodes[i] + 1;
-                r[i] = n0 > 0 ? std::sqrt(n2) / std::sqrt(n0) : std::sqrt(n2);   // as mg_vcycle
-                s[i]->rho = r[i];
-                const int err = (int)h_out[3 * i + 2];
-                if ((err & 1) && rc == MG_OK) rc = fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
-                if ((err & 4) && rc == MG_OK) {
-                    CK(cudaMemsetAsync(&s[i]->dsc->err, 0, sizeof(int), st));
-                    rc = fail(MG_ERR_TIMEOUT, "a tile copy into shared memory did not complete within the wait limit");
-                }
-                hist[i].push_back(r[i]);
-                if (r[i] <= tol) { active[i] = 0; continue; }
-                const mg_params &pi = s[i]->p;
-                const bool control = pi.stall_ratio > 0;
-                const bool bad = !std::isfinite(r[i]) || r[i] > 1e3;
-                const bool stop = bad || (int)hist[i].size() >= max_cycles || attempt_stalled(hist[i], pi.stall_ratio);
-                if (!control) {
-                    if (!std::isfinite(r[i]) && rc == MG_OK) rc = fail(MG_ERR_NAN, "non-finite residual");
-                    if ((int)hist[i].size() >= max_cycles) {
+        for (;;) {
+            bool any = true;
+            while (any && rc == MG_OK) {
+                CK(cudaGraphLaunch(exec, st));
+                CK(cudaStreamSynchronize(st));
+                any = false;
+                for (int i = 0; i < count; ++i) {
+                    if (!active[i]) continue;
+                    const double n2 = h_out[3 * i], n0 = h_out[3 * i + 1];
+                    ++cyc[i];
+                    s[i]->cycles_step = cyc[i];
+                    ++s[i]->cycles_total;
+                    s[i]->launches += nodes[i] + 1;
+                    r[i] = n0 > 0 ? std::sqrt(n2) / std::sqrt(n0) : std::sqrt(n2);   // as mg_vcycle
+                    s[i]->rho = r[i];
+                    const int err = (int)h_out[3 * i + 2];
+                    if ((err & 1) && rc == MG_OK) rc = fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
+                    if ((err & 4) && rc == MG_OK) {
+                        CK(cudaMemsetAsync(&s[i]->dsc->err, 0, sizeof(int), st));
+                        rc = fail(MG_ERR_TIMEOUT, "a tile copy into shared memory did not complete within the wait limit");
+                    }
+                    hist[i].push_back(r[i]);
+                    if (r[i] <= tol) { active[i] = 0; continue; }
+                    const mg_params &pi = s[i]->p;
+                    const bool control = pi.stall_ratio > 0;
+                    const bool bad = !std::isfinite(r[i]) || r[i] > 1e3;
+                    const bool capped = (int)hist[i].size() >= max_cycles;
+                    if (!control) {
+                        if (!std::isfinite(r[i]) && rc == MG_OK) rc = fail(MG_ERR_NAN, "non-finite residual");
+                        if (capped) failed[i] = 1;
+                    } else if (bad || capped || attempt_stalled(hist[i], pi.stall_ratio)) {
+                        if (halvings[i] >= pi.max_halvings) failed[i] = 1;
+                        else restart[i] = 1;
+                    }
+                    if (failed[i] || restart[i]) {
                         active[i] = 0;
-                        failed[i] = 1;
-                        CK(cudaMemsetAsync(&s[i]->dsc->halt, 1, sizeof(int), st));
+                        if (bad && failed[i] && rc == MG_OK && !(rc = s[i]->restart_step(pi.tau)))
+                            rc = s[i]->begin_step(nullptr);   // keep phi^n, not a diverged state
+                        CK(cudaMemsetAsync(&s[i]->dsc->halt, 1, sizeof(int), st));   // after any begin_step
                         continue;
                     }
-                } else if (stop) {
-                    if (halvings[i] >= pi.max_halvings) {
-                        active[i] = 0;
-                        failed[i] = 1;
-                        if (bad && rc == MG_OK && !(rc = s[i]->restart_step(pi.tau))) rc = s[i]->begin_step(nullptr);
-                        CK(cudaMemsetAsync(&s[i]->dsc->halt, 1, sizeof(int), st));
-                        continue;
-                    }
-                    ++halvings[i];
-                    hist[i].clear();
-                    if (rc == MG_OK) rc = s[i]->restart_step(0.5 * pi.tau);
-                    if (rc == MG_OK) rc = s[i]->begin_step(nullptr);
-                    rebuild = true;
+                    any = true;
                 }
-                any = any || active[i];
             }
-            if (rc || !any) break;
-            if (rebuild && (rc = build(tol))) break;
+            if (rc) break;
+            bool again = false;
+            for (int i = 0; i < count && rc == MG_OK; ++i) {
+                if (!restart[i]) continue;
+                restart[i] = 0;
+                ++halvings[i];
+                hist[i].clear();
+                if (!(rc = s[i]->restart_step(0.5 * s[i]->p.tau))) rc = s[i]->begin_step(nullptr);
+                active[i] = 1;
+                again = true;
+            }
+            if (rc || !again) break;
+            if ((rc = build(tol))) break;
         }
         if (cycles) for (int i = 0; i < count; ++i) cycles[i] = cyc[i];
         if (rho) for (int i = 0; i < count; ++i) rho[i] = r[i];
@@ -1537,6 +1629,9 @@ int mg_get_level(mg_handle h, int level, int field, void *out) {
     return (h && out) ? h->s->get_level(level, field, out) : fail(MG_ERR_ARG, "NULL argument");
 }
 int mg_get_stats(mg_handle h, mg_stats *s) { return (h && s) ? h->s->stats(s) : fail(MG_ERR_ARG, "NULL argument"); }
+int mg_set_snapshot_kernel(mg_handle h, int kind) {
+    return h ? h->s->set_snapshot_kernel(kind) : fail(MG_ERR_ARG, "NULL handle");
+}
 int mg_inject_divergence(mg_handle h, int cycle) {
     return h ? h->s->inject_divergence(cycle) : fail(MG_ERR_ARG, "NULL handle");
 }
@@ -1824,13 +1919,7 @@ int mg_batch_solve_step(mg_batch b, double tol, int max_cycles, int *cycles, dou
 
 int mg_batch_autotune(mg_batch b, int reps) {
     if (!b || reps < 1) return fail(MG_ERR_ARG, "NULL batch or reps < 1");
-    for (auto *x : b->b.s) {
-        int rc = x->begin_step(nullptr);
-        if (!rc) rc = x->autotune(reps, nullptr);
-        if (rc) return rc;
-    }
-    if (b->b.exec) { cudaGraphExecDestroy(b->b.exec); b->b.exec = nullptr; }
-    return MG_OK;
+    return b->b.autotune(reps);
 }
 
 mg_handle mg_batch_handle(mg_batch b, int i) {

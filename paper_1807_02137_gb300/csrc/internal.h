@@ -118,8 +118,9 @@ void launch_energy(const LevelView<T> &L, ModelParams mp, double *partials, int 
 int num_partials(int n, int m);
 
 // smooth_kernels.cu
+// kind: 0 by grid size, 1 shared-memory tiles, 2 register windows (same results)
 template <typename T>
-void launch_snapshot(const LevelView<T> &L, const double *area, cudaStream_t st);
+void launch_snapshot(const LevelView<T> &L, const double *area, int kind, cudaStream_t st);
 constexpr int kTileShapes = 6;   // fused-sweep tile shapes (rows x columns, threads): 32x64 256, 32x32 128,
                                  // 64x64 512, 32x64 512, 32x32 256, 32x32 512 (see smooth_kernels.cu)
 template <typename T>
