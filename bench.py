@@ -413,6 +413,11 @@ def run_profile_case(args):
     if args.tile_shape >= 0:
         s.set_tile_shapes([args.tile_shape] * (p.levels - 1))
     s.begin_step()
+    if args.autotune:        # the bench's kernel choices (tile shapes, bottom of the V-cycle)
+        s.autotune(reps=3)
+        s.end_step()
+        s.reset(torch.as_tensor(img, device="cuda"), mk)
+        s.begin_step()
     for _ in range(args.cycles):
         r = s.vcycle()
     print(json.dumps({"profile_case": N, "cycles": args.cycles, "rho": r, **s.stats()}), flush=True)
@@ -725,6 +730,7 @@ def main():
     ap.add_argument("--profile", type=int, default=0, help="run the N x N ncu profiling case instead")
     ap.add_argument("--cycles", type=int, default=2)
     ap.add_argument("--tile-shape", type=int, default=-1, help="profiling case: this tile shape on every grid")
+    ap.add_argument("--autotune", action="store_true", help="profiling case: mg_autotune first, as the bench")
     ap.add_argument("--config3", type=int, default=0, help="run the mixed-precision N x N report")
     ap.add_argument("--config4", type=int, default=0, help="run the batched report with this many images")
     ap.add_argument("--algorithms", type=int, default=0, help="compare Algorithms 1-3 on an N x N image")

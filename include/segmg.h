@@ -219,13 +219,6 @@ int mg_get_stats(mg_handle h, mg_stats *s);
  * counterpart.  Errors: MG_ERR_ARG (rounds < 0). */
 int mg_set_wait_limit(mg_handle h, long long rounds);
 
-/* Which kernel forms the coefficient snapshot (a tuning step of this implementation; the paper
- * has no counterpart): 1 = 32 x 32 tiles staged in shared memory (short critical path, for
- * small grids), 2 = one warp per tile walking down its rows with register windows (fewer
- * instructions per cell, for large HBM-bound grids), 0 = chosen per grid by its size (the
- * default).  All give bitwise the same results.  Errors: MG_ERR_ARG. */
-int mg_set_snapshot_kernel(mg_handle h, int kind);
-
 /* Host-side fault injection for tests of the error paths (no counterpart in the paper): the
  * `cycle`-th V-cycle (1-based, counted from the start of the current or next step attempt) run
  * after this call reports a residual ratio of 1e9, as a diverged V-cycle would; mg_vcycle then

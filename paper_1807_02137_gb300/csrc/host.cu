@@ -63,6 +63,25 @@ int fail(int code, const std::string &msg) {
         if (e_ != cudaSuccess) return fail(MG_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
     } while (0)
 
+// The end of one V-cycle of the device step loop: rho of the V-cycle (the same FP64 expression
+// as the host's), the step control's tests in the host's order, and the loop condition.
+__global__ void k_step_loop(cudaGraphConditionalHandle h, Scalars *sc, double tol, int max_cycles,
+                            double stall_ratio) {
+    const int j = sc->loop_j + 1;
+    sc->loop_j = j;
+    const double res0 = sqrt(sc->norm2_0);
+    const double rho = res0 > 0 ? sqrt(sc->norm2) / res0 : sqrt(sc->norm2);
+    sc->loop_rho[j] = rho;
+    int stop = 0;
+    if (sc->err != 0) stop = 5;
+    else if (!isfinite(rho) || rho > 1e3) stop = 4;
+    else if (rho <= tol) stop = 1;
+    else if (stall_ratio > 0 && j >= 4 && rho > stall_ratio * sc->loop_rho[j - 2]) stop = 2;
+    else if (j >= max_cycles) stop = 3;
+    sc->loop_stop = stop;
+    cudaGraphSetConditional(h, stop == 0 ? 1u : 0u);
+}
+
 __global__ void k_check_finite(const void *img, int is_double, size_t N, int *flag) {
     size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (; q < N; q += (size_t)gridDim.x * blockDim.x) {
@@ -144,7 +163,9 @@ struct SolverBase {
     virtual void set_cycles_step(int c) = 0;
     virtual int set_wait_limit(long long rounds) = 0;
     virtual int inject_divergence(int cycle) = 0;
-    virtual int set_snapshot_kernel(int kind) = 0;
+    // one attempt's V-cycles in one graph launch (the device step loop); MG_ERR_STATE when it
+    // does not apply (the caller then runs V-cycles one by one)
+    virtual int loop_attempt(double tol, int max_cycles, std::vector<double> &hist, int &stop) = 0;
 };
 
 template <typename T>
@@ -184,7 +205,6 @@ struct Solver final : SolverBase {
     double tau0 = 1.0;            // tau of the parameters (the step control halves p.tau)
     long long graph_epoch = 0;    // counts drop_graphs(): a batch rebuilds its graph when it changed
     long long wait_limit = kDefaultWaitLimit;   // try_wait rounds of the TMA sweep's bounded waits
-    int snap_kind = 0;            // mg_set_snapshot_kernel: 0 by grid size, 1 tiles, 2 register windows
     int inject_cycle = 0;         // mg_inject_divergence: V-cycle (of a step attempt) that reports
                                   // a diverged residual once; 0 = none
     bool in_step = false;
@@ -209,6 +229,10 @@ struct Solver final : SolverBase {
     T *ubak = nullptr;            // finest-grid increment saved before a learned V-cycle (and
                                   // while mg_autotune times V-cycles)
     cudaGraphExec_t gexec_l = nullptr, gexec_li = nullptr;   // learned V-cycle; with inference
+    cudaGraphExec_t gloop = nullptr;   // device step loop (while node around the V-cycle)
+    double gloop_tol = -1.0;
+    int gloop_max = -1;
+    long long gloop_nodes = 0;
     long long nodes_l = 0, nodes_li = 0;
     double plain_rate = -1.0;     // contraction of the last plain V-cycle of the step
     int learn_skip = 0, learn_backoff = 1;   // plain V-cycles left before the next learned try
@@ -223,7 +247,8 @@ struct Solver final : SolverBase {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (gexec_l) cudaGraphExecDestroy(gexec_l);
         if (gexec_li) cudaGraphExecDestroy(gexec_li);
-        gexec = gexec_l = gexec_li = nullptr;
+        if (gloop) cudaGraphExecDestroy(gloop);
+        gexec = gexec_l = gexec_li = gloop = nullptr;
     }
 
     void release() {
@@ -418,7 +443,7 @@ struct Solver final : SolverBase {
         int it = 0;
         while (it < max_iter) {
             area_term(0, lv[0].u);
-            launch_snapshot<T>(view(0), area_ptr(), snap_kind, st);
+            launch_snapshot<T>(view(0), area_ptr(), st);
             launch_aos_iteration<T>(view(0), area_ptr(), dt, partials, dsc->aos, st);
             launches += area_launches() + 4;
             ++it;
@@ -620,7 +645,7 @@ struct Solver final : SolverBase {
         Range range("smoothing iteration");
         area_term(l, lv[l].u);
         LevelView<T> v = view(l);
-        launch_snapshot<T>(v, area_ptr(), snap_kind, st);
+        launch_snapshot<T>(v, area_ptr(), st);
         if (use_omega && infer_pending[l] && omega_buf[l]) {
             launch_omega_infer<T>(v, net, omega_buf[l], st);   // weights from this snapshot's G
             infer_pending[l] = false;
@@ -722,7 +747,7 @@ struct Solver final : SolverBase {
                 auto enqueue = [&]() {
                     for (int r = 0; r < reps; ++r) {
                         area_term(l, L.u);
-                        launch_snapshot<T>(v, area_ptr(), snap_kind, st);
+                        launch_snapshot<T>(v, area_ptr(), st);
                         for (int k = 0; k < 4; ++k) sweep(l, v, k, sh);
                     }
                 };
@@ -1011,6 +1036,90 @@ struct Solver final : SolverBase {
     const mg_params &params() const override { return p; }
 
     // phi = phi^n again on the finest grid (the increment zeroed), nothing else changed
+    // The step loop graph: reset the loop counter, then a while node whose body is one V-cycle
+    // (captured) and k_step_loop, then the copy of the scalars to the host.
+    int build_loop(double tol, int max_cycles) {
+        if (gloop) { cudaGraphExecDestroy(gloop); gloop = nullptr; }
+        cudaGraph_t vg = nullptr, G = nullptr;
+        long long nodes = 0;
+        int rc = capture_vcycle(&vg, &nodes);
+        if (rc) return rc;
+        cudaError_t e = cudaGraphCreate(&G, 0);
+        cudaGraphNode_t ms = nullptr, wn = nullptr, child = nullptr, kn = nullptr, mc = nullptr;
+        if (e == cudaSuccess) {
+            cudaMemsetParams mp_{};
+            mp_.dst = &dsc->loop_j;
+            mp_.value = 0;
+            mp_.elementSize = sizeof(int);
+            mp_.width = 1;
+            mp_.height = 1;
+            e = cudaGraphAddMemsetNode(&ms, G, nullptr, 0, &mp_);
+        }
+        cudaGraphConditionalHandle hc{};
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, G, 1, cudaGraphCondAssignDefault);
+        cudaGraph_t body = nullptr;
+        if (e == cudaSuccess) {
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = hc;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&wn, G, &ms, nullptr, 1, &cp);
+            if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+        }
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, body, nullptr, 0, vg);
+        if (e == cudaSuccess) {
+            Scalars *sc = dsc;
+            double t = tol, sr = p.stall_ratio;
+            int mx = max_cycles;
+            void *args[] = {&hc, (void *)&sc, &t, &mx, &sr};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void *)k_step_loop;
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(1);
+            kp.kernelParams = args;
+            e = cudaGraphAddKernelNode(&kn, body, &child, 1, &kp);
+        }
+        if (e == cudaSuccess) e = cudaGraphAddMemcpyNode1D(&mc, G, &wn, 1, hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gloop, G, 0);
+        if (vg) cudaGraphDestroy(vg);
+        if (G) cudaGraphDestroy(G);
+        if (e != cudaSuccess) { gloop = nullptr; return fail(MG_ERR_CUDA, std::string("step loop graph: ") + cudaGetErrorString(e)); }
+        gloop_tol = tol;
+        gloop_max = max_cycles;
+        gloop_nodes = nodes;
+        return MG_OK;
+    }
+
+    int loop_attempt(double tol, int max_cycles, std::vector<double> &hist, int &stop) override {
+        // per-V-cycle host decisions (learned weights, injected faults) or no graphs: not here
+        if (!p.use_graph || learn_mode != 0 || inject_cycle > 0 || max_cycles > kLoopMaxCycles)
+            return MG_ERR_STATE;
+        if (!in_step) return fail(MG_ERR_STATE, "step loop outside a step");
+        if (!gloop || gloop_tol != tol || gloop_max != max_cycles) {
+            int rc = build_loop(tol, max_cycles);
+            if (rc) return rc;
+        }
+        CK(cudaGraphLaunch(gloop, st));
+        CK(cudaStreamSynchronize(st));
+        const int j = hsc->loop_j;
+        stop = hsc->loop_stop;
+        hist.assign(hsc->loop_rho + 1, hsc->loop_rho + 1 + j);
+        cycles_step += j;
+        cycles_total += j;
+        launches += (long long)j * (gloop_nodes + 1) + 1;
+        rho = j > 0 ? hist.back() : 1.0;
+        if (hsc->err & 1) return fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
+        if (hsc->err & 4) {
+            CK(cudaMemsetAsync(&dsc->err, 0, sizeof(int), st));
+            CK(cudaStreamSynchronize(st));
+            return fail(MG_ERR_TIMEOUT, "a tile copy into shared memory did not complete within the wait limit");
+        }
+        if (stop == 4) return std::isfinite(rho) ? fail(MG_ERR_DIVERGED, "residual grew by more than 1e3")
+                                                 : fail(MG_ERR_NAN, "non-finite residual");
+        return MG_OK;
+    }
+
     int zero_increment() {
         Level<T> &F = lv[0];
         CK(cudaMemset2DAsync(F.u, (size_t)F.pitch * sizeof(T), 0, (size_t)F.m * sizeof(T), F.n, st));
@@ -1020,13 +1129,6 @@ struct Solver final : SolverBase {
     int inject_divergence(int cycle) override {
         if (cycle < 0) return fail(MG_ERR_ARG, "cycle < 0");
         inject_cycle = cycle;
-        return MG_OK;
-    }
-
-    int set_snapshot_kernel(int kind) override {
-        if (kind < 0 || kind > 2) return fail(MG_ERR_ARG, "snapshot kernel kind must be 0, 1 or 2");
-        snap_kind = kind;
-        drop_graphs();
         return MG_OK;
     }
 
@@ -1143,7 +1245,7 @@ struct Solver final : SolverBase {
         for (int r = 0; r < reps; ++r) {
             area_term(l, lv[l].u);
             cudaEventRecord(ev[0], st);
-            launch_snapshot<T>(v, area_ptr(), snap_kind, st);
+            launch_snapshot<T>(v, area_ptr(), st);
             cudaEventRecord(ev[1], st);
             if (p.smoother == MG_SMOOTH_GSLINE || p.smoother == MG_SMOOTH_HS1) {
                 relax(l, v, shape[l]);        // the whole smoother in the first slot
@@ -1223,21 +1325,41 @@ int solve_step_controlled(SolverBase *s, double tol, int max_cycles, int *cycles
         if ((rc = s->begin_step(nullptr))) return rc;
         std::vector<double> hist;
         bool bad = false;   // diverged or non-finite: the state is not kept
-        for (int j = 1; j <= max_cycles; ++j) {
-            const auto t0 = std::chrono::steady_clock::now();
-            rc = s->vcycle(&r);
-            ++total;
-            log_cycle(st0.steps, attempt, j, r, s->params().tau,
-                      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+        // the attempt's V-cycles in one graph launch, the step control's tests on the device ...
+        int stop = 0;
+        const auto t0 = std::chrono::steady_clock::now();
+        rc = s->loop_attempt(tol, max_cycles, hist, stop);
+        if (rc != MG_ERR_STATE || !hist.empty()) {
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            for (size_t k = 0; k < hist.size(); ++k)
+                log_cycle(st0.steps, attempt, (int)k + 1, hist[k], s->params().tau, ms / (double)hist.size());
+            total += (int)hist.size();
+            if (!hist.empty()) r = hist.back();
             if (rc == MG_ERR_DIVERGED || rc == MG_ERR_NAN) {
                 if (!control) return rc;
                 bad = true;
-                break;
+            } else if (rc) {
+                return rc;
             }
-            if (rc) return rc;
-            hist.push_back(r);
-            if (r <= tol) { ok = true; break; }
-            if (control && attempt_stalled(hist, s->params().stall_ratio)) break;
+            ok = stop == 1;   // (without the step control the loop ends only at tol or the cap)
+        } else {
+            // ... or one V-cycle per launch with the tests on the host
+            for (int j = 1; j <= max_cycles; ++j) {
+                const auto t1 = std::chrono::steady_clock::now();
+                rc = s->vcycle(&r);
+                ++total;
+                log_cycle(st0.steps, attempt, j, r, s->params().tau,
+                          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count());
+                if (rc == MG_ERR_DIVERGED || rc == MG_ERR_NAN) {
+                    if (!control) return rc;
+                    bad = true;
+                    break;
+                }
+                if (rc) return rc;
+                hist.push_back(r);
+                if (r <= tol) { ok = true; break; }
+                if (control && attempt_stalled(hist, s->params().stall_ratio)) break;
+            }
         }
         if (ok || !control) break;
         const double tau = s->params().tau;
@@ -1629,9 +1751,6 @@ int mg_get_level(mg_handle h, int level, int field, void *out) {
     return (h && out) ? h->s->get_level(level, field, out) : fail(MG_ERR_ARG, "NULL argument");
 }
 int mg_get_stats(mg_handle h, mg_stats *s) { return (h && s) ? h->s->stats(s) : fail(MG_ERR_ARG, "NULL argument"); }
-int mg_set_snapshot_kernel(mg_handle h, int kind) {
-    return h ? h->s->set_snapshot_kernel(kind) : fail(MG_ERR_ARG, "NULL handle");
-}
 int mg_inject_divergence(mg_handle h, int cycle) {
     return h ? h->s->inject_divergence(cycle) : fail(MG_ERR_ARG, "NULL handle");
 }

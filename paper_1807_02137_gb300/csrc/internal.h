@@ -19,6 +19,7 @@ constexpr int kChunk = 32;        // partial-line groups are cut at multiples of
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarseCells = 4096;
 constexpr int kMaxCoarseBand = 64;
+constexpr int kLoopMaxCycles = 128;   // cycle cap of an attempt run by the device step loop
 
 // Partial-line group membership is stored as one 32-bit mask per 32-cell piece of a line:
 // mrow[(k * n + i) * npm + (j >> 5)] bit (j & 31) for sweeps A (k = 0) and B (k = 1) along row
@@ -61,6 +62,11 @@ struct Scalars {
     int err;                 // 1 = non-positive Cholesky pivot
     int halt;                // nonzero: a batch skips this image's V-cycles (set by the host when
                              // the image gives up a step; cleared by every step's start)
+    // the step loop on the device (one graph launch runs an attempt's V-cycles): V-cycles run,
+    // why the loop ended (1 tolerance, 2 stalled, 3 cycle cap, 4 diverged or non-finite, 5 an
+    // error bit), and rho after each V-cycle (1-based)
+    int loop_j, loop_stop;
+    double loop_rho[kLoopMaxCycles + 1];
 };
 
 struct ModelParams {
@@ -118,9 +124,8 @@ void launch_energy(const LevelView<T> &L, ModelParams mp, double *partials, int 
 int num_partials(int n, int m);
 
 // smooth_kernels.cu
-// kind: 0 by grid size, 1 shared-memory tiles, 2 register windows (same results)
 template <typename T>
-void launch_snapshot(const LevelView<T> &L, const double *area, int kind, cudaStream_t st);
+void launch_snapshot(const LevelView<T> &L, const double *area, cudaStream_t st);
 constexpr int kTileShapes = 6;   // fused-sweep tile shapes (rows x columns, threads): 32x64 256, 32x32 128,
                                  // 64x64 512, 32x64 512, 32x32 256, 32x32 512 (see smooth_kernels.cu)
 template <typename T>

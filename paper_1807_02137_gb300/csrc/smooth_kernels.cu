@@ -142,146 +142,6 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_snapshot(LevelView<T> L, c
 }
 
 // ---------------------------------------------------------------------------------------
-// Snapshot for large grids, without shared memory: one warp per 32 x 32 tile, lane = column,
-// walking down the rows with the values it needs in registers, each loaded one step ahead:
-// at row r, pn of rows r-1 .. r+2, u of rows r .. r+2, w of row r+1, F and the FAS right-hand
-// side of row r, G of rows r-1 .. r+1; the values of the neighbouring columns come from the
-// neighbouring lanes by shuffles.  The columns just outside the tile, j0 - 1 and j0 + 32 (the
-// "ring"), are held by lanes 0 and 31, with the column beyond each (j0 - 2, j0 + 33) for the
-// ring's own G.  The row pieces (sweeps A, B) of a tile row are the warp's 32 lanes (one ballot
-// each); the column pieces (sweeps C, D) are collected bit by bit in each lane on the way down.
-// Every value is formed with the same operations, on the same (mirror-clamped) operands, as in
-// k_snapshot: G, f, the member masks and the class bytes are bitwise those of k_snapshot.
-// ---------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_snapshot_rw(LevelView<T> L, const double *area) {
-    constexpr unsigned kFull = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int n = L.n, m = L.m, p = L.pitch;
-    const int ntx = (m + 31) >> 5, nty = (n + 31) >> 5;
-    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (tile >= ntx * nty) return;   // the whole warp leaves
-    const int ty = tile / ntx, tx = tile - ty * ntx;
-    const int i0 = ty * 32, j0 = tx * 32;
-    const int j = j0 + lane, jc = min(j, m - 1);
-    const bool ring = lane == 0 || lane == 31;
-    const int jr = lane == 0 ? j0 - 1 : j0 + 32;            // ring column of lanes 0 / 31
-    const bool r_in = ring && jr >= 0 && jr < m;
-    const int jrc = min(max(jr, 0), m - 1);
-    const int jo = lane == 0 ? max(j0 - 2, 0) : min(j0 + 33, m - 1);
-    const bool hE = j + 1 < m, hW = j > 0;
-    const T *__restrict__ pn = L.pn;
-    const T *__restrict__ uu = L.u;
-    const T *__restrict__ Fp = L.F;
-    const T *__restrict__ Rp = L.has_rhs ? L.rhs : nullptr;
-    auto rowo = [&](int r) { return (size_t)min(max(r, 0), n - 1) * p; };   // row r clamped (mirror)
-    auto wt = [&](size_t o) { return L.wb ? T(__bfloat162float(__ldg(L.wb + o))) : __ldg(L.w + o); };
-    // the value of column j + 1 (j - 1) in the same row: the lane's own value where the grid
-    // ends (mirror), the ring value on lane 31 (0); every lane takes part in the shuffle
-    auto east = [&](T own, T ringv) {
-        const T s = __shfl_down_sync(kFull, own, 1);
-        return hE ? (lane < 31 ? s : ringv) : own;
-    };
-    auto west = [&](T own, T ringv) {
-        const T s = __shfl_up_sync(kFull, own, 1);
-        return hW ? (lane > 0 ? s : ringv) : own;
-    };
-    const T ar = area ? T(area[L.level]) : T(0);
-    const int lenr = min(32, m - j0), lenc = min(32, n - i0);
-    const int iend = min(i0 + 32, n);
-    // queues at the first step r = i0 - 2 (suffix = row offset from r: m1 = r - 1, 0 = r, ...)
-    T pm1, p0, p1, p2, u0, u1, u2, w1, F0 = T(0), R0 = T(0);
-    T rp0 = T(0), rp1 = T(0), rp2 = T(0), ru0 = T(0), ru1 = T(0), ru2 = T(0), rw1 = T(0), op1 = T(0), ou1 = T(0);
-    {
-        const int r = i0 - 2;
-        const size_t om1 = rowo(r - 1), o0 = rowo(r), o1 = rowo(r + 1), o2 = rowo(r + 2);
-        pm1 = __ldg(pn + om1 + jc);
-        p0 = __ldg(pn + o0 + jc); p1 = __ldg(pn + o1 + jc); p2 = __ldg(pn + o2 + jc);
-        u0 = __ldg(uu + o0 + jc); u1 = __ldg(uu + o1 + jc); u2 = __ldg(uu + o2 + jc);
-        w1 = wt(o1 + jc);
-        if (ring) {
-            rp0 = __ldg(pn + o0 + jrc); rp1 = __ldg(pn + o1 + jrc); rp2 = __ldg(pn + o2 + jrc);
-            ru0 = __ldg(uu + o0 + jrc); ru1 = __ldg(uu + o1 + jrc); ru2 = __ldg(uu + o2 + jrc);
-            rw1 = wt(o1 + jrc);
-            op1 = __ldg(pn + o1 + jo); ou1 = __ldg(uu + o1 + jo);
-        }
-    }
-    T Gm = T(0), Gc = T(0), rGc = T(0);
-    uint32_t colC = 0, colD = 0;
-    for (int r = i0 - 2; r < iend; ++r) {
-        // loads for the next step: pn, u of row r+3; w of row r+2; F, rhs of row r+1
-        const size_t o3 = rowo(r + 3), o2 = rowo(r + 2), o1 = rowo(r + 1);
-        const T p3 = __ldg(pn + o3 + jc), u3 = __ldg(uu + o3 + jc), w2 = wt(o2 + jc);
-        const T F1 = __ldg(Fp + o1 + jc), R1 = Rp ? __ldg(Rp + o1 + jc) : T(0);
-        T rp3 = T(0), ru3 = T(0), rw2 = T(0), op2 = T(0), ou2 = T(0);
-        if (ring) {
-            rp3 = __ldg(pn + o3 + jrc); ru3 = __ldg(uu + o3 + jrc); rw2 = wt(o2 + jrc);
-            op2 = __ldg(pn + o2 + jo); ou2 = __ldg(uu + o2 + jo);
-        }
-        // G of row r + 1 from rows r .. r + 2 (zero outside the grid)
-        const int g1 = r + 1;
-        const T pE = east(p1, rp1), pW = west(p1, rp1);
-        const T uE = east(u1, ru1), uW = west(u1, ru1);
-        T Gp = T(0), rGp = T(0);
-        if (g1 >= 0 && g1 < n) {
-            if (j < m) Gp = cell_G(w1, p2, p0, pE, pW, u2, u0, uE, uW, L.inv_2h, L.beta);
-            if (r_in) {   // lanes 0 / 31: the ring cell; its row neighbours are the tile's edge column and jo
-                const T rE = lane == 0 ? p1 : (jr + 1 < m ? op1 : rp1);
-                const T rW = lane == 0 ? (jr > 0 ? op1 : rp1) : p1;
-                const T qE = lane == 0 ? u1 : (jr + 1 < m ? ou1 : ru1);
-                const T qW = lane == 0 ? (jr > 0 ? ou1 : ru1) : u1;
-                rGp = cell_G(rw1, rp2, rp0, rE, rW, ru2, ru0, qE, qW, L.inv_2h, L.beta);
-            }
-        }
-        if (r >= i0) {   // the cells of row i = r (pn of rows i-1, i, i+1: pm1, p0, p1)
-            const int i = r;
-            const T gE = east(Gc, rGc), gW = west(Gc, rGc);
-            const T cE = east(p0, rp0), cW = west(p0, rp0);
-            uint8_t star = 0;
-            if (j < m) {
-                const bool hS = i + 1 < n, hN = i > 0;
-                const T gc = Gc;
-                const T aS = face(gc, Gp, hS), aN = face(gc, Gm, hN);
-                const T aE = face(gc, gE, hE), aW = face(gc, gW, hW);
-                const T pc = p0;
-                T ds = mul_rn(aS, sub_rn(p1, pc));
-                ds = fma_rn(aN, sub_rn(pm1, pc), ds);
-                ds = fma_rn(aE, sub_rn(cE, pc), ds);
-                ds = fma_rn(aW, sub_rn(cW, pc), ds);
-                T base = add_rn(F0, ar);
-                if (L.has_rhs) base = add_rn(base, R0);
-                const size_t o = (size_t)i * p + j;
-                L.f[o] = fma_rn(-L.cdiff, ds, base);
-                L.G[o] = gc;
-                const T big = T(3.0e38);
-                const T vS = hS ? aS : big, vN = hN ? aN : big, vE = hE ? aE : big, vW = hW ? aW : big;
-                const T mn = fmin(fmin(vS, vN), fmin(vE, vW));
-                const T mx = fmax(fmax(hS ? aS : T(-1), hN ? aN : T(-1)), fmax(hE ? aE : T(-1), hW ? aW : T(-1)));
-                const int am = vS == mn ? 0 : (vN == mn ? 1 : (vE == mn ? 2 : 3));
-                const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
-                if (cnt >= 2 && mx > mul_rn(L.Sigma, mn)) star = (uint8_t)(1u << am);
-                if (L.cls) L.cls[o] = star;
-            }
-            const uint32_t bA = __ballot_sync(kFull, star & 1u), bB = __ballot_sync(kFull, star & 2u);
-            if (lane < 2) L.mrow[((size_t)lane * n + i) * L.npm + tx] = members_of(lane ? bB : bA, lenr);
-            colC |= (uint32_t)((star >> 2) & 1u) << (i - i0);
-            colD |= (uint32_t)((star >> 3) & 1u) << (i - i0);
-        }
-        Gm = Gc; Gc = Gp; rGc = rGp;
-        pm1 = p0; p0 = p1; p1 = p2; p2 = p3;
-        u0 = u1; u1 = u2; u2 = u3;
-        w1 = w2; F0 = F1; R0 = R1;
-        rp0 = rp1; rp1 = rp2; rp2 = rp3;
-        ru0 = ru1; ru1 = ru2; ru2 = ru3;
-        rw1 = rw2; op1 = op2; ou1 = ou2;
-    }
-    if (j < m) {
-        L.mcol[((size_t)0 * m + j) * L.npn + ty] = members_of(colC, lenc);
-        L.mcol[((size_t)1 * m + j) * L.npn + ty] = members_of(colD, lenc);
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // Phased path
 // ---------------------------------------------------------------------------------------
 template <typename T>
@@ -557,19 +417,13 @@ const SnapOcc<T> &snap_occ() {
     return o;
 }
 
-// kind 1: shared-memory tiles with the most threads per tile with which every tile of the grid
-// still gets a resident block; kind 2: register windows (k_snapshot_rw); kind 0: register
-// windows once the tiles fill more than two waves of 8-warp tile blocks, else kind 1.  Every
-// kind gives bitwise the same G, f and masks.
+// The most threads per tile with which every tile of the grid still gets a resident block.
 template <typename T>
-void launch_snapshot(const LevelView<T> &L, const double *area, int kind, cudaStream_t st) {
+void launch_snapshot(const LevelView<T> &L, const double *area, cudaStream_t st) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
     const long tiles = (long)grid.x * grid.y;
     const SnapOcc<T> &o = snap_occ<T>();
-    if (kind == 0) kind = tiles > 2L * o.sms * o.per_sm[0] ? 2 : 1;
-    if (kind == 2)
-        k_snapshot_rw<T><<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(L, area);
-    else if (tiles <= (long)o.sms * o.per_sm[2])
+    if (tiles <= (long)o.sms * o.per_sm[2])
         k_snapshot<T, 32><<<grid, dim3(32, 32), 0, st>>>(L, area);
     else if (tiles <= (long)o.sms * o.per_sm[1])
         k_snapshot<T, 16><<<grid, dim3(32, 16), 0, st>>>(L, area);
@@ -648,8 +502,8 @@ void launch_sweep_fused(const LevelView<T> &L, int sweep, int shape, cudaStream_
     else launch_fused_shape<T, Tile0>(L, sweep, st);
 }
 
-template void launch_snapshot<float>(const LevelView<float> &, const double *, int, cudaStream_t);
-template void launch_snapshot<double>(const LevelView<double> &, const double *, int, cudaStream_t);
+template void launch_snapshot<float>(const LevelView<float> &, const double *, cudaStream_t);
+template void launch_snapshot<double>(const LevelView<double> &, const double *, cudaStream_t);
 template void launch_sweep_phased<float>(const LevelView<float> &, int, cudaStream_t);
 template void launch_sweep_phased<double>(const LevelView<double> &, int, cudaStream_t);
 template void launch_sweep_fused<float>(const LevelView<float> &, int, int, cudaStream_t);

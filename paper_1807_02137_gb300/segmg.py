@@ -22,7 +22,7 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
           -5: "MG_ERR_TIMEOUT", -6: "MG_ERR_NOT_SPD", -7: "MG_ERR_NOMEM", -8: "MG_ERR_STATE"}
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
-           "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_inject_divergence", "mg_set_snapshot_kernel", "mg_segment_host", "mg_get_stream", "mg_destroy",
+           "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_inject_divergence", "mg_segment_host", "mg_get_stream", "mg_destroy",
            "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_set_cluster_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
            "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_grad",
            "mg_trainer_train", "mg_trainer_get", "mg_trainer_destroy",
@@ -98,7 +98,6 @@ def lib():
             "mg_get_stats": ([vp, C.POINTER(Stats)], i),
             "mg_set_wait_limit": ([vp, C.c_longlong], i),
             "mg_inject_divergence": ([vp, i], i),
-            "mg_set_snapshot_kernel": ([vp, i], i),
             "mg_segment_host": ([vp, i, i, D, i, P, d, i, d, i, vp, vp, C.POINTER(Stats)], i),
             "mg_get_stream": ([vp], vp),
             "mg_time_kernels": ([vp, i, i, D], i),
@@ -345,10 +344,6 @@ class Solver:
     def set_wait_limit(self, rounds):
         """Bound of the fused sweep's device-side waits (mg_set_wait_limit); 0 gives up at once."""
         _check(lib().mg_set_wait_limit(self._h, int(rounds)), "mg_set_wait_limit")
-
-    def set_snapshot_kernel(self, kind):
-        """mg_set_snapshot_kernel: 0 by grid size, 1 shared-memory tiles, 2 register windows."""
-        _check(lib().mg_set_snapshot_kernel(self._h, int(kind)), "mg_set_snapshot_kernel")
 
     def inject_divergence(self, cycle):
         """mg_inject_divergence: the cycle-th V-cycle from now reports a diverged residual once."""

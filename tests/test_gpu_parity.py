@@ -666,31 +666,3 @@ def test_checkpoint_and_resume_at_a_step_boundary_is_bitwise(segmg):
     sa, sc = a.stats(), c.stats()
     assert (sa["c1"], sa["c2"], sa["tau"]) == (sc["c1"], sc["c2"], sc["tau"])
     a.close(); c.close()
-
-
-@pytest.mark.parametrize("shape", [(1000, 1234), (300, 173), (64, 64), (33, 65), (7, 130)])
-@pytest.mark.parametrize("case", ["f32", "mixed", "f64_rc", "f32_hs1"])
-def test_snapshot_kernels_are_bitwise_equal(segmg, shape, case):
-    # the register-window snapshot (one warp per tile walking down its rows) and the shared-memory
-    # tile snapshot form G, f, the member masks and the class bytes with the same operations:
-    # every V-cycle gives bitwise the same phi and residual
-    n, m = shape
-    img, mk, _ = synth.ellipses(n, m, 8, (4, max(6, min(n, m) / 2)), 5, 0.05, 70 + n)
-    kw = {"f32": dict(precision=segmg.MG_F32), "mixed": dict(precision=segmg.MG_MIXED),
-          "f64_rc": dict(precision=segmg.MG_F64, model=segmg.MG_MODEL_RC),
-          "f32_hs1": dict(precision=segmg.MG_F32, smoother=segmg.MG_SMOOTH_HS1)}[case]
-    if kw["precision"] != segmg.MG_F64:
-        img = img.astype(np.float32)
-    outs = []
-    for kind in (1, 2):
-        s, p = gpu_solver(segmg, img, mk, **kw)
-        if kw["precision"] != segmg.MG_F64 and "smoother" not in kw:
-            s.set_bottom_kernel(False)    # every grid through the per-grid kernels
-        s.set_snapshot_kernel(kind)
-        s.begin_step()
-        rhos = [s.vcycle() for _ in range(2)]
-        outs.append((s.phi().cpu().numpy(), rhos, s.level(0, "G").cpu().numpy()))
-        s.close()
-    assert np.array_equal(outs[0][0], outs[1][0])
-    assert outs[0][1] == outs[1][1]
-    assert np.array_equal(outs[0][2], outs[1][2])
