@@ -277,19 +277,19 @@ __device__ void b_residual(const BGrid &B, const float *uu, float *out, int mode
     __syncthreads();
 }
 
-__device__ __forceinline__ int fw(int I, int n, int *idx, double *wt) {
+__device__ __forceinline__ int fw(int I, int n, int *idx, float *wt) {
     const int q = 2 * I + 1;
-    if (q + 1 < n) { idx[0] = q - 1; idx[1] = q; idx[2] = q + 1; wt[0] = 0.25; wt[1] = 0.5; wt[2] = 0.25; return 3; }
-    idx[0] = q - 1; idx[1] = q; wt[0] = 0.5; wt[1] = 0.5;
+    if (q + 1 < n) { idx[0] = q - 1; idx[1] = q; idx[2] = q + 1; wt[0] = 0.25f; wt[1] = 0.5f; wt[2] = 0.25f; return 3; }
+    idx[0] = q - 1; idx[1] = q; wt[0] = 0.5f; wt[1] = 0.5f;
     return 2;
 }
 
-__device__ __forceinline__ int bl(int p, int nc, int *idx, double *wt) {
-    if (p & 1) { idx[0] = (p - 1) / 2; wt[0] = 1.0; return 1; }
-    if (p == 0) { idx[0] = 0; wt[0] = 1.0; return 1; }
+__device__ __forceinline__ int bl(int p, int nc, int *idx, float *wt) {
+    if (p & 1) { idx[0] = (p - 1) / 2; wt[0] = 1.0f; return 1; }
+    if (p == 0) { idx[0] = 0; wt[0] = 1.0f; return 1; }
     const int I = p / 2 - 1;
-    if (I + 1 < nc) { idx[0] = I; idx[1] = I + 1; wt[0] = 0.5; wt[1] = 0.5; return 2; }
-    idx[0] = I; wt[0] = 1.0;
+    if (I + 1 < nc) { idx[0] = I; idx[1] = I + 1; wt[0] = 0.5f; wt[1] = 0.5f; return 2; }
+    idx[0] = I; wt[0] = 1.0f;
     return 1;
 }
 
@@ -298,7 +298,7 @@ __device__ void b_restrict(const BGrid &F, const float *src, const BGrid &C, flo
     const Map2 M = map_for(C.m);
     FOR_CELLS(M, C.n, C.m, I, J) {
         int ri[3], ci[3];
-        double rw[3], cw[3];
+        float rw[3], cw[3];
         const int nr = fw(I, F.n, ri, rw), nk = fw(J, F.m, ci, cw);
         float s = 0.f;
         for (int a = 0; a < nr; ++a) {
@@ -318,7 +318,7 @@ __device__ void b_interp_add(const BGrid &F, const BGrid &C) {
     const Map2 M = map_for(F.m);
     FOR_CELLS(M, F.n, F.m, i, j) {
         int ri[2], ci[2];
-        double rw[2], cw[2];
+        float rw[2], cw[2];
         const int nr = bl(i, C.n, ri, rw), nk = bl(j, C.m, ci, cw);
         float s = 0.f;
         for (int a = 0; a < nr; ++a)
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
         const Map2 M = map_for(C.m);
         FOR_CELLS(M, C.n, C.m, I, J) {
             int ri[3], ci[3];
-            double rw[3], cw[3];
+            float rw[3], cw[3];
             const int nr = fw(I, n, ri, rw), nk = fw(J, m, ci, cw);
             float sr = 0.f, su = 0.f;
             for (int a = 0; a < nr; ++a) {
@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
         const float *Cu = cl.map_shared_rank(C.u, 0), *Cu0 = cl.map_shared_rank(C.u0, 0);
         if (own) {
             int ri[2], ci[2];
-            double rw[2], cw[2];
+            float rw[2], cw[2];
             const int nr = bl(i, C.n, ri, rw), nk = bl(j, C.m, ci, cw);
             float sum = 0.f;
             for (int a = 0; a < nr; ++a)

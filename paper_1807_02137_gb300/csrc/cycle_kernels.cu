@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256, MINB)
     }
 }
 
-__device__ __forceinline__ int fw_taps(int I, int n, int *idx, double *wt);
+__device__ __forceinline__ int fw_taps(int I, int n, int *idx, float *wt);
 
 // Loads the window dst[a][b] = src[clamp(r0 + a)][clamp(c0 + b)], a < ROWS, b < COLS, of one or
 // two pitched FP32 grid functions (indices clamped into the grid: the mirror ghosts), with
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict(LevelView<float> L, L
         const int I = blockIdx.y * 16 + tid / 16, J = blockIdx.x * 16 + tid % 16;
         if (I < C.n && J < C.m) {
             int ri[3], ci[3];
-            double rw[3], cw[3];
+            float rw[3], cw[3];
             const int nr = fw_taps(I, n, ri, rw), nk = fw_taps(J, m, ci, cw);
             float sr = 0.f, su = 0.f;
             for (int a = 0; a < nr; ++a) {
@@ -215,15 +215,15 @@ __global__ void k_sum_partials(const double *partials, int np, double *out) {
 
 // One-dimensional full-weighting taps (Sec. 3.1): coarse I sits on fine 2I+1; (1/4, 1/2, 1/4)
 // on 2I, 2I+1, 2I+2, or (1/2, 1/2) on 2I, 2I+1 when fine 2I+2 does not exist.
-__device__ __forceinline__ int fw_taps(int I, int n, int *idx, double *wt) {
+__device__ __forceinline__ int fw_taps(int I, int n, int *idx, float *wt) {
     int q = 2 * I + 1;
     if (q + 1 < n) {
         idx[0] = q - 1; idx[1] = q; idx[2] = q + 1;
-        wt[0] = 0.25; wt[1] = 0.5; wt[2] = 0.25;
+        wt[0] = 0.25f; wt[1] = 0.5f; wt[2] = 0.25f;
         return 3;
     }
     idx[0] = q - 1; idx[1] = q;
-    wt[0] = 0.5; wt[1] = 0.5;
+    wt[0] = 0.5f; wt[1] = 0.5f;
     return 2;
 }
 
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) k_restrict(const T *f, int n, int m, int 
     const int nc = n / 2, mc = m / 2;
     if (I >= nc || J >= mc) return;
     int ri[3], ci[3];
-    double rw[3], cw[3];
+    float rw[3], cw[3];
     int nr = fw_taps(I, n, ri, rw), nk = fw_taps(J, m, ci, cw);
     T s = T(0);
     for (int a = 0; a < nr; ++a) {
@@ -247,12 +247,12 @@ __global__ void __launch_bounds__(256) k_restrict(const T *f, int n, int m, int 
 
 // One-dimensional bilinear taps (Sec. 3.1): fine 2I+1 takes coarse I; fine 2I+2 the mean of
 // coarse I and I+1; fine 0 (and fine n-1 for odd n) the single nearest coarse value.
-__device__ __forceinline__ int bl_taps(int p, int nc, int *idx, double *wt) {
-    if (p & 1) { idx[0] = (p - 1) / 2; wt[0] = 1.0; return 1; }
-    if (p == 0) { idx[0] = 0; wt[0] = 1.0; return 1; }
+__device__ __forceinline__ int bl_taps(int p, int nc, int *idx, float *wt) {
+    if (p & 1) { idx[0] = (p - 1) / 2; wt[0] = 1.0f; return 1; }
+    if (p == 0) { idx[0] = 0; wt[0] = 1.0f; return 1; }
     int I = p / 2 - 1;
-    if (I + 1 < nc) { idx[0] = I; idx[1] = I + 1; wt[0] = 0.5; wt[1] = 0.5; return 2; }
-    idx[0] = I; wt[0] = 1.0;
+    if (I + 1 < nc) { idx[0] = I; idx[1] = I + 1; wt[0] = 0.5f; wt[1] = 0.5f; return 2; }
+    idx[0] = I; wt[0] = 1.0f;
     return 1;
 }
 
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256) k_interp_add(LevelView<T> Lf, LevelView<T
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
     if (i >= Lf.n || j >= Lf.m) return;
     int ri[2], ci[2];
-    double rw[2], cw[2];
+    float rw[2], cw[2];
     int nr = bl_taps(i, Lc.n, ri, rw), nk = bl_taps(j, Lc.m, ci, cw);
     T s = T(0);
     for (int a = 0; a < nr; ++a)
