@@ -418,6 +418,10 @@ def run_profile_case(args):
         s.end_step()
         s.reset(torch.as_tensor(img, device="cuda"), mk)
         s.begin_step()
+    if args.shapes:          # or given explicitly (as a bench line reports them)
+        s.set_tile_shapes([int(x) for x in args.shapes.split(",")])
+    if args.cluster_level is not None:
+        s.set_cluster_level(args.cluster_level)
     for _ in range(args.cycles):
         r = s.vcycle()
     print(json.dumps({"profile_case": N, "cycles": args.cycles, "rho": r, **s.stats()}), flush=True)
@@ -731,6 +735,8 @@ def main():
     ap.add_argument("--cycles", type=int, default=2)
     ap.add_argument("--tile-shape", type=int, default=-1, help="profiling case: this tile shape on every grid")
     ap.add_argument("--autotune", action="store_true", help="profiling case: mg_autotune first, as the bench")
+    ap.add_argument("--shapes", default="", help="profiling case: tile shape per grid, comma-separated")
+    ap.add_argument("--cluster-level", type=int, default=None, help="profiling case: first grid of the cluster bottom")
     ap.add_argument("--config3", type=int, default=0, help="run the mixed-precision N x N report")
     ap.add_argument("--config4", type=int, default=0, help="run the batched report with this many images")
     ap.add_argument("--algorithms", type=int, default=0, help="compare Algorithms 1-3 on an N x N image")
