@@ -44,7 +44,8 @@ def peaks():
 
 
 class Clocks:
-    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+    """Samples nvidia-smi SM clocks and throttle reasons while running (a reader thread stamps
+    each sample with the host time, so summary() can keep the samples after mark())."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -53,27 +54,41 @@ class Clocks:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.p = None
+        self.rows = []
+        self.t_mark = None
 
     def __enter__(self):
+        import threading
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+        if self.p:
+            def read():
+                for line in self.p.stdout:
+                    self.rows.append((time.time(), line))
+            self.th = threading.Thread(target=read, daemon=True)
+            self.th.start()
         return self
 
+    def mark(self):
+        """Samples from here on only (the sampler keeps running)."""
+        self.t_mark = time.time()
+
     def __exit__(self, *a):
-        self.out = ""
         if self.p:
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
+                self.th.join(timeout=5)
             except Exception:
                 self.p.kill()
 
     def summary(self):
-        rows = [r.split(",") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 8]
+        rows = [r.split(",") for t, r in self.rows
+                if r.count(",") >= 8 and (self.t_mark is None or t >= self.t_mark)]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm = [float(r[1]) for r in rows]
@@ -248,6 +263,8 @@ def run_ours(args):
         s.mask(out=mask)
         return c, r
 
+    # the clock sampler starts before the warm-up: its start-up (NVML) is outside the timed steps
+    clk = Clocks(lrank).__enter__()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -256,7 +273,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     times, cycles, rhos = [], [], []
     l0 = s.stats()["launches"]
-    with Clocks(lrank) as clk:
+    clk.mark()
+    try:
         t_wall = time.perf_counter()
         for _ in range(args.steps):
             with torch.cuda.stream(st):
@@ -271,6 +289,8 @@ def run_ours(args):
             rhos.append(r)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+    finally:
+        clk.__exit__(None, None, None)
     launches = s.stats()["launches"] - l0
     if dist:
         dist.barrier()
