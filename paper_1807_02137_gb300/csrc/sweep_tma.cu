@@ -158,11 +158,50 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
     const int tid = threadIdx.x;
     const int ntx = (m + kOW - 1) / kOW, ntiles = ntx * ((n + kOH - 1) / kOH);
     float *uout = (SWEEP & 1) ? L.u : L.t;   // ping-pong (see k_sweep)
-    if (tid == 0) {
-        for (int k = 0; k < STAGES; ++k) mbar_init(&S.bar[k], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
+    // the member masks of every line piece that touches a tile's box (zero outside the grid):
+    // loaded into registers ahead of use (the first tile's before the block's set-up, the next
+    // tile's while a tile is smoothed), stored to shared memory when the tile starts
+    constexpr int kMaskWords = rowwise ? kRH * kRowPieces : kRW * kColPieces;
+    constexpr int kMaskPer = (kMaskWords + TS::NT - 1) / TS::NT;
+    auto load_masks = [&](int t, uint32_t (&w)[kMaskPer]) {
+        const int ty = t / ntx, tx = t - ty * ntx;
+        const int i0 = ty * kOH, j0 = tx * kOW;
+#pragma unroll
+        for (int r = 0; r < kMaskPer; ++r) {
+            const int q = tid + r * TS::NT;
+            w[r] = 0;
+            if (q >= kMaskWords || t >= ntiles) continue;
+            if (rowwise) {
+                const int a = q / kRowPieces, pc = q % kRowPieces;
+                const int gi = i0 - kH + a, piece = (j0 >> 5) - 1 + pc;
+                if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm)
+                    w[r] = __ldg(L.mrow + ((size_t)SWEEP * n + gi) * L.npm + piece);
+            } else {
+                const int b = q / kColPieces, pc = q % kColPieces;
+                const int gj = j0 - kH + b, piece = (i0 >> 5) - 1 + pc;
+                if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn)
+                    w[r] = __ldg(L.mcol + ((size_t)(SWEEP - 2) * m + gj) * L.npn + piece);
+            }
+        }
+    };
+    auto store_masks = [&](const uint32_t (&w)[kMaskPer]) {   // true: a piece the line phases solve has a member
+        bool lm = false;
+#pragma unroll
+        for (int r = 0; r < kMaskPer; ++r) {
+            const int q = tid + r * TS::NT;
+            if (q >= kMaskWords) continue;
+            if (rowwise) {
+                const int a = q / kRowPieces, pc = q % kRowPieces;
+                S.mk[a][pc] = w[r];
+                lm |= solves_word<kH, kOH, kOW, true>(a, pc, w[r]);
+            } else {
+                const int b = q / kColPieces, pc = q % kColPieces;
+                S.mk[b][pc] = w[r];
+                lm |= solves_word<kH, kOH, kOW, false>(b, pc, w[r]);
+            }
+        }
+        return lm;
+    };
     auto issue = [&](int tile, int stage) {   // one thread
         const int ty = tile / ntx, tx = tile - ty * ntx;
         const int x = tx * kOW - kH, y = ty * kOH - kH;
@@ -173,7 +212,14 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
         tma_load(&S.box[stage][2][0][0], &tf, x, y, &S.bar[stage]);
     };
     int tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles) issue(tile, 0);
+    uint32_t mw[kMaskPer];
+    load_masks(tile, mw);
+    if (tid == 0) {   // the thread that initialises the barriers issues the first tile's copies
+        for (int k = 0; k < STAGES; ++k) mbar_init(&S.bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        if (tile < ntiles) issue(tile, 0);
+    }
+    __syncthreads();
     for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
         const int st = STAGES == 2 ? (k & 1) : 0;
         const unsigned parity = STAGES == 2 ? (unsigned)((k >> 1) & 1) : (unsigned)(k & 1);
@@ -181,29 +227,8 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
         if (STAGES == 2 && tid == 0 && next < ntiles) issue(next, st ^ 1);
         const int ty = tile / ntx, tx = tile - ty * ntx;
         const int i0 = ty * kOH, j0 = tx * kOW;
-        // member masks of every line piece that touches the box (zero outside the grid)
-        bool lm = false;   // a piece the line phases solve has a member
-        if (rowwise) {
-            for (int q = tid; q < kRH * kRowPieces; q += TS::NT) {
-                const int a = q / kRowPieces, pc = q % kRowPieces;
-                const int gi = i0 - kH + a, piece = (j0 >> 5) - 1 + pc;
-                uint32_t w = 0;
-                if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm)
-                    w = __ldg(L.mrow + ((size_t)SWEEP * n + gi) * L.npm + piece);
-                S.mk[a][pc] = w;
-                lm |= solves_word<kH, kOH, kOW, true>(a, pc, w);
-            }
-        } else {
-            for (int q = tid; q < kRW * kColPieces; q += TS::NT) {
-                const int b = q / kColPieces, pc = q % kColPieces;
-                const int gj = j0 - kH + b, piece = (i0 >> 5) - 1 + pc;
-                uint32_t w = 0;
-                if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn)
-                    w = __ldg(L.mcol + ((size_t)(SWEEP - 2) * m + gj) * L.npn + piece);
-                S.mk[b][pc] = w;
-                lm |= solves_word<kH, kOH, kOW, false>(b, pc, w);
-            }
-        }
+        const bool lm = store_masks(mw);
+        load_masks(next, mw);   // in flight while this tile is smoothed (zeros past the last tile)
         const bool ok = mbar_wait(&S.bar[st], parity, wait_limit);
         if (__syncthreads_or(!ok)) {
             // a copy did not complete within wait_limit rounds: report, give the copies in flight a
