@@ -683,6 +683,7 @@ def run_learned(args):
     dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
     tr = segmg.Trainer(capacity=200 * 24, batch_max=64, seed=5)
+    tr.set_loss(args.loss)
     for k in range(200):
         img, mk, _ = synth.ellipses(1024, 1024, 12, (20, 200), 8, 0.05, 100 + k)
         s = segmg.Solver(torch.as_tensor(img.astype(np.float32), device=dev), mk, segmg.default_params(1024, 1024))
@@ -732,7 +733,7 @@ def run_learned(args):
                          "learned_accepted": stt["learned_accepted"] - a0["learned_accepted"],
                          "learned_rejected": stt["learned_rejected"] - a0["learned_rejected"]})
             s.close()
-    print(json.dumps({"learned": {"crops": tr.count, "record_s": t_rec, "train_iters": args.train_iters,
+    print(json.dumps({"learned": {"loss": args.loss, "crops": tr.count, "record_s": t_rec, "train_iters": args.train_iters,
                                   "train_s": t_train, "loss_before": loss0, "loss_after": loss1,
                                   "last_batch_loss": loss, "refresh": args.refresh},
                       "rows": rows}), flush=True)
@@ -764,6 +765,8 @@ def main():
                     help="train the learned relaxation weights, then compare at these sizes")
     ap.add_argument("--train-iters", type=int, default=1000)
     ap.add_argument("--refresh", type=int, default=4)
+    ap.add_argument("--loss", choices=["full", "hf"], default="full",
+                    help="learned weights: train on the residual or on its high-frequency part")
     args = ap.parse_args()
     if args.learned is not None:
         if not args.learned:

@@ -300,6 +300,12 @@ int mg_trainer_record(mg_trainer t, mg_handle h, int count);
 /* Appends `count` crop records from host memory. */
 int mg_trainer_load(mg_trainer t, const float *records, int count);
 int mg_trainer_count(mg_trainer t);
+/* The training loss: 0 (the default) the residual as above; 1 its high-frequency part, the
+ * quantity a multigrid smoother is responsible for (the coarse grid corrects the smooth part):
+ * v = 4 r - (the sum of r at the four neighbours), loss = 1/2 the mean of v^2 over the same cells
+ * (the 5-point Laplacian of r, whose symbol vanishes on smooth modes and peaks on the
+ * checkerboard mode).  Errors: MG_ERR_ARG. */
+int mg_trainer_set_loss(mg_trainer t, int kind);
 /* Mean loss and gradient over the crops idx[0..batch-1] (host) without a step. */
 int mg_trainer_grad(mg_trainer t, const int *idx, int batch, float *grad, double *loss);
 /* `iters` Adam steps on random batches; *loss gets the last batch's mean loss.  Waits. */

@@ -23,6 +23,14 @@ state u recorded from a plain solve): one red and one black damped point update 
 least one cell inside the crop, then
       loss = 1/2 mean over the cells at least two cells inside of r^2,  r = f - (sum_X c_X u_X - S u)
 the residual of the frozen equations (the quantity the smoother must reduce).
+
+A second loss ("hf") keeps only the high-frequency part of that residual, the part a multigrid
+smoother is responsible for (the coarse grid corrects the smooth part, Sec. 3.1):
+      h = 4 r - (r_S + r_N + r_E + r_W)      (the 5-point Laplacian of r; r as above, zero
+                                              outside the cells at least one cell inside)
+      loss = 1/2 mean over the cells at least two cells inside of h^2.
+The Laplacian's Fourier symbol 4 - 2 cos t1 - 2 cos t2 vanishes on constants and is largest (8)
+on the checkerboard mode, so the loss weighs each residual mode by the square of that symbol.
 """
 from __future__ import annotations
 
@@ -150,16 +158,26 @@ def loss_cells(n, m):
     return (ii >= 2) & (ii < n - 2) & (jj >= 2) & (jj < m - 2)
 
 
-def crop_loss(theta, c, S, f, u, parity0=0):
-    """The training loss of one crop (module docstring)."""
+def high_pass(r):
+    """h = 4 r - (sum of the four neighbours of r), on the cells at least one inside (the
+    neighbours of the loss cells are all defined there)."""
+    h = np.zeros_like(r)
+    h[1:-1, 1:-1] = 4.0 * r[1:-1, 1:-1] - (r[2:, 1:-1] + r[:-2, 1:-1] + r[1:-1, 2:] + r[1:-1, :-2])
+    return h
+
+
+def crop_loss(theta, c, S, f, u, parity0=0, loss="full"):
+    """The training loss of one crop (module docstring); loss "full" or "hf"."""
     omega, _ = forward(theta, features(*c))
     u2 = damped_rb(c, S, f, u, omega, parity0)
     r = residual(c, S, f, u2)
+    if loss == "hf":
+        r = high_pass(r)
     L = loss_cells(*u.shape)
     return 0.5 * np.mean(r[L] ** 2)
 
 
-def crop_loss_grad(theta, c, S, f, u, parity0=0):
+def crop_loss_grad(theta, c, S, f, u, parity0=0, loss="full"):
     """Loss and its gradient with respect to theta (reverse-mode, written out by hand)."""
     n, m = u.shape
     x = features(*c)
@@ -185,9 +203,18 @@ def crop_loss_grad(theta, c, S, f, u, parity0=0):
     r = residual(c, S, f, u2)
     L = loss_cells(n, m)
     cnt = L.sum()
-    loss = 0.5 * np.sum(r[L] ** 2) / cnt
-    # dL/dr, then dL/du2 through r = f - (sum c_X u_X - S u)
-    dr = np.where(L, r / cnt, 0.0)
+    if loss == "hf":
+        h = high_pass(r)
+        value = 0.5 * np.sum(h[L] ** 2) / cnt
+        # dL/dr through h = 4 r - sum of neighbours (the stencil is symmetric: its transpose)
+        dh = np.where(L, h / cnt, 0.0)
+        dr = high_pass(dh)
+        ii, jj = np.mgrid[0:n, 0:m]
+        dr = np.where((ii >= 1) & (ii < n - 1) & (jj >= 1) & (jj < m - 1), dr, 0.0)
+    else:
+        value = 0.5 * np.sum(r[L] ** 2) / cnt
+        dr = np.where(L, r / cnt, 0.0)
+    # dL/du2 through r = f - (sum c_X u_X - S u)
     du = np.zeros_like(u2)
     du[1:-1, 1:-1] += S[1:-1, 1:-1] * dr[1:-1, 1:-1]
     du[2:, 1:-1] -= c[0][1:-1, 1:-1] * dr[1:-1, 1:-1]
@@ -217,7 +244,7 @@ def crop_loss_grad(theta, c, S, f, u, parity0=0):
     dz1 = da1 * (cache["z1"] > 0)
     dW1, db1, _ = conv3_backward(cache["x"], W1, dz1)
     grad = np.concatenate([a.ravel() for a in (dW1, db1, dW2, db2, dW3, db3)])
-    return loss, grad
+    return value, grad
 
 
 def adam_step(theta, grad, state, lr, b1=0.9, b2=0.999, eps=1e-8):

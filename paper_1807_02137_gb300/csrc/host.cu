@@ -1832,6 +1832,7 @@ int mg_learned_nparam(void) { return learned_nparam(); }
 
 struct mg_trainer_s {
     int cap = 0, count = 0, batch_max = 0, step = 0;
+    int loss_kind = 0;   // mg_trainer_set_loss
     unsigned long long seed = 0;
     cudaStream_t st = nullptr;
     float *data = nullptr, *theta = nullptr, *mom = nullptr, *vel = nullptr, *grad = nullptr, *loss = nullptr;
@@ -1912,13 +1913,19 @@ int mg_trainer_load(mg_trainer t, const float *records, int count) {
 
 int mg_trainer_count(mg_trainer t) { return t ? t->count : 0; }
 
+int mg_trainer_set_loss(mg_trainer t, int kind) {
+    if (!t || kind < 0 || kind > 1) return fail(MG_ERR_ARG, "NULL trainer or loss kind not 0 / 1");
+    t->loss_kind = kind;
+    return MG_OK;
+}
+
 // One batch: mean loss and gradient over the given crops; with lr > 0 also the Adam step.
 static int trainer_batch(mg_trainer t, const int *idx, int batch, double lr, double *loss_out, float *grad_out) {
     if (cudaMemcpyAsync(t->idx, idx, sizeof(int) * batch, cudaMemcpyHostToDevice, t->st) != cudaSuccess)
         return fail(MG_ERR_CUDA, "index upload");
     if (lr > 0) ++t->step;
     launch_train_step(t->theta, t->mom, t->vel, t->data, t->idx, batch, t->grad, t->loss, t->gmean, t->lmean,
-                      (float)lr, lr > 0 ? t->step : 0, t->st);
+                      (float)lr, lr > 0 ? t->step : 0, t->loss_kind, t->st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(MG_ERR_CUDA, cudaGetErrorString(e));
     float l = 0.f;

@@ -164,7 +164,8 @@ template <typename T>
 void launch_record_crops(const LevelView<T> &L, const int *origins, int count, float *data, int first,
                          cudaStream_t st);
 void launch_train_step(float *theta, float *mom, float *vel, const float *data, const int *idx, int batch,
-                       float *grad, float *loss, float *gmean, float *lmean, float lr, int step, cudaStream_t st);
+                       float *grad, float *loss, float *gmean, float *lmean, float lr, int step, int loss_kind,
+                       cudaStream_t st);
 
 // cycle_kernels.cu
 template <typename T>

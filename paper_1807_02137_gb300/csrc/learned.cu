@@ -14,8 +14,9 @@
 // Training: crops of 24 x 24 cells recorded from plain solves (row-scaled coefficients c_X,
 // right-hand side f, state u, 1/tau, colour parity of the crop's origin).  Loss of a crop: one
 // red and one black damped point update on the cells at least one cell inside, then 1/2 the
-// mean of r^2 over the cells at least two inside, r = f - (sum_X c_X u_X - S u),
-// S = sum_X c_X + 1/tau.  One block per crop computes the loss and its gradient by reverse mode;
+// mean of v^2 over the cells at least two inside, with v = r = f - (sum_X c_X u_X - S u),
+// S = sum_X c_X + 1/tau (loss 0), or v = 4 r - (the sum of r at the four neighbours), the
+// residual's high-frequency part, which the smoother of a multigrid cycle must remove (loss 1).  One block per crop computes the loss and its gradient by reverse mode;
 // a second kernel averages the gradients over the batch in a fixed order and a third applies
 // Adam.
 #include <cuda_bf16.h>
@@ -177,7 +178,7 @@ __device__ __forceinline__ float conv_at(const float *W, int o, int cin, const f
 }
 
 __global__ void __launch_bounds__(256) k_train_crop(const float *theta, const float *data, const int *idx,
-                                                    float *grad, float *loss) {
+                                                    float *grad, float *loss, int hf) {
     extern __shared__ __align__(16) unsigned char smem_tr[];
     TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_tr);
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -230,21 +231,35 @@ __global__ void __launch_bounds__(256) k_train_crop(const float *theta, const fl
         }
         __syncthreads();
     }
-    // residual, loss over the cells at least two inside
+    // residual (in t), the loss over the cells at least two inside
     const int cnt = (kCrop - 4) * (kCrop - 4);
-    double ls = 0.0;
     for (int q = tid; q < kCC; q += nt) {
         float r = 0.f;
         if (inner(q))
             r = S.f[q] - (S.c[0][q] * S.u2[q + kCrop] + S.c[1][q] * S.u2[q - kCrop] + S.c[2][q] * S.u2[q + 1] +
                           S.c[3][q] * S.u2[q - 1] - S.S[q] * S.u2[q]);
+        S.t[q] = r;
+    }
+    __syncthreads();
+    double ls = 0.0;
+    for (int q = tid; q < kCC; q += nt) {
         const int rr = q / kCrop, cc = q % kCrop;
         const bool lc = rr >= 2 && rr < kCrop - 2 && cc >= 2 && cc < kCrop - 2;
-        S.r[q] = lc ? r / cnt : 0.f;            // dL/dr
-        if (lc) ls += 0.5 * (double)r * r;
+        float v = 0.f;
+        if (lc) {
+            v = hf ? 4.f * S.t[q] - (S.t[q + kCrop] + S.t[q - kCrop] + S.t[q + 1] + S.t[q - 1]) : S.t[q];
+            ls += 0.5 * (double)v * v;
+        }
+        S.du[q] = lc ? v / cnt : 0.f;           // dL/dv
     }
     ls = block_sum(ls, S.red);
     if (tid == 0) loss[blockIdx.x] = (float)(ls / cnt);
+    __syncthreads();
+    for (int q = tid; q < kCC; q += nt) {      // dL/dr (the high-pass stencil is symmetric)
+        float d = S.du[q];
+        if (hf) d = inner(q) ? 4.f * S.du[q] - (S.du[q + kCrop] + S.du[q - kCrop] + S.du[q + 1] + S.du[q - 1]) : 0.f;
+        S.r[q] = d;
+    }
     __syncthreads();
     // dL/du2 through r = f - (sum c u_X - S u)
     for (int q = tid; q < kCC; q += nt) {
@@ -414,8 +429,9 @@ void launch_record_crops(const LevelView<T> &L, const int *origins, int count, f
 }
 
 void launch_train_step(float *theta, float *mom, float *vel, const float *data, const int *idx, int batch,
-                       float *grad, float *loss, float *gmean, float *lmean, float lr, int step, cudaStream_t st) {
-    k_train_crop<<<batch, 256, sizeof(TrainSmem), st>>>(theta, data, idx, grad, loss);
+                       float *grad, float *loss, float *gmean, float *lmean, float lr, int step, int loss_kind,
+                       cudaStream_t st) {
+    k_train_crop<<<batch, 256, sizeof(TrainSmem), st>>>(theta, data, idx, grad, loss, loss_kind);
     k_train_reduce<<<(kNP + 255) / 256, 256, 0, st>>>(grad, loss, batch, gmean, lmean);
     if (!(lr > 0.f)) return;   // gradient only
     const float b1 = 0.9f, b2 = 0.999f;

@@ -24,7 +24,7 @@ EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcy
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
            "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_inject_divergence", "mg_segment_host", "mg_get_stream", "mg_destroy",
            "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_set_cluster_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
-           "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_grad",
+           "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_set_loss", "mg_trainer_grad",
            "mg_trainer_train", "mg_trainer_get", "mg_trainer_destroy",
            "mg_batch_setup", "mg_batch_solve_step", "mg_batch_autotune", "mg_batch_handle",
            "mg_batch_destroy"]
@@ -116,6 +116,7 @@ def lib():
             "mg_trainer_record": ([vp, vp, i], i),
             "mg_trainer_load": ([vp, C.POINTER(C.c_float), i], i),
             "mg_trainer_count": ([vp], i),
+            "mg_trainer_set_loss": ([vp, i], i),
             "mg_trainer_grad": ([vp, C.POINTER(i), i, C.POINTER(C.c_float), C.POINTER(C.c_double)], i),
             "mg_trainer_train": ([vp, i, i, C.c_double, C.POINTER(C.c_double)], i),
             "mg_trainer_get": ([vp, C.POINTER(C.c_float)], i),
@@ -501,6 +502,10 @@ class Trainer:
     @property
     def count(self):
         return lib().mg_trainer_count(self._h)
+
+    def set_loss(self, kind):
+        """mg_trainer_set_loss: 0 the residual, 1 its high-frequency part ("hf")."""
+        _check(lib().mg_trainer_set_loss(self._h, {"full": 0, "hf": 1}.get(kind, kind)), "mg_trainer_set_loss")
 
     def grad(self, idx):
         import numpy as np

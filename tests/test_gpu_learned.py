@@ -90,10 +90,12 @@ def _crops(count, seed):
     return recs
 
 
-def test_training_loss_and_gradient_match_oracle(segmg):
+@pytest.mark.parametrize("kind", ["full", "hf"])
+def test_training_loss_and_gradient_match_oracle(segmg, kind):
     recs = _crops(6, 11)
     th = _theta(12).astype(np.float32)
     t = segmg.Trainer(capacity=16, batch_max=8, seed=1, theta0=th)
+    t.set_loss(kind)
     t.load(recs.reshape(6, -1))
     idx = [0, 3, 5, 2]
     loss, g = t.grad(idx)
@@ -102,13 +104,14 @@ def test_training_loss_and_gradient_match_oracle(segmg):
         r = recs[k].astype(np.float64)
         c = r[:4]
         S = c.sum(axis=0) + r[6, 0, 0]
-        l1, g1 = NL.crop_loss_grad(th.astype(np.float64), c, S, r[4], r[5], parity0=int(r[6, 0, 1]))
+        l1, g1 = NL.crop_loss_grad(th.astype(np.float64), c, S, r[4], r[5], parity0=int(r[6, 0, 1]), loss=kind)
         lo += l1 / len(idx)
         go += g1 / len(idx)
     assert abs(loss - lo) <= 1e-4 * lo
     assert np.linalg.norm(g - go) <= 2e-3 * np.linalg.norm(go)
     # an Adam step lowers the loss of a fixed batch from omega = 1
     t2 = segmg.Trainer(capacity=16, batch_max=8, seed=2)
+    t2.set_loss(kind)
     t2.load(recs.reshape(6, -1))
     l0, _ = t2.grad(list(range(6)))
     for _ in range(30):

@@ -64,22 +64,44 @@ def test_damped_red_black_residual_identities():
     assert np.allclose(NL.residual(c, S, f, u1)[red], 0.0, atol=1e-12)
 
 
-@pytest.mark.parametrize("seed", [3, 4])
-def test_loss_gradient_matches_finite_differences(seed):
+@pytest.mark.parametrize("seed,loss", [(3, "full"), (4, "full"), (5, "hf"), (6, "hf")])
+def test_loss_gradient_matches_finite_differences(seed, loss):
     rng = np.random.default_rng(seed)
     c, S, f, u = _crop(10, 12, seed)
     theta = rng.normal(0, 0.3, NL.NPARAM)
-    loss, g = NL.crop_loss_grad(theta, c, S, f, u)
-    assert np.isclose(loss, NL.crop_loss(theta, c, S, f, u), rtol=1e-13)
+    value, g = NL.crop_loss_grad(theta, c, S, f, u, loss=loss)
+    assert np.isclose(value, NL.crop_loss(theta, c, S, f, u, loss=loss), rtol=1e-13)
     idx = rng.choice(NL.NPARAM, 40, replace=False)
     idx = np.concatenate([idx, [NL.NPARAM - 1, 0, 720, 736]])   # b3, W1, b1, W2 first entries
-    h = 1e-6
-    for k in idx:
+    def fd(k, h):
         tp, tm = theta.copy(), theta.copy()
         tp[k] += h
         tm[k] -= h
-        fd = (NL.crop_loss(tp, c, S, f, u) - NL.crop_loss(tm, c, S, f, u)) / (2 * h)
-        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (k, fd, g[k])
+        return (NL.crop_loss(tp, c, S, f, u, loss=loss) - NL.crop_loss(tm, c, S, f, u, loss=loss)) / (2 * h)
+
+    for k in idx:
+        if loss == "full":
+            d = fd(k, 1e-6)
+        else:
+            # the high-pass loss is larger and more curved: Richardson extrapolation of two
+            # central differences (error O(h^4)) at a step where rounding stays small
+            d = (4.0 * fd(k, 5e-5) - fd(k, 1e-4)) / 3.0
+        assert abs(d - g[k]) <= 1e-6 * max(1.0, abs(d)) + 1e-9, (k, d, g[k])
+
+
+def test_high_pass_symbol():
+    # h = 4 r - (sum of the neighbours): zero on constants and linear functions, 8 r on the
+    # checkerboard mode, (4 - 2 cos t1 - 2 cos t2) r on a plane wave (interior cells)
+    n = 12
+    ii, jj = np.mgrid[0:n, 0:n].astype(float)
+    inner = (slice(2, n - 2), slice(2, n - 2))
+    assert np.allclose(NL.high_pass(np.full((n, n), 3.0))[inner], 0.0)
+    assert np.allclose(NL.high_pass(2 * ii - jj + 1)[inner], 0.0)
+    chk = (-1.0) ** (ii + jj)
+    assert np.allclose(NL.high_pass(chk)[inner], 8.0 * chk[inner])
+    t1, t2 = 0.7, 1.9
+    wave = np.cos(t1 * ii + t2 * jj)
+    assert np.allclose(NL.high_pass(wave)[inner], (4 - 2 * np.cos(t1) - 2 * np.cos(t2)) * wave[inner])
 
 
 def test_first_adam_step_moves_by_lr_times_sign():
