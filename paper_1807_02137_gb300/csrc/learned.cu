@@ -1,5 +1,6 @@
 // learned.cu -- learned per-cell relaxation weights for the point updates of Hybrid Smoother 2:
-// inference (BF16 weights and activations, FP32 accumulation) and training (FP32).
+// inference (BF16 weights and activations on the tensor cores, FP32 accumulation) and training
+// (FP32).
 //
 // The paper chooses its smoother cell by cell from the local coefficients (Sec. 4).  This
 // extension learns a weight omega in (0, 2) for the point update phi += omega (g - phi) of every
@@ -44,15 +45,94 @@ __device__ __forceinline__ void cell_features(float aS, float aN, float aE, floa
 
 // ---------------------------------------------------------------------------------------
 // Inference: one 16 x 16 tile of omega per block (256 threads), all three layers in shared
-// memory (features on the tile + 3 cells, layer 1 on + 2, layer 2 on + 1).
+// memory (features on the tile + 3 cells, layer 1 on + 2, layer 2 on + 1).  The two hidden
+// convolutions run on the tensor cores as implicit GEMMs (mma.sync m16n8k16, BF16 operands,
+// FP32 accumulation): rows = the window's pixels (16 per MMA), columns = the 16 output
+// channels (two n8 blocks), K = 9 taps x 16 input channels (one k16 step per tap; layer 1's
+// 5 input channels padded with zeros).  Activations are stored channel-minor (16 BF16 = 32 bytes
+// per pixel), so a fragment's pair of channels is one 32-bit word.  The output convolution
+// (16 -> 1) runs on the CUDA cores.
 // ---------------------------------------------------------------------------------------
 struct InferSmem {
     float G[24][25];
-    __nv_bfloat16 X[kCin][22][22];
-    __nv_bfloat16 A1[kCh][20][20];
-    __nv_bfloat16 A2[kCh][18][18];
+    __nv_bfloat16 X[22][22][kCh];   // features, channels 5..15 zero
+    __nv_bfloat16 A1[20][20][kCh];
+    __nv_bfloat16 A2[18][18][kCh];
     float W[kNP];
 };
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const uint32_t l = __bfloat16_as_ushort(__float2bfloat16(lo));
+    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16(hi));
+    return l | (h << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One hidden 3x3 convolution of the tile on the tensor cores: input IN (an IW x IW window of
+// pixels, 16 channels each), output OUT (the (IW-2) x (IW-2) window inside it), weights Wt
+// (o, cin, 3, 3) at S.W + wofs with cin input channels, bias at S.W + bofs, ReLU; pixels outside
+// the grid (window origin gi0, gj0) get 0.  One warp per M-tile of 16 pixels.
+template <int IW>
+__device__ __forceinline__ void conv_tc(const InferSmem &S, const __nv_bfloat16 (*IN)[IW][kCh],
+                                        __nv_bfloat16 (*OUT)[IW - 2][kCh], int wofs, int bofs, int cin,
+                                        int gi0, int gj0, int n, int m) {
+    constexpr int OW = IW - 2, NPIX = OW * OW, MT = (NPIX + 15) / 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+    // B fragments of the 9 taps and the two n8 blocks: k = input channel, n = output channel
+    uint32_t bf[9][2][2];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+            const int o = g + 8 * nb;
+            float w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = 2 * t4 + (e & 1) + 8 * (e >> 1);
+                w[e] = i < cin ? S.W[wofs + (o * cin + i) * 9 + tap] : 0.f;
+            }
+            bf[tap][nb][0] = pack_bf16(w[0], w[1]);
+            bf[tap][nb][1] = pack_bf16(w[2], w[3]);
+        }
+    const uint32_t *in32 = reinterpret_cast<const uint32_t *>(&IN[0][0][0]);   // 8 words per pixel
+    for (int mt = warp; mt < MT; mt += 8) {
+        const int p0 = min(mt * 16 + g, NPIX - 1), p1 = min(mt * 16 + g + 8, NPIX - 1);
+        const int r0 = p0 / OW, c0 = p0 - r0 * OW, r1 = p1 / OW, c1 = p1 - r1 * OW;
+        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dr = tap / 3, dc = tap % 3;
+            const int q0 = ((r0 + dr) * IW + c0 + dc) * 8, q1 = ((r1 + dr) * IW + c1 + dc) * 8;
+            const uint32_t a0 = in32[q0 + t4], a1 = in32[q1 + t4], a2 = in32[q0 + t4 + 4], a3 = in32[q1 + t4 + 4];
+            mma_bf16(acc[0], a0, a1, a2, a3, bf[tap][0][0], bf[tap][0][1]);
+            mma_bf16(acc[1], a0, a1, a2, a3, bf[tap][1][0], bf[tap][1][1]);
+        }
+        // epilogue: bias, ReLU, zero outside the grid, BF16
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int pp = mt * 16 + g + 8 * half;
+            if (pp >= NPIX) continue;
+            const int r = pp / OW, c = pp - r * OW, gi = gi0 + r, gj = gj0 + c;
+            const bool in = gi >= 0 && gi < n && gj >= 0 && gj < m;
+#pragma unroll
+            for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int o = 8 * nb + 2 * t4 + e;
+                    const float v = in ? fmaxf(acc[nb][2 * half + e] + S.W[bofs + o], 0.f) : 0.f;
+                    OUT[r][c][o] = __float2bfloat16(v);
+                }
+        }
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_omega_infer(LevelView<T> L, const __nv_bfloat16 *net, T *omega) {
@@ -75,38 +155,12 @@ __global__ void __launch_bounds__(256) k_omega_infer(LevelView<T> L, const __nv_
             cell_features(face(gc, S.G[a + 1][b], gi + 1 < n), face(gc, S.G[a - 1][b], gi > 0),
                           face(gc, S.G[a][b + 1], gj + 1 < m), face(gc, S.G[a][b - 1], gj > 0), x);
         }
-        for (int k = 0; k < kCin; ++k) S.X[k][r][c] = __float2bfloat16(x[k]);
+        for (int k = 0; k < kCh; ++k) S.X[r][c][k] = __float2bfloat16(k < kCin ? x[k] : 0.f);
     }
     __syncthreads();
-    for (int q = tid; q < kCh * 20 * 20; q += 256) {
-        const int o = q / 400, r = (q / 20) % 20, c = q % 20, gi = i0 - 2 + r, gj = j0 - 2 + c;
-        float acc = 0.f;
-        if (gi >= 0 && gi < n && gj >= 0 && gj < m) {
-            acc = S.W[oB1 + o];
-            for (int i = 0; i < kCin; ++i)
-                for (int di = 0; di < 3; ++di)
-                    for (int dj = 0; dj < 3; ++dj)
-                        acc = fmaf(S.W[oW1 + ((o * kCin + i) * 3 + di) * 3 + dj],
-                                   __bfloat162float(S.X[i][r + di][c + dj]), acc);
-            acc = fmaxf(acc, 0.f);
-        }
-        S.A1[o][r][c] = __float2bfloat16(acc);
-    }
+    conv_tc<22>(S, S.X, S.A1, oW1, oB1, kCin, i0 - 2, j0 - 2, n, m);
     __syncthreads();
-    for (int q = tid; q < kCh * 18 * 18; q += 256) {
-        const int o = q / 324, r = (q / 18) % 18, c = q % 18, gi = i0 - 1 + r, gj = j0 - 1 + c;
-        float acc = 0.f;
-        if (gi >= 0 && gi < n && gj >= 0 && gj < m) {
-            acc = S.W[oB2 + o];
-            for (int i = 0; i < kCh; ++i)
-                for (int di = 0; di < 3; ++di)
-                    for (int dj = 0; dj < 3; ++dj)
-                        acc = fmaf(S.W[oW2 + ((o * kCh + i) * 3 + di) * 3 + dj],
-                                   __bfloat162float(S.A1[i][r + di][c + dj]), acc);
-            acc = fmaxf(acc, 0.f);
-        }
-        S.A2[o][r][c] = __float2bfloat16(acc);
-    }
+    conv_tc<20>(S, S.A1, S.A2, oW2, oB2, kCh, i0 - 1, j0 - 1, n, m);
     __syncthreads();
     {
         const int r = tid / 16, c = tid % 16, gi = i0 + r, gj = j0 + c;
@@ -115,7 +169,7 @@ __global__ void __launch_bounds__(256) k_omega_infer(LevelView<T> L, const __nv_
             for (int i = 0; i < kCh; ++i)
                 for (int di = 0; di < 3; ++di)
                     for (int dj = 0; dj < 3; ++dj)
-                        z = fmaf(S.W[oW3 + (i * 3 + di) * 3 + dj], __bfloat162float(S.A2[i][r + di][c + dj]), z);
+                        z = fmaf(S.W[oW3 + (i * 3 + di) * 3 + dj], __bfloat162float(S.A2[r + di][c + dj][i]), z);
             omega[(size_t)gi * p + gj] = T(2.f / (1.f + expf(-z)));
         }
     }
