@@ -226,6 +226,30 @@ int mg_set_wait_limit(mg_handle h, long long rounds);
  * once; 0 cancels it.  The device state is left as the V-cycle computed it.  Errors: MG_ERR_ARG. */
 int mg_inject_divergence(mg_handle h, int cycle);
 
+/* Index bounds checks of the debug build (no counterpart in the paper).  A library compiled with
+ * -DMG_DEBUG compares the index of each checked global-memory access of its kernels with the size
+ * of the buffer it addresses; an out-of-range access is skipped (a load reads 0), never trapped,
+ * and recorded in device error words (one set per compiled source file).  mg_debug_status waits
+ * for the device, ORs the words of all files into *out and, if clear is nonzero, zeroes them.
+ * In the default build it reports enabled = 0 and nothing else.  Errors: MG_ERR_ARG (NULL out),
+ * MG_ERR_CUDA. */
+typedef struct mg_debug_info {
+    int enabled;                 /* 1: the library was built with MG_DEBUG */
+    int first_site;              /* site of the first out-of-range index one file recorded, -1: none
+                                  * (0 set-up, 1 tile loads, 2 snapshot, 3 mask stores, 4 mask
+                                  * loads, 5 sweeps, 6 residual / restriction, 7 interpolation,
+                                  * 8 bottom kernels, 9 coarsest solve, 10 other smoothers) */
+    long long first_index;       /* that index (elements of the addressed buffer) */
+    unsigned long long sites;    /* bit s: site s saw an out-of-range index */
+    long long count;             /* out-of-range accesses skipped, all files */
+} mg_debug_info;
+int mg_debug_status(mg_debug_info *out, int clear);
+
+/* Test of the reporting path of the debug build: a one-thread kernel passes the index limit + 5
+ * through the check of site 10 with no memory access behind it, so mg_debug_status then shows
+ * site 10, that index and one more count.  Synchronous.  Does nothing in the default build. */
+int mg_debug_selftest(void);
+
 /* Whole pipeline through host buffers: copies the float image to the device, runs mg_setup,
  * then mg_solve(tol, max_cycles, eta_stop, max_steps) with the given parameters (precision
  * forced to MG_F32), and copies the mask (and phi if phi_host is not NULL) back.  All host

@@ -64,12 +64,12 @@ __global__ void __launch_bounds__(128) k_aos_lines(LevelView<T> L, const double 
                 y = (rr[o] + T(2) * dt * cn * y) / dd[o];
             }
             if (DIR == 0) {
-                yx[o] = y;
+                stc(yx, o, (size_t)L.n * L.pitch, kDbgOther, y);
             } else {
                 const T uo = L.u[o], un = T(0.5) * (yx[o] + y);
                 sd += (double)(un - uo) * (double)(un - uo);
                 sp += (double)(L.pn[o] + uo) * (double)(L.pn[o] + uo);
-                L.u[o] = un;
+                stc(L.u, o, (size_t)L.n * L.pitch, kDbgOther, un);
             }
         }
     }

@@ -173,7 +173,8 @@ __device__ __forceinline__ void load_halo2(T (*dA)[37], const T *sA, T (*dB)[37]
         const int q = tid + k * NT;
         if (q >= NVEC) break;
         const int a = q / NV, gi = i0 - 2 + a, gj = j0 - 4 + (q % NV) * VN;
-        if (gi >= 0 && gi < n && gj >= 0 && gj + VN <= m) {
+        if (gi >= 0 && gi < n && gj >= 0 && gj + VN <= m &&
+            MG_DBG_OK((size_t)gi * p + gj + VN - 1, (size_t)n * p, kDbgHaloLoad)) {
             const size_t o = (size_t)gi * p + gj;
             V va = __ldg(reinterpret_cast<const V *>(sA + o));
             memcpy(xa[k], &va, sizeof(V));
@@ -186,8 +187,8 @@ __device__ __forceinline__ void load_halo2(T (*dA)[37], const T *sA, T (*dB)[37]
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
                 const size_t o = ro + clamp_idx(gj + e, m - 1);
-                xa[k][e] = sA[o];
-                if (sB) xb[k][e] = sB[o];
+                xa[k][e] = ldc(sA, o, (size_t)n * p, kDbgHaloLoad);
+                if (sB) xb[k][e] = ldc(sB, o, (size_t)n * p, kDbgHaloLoad);
             }
         }
     }
@@ -220,7 +221,7 @@ __device__ __forceinline__ void load_tile32(T (*dA)[33], const T *sA, T (*dB)[33
         const int q = tid + k * NT;
         if (q >= NVEC) break;
         const int a = q / NV, gi = i0 + a, gj = j0 + (q % NV) * VN;
-        if (gi < n && gj + VN <= m) {
+        if (gi < n && gj + VN <= m && MG_DBG_OK((size_t)gi * p + gj + VN - 1, (size_t)n * p, kDbgHaloLoad)) {
             const size_t o = (size_t)gi * p + gj;
             V va = __ldg(reinterpret_cast<const V *>(sA + o));
             memcpy(xa[k], &va, sizeof(V));
@@ -233,8 +234,8 @@ __device__ __forceinline__ void load_tile32(T (*dA)[33], const T *sA, T (*dB)[33
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
                 const size_t o = ro + clamp_idx(gj + e, m - 1);
-                xa[k][e] = sA[o];
-                if (sB) xb[k][e] = sB[o];
+                xa[k][e] = ldc(sA, o, (size_t)n * p, kDbgHaloLoad);
+                if (sB) xb[k][e] = ldc(sB, o, (size_t)n * p, kDbgHaloLoad);
             }
         }
     }

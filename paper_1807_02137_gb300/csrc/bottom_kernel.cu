@@ -62,7 +62,8 @@ __device__ void b_G(const BGrid &B, const float *uu) {
         const int q = i * m + j;
         const int s = (i + 1 < n ? i + 1 : n - 1) * m + j, nn = (i > 0 ? i - 1 : 0) * m + j;
         const int e = q + (j + 1 < m ? 1 : 0), w = q - (j > 0 ? 1 : 0);
-        B.G[q] = cell_G(B.w[q], B.pn[s], B.pn[nn], B.pn[e], B.pn[w], uu[s], uu[nn], uu[e], uu[w], B.inv_2h, B.beta);
+        stc(B.G, q, (size_t)n * m, kDbgBottom,
+            cell_G(B.w[q], B.pn[s], B.pn[nn], B.pn[e], B.pn[w], uu[s], uu[nn], uu[e], uu[w], B.inv_2h, B.beta));
     }
     __syncthreads();
 }
@@ -86,14 +87,14 @@ __device__ void b_snapshot(const BGrid &B, uint8_t *star) {
         ds = fma_rn(aW, sub_rn(B.pn[oW], pc), ds);
         float base = add_rn(B.F[q], 0.0f);
         if (B.has_rhs) base = add_rn(base, B.rhs[q]);
-        B.f[q] = fma_rn(-B.cdiff, ds, base);
+        stc(B.f, q, (size_t)n * m, kDbgBottom, fma_rn(-B.cdiff, ds, base));
         const float big = 3.0e38f;
         const float vS = hS ? aS : big, vN = hN ? aN : big, vE = hE ? aE : big, vW = hW ? aW : big;
         const float mn = fminf(fminf(vS, vN), fminf(vE, vW));
         const float mx = fmaxf(fmaxf(hS ? aS : -1.f, hN ? aN : -1.f), fmaxf(hE ? aE : -1.f, hW ? aW : -1.f));
         const int am = vS == mn ? 0 : (vN == mn ? 1 : (vE == mn ? 2 : 3));
         const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
-        star[q] = (cnt >= 2 && mx > mul_rn(B.Sigma, mn)) ? (uint8_t)(1u << am) : (uint8_t)0;
+        stc(star, q, (size_t)n * m, kDbgBottom, (cnt >= 2 && mx > mul_rn(B.Sigma, mn)) ? (uint8_t)(1u << am) : (uint8_t)0);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -104,8 +105,8 @@ __device__ void b_snapshot(const BGrid &B, uint8_t *star) {
             const uint32_t mA = members_of(__ballot_sync(0xffffffffu, s & 1u), len);
             const uint32_t mB = members_of(__ballot_sync(0xffffffffu, s & 2u), len);
             if (lane == 0) {
-                B.mrow[(0 * n + i) * B.npm + pc] = mA;
-                B.mrow[(1 * n + i) * B.npm + pc] = mB;
+                stc(B.mrow, (size_t)(0 * n + i) * B.npm + pc, (size_t)2 * n * B.npm, kDbgBottom, mA);
+                stc(B.mrow, (size_t)(1 * n + i) * B.npm + pc, (size_t)2 * n * B.npm, kDbgBottom, mB);
             }
         }
     for (int j = warp; j < m; j += kBT / 32)                  // column pieces: sweeps C, D
@@ -115,8 +116,8 @@ __device__ void b_snapshot(const BGrid &B, uint8_t *star) {
             const uint32_t mC = members_of(__ballot_sync(0xffffffffu, s & 4u), len);
             const uint32_t mD = members_of(__ballot_sync(0xffffffffu, s & 8u), len);
             if (lane == 0) {
-                B.mcol[(0 * m + j) * B.npn + pc] = mC;
-                B.mcol[(1 * m + j) * B.npn + pc] = mD;
+                stc(B.mcol, (size_t)(0 * m + j) * B.npn + pc, (size_t)2 * m * B.npn, kDbgBottom, mC);
+                stc(B.mcol, (size_t)(1 * m + j) * B.npn + pc, (size_t)2 * m * B.npn, kDbgBottom, mD);
             }
         }
     __syncthreads();
@@ -173,7 +174,7 @@ __device__ void b_lines(const BGrid &B, int sweep, float *endv) {
                 };
                 float x;
                 if (pcr_piece<float>(mk, len, B.cdiff, B.inv_tau, own, ev[2 * pc], ev[2 * pc + 1], at, x))
-                    B.u[base + tt * step] = x;
+                    stc(B.u, (size_t)(base + tt * step), (size_t)n * m, kDbgBottom, x);
             }
             __syncwarp();
         }
@@ -199,7 +200,8 @@ __device__ void b_sweep(const BGrid &B, int sweep, float *endv) {
             const float gc = B.G[q];
             const float aS = face(gc, B.G[oS], hS), aN = face(gc, B.G[oN], hN);
             const float aE = face(gc, B.G[oE], hE), aW = face(gc, B.G[oW], hW);
-            B.u[q] = point_relax(B.cdiff, B.inv_tau, aS, aN, aE, aW, B.u[oS], B.u[oN], B.u[oE], B.u[oW], B.f[q]);
+            stc(B.u, q, (size_t)n * m, kDbgBottom,
+                point_relax(B.cdiff, B.inv_tau, aS, aN, aE, aW, B.u[oS], B.u[oN], B.u[oE], B.u[oW], B.f[q]));
         }
         __syncthreads();
     }
@@ -245,7 +247,7 @@ __device__ void b_smooth_small(const BGrid &B, uint8_t *star, float *endv) {
                 num = fma_rn(aN, B.u[oN], num);
                 num = fma_rn(aE, B.u[oE], num);
                 num = fma_rn(aW, B.u[oW], num);
-                B.u[q] = div_relax(fma_rn(B.cdiff, num, -fq), dv);
+                stc(B.u, q, (size_t)n * m, kDbgBottom, div_relax(fma_rn(B.cdiff, num, -fq), dv));
             }
             __syncthreads();
         }
@@ -271,8 +273,8 @@ __device__ void b_residual(const BGrid &B, const float *uu, float *out, int mode
         fl = fma_rn(aE, add_rn(sub_rn(B.pn[oE], pc), sub_rn(uu[oE], uc)), fl);
         fl = fma_rn(aW, add_rn(sub_rn(B.pn[oW], pc), sub_rn(uu[oW], uc)), fl);
         const float Lv = sub_rn(fma_rn(B.cdiff, fl, -add_rn(B.F[q], 0.0f)), mul_rn(B.inv_tau, uc));
-        if (mode == 0) out[q] = B.has_rhs ? sub_rn(B.rhs[q], Lv) : -Lv;
-        else out[q] = add_rn(out[q], Lv);
+        if (mode == 0) stc(out, q, (size_t)n * m, kDbgBottom, B.has_rhs ? sub_rn(B.rhs[q], Lv) : -Lv);
+        else stc(out, q, (size_t)n * m, kDbgBottom, add_rn(out[q], Lv));
     }
     __syncthreads();
 }
@@ -303,12 +305,13 @@ __device__ void b_restrict(const BGrid &F, const float *src, const BGrid &C, flo
         float s = 0.f;
         for (int a = 0; a < nr; ++a) {
             float row = 0.f;
-            for (int b = 0; b < nk; ++b) row = fma_rn((float)cw[b], src[ri[a] * F.m + ci[b]], row);
+            for (int b = 0; b < nk; ++b)
+                row = fma_rn((float)cw[b], ldc(src, (size_t)ri[a] * F.m + ci[b], (size_t)F.n * F.m, kDbgBottom), row);
             s = fma_rn((float)rw[a], row, s);
         }
         const int q = I * C.m + J;
-        dst[q] = s;
-        if (dst2) dst2[q] = s;
+        stc(dst, q, (size_t)C.n * C.m, kDbgBottom, s);
+        if (dst2) stc(dst2, q, (size_t)C.n * C.m, kDbgBottom, s);
     }
     __syncthreads();
 }
@@ -324,10 +327,11 @@ __device__ void b_interp_add(const BGrid &F, const BGrid &C) {
         for (int a = 0; a < nr; ++a)
             for (int b = 0; b < nk; ++b) {
                 const int o = ri[a] * C.m + ci[b];
-                s = fma_rn((float)(rw[a] * cw[b]), sub_rn(C.u[o], C.u0[o]), s);
+                const size_t lc = (size_t)C.n * C.m;
+                s = fma_rn((float)(rw[a] * cw[b]), sub_rn(ldc(C.u, o, lc, kDbgBottom), ldc(C.u0, o, lc, kDbgBottom)), s);
             }
         const int q = i * F.m + j;
-        F.u[q] = add_rn(F.u[q], s);
+        stc(F.u, q, (size_t)F.n * F.m, kDbgBottom, add_rn(F.u[q], s));
     }
     __syncthreads();
 }
@@ -438,13 +442,13 @@ __device__ void bottom_setup(const BottomArgs &A, BGrid *Bs, int lb, bool load_f
         const Map2 M = map_for(B.m);
         FOR_CELLS(M, B.n, B.m, i, j) {
             const int q = i * B.m + j;
-            const size_t o = (size_t)i * G.pitch + j;
-            B.pn[q] = G.pn[o];
+            const size_t o = (size_t)i * G.pitch + j, lim = (size_t)G.n * G.pitch;
+            B.pn[q] = ldc(G.pn, o, lim, kDbgBottom);
             B.w[q] = weight_at(G, o);
-            B.F[q] = G.F[o];
+            B.F[q] = ldc(G.F, o, lim, kDbgBottom);
             if (load_first && l == lb) {
-                B.u[q] = G.u[o];
-                B.rhs[q] = G.has_rhs ? G.rhs[o] : 0.f;
+                B.u[q] = ldc(G.u, o, lim, kDbgBottom);
+                B.rhs[q] = G.has_rhs ? ldc(G.rhs, o, lim, kDbgBottom) : 0.f;
             }
         }
     }
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
         const LevelView<float> &G = A.g[A.lb];
         const BGrid &B = Bs[A.lb];
         const Map2 M = map_for(B.m);
-        FOR_CELLS(M, B.n, B.m, i, j) G.u[(size_t)i * G.pitch + j] = B.u[i * B.m + j];
+        FOR_CELLS(M, B.n, B.m, i, j) stc(G.u, (size_t)i * G.pitch + j, (size_t)G.n * G.pitch, kDbgBottom, B.u[i * B.m + j]);
     }
 }
 
@@ -541,12 +545,12 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
         }
     };
     if (own) {
-        const size_t o = (size_t)i * Lg.pitch + j;
-        T.P[r0][c0] = Lg.pn[o];
-        T.U[r0][c0] = Lg.u[o];
+        const size_t o = (size_t)i * Lg.pitch + j, lim = (size_t)n * Lg.pitch;
+        T.P[r0][c0] = ldc(Lg.pn, o, lim, kDbgBottom);
+        T.U[r0][c0] = ldc(Lg.u, o, lim, kDbgBottom);
         T.W[ti][lane] = weight_at(Lg, o);
-        T.F[ti][lane] = Lg.F[o];
-        T.R[ti][lane] = has_rhs ? Lg.rhs[o] : 0.f;
+        T.F[ti][lane] = ldc(Lg.F, o, lim, kDbgBottom);
+        T.R[ti][lane] = has_rhs ? ldc(Lg.rhs, o, lim, kDbgBottom) : 0.f;
     }
     // grids lc+1 .. L-1: every CTA carves the same offsets (CTA 0's arrays are then reached by
     // mapping this CTA's addresses); their pn, w, F are loaded
@@ -747,7 +751,7 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
     ring(1);
     __syncthreads();
     for (int t = 0; t < A.nu2; ++t) smooth();
-    if (own) Lg.u[(size_t)i * Lg.pitch + j] = T.U[r0][c0];
+    if (own) stc(Lg.u, (size_t)i * Lg.pitch + j, (size_t)n * Lg.pitch, kDbgBottom, T.U[r0][c0]);
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 

@@ -227,7 +227,7 @@ __device__ void coarse_solve_team(const CoarseGrid<T> &L, ModelParams mp, double
                 diag += a;
                 pflux += g * (pn_at(i2, j2) - pc);
                 int c = idx(i2, j2);
-                if (c < r) band[(size_t)r * bw1 + (r - c)] = -a;
+                if (c < r && MG_DBG_OK(r - c, bw1, kDbgCoarse)) band[(size_t)r * bw1 + (r - c)] = -a;
             };
             if (i + 1 < n) off(i + 1, j);
             if (i > 0) off(i - 1, j);
@@ -264,13 +264,18 @@ __device__ void coarse_solve_team(const CoarseGrid<T> &L, ModelParams mp, double
                 if ((*s_err)) break;
                 const C rkk = band[(size_t)k * bw1];
                 const int last = min(k + bw, N - 1), cnt = last - k;
-                for (int t = tid; t < cnt; t += nt) band[(size_t)(k + 1 + t) * bw1 + (1 + t)] *= rkk;
+                for (int t = tid; t < cnt; t += nt)
+                    if (MG_DBG_OK((size_t)(k + 1 + t) * bw1 + (1 + t), (size_t)N * bw1, kDbgCoarse))
+                        band[(size_t)(k + 1 + t) * bw1 + (1 + t)] *= rkk;
                 TM::sync();
                 for (int t = tid; t < cnt * cnt; t += nt) {
                     // the trailing triangle: rows ii >= columns jj (integer indexing only)
                     const int ii = t / cnt, jj = t - ii * cnt;
                     if (jj > ii) continue;
                     int ri = k + 1 + ii, rj = k + 1 + jj;
+                    if (!MG_DBG_OK((size_t)ri * bw1 + (ri - rj), (size_t)N * bw1, kDbgCoarse) ||
+                        !MG_DBG_OK(ri - k, bw1, kDbgCoarse) || !MG_DBG_OK(rj - k, bw1, kDbgCoarse))
+                        continue;
                     band[(size_t)ri * bw1 + (ri - rj)] -= band[(size_t)ri * bw1 + (ri - k)] * band[(size_t)rj * bw1 + (rj - k)];
                 }
                 TM::sync();
@@ -311,7 +316,7 @@ __device__ void coarse_solve_team(const CoarseGrid<T> &L, ModelParams mp, double
     }
     for (int q = tid; q < N; q += nt) {
         int i = q / m, j = q % m;
-        L.u[(size_t)i * p + j] = (T)x[idx(i, j)];
+        stc(L.u, (size_t)i * p + j, (size_t)n * p, kDbgCoarse, (T)x[idx(i, j)]);
     }
     *it_out = it;
     *res_out = res;
@@ -402,7 +407,7 @@ __device__ void aos_solve_team(const CoarseGrid<T> &L, ModelParams mp, double A1
             TM::sync();
         }
     }
-    for (int q = tid; q < N; q += NT) L.u[(size_t)(q / m) * p + (q % m)] = (T)x[q];
+    for (int q = tid; q < N; q += NT) stc(L.u, (size_t)(q / m) * p + (q % m), (size_t)n * p, kDbgCoarse, (T)x[q]);
     TM::sync();
 }
 

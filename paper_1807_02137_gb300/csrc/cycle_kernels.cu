@@ -68,14 +68,15 @@ __global__ void __launch_bounds__(256, MINB)
         fl = fma_rn(aE, add_rn(sub_rn(sP[a][b + 1], pc), sub_rn(sU[a][b + 1], uc)), fl);
         fl = fma_rn(aW, add_rn(sub_rn(sP[a][b - 1], pc), sub_rn(sU[a][b - 1], uc)), fl);
         size_t o = (size_t)gi * p + gj;
-        T Fv = kStage ? sF[kStage ? ti : 0][kStage ? tj : 0] : L.F[o];
+        const size_t lim = (size_t)n * p;
+        T Fv = kStage ? sF[kStage ? ti : 0][kStage ? tj : 0] : ldc(L.F, o, lim, kDbgResidual);
         T Lv = sub_rn(fma_rn(L.cdiff, fl, -add_rn(Fv, ar)), mul_rn(L.inv_tau, uc));
         if (mode == 0) {
-            T r = L.has_rhs ? sub_rn(L.rhs[o], Lv) : -Lv;
-            out[o] = r;
+            T r = L.has_rhs ? sub_rn(ldc(L.rhs, o, lim, kDbgResidual), Lv) : -Lv;
+            stc(out, o, lim, kDbgResidual, r);
             acc = add_square(acc, r);
         } else {
-            out[o] = add_rn(out[o], Lv);
+            stc(out, o, lim, kDbgResidual, add_rn(ldc(out, o, lim, kDbgResidual), Lv));
         }
     }
     if (mode == 0 && partials) {
@@ -96,7 +97,7 @@ __device__ __forceinline__ void load_window(float (*dA)[COLS + 1], const float *
     for (int q = tid; q < NVEC; q += NT) {
         const int a = q / NV, k = q % NV, gi = r0 + a, gj = c0 - OFF + 4 * k;
         float xa[4], xb[4];
-        if (gi >= 0 && gi < n && gj >= 0 && gj + 4 <= m) {
+        if (gi >= 0 && gi < n && gj >= 0 && gj + 4 <= m && MG_DBG_OK((size_t)gi * p + gj + 3, (size_t)n * p, kDbgHaloLoad)) {
             const size_t o = (size_t)gi * p + gj;
             const float4 va = __ldg(reinterpret_cast<const float4 *>(sA + o));
             xa[0] = va.x; xa[1] = va.y; xa[2] = va.z; xa[3] = va.w;
@@ -109,8 +110,8 @@ __device__ __forceinline__ void load_window(float (*dA)[COLS + 1], const float *
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const size_t o = ro + clamp_idx(gj + e, m - 1);
-                xa[e] = sA[o];
-                if (sB) xb[e] = sB[o];
+                xa[e] = ldc(sA, o, (size_t)n * p, kDbgHaloLoad);
+                if (sB) xb[e] = ldc(sB, o, (size_t)n * p, kDbgHaloLoad);
             }
         }
 #pragma unroll
@@ -190,16 +191,17 @@ __global__ void __launch_bounds__(256) k_residual_restrict(LevelView<float> L, L
             for (int a = 0; a < nr; ++a) {
                 float rowr = 0.f, rowu = 0.f;
                 for (int b = 0; b < nk; ++b) {
+                    if (!MG_DBG_OK(ri[a] - i0, 33, kDbgResidual) || !MG_DBG_OK(ci[b] - j0, 33, kDbgResidual)) continue;
                     rowr = fma_rn(float(cw[b]), S.R[ri[a] - i0][ci[b] - j0], rowr);
                     rowu = fma_rn(float(cw[b]), S.U[ri[a] - i0 + 2][ci[b] - j0 + 2], rowu);
                 }
                 sr = fma_rn(float(rw[a]), rowr, sr);
                 su = fma_rn(float(rw[a]), rowu, su);
             }
-            const size_t o = (size_t)I * C.pitch + J;
-            C.rhs[o] = sr;
-            C.u[o] = su;
-            C.u0[o] = su;
+            const size_t o = (size_t)I * C.pitch + J, lc = (size_t)C.n * C.pitch;
+            stc(C.rhs, o, lc, kDbgResidual, sr);
+            stc(C.u, o, lc, kDbgResidual, su);
+            stc(C.u0, o, lc, kDbgResidual, su);
         }
     }
 }
@@ -238,11 +240,12 @@ __global__ void __launch_bounds__(256) k_restrict(const T *f, int n, int m, int 
     T s = T(0);
     for (int a = 0; a < nr; ++a) {
         T row = T(0);
-        for (int b = 0; b < nk; ++b) row = fma_rn(T(cw[b]), f[(size_t)ri[a] * pf + ci[b]], row);
+        for (int b = 0; b < nk; ++b)
+            row = fma_rn(T(cw[b]), ldc(f, (size_t)ri[a] * pf + ci[b], (size_t)n * pf, kDbgResidual), row);
         s = fma_rn(T(rw[a]), row, s);
     }
-    c[(size_t)I * pc + J] = s;
-    if (c2) c2[(size_t)I * pc + J] = s;
+    stc(c, (size_t)I * pc + J, (size_t)nc * pc, kDbgResidual, s);
+    if (c2) stc(c2, (size_t)I * pc + J, (size_t)nc * pc, kDbgResidual, s);
 }
 
 // One-dimensional bilinear taps (Sec. 3.1): fine 2I+1 takes coarse I; fine 2I+2 the mean of
@@ -267,11 +270,11 @@ __global__ void __launch_bounds__(256) k_interp_add(LevelView<T> Lf, LevelView<T
     T s = T(0);
     for (int a = 0; a < nr; ++a)
         for (int b = 0; b < nk; ++b) {
-            size_t o = (size_t)ri[a] * Lc.pitch + ci[b];
-            s = fma_rn(T(rw[a] * cw[b]), sub_rn(Lc.u[o], Lc.u0[o]), s);
+            size_t o = (size_t)ri[a] * Lc.pitch + ci[b], lc = (size_t)Lc.n * Lc.pitch;
+            s = fma_rn(T(rw[a] * cw[b]), sub_rn(ldc(Lc.u, o, lc, kDbgInterp), ldc(Lc.u0, o, lc, kDbgInterp)), s);
         }
     size_t o = (size_t)i * Lf.pitch + j;
-    Lf.u[o] = add_rn(Lf.u[o], s);
+    stc(Lf.u, o, (size_t)Lf.n * Lf.pitch, kDbgInterp, add_rn(Lf.u[o], s));
 }
 
 // The coarsest solve (coarse_body.cuh) as its own one-block kernel.

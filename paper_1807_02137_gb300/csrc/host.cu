@@ -17,6 +17,17 @@
 
 namespace segmg {
 void prepare_smoother_kernels();
+
+// Readers of the MG_DEBUG error words, one per translation unit (registered at load time).
+using DebugReader = int (*)(unsigned long long *, int);
+static std::vector<DebugReader> &debug_readers() {
+    static std::vector<DebugReader> v;
+    return v;
+}
+int register_debug_reader(int (*read)(unsigned long long *words, int clear)) {
+    debug_readers().push_back(read);
+    return (int)debug_readers().size();
+}
 }
 
 namespace {
@@ -1756,6 +1767,44 @@ int mg_inject_divergence(mg_handle h, int cycle) {
 }
 int mg_set_wait_limit(mg_handle h, long long rounds) {
     return h ? h->s->set_wait_limit(rounds) : fail(MG_ERR_ARG, "NULL handle");
+}
+
+#ifdef MG_DEBUG
+namespace {
+__global__ void k_debug_selftest(long long lim) { (void)MG_DBG_OK(lim + 5, lim, kDbgOther); }
+}  // namespace
+#endif
+
+int mg_debug_selftest(void) {
+#ifdef MG_DEBUG
+    k_debug_selftest<<<1, 1>>>(1000);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+#endif
+    return MG_OK;
+}
+
+int mg_debug_status(mg_debug_info *out, int clear) {
+    if (!out) return fail(MG_ERR_ARG, "NULL argument");
+    *out = mg_debug_info{};
+    out->first_site = -1;
+#ifdef MG_DEBUG
+    out->enabled = 1;
+    CK(cudaDeviceSynchronize());
+    for (auto rd : segmg::debug_readers()) {
+        unsigned long long w[4] = {0, 0, 0, 0};
+        if (rd(w, clear) != 0) return fail(MG_ERR_CUDA, "reading the debug words");
+        out->sites |= w[0];
+        if (out->first_site < 0 && w[2] != 0) {
+            out->first_site = (int)w[2] - 1;
+            out->first_index = (long long)w[1];
+        }
+        out->count += (long long)w[3];
+    }
+#else
+    (void)clear;
+#endif
+    return MG_OK;
 }
 
 int mg_segment_host(const float *image_host, int n, int m, const double *markers_xy, int k,

@@ -13,6 +13,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "debug.cuh"
+
 namespace segmg {
 
 constexpr int kChunk = 32;        // partial-line groups are cut at multiples of 32 cells
@@ -77,14 +79,18 @@ struct ModelParams {
 // Member bit of cell (i, j) in sweep 0..3 (A, B, C, D).
 template <typename T>
 __device__ __forceinline__ bool member_bit(const LevelView<T> &L, int sweep, int i, int j) {
-    if (sweep < 2) return (L.mrow[((size_t)sweep * L.n + i) * L.npm + (j >> 5)] >> (j & 31)) & 1u;
-    return (L.mcol[((size_t)(sweep - 2) * L.m + j) * L.npn + (i >> 5)] >> (i & 31)) & 1u;
+    if (sweep < 2)
+        return (ldc(L.mrow, ((size_t)sweep * L.n + i) * L.npm + (j >> 5), (size_t)2 * L.n * L.npm, kDbgMaskLoad) >>
+                (j & 31)) & 1u;
+    return (ldc(L.mcol, ((size_t)(sweep - 2) * L.m + j) * L.npn + (i >> 5), (size_t)2 * L.m * L.npn, kDbgMaskLoad) >>
+            (i & 31)) & 1u;
 }
 
 // The length weight w of cell o: BF16 storage in mixed precision, else the storage type.
 template <typename T>
 __device__ __forceinline__ T weight_at(const LevelView<T> &L, size_t o) {
-    return L.wb ? T(__bfloat162float(L.wb[o])) : L.w[o];
+    const size_t lim = (size_t)L.n * L.pitch;
+    return L.wb ? T(__bfloat162float(ldc(L.wb, o, lim, kDbgSnapshot))) : ldc(L.w, o, lim, kDbgSnapshot);
 }
 
 // ---- launchers (each enqueues on `st`) -------------------------------------------------

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_omega_infer(LevelView<T> L, const __nv_
                 for (int di = 0; di < 3; ++di)
                     for (int dj = 0; dj < 3; ++dj)
                         z = fmaf(S.W[oW3 + (i * 3 + di) * 3 + dj], __bfloat162float(S.A2[r + di][c + dj][i]), z);
-            omega[(size_t)gi * p + gj] = T(2.f / (1.f + expf(-z)));
+            stc(omega, (size_t)gi * p + gj, (size_t)n * p, kDbgOther, T(2.f / (1.f + expf(-z))));
         }
     }
 }

@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(128) k_gsline(LevelView<T> L, int parity, T *_
                 di = fma_rn(-wgt, cup_prev, di);
                 rhs = fma_rn(-wgt, crh_prev, rhs);
             }
-            dg[o] = di;
-            rg[o] = rhs;
+            stc(dg, o, (size_t)n * p, kDbgOther, di);
+            stc(rg, o, (size_t)n * p, kDbgOther, rhs);
             cup_prev = up;
             cdi_prev = di;
             crh_prev = rhs;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(128) k_gsline(LevelView<T> L, int parity, T *_
         g_next = g[R < n - i0 ? R : n - i0];
     }
     T x = div_relax(crh_prev, cdi_prev);
-    L.u[(size_t)(n - 1) * p + j] = x;
+    stc(L.u, (size_t)(n - 1) * p + j, (size_t)n * p, kDbgOther, x);
     for (int i1 = n - 2; i1 >= 0; i1 -= R) {
         T gg[R + 1], d[R], rr[R];
 #pragma unroll
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(128) k_gsline(LevelView<T> L, int parity, T *_
             if (i < 0) break;
             const T up = mul_rn(L.cdiff, face(gg[r], g_below, true));
             x = div_relax(fma_rn(-up, x, rr[r]), d[r]);
-            L.u[(size_t)i * p + j] = x;
+            stc(L.u, (size_t)i * p + j, (size_t)n * p, kDbgOther, x);
             g_below = gg[r];
         }
     }
@@ -167,10 +167,10 @@ __global__ void __launch_bounds__(256) k_hs1(LevelView<T> L, int ci, int cj) {
         den += cP[t] * c[back] / S;
     }
     const T xP = (rP + num) / den;
-    L.u[o] = xP;
+    stc(L.u, o, (size_t)n * p, kDbgOther, xP);
     for (int t = 0; t < 4; ++t) {
         if (!leaf[t]) continue;
-        L.u[(size_t)(i + di[t]) * p + (j + dj[t])] = (cl[t] * xP - rl[t]) / Sl[t];
+        stc(L.u, (size_t)(i + di[t]) * p + (j + dj[t]), (size_t)n * p, kDbgOther, (cl[t] * xP - rl[t]) / Sl[t]);
     }
 }
 

@@ -22,7 +22,8 @@ struct Taps {
 template <typename T>
 __global__ void k_copy(const T *src, int ps, T *dst, int pd, int n, int m) {
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
-    if (i < n && j < m) dst[(size_t)i * pd + j] = src[(size_t)i * ps + j];
+    if (i < n && j < m)
+        stc(dst, (size_t)i * pd + j, (size_t)n * pd, kDbgSetup, ldc(src, (size_t)i * ps + j, (size_t)n * ps, kDbgSetup));
 }
 
 // Separable Gaussian G_sigma * z with mirror boundary; `dir` 0 = along rows, 1 = along columns.
@@ -30,13 +31,14 @@ template <typename T>
 __global__ void k_blur(const T *src, T *dst, int n, int m, int ps, int pd, Taps tp, int R, int dir) {
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
     if (i >= n || j >= m) return;
+    const size_t lim = (size_t)n * ps;
     double a = 0.0;
     for (int t = -R; t <= R; ++t) {
-        double v = dir == 0 ? (double)src[(size_t)i * ps + mirror(j + t, m)]
-                            : (double)src[(size_t)mirror(i + t, n) * ps + j];
+        double v = dir == 0 ? (double)ldc(src, (size_t)i * ps + mirror(j + t, m), lim, kDbgSetup)
+                            : (double)ldc(src, (size_t)mirror(i + t, n) * ps + j, lim, kDbgSetup);
         a += tp.w[t + R] * v;
     }
-    dst[(size_t)i * pd + j] = (T)a;
+    stc(dst, (size_t)i * pd + j, (size_t)n * pd, kDbgSetup, (T)a);
 }
 
 // Edge detector g = 1 / (1 + beta_edge |grad (G*z)|^2) (central differences, mirror ghosts),
@@ -57,8 +59,9 @@ __global__ void k_edge_distance(const T *zb, T *w, T *d, int n, int m, int p, do
         dd *= T(1) - exp(-dx * dx * inv_s2) * exp(-dy * dy * inv_s2);
     }
     size_t o = (size_t)i * p + j;
-    d[o] = dd;
-    w[o] = model == 1 ? dd * g : g;
+    const size_t lim = (size_t)n * p;
+    stc(d, o, lim, kDbgSetup, dd);
+    stc(w, o, lim, kDbgSetup, model == 1 ? dd * g : g);
 }
 
 // Signed distance (px, positive inside) to the boundary of a convex polygon given counter-
@@ -87,8 +90,9 @@ __global__ void k_initial_phi(T *pn, T *u, int n, int m, int p, const double *hu
         val = inside ? dmin : -dmin;
     }
     size_t o = (size_t)i * p + j;
-    pn[o] = val;
-    u[o] = T(0);
+    const size_t lim = (size_t)n * p;
+    stc(pn, o, lim, kDbgSetup, val);
+    stc(u, o, lim, kDbgSetup, T(0));
 }
 
 // Fitting field of the step: lambda1 (z - c1)^2 - lambda2 (z - c2)^2 (+ theta d for SC).
@@ -100,7 +104,7 @@ __global__ void k_fitting(LevelView<T> L, const Scalars *sc, ModelParams mp) {
     double z = (double)L.z[o], c1 = sc->c1, c2 = sc->c2;
     double F = mp.lambda1 * (z - c1) * (z - c1) - mp.lambda2 * (z - c2) * (z - c2);
     if (mp.model == 0) F += mp.theta * (double)L.d[o];
-    L.F[o] = (T)F;
+    stc(L.F, o, (size_t)L.n * L.pitch, kDbgSetup, (T)F);
 }
 
 // phi^n <- phi^n + u, u <- 0 (start of a pseudo-time step on the finest grid).
@@ -109,8 +113,9 @@ __global__ void k_fold(LevelView<T> L) {
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
     if (i >= L.n || j >= L.m) return;
     size_t o = (size_t)i * L.pitch + j;
-    L.pn[o] = add_rn(L.pn[o], L.u[o]);
-    L.u[o] = T(0);
+    const size_t lim = (size_t)L.n * L.pitch;
+    stc(L.pn, o, lim, kDbgSetup, add_rn(L.pn[o], L.u[o]));
+    stc(L.u, o, lim, kDbgSetup, T(0));
 }
 
 __device__ double block_sum_setup(double v, double *red) {
@@ -262,12 +267,12 @@ __global__ void k_mask(LevelView<T> L, uint8_t *mask) {
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
     if (i >= L.n || j >= L.m) return;
     size_t o = (size_t)i * L.pitch + j;
-    mask[(size_t)i * L.m + j] = add_rn(L.pn[o], L.u[o]) > T(0) ? 1 : 0;
+    stc(mask, (size_t)i * L.m + j, (size_t)L.n * L.m, kDbgSetup, (uint8_t)(add_rn(L.pn[o], L.u[o]) > T(0) ? 1 : 0));
 }
 
 __global__ void k_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, int p) {
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
-    if (i < n && j < m) dst[(size_t)i * p + j] = __float2bfloat16_rn(src[(size_t)i * p + j]);
+    if (i < n && j < m) stc(dst, (size_t)i * p + j, (size_t)n * p, kDbgSetup, __float2bfloat16_rn(src[(size_t)i * p + j]));
 }
 
 inline dim3 grid2(int n, int m) { return dim3((m + 31) / 32, (n + 7) / 8); }

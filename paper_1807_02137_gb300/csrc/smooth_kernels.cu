@@ -101,10 +101,12 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_snapshot(LevelView<T> L, c
             ds = fma_rn(aE, sub_rn(sP[a][b + 1], pc), ds);
             ds = fma_rn(aW, sub_rn(sP[a][b - 1], pc), ds);
             size_t o = (size_t)gi * p + gj;
-            T base = add_rn(kStage ? sF[kStage ? ti : 0][kStage ? lane : 0] : L.F[o], ar);
-            if (L.has_rhs) base = add_rn(base, kStage ? sR[kStage ? ti : 0][kStage ? lane : 0] : L.rhs[o]);
-            L.f[o] = fma_rn(-L.cdiff, ds, base);
-            L.G[o] = gc;
+            const size_t lim = (size_t)n * p;
+            T base = add_rn(kStage ? sF[kStage ? ti : 0][kStage ? lane : 0] : ldc(L.F, o, lim, kDbgSnapshot), ar);
+            if (L.has_rhs)
+                base = add_rn(base, kStage ? sR[kStage ? ti : 0][kStage ? lane : 0] : ldc(L.rhs, o, lim, kDbgSnapshot));
+            stc(L.f, o, lim, kDbgSnapshot, fma_rn(-L.cdiff, ds, base));
+            stc(L.G, o, lim, kDbgSnapshot, gc);
             // jump set D (Sec. 4.1): max > Sigma * min over the faces inside the domain;
             // smallest coefficient with ties to the earlier of A, B, C, D (Sec. 4.1.3).
             const T big = T(3.0e38);
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_snapshot(LevelView<T> L, c
             const int am = vS == mn ? 0 : (vN == mn ? 1 : (vE == mn ? 2 : 3));
             const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
             if (cnt >= 2 && mx > mul_rn(L.Sigma, mn)) star = (uint8_t)(1u << am);
-            if (L.cls) L.cls[o] = star;
+            if (L.cls) stc(L.cls, o, lim, kDbgSnapshot, star);
         }
         sStar[ti][lane] = star;
         const uint32_t bA = __ballot_sync(0xffffffffu, star & 1u), bB = __ballot_sync(0xffffffffu, star & 2u);
@@ -134,9 +136,10 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_snapshot(LevelView<T> L, c
         const int line = wy + WARPS * ((lane >> 1) % RPW), s = lane & 1;
         const uint32_t mk = members_of(bits, row ? lenr : lenc);
         if (row) {
-            if (i0 + line < n) L.mrow[((size_t)s * n + i0 + line) * L.npm + (j0 >> 5)] = mk;
+            if (i0 + line < n)
+                stc(L.mrow, ((size_t)s * n + i0 + line) * L.npm + (j0 >> 5), (size_t)2 * n * L.npm, kDbgMaskStore, mk);
         } else if (j0 + line < m) {
-            L.mcol[((size_t)s * m + j0 + line) * L.npn + (i0 >> 5)] = mk;
+            stc(L.mcol, ((size_t)s * m + j0 + line) * L.npn + (i0 >> 5), (size_t)2 * m * L.npn, kDbgMaskStore, mk);
         }
     }
 }
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(256) k_rb(LevelView<T> L, int colour, int swee
     T aE = face(gc, L.G[oE], hE), aW = face(gc, L.G[oW], hW);
     T v = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, L.u[oS], L.u[oN], L.u[oE], L.u[oW], L.f[o]);
     if (L.omega) v = relax_weighted(L.omega[o], v, L.u[o]);
-    L.u[o] = v;
+    stc(L.u, o, (size_t)n * p, kDbgSweep, v);
 }
 
 // One warp per (line, 32-cell piece), solved together by pcr_piece; groups are read from upre
@@ -177,8 +180,8 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
     auto cell = [&](int t) -> size_t {
         return rowwise ? (size_t)line * p + (t0 + t) : (size_t)(t0 + t) * p + line;
     };
-    const uint32_t mask = rowwise ? L.mrow[((size_t)sweep * n + line) * L.npm + piece]
-                                  : L.mcol[((size_t)(sweep - 2) * m + line) * L.npn + piece];
+    const uint32_t mask = rowwise ? ldc(L.mrow, ((size_t)sweep * n + line) * L.npm + piece, (size_t)2 * n * L.npm, kDbgMaskLoad)
+                                  : ldc(L.mcol, ((size_t)(sweep - 2) * m + line) * L.npn + piece, (size_t)2 * m * L.npn, kDbgMaskLoad);
     if (!mask) return;   // the whole warp
     const T *up = L.upre;
     auto at = [&](int t) -> RunCell<T> {
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(256) k_seg(LevelView<T> L, int sweep, int pari
     if (t0 > 0) endp = up[rowwise ? (size_t)line * p + t0 - 1 : (size_t)(t0 - 1) * p + line];
     if (t0 + len < llen) endn = up[rowwise ? (size_t)line * p + t0 + len : (size_t)(t0 + len) * p + line];
     T x;
-    if (pcr_piece<T>(mask, len, L.cdiff, L.inv_tau, own, endp, endn, at, x)) L.u[cell(lane)] = x;
+    if (pcr_piece<T>(mask, len, L.cdiff, L.inv_tau, own, endp, endn, at, x)) stc(L.u, cell(lane), (size_t)n * p, kDbgSweep, x);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -309,7 +312,8 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
             const int q = tid + (k0 + k) * kThreads;
             const int a = q / NV, b0 = (q % NV) * VN;
             const int gi = i0 - kH + a, gj = j0 - kH + b0;
-            if (k0 + k < PER && q < NVEC && gi >= 0 && gi < n && gj >= 0 && gj < p) {
+            if (k0 + k < PER && q < NVEC && gi >= 0 && gi < n && gj >= 0 && gj < p &&
+                MG_DBG_OK((size_t)gi * p + gj + VN - 1, (size_t)n * p, kDbgSweep)) {
                 const size_t o = (size_t)gi * p + gj;
                 x[k][0] = __ldg(reinterpret_cast<const V *>(uin + o));
                 x[k][1] = __ldg(reinterpret_cast<const V *>(L.G + o));
@@ -340,7 +344,8 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
             const int a = q / kRowPieces, pc = q % kRowPieces;
             const int gi = i0 - kH + a, piece = (j0 >> 5) - 1 + pc;
             uint32_t w = 0;
-            if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm)
+            if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm &&
+                MG_DBG_OK(((size_t)SWEEP * n + gi) * L.npm + piece, (size_t)2 * n * L.npm, kDbgMaskLoad))
                 w = __ldg(L.mrow + ((size_t)SWEEP * n + gi) * L.npm + piece);
             S.mk[a][pc] = w;
             lm |= solves_word<kH, kOH, kOW, true>(a, pc, w);
@@ -350,7 +355,8 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
             const int b = q / kColPieces, pc = q % kColPieces;
             const int gj = j0 - kH + b, piece = (i0 >> 5) - 1 + pc;
             uint32_t w = 0;
-            if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn)
+            if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn &&
+                MG_DBG_OK(((size_t)(SWEEP - 2) * m + gj) * L.npn + piece, (size_t)2 * m * L.npn, kDbgMaskLoad))
                 w = __ldg(L.mcol + ((size_t)(SWEEP - 2) * m + gj) * L.npn + piece);
             S.mk[b][pc] = w;
             lm |= solves_word<kH, kOH, kOW, false>(b, pc, w);
@@ -381,6 +387,7 @@ __global__ void __launch_bounds__(TS::NT) k_sweep(LevelView<T> L) {
         const int a = kH + q / NVO, b0 = kH + (q % NVO) * VN;
         const int gi = i0 + q / NVO, gj = j0 + (q % NVO) * VN;
         if (gi >= n || gj >= p) continue;
+        if (!MG_DBG_OK((size_t)gi * p + gj + VN - 1, (size_t)n * p, kDbgSweep)) continue;
         T uu[VN];
         for (int e = 0; e < VN; ++e) uu[e] = SW_AT(u, a, b0 + e);
         V xv;

@@ -134,7 +134,7 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
                               u[a][b - 1], f[a][b]);
         if (WEIGHTED) {
             const size_t o = (size_t)(i0 - kH + a) * L.pitch + (j0 - kH + b);
-            v = relax_weighted(__ldg(L.omega + o), v, u[a][b]);
+            v = relax_weighted(ldc(L.omega, o, (size_t)L.n * L.pitch, kDbgSweep), v, u[a][b]);
         }
         u[a][b] = v;
     }
@@ -174,12 +174,14 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
             if (rowwise) {
                 const int a = q / kRowPieces, pc = q % kRowPieces;
                 const int gi = i0 - kH + a, piece = (j0 >> 5) - 1 + pc;
-                if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm)
+                if (gi >= 0 && gi < n && piece >= 0 && piece < L.npm &&
+                    MG_DBG_OK(((size_t)SWEEP * n + gi) * L.npm + piece, (size_t)2 * n * L.npm, kDbgMaskLoad))
                     w[r] = __ldg(L.mrow + ((size_t)SWEEP * n + gi) * L.npm + piece);
             } else {
                 const int b = q / kColPieces, pc = q % kColPieces;
                 const int gj = j0 - kH + b, piece = (i0 >> 5) - 1 + pc;
-                if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn)
+                if (gj >= 0 && gj < m && piece >= 0 && piece < L.npn &&
+                    MG_DBG_OK(((size_t)(SWEEP - 2) * m + gj) * L.npn + piece, (size_t)2 * m * L.npn, kDbgMaskLoad))
                     w[r] = __ldg(L.mcol + ((size_t)(SWEEP - 2) * m + gj) * L.npn + piece);
             }
         }
@@ -271,6 +273,7 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
             const int a = kH + q / NVO, b0 = kH + (q % NVO) * 4;
             const int gi = i0 + q / NVO, gj = j0 + (q % NVO) * 4;
             if (gi >= n || gj >= p) continue;
+            if (!MG_DBG_OK((size_t)gi * p + gj + 3, (size_t)n * p, kDbgSweep)) continue;
             *reinterpret_cast<float4 *>(uout + (size_t)gi * p + gj) = *reinterpret_cast<const float4 *>(&u[a][b0]);
         }
         __syncthreads();   // the stage is free for the next copy into it

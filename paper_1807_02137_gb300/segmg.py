@@ -22,7 +22,7 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
           -5: "MG_ERR_TIMEOUT", -6: "MG_ERR_NOT_SPD", -7: "MG_ERR_NOMEM", -8: "MG_ERR_STATE"}
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
-           "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_inject_divergence", "mg_segment_host", "mg_get_stream", "mg_destroy",
+           "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_inject_divergence", "mg_debug_status", "mg_debug_selftest", "mg_segment_host", "mg_get_stream", "mg_destroy",
            "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_set_cluster_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
            "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_set_loss", "mg_trainer_grad",
            "mg_trainer_train", "mg_trainer_get", "mg_trainer_destroy",
@@ -68,16 +68,31 @@ class SegmgError(RuntimeError):
         super().__init__(f"{where}: {ERRORS.get(code, code)} ({detail})")
 
 
+class DebugInfo(C.Structure):
+    """mg_debug_info: the device error words of the bounds-checked (MG_DEBUG) build."""
+    _fields_ = [("enabled", C.c_int), ("first_site", C.c_int), ("first_index", C.c_longlong),
+                ("sites", C.c_ulonglong), ("count", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
+
+
+def library_path():
+    """The library this process loads: the bounds-checked build when SEGMG_DEBUG=1."""
+    return _build.LIB_DEBUG if os.environ.get("SEGMG_DEBUG") == "1" else _build.LIB
 
 
 def lib():
     """Loads the built library (no build here: a missing library is an error)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"CUDA library not built: {_build.LIB} (run paper_1807_02137_gb300.build())")
-        L = C.CDLL(_build.LIB)
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run paper_1807_02137_gb300.build())")
+        L = C.CDLL(path)
         vp, i, d = C.c_void_p, C.c_int, C.c_double
         P = C.POINTER(Params)
         D = C.POINTER(C.c_double)
@@ -98,6 +113,8 @@ def lib():
             "mg_get_stats": ([vp, C.POINTER(Stats)], i),
             "mg_set_wait_limit": ([vp, C.c_longlong], i),
             "mg_inject_divergence": ([vp, i], i),
+            "mg_debug_status": ([C.POINTER(DebugInfo), i], i),
+            "mg_debug_selftest": ([], i),
             "mg_segment_host": ([vp, i, i, D, i, P, d, i, d, i, vp, vp, C.POINTER(Stats)], i),
             "mg_get_stream": ([vp], vp),
             "mg_time_kernels": ([vp, i, i, D], i),
@@ -141,6 +158,20 @@ def lib():
 def _check(rc, where):
     if rc != 0:
         raise SegmgError(rc, where, lib().mg_last_error().decode())
+
+
+def debug_status(clear=False) -> dict:
+    """mg_debug_status: out-of-range indices the bounds-checked build recorded (enabled = 0 in
+    the default build); clear=True zeroes the device words after reading them."""
+    d = DebugInfo()
+    _check(lib().mg_debug_status(C.byref(d), 1 if clear else 0), "mg_debug_status")
+    return d.as_dict()
+
+
+def debug_selftest():
+    """mg_debug_selftest: records one out-of-range index (no memory access) in the bounds-checked
+    build, to test the reporting path; nothing in the default build."""
+    _check(lib().mg_debug_selftest(), "mg_debug_selftest")
 
 
 def default_params(n, m, **kw) -> Params:

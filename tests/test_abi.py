@@ -43,13 +43,15 @@ def test_library_loads_and_binding_matches_struct_layouts(libpath):
         assert hasattr(L, name)
     # sizes of the C structs, compiled with the host compiler from the header
     code = ('#include <stdio.h>\n#include "segmg.h"\n'
-            'int main(){printf("%zu %zu %zu", sizeof(mg_params), sizeof(mg_stats), sizeof(mg_allocator));}')
+            'int main(){printf("%zu %zu %zu %zu", sizeof(mg_params), sizeof(mg_stats), sizeof(mg_allocator),'
+            ' sizeof(mg_debug_info));}')
     exe = os.path.join(os.path.dirname(libpath), "abi_sizes")
     subprocess.run(["gcc", "-x", "c", "-", "-I", os.path.join(ROOT, "include"), "-o", exe], input=code,
                    text=True, check=True)
     sizes = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     assert int(sizes[0]) == ctypes.sizeof(segmg.Params)
     assert int(sizes[1]) == ctypes.sizeof(segmg.Stats)
+    assert int(sizes[3]) == ctypes.sizeof(segmg.DebugInfo)
 
 
 def test_host_only_calls_without_a_gpu(libpath):
@@ -77,3 +79,25 @@ def test_noalloc_binding_refuses_mismatched_tensors_before_any_call(libpath):
         segmg.residual_norm_noalloc(f64, f64, torch.zeros(8, 16, dtype=torch.float64)[:, ::2], p)
     with pytest.raises(TypeError, match="CUDA"):
         segmg.residual_norm_noalloc(f64, f64, f64, p)
+
+
+def test_default_build_reports_no_bounds_checks(libpath):
+    # the default library has no checks: mg_debug_status says so without touching the device,
+    # and the self-test of the reporting path does nothing
+    from paper_1807_02137_gb300 import segmg
+    if os.environ.get("SEGMG_DEBUG") == "1":
+        pytest.skip("the bounds-checked library is selected")
+    d = segmg.debug_status()
+    assert d == {"enabled": 0, "first_site": -1, "first_index": 0, "sites": 0, "count": 0}
+    segmg.debug_selftest()
+    assert segmg.lib().mg_debug_status(None, 0) == -1
+
+
+def test_bounds_checked_build_compiles_and_exports_every_symbol():
+    # -DMG_DEBUG variant: its own objects, the same C ABI
+    from paper_1807_02137_gb300 import buildlib
+    path = buildlib.build(debug=True)
+    assert path.endswith("libsegmg_debug.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (mg_\w+)", out))
+    assert not set(declared_functions()) - exported
