@@ -189,6 +189,7 @@ struct Level {
     __nv_bfloat16 *wb = nullptr;   // mixed precision only
     uint8_t *cls = nullptr;        // Hybrid Smoother 1 only
     SweepMaps maps[kTileShapes];   // FP32 storage: tensor maps of the TMA sweep, per tile shape
+    SnapMaps smaps;                // FP32 storage: tensor maps of the TMA snapshot
 };
 
 template <typename T>
@@ -363,6 +364,9 @@ struct Solver final : SolverBase {
                     for (int sh = 0; sh < kTileShapes; ++sh)
                         if (!encode_sweep_maps(view(l), sh, &lv[l].maps[sh]))
                             return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a grid");
+            for (int l = 0; l < nlev; ++l)
+                if (!encode_snapshot_maps(view(l), &lv[l].smaps))
+                    return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a grid (snapshot)");
         }
         // default tile shapes (what mg_autotune chooses on grids up to 1024^2): 32 x 32 tiles (256
         // threads on the finest grid, 512 below) where they all fit one wave of 8 blocks per SM;
@@ -454,7 +458,7 @@ struct Solver final : SolverBase {
         int it = 0;
         while (it < max_iter) {
             area_term(0, lv[0].u);
-            launch_snapshot<T>(view(0), area_ptr(), st);
+            snapshot(0, view(0));
             launch_aos_iteration<T>(view(0), area_ptr(), dt, partials, dsc->aos, st);
             launches += area_launches() + 4;
             ++it;
@@ -628,6 +632,13 @@ struct Solver final : SolverBase {
         return k;
     }
 
+    // The coefficient snapshot of grid l (v = view(l)): TMA-staged for FP32 storage.
+    void snapshot(int l, const LevelView<T> &v) {
+        if constexpr (std::is_same<T, float>::value)
+            launch_snapshot_tma(v, area_ptr(), lv[l].smaps, &dsc->err, wait_limit, st);
+        else launch_snapshot<T>(v, area_ptr(), st);
+    }
+
     // One directional sweep k of grid l with tile shape sh.
     void sweep(int l, const LevelView<T> &v, int k, int sh) {
         if (p.smoother == MG_SMOOTH_PHASED) {
@@ -656,7 +667,7 @@ struct Solver final : SolverBase {
         Range range("smoothing iteration");
         area_term(l, lv[l].u);
         LevelView<T> v = view(l);
-        launch_snapshot<T>(v, area_ptr(), st);
+        snapshot(l, v);
         if (use_omega && infer_pending[l] && omega_buf[l]) {
             launch_omega_infer<T>(v, net, omega_buf[l], st);   // weights from this snapshot's G
             infer_pending[l] = false;
@@ -758,7 +769,7 @@ struct Solver final : SolverBase {
                 auto enqueue = [&]() {
                     for (int r = 0; r < reps; ++r) {
                         area_term(l, L.u);
-                        launch_snapshot<T>(v, area_ptr(), st);
+                        snapshot(l, v);
                         for (int k = 0; k < 4; ++k) sweep(l, v, k, sh);
                     }
                 };
@@ -1256,7 +1267,7 @@ struct Solver final : SolverBase {
         for (int r = 0; r < reps; ++r) {
             area_term(l, lv[l].u);
             cudaEventRecord(ev[0], st);
-            launch_snapshot<T>(v, area_ptr(), st);
+            snapshot(l, v);
             cudaEventRecord(ev[1], st);
             if (p.smoother == MG_SMOOTH_GSLINE || p.smoother == MG_SMOOTH_HS1) {
                 relax(l, v, shape[l]);        // the whole smoother in the first slot
@@ -1693,6 +1704,7 @@ int mg_setup(mg_handle *out, const void *image, int n, int m, const double *mark
     prepare_coarse_kernels();
     prepare_bottom_kernel();
     prepare_sweep_tma();
+    prepare_snapshot_tma();
     prepare_learned_kernels();
     SolverBase *s = nullptr;
     if (p->precision != MG_F64) {
@@ -2054,6 +2066,7 @@ int mg_batch_setup(mg_batch *out, int count, const void *const *images, const in
     prepare_coarse_kernels();
     prepare_bottom_kernel();
     prepare_sweep_tma();
+    prepare_snapshot_tma();
     prepare_learned_kernels();
     auto *B = new mg_batch_s();
     Batch &b = B->b;

@@ -153,8 +153,27 @@ struct SweepMaps {
     alignas(64) unsigned char G[128];
     alignas(64) unsigned char f[128];
 };
+// Tensor maps of the TMA-staged snapshot of one FP32 grid (snapshot_tma.cu): pn, u and w boxes
+// of 36 rows (w in BF16 when mixed), F and rhs tiles of 32 x 32.
+struct SnapMaps {
+    alignas(64) unsigned char P[128];
+    alignas(64) unsigned char U[128];
+    alignas(64) unsigned char W[128];
+    alignas(64) unsigned char F[128];
+    alignas(64) unsigned char R[128];
+    bool mixed = false;
+};
+void prepare_snapshot_tma();
+bool encode_snapshot_maps(const LevelView<float> &L, SnapMaps *M);
+// The snapshot of an FP32 grid (the operations of launch_snapshot); a copy that does not
+// complete within wait_limit try_wait rounds sets bit 4 of *err.
+void launch_snapshot_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err,
+                         long long wait_limit, cudaStream_t st);
 void prepare_sweep_tma();
 bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M);
+// One n x m grid function (FP32: elem 4, BF16: elem 2) with row pitch `pitch` elements as a 2-D
+// tensor map with box RW x RH (zero fill outside the grid); false when the driver refuses it.
+bool encode_map_2d(void *out, void *base, int elem, int n, int m, int pitch, int RH, int RW);
 constexpr long long kDefaultWaitLimit = 1LL << 22;   // try_wait rounds before a TMA wait gives up
 void launch_sweep_tma(const LevelView<float> &L, int sweep, int shape, const SweepMaps &M, int *err,
                       long long wait_limit, cudaStream_t st);

@@ -478,8 +478,7 @@ void prepare_smoother_kernels() {
     set_fused_attrs<float, Tile3>(); set_fused_attrs<float, Tile4>(); set_fused_attrs<float, Tile5>();
     set_fused_attrs<double, Tile0>(); set_fused_attrs<double, Tile1>(); set_fused_attrs<double, Tile2>();
     set_fused_attrs<double, Tile3>(); set_fused_attrs<double, Tile4>(); set_fused_attrs<double, Tile5>();
-    (void)snap_occ<float>();   // snapshot occupancy, measured here rather than inside a capture
-    (void)snap_occ<double>();
+    (void)snap_occ<double>();   // snapshot occupancy, measured here rather than inside a capture
 }
 
 template <typename T, int SW, typename TS>
@@ -509,7 +508,6 @@ void launch_sweep_fused(const LevelView<T> &L, int sweep, int shape, cudaStream_
     else launch_fused_shape<T, Tile0>(L, sweep, st);
 }
 
-template void launch_snapshot<float>(const LevelView<float> &, const double *, cudaStream_t);
 template void launch_snapshot<double>(const LevelView<double> &, const double *, cudaStream_t);
 template void launch_sweep_phased<float>(const LevelView<float> &, int, cudaStream_t);
 template void launch_sweep_phased<double>(const LevelView<double> &, int, cudaStream_t);

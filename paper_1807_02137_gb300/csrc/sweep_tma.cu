@@ -23,6 +23,7 @@
 
 #include "arith.cuh"
 #include "line_phase.cuh"
+#include "tma.cuh"
 
 namespace segmg {
 
@@ -56,47 +57,6 @@ struct TmaSmem {
     unsigned long long bar[STAGES];            // one mbarrier per stage
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Bounded wait for the completion of phase `parity` (at most `limit` try_wait rounds); false on
-// time-out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
-    const unsigned a = smem_u32(bar);
-    for (long long it = 0; it < limit; ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n.reg .pred p;\n"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// 2-D tiled TMA load of the box at column x, row y (elements; x * 4 bytes is a multiple of 16)
-// into dst, completing on bar.
-__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
 
 template <typename TS, int STAGES, bool ROWWISE>
 __device__ __forceinline__ bool member(const TmaSmem<TS, STAGES> &S, int a, int b) {
@@ -353,18 +313,8 @@ EncodeFn encoder() {
     return fn;
 }
 
-// One FP32 n x m grid function with row pitch `pitch` (elements) as a 2-D tensor, box RW x RH,
-// zero fill outside.
 bool encode(void *out, float *base, int n, int m, int pitch, int RH, int RW) {
-    EncodeFn fn = encoder();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
-    cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)RW, (cuuint32_t)RH};
-    cuuint32_t estr[2] = {1, 1};
-    return fn(reinterpret_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return encode_map_2d(out, base, 4, n, m, pitch, RH, RW);
 }
 
 template <typename TS>
@@ -376,6 +326,21 @@ bool encode_shape(const LevelView<float> &L, SweepMaps &M) {
 int g_sms = 0;
 
 }  // namespace
+
+// One n x m grid function (FP32, elem = 4, or BF16, elem = 2) with row pitch `pitch` (elements) as
+// a 2-D tensor, box RW x RH, zero fill outside.
+bool encode_map_2d(void *out, void *base, int elem, int n, int m, int pitch, int RH, int RW) {
+    EncodeFn fn = encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * (cuuint64_t)elem};
+    cuuint32_t box[2] = {(cuuint32_t)RW, (cuuint32_t)RH};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(reinterpret_cast<CUtensorMap *>(out),
+              elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides,
+              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 void prepare_sweep_tma() {
     set_attrs<TT0>(); set_attrs<TT1>(); set_attrs<TT2>(); set_attrs<TT3>(); set_attrs<TT4>(); set_attrs<TT5>();
