@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsegmg.so")
 LIB_DEBUG = os.path.join(OUT_DIR, "libsegmg_debug.so")
-SOURCES = ["host.cu", "smooth_kernels.cu", "cycle_kernels.cu", "setup_kernels.cu", "bottom_kernel.cu", "sweep_tma.cu", "snapshot_tma.cu", "line_smoothers.cu", "aos_kernels.cu", "learned.cu", "noalloc.cu"]
+SOURCES = ["host.cu", "smooth_kernels.cu", "cycle_kernels.cu", "setup_kernels.cu", "bottom_kernel.cu", "sweep_tma.cu", "snapshot_tma.cu", "residual_tma.cu", "line_smoothers.cu", "aos_kernels.cu", "learned.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -252,6 +252,20 @@ __device__ __forceinline__ void load_tile32(T (*dA)[33], const T *sA, T (*dB)[33
     }
 }
 
+// One-dimensional full-weighting taps (Sec. 3.1): coarse I sits on fine 2I+1; (1/4, 1/2, 1/4)
+// on 2I, 2I+1, 2I+2, or (1/2, 1/2) on 2I, 2I+1 when fine 2I+2 does not exist.
+__device__ __forceinline__ int fw_taps(int I, int n, int *idx, float *wt) {
+    int q = 2 * I + 1;
+    if (q + 1 < n) {
+        idx[0] = q - 1; idx[1] = q; idx[2] = q + 1;
+        wt[0] = 0.25f; wt[1] = 0.5f; wt[2] = 0.25f;
+        return 3;
+    }
+    idx[0] = q - 1; idx[1] = q;
+    wt[0] = 0.5f; wt[1] = 0.5f;
+    return 2;
+}
+
 // Sum of squares of the residual values a thread visits: accumulated in the storage precision
 // (a handful of values per thread), then widened to FP64 for the block and grid reductions.
 // FP64 arithmetic is slow on this GPU, so the per-cell work stays in FP32 on the FP32 path.

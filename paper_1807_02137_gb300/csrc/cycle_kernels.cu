@@ -85,8 +85,6 @@ __global__ void __launch_bounds__(256, MINB)
     }
 }
 
-__device__ __forceinline__ int fw_taps(int I, int n, int *idx, float *wt);
-
 // Loads the window dst[a][b] = src[clamp(r0 + a)][clamp(c0 + b)], a < ROWS, b < COLS, of one or
 // two pitched FP32 grid functions (indices clamped into the grid: the mirror ghosts), with
 // 16-byte vector loads where the window lies inside; c0 mod 4 == OFF.  NT threads.
@@ -215,20 +213,6 @@ __global__ void k_sum_partials(const double *partials, int np, double *out) {
     if (threadIdx.x == 0) *out = s;
 }
 
-// One-dimensional full-weighting taps (Sec. 3.1): coarse I sits on fine 2I+1; (1/4, 1/2, 1/4)
-// on 2I, 2I+1, 2I+2, or (1/2, 1/2) on 2I, 2I+1 when fine 2I+2 does not exist.
-__device__ __forceinline__ int fw_taps(int I, int n, int *idx, float *wt) {
-    int q = 2 * I + 1;
-    if (q + 1 < n) {
-        idx[0] = q - 1; idx[1] = q; idx[2] = q + 1;
-        wt[0] = 0.25f; wt[1] = 0.5f; wt[2] = 0.25f;
-        return 3;
-    }
-    idx[0] = q - 1; idx[1] = q;
-    wt[0] = 0.5f; wt[1] = 0.5f;
-    return 2;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(const T *f, int n, int m, int pf, T *c, T *c2, int pc) {
     const int J = blockIdx.x * 32 + threadIdx.x, I = blockIdx.y * 8 + threadIdx.y;
@@ -350,6 +334,10 @@ void launch_interp_add(const LevelView<T> &Lf, const LevelView<T> &Lc, cudaStrea
 }
 
 constexpr size_t kCoarseSmemMax = 200 * 1024;
+
+void launch_sum_partials(const double *partials, int np, double *out, cudaStream_t st) {
+    k_sum_partials<<<1, 1024, 0, st>>>(partials, np, out);
+}
 
 void launch_residual_restrict(const LevelView<float> &L, const LevelView<float> &C, const double *area,
                               cudaStream_t st) {

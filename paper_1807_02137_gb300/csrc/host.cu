@@ -190,6 +190,7 @@ struct Level {
     uint8_t *cls = nullptr;        // Hybrid Smoother 1 only
     SweepMaps maps[kTileShapes];   // FP32 storage: tensor maps of the TMA sweep, per tile shape
     SnapMaps smaps;                // FP32 storage: tensor maps of the TMA snapshot
+    ResMaps rmaps;                 // FP32 storage: tensor maps of the TMA residual kernels
 };
 
 template <typename T>
@@ -365,8 +366,8 @@ struct Solver final : SolverBase {
                         if (!encode_sweep_maps(view(l), sh, &lv[l].maps[sh]))
                             return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a grid");
             for (int l = 0; l < nlev; ++l)
-                if (!encode_snapshot_maps(view(l), &lv[l].smaps))
-                    return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a grid (snapshot)");
+                if (!encode_snapshot_maps(view(l), &lv[l].smaps) || !encode_residual_maps(view(l), &lv[l].rmaps))
+                    return fail(MG_ERR_CUDA, "cuTensorMapEncodeTiled failed for a grid (snapshot, residual)");
         }
         // default tile shapes (what mg_autotune chooses on grids up to 1024^2): 32 x 32 tiles (256
         // threads on the finest grid, 512 below) where they all fit one wave of 8 blocks per SM;
@@ -470,7 +471,7 @@ struct Solver final : SolverBase {
             if (std::sqrt(s2[0]) <= eta_stop * std::sqrt(s2[1])) break;
         }
         area_term(0, lv[0].u);
-        launch_residual<T>(view(0), lv[0].u, area_ptr(), lv[0].r, 0, partials, npart, &dsc->norm2, st);
+        norm_residual(&dsc->norm2);
         launches += area_launches() + 2;
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -598,7 +599,7 @@ struct Solver final : SolverBase {
         }
         for (int l = 0; l < nlev; ++l) launch_fitting<T>(view(l), dsc, mp, st);
         area_term(0, lv[0].u);
-        launch_residual<T>(view(0), lv[0].u, area_ptr(), lv[0].r, 0, partials, npart, &dsc->norm2_0, st);
+        norm_residual(&dsc->norm2_0);
         CKL();
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -630,6 +631,15 @@ struct Solver final : SolverBase {
         if (p.smoother == MG_SMOOTH_HS1)
             for (int c = 0; c < 16; ++c) k += (lv[l].n - c / 4 + 3) / 4 > 0 && (lv[l].m - c % 4 + 3) / 4 > 0;
         return k;
+    }
+
+    // sum r^2 of the finest residual r = -L(phi) into *norm_out (r itself is not kept for FP32
+    // storage)
+    void norm_residual(double *norm_out) {
+        if constexpr (std::is_same<T, float>::value)
+            launch_residual_tma(view(0), 0, area_ptr(), nullptr, 0, partials, npart, norm_out, lv[0].smaps,
+                                lv[0].rmaps, &dsc->err, wait_limit, st);
+        else launch_residual<T>(view(0), lv[0].u, area_ptr(), lv[0].r, 0, partials, npart, norm_out, st);
     }
 
     // The coefficient snapshot of grid l (v = view(l)): TMA-staged for FP32 storage.
@@ -703,7 +713,7 @@ struct Solver final : SolverBase {
         Level<T> &L = lv[l], &C = lv[l + 1];
         area_term(l, L.u);
         if constexpr (std::is_same<T, float>::value) {
-            launch_residual_restrict(view(l), view(l + 1), area_ptr(), st);
+            launch_residual_restrict_tma(view(l), view(l + 1), area_ptr(), L.rmaps, &dsc->err, wait_limit, st);
             launches += 1;
         } else {
             launch_residual<T>(view(l), L.u, area_ptr(), L.r, 0, partials, 0, nullptr, st);
@@ -712,7 +722,10 @@ struct Solver final : SolverBase {
             launches += 3;
         }
         area_term(l + 1, C.u0);
-        launch_residual<T>(view(l + 1), C.u0, area_ptr(), C.rhs, 1, partials, 0, nullptr, st);
+        if constexpr (std::is_same<T, float>::value)
+            launch_residual_tma(view(l + 1), 1, area_ptr(), C.rhs, 1, partials, 0, nullptr, C.smaps, C.rmaps, &dsc->err,
+                                wait_limit, st);
+        else launch_residual<T>(view(l + 1), C.u0, area_ptr(), C.rhs, 1, partials, 0, nullptr, st);
         launches += 2 * area_launches() + 1;
         cycle(l + 1);
         launch_interp_add<T>(view(l), view(l + 1), st);
@@ -723,7 +736,7 @@ struct Solver final : SolverBase {
     void enqueue_vcycle(bool readback = true) {
         cycle(0);
         area_term(0, lv[0].u);
-        launch_residual<T>(view(0), lv[0].u, area_ptr(), lv[0].r, 0, partials, npart, &dsc->norm2, st);
+        norm_residual(&dsc->norm2);
         launches += area_launches() + 2;
         if (readback) cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
     }
@@ -1278,7 +1291,10 @@ struct Solver final : SolverBase {
                     cudaEventRecord(ev[2 + k], st);
                 }
             }
-            launch_residual<T>(v, lv[l].u, area_ptr(), lv[l].r, 0, partials, 0, nullptr, st);
+            if constexpr (std::is_same<T, float>::value)
+                launch_residual_tma(v, 0, area_ptr(), lv[l].r, 0, partials, 0, nullptr, lv[l].smaps, lv[l].rmaps,
+                                    &dsc->err, wait_limit, st);
+            else launch_residual<T>(v, lv[l].u, area_ptr(), lv[l].r, 0, partials, 0, nullptr, st);
             cudaEventRecord(ev[6], st);
             launches += area_launches() + 2 + smoother_launches(l);
             CKL();
@@ -1705,6 +1721,7 @@ int mg_setup(mg_handle *out, const void *image, int n, int m, const double *mark
     prepare_bottom_kernel();
     prepare_sweep_tma();
     prepare_snapshot_tma();
+    prepare_residual_tma();
     prepare_learned_kernels();
     SolverBase *s = nullptr;
     if (p->precision != MG_F64) {
@@ -2067,6 +2084,7 @@ int mg_batch_setup(mg_batch *out, int count, const void *const *images, const in
     prepare_bottom_kernel();
     prepare_sweep_tma();
     prepare_snapshot_tma();
+    prepare_residual_tma();
     prepare_learned_kernels();
     auto *B = new mg_batch_s();
     Batch &b = B->b;

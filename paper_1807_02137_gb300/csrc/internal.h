@@ -169,6 +169,29 @@ bool encode_snapshot_maps(const LevelView<float> &L, SnapMaps *M);
 // complete within wait_limit try_wait rounds sets bit 4 of *err.
 void launch_snapshot_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err,
                          long long wait_limit, cudaStream_t st);
+// Tensor maps of the TMA-staged residual kernels of one FP32 grid (residual_tma.cu): pn, u and w
+// boxes of 37 rows and F and rhs tiles of 33 x 36 (the residual with restriction), and the u0
+// box of 36 rows (the FAS right-hand side).
+struct ResMaps {
+    alignas(64) unsigned char P37[128];
+    alignas(64) unsigned char U37[128];
+    alignas(64) unsigned char W37[128];
+    alignas(64) unsigned char F33[128];
+    alignas(64) unsigned char R33[128];
+    alignas(64) unsigned char U0[128];
+};
+void prepare_residual_tma();
+bool encode_residual_maps(const LevelView<float> &L, ResMaps *R);
+// launch_residual for an FP32 grid (uin = the grid's u, or its u0 when uin_is_u0; out may be
+// NULL in mode 0 when only the norm is wanted) and launch_residual_restrict, with the same
+// operations; a copy that does not complete within wait_limit try_wait rounds sets bit 4 of *err.
+void launch_residual_tma(const LevelView<float> &L, int uin_is_u0, const double *area, float *out, int mode,
+                         double *partials, int npart, double *norm_out, const SnapMaps &M, const ResMaps &R, int *err,
+                         long long wait_limit, cudaStream_t st);
+void launch_residual_restrict_tma(const LevelView<float> &L, const LevelView<float> &C, const double *area,
+                                  const ResMaps &R, int *err, long long wait_limit, cudaStream_t st);
+// Sums np FP64 partials in a fixed order into *out (one block).
+void launch_sum_partials(const double *partials, int np, double *out, cudaStream_t st);
 void prepare_sweep_tma();
 bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M);
 // One n x m grid function (FP32: elem 4, BF16: elem 2) with row pitch `pitch` elements as a 2-D
