@@ -250,13 +250,22 @@ int mg_debug_status(mg_debug_info *out, int clear);
  * site 10, that index and one more count.  Synchronous.  Does nothing in the default build. */
 int mg_debug_selftest(void);
 
-/* Whole pipeline through host buffers: copies the float image to the device, runs mg_setup,
- * then mg_solve(tol, max_cycles, eta_stop, max_steps) with the given parameters (precision
- * forced to MG_F32), and copies the mask (and phi if phi_host is not NULL) back.  All host
- * buffers are n*m elements; stats may be NULL.  Synchronous. */
+/* Whole pipeline through host buffers: copies the float image to the device, runs mg_setup (or
+ * mg_reset on the context kept from the previous call, see below), then mg_solve(tol,
+ * max_cycles, eta_stop, max_steps) with the given parameters (precision forced to MG_F32), and
+ * copies the mask (and phi if phi_host is not NULL) back.  All host buffers are n*m elements
+ * (page-locked buffers copy fastest); stats may be NULL.  Synchronous. */
 int mg_segment_host(const float *image_host, int n, int m, const double *markers_xy, int k,
                     const mg_params *p, double tol, int max_cycles, double eta_stop,
                     int max_steps, unsigned char *mask_host, float *phi_host, mg_stats *stats);
+
+/* mg_segment_host keeps its handle, device buffers and stream after a successful call: the next
+ * call on the same device with the same size and parameters (and at most max(k, 16) markers)
+ * reuses them through mg_reset, which redoes the image's set-up, so only the copies, the set-up
+ * kernels and the solve remain per call.  Calls are serialised by a lock.  A call with another
+ * size or other parameters, or a failed call, frees the kept context first.
+ * mg_segment_host_release frees it (before cudaDeviceReset, for example). */
+void mg_segment_host_release(void);
 
 /* Tile-shape autotuner (a tuning step of this implementation; the paper has no counterpart):
  * inside a pseudo-time step (after mg_begin_step), times one outer smoothing iteration of every

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <mutex>
 #include <random>
 #include <vector>
 
@@ -1836,6 +1837,35 @@ int mg_debug_status(mg_debug_info *out, int clear) {
     return MG_OK;
 }
 
+namespace {
+
+// The context of mg_segment_host kept between calls: the handle, its device buffers and stream,
+// for the size, parameters and device of the last call (one per process, under a lock).
+struct HostContext {
+    std::mutex mu;
+    int dev = -1, n = 0, m = 0, kcap = 0;
+    mg_params q{};
+    mg_handle h = nullptr;
+    float *dimg = nullptr, *dphi = nullptr;
+    unsigned char *dmask = nullptr;
+    cudaStream_t st = nullptr;
+    void release() {
+        if (h) mg_destroy(h);
+        if (dimg) cudaFree(dimg);
+        if (dmask) cudaFree(dmask);
+        if (dphi) cudaFree(dphi);
+        if (st) cudaStreamDestroy(st);
+        h = nullptr; dimg = nullptr; dmask = nullptr; dphi = nullptr; st = nullptr;
+        dev = -1; n = m = kcap = 0;
+    }
+};
+HostContext &host_context() {
+    static HostContext *c = new HostContext();   // never destroyed: no CUDA calls at process exit
+    return *c;
+}
+
+}  // namespace
+
 int mg_segment_host(const float *image_host, int n, int m, const double *markers_xy, int k,
                     const mg_params *p, double tol, int max_cycles, double eta_stop, int max_steps,
                     unsigned char *mask_host, float *phi_host, mg_stats *stats) {
@@ -1844,39 +1874,56 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
     if (q.precision == MG_F64) q.precision = MG_F32;
     int rc = check_params(&q, n, m);
     if (rc) return rc;
-    size_t N = (size_t)n * m;
-    float *dimg = nullptr;
-    unsigned char *dmask = nullptr;
-    float *dphi = nullptr;
-    cudaStream_t st;
-    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    mg_handle h = nullptr;
-    auto cleanup = [&]() {
-        if (h) mg_destroy(h);
-        if (dimg) cudaFree(dimg);
-        if (dmask) cudaFree(dmask);
-        if (dphi) cudaFree(dphi);
-        cudaStreamDestroy(st);
-    };
-    cudaError_t e = cudaMalloc(&dimg, N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&dmask, N);
-    if (e == cudaSuccess && phi_host) e = cudaMalloc(&dphi, N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dimg, image_host, N * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) { cleanup(); return fail(MG_ERR_CUDA, cudaGetErrorString(e)); }
-    rc = mg_setup(&h, dimg, n, m, markers_xy, k, &q, nullptr, st);
-    if (!rc) rc = mg_solve(h, tol, max_cycles, eta_stop, max_steps, nullptr);
-    if (!rc) rc = mg_mask(h, dmask);
-    if (!rc && phi_host) rc = mg_get_phi(h, dphi);
-    if (!rc && stats) rc = mg_get_stats(h, stats);
+    if ((rc = check_markers(markers_xy, k, n, m))) return rc;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    HostContext &c = host_context();
+    std::lock_guard<std::mutex> lock(c.mu);
+    const size_t N = (size_t)n * m;
+    const bool same = c.h && c.dev == dev && c.n == n && c.m == m && k <= c.kcap &&
+                      std::memcmp(&c.q, &q, sizeof(mg_params)) == 0;
+    if (!same) c.release();
+    cudaError_t e = cudaSuccess;
+    if (!c.st) e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c.dimg) e = cudaMalloc(&c.dimg, N * sizeof(float));
+    if (e == cudaSuccess && !c.dmask) e = cudaMalloc(&c.dmask, N);
+    if (e == cudaSuccess && phi_host && !c.dphi) e = cudaMalloc(&c.dphi, N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.dimg, image_host, N * sizeof(float), cudaMemcpyHostToDevice, c.st);
+    if (e != cudaSuccess) {
+        c.release();
+        return fail(e == cudaErrorMemoryAllocation ? MG_ERR_NOMEM : MG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (same) {
+        rc = mg_reset(c.h, c.dimg, markers_xy, k);
+    } else {
+        rc = mg_setup(&c.h, c.dimg, n, m, markers_xy, k, &q, nullptr, c.st);
+        if (!rc) {
+            c.dev = dev; c.n = n; c.m = m; c.kcap = std::max(k, 16); c.q = q;
+        }
+    }
+    if (!rc) rc = mg_solve(c.h, tol, max_cycles, eta_stop, max_steps, nullptr);
+    if (!rc) rc = mg_mask(c.h, c.dmask);
+    if (!rc && phi_host) rc = mg_get_phi(c.h, c.dphi);
+    if (!rc && stats) rc = mg_get_stats(c.h, stats);
     if (!rc) {
-        e = cudaMemcpy(mask_host, dmask, N, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && phi_host) e = cudaMemcpy(phi_host, dphi, N * sizeof(float), cudaMemcpyDeviceToHost);
+        e = cudaMemcpyAsync(mask_host, c.dmask, N, cudaMemcpyDeviceToHost, c.st);
+        if (e == cudaSuccess && phi_host)
+            e = cudaMemcpyAsync(phi_host, c.dphi, N * sizeof(float), cudaMemcpyDeviceToHost, c.st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
         if (e != cudaSuccess) rc = fail(MG_ERR_CUDA, cudaGetErrorString(e));
     }
-    std::string keep = g_err;
-    cleanup();
-    g_err = keep;
+    if (rc) {   // a failed call keeps nothing
+        std::string keep = g_err;
+        c.release();
+        g_err = keep;
+    }
     return rc;
+}
+
+void mg_segment_host_release(void) {
+    HostContext &c = host_context();
+    std::lock_guard<std::mutex> lock(c.mu);
+    c.release();
 }
 
 int mg_autotune(mg_handle h, int reps, int *shapes) {

@@ -22,7 +22,7 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
           -5: "MG_ERR_TIMEOUT", -6: "MG_ERR_NOT_SPD", -7: "MG_ERR_NOMEM", -8: "MG_ERR_STATE"}
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
-           "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_inject_divergence", "mg_debug_status", "mg_debug_selftest", "mg_segment_host", "mg_get_stream", "mg_destroy",
+           "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_inject_divergence", "mg_debug_status", "mg_debug_selftest", "mg_segment_host", "mg_segment_host_release", "mg_get_stream", "mg_destroy",
            "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_set_cluster_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
            "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_set_loss", "mg_trainer_grad",
            "mg_trainer_train", "mg_trainer_get", "mg_trainer_destroy",
@@ -116,6 +116,7 @@ def lib():
             "mg_debug_status": ([C.POINTER(DebugInfo), i], i),
             "mg_debug_selftest": ([], i),
             "mg_segment_host": ([vp, i, i, D, i, P, d, i, d, i, vp, vp, C.POINTER(Stats)], i),
+            "mg_segment_host_release": ([], None),
             "mg_get_stream": ([vp], vp),
             "mg_time_kernels": ([vp, i, i, D], i),
             "mg_residual_norm_noalloc": ([vp, vp, vp, i, i, P, D, vp], i),
@@ -483,12 +484,19 @@ def residual_norm_noalloc(phi, w, F, params: Params) -> float:
 
 
 def segment_host(image, markers, params: Params, tol=1e-6, max_cycles=50, eta_stop=0.0,
-                 max_steps=1, want_phi=False):
-    """Whole pipeline from host buffers (mg_segment_host): returns (mask, phi or None, stats)."""
+                 max_steps=1, want_phi=False, mask_out=None):
+    """Whole pipeline from host buffers (mg_segment_host): returns (mask, phi or None, stats).
+    mask_out: an n x m uint8 C-contiguous array to write the mask into (for example one in
+    page-locked memory, reused across calls); a new array when None."""
     img = np.ascontiguousarray(image, dtype=np.float32)
     n, m = img.shape
     _, pm, k = _markers(markers)
-    mask = np.empty((n, m), dtype=np.uint8)
+    if mask_out is not None:
+        if mask_out.shape != (n, m) or mask_out.dtype != np.uint8 or not mask_out.flags["C_CONTIGUOUS"]:
+            raise TypeError("mask_out must be a C-contiguous n x m uint8 array")
+        mask = mask_out
+    else:
+        mask = np.empty((n, m), dtype=np.uint8)
     phi = np.empty((n, m), dtype=np.float32) if want_phi else None
     st = Stats()
     _check(lib().mg_segment_host(img.ctypes.data_as(C.c_void_p), n, m, pm, k, C.byref(params), tol,
@@ -496,6 +504,11 @@ def segment_host(image, markers, params: Params, tol=1e-6, max_cycles=50, eta_st
                                  phi.ctypes.data_as(C.c_void_p) if want_phi else None, C.byref(st)),
            "mg_segment_host")
     return mask, phi, st.as_dict()
+
+
+def segment_host_release():
+    """mg_segment_host_release: frees the context mg_segment_host keeps between calls."""
+    lib().mg_segment_host_release()
 
 
 class Trainer:

@@ -171,6 +171,35 @@ def test_host_pipeline_matches_device_pipeline(segmg):
     assert st["steps"] == 1 and st["rho"] <= 1e-6
 
 
+def test_host_pipeline_kept_context_equals_a_fresh_one(segmg):
+    # mg_segment_host keeps its handle between calls of one size: a second image through the kept
+    # context, a size change, and a marker-count change give bitwise what a fresh context gives
+    imgs = [synth.ellipses(192, 160, 8, (16, 60), 6, 0.05, s)[:2] for s in (21, 22)]
+    other = synth.ellipses(96, 128, 6, (10, 40), 5, 0.05, 23)[:2]
+    p = segmg.default_params(192, 160)
+    p2 = segmg.default_params(96, 128)
+
+    def run(img, mk, params, fresh):
+        if fresh:
+            segmg.segment_host_release()
+        mask_out = np.empty(img.shape, dtype=np.uint8)
+        mask, phi, st = segmg.segment_host(img, mk, params, 1e-6, 50, 0.0, 1, want_phi=True, mask_out=mask_out)
+        assert mask is mask_out
+        return mask.copy(), phi, st
+
+    fresh = [run(i, m, p, True) for i, m in imgs] + [run(other[0], other[1], p2, True)]
+    segmg.segment_host_release()
+    kept = [run(i, m, p, False) for i, m in imgs] + [run(other[0], other[1], p2, False)]
+    # more markers than the kept context was set up for: a new context
+    mk_many = np.array([[20 + 7 * q, 30 + 5 * q] for q in range(20)], dtype=float)
+    many_kept = run(imgs[0][0], mk_many, p, False)
+    many_fresh = run(imgs[0][0], mk_many, p, True)
+    for a, b in zip(kept + [many_kept], fresh + [many_fresh]):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert a[2]["cycles_total"] == b[2]["cycles_total"] and a[2]["rho"] == b[2]["rho"]
+    segmg.segment_host_release()
+
+
 def test_errors_are_reported_not_raised_on_the_gpu(segmg):
     img, mk, _ = synth.disc_square(64, 0.05, 0)
     bad = img.copy()
