@@ -48,12 +48,15 @@ struct TShape {
 // (8192^2: 0.28 -> 0.24 ms per sweep)
 using TT0 = TShape<32, 64, 256, 6, true>;
 using TT1 = TShape<32, 32, 128>;
-using TT2 = TShape<64, 64, 512>;
-using TT3 = TShape<32, 64, 512>;
+using TT2 = TShape<64, 64, 512, 2>;   // 512-thread shapes: at most 64 registers, two blocks per SM
+using TT3 = TShape<32, 64, 512, 2>;
 // 8 blocks of 256 threads per SM (at most 32 registers): every 32 x 32 tile of a 1024^2 grid
 // then has its own resident block, one stage and no persistent loop
 using TT4 = TShape<32, 32, 256, 8>;
-using TT5 = TShape<32, 32, 512>;
+// at most 64 registers: two blocks per SM for every sweep direction, so that every tile of a 512^2
+// grid gets its own block (sweep D's code otherwise took more registers than A to C, fitting
+// one block per SM and running persistent: 7.0 against 5.4 us per launch)
+using TT5 = TShape<32, 32, 512, 2>;
 
 template <typename TS, int STAGES>
 struct TmaSmem {
