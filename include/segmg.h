@@ -210,9 +210,9 @@ int mg_get_level(mg_handle h, int level, int field, void *out);
 
 int mg_get_stats(mg_handle h, mg_stats *s);
 
-/* Bound of the device-side waits of the FP32 fused sweep (the Tensor Memory Accelerator copies of
- * a tile into shared memory complete on an mbarrier; each wait polls it at most `rounds` times,
- * default 4,194,304).  When a wait gives up, the block records it, waits once more (with the
+/* Bound of the device-side waits of the FP32 kernels staged by the Tensor Memory Accelerator
+ * (fused sweep, coefficient snapshot, residual kernels: the copies of a tile into shared memory
+ * complete on an mbarrier; each wait polls it at most `rounds` times, default 4,194,304).  When a wait gives up, the block records it, waits once more (with the
  * default bound) for the copies it has in flight, and ends; the next mg_vcycle / mg_solve_step
  * returns MG_ERR_TIMEOUT and the handle stays usable.  rounds = 0 makes every such wait give up at
  * once (for tests of that path).  A diagnostic setting of this implementation; the paper has no
