@@ -23,6 +23,9 @@ namespace segmg {
 namespace {
 
 constexpr int kC = 40, kCb = 48;   // FP32 / BF16 box columns (from j0-4 / j0-8)
+// resident blocks per SM asked of the compiler: 8 x 256 threads at most 32 registers (the
+// residual's FP32 shared memory, 26 KB, fits 8 blocks); 6 for the residual with restriction
+constexpr int kResMinB = 8, kRRMinB = 6;
 constexpr long long kResDrain = 1LL << 22;
 
 // ---------------------------------------------------------------------------------------
@@ -32,17 +35,16 @@ template <bool MIXED>
 struct ResTmaSmem {
     alignas(128) float P[36][kC];
     alignas(128) float U[36][kC];
-    alignas(128) float G[36][kC];
-    alignas(128) float W[MIXED ? 1 : 36][kC];
-    alignas(128) __nv_bfloat16 Wb[MIXED ? 36 : 1][kCb];
+    alignas(128) float W[36][kC];   // FP32: w, overwritten in place by G (a cell reads only its own w)
+    alignas(128) __nv_bfloat16 Wb[MIXED ? 36 : 1][kCb];   // mixed precision: w; G is then in W
     alignas(128) float F[32][32];
     alignas(128) float X[32][32];   // MODE 0: rhs; MODE 1: the output's values before the update
     double red[33];
     unsigned long long bar;
 };
 
-template <int MODE, bool MIXED, bool NORM>
-__global__ void __launch_bounds__(256, 5)
+template <int MODE, bool MIXED, bool NORM, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     k_residual_tma(LevelView<float> L, const double *area, float *out, double *partials,
                    const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mU,
                    const __grid_constant__ CUtensorMap mW, const __grid_constant__ CUtensorMap mF,
@@ -95,11 +97,11 @@ __global__ void __launch_bounds__(256, 5)
         const int gi = i0 - 2 + a, gj = j0 - 4 + c;
         T g = T(0);
         if (!check || (gi >= 0 && gi < n && gj >= 0 && gj < m)) {
-            const T w = MIXED ? __bfloat162float(S.Wb[MIXED ? a : 0][c + 4]) : S.W[MIXED ? 0 : a][c];
+            const T w = MIXED ? __bfloat162float(S.Wb[MIXED ? a : 0][c + 4]) : S.W[a][c];
             g = cell_G(w, S.P[a + 1][c], S.P[a - 1][c], S.P[a][c + 1], S.P[a][c - 1], S.U[a + 1][c], S.U[a - 1][c],
                        S.U[a][c + 1], S.U[a][c - 1], L.inv_2h, L.beta);
         }
-        S.G[a][c] = g;
+        S.W[a][c] = g;
     };
     if (interior) {
 #pragma unroll
@@ -120,9 +122,9 @@ __global__ void __launch_bounds__(256, 5)
         const int ti = wy + 8 * k, a = ti + 2, gi = i0 + ti;
         if (!(IN || (gi < n && gj < m))) return;
         const bool hS = IN || gi + 1 < n, hN = IN || gi > 0, hE = IN || gj + 1 < m, hW = IN || gj > 0;
-        const T gc = S.G[a][c];
-        const T aS = face(gc, S.G[a + 1][c], hS), aN = face(gc, S.G[a - 1][c], hN);
-        const T aE = face(gc, S.G[a][c + 1], hE), aW = face(gc, S.G[a][c - 1], hW);
+        const T gc = S.W[a][c];
+        const T aS = face(gc, S.W[a + 1][c], hS), aN = face(gc, S.W[a - 1][c], hN);
+        const T aE = face(gc, S.W[a][c + 1], hE), aW = face(gc, S.W[a][c - 1], hW);
         const T pc = S.P[a][c], uc = S.U[a][c];
         T fl = mul_rn(aS, add_rn(sub_rn(S.P[a + 1][c], pc), sub_rn(S.U[a + 1][c], uc)));
         fl = fma_rn(aN, add_rn(sub_rn(S.P[a - 1][c], pc), sub_rn(S.U[a - 1][c], uc)), fl);
@@ -157,8 +159,7 @@ template <bool MIXED>
 struct RRTmaSmem {
     alignas(128) float P[37][kC];   // rows i0-2 .. i0+34, columns j0-4 .. j0+35
     alignas(128) float U[37][kC];
-    alignas(128) float G[37][kC];
-    alignas(128) float W[MIXED ? 1 : 37][kC];
+    alignas(128) float W[37][kC];   // FP32: w, overwritten in place by G; mixed: G
     alignas(128) __nv_bfloat16 Wb[MIXED ? 37 : 1][kCb];
     alignas(128) float F[33][36];   // rows i0 .. i0+32, columns j0 .. j0+35
     alignas(128) float RH[33][36];
@@ -166,8 +167,8 @@ struct RRTmaSmem {
     unsigned long long bar;
 };
 
-template <bool MIXED>
-__global__ void __launch_bounds__(256, 4)
+template <bool MIXED, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     k_residual_restrict_tma(LevelView<float> L, LevelView<float> C, const double *area,
                             const __grid_constant__ CUtensorMap mP, const __grid_constant__ CUtensorMap mU,
                             const __grid_constant__ CUtensorMap mW, const __grid_constant__ CUtensorMap mF,
@@ -219,11 +220,11 @@ __global__ void __launch_bounds__(256, 4)
         const int gi = i0 - 2 + a, gj = j0 - 4 + c;
         float g = 0.f;
         if (!check || (gi >= 0 && gi < n && gj >= 0 && gj < m)) {
-            const float w = MIXED ? __bfloat162float(S.Wb[MIXED ? a : 0][c + 4]) : S.W[MIXED ? 0 : a][c];
+            const float w = MIXED ? __bfloat162float(S.Wb[MIXED ? a : 0][c + 4]) : S.W[a][c];
             g = cell_G(w, S.P[a + 1][c], S.P[a - 1][c], S.P[a][c + 1], S.P[a][c - 1], S.U[a + 1][c], S.U[a - 1][c],
                        S.U[a][c + 1], S.U[a][c - 1], L.inv_2h, L.beta);
         }
-        S.G[a][c] = g;
+        S.W[a][c] = g;
     };
     if (gin) {
 #pragma unroll
@@ -245,9 +246,9 @@ __global__ void __launch_bounds__(256, 4)
         if (IN || (gi < n && gj < m)) {
             const int a = ti + 2, c = tj + 4;   // box coordinates
             const bool hS = IN || gi + 1 < n, hN = IN || gi > 0, hE = IN || gj + 1 < m, hW = IN || gj > 0;
-            const float gc = S.G[a][c];
-            const float aS = face(gc, S.G[a + 1][c], hS), aN = face(gc, S.G[a - 1][c], hN);
-            const float aE = face(gc, S.G[a][c + 1], hE), aW = face(gc, S.G[a][c - 1], hW);
+            const float gc = S.W[a][c];
+            const float aS = face(gc, S.W[a + 1][c], hS), aN = face(gc, S.W[a - 1][c], hN);
+            const float aE = face(gc, S.W[a][c + 1], hE), aW = face(gc, S.W[a][c - 1], hW);
             const float pc = S.P[a][c], uc = S.U[a][c];
             float fl = mul_rn(aS, add_rn(sub_rn(S.P[a + 1][c], pc), sub_rn(S.U[a + 1][c], uc)));
             fl = fma_rn(aN, add_rn(sub_rn(S.P[a - 1][c], pc), sub_rn(S.U[a - 1][c], uc)), fl);
@@ -299,7 +300,7 @@ size_t rr_smem() { return sizeof(RRTmaSmem<MIXED>) + 128; }
 
 template <int MODE, bool MIXED, bool NORM>
 void res_attr() {
-    cudaFuncSetAttribute(k_residual_tma<MODE, MIXED, NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_residual_tma<MODE, MIXED, NORM, kResMinB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)res_smem<MODE, MIXED, NORM>());
 }
 
@@ -309,7 +310,7 @@ template <int MODE, bool MIXED, bool NORM>
 void launch_res(const LevelView<float> &L, const double *area, float *out, double *partials, const SnapMaps &M,
                 const unsigned char *mU, const unsigned char *mX, int *err, long long wl, cudaStream_t st) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, 8);
-    k_residual_tma<MODE, MIXED, NORM><<<grid, block, res_smem<MODE, MIXED, NORM>(), st>>>(
+    k_residual_tma<MODE, MIXED, NORM, kResMinB><<<grid, block, res_smem<MODE, MIXED, NORM>(), st>>>(
         L, area, out, partials, *tm(M.P), *tm(mU), *tm(M.W), *tm(M.F), *tm(mX), err, wl);
 }
 
@@ -327,9 +328,9 @@ void launch_res_mixed(const LevelView<float> &L, int uin_is_u0, const double *ar
 void prepare_residual_tma() {
     res_attr<0, false, false>(); res_attr<0, false, true>(); res_attr<1, false, false>();
     res_attr<0, true, false>(); res_attr<0, true, true>(); res_attr<1, true, false>();
-    cudaFuncSetAttribute(k_residual_restrict_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_residual_restrict_tma<false, kRRMinB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)rr_smem<false>());
-    cudaFuncSetAttribute(k_residual_restrict_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_residual_restrict_tma<true, kRRMinB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)rr_smem<true>());
 }
 
@@ -358,11 +359,11 @@ void launch_residual_restrict_tma(const LevelView<float> &L, const LevelView<flo
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, 8);
     const unsigned char *mR = L.has_rhs ? R.R33 : R.F33;
     if (L.wb)
-        k_residual_restrict_tma<true><<<grid, block, rr_smem<true>(), st>>>(L, C, area, *tm(R.P37), *tm(R.U37),
+        k_residual_restrict_tma<true, kRRMinB><<<grid, block, rr_smem<true>(), st>>>(L, C, area, *tm(R.P37), *tm(R.U37),
                                                                            *tm(R.W37), *tm(R.F33), *tm(mR), err,
                                                                            wait_limit);
     else
-        k_residual_restrict_tma<false><<<grid, block, rr_smem<false>(), st>>>(L, C, area, *tm(R.P37), *tm(R.U37),
+        k_residual_restrict_tma<false, kRRMinB><<<grid, block, rr_smem<false>(), st>>>(L, C, area, *tm(R.P37), *tm(R.U37),
                                                                              *tm(R.W37), *tm(R.F33), *tm(mR), err,
                                                                              wait_limit);
 }

@@ -34,9 +34,8 @@ template <int WARPS, bool MIXED>
 struct SnapTmaSmem {
     alignas(128) float P[kBR][kBC];
     alignas(128) float U[kBR][kBC];
-    alignas(128) float G[kBR][kBC];
-    alignas(128) float W[MIXED ? 1 : kBR][kBC];                 // w (FP32 storage)
-    alignas(128) __nv_bfloat16 Wb[MIXED ? kBR : 1][kBCb];      // w (mixed precision), from column j0-8
+    alignas(128) float W[kBR][kBC];   // FP32: w, overwritten in place by G (a cell reads only its own w)
+    alignas(128) __nv_bfloat16 Wb[MIXED ? kBR : 1][kBCb];      // mixed precision: w (from column j0-8); G in W
     alignas(128) float F[32][32];
     alignas(128) float R[32][32];
     uint32_t cm[2][WARPS][32];   // column member bits of sweeps C, D per warp
@@ -104,11 +103,11 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         const int gi = i0 - 2 + a, gj = j0 - 4 + c;
         T g = T(0);
         if (!check || (gi >= 0 && gi < n && gj >= 0 && gj < m)) {
-            const T w = MIXED ? __bfloat162float(S.Wb[MIXED ? a : 0][c + 4]) : S.W[MIXED ? 0 : a][c];
+            const T w = MIXED ? __bfloat162float(S.Wb[MIXED ? a : 0][c + 4]) : S.W[a][c];
             g = cell_G(w, S.P[a + 1][c], S.P[a - 1][c], S.P[a][c + 1], S.P[a][c - 1], S.U[a + 1][c], S.U[a - 1][c],
                        S.U[a][c + 1], S.U[a][c - 1], L.inv_2h, L.beta);
         }
-        S.G[a][c] = g;
+        S.W[a][c] = g;
     };
     if (interior) {
 #pragma unroll
@@ -130,9 +129,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         uint32_t star = 0;
         if (IN || (gi < n && gj < m)) {
             const bool hS = IN || gi + 1 < n, hN = IN || gi > 0, hE = IN || gj + 1 < m, hW = IN || gj > 0;
-            const T gc = S.G[a][c];
-            const T aS = face(gc, S.G[a + 1][c], hS), aN = face(gc, S.G[a - 1][c], hN);
-            const T aE = face(gc, S.G[a][c + 1], hE), aW = face(gc, S.G[a][c - 1], hW);
+            const T gc = S.W[a][c];
+            const T aS = face(gc, S.W[a + 1][c], hS), aN = face(gc, S.W[a - 1][c], hN);
+            const T aE = face(gc, S.W[a][c + 1], hE), aW = face(gc, S.W[a][c - 1], hW);
             const T pc = S.P[a][c];
             T ds = mul_rn(aS, sub_rn(S.P[a + 1][c], pc));
             ds = fma_rn(aN, sub_rn(S.P[a - 1][c], pc), ds);
@@ -231,7 +230,7 @@ void launch_mixed(const LevelView<float> &L, const double *area, const SnapMaps 
     // the most threads per tile with which every tile still gets a resident block
     if (tiles <= (long)g_snap_occ.sms * ps[0]) launch_v<32, 1, MIXED>(L, area, M, err, wl, st);
     else if (tiles <= (long)g_snap_occ.sms * ps[1]) launch_v<16, 1, MIXED>(L, area, M, err, wl, st);
-    else launch_v<8, 5, MIXED>(L, area, M, err, wl, st);
+    else launch_v<8, 7, MIXED>(L, area, M, err, wl, st);
 }
 
 }  // namespace
@@ -242,10 +241,10 @@ void prepare_snapshot_tma() {
     if (g_snap_occ.sms < 1) g_snap_occ.sms = 1;
     g_snap_occ.per_sm[0][0] = snap_attr<32, 1, false>();
     g_snap_occ.per_sm[0][1] = snap_attr<16, 1, false>();
-    g_snap_occ.per_sm[0][2] = snap_attr<8, 5, false>();
+    g_snap_occ.per_sm[0][2] = snap_attr<8, 7, false>();
     g_snap_occ.per_sm[1][0] = snap_attr<32, 1, true>();
     g_snap_occ.per_sm[1][1] = snap_attr<16, 1, true>();
-    g_snap_occ.per_sm[1][2] = snap_attr<8, 5, true>();
+    g_snap_occ.per_sm[1][2] = snap_attr<8, 7, true>();
 }
 
 bool encode_snapshot_maps(const LevelView<float> &L, SnapMaps *M) {
