@@ -384,11 +384,14 @@ def run_ours(args):
         cpu_line = cpu
 
     # the other configurations, measured in the same run (extra keys of this line): 25000^2 mixed
-    # precision with its error against the oracle on a 2048^2 crop, and the 64-image batch
+    # precision with its error against the oracle on a 2048^2 crop, the 64-image batch, and the
+    # learned relaxation weights (trained on recorded states, then one step at 4096^2 plain and
+    # learned)
     extra = {}
     if not args.no_extra:
         for key, fn in (("config3_mixed_25000", lambda: config3_report(25000, 1, 2048, lrank)),
-                        ("config4_batch_64", lambda: config4_report(64, 1, lrank))):
+                        ("config4_batch_64", lambda: config4_report(64, 1, lrank)),
+                        ("config5_learned_4096", lambda: learned_report([4096], "hf", 1000, 4, lrank))):
             try:
                 t0 = time.perf_counter()
                 extra[key] = fn()
@@ -678,6 +681,10 @@ def run_algorithms(args):
 
 
 def run_learned(args):
+    print(json.dumps(learned_report(args.learned, args.loss, args.train_iters, args.refresh)), flush=True)
+
+
+def learned_report(sizes, loss_kind="hf", train_iters=1000, refresh=4, dev_index=0):
     """Learned relaxation weights (the config-5 form): train on states recorded from 200 plain
     solves of 1024^2 ellipse images (seeds 100-299), then time one pseudo-time step to
     rho <= 1e-6 at the given sizes with the plain smoother and with the learned weights kept per
@@ -685,10 +692,10 @@ def run_learned(args):
     import torch
     from paper_1807_02137_gb300 import buildlib, segmg, synth
     buildlib.build()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", dev_index)
     t0 = time.perf_counter()
     tr = segmg.Trainer(capacity=200 * 24, batch_max=64, seed=5)
-    tr.set_loss(args.loss)
+    tr.set_loss(loss_kind)
     for k in range(200):
         img, mk, _ = synth.ellipses(1024, 1024, 12, (20, 200), 8, 0.05, 100 + k)
         s = segmg.Solver(torch.as_tensor(img.astype(np.float32), device=dev), mk, segmg.default_params(1024, 1024))
@@ -701,12 +708,12 @@ def run_learned(args):
     t_rec = time.perf_counter() - t0
     loss0 = tr.grad(list(range(64)))[0]
     t1 = time.perf_counter()
-    loss = tr.train(args.train_iters, 64, 3e-3)
+    loss = tr.train(train_iters, 64, 3e-3)
     t_train = time.perf_counter() - t1
     loss1 = tr.grad(list(range(64)))[0]
     theta = tr.theta()
     rows = []
-    for N in args.learned:
+    for N in sizes:
         # the config-3 image recipe scaled to N (200 ellipses, axes 100-3000 px at 25000^2, the
         # device-side generator of the config-3 run)
         img, mk = synth.ellipses_device(N, N, 200, (100 * N / 25000, 3000 * N / 25000), 20, 0.05, 2, dev)
@@ -721,7 +728,7 @@ def run_learned(args):
             p = segmg.default_params(N, N, levels=W.levels)
             s = segmg.Solver(timg, W.markers, p)
             if mode:
-                s.set_learned(theta, mode=1, refresh=args.refresh)
+                s.set_learned(theta, mode=1, refresh=refresh)
             st = torch.cuda.ExternalStream(s.stream_ptr)
             for rep in range(2):                    # the second run is timed
                 s.reset(timg, W.markers)
@@ -738,11 +745,12 @@ def run_learned(args):
                          "learned_accepted": stt["learned_accepted"] - a0["learned_accepted"],
                          "learned_rejected": stt["learned_rejected"] - a0["learned_rejected"]})
             s.close()
-    print(json.dumps({"learned": {"loss": args.loss, "crops": tr.count, "record_s": t_rec, "train_iters": args.train_iters,
-                                  "train_s": t_train, "loss_before": loss0, "loss_after": loss1,
-                                  "last_batch_loss": loss, "refresh": args.refresh},
-                      "rows": rows}), flush=True)
+    crops = tr.count
     tr.close()
+    return {"learned": {"loss": loss_kind, "crops": crops, "record_s": t_rec, "train_iters": train_iters,
+                        "train_s": t_train, "loss_before": loss0, "loss_after": loss1, "last_batch_loss": loss,
+                        "refresh": refresh},
+            "rows": rows}
 
 
 def main():
