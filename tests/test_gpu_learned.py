@@ -57,12 +57,20 @@ def _theta(seed):
     return th
 
 
-def test_inference_matches_oracle(segmg):
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_inference_matches_oracle(segmg, precision):
     # omega of the finest grid from the first snapshot of a V-cycle, against the oracle's
-    # network on its own coefficients at the same state (BF16 storage emulated)
+    # network on its own coefficients at the same state (BF16 storage emulated).  Both sides
+    # round features and activations to BF16 (8-bit significand); a value whose FP32 (GPU,
+    # tensor-core accumulation) and FP64 (oracle) evaluations fall on either side of a BF16
+    # rounding boundary differs by one BF16 ulp (2^-8 relative), which moves omega = 2 sigmoid(z)
+    # of the cells downstream by at most a few 1e-3 for this network; elsewhere the sides agree to
+    # the FP32 accumulation error.  Measured: max 3.4e-3, mean 2.6e-4, 99th percentile 2.0e-3
+    # (the same for FP32 and FP64 handles).
     img, mk, _ = synth.ellipses(130, 147, 6, (20, 70), 5, 0.05, 33)
     th = _theta(7)
-    s, p = gpu_solver(segmg, img, mk, precision=segmg.MG_F64, levels=4)
+    prec = segmg.MG_F64 if precision == "f64" else segmg.MG_F32
+    s, p = gpu_solver(segmg, img, mk, precision=prec, levels=4)
     s.set_learned(th.astype(np.float32), mode=2, refresh=1)
     o = O.Solver(img, mk, oracle_params(130, 147, p))
     o.begin_step()
@@ -72,8 +80,8 @@ def test_inference_matches_oracle(segmg):
     s.begin_step()
     s.vcycle()
     w_gpu = s.level(0, "omega").cpu().numpy()
-    d = np.abs(w_gpu - w_or)
-    assert d.max() < 3e-2 and d.mean() < 2e-3
+    d = np.abs(w_gpu.astype(np.float64) - w_or)
+    assert d.max() < 1e-2 and d.mean() < 5e-4 and np.quantile(d, 0.99) < 4e-3
     assert 0 < w_gpu.min() and w_gpu.max() < 2
 
 
