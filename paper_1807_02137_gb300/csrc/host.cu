@@ -247,6 +247,13 @@ struct Solver final : SolverBase {
     double gloop_tol = -1.0;
     int gloop_max = -1;
     long long gloop_nodes = 0;
+    // the fused form of the loop (FP32 storage): the finest grid's first snapshot of each V-cycle
+    // also computes the norm of the state the previous V-cycle left, run at the end of the
+    // previous loop iteration, before its step-control tests; gloop_first: kernels of that part
+    bool gloop_fused = false;
+    long long gloop_first = 0;
+    int skip_first_snapshot = 0;   // capture of the rest of a V-cycle: the first smoothing of the
+                                   // finest grid starts after its snapshot
     long long nodes_l = 0, nodes_li = 0;
     double plain_rate = -1.0;     // contraction of the last plain V-cycle of the step
     int learn_skip = 0, learn_backoff = 1;   // plain V-cycles left before the next learned try
@@ -676,9 +683,14 @@ struct Solver final : SolverBase {
 
     void smooth(int l) {
         Range range("smoothing iteration");
-        area_term(l, lv[l].u);
         LevelView<T> v = view(l);
-        snapshot(l, v);
+        if (l == 0 && skip_first_snapshot) {
+            skip_first_snapshot = 0;   // area term and snapshot are in the loop's first part
+            launches -= area_launches() + 1;
+        } else {
+            area_term(l, lv[l].u);
+            snapshot(l, v);
+        }
         if (use_omega && infer_pending[l] && omega_buf[l]) {
             launch_omega_infer<T>(v, net, omega_buf[l], st);   // weights from this snapshot's G
             infer_pending[l] = false;
@@ -1074,8 +1086,113 @@ struct Solver final : SolverBase {
     // phi = phi^n again on the finest grid (the increment zeroed), nothing else changed
     // The step loop graph: reset the loop counter, then a while node whose body is one V-cycle
     // (captured) and k_step_loop, then the copy of the scalars to the host.
+    // Whether the fused form of the step loop applies: FP32 storage, the V-cycle starts with a
+    // smoothing iteration of the finest grid run by the per-grid kernels.
+    bool loop_fusable() const {
+        if constexpr (!std::is_same<T, float>::value) return false;
+        else return p.nu1 >= 1 && nlev >= 2 && lb != 0 && lc != 0 && !use_omega;
+    }
+
+    // The fused loop's first part: the area term and the finest grid's snapshot, which also
+    // writes the norm of the state it reads to dsc->norm2.
+    int capture_first(cudaGraph_t *g, long long *nodes) {
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        area_term(0, lv[0].u);
+        if constexpr (std::is_same<T, float>::value)
+            launch_snapshot_norm_tma(view(0), area_ptr(), lv[0].smaps, partials, &dsc->err, wait_limit, st);
+        launch_sum_partials(partials, npart, &dsc->norm2, st);
+        *nodes = area_launches() + 2;
+        cudaError_t e = cudaStreamEndCapture(st, g);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        return MG_OK;
+    }
+
+    // The rest of a V-cycle after that snapshot (no norm at its end).
+    int capture_rest(cudaGraph_t *g, long long *nodes) {
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        long long before = launches;
+        skip_first_snapshot = 1;
+        cycle(0);
+        skip_first_snapshot = 0;
+        *nodes = launches - before;
+        launches = before;
+        cudaError_t e = cudaStreamEndCapture(st, g);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        return MG_OK;
+    }
+
+    // first part; while (go) { rest of the V-cycle; first part (the next V-cycle's snapshot, with
+    // the norm of the state this V-cycle left); the step control's tests (set go) }.  The snapshot
+    // of the V-cycle that does not run when the attempt stops is the only extra work.
+    int build_loop_fused(double tol, int max_cycles) {
+        cudaGraph_t gf = nullptr, gr = nullptr, G = nullptr;
+        long long nf = 0, nr = 0;
+        int rc = capture_first(&gf, &nf);
+        if (!rc) rc = capture_rest(&gr, &nr);
+        if (rc) {
+            if (gf) cudaGraphDestroy(gf);
+            return rc;
+        }
+        cudaError_t e = cudaGraphCreate(&G, 0);
+        cudaGraphNode_t ms = nullptr, f0 = nullptr, wn = nullptr, cr = nullptr, cf = nullptr, kn = nullptr,
+                        mc = nullptr;
+        if (e == cudaSuccess) {
+            cudaMemsetParams mp_{};
+            mp_.dst = &dsc->loop_j;
+            mp_.value = 0;
+            mp_.elementSize = sizeof(int);
+            mp_.width = 1;
+            mp_.height = 1;
+            e = cudaGraphAddMemsetNode(&ms, G, nullptr, 0, &mp_);
+        }
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&f0, G, &ms, 1, gf);
+        cudaGraphConditionalHandle hw{};
+        cudaGraph_t body = nullptr;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = hw;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&wn, G, &f0, nullptr, 1, &cp);
+            if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+        }
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&cr, body, nullptr, 0, gr);
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&cf, body, &cr, 1, gf);
+        if (e == cudaSuccess) {
+            Scalars *sc = dsc;
+            double t = tol, sr = p.stall_ratio;
+            int mx = max_cycles;
+            void *args[] = {&hw, (void *)&sc, &t, &mx, &sr};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void *)k_step_loop;
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(1);
+            kp.kernelParams = args;
+            e = cudaGraphAddKernelNode(&kn, body, &cf, 1, &kp);
+        }
+        if (e == cudaSuccess) e = cudaGraphAddMemcpyNode1D(&mc, G, &wn, 1, hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gloop, G, 0);
+        if (gf) cudaGraphDestroy(gf);
+        if (gr) cudaGraphDestroy(gr);
+        if (G) cudaGraphDestroy(G);
+        if (e != cudaSuccess) {
+            gloop = nullptr;
+            return fail(MG_ERR_CUDA, std::string("fused step loop graph: ") + cudaGetErrorString(e));
+        }
+        gloop_tol = tol;
+        gloop_max = max_cycles;
+        gloop_nodes = nr;
+        gloop_first = nf;
+        gloop_fused = true;
+        return MG_OK;
+    }
+
     int build_loop(double tol, int max_cycles) {
         if (gloop) { cudaGraphExecDestroy(gloop); gloop = nullptr; }
+        if (loop_fusable()) return build_loop_fused(tol, max_cycles);
+        gloop_fused = false;
         cudaGraph_t vg = nullptr, G = nullptr;
         long long nodes = 0;
         int rc = capture_vcycle(&vg, &nodes);
@@ -1143,7 +1260,10 @@ struct Solver final : SolverBase {
         hist.assign(hsc->loop_rho + 1, hsc->loop_rho + 1 + j);
         cycles_step += j;
         cycles_total += j;
-        launches += (long long)j * (gloop_nodes + 1) + 1;
+        if (gloop_fused)   // the first part once before the loop and once per V-cycle
+            launches += (long long)(j + 1) * gloop_first + (long long)j * (gloop_nodes + 1) + 1;
+        else
+            launches += (long long)j * (gloop_nodes + 1) + 1;
         rho = j > 0 ? hist.back() : 1.0;
         if (hsc->err & 1) return fail(MG_ERR_NOT_SPD, "coarsest Cholesky: non-positive pivot");
         if (hsc->err & 4) {

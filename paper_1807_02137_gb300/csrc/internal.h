@@ -169,6 +169,10 @@ bool encode_snapshot_maps(const LevelView<float> &L, SnapMaps *M);
 // complete within wait_limit try_wait rounds sets bit 4 of *err.
 void launch_snapshot_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err,
                          long long wait_limit, cudaStream_t st);
+// The same snapshot (8 warps per tile) that also writes each tile's sum of r^2, r = rhs - L(pn + u)
+// at the state it reads, to partials: bitwise the partials of launch_residual_tma's norm.
+void launch_snapshot_norm_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, double *partials,
+                              int *err, long long wait_limit, cudaStream_t st);
 // Tensor maps of the TMA-staged residual kernels of one FP32 grid (residual_tma.cu): pn, u and w
 // boxes of 37 rows and F and rhs tiles of 33 x 36 (the residual with restriction), and the u0
 // box of 36 rows (the FAS right-hand side).

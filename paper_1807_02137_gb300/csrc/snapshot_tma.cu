@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "reduce.cuh"
 #include "tma.cuh"
 
 namespace segmg {
@@ -39,17 +40,22 @@ struct SnapTmaSmem {
     alignas(128) float F[32][32];
     alignas(128) float R[32][32];
     uint32_t cm[2][WARPS][32];   // column member bits of sweeps C, D per warp
+    double red[33];              // NORM: the block's sum of squares
     unsigned long long bar;
 };
 
 // One 32 x 32 tile per block of WARPS warps; thread (wy, lane) owns tile column lane, rows
 // wy, wy + WARPS, ....  Box coordinates: row a = tile row + 2, column c = tile column + 4.
-template <int WARPS, int MINB, bool MIXED>
+// NORM (8 warps): the block also writes sum r^2 of its tile, r = rhs - L(pn + u) at the state
+// the snapshot reads, to partials[block]: the operations and the order of k_residual_tma's norm
+// (the same G box, faces, flux and per-thread order), so the partials are bitwise its partials.
+template <int WARPS, int MINB, bool MIXED, bool NORM = false>
 __global__ void __launch_bounds__(32 * WARPS, MINB)
     k_snapshot_tma(LevelView<float> L, const double *area, const __grid_constant__ CUtensorMap mP,
                    const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mW,
                    const __grid_constant__ CUtensorMap mF, const __grid_constant__ CUtensorMap mR, int *err,
-                   long long wait_limit) {
+                   long long wait_limit, double *partials) {
+    static_assert(!NORM || WARPS == 8, "the norm's thread-to-cell map is that of 8 warps per tile");
     using T = float;
     using Smem = SnapTmaSmem<WARPS, MIXED>;
     constexpr int NT = 32 * WARPS, RPW = 32 / WARPS;
@@ -122,6 +128,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     const T ar = area ? T(area[L.level]) : T(0);
     const int gj = j0 + lane, c = lane + 4;
     const int lenr = min(32, m - j0), lenc = min(32, n - i0);
+    T acc = T(0);   // NORM: this thread's sum of r^2
     // f, G and the jump-set class of tile row wy + WARPS k (IN: no bounds tests needed)
     auto cell = [&](int k, auto in_tag) -> uint32_t {
         constexpr bool IN = decltype(in_tag)::value;
@@ -152,6 +159,16 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
             const int cnt = (int)hS + (int)hN + (int)hE + (int)hW;
             if (cnt >= 2 && mx > mul_rn(L.Sigma, mn)) star = 1u << am;
             if (L.cls) stc(L.cls, o, lim, kDbgSnapshot, (uint8_t)star);
+            if (NORM) {   // the residual of the cell at this state (as k_residual_tma, mode 0)
+                const T uc = S.U[a][c];
+                T fl = mul_rn(aS, add_rn(sub_rn(S.P[a + 1][c], pc), sub_rn(S.U[a + 1][c], uc)));
+                fl = fma_rn(aN, add_rn(sub_rn(S.P[a - 1][c], pc), sub_rn(S.U[a - 1][c], uc)), fl);
+                fl = fma_rn(aE, add_rn(sub_rn(S.P[a][c + 1], pc), sub_rn(S.U[a][c + 1], uc)), fl);
+                fl = fma_rn(aW, add_rn(sub_rn(S.P[a][c - 1], pc), sub_rn(S.U[a][c - 1], uc)), fl);
+                const T Lv = sub_rn(fma_rn(L.cdiff, fl, -add_rn(S.F[ti][lane], ar)), mul_rn(L.inv_tau, uc));
+                const T r = L.has_rhs ? sub_rn(S.R[ti][lane], Lv) : -Lv;
+                acc = add_square(acc, r);
+            }
         }
         return star;
     };
@@ -184,9 +201,13 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         stc(L.mcol, ((size_t)wy * m + j0 + lane) * L.npn + (i0 >> 5), (size_t)2 * m * L.npn, kDbgMaskStore,
             members_of(v, lenc));
     }
+    if (NORM) {
+        const double s = block_sum((double)acc, S.red);
+        if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
 }
 
-template <int WARPS, int MINB, bool MIXED>
+template <int WARPS, int MINB, bool MIXED, bool NORM = false>
 size_t snap_smem() {
     return sizeof(SnapTmaSmem<WARPS, MIXED>) + 128;
 }
@@ -198,28 +219,28 @@ struct SnapTmaOcc {
 };
 SnapTmaOcc g_snap_occ;
 
-template <int WARPS, int MINB, bool MIXED>
+template <int WARPS, int MINB, bool MIXED, bool NORM = false>
 int snap_attr() {
     const int smem = (int)snap_smem<WARPS, MINB, MIXED>();
-    cudaFuncSetAttribute(k_snapshot_tma<WARPS, MINB, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_snapshot_tma<WARPS, MINB, MIXED, NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot_tma<WARPS, MINB, MIXED>, 32 * WARPS, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot_tma<WARPS, MINB, MIXED, NORM>, 32 * WARPS, smem) !=
             cudaSuccess || v < 1)
         v = 1;
     return v;
 }
 
-template <int WARPS, int MINB, bool MIXED>
+template <int WARPS, int MINB, bool MIXED, bool NORM = false>
 void launch_v(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err, long long wl,
-              cudaStream_t st) {
+              cudaStream_t st, double *partials = nullptr) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, WARPS);
     const auto *mp = reinterpret_cast<const CUtensorMap *>(M.P);
     const auto *mu = reinterpret_cast<const CUtensorMap *>(M.U);
     const auto *mw = reinterpret_cast<const CUtensorMap *>(M.W);
     const auto *mf = reinterpret_cast<const CUtensorMap *>(M.F);
     const auto *mr = reinterpret_cast<const CUtensorMap *>(L.has_rhs ? M.R : M.F);
-    k_snapshot_tma<WARPS, MINB, MIXED><<<grid, block, snap_smem<WARPS, MINB, MIXED>(), st>>>(L, area, *mp, *mu, *mw,
-                                                                                           *mf, *mr, err, wl);
+    k_snapshot_tma<WARPS, MINB, MIXED, NORM><<<grid, block, snap_smem<WARPS, MINB, MIXED>(), st>>>(
+        L, area, *mp, *mu, *mw, *mf, *mr, err, wl, partials);
 }
 
 template <bool MIXED>
@@ -245,6 +266,8 @@ void prepare_snapshot_tma() {
     g_snap_occ.per_sm[1][0] = snap_attr<32, 1, true>();
     g_snap_occ.per_sm[1][1] = snap_attr<16, 1, true>();
     g_snap_occ.per_sm[1][2] = snap_attr<8, 7, true>();
+    (void)snap_attr<8, 7, false, true>();
+    (void)snap_attr<8, 7, true, true>();
 }
 
 bool encode_snapshot_maps(const LevelView<float> &L, SnapMaps *M) {
@@ -262,6 +285,12 @@ void launch_snapshot_tma(const LevelView<float> &L, const double *area, const Sn
                          long long wait_limit, cudaStream_t st) {
     if (M.mixed) launch_mixed<true>(L, area, M, err, wait_limit, st);
     else launch_mixed<false>(L, area, M, err, wait_limit, st);
+}
+
+void launch_snapshot_norm_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, double *partials,
+                              int *err, long long wait_limit, cudaStream_t st) {
+    if (M.mixed) launch_v<8, 7, true, true>(L, area, M, err, wait_limit, st, partials);
+    else launch_v<8, 7, false, true>(L, area, M, err, wait_limit, st, partials);
 }
 
 }  // namespace segmg
