@@ -160,6 +160,24 @@ def test_graph_and_eager_launches_agree(segmg):
     assert np.array_equal(outs[0], outs[1])
 
 
+def test_device_step_loop_equals_host_driven_step(segmg):
+    # a whole pseudo-time step run as one graph launch (the device step loop, whose V-cycle norm
+    # is computed by the next V-cycle's first snapshot) and the same step run V-cycle by V-cycle
+    # from the host with eager launches (the separate norm kernel): same V-cycles, same rho,
+    # same phi, bitwise; FP32 and mixed storage
+    img, mk, _ = synth.ellipses(192, 176, 8, (16, 70), 6, 0.05, 19)
+    for prec in (segmg.MG_F32, segmg.MG_MIXED):
+        res = []
+        for g in (1, 0):
+            s, _ = gpu_solver(segmg, img, mk, precision=prec, levels=6, use_graph=g)
+            cyc, rho = s.solve_step(1e-6, 50)
+            res.append((cyc, rho, s.phi().cpu().numpy(), s.stats()["tau"]))
+            s.close()
+        assert res[0][0] == res[1][0] and res[0][1] == res[1][1] and res[0][3] == res[1][3]
+        assert np.array_equal(res[0][2], res[1][2])
+        assert res[0][1] <= 1e-6
+
+
 def test_host_pipeline_matches_device_pipeline(segmg):
     img, mk, _ = synth.ellipses(256, 256, 10, (20, 80), 8, 0.05, 4)
     p = segmg.default_params(256, 256)
