@@ -101,3 +101,16 @@ def test_bounds_checked_build_compiles_and_exports_every_symbol():
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (mg_\w+)", out))
     assert not set(declared_functions()) - exported
+
+
+def test_segment_host_binding_refuses_a_bad_mask_buffer_before_any_call(libpath):
+    # the mask buffer is written by the library: wrong shape, type or layout is refused first
+    import numpy as np
+    from paper_1807_02137_gb300 import segmg
+    p = segmg.default_params(16, 16)
+    img = np.zeros((16, 16), np.float32)
+    mk = np.array([[8.0, 8.0]])
+    for bad in (np.zeros((16, 15), np.uint8), np.zeros((16, 16), np.int32), np.zeros((16, 32), np.uint8)[:, ::2]):
+        with pytest.raises(TypeError, match="mask_out"):
+            segmg.segment_host(img, mk, p, mask_out=bad)
+    segmg.segment_host_release()   # nothing kept: a no-op without a device
