@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256, MINB)
         }
     }
     if (mode == 0 && partials) {
-        double s = block_sum((double)acc, red);
+        double s = block_sum_warps(acc, red);
         if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
     }
 }
@@ -213,11 +213,14 @@ __global__ void k_sum_partials(const double *partials, int np, double *out) {
     if (threadIdx.x == 0) *out = s;
 }
 
+// Full weighting of up to three fields of one grid in one launch (blockIdx.z picks the field).
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict(const T *f, int n, int m, int pf, T *c, T *c2, int pc) {
+__global__ void __launch_bounds__(256) k_restrict(RestrictFields<T> F, int n, int m, int pf, int pc) {
     const int J = blockIdx.x * 32 + threadIdx.x, I = blockIdx.y * 8 + threadIdx.y;
     const int nc = n / 2, mc = m / 2;
     if (I >= nc || J >= mc) return;
+    const T *f = F.f[blockIdx.z];
+    T *c = F.c[blockIdx.z], *c2 = F.c2[blockIdx.z];
     int ri[3], ci[3];
     float rw[3], cw[3];
     int nr = fw_taps(I, n, ri, rw), nk = fw_taps(J, m, ci, cw);
@@ -318,13 +321,20 @@ void launch_residual(const LevelView<T> &L, const T *uin, const double *area, T 
                                                                       norm_out ? partials : nullptr);
     else
         k_residual<T><<<grid, block, 0, st>>>(L, uin, area, out, mode, norm_out ? partials : nullptr);
-    if (mode == 0 && norm_out) k_sum_partials<<<1, 1024, 0, st>>>(partials, npart, norm_out);
+    if (mode == 0 && norm_out) k_sum_partials<<<1, 256, 0, st>>>(partials, npart, norm_out);
 }
 
 template <typename T>
 void launch_restrict(const T *f, int n, int m, int pf, T *c, T *c2, int pc, cudaStream_t st) {
-    dim3 grid((m / 2 + 31) / 32, (n / 2 + 7) / 8), block(32, 8);
-    k_restrict<T><<<grid, block, 0, st>>>(f, n, m, pf, c, c2, pc);
+    RestrictFields<T> F{};
+    F.f[0] = f; F.c[0] = c; F.c2[0] = c2; F.nf = 1;
+    launch_restrict_fields(F, n, m, pf, pc, st);
+}
+
+template <typename T>
+void launch_restrict_fields(const RestrictFields<T> &F, int n, int m, int pf, int pc, cudaStream_t st) {
+    dim3 grid((m / 2 + 31) / 32, (n / 2 + 7) / 8, F.nf), block(32, 8);
+    k_restrict<T><<<grid, block, 0, st>>>(F, n, m, pf, pc);
 }
 
 template <typename T>
@@ -336,7 +346,7 @@ void launch_interp_add(const LevelView<T> &Lf, const LevelView<T> &Lc, cudaStrea
 constexpr size_t kCoarseSmemMax = 200 * 1024;
 
 void launch_sum_partials(const double *partials, int np, double *out, cudaStream_t st) {
-    k_sum_partials<<<1, 1024, 0, st>>>(partials, np, out);
+    k_sum_partials<<<1, 256, 0, st>>>(partials, np, out);
 }
 
 void launch_residual_restrict(const LevelView<float> &L, const LevelView<float> &C, const double *area,
@@ -376,6 +386,7 @@ void launch_coarse_solve(const LevelView<T> &L, int fp64, ModelParams mp, double
     template void launch_residual<T>(const LevelView<T> &, const T *, const double *, T *, int,    \
                                      double *, int, double *, cudaStream_t);                       \
     template void launch_restrict<T>(const T *, int, int, int, T *, T *, int, cudaStream_t);       \
+    template void launch_restrict_fields<T>(const RestrictFields<T> &, int, int, int, int, cudaStream_t); \
     template void launch_interp_add<T>(const LevelView<T> &, const LevelView<T> &, cudaStream_t);  \
     template void launch_coarse_solve<T>(const LevelView<T> &, int, ModelParams, double,            \
                                          double, int, double, double *, Scalars *, int, double,     \

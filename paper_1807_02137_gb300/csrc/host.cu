@@ -94,14 +94,6 @@ __global__ void k_step_loop(cudaGraphConditionalHandle h, Scalars *sc, double to
     cudaGraphSetConditional(h, stop == 0 ? 1u : 0u);
 }
 
-__global__ void k_check_finite(const void *img, int is_double, size_t N, int *flag) {
-    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; q < N; q += (size_t)gridDim.x * blockDim.x) {
-        double v = is_double ? ((const double *)img)[q] : (double)((const float *)img)[q];
-        if (!isfinite(v)) { atomicOr(flag, 2); return; }
-    }
-}
-
 template <typename T>
 __global__ void k_phi_out(const T *pn, const T *u, int n, int m, int p, T *out) {
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
@@ -212,6 +204,7 @@ struct Solver final : SolverBase {
     double *coarse = nullptr;
     double *dmk = nullptr;    // markers (2 * kcap)
     double *dhull = nullptr;  // hull (2 * kcap + 4)
+    double *hstage = nullptr; // pinned host staging of markers, hull and A1 / (n m) (6 kcap + 9)
     int kcap = 0;
     double A1 = 0, res0 = 0, rho = 0, eta = 0;
     int steps = 0, cycles_step = 0, cycles_total = 0;
@@ -288,6 +281,8 @@ struct Solver final : SolverBase {
         pool = nullptr;
         if (hsc) cudaFreeHost(hsc);
         hsc = nullptr;
+        if (hstage) cudaFreeHost(hstage);
+        hstage = nullptr;
         if (own_stream && st) cudaStreamDestroy(st);
         st = nullptr;
     }
@@ -367,6 +362,7 @@ struct Solver final : SolverBase {
         dmk = (double *)(base + o_mk);
         dhull = (double *)(base + o_hull);
         CK(cudaMallocHost(&hsc, sizeof(Scalars)));
+        CK(cudaMallocHost(&hstage, sizeof(double) * (6 * (size_t)kcap + 9)));
         if constexpr (std::is_same<T, float>::value) {
             if (p.smoother == MG_SMOOTH_FUSED)
                 for (int l = 0; l < nlev; ++l)
@@ -491,7 +487,7 @@ struct Solver final : SolverBase {
 
     int energy(double *E) override {
         launch_energy<T>(view(0), mp, partials, npart, dsc, &dsc->sums[7], st);
-        ++launches;
+        launches += 2;
         CKL();
         CK(cudaMemcpyAsync(E, &dsc->sums[7], sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -532,17 +528,9 @@ struct Solver final : SolverBase {
         rho = eta = res0 = 0;
         Level<T> &L0 = lv[0];
         CK(cudaMemsetAsync(dsc, 0, sizeof(Scalars), st));
-        {
-            size_t N = (size_t)n * m;
-            int blocks = (int)std::min<size_t>((N + 255) / 256, 4096);
-            k_check_finite<<<blocks, 256, 0, st>>>(image, sizeof(T) == 8, N, &dsc->err);
-            CKL();
-            int flag = 0;
-            CK(cudaMemcpyAsync(&flag, &dsc->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (flag & 2) return fail(MG_ERR_NAN, "image has NaN or Inf values");
-        }
-        launch_copy_in<T>((const T *)image, L0.z, n, m, L0.pitch, st);
+        // the image's finiteness is checked while it is copied in and read back at the end of
+        // the set-up (no value of the image decides an index, so a NaN only spoils values)
+        launch_copy_in<T>((const T *)image, L0.z, n, m, L0.pitch, &dsc->err, st);
         // blur taps (Sec. 2.2 edge detector applied to the smoothed image)
         int R = std::min(16, (int)std::ceil(3.0 * p.sigma_blur));
         std::vector<double> taps(2 * R + 1);
@@ -550,13 +538,19 @@ struct Solver final : SolverBase {
         for (int t = -R; t <= R; ++t) { taps[t + R] = std::exp(-(double)t * t / (2 * p.sigma_blur * p.sigma_blur)); s += taps[t + R]; }
         for (double &t : taps) t /= s;
         launch_blur<T>(L0.z, L0.G, L0.f, n, m, L0.pitch, L0.pitch, taps.data(), R, st);
-        CK(cudaMemcpyAsync(dmk, mk, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, st));
+        // markers, hull and the initial area go through pinned staging (asynchronous copies)
+        double *smk = hstage, *shull = hstage + 2 * kcap, *sA1 = hstage + 6 * kcap + 8;
+        std::memcpy(smk, mk, sizeof(double) * 2 * k);
+        CK(cudaMemcpyAsync(dmk, smk, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, st));
         launch_edge_distance<T>(L0.f, L0.w, L0.d, n, m, L0.pitch, p.beta_edge, dmk, k, p.sigma_d, p.model, st);
         for (int l = 1; l < nlev; ++l) {
             Level<T> &Pf = lv[l - 1], &Lc = lv[l];
-            launch_restrict<T>(Pf.w, Pf.n, Pf.m, Pf.pitch, Lc.w, nullptr, Lc.pitch, st);
-            launch_restrict<T>(Pf.z, Pf.n, Pf.m, Pf.pitch, Lc.z, nullptr, Lc.pitch, st);
-            launch_restrict<T>(Pf.d, Pf.n, Pf.m, Pf.pitch, Lc.d, nullptr, Lc.pitch, st);
+            RestrictFields<T> F{};
+            F.f[0] = Pf.w; F.c[0] = Lc.w;
+            F.f[1] = Pf.z; F.c[1] = Lc.z;
+            F.f[2] = Pf.d; F.c[2] = Lc.d;
+            F.nf = 3;
+            launch_restrict_fields<T>(F, Pf.n, Pf.m, Pf.pitch, Lc.pitch, st);
         }
         if (p.precision == MG_MIXED)   // w in BF16 on every grid (restricted in FP32 first)
             for (int l = 0; l < nlev; ++l)
@@ -577,15 +571,23 @@ struct Solver final : SolverBase {
             cx /= k; cy /= k;
             area = M_PI * r0 * r0;
         } else {
-            CK(cudaMemcpyAsync(dhull, hull.data(), sizeof(double) * hull.size(), cudaMemcpyHostToDevice, st));
+            std::memcpy(shull, hull.data(), sizeof(double) * hull.size());
+            CK(cudaMemcpyAsync(dhull, shull, sizeof(double) * hull.size(), cudaMemcpyHostToDevice, st));
         }
         A1 = area;
         launch_initial_phi<T>(L0.pn, L0.u, n, m, L0.pitch, dhull, nh, cx, cy, r0, st);
-        double A1frac = area / ((double)n * m);
-        CK(cudaMemcpyAsync(&dsc->A1frac, &A1frac, sizeof(double), cudaMemcpyHostToDevice, st));
+        *sA1 = area / ((double)n * m);
+        CK(cudaMemcpyAsync(&dsc->A1frac, sA1, sizeof(double), cudaMemcpyHostToDevice, st));
         launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
+        // copy-in, two blur passes, edge / distance, initial phi, region sums (2), restrictions
+        launches += 7 + (nlev - 1) + (p.precision == MG_MIXED ? nlev : 0);
         CKL();
-        CK(cudaStreamSynchronize(st));   // host marker / hull buffers go out of scope
+        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));   // the staging buffer is free again; the image's check
+        if (hsc->err & 2) {
+            CK(cudaMemsetAsync(&dsc->err, 0, sizeof(int), st));
+            return fail(MG_ERR_NAN, "image has NaN or Inf values");
+        }
         return MG_OK;
     }
 
@@ -605,9 +607,12 @@ struct Solver final : SolverBase {
             Level<T> &Pf = lv[l - 1], &Lc = lv[l];
             launch_restrict<T>(Pf.pn, Pf.n, Pf.m, Pf.pitch, Lc.pn, nullptr, Lc.pitch, st);
         }
-        for (int l = 0; l < nlev; ++l) launch_fitting<T>(view(l), dsc, mp, st);
+        LevelView<T> views[kMaxLevels];
+        for (int l = 0; l < nlev; ++l) views[l] = view(l);
+        launch_fitting<T>(views, nlev, dsc, mp, st);
         area_term(0, lv[0].u);
         norm_residual(&dsc->norm2_0);
+        launches += 1 + (nlev - 1) + 1 + area_launches() + 2;   // fold, restrictions, fitting, norm
         CKL();
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1314,6 +1319,7 @@ struct Solver final : SolverBase {
         Range range("end step");
         if (!in_step) return fail(MG_ERR_STATE, "mg_end_step before mg_begin_step");
         launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
+        launches += 2;
         CKL();
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1326,6 +1332,7 @@ struct Solver final : SolverBase {
 
     int mask(unsigned char *out) override {
         launch_mask<T>(view(0), out, st);
+        ++launches;
         CKL();
         CK(cudaStreamSynchronize(st));
         return MG_OK;
@@ -1334,6 +1341,7 @@ struct Solver final : SolverBase {
     int get_phi(void *out) override {
         dim3 grid((m + 31) / 32, (n + 7) / 8);
         k_phi_out<T><<<grid, dim3(32, 8), 0, st>>>(lv[0].pn, lv[0].u, n, m, lv[0].pitch, (T *)out);
+        ++launches;
         CKL();
         CK(cudaStreamSynchronize(st));
         return MG_OK;

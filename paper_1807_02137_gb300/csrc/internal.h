@@ -102,8 +102,10 @@ void launch_blur(const T *src, T *tmp, T *dst, int n, int m, int pitch_src, int 
 template <typename T>
 void launch_edge_distance(const T *zb, T *w, T *d, int n, int m, int pitch, double beta_edge,
                           const double *mk, int k, double sigma_d, int model, cudaStream_t st);
+// The n x m image (row-major, no padding) into the pitched finest z; bit 2 of *flag is set
+// when a value is NaN or Inf.
 template <typename T>
-void launch_copy_in(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st);
+void launch_copy_in(const T *src, T *dst, int n, int m, int pitch, int *flag, cudaStream_t st);
 template <typename T>
 void launch_copy_out(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st);
 template <typename T>
@@ -111,8 +113,25 @@ void launch_initial_phi(T *pn, T *u, int n, int m, int pitch, const double *hull
                         double cx, double cy, double r0, cudaStream_t st);
 template <typename T>
 void launch_restrict(const T *f, int n, int m, int pf, T *c, T *c2, int pc, cudaStream_t st);
+// Up to three fields of the same grid restricted in one launch (c2[q] may be NULL).
 template <typename T>
-void launch_fitting(const LevelView<T> &L, const Scalars *sc, ModelParams mp, cudaStream_t st);
+struct RestrictFields {
+    const T *f[3];
+    T *c[3], *c2[3];
+    int nf;
+};
+template <typename T>
+void launch_restrict_fields(const RestrictFields<T> &F, int n, int m, int pf, int pc, cudaStream_t st);
+// Per-grid pointers and sizes of the fitting fields of all grids (one launch).
+template <typename T>
+struct FitGrids {
+    const T *z[kMaxLevels], *d[kMaxLevels];
+    T *F[kMaxLevels];
+    int n[kMaxLevels], m[kMaxLevels], pitch[kMaxLevels], first_block[kMaxLevels];
+    int nlev;
+};
+template <typename T>
+void launch_fitting(const LevelView<T> *L, int nlev, const Scalars *sc, ModelParams mp, cudaStream_t st);
 template <typename T>
 void launch_fold(const LevelView<T> &L, cudaStream_t st);
 template <typename T>

@@ -31,11 +31,14 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxTiles + 1];
 std::mutex g_mu;
 double *g_addr[kMaxDevices] = {};
 
-__device__ double block_sum_na(double v, double *red) {
+// Block sum as the solver's norm kernels form it: each warp adds its lanes in C (the storage
+// precision of the norm's per-thread sums), the warp sums are added in FP64.
+template <typename C>
+__device__ double block_sum_na(C v, double *red) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = v;
+    if ((tid & 31) == 0) red[tid >> 5] = (double)v;
     __syncthreads();
     if (tid < 32) {
         double s = tid < (nt + 31) / 32 ? red[tid] : 0.0;
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(256) k_residual_static(const T *phi, const T *
         T r = -Lv;
         acc = add_square(acc, r);
     }
-    double s = block_sum_na((double)acc, red);
+    double s = block_sum_na(acc, red);
     if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
@@ -116,7 +119,7 @@ int run(const void *phi, const void *w, const void *F, int n, int m, const mg_pa
     dim3 grid((m + 31) / 32, (n + 31) / 32), block(32, 8);
     k_residual_static<T><<<grid, block, 0, st>>>((const T *)phi, (const T *)w, (const T *)F, n, m,
                                                  (T)(p->mu), (T)0.5, (T)p->beta, scratch);
-    k_sum_static<<<1, 1024, 0, st>>>(scratch, (int)(grid.x * grid.y), scratch + kNoAllocMaxTiles);
+    k_sum_static<<<1, 256, 0, st>>>(scratch, (int)(grid.x * grid.y), scratch + kNoAllocMaxTiles);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MG_OK : err(MG_ERR_CUDA, cudaGetErrorString(e));
 }

@@ -22,6 +22,28 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return r;
 }
 
+// Sum of a per-thread value of type C over the block, returned to every thread: each warp adds
+// its 32 values in C (pairwise, by shuffles), the warp sums are added in FP64 as in block_sum.
+// FP64 arithmetic costs much more than FP32 here, so an FP32 value leaves only the block's
+// few warp sums to FP64; for C = double this is block_sum.  Fixed order: deterministic.
+template <typename C>
+__device__ __forceinline__ double block_sum_warps(C v, double *red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = (double)v;
+    __syncthreads();
+    if (tid < 32) {
+        double s = tid < (nt + 31) / 32 ? red[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (tid == 0) red[32] = s;
+    }
+    __syncthreads();
+    double r = red[32];
+    __syncthreads();
+    return r;
+}
+
 __device__ __forceinline__ double block_max(double v, double *red) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256, MINB)
         else cell(k, std::false_type{});
     }
     if (NORM) {
-        const double s = block_sum((double)acc, S.red);
+        const double s = block_sum_warps(acc, S.red);
         if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
     }
 }

@@ -1,6 +1,7 @@
 // setup_kernels.cu -- image-derived data (Sec. 2.2), initial level set and per-step fields
 // (Sec. 5), region averages (eq. c1c2), mask and the Rada-Chen area term.
 #include "arith.cuh"
+#include "reduce.cuh"
 
 namespace segmg {
 
@@ -15,8 +16,10 @@ __device__ __forceinline__ int mirror(int t, int n) {
     return t;
 }
 
+// Blur taps in the accumulation type of the blur: FP32 for the FP32 path, FP64 for FP64.
+template <typename A>
 struct Taps {
-    double w[33];
+    A w[33];
 };
 
 template <typename T>
@@ -26,38 +29,67 @@ __global__ void k_copy(const T *src, int ps, T *dst, int pd, int n, int m) {
         stc(dst, (size_t)i * pd + j, (size_t)n * pd, kDbgSetup, ldc(src, (size_t)i * ps + j, (size_t)n * ps, kDbgSetup));
 }
 
+// The image copied into the finest grid's z; bit 2 of *flag is set when a value is NaN or Inf.
+template <typename T>
+__global__ void k_copy_check(const T *src, T *dst, int pd, int n, int m, int *flag) {
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+    bool bad = false;
+    if (i < n && j < m) {
+        const T v = ldc(src, (size_t)i * m + j, (size_t)n * m, kDbgSetup);
+        bad = !isfinite(v);
+        stc(dst, (size_t)i * pd + j, (size_t)n * pd, kDbgSetup, v);
+    }
+    if (__any_sync(0xffffffffu, bad) && threadIdx.x == 0) atomicOr(flag, 2);
+}
+
 // Separable Gaussian G_sigma * z with mirror boundary; `dir` 0 = along rows, 1 = along columns.
 template <typename T>
-__global__ void k_blur(const T *src, T *dst, int n, int m, int ps, int pd, Taps tp, int R, int dir) {
+__global__ void k_blur(const T *src, T *dst, int n, int m, int ps, int pd, Taps<T> tp, int R, int dir) {
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
     if (i >= n || j >= m) return;
     const size_t lim = (size_t)n * ps;
-    double a = 0.0;
+    T a = T(0);
     for (int t = -R; t <= R; ++t) {
-        double v = dir == 0 ? (double)ldc(src, (size_t)i * ps + mirror(j + t, m), lim, kDbgSetup)
-                            : (double)ldc(src, (size_t)mirror(i + t, n) * ps + j, lim, kDbgSetup);
+        const T v = dir == 0 ? ldc(src, (size_t)i * ps + mirror(j + t, m), lim, kDbgSetup)
+                             : ldc(src, (size_t)mirror(i + t, n) * ps + j, lim, kDbgSetup);
         a += tp.w[t + R] * v;
     }
-    stc(dst, (size_t)i * pd + j, (size_t)n * pd, kDbgSetup, (T)a);
+    stc(dst, (size_t)i * pd + j, (size_t)n * pd, kDbgSetup, a);
 }
 
 // Edge detector g = 1 / (1 + beta_edge |grad (G*z)|^2) (central differences, mirror ghosts),
 // distance function d = prod_k (1 - exp(-dx^2 / 2s^2) exp(-dy^2 / 2s^2)) and the length
-// weight w = g (Spencer-Chen) or d g (Rada-Chen).
+// weight w = g (Spencer-Chen) or d g (Rada-Chen).  Arithmetic in the storage precision; the
+// two exponential factors of a marker depend on the column alone and on the row alone, so a
+// block of 32 x 8 cells evaluates them once per column and row (40 instead of 256 per marker).
 template <typename T>
-__global__ void k_edge_distance(const T *zb, T *w, T *d, int n, int m, int p, double beta_edge,
-                                const double *mk, int k, double sigma_d, int model) {
-    // arithmetic in the storage precision (FP32 exp for the FP32 path)
-    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
+__global__ void __launch_bounds__(256) k_edge_distance(const T *zb, T *w, T *d, int n, int m, int p, T beta_edge,
+                                                       const double *mk, int k, T inv_s2, int model) {
+    constexpr int KC = 32;                       // markers per shared-memory chunk
+    __shared__ T ex[KC][32], ey[KC][8];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 8, j = j0 + tx, i = i0 + ty;
+    T dd = T(1);
+    for (int q0 = 0; q0 < k; q0 += KC) {
+        const int kc = min(KC, k - q0);
+        __syncthreads();                         // the previous chunk's factors are used up
+        for (int e = tid; e < kc * 32; e += 256) {
+            const int q = e >> 5, c = e & 31;
+            const T dx = T(mk[2 * (q0 + q)]) - T(j0 + c);
+            ex[q][c] = exp(-dx * dx * inv_s2);
+        }
+        for (int e = tid; e < kc * 8; e += 256) {
+            const int q = e >> 3, r = e & 7;
+            const T dy = T(mk[2 * (q0 + q) + 1]) - T(i0 + r);
+            ey[q][r] = exp(-dy * dy * inv_s2);
+        }
+        __syncthreads();
+        for (int q = 0; q < kc; ++q) dd *= T(1) - ex[q][tx] * ey[q][ty];
+    }
     if (i >= n || j >= m) return;
     T zx = (zb[(size_t)i * p + mirror(j + 1, m)] - zb[(size_t)i * p + mirror(j - 1, m)]) * T(0.5);
     T zy = (zb[(size_t)mirror(i + 1, n) * p + j] - zb[(size_t)mirror(i - 1, n) * p + j]) * T(0.5);
-    T g = T(1) / (T(1) + T(beta_edge) * (zx * zx + zy * zy));
-    T inv_s2 = T(1.0 / (2.0 * sigma_d * sigma_d)), dd = T(1);
-    for (int q = 0; q < k; ++q) {
-        T dx = T(mk[2 * q]) - T(j), dy = T(mk[2 * q + 1]) - T(i);
-        dd *= T(1) - exp(-dx * dx * inv_s2) * exp(-dy * dy * inv_s2);
-    }
+    T g = T(1) / (T(1) + beta_edge * (zx * zx + zy * zy));
     size_t o = (size_t)i * p + j;
     const size_t lim = (size_t)n * p;
     stc(d, o, lim, kDbgSetup, dd);
@@ -65,46 +97,67 @@ __global__ void k_edge_distance(const T *zb, T *w, T *d, int n, int m, int p, do
 }
 
 // Signed distance (px, positive inside) to the boundary of a convex polygon given counter-
-// clockwise, or to a circle of radius r0 about (cx, cy) when nh == 0.
+// clockwise, or to a circle of radius r0 about (cx, cy) when nh == 0.  The polygon's vertices
+// go through shared memory in the storage precision, 64 edges at a time.
 template <typename T>
-__global__ void k_initial_phi(T *pn, T *u, int n, int m, int p, const double *hull, int nh,
-                              double cx, double cy, double r0) {
+__global__ void __launch_bounds__(256) k_initial_phi(T *pn, T *u, int n, int m, int p, const double *hull, int nh,
+                                                     T cx, T cy, T r0) {
+    constexpr int EC = 64;                       // edges per shared-memory chunk
+    __shared__ T hx[EC + 1], hy[EC + 1];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
-    if (i >= n || j >= m) return;
     T px = T(j), py = T(i), val;
     if (nh == 0) {
-        val = T(r0) - sqrt((px - T(cx)) * (px - T(cx)) + (py - T(cy)) * (py - T(cy)));
+        val = r0 - sqrt((px - cx) * (px - cx) + (py - cy) * (py - cy));
     } else {
         T dmin = T(1e30);
         bool inside = true;
-        for (int q = 0; q < nh; ++q) {
-            int r = q + 1 == nh ? 0 : q + 1;
-            T ax = T(hull[2 * q]), ay = T(hull[2 * q + 1]), bx = T(hull[2 * r]), by = T(hull[2 * r + 1]);
-            T ex = bx - ax, ey = by - ay;
-            if (ex * (py - ay) - ey * (px - ax) < T(0)) inside = false;
-            T t = ((px - ax) * ex + (py - ay) * ey) / (ex * ex + ey * ey);
-            t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
-            T dx = px - (ax + t * ex), dy = py - (ay + t * ey);
-            dmin = fmin(dmin, sqrt(dx * dx + dy * dy));
+        for (int q0 = 0; q0 < nh; q0 += EC) {
+            const int ec = min(EC, nh - q0);
+            __syncthreads();
+            if (tid <= ec) {                     // vertices q0 .. q0 + ec (the last wraps to 0)
+                const int v = q0 + tid == nh ? 0 : q0 + tid;
+                hx[tid] = T(hull[2 * v]);
+                hy[tid] = T(hull[2 * v + 1]);
+            }
+            __syncthreads();
+            for (int e = 0; e < ec; ++e) {
+                const T ax = hx[e], ay = hy[e], bx = hx[e + 1], by = hy[e + 1];
+                const T ex = bx - ax, ey = by - ay;
+                if (ex * (py - ay) - ey * (px - ax) < T(0)) inside = false;
+                T t = ((px - ax) * ex + (py - ay) * ey) / (ex * ex + ey * ey);
+                t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+                const T dx = px - (ax + t * ex), dy = py - (ay + t * ey);
+                dmin = fmin(dmin, sqrt(dx * dx + dy * dy));
+            }
         }
         val = inside ? dmin : -dmin;
     }
+    if (i >= n || j >= m) return;
     size_t o = (size_t)i * p + j;
     const size_t lim = (size_t)n * p;
     stc(pn, o, lim, kDbgSetup, val);
     stc(u, o, lim, kDbgSetup, T(0));
 }
 
-// Fitting field of the step: lambda1 (z - c1)^2 - lambda2 (z - c2)^2 (+ theta d for SC).
+// Fitting field of the step on every grid in one launch: lambda1 (z - c1)^2 - lambda2 (z - c2)^2
+// (+ theta d for SC), in the storage precision.  Blocks of 32 x 8 cells, numbered grid by grid.
 template <typename T>
-__global__ void k_fitting(LevelView<T> L, const Scalars *sc, ModelParams mp) {
-    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y * 8 + threadIdx.y;
-    if (i >= L.n || j >= L.m) return;
-    size_t o = (size_t)i * L.pitch + j;
-    double z = (double)L.z[o], c1 = sc->c1, c2 = sc->c2;
-    double F = mp.lambda1 * (z - c1) * (z - c1) - mp.lambda2 * (z - c2) * (z - c2);
-    if (mp.model == 0) F += mp.theta * (double)L.d[o];
-    stc(L.F, o, (size_t)L.n * L.pitch, kDbgSetup, (T)F);
+__global__ void __launch_bounds__(256) k_fitting(FitGrids<T> G, const Scalars *sc, T lambda1, T lambda2, T theta,
+                                                 int model) {
+    __shared__ T c12[2];             // c1, c2 converted once per block
+    if (threadIdx.x < 2 && threadIdx.y == 0) c12[threadIdx.x] = T(threadIdx.x == 0 ? sc->c1 : sc->c2);
+    __syncthreads();
+    int l = 0;
+    while (l + 1 < G.nlev && (int)blockIdx.x >= G.first_block[l + 1]) ++l;
+    const int b = blockIdx.x - G.first_block[l], bx = (G.m[l] + 31) / 32;
+    const int j = (b % bx) * 32 + threadIdx.x, i = (b / bx) * 8 + threadIdx.y;
+    if (i >= G.n[l] || j >= G.m[l]) return;
+    const size_t o = (size_t)i * G.pitch[l] + j;
+    const T z = G.z[l][o], c1 = c12[0], c2 = c12[1];
+    T F = lambda1 * (z - c1) * (z - c1) - lambda2 * (z - c2) * (z - c2);
+    if (model == 0) F += theta * G.d[l][o];
+    stc(G.F[l], o, (size_t)G.n[l] * G.pitch[l], kDbgSetup, F);
 }
 
 // phi^n <- phi^n + u, u <- 0 (start of a pseudo-time step on the finest grid).
@@ -136,10 +189,12 @@ __device__ double block_sum_setup(double v, double *red) {
 }
 
 // Per-block partial sums over 32 x 32 tiles of: H z, H, (1-H) z, (1-H), u^2, pn^2 with
-// H = H_eps(pn + u) = 1/2 + atan((pn + u) / eps) / pi (Sec. 2.1).
+// H = H_eps(pn + u) = 1/2 + atan((pn + u) / eps) / pi (Sec. 2.1).  Each warp sums its 128 cells
+// in the storage precision (pairwise, by shuffles); the block's eight warp sums are added in
+// FP64 in a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_region_partials(LevelView<T> L, double eps, double *part) {
-    __shared__ double red[33];
+__global__ void __launch_bounds__(256) k_region_partials(LevelView<T> L, T eps, double *part) {
+    __shared__ double red[6][8];
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tid = threadIdx.y * 32 + threadIdx.x;
     T s[6] = {0, 0, 0, 0, 0, 0};     // per-thread sums in the storage precision (4 cells)
     for (int q = tid; q < 1024; q += 256) {
@@ -147,26 +202,35 @@ __global__ void __launch_bounds__(256) k_region_partials(LevelView<T> L, double 
         if (gi >= L.n || gj >= L.m) continue;
         size_t o = (size_t)gi * L.pitch + gj;
         T pn = L.pn[o], u = L.u[o], z = L.z[o];
-        T H = T(0.5) + atan((pn + u) / T(eps)) * T(M_1_PI);
+        T H = T(0.5) + atan((pn + u) / eps) * T(M_1_PI);
         s[0] += H * z; s[1] += H; s[2] += (T(1) - H) * z; s[3] += T(1) - H; s[4] += u * u; s[5] += pn * pn;
     }
-    const int b = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+#pragma unroll
     for (int k = 0; k < 6; ++k) {
-        double v = block_sum_setup((double)s[k], red);
-        if (tid == 0) part[(size_t)k * nb + b] = v;
+        T v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[k][tid >> 5] = (double)v;
+    }
+    __syncthreads();
+    if (tid < 6) {
+        const double *r = red[tid];
+        const double a0 = r[0] + r[4], a1 = r[1] + r[5], a2 = r[2] + r[6], a3 = r[3] + r[7];
+        const int b = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+        part[(size_t)tid * nb + b] = (a0 + a2) + (a1 + a3);
     }
 }
 
-__global__ void k_region_final(const double *part, int nb, Scalars *sc, int set_c) {
-    __shared__ double red[33];
-    double tot[6];
-    for (int k = 0; k < 6; ++k) {
-        double v = 0.0;
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) v += part[(size_t)k * nb + q];
-        tot[k] = block_sum_setup(v, red);
-    }
+// The six totals over the per-block partials (one warp per total, FP64) and c1, c2 (eq. c1c2).
+__global__ void __launch_bounds__(192) k_region_final(const double *part, int nb, Scalars *sc, int set_c) {
+    __shared__ double tot[6];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int q = lane; q < nb; q += 32) v += part[(size_t)k * nb + q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) tot[k] = v;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 6; ++k) sc->sums[k] = tot[k];
+        for (int q = 0; q < 6; ++q) sc->sums[q] = tot[q];
         if (set_c) {
             sc->c1 = tot[1] > 0 ? tot[0] / tot[1] : 0.0;
             sc->c2 = tot[3] > 0 ? tot[2] / tot[3] : 0.0;
@@ -239,7 +303,7 @@ __global__ void k_energy_final(const double *part, int nb, ModelParams mp, doubl
 
 // Rada-Chen area term 2 nu (h^2 sum H(pn + uin) / (n0 m0) - A1 / (n0 m0)) of one grid.
 template <typename T>
-__global__ void __launch_bounds__(256) k_area_partials(LevelView<T> L, const T *uin, double eps, double *part) {
+__global__ void __launch_bounds__(256) k_area_partials(LevelView<T> L, const T *uin, T eps, double *part) {
     __shared__ double red[33];
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, tid = threadIdx.y * 32 + threadIdx.x;
     T s = T(0);
@@ -247,9 +311,9 @@ __global__ void __launch_bounds__(256) k_area_partials(LevelView<T> L, const T *
         int gi = i0 + q / 32, gj = j0 + q % 32;
         if (gi >= L.n || gj >= L.m) continue;
         size_t o = (size_t)gi * L.pitch + gj;
-        s += T(0.5) + atan((L.pn[o] + uin[o]) / T(eps)) * T(M_1_PI);
+        s += T(0.5) + atan((L.pn[o] + uin[o]) / eps) * T(M_1_PI);
     }
-    double v = block_sum_setup((double)s, red);
+    double v = block_sum_warps(s, red);
     if (tid == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = v;
 }
 
@@ -289,8 +353,8 @@ void launch_energy(const LevelView<T> &L, ModelParams mp, double *partials, int 
 
 
 template <typename T>
-void launch_copy_in(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st) {
-    k_copy<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(src, m, dst, pitch, n, m);
+void launch_copy_in(const T *src, T *dst, int n, int m, int pitch, int *flag, cudaStream_t st) {
+    k_copy_check<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(src, dst, pitch, n, m, flag);
 }
 template <typename T>
 void launch_copy_out(const T *src, T *dst, int n, int m, int pitch, cudaStream_t st) {
@@ -300,8 +364,8 @@ void launch_copy_out(const T *src, T *dst, int n, int m, int pitch, cudaStream_t
 template <typename T>
 void launch_blur(const T *src, T *tmp, T *dst, int n, int m, int pitch_src, int pitch, const double *taps,
                  int R, cudaStream_t st) {
-    Taps tp;
-    for (int t = 0; t <= 2 * R && t < 33; ++t) tp.w[t] = taps[t];
+    Taps<T> tp;
+    for (int t = 0; t <= 2 * R && t < 33; ++t) tp.w[t] = T(taps[t]);
     k_blur<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(src, tmp, n, m, pitch_src, pitch, tp, R, 0);
     k_blur<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(tmp, dst, n, m, pitch, pitch, tp, R, 1);
 }
@@ -309,19 +373,29 @@ void launch_blur(const T *src, T *tmp, T *dst, int n, int m, int pitch_src, int 
 template <typename T>
 void launch_edge_distance(const T *zb, T *w, T *d, int n, int m, int pitch, double beta_edge,
                           const double *mk, int k, double sigma_d, int model, cudaStream_t st) {
-    k_edge_distance<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(zb, w, d, n, m, pitch, beta_edge, mk, k,
-                                                            sigma_d, model);
+    const T inv_s2 = T(1.0 / (2.0 * sigma_d * sigma_d));
+    k_edge_distance<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(zb, w, d, n, m, pitch, T(beta_edge), mk, k,
+                                                            inv_s2, model);
 }
 
 template <typename T>
 void launch_initial_phi(T *pn, T *u, int n, int m, int pitch, const double *hull, int nh, double cx,
                         double cy, double r0, cudaStream_t st) {
-    k_initial_phi<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(pn, u, n, m, pitch, hull, nh, cx, cy, r0);
+    k_initial_phi<T><<<grid2(n, m), dim3(32, 8), 0, st>>>(pn, u, n, m, pitch, hull, nh, T(cx), T(cy), T(r0));
 }
 
 template <typename T>
-void launch_fitting(const LevelView<T> &L, const Scalars *sc, ModelParams mp, cudaStream_t st) {
-    k_fitting<T><<<grid2(L.n, L.m), dim3(32, 8), 0, st>>>(L, sc, mp);
+void launch_fitting(const LevelView<T> *L, int nlev, const Scalars *sc, ModelParams mp, cudaStream_t st) {
+    FitGrids<T> G{};
+    int blocks = 0;
+    G.nlev = nlev;
+    for (int l = 0; l < nlev; ++l) {
+        G.z[l] = L[l].z; G.d[l] = L[l].d; G.F[l] = L[l].F;
+        G.n[l] = L[l].n; G.m[l] = L[l].m; G.pitch[l] = L[l].pitch;
+        G.first_block[l] = blocks;
+        blocks += ((L[l].m + 31) / 32) * ((L[l].n + 7) / 8);
+    }
+    k_fitting<T><<<blocks, dim3(32, 8), 0, st>>>(G, sc, T(mp.lambda1), T(mp.lambda2), T(mp.theta), mp.model);
 }
 
 template <typename T>
@@ -333,16 +407,16 @@ template <typename T>
 void launch_region_sums(const LevelView<T> &L, double eps, double *partials, int npart, Scalars *sc,
                         int finalize_c, cudaStream_t st) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
-    k_region_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, eps, partials);
-    k_region_final<<<1, 1024, 0, st>>>(partials, npart, sc, finalize_c);
+    k_region_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, T(eps), partials);
+    k_region_final<<<1, 192, 0, st>>>(partials, npart, sc, finalize_c);
 }
 
 template <typename T>
 void launch_area(const LevelView<T> &L, const T *uin, double eps, double nu, double h2nm,
                  double *partials, int npart, double *out, const Scalars *sc, cudaStream_t st) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
-    k_area_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, uin, eps, partials);
-    k_area_final<<<1, 1024, 0, st>>>(partials, npart, nu, h2nm, sc, out);
+    k_area_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, uin, T(eps), partials);
+    k_area_final<<<1, 256, 0, st>>>(partials, npart, nu, h2nm, sc, out);
 }
 
 template <typename T>
@@ -355,7 +429,7 @@ void launch_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, int pitc
 }
 
 #define INST(T)                                                                                      \
-    template void launch_copy_in<T>(const T *, T *, int, int, int, cudaStream_t);                    \
+    template void launch_copy_in<T>(const T *, T *, int, int, int, int *, cudaStream_t);             \
     template void launch_copy_out<T>(const T *, T *, int, int, int, cudaStream_t);                   \
     template void launch_blur<T>(const T *, T *, T *, int, int, int, int, const double *, int,        \
                                  cudaStream_t);                                                       \
@@ -363,7 +437,7 @@ void launch_to_bf16(const float *src, __nv_bfloat16 *dst, int n, int m, int pitc
                                           int, double, int, cudaStream_t);                            \
     template void launch_initial_phi<T>(T *, T *, int, int, int, const double *, int, double, double, \
                                         double, cudaStream_t);                                        \
-    template void launch_fitting<T>(const LevelView<T> &, const Scalars *, ModelParams, cudaStream_t); \
+    template void launch_fitting<T>(const LevelView<T> *, int, const Scalars *, ModelParams, cudaStream_t); \
     template void launch_fold<T>(const LevelView<T> &, cudaStream_t);                                \
     template void launch_region_sums<T>(const LevelView<T> &, double, double *, int, Scalars *, int,  \
                                         cudaStream_t);                                                \

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
             members_of(v, lenc));
     }
     if (NORM) {
-        const double s = block_sum((double)acc, S.red);
+        const double s = block_sum_warps(acc, S.red);
         if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
     }
 }
