@@ -418,6 +418,15 @@ void mg_batch_destroy(mg_batch b);
  * [5] the residual kernel to ms[0..5].  Changes phi like real smoothing does.  Waits. */
 int mg_time_kernels(mg_handle h, int level, int reps, double *ms);
 
+/* Times, on grid `level` inside a step, the residual kernels a V-cycle runs there, `reps` times
+ * each (CUDA events on the handle's stream): mean milliseconds of [0] the residual norm
+ * ||rhs - L(phi)|| (the per-tile kernel and the final FP64 sum; the norm goes to a scratch
+ * slot, not to the step's norms) and [1] the residual with full weighting into grid level + 1
+ * (Sec. 3.1: the coarse right-hand side's restriction and the restriction of u; -1 on the
+ * coarsest grid) to ms[0..1].  Writes grid level + 1's right-hand side, u and u0 as a V-cycle
+ * does.  MG_ERR_STATE outside a step, MG_ERR_ARG for a bad level or reps < 1.  Waits. */
+int mg_time_residuals(mg_handle h, int level, int reps, double *ms);
+
 /* Residual norm ||L(phi)||_2 of one grid function, with no device allocation.  The paper has no
  * counterpart: this serves callers that cannot allocate device memory when they need the norm,
  * such as code whose device memory is owned by a framework's pool or a running real-time loop

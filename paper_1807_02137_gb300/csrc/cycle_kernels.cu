@@ -204,12 +204,18 @@ __global__ void __launch_bounds__(256) k_residual_restrict(LevelView<float> L, L
     }
 }
 
-// Sums `np` partials in a fixed order into *out.
-__global__ void k_sum_partials(const double *partials, int np, double *out) {
+// stage[k * gridDim.x + b] = sum of chunk b of the k-th array of np partials (blockIdx.y = k).
+__global__ void __launch_bounds__(256) k_chunk_sums(const double *part, int np, double *stage) {
     __shared__ double red[33];
-    double v = 0.0;
-    for (int q = threadIdx.x; q < np; q += blockDim.x) v += partials[q];
-    double s = block_sum(v, red);
+    const int b = blockIdx.x, k = blockIdx.y;
+    const double s = chunk_sum(part + (size_t)k * np, b * kSumChunk, min(np, (b + 1) * kSumChunk), red);
+    if (threadIdx.x == 0) stage[(size_t)k * gridDim.x + b] = s;
+}
+
+// Sums `np` partials in a fixed order into *out (one block).
+__global__ void __launch_bounds__(256) k_sum_partials(const double *partials, int np, double *out) {
+    __shared__ double red[33];
+    const double s = chunk_sum(partials, 0, np, red);
     if (threadIdx.x == 0) *out = s;
 }
 
@@ -321,7 +327,7 @@ void launch_residual(const LevelView<T> &L, const T *uin, const double *area, T 
                                                                       norm_out ? partials : nullptr);
     else
         k_residual<T><<<grid, block, 0, st>>>(L, uin, area, out, mode, norm_out ? partials : nullptr);
-    if (mode == 0 && norm_out) k_sum_partials<<<1, 256, 0, st>>>(partials, npart, norm_out);
+    if (mode == 0 && norm_out) launch_sum_partials(partials, npart, norm_out, st);
 }
 
 template <typename T>
@@ -345,8 +351,18 @@ void launch_interp_add(const LevelView<T> &Lf, const LevelView<T> &Lc, cudaStrea
 
 constexpr size_t kCoarseSmemMax = 200 * 1024;
 
-void launch_sum_partials(const double *partials, int np, double *out, cudaStream_t st) {
-    k_sum_partials<<<1, 256, 0, st>>>(partials, np, out);
+void launch_chunk_sums(const double *part, int np, int K, double *stage, cudaStream_t st) {
+    k_chunk_sums<<<dim3(sum_blocks(np), K), 256, 0, st>>>(part, np, stage);
+}
+
+void launch_sum_partials(double *partials, int np, double *out, cudaStream_t st) {
+    const int G = sum_blocks(np);
+    if (G == 1) {
+        k_sum_partials<<<1, 256, 0, st>>>(partials, np, out);
+    } else {   // the chunk sums go to the G doubles after the partials
+        launch_chunk_sums(partials, np, 1, partials + np, st);
+        k_sum_partials<<<1, 256, 0, st>>>(partials + np, G, out);
+    }
 }
 
 void launch_residual_restrict(const LevelView<float> &L, const LevelView<float> &C, const double *area,

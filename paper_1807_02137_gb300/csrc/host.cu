@@ -150,6 +150,7 @@ struct SolverBase {
     virtual int stats(mg_stats *s) = 0;
     virtual cudaStream_t stream() const = 0;
     virtual int time_kernels(int level, int reps, double *ms) = 0;
+    virtual int time_residuals(int level, int reps, double *ms) = 0;
     virtual int autotune(int reps, int *out) = 0;
     virtual int set_shapes(const int *shapes) = 0;
     virtual int set_bottom(int enable) = 0;
@@ -476,7 +477,7 @@ struct Solver final : SolverBase {
         }
         area_term(0, lv[0].u);
         norm_residual(&dsc->norm2);
-        launches += area_launches() + 2;
+        launches += area_launches() + norm_launches();
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         rho = res0 > 0 ? std::sqrt(hsc->norm2) / res0 : std::sqrt(hsc->norm2);
@@ -580,7 +581,7 @@ struct Solver final : SolverBase {
         CK(cudaMemcpyAsync(&dsc->A1frac, sA1, sizeof(double), cudaMemcpyHostToDevice, st));
         launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
         // copy-in, two blur passes, edge / distance, initial phi, region sums (2), restrictions
-        launches += 7 + (nlev - 1) + (p.precision == MG_MIXED ? nlev : 0);
+        launches += 5 + norm_launches() + (nlev - 1) + (p.precision == MG_MIXED ? nlev : 0);
         CKL();
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));   // the staging buffer is free again; the image's check
@@ -612,7 +613,7 @@ struct Solver final : SolverBase {
         launch_fitting<T>(views, nlev, dsc, mp, st);
         area_term(0, lv[0].u);
         norm_residual(&dsc->norm2_0);
-        launches += 1 + (nlev - 1) + 1 + area_launches() + 2;   // fold, restrictions, fitting, norm
+        launches += 1 + (nlev - 1) + 1 + area_launches() + norm_launches();   // fold, restrictions, fitting, norm
         CKL();
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -633,7 +634,10 @@ struct Solver final : SolverBase {
     }
 
     // kernels per call of each enqueue helper (for the launch counter)
-    int area_launches() const { return p.model == MG_MODEL_RC ? 2 : 0; }
+    // (a chunked FP64 sum adds a launch above 1024 partials)
+    int sum_launches(int l) const { return num_partials(lv[l].n, lv[l].m) > 1024 ? 2 : 1; }
+    int area_launches(int l = 0) const { return p.model == MG_MODEL_RC ? 1 + sum_launches(l) : 0; }
+    int norm_launches(int l = 0) const { return 1 + sum_launches(l); }
     bool fused() const { return p.smoother == MG_SMOOTH_FUSED || p.smoother == MG_SMOOTH_FUSED_VEC; }
     // kernels of one outer smoothing iteration after the snapshot on grid l
     int smoother_launches(int l) const {
@@ -691,7 +695,7 @@ struct Solver final : SolverBase {
         LevelView<T> v = view(l);
         if (l == 0 && skip_first_snapshot) {
             skip_first_snapshot = 0;   // area term and snapshot are in the loop's first part
-            launches -= area_launches() + 1;
+            launches -= area_launches(l) + 1;
         } else {
             area_term(l, lv[l].u);
             snapshot(l, v);
@@ -702,7 +706,7 @@ struct Solver final : SolverBase {
             ++launches;
         }
         relax(l, v, shape[l]);
-        launches += area_launches() + 1 + smoother_launches(l);
+        launches += area_launches(l) + 1 + smoother_launches(l);
     }
 
     void cycle(int l) {
@@ -744,7 +748,7 @@ struct Solver final : SolverBase {
             launch_residual_tma(view(l + 1), 1, area_ptr(), C.rhs, 1, partials, 0, nullptr, C.smaps, C.rmaps, &dsc->err,
                                 wait_limit, st);
         else launch_residual<T>(view(l + 1), C.u0, area_ptr(), C.rhs, 1, partials, 0, nullptr, st);
-        launches += 2 * area_launches() + 1;
+        launches += area_launches(l) + area_launches(l + 1) + 1;
         cycle(l + 1);
         launch_interp_add<T>(view(l), view(l + 1), st);
         ++launches;
@@ -755,7 +759,7 @@ struct Solver final : SolverBase {
         cycle(0);
         area_term(0, lv[0].u);
         norm_residual(&dsc->norm2);
-        launches += area_launches() + 2;
+        launches += area_launches() + norm_launches();
         if (readback) cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
     }
 
@@ -1106,7 +1110,7 @@ struct Solver final : SolverBase {
         if constexpr (std::is_same<T, float>::value)
             launch_snapshot_norm_tma(view(0), area_ptr(), lv[0].smaps, partials, &dsc->err, wait_limit, st);
         launch_sum_partials(partials, npart, &dsc->norm2, st);
-        *nodes = area_launches() + 2;
+        *nodes = area_launches() + 1 + sum_launches(0);
         cudaError_t e = cudaStreamEndCapture(st, g);
         if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
         return MG_OK;
@@ -1319,7 +1323,7 @@ struct Solver final : SolverBase {
         Range range("end step");
         if (!in_step) return fail(MG_ERR_STATE, "mg_end_step before mg_begin_step");
         launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
-        launches += 2;
+        launches += norm_launches();   // region partials and their (chunked) sums
         CKL();
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1425,7 +1429,7 @@ struct Solver final : SolverBase {
                                     &dsc->err, wait_limit, st);
             else launch_residual<T>(v, lv[l].u, area_ptr(), lv[l].r, 0, partials, 0, nullptr, st);
             cudaEventRecord(ev[6], st);
-            launches += area_launches() + 2 + smoother_launches(l);
+            launches += area_launches(l) + 2 + smoother_launches(l);
             CKL();
             CK(cudaEventSynchronize(ev[6]));
             for (int k = 0; k < 6; ++k) {
@@ -1436,6 +1440,53 @@ struct Solver final : SolverBase {
         }
         for (auto &e : ev) cudaEventDestroy(e);
         for (int k = 0; k < 6; ++k) ms[k] = acc[k] / reps;
+        return MG_OK;
+    }
+
+    // The residual kernels a V-cycle runs on grid l: [0] the residual norm (the tile kernel and
+    // the final sum; the norm goes to a scratch slot), [1] the residual with full weighting into
+    // grid l + 1 (-1 on the coarsest grid).  Writes grid l + 1's rhs, u and u0.
+    int time_residuals(int l, int reps, double *ms) override {
+        if (l < 0 || l >= nlev || reps < 1) return fail(MG_ERR_ARG, "level / reps");
+        if (!in_step) return fail(MG_ERR_STATE, "mg_time_residuals outside a step");
+        cudaEvent_t ev[3];
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        double acc[2] = {0, 0};
+        const LevelView<T> v = view(l);
+        const int np = num_partials(lv[l].n, lv[l].m);
+        for (int r = 0; r < reps; ++r) {
+            area_term(l, lv[l].u);
+            cudaEventRecord(ev[0], st);
+            if constexpr (std::is_same<T, float>::value)
+                launch_residual_tma(v, 0, area_ptr(), nullptr, 0, partials, np, &dsc->sums[6], lv[l].smaps,
+                                    lv[l].rmaps, &dsc->err, wait_limit, st);
+            else launch_residual<T>(v, lv[l].u, area_ptr(), lv[l].r, 0, partials, np, &dsc->sums[6], st);
+            cudaEventRecord(ev[1], st);
+            launches += area_launches(l) + norm_launches(l);
+            if (l + 1 < nlev) {
+                Level<T> &L = lv[l], &C = lv[l + 1];
+                if constexpr (std::is_same<T, float>::value) {
+                    launch_residual_restrict_tma(v, view(l + 1), area_ptr(), L.rmaps, &dsc->err, wait_limit, st);
+                    launches += 1;
+                } else {
+                    launch_residual<T>(v, L.u, area_ptr(), L.r, 0, partials, 0, nullptr, st);
+                    launch_restrict<T>(L.r, L.n, L.m, L.pitch, C.rhs, nullptr, C.pitch, st);
+                    launch_restrict<T>(L.u, L.n, L.m, L.pitch, C.u, C.u0, C.pitch, st);
+                    launches += 3;
+                }
+            }
+            cudaEventRecord(ev[2], st);
+            CKL();
+            CK(cudaEventSynchronize(ev[2]));
+            float t0 = 0, t1 = 0;
+            cudaEventElapsedTime(&t0, ev[0], ev[1]);
+            cudaEventElapsedTime(&t1, ev[1], ev[2]);
+            acc[0] += t0;
+            acc[1] += t1;
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        ms[0] = acc[0] / reps;
+        ms[1] = l + 1 < nlev ? acc[1] / reps : -1.0;
         return MG_OK;
     }
 };
@@ -2320,6 +2371,10 @@ void *mg_get_stream(mg_handle h) { return h ? (void *)h->s->stream() : nullptr; 
 
 int mg_time_kernels(mg_handle h, int level, int reps, double *ms) {
     return (h && ms) ? h->s->time_kernels(level, reps, ms) : fail(MG_ERR_ARG, "NULL argument");
+}
+
+int mg_time_residuals(mg_handle h, int level, int reps, double *ms) {
+    return (h && ms) ? h->s->time_residuals(level, reps, ms) : fail(MG_ERR_ARG, "NULL argument");
 }
 
 const char *mg_strerror(int code) {

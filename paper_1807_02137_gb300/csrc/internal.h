@@ -214,7 +214,11 @@ void launch_residual_tma(const LevelView<float> &L, int uin_is_u0, const double 
 void launch_residual_restrict_tma(const LevelView<float> &L, const LevelView<float> &C, const double *area,
                                   const ResMaps &R, int *err, long long wait_limit, cudaStream_t st);
 // Sums np FP64 partials in a fixed order into *out (one block).
-void launch_sum_partials(const double *partials, int np, double *out, cudaStream_t st);
+// Sum of np partials into *out in a fixed order.  Above 1024 partials the chunk sums are kept
+// in the ceil(np / 1024) doubles after the partials, so the buffer must hold that many more.
+void launch_sum_partials(double *partials, int np, double *out, cudaStream_t st);
+// stage[k * G + b] = sum of part[k * np + 1024 b .. 1024 (b + 1)) for k < K, G = ceil(np / 1024).
+void launch_chunk_sums(const double *part, int np, int K, double *stage, cudaStream_t st);
 void prepare_sweep_tma();
 bool encode_sweep_maps(const LevelView<float> &L, int shape, SweepMaps *M);
 // One n x m grid function (FP32: elem 4, BF16: elem 2) with row pitch `pitch` elements as a 2-D

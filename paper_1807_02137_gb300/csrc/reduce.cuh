@@ -44,6 +44,23 @@ __device__ __forceinline__ double block_sum_warps(C v, double *red) {
     return r;
 }
 
+// Sums of many per-block partials.  One block adding tens of thousands of FP64 values is bound
+// by its loads' latency and by one SM's FP64 rate, so above kSumChunk values the partials are
+// first cut into chunks, one block per chunk (k_chunk_sums), and the chunk sums are then added
+// in chunk order by one block: a fixed order, as before.
+constexpr int kSumChunk = 1024;
+
+// Sum of a[begin, end) over the block, returned to every thread.
+__device__ __forceinline__ double chunk_sum(const double *a, int begin, int end, double *red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    double v = 0.0;
+    for (int q = begin + tid; q < end; q += nt) v += a[q];
+    return block_sum(v, red);
+}
+
+// Chunks of the chunked sum of n partials (1: no chunk stage).
+inline int sum_blocks(int n) { return n > kSumChunk ? (n + kSumChunk - 1) / kSumChunk : 1; }
+
 __device__ __forceinline__ double block_max(double v, double *red) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));

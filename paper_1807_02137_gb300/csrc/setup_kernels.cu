@@ -220,15 +220,17 @@ __global__ void __launch_bounds__(256) k_region_partials(LevelView<T> L, T eps, 
     }
 }
 
-// The six totals over the per-block partials (one warp per total, FP64) and c1, c2 (eq. c1c2).
-__global__ void __launch_bounds__(192) k_region_final(const double *part, int nb, Scalars *sc, int set_c) {
-    __shared__ double tot[6];
-    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double v = 0.0;
-    for (int q = lane; q < nb; q += 32) v += part[(size_t)k * nb + q];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) tot[k] = v;
-    __syncthreads();
+// The six totals over n per-block (or per-chunk) partials of each sum (FP64, fixed order) and
+// c1, c2 (eq. c1c2).
+__global__ void __launch_bounds__(256) k_region_final(const double *part, int n, Scalars *sc, int set_c) {
+    __shared__ double red[33];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = threadIdx.x; q < n; q += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += part[(size_t)k * n + q];
+    double tot[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) tot[k] = block_sum(v[k], red);
     if (threadIdx.x == 0) {
         for (int q = 0; q < 6; ++q) sc->sums[q] = tot[q];
         if (set_c) {
@@ -317,12 +319,10 @@ __global__ void __launch_bounds__(256) k_area_partials(LevelView<T> L, const T *
     if (tid == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = v;
 }
 
-__global__ void k_area_final(const double *part, int nb, double nu, double h2nm, const Scalars *sc,
-                             double *out) {
+__global__ void __launch_bounds__(256) k_area_final(const double *part, int nb, double nu, double h2nm,
+                                                    const Scalars *sc, double *out) {
     __shared__ double red[33];
-    double v = 0.0;
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) v += part[q];
-    double s = block_sum_setup(v, red);
+    const double s = chunk_sum(part, 0, nb, red);
     if (threadIdx.x == 0) *out = 2.0 * nu * (h2nm * s - sc->A1frac);
 }
 
@@ -408,7 +408,12 @@ void launch_region_sums(const LevelView<T> &L, double eps, double *partials, int
                         int finalize_c, cudaStream_t st) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
     k_region_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, T(eps), partials);
-    k_region_final<<<1, 192, 0, st>>>(partials, npart, sc, finalize_c);
+    if (sum_blocks(npart) == 1) {
+        k_region_final<<<1, 256, 0, st>>>(partials, npart, sc, finalize_c);
+    } else {   // chunk sums of the six arrays after them
+        launch_chunk_sums(partials, npart, 6, partials + 6 * (size_t)npart, st);
+        k_region_final<<<1, 256, 0, st>>>(partials + 6 * (size_t)npart, sum_blocks(npart), sc, finalize_c);
+    }
 }
 
 template <typename T>
@@ -416,7 +421,12 @@ void launch_area(const LevelView<T> &L, const T *uin, double eps, double nu, dou
                  double *partials, int npart, double *out, const Scalars *sc, cudaStream_t st) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32);
     k_area_partials<T><<<grid, dim3(32, 8), 0, st>>>(L, uin, T(eps), partials);
-    k_area_final<<<1, 256, 0, st>>>(partials, npart, nu, h2nm, sc, out);
+    if (sum_blocks(npart) == 1) {
+        k_area_final<<<1, 256, 0, st>>>(partials, npart, nu, h2nm, sc, out);
+    } else {
+        launch_chunk_sums(partials, npart, 1, partials + npart, st);
+        k_area_final<<<1, 256, 0, st>>>(partials + npart, sum_blocks(npart), nu, h2nm, sc, out);
+    }
 }
 
 template <typename T>

@@ -713,3 +713,65 @@ def test_checkpoint_and_resume_at_a_step_boundary_is_bitwise(segmg):
     sa, sc = a.stats(), c.stats()
     assert (sa["c1"], sa["c2"], sa["tau"]) == (sc["c1"], sc["c2"], sc["tau"])
     a.close(); c.close()
+
+
+@pytest.mark.parametrize("k", [33, 150])
+def test_setup_fields_with_many_markers_on_a_circle(segmg, k):
+    # markers on a circle: every marker is a hull vertex, so the set-up handles more markers than
+    # one shared-memory chunk of the distance kernel (32) and, for k = 150, more hull edges than
+    # one chunk of the initial-level-set kernel (64); FP64 against the oracle
+    n, m = 150, 131
+    img, _, _ = synth.disc_square(150, 0.05, 3)
+    img = img[:n, :m].copy()
+    t = 2 * np.pi * np.arange(k) / k
+    mk = np.stack([65.0 + 40.0 * np.cos(t), 75.0 + 45.0 * np.sin(t)], axis=1)
+    s, o, p = both(segmg, img, mk, precision=segmg.MG_F64, levels=3)
+    for l in range(3):
+        for f in ("w", "z", "d"):
+            assert relmax(s.level(l, f).cpu().numpy(), o.level(l, f)) < 1e-13, (l, f)
+    assert relmax(s.phi().cpu().numpy(), o.phi) < 1e-13
+    st, so = s.stats(), o.scalars()
+    assert abs(st["c1"] - so["c1"]) < 1e-12 and abs(st["c2"] - so["c2"]) < 1e-12
+    assert abs(st["A1"] - so["A1"]) < 1e-9
+    # FP32 storage: the same fields to FP32 rounding
+    s32, _ = gpu_solver(segmg, img.astype(np.float32), mk, precision=segmg.MG_F32, levels=3)
+    for f in ("w", "d"):   # d: a product of k factors, each rounded in FP32
+        assert relmax(s32.level(0, f).cpu().numpy(), o.level(0, f)) < 3e-5, f
+    assert relmax(s32.phi().cpu().numpy(), o.phi) < 1e-6
+
+
+def test_reset_after_a_non_finite_image_recovers(segmg):
+    # the image check runs while the image is copied in and is read at the end of the set-up:
+    # a NaN image is refused with MG_ERR_NAN, and a following reset with a good image gives
+    # what a fresh handle gives, bitwise
+    img, mk, _ = synth.ellipses(96, 80, 6, (10, 50), 5, 0.05, 8)
+    s, p = gpu_solver(segmg, img, mk, levels=4)
+    bad = img.copy()
+    bad[50, 7] = np.inf
+    with pytest.raises(segmg.SegmgError) as e:
+        s.reset(torch.as_tensor(bad, device="cuda"), mk)
+    assert e.value.code == -2
+    s.reset(torch.as_tensor(img, device="cuda"), mk)
+    s.solve_step(1e-6, 40)
+    ref, _ = gpu_solver(segmg, img, mk, levels=4)
+    ref.solve_step(1e-6, 40)
+    assert np.array_equal(s.phi().cpu().numpy(), ref.phi().cpu().numpy())
+
+
+def test_time_residuals_reports_the_v_cycle_residual_kernels(segmg):
+    img, mk, _ = synth.ellipses(256, 200, 6, (20, 80), 5, 0.05, 4)
+    s, p = gpu_solver(segmg, img, mk, levels=5)
+    with pytest.raises(segmg.SegmgError) as e:
+        s.time_residuals(0, 1)
+    assert e.value.code == -8          # outside a step
+    s.begin_step()
+    for l in range(p.levels):
+        norm_ms, rr_ms = s.time_residuals(l, 2)
+        assert norm_ms > 0
+        assert (rr_ms > 0) if l + 1 < p.levels else rr_ms == -1.0
+    with pytest.raises(segmg.SegmgError):
+        s.time_residuals(p.levels, 1)
+    s.end_step()
+    # the timing runs leave the step's state usable: a fresh step still converges
+    cyc, rho = s.solve_step(1e-6, 60)
+    assert rho <= 1e-6
