@@ -74,7 +74,8 @@ __device__ __forceinline__ bool member(const TmaSmem<TS, STAGES> &S, int a, int 
 
 // One checkerboard phase over the box cells within distance 3 - ph of the output tile (the
 // cells and the operations of rb_phase in smooth_kernels.cu).
-template <typename TS, int STAGES, int SWEEP, bool INTERIOR, bool WEIGHTED>
+// MEMBERS = false: no line piece that crosses the box has a member cell, so no cell is skipped.
+template <typename TS, int STAGES, int SWEEP, bool INTERIOR, bool WEIGHTED, bool MEMBERS = true>
 __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const LevelView<float> &L, int ph, int i0,
                                          int j0) {
     constexpr int kRH = TS::RH, kRW = TS::RW;
@@ -94,7 +95,7 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
             if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
             hS = gi + 1 < n; hN = gi > 0; hE = gj + 1 < m; hW = gj > 0;
         }
-        if (member<TS, STAGES, (SWEEP < 2)>(S, a, b)) continue;
+        if (MEMBERS && member<TS, STAGES, (SWEEP < 2)>(S, a, b)) continue;
         const float gc = G[a][b];
         const float aS = face(gc, G[a + 1][b], hS), aN = face(gc, G[a - 1][b], hN);
         const float aE = face(gc, G[a][b + 1], hE), aW = face(gc, G[a][b - 1], hW);
@@ -154,12 +155,14 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
             }
         }
     };
-    auto store_masks = [&](const uint32_t (&w)[kMaskPer]) {   // true: a piece the line phases solve has a member
+    // true: a piece the line phases solve has a member; anym: some staged piece has one
+    auto store_masks = [&](const uint32_t (&w)[kMaskPer], bool &anym) {
         bool lm = false;
 #pragma unroll
         for (int r = 0; r < kMaskPer; ++r) {
             const int q = tid + r * TS::NT;
             if (q >= kMaskWords) continue;
+            anym |= w[r] != 0u;
             if (rowwise) {
                 const int a = q / kRowPieces, pc = q % kRowPieces;
                 S.mk[a][pc] = w[r];
@@ -197,7 +200,8 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
         if (STAGES == 2 && tid == 0 && next < ntiles) issue(next, st ^ 1);
         const int ty = tile / ntx, tx = tile - ty * ntx;
         const int i0 = ty * kOH, j0 = tx * kOW;
-        const bool lm = store_masks(mw);
+        bool anym = false;
+        const bool lm = store_masks(mw, anym);
         load_masks(next, mw);   // in flight while this tile is smoothed (zeros past the last tile)
         const bool ok = mbar_wait(&S.bar[st], parity, wait_limit);
         if (__syncthreads_or(!ok)) {
@@ -213,6 +217,7 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
             return;
         }
         const bool lines = __syncthreads_or(lm);
+        const bool members = __syncthreads_or(anym);   // else the checkerboard skips no cell
         float (*u)[kRW] = S.box[st][0];
         const float (*G)[kRW] = S.box[st][1];
         const float (*f)[kRW] = S.box[st][2];
@@ -224,8 +229,12 @@ __global__ void __launch_bounds__(TS::NT, TS::MinBlocks) k_sweep_tma(LevelView<f
                 if (interior) rb_phase<TS, STAGES, SWEEP, true, true>(S, st, L, ph, i0, j0);
                 else rb_phase<TS, STAGES, SWEEP, false, true>(S, st, L, ph, i0, j0);
             } else {
-                if (interior) rb_phase<TS, STAGES, SWEEP, true, false>(S, st, L, ph, i0, j0);
-                else rb_phase<TS, STAGES, SWEEP, false, false>(S, st, L, ph, i0, j0);
+                if (interior) {
+                    if (members) rb_phase<TS, STAGES, SWEEP, true, false>(S, st, L, ph, i0, j0);
+                    else rb_phase<TS, STAGES, SWEEP, true, false, false>(S, st, L, ph, i0, j0);
+                } else {
+                    rb_phase<TS, STAGES, SWEEP, false, false>(S, st, L, ph, i0, j0);
+                }
             }
             __syncthreads();
         }
