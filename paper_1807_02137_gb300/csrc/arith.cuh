@@ -37,6 +37,15 @@ __device__ __forceinline__ T face(T gc, T gn, bool has) {
     return has ? mul_rn(add_rn(gc, gn), T(0.5)) : T(0);
 }
 
+// Twice the face value, G_c + G_X.  A kernel whose faces only enter products and sums that are
+// then multiplied by cdiff can use these with cdiff / 2: halving is exact, so every product, sum
+// and the final values are the same numbers as with face() and cdiff (and comparisons between
+// faces keep their outcome), while the four multiplications by 1/2 drop out.
+template <typename T>
+__device__ __forceinline__ T face2(T gc, T gn, bool has) {
+    return has ? add_rn(gc, gn) : T(0);
+}
+
 // G = w / |grad phi|_beta at a cell from the four neighbour values of pn and u (central
 // differences, spacing h; mirror ghosts are supplied by the caller as clamped neighbours).
 // FP32 uses the hardware reciprocal square root (about 2 ulp); FP64 the IEEE square root and

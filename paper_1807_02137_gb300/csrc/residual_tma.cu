@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(256, MINB)
     }
     __syncthreads();
     const T ar = area ? T(area[L.level]) : T(0);
+    const T c2 = L.cdiff * T(0.5);
     const int gj = j0 + lane, c = lane + 4;
     const size_t lim = (size_t)n * p;
     T acc = T(0);
@@ -123,14 +124,14 @@ __global__ void __launch_bounds__(256, MINB)
         if (!(IN || (gi < n && gj < m))) return;
         const bool hS = IN || gi + 1 < n, hN = IN || gi > 0, hE = IN || gj + 1 < m, hW = IN || gj > 0;
         const T gc = S.W[a][c];
-        const T aS = face(gc, S.W[a + 1][c], hS), aN = face(gc, S.W[a - 1][c], hN);
-        const T aE = face(gc, S.W[a][c + 1], hE), aW = face(gc, S.W[a][c - 1], hW);
+        const T aS = face2(gc, S.W[a + 1][c], hS), aN = face2(gc, S.W[a - 1][c], hN);   // with c2 (arith.cuh)
+        const T aE = face2(gc, S.W[a][c + 1], hE), aW = face2(gc, S.W[a][c - 1], hW);
         const T pc = S.P[a][c], uc = S.U[a][c];
         T fl = mul_rn(aS, add_rn(sub_rn(S.P[a + 1][c], pc), sub_rn(S.U[a + 1][c], uc)));
         fl = fma_rn(aN, add_rn(sub_rn(S.P[a - 1][c], pc), sub_rn(S.U[a - 1][c], uc)), fl);
         fl = fma_rn(aE, add_rn(sub_rn(S.P[a][c + 1], pc), sub_rn(S.U[a][c + 1], uc)), fl);
         fl = fma_rn(aW, add_rn(sub_rn(S.P[a][c - 1], pc), sub_rn(S.U[a][c - 1], uc)), fl);
-        const T Lv = sub_rn(fma_rn(L.cdiff, fl, -add_rn(S.F[ti][lane], ar)), mul_rn(L.inv_tau, uc));
+        const T Lv = sub_rn(fma_rn(c2, fl, -add_rn(S.F[ti][lane], ar)), mul_rn(L.inv_tau, uc));
         const size_t o = (size_t)gi * p + gj;
         if (MODE == 0) {
             const T r = L.has_rhs ? sub_rn(S.X[ti][lane], Lv) : -Lv;
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(256, MINB)
     __syncthreads();
     // r on rows i0 .. i0+32, columns j0 .. j0+32 (zero outside the grid)
     const float ar = area ? float(area[L.level]) : 0.f;
+    const float c2 = L.cdiff * 0.5f;
     const bool rin = gin;   // every r cell has its four faces and its G ring inside the grid
     auto r_at = [&](int ti, int tj, auto in_tag) {
         constexpr bool IN = decltype(in_tag)::value;
@@ -247,14 +249,14 @@ __global__ void __launch_bounds__(256, MINB)
             const int a = ti + 2, c = tj + 4;   // box coordinates
             const bool hS = IN || gi + 1 < n, hN = IN || gi > 0, hE = IN || gj + 1 < m, hW = IN || gj > 0;
             const float gc = S.W[a][c];
-            const float aS = face(gc, S.W[a + 1][c], hS), aN = face(gc, S.W[a - 1][c], hN);
-            const float aE = face(gc, S.W[a][c + 1], hE), aW = face(gc, S.W[a][c - 1], hW);
+            const float aS = face2(gc, S.W[a + 1][c], hS), aN = face2(gc, S.W[a - 1][c], hN);   // with c2
+            const float aE = face2(gc, S.W[a][c + 1], hE), aW = face2(gc, S.W[a][c - 1], hW);
             const float pc = S.P[a][c], uc = S.U[a][c];
             float fl = mul_rn(aS, add_rn(sub_rn(S.P[a + 1][c], pc), sub_rn(S.U[a + 1][c], uc)));
             fl = fma_rn(aN, add_rn(sub_rn(S.P[a - 1][c], pc), sub_rn(S.U[a - 1][c], uc)), fl);
             fl = fma_rn(aE, add_rn(sub_rn(S.P[a][c + 1], pc), sub_rn(S.U[a][c + 1], uc)), fl);
             fl = fma_rn(aW, add_rn(sub_rn(S.P[a][c - 1], pc), sub_rn(S.U[a][c - 1], uc)), fl);
-            const float Lv = sub_rn(fma_rn(L.cdiff, fl, -add_rn(S.F[ti][tj], ar)), mul_rn(L.inv_tau, uc));
+            const float Lv = sub_rn(fma_rn(c2, fl, -add_rn(S.F[ti][tj], ar)), mul_rn(L.inv_tau, uc));
             r = L.has_rhs ? sub_rn(S.RH[ti][tj], Lv) : -Lv;
         }
         S.R[ti][tj] = r;

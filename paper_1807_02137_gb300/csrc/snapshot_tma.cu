@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
     const int gj = j0 + lane, c = lane + 4;
     const int lenr = min(32, m - j0), lenc = min(32, n - i0);
     T acc = T(0);   // NORM: this thread's sum of r^2
+    const T c2 = L.cdiff * T(0.5);
     // f, G and the jump-set class of tile row wy + WARPS k (IN: no bounds tests needed)
     auto cell = [&](int k, auto in_tag) -> uint32_t {
         constexpr bool IN = decltype(in_tag)::value;
@@ -137,8 +138,9 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         if (IN || (gi < n && gj < m)) {
             const bool hS = IN || gi + 1 < n, hN = IN || gi > 0, hE = IN || gj + 1 < m, hW = IN || gj > 0;
             const T gc = S.W[a][c];
-            const T aS = face(gc, S.W[a + 1][c], hS), aN = face(gc, S.W[a - 1][c], hN);
-            const T aE = face(gc, S.W[a][c + 1], hE), aW = face(gc, S.W[a][c - 1], hW);
+            // twice the faces, with c2 = cdiff / 2 (face2 in arith.cuh: the same values)
+            const T aS = face2(gc, S.W[a + 1][c], hS), aN = face2(gc, S.W[a - 1][c], hN);
+            const T aE = face2(gc, S.W[a][c + 1], hE), aW = face2(gc, S.W[a][c - 1], hW);
             const T pc = S.P[a][c];
             T ds = mul_rn(aS, sub_rn(S.P[a + 1][c], pc));
             ds = fma_rn(aN, sub_rn(S.P[a - 1][c], pc), ds);
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
             const size_t o = (size_t)gi * p + gj, lim = (size_t)n * p;
             T base = add_rn(S.F[ti][lane], ar);
             if (L.has_rhs) base = add_rn(base, S.R[ti][lane]);
-            stc(L.f, o, lim, kDbgSnapshot, fma_rn(-L.cdiff, ds, base));
+            stc(L.f, o, lim, kDbgSnapshot, fma_rn(-c2, ds, base));
             stc(L.G, o, lim, kDbgSnapshot, gc);
             // jump set D (Sec. 4.1): max > Sigma * min over the faces inside the domain; the
             // smallest coefficient, ties to the earlier of A, B, C, D (Sec. 4.1.3)
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
                 fl = fma_rn(aN, add_rn(sub_rn(S.P[a - 1][c], pc), sub_rn(S.U[a - 1][c], uc)), fl);
                 fl = fma_rn(aE, add_rn(sub_rn(S.P[a][c + 1], pc), sub_rn(S.U[a][c + 1], uc)), fl);
                 fl = fma_rn(aW, add_rn(sub_rn(S.P[a][c - 1], pc), sub_rn(S.U[a][c - 1], uc)), fl);
-                const T Lv = sub_rn(fma_rn(L.cdiff, fl, -add_rn(S.F[ti][lane], ar)), mul_rn(L.inv_tau, uc));
+                const T Lv = sub_rn(fma_rn(c2, fl, -add_rn(S.F[ti][lane], ar)), mul_rn(L.inv_tau, uc));
                 const T r = L.has_rhs ? sub_rn(S.R[ti][lane], Lv) : -Lv;
                 acc = add_square(acc, r);
             }

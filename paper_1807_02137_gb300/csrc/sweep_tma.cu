@@ -85,6 +85,7 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
     const float (*f)[kRW] = S.box[st][2];
     const int colour = rev ? 1 - ph : ph, lo = 1 + ph;
     const int n = L.n, m = L.m;
+    const float c2 = L.cdiff * 0.5f;   // with face2 (see arith.cuh)
     for (int q = threadIdx.x; q < (kRH / 2) * kRW; q += TS::NT) {
         const int pr = q / kRW, e = q - pr * kRW;
         const int a = 2 * pr + (e & 1), b = (e & ~1) + ((a + colour) & 1);
@@ -97,10 +98,10 @@ __device__ __forceinline__ void rb_phase(TmaSmem<TS, STAGES> &S, int st, const L
         }
         if (MEMBERS && member<TS, STAGES, (SWEEP < 2)>(S, a, b)) continue;
         const float gc = G[a][b];
-        const float aS = face(gc, G[a + 1][b], hS), aN = face(gc, G[a - 1][b], hN);
-        const float aE = face(gc, G[a][b + 1], hE), aW = face(gc, G[a][b - 1], hW);
-        float v = point_relax(L.cdiff, L.inv_tau, aS, aN, aE, aW, u[a + 1][b], u[a - 1][b], u[a][b + 1],
-                              u[a][b - 1], f[a][b]);
+        const float sS = face2(gc, G[a + 1][b], hS), sN = face2(gc, G[a - 1][b], hN);
+        const float sE = face2(gc, G[a][b + 1], hE), sW = face2(gc, G[a][b - 1], hW);
+        float v = point_relax(c2, L.inv_tau, sS, sN, sE, sW, u[a + 1][b], u[a - 1][b], u[a][b + 1], u[a][b - 1],
+                              f[a][b]);
         if (WEIGHTED) {
             const size_t o = (size_t)(i0 - kH + a) * L.pitch + (j0 - kH + b);
             v = relax_weighted(ldc(L.omega, o, (size_t)L.n * L.pitch, kDbgSweep), v, u[a][b]);
