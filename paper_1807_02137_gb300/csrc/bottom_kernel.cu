@@ -527,22 +527,15 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
     auto pr = [&](int a) { return min(max(a, 0), n - 1) - i0 + 1; };
     auto pc = [&](int b) { return min(max(b, 0), m - 1) - j0 + 1; };
     const int r0 = ti + 1, c0 = lane + 1, rS = pr(i + 1), rN = pr(i - 1), cE = pc(j + 1), cW = pc(j - 1);
-    // the ring of field f (0: pn, 1: u, 2: G) from the neighbouring tiles (after a cluster barrier)
+    // field f (0: pn, 1: u, 2: G) of a tile
     auto field = [&](CTile *t, int f) -> float (*)[kHP] { return f == 0 ? t->P : (f == 1 ? t->U : t->G); };
-    auto ring = [&](int f) {
-        if (q < 128) {
-            const int side = q >> 5, k = q & 31;
-            float (*X)[kHP] = field(&T, f);
-            if (side == 0) {
-                if (i0 > 0 && j0 + k < m) X[0][k + 1] = field(tp[rank - TX], f)[32][k + 1];
-            } else if (side == 1) {
-                if (i0 + 32 < n && j0 + k < m) X[33][k + 1] = field(tp[rank + TX], f)[1][k + 1];
-            } else if (side == 2) {
-                if (j0 > 0 && i0 + k < n) X[k + 1][0] = field(tp[rank - 1], f)[k + 1][32];
-            } else {
-                if (j0 + 32 < m && i0 + k < n) X[k + 1][33] = field(tp[rank + 1], f)[k + 1][1];
-            }
-        }
+    // value v of tile cell (a, b) of field f into the rings of the neighbouring tiles that hold it
+    // (a cell on the tile's edge; a remote store: the cluster barrier that follows publishes it)
+    auto push = [&](int f, int a, int b, float v) {
+        if (a == 0 && i0 > 0) field(tp[rank - TX], f)[33][b + 1] = v;
+        if (a == 31 && i0 + 32 < n) field(tp[rank + TX], f)[0][b + 1] = v;
+        if (b == 0 && j0 > 0) field(tp[rank - 1], f)[a + 1][33] = v;
+        if (b == 31 && j0 + 32 < m) field(tp[rank + 1], f)[a + 1][0] = v;
     };
     if (own) {
         const size_t o = (size_t)i * Lg.pitch + j, lim = (size_t)n * Lg.pitch;
@@ -555,17 +548,20 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
     // grids lc+1 .. L-1: every CTA carves the same offsets (CTA 0's arrays are then reached by
     // mapping this CTA's addresses); their pn, w, F are loaded
     bottom_setup(A, Bs, lc + 1, false, sm + kTileBytes, s_off);
+    cl.sync();   // every CTA of the cluster runs: its shared memory may be written
+    if (own) {
+        push(0, ti, lane, T.P[r0][c0]);
+        push(1, ti, lane, T.U[r0][c0]);
+    }
     cl.sync();
-    ring(0);
-    ring(1);
-    __syncthreads();
-    auto g_phase = [&]() {   // G at pn + u of the own cell, then its ring
-        if (own)
-            T.G[r0][c0] = cell_G(T.W[ti][lane], T.P[rS][c0], T.P[rN][c0], T.P[r0][cE], T.P[r0][cW], T.U[rS][c0],
-                                 T.U[rN][c0], T.U[r0][cE], T.U[r0][cW], inv_2h, beta);
+    auto g_phase = [&]() {   // G at pn + u of the own cell, into the neighbours' rings
+        if (own) {
+            const float g = cell_G(T.W[ti][lane], T.P[rS][c0], T.P[rN][c0], T.P[r0][cE], T.P[r0][cW], T.U[rS][c0],
+                                   T.U[rN][c0], T.U[r0][cE], T.U[r0][cW], inv_2h, beta);
+            T.G[r0][c0] = g;
+            push(2, ti, lane, g);
+        }
         cl.sync();
-        ring(2);
-        __syncthreads();
     };
     const bool hS = i + 1 < n, hN = i > 0, hE = j + 1 < m, hW = j > 0;
     const int colour = (i + j) & 1;
@@ -630,27 +626,33 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
                     num = fma_rn(aN, T.U[rN][c0], num);
                     num = fma_rn(aE, T.U[r0][cE], num);
                     num = fma_rn(aW, T.U[r0][cW], num);
-                    T.U[r0][c0] = div_relax(fma_rn(cdiff, num, -fq), dv);
+                    const float v = div_relax(fma_rn(cdiff, num, -fq), dv);
+                    T.U[r0][c0] = v;
+                    // the neighbours read only the other colour in this phase: the push can go now
+                    push(1, ti, lane, v);
                 }
                 cl.sync();
                 if (k == 0 && ph == 0)
                     for (int r = 0; r < (int)cl.num_blocks(); ++r) any |= tp[r]->any;
-                ring(1);
-                __syncthreads();
             }
             if (!((any >> k) & 1u)) continue;
             // partial-line phases: warp ti owns tile row ti (rowwise) or tile column ti
             for (int ph = 0; ph < 2; ++ph) {
-                cl.sync();   // every neighbour has copied this tile's ring cells
                 const int parity = rev ? 1 - ph : ph;
                 const int gl = (rowwise ? i0 : j0) + ti, llen = rowwise ? m : n, t0 = rowwise ? j0 : i0;
                 const int len = min(32, llen - t0);
                 const bool ok = gl < (rowwise ? n : m) && (gl & 1) == parity;
                 const uint32_t mk = ok ? (rowwise ? T.mrow[k][ti] : T.mcol[k - 2][ti]) : 0u;
+                // the end values (the neighbouring tiles' cells of this line) as the phase starts,
+                // read before the barrier after which this phase's pushes may overwrite them
+                float e0 = 0.f, e1 = 0.f;
                 if (mk) {
-                    float e0 = 0.f, e1 = 0.f, ownv = 0.f;
                     if (t0 > 0) e0 = rowwise ? T.U[r0][0] : T.U[0][r0];
                     if (t0 + len < llen) e1 = rowwise ? T.U[r0][len + 1] : T.U[len + 1][r0];
+                }
+                cl.sync();
+                if (mk) {
+                    float ownv = 0.f;
                     if (lane < len) ownv = rowwise ? T.U[r0][lane + 1] : T.U[lane + 1][r0];
                     __syncwarp();
                     auto at = [&](int r) -> RunCell<float> {
@@ -669,13 +671,17 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
                     };
                     float x;
                     if (pcr_piece<float>(mk, len, cdiff, inv_tau, ownv, e0, e1, at, x)) {
-                        if (rowwise) T.U[r0][lane + 1] = x;
-                        else T.U[lane + 1][r0] = x;
+                        // the neighbours read only lines of the other parity in this phase
+                        if (rowwise) {
+                            T.U[r0][lane + 1] = x;
+                            push(1, ti, lane, x);
+                        } else {
+                            T.U[lane + 1][r0] = x;
+                            push(1, lane, ti, x);
+                        }
                     }
                 }
                 cl.sync();
-                ring(1);
-                __syncthreads();
             }
         }
     };
@@ -744,12 +750,12 @@ __global__ void __launch_bounds__(kBT) k_cluster(BottomArgs A) {
                     const int o = ri[a] * C.m + ci[b];
                     sum = fma_rn((float)(rw[a] * cw[b]), sub_rn(Cu[o], Cu0[o]), sum);
                 }
-            T.U[r0][c0] = add_rn(T.U[r0][c0], sum);
+            const float v = add_rn(T.U[r0][c0], sum);
+            T.U[r0][c0] = v;
+            push(1, ti, lane, v);
         }
     }
     cl.sync();
-    ring(1);
-    __syncthreads();
     for (int t = 0; t < A.nu2; ++t) smooth();
     if (own) stc(Lg.u, (size_t)i * Lg.pitch + j, (size_t)n * Lg.pitch, kDbgBottom, T.U[r0][c0]);
     cl.sync();   // no CTA leaves while another may still read its shared memory
