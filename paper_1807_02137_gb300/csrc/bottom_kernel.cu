@@ -480,12 +480,13 @@ __global__ void __launch_bounds__(kBT) k_bottom(BottomArgs A) {
 // 64^2 every per-grid launch is latency-bound (a V-cycle spends about 23 launches per grid) while
 // one block is too little for the grid.  Here one 1024-thread CTA owns each 32 x 32 tile of grid
 // lc (one cell per thread, at most 16 tiles: one cluster) in its shared memory, pn, u and G with
-// a ring of the neighbouring tiles' edge cells.  After each phase a cluster barrier, then the
-// ring is copied from the neighbours' shared memory (distributed shared memory), so every phase
-// computes from local shared memory.  A checkerboard phase needs one barrier: a neighbour that
-// copies a ring cell after this CTA has already overwritten it (next colour) copies it again
-// before using it.  A partial-line phase writes cells whose start-of-phase values neighbours use
-// as end values, so it waits for every copy to finish first.  CTA 0 also holds grids
+// a ring of the neighbouring tiles' edge cells, so every phase computes from local shared
+// memory.  A thread that changes an edge cell also stores the value into the rings of the
+// neighbouring tiles (distributed shared memory); the cluster barrier after the phase publishes
+// it.  The store may land while a neighbour is still in the same phase: a checkerboard phase's
+// neighbours read only cells of the other colour, and a partial-line phase's neighbours read
+// only lines of the other parity, except for the end values of their own pieces, which every CTA
+// reads before a barrier at the start of the phase.  CTA 0 also holds grids
 // lc+1 .. L-1 and runs their sub-cycle (bottom_subcycle) between the restriction and the
 // interpolation.  Every cell performs the per-grid kernels' operations, so the results are the
 // same.
