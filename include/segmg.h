@@ -364,7 +364,10 @@ int mg_energy(mg_handle h, double *E);
  * per thread; larger grids run faster as per-grid launches), else the largest such grid;
  * mg_set_bottom_level and mg_autotune change it.  It performs the same operations per cell as
  * the per-grid kernels, so the results are identical.  enable = 1 (the default at set-up) or 0;
- * *first_level (may be NULL) gets the first grid it covers, -1 when it does not apply.
+ * *first_level (may be NULL) gets the first grid it covers, -1 when it does not apply.  At
+ * set-up the cluster bottom kernel (mg_set_cluster_level) is also chosen, from the largest grid
+ * the one-block kernel can start at, when that grid has at most 16 tiles of 32 x 32 and such a
+ * cluster fits the GPU; this call and mg_set_bottom_level switch the cluster off.
  * Errors: MG_ERR_ARG. */
 int mg_set_bottom_kernel(mg_handle h, int enable, int *first_level);
 /* Sets the first grid of the one-block bottom kernel (a tuning step of this implementation; the

@@ -393,8 +393,10 @@ def test_cluster_bottom_equals_one_block_and_per_grid(segmg, shape, levels, prec
     n, m = shape
     img, mk, _ = synth.ellipses(n, m, 14, (6, min(n, m) / 2), 6, 0.1, 91 + n)
     s, p = gpu_solver(segmg, img, mk, precision=prec, levels=levels)
+    # the default at set-up: the cluster from the largest grid the one-block kernel can start at
+    default_cluster = s.stats()["cluster_level"]
     first = largest_fitting_bottom(s, p.levels)
-    assert first >= 0
+    assert first >= 0 and default_cluster == first
     s.close()
     # the largest grid the one-block kernel can start at always fits a cluster here; the grid above it may
     # not (its cluster needs one SM per tile within one GPC), and is then refused
@@ -402,7 +404,10 @@ def test_cluster_bottom_equals_one_block_and_per_grid(segmg, shape, levels, prec
     outs = []
     for kind, lc in runs:
         s, p = gpu_solver(segmg, img, mk, precision=prec, levels=levels)
-        if kind == "none":
+        if kind == "one-block":
+            s.set_bottom_kernel(True)   # (the default at set-up may be the cluster)
+            assert s.stats()["cluster_level"] == -1
+        elif kind == "none":
             s.set_bottom_kernel(False)
         elif kind == "cluster":
             try:
