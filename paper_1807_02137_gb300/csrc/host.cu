@@ -221,6 +221,7 @@ struct Solver final : SolverBase {
     int shape[kMaxLevels] = {};   // fused-sweep tile shape per grid (mg_autotune)
     int lb = -1;                  // first grid of the one-block bottom kernel (-1: not used)
     int lb_first = -1;            // the largest grid it can start at (-1: it does not apply)
+    int fas_level = -1;           // the grid whose next snapshot completes its FAS right-hand side
     int lc = -1;                  // first grid of the cluster bottom kernel (-1: not used); it runs
                                   // grids lc .. nlev-1 (lb is then unused)
     int lc_tiles = 0;
@@ -719,7 +720,13 @@ struct Solver final : SolverBase {
             launches -= area_launches(l) + 1;
         } else {
             area_term(l, lv[l].u);
-            snapshot(l, v);
+            if (l == fas_level) {   // the first snapshot after the restriction also completes the rhs
+                if constexpr (std::is_same<T, float>::value)
+                    launch_snapshot_fas_tma(v, area_ptr(), lv[l].smaps, &dsc->err, wait_limit, st);
+                fas_level = -1;
+            } else {
+                snapshot(l, v);
+            }
         }
         if (use_omega && infer_pending[l] && omega_buf[l]) {
             launch_omega_infer<T>(v, net, omega_buf[l], st);   // weights from this snapshot's G
@@ -764,12 +771,22 @@ struct Solver final : SolverBase {
             launch_restrict<T>(L.u, L.n, L.m, L.pitch, C.u, C.u0, C.pitch, st);
             launches += 3;
         }
-        area_term(l + 1, C.u0);
-        if constexpr (std::is_same<T, float>::value)
-            launch_residual_tma(view(l + 1), 1, area_ptr(), C.rhs, 1, partials, 0, nullptr, C.smaps, C.rmaps, &dsc->err,
-                                wait_limit, st);
-        else launch_residual<T>(view(l + 1), C.u0, area_ptr(), C.rhs, 1, partials, 0, nullptr, st);
-        launches += area_launches(l) + area_launches(l + 1) + 1;
+        // FAS right-hand side on grid l+1: rhs += L(pn + u0).  FP32 storage with a pre-smoothing
+        // on grid l+1 by the per-grid kernels: its first snapshot completes it (fas_level);
+        // otherwise a residual launch here
+        const bool fas_in_snapshot = std::is_same<T, float>::value && p.nu1 >= 1 && l + 1 != lc && l + 1 != lb &&
+                                     l + 1 < nlev - 1;
+        if (fas_in_snapshot) {
+            fas_level = l + 1;
+            launches += area_launches(l);
+        } else {
+            area_term(l + 1, C.u0);
+            if constexpr (std::is_same<T, float>::value)
+                launch_residual_tma(view(l + 1), 1, area_ptr(), C.rhs, 1, partials, 0, nullptr, C.smaps, C.rmaps,
+                                    &dsc->err, wait_limit, st);
+            else launch_residual<T>(view(l + 1), C.u0, area_ptr(), C.rhs, 1, partials, 0, nullptr, st);
+            launches += area_launches(l) + area_launches(l + 1) + 1;
+        }
         cycle(l + 1);
         launch_interp_add<T>(view(l), view(l + 1), st);
         ++launches;

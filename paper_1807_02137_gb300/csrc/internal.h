@@ -190,6 +190,11 @@ void launch_snapshot_tma(const LevelView<float> &L, const double *area, const Sn
                          long long wait_limit, cudaStream_t st);
 // The same snapshot (8 warps per tile) that also writes each tile's sum of r^2, r = rhs - L(pn + u)
 // at the state it reads, to partials: bitwise the partials of launch_residual_tma's norm.
+// The first snapshot of a coarse grid right after its restriction (u = u0): also completes the
+// FAS right-hand side, rhs += L(pn + u0), written back and used in f (the separate mode-1
+// residual launch then does not run).
+void launch_snapshot_fas_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err,
+                             long long wait_limit, cudaStream_t st);
 void launch_snapshot_norm_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, double *partials,
                               int *err, long long wait_limit, cudaStream_t st);
 // Tensor maps of the TMA-staged residual kernels of one FP32 grid (residual_tma.cu): pn, u and w

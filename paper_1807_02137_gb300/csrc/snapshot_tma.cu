@@ -49,7 +49,12 @@ struct SnapTmaSmem {
 // NORM (8 warps): the block also writes sum r^2 of its tile, r = rhs - L(pn + u) at the state
 // the snapshot reads, to partials[block]: the operations and the order of k_residual_tma's norm
 // (the same G box, faces, flux and per-thread order), so the partials are bitwise its partials.
-template <int WARPS, int MINB, bool MIXED, bool NORM = false>
+// FAS (the first snapshot of a coarse grid's pre-smoothing, right after the restriction, when
+// u = u0 there): the block also completes the grid's FAS right-hand side, rhs += L(pn + u0)
+// (Algorithm 1), with the G it forms anyway, writes it and takes it into f, instead of a
+// separate residual launch before the snapshot.  The same operations as that launch, so the
+// same values.
+template <int WARPS, int MINB, bool MIXED, bool NORM = false, bool FAS = false>
 __global__ void __launch_bounds__(32 * WARPS, MINB)
     k_snapshot_tma(LevelView<float> L, const double *area, const __grid_constant__ CUtensorMap mP,
                    const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mW,
@@ -148,7 +153,19 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
             ds = fma_rn(aW, sub_rn(S.P[a][c - 1], pc), ds);
             const size_t o = (size_t)gi * p + gj, lim = (size_t)n * p;
             T base = add_rn(S.F[ti][lane], ar);
-            if (L.has_rhs) base = add_rn(base, S.R[ti][lane]);
+            if (FAS) {   // as k_residual_tma, mode 1, with uin = u (= u0 here)
+                const T uc = S.U[a][c];
+                T fl = mul_rn(aS, add_rn(sub_rn(S.P[a + 1][c], pc), sub_rn(S.U[a + 1][c], uc)));
+                fl = fma_rn(aN, add_rn(sub_rn(S.P[a - 1][c], pc), sub_rn(S.U[a - 1][c], uc)), fl);
+                fl = fma_rn(aE, add_rn(sub_rn(S.P[a][c + 1], pc), sub_rn(S.U[a][c + 1], uc)), fl);
+                fl = fma_rn(aW, add_rn(sub_rn(S.P[a][c - 1], pc), sub_rn(S.U[a][c - 1], uc)), fl);
+                const T Lv = sub_rn(fma_rn(c2, fl, -add_rn(S.F[ti][lane], ar)), mul_rn(L.inv_tau, uc));
+                const T rn = add_rn(S.R[ti][lane], Lv);
+                stc(L.rhs, o, lim, kDbgSnapshot, rn);
+                base = add_rn(base, rn);
+            } else if (L.has_rhs) {
+                base = add_rn(base, S.R[ti][lane]);
+            }
             stc(L.f, o, lim, kDbgSnapshot, fma_rn(-c2, ds, base));
             stc(L.G, o, lim, kDbgSnapshot, gc);
             // jump set D (Sec. 4.1): max > Sigma * min over the faces inside the domain; the
@@ -221,18 +238,18 @@ struct SnapTmaOcc {
 };
 SnapTmaOcc g_snap_occ;
 
-template <int WARPS, int MINB, bool MIXED, bool NORM = false>
+template <int WARPS, int MINB, bool MIXED, bool NORM = false, bool FAS = false>
 int snap_attr() {
     const int smem = (int)snap_smem<WARPS, MINB, MIXED>();
-    cudaFuncSetAttribute(k_snapshot_tma<WARPS, MINB, MIXED, NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_snapshot_tma<WARPS, MINB, MIXED, NORM, FAS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot_tma<WARPS, MINB, MIXED, NORM>, 32 * WARPS, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot_tma<WARPS, MINB, MIXED, NORM, FAS>, 32 * WARPS, smem) !=
             cudaSuccess || v < 1)
         v = 1;
     return v;
 }
 
-template <int WARPS, int MINB, bool MIXED, bool NORM = false>
+template <int WARPS, int MINB, bool MIXED, bool NORM = false, bool FAS = false>
 void launch_v(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err, long long wl,
               cudaStream_t st, double *partials = nullptr) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, WARPS);
@@ -241,19 +258,19 @@ void launch_v(const LevelView<float> &L, const double *area, const SnapMaps &M, 
     const auto *mw = reinterpret_cast<const CUtensorMap *>(M.W);
     const auto *mf = reinterpret_cast<const CUtensorMap *>(M.F);
     const auto *mr = reinterpret_cast<const CUtensorMap *>(L.has_rhs ? M.R : M.F);
-    k_snapshot_tma<WARPS, MINB, MIXED, NORM><<<grid, block, snap_smem<WARPS, MINB, MIXED>(), st>>>(
+    k_snapshot_tma<WARPS, MINB, MIXED, NORM, FAS><<<grid, block, snap_smem<WARPS, MINB, MIXED>(), st>>>(
         L, area, *mp, *mu, *mw, *mf, *mr, err, wl, partials);
 }
 
-template <bool MIXED>
+template <bool MIXED, bool FAS = false>
 void launch_mixed(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err, long long wl,
                   cudaStream_t st) {
     const long tiles = (long)((L.m + 31) / 32) * ((L.n + 31) / 32);
     const int *ps = g_snap_occ.per_sm[MIXED ? 1 : 0];
     // the most threads per tile with which every tile still gets a resident block
-    if (tiles <= (long)g_snap_occ.sms * ps[0]) launch_v<32, 1, MIXED>(L, area, M, err, wl, st);
-    else if (tiles <= (long)g_snap_occ.sms * ps[1]) launch_v<16, 1, MIXED>(L, area, M, err, wl, st);
-    else launch_v<8, 7, MIXED>(L, area, M, err, wl, st);
+    if (tiles <= (long)g_snap_occ.sms * ps[0]) launch_v<32, 1, MIXED, false, FAS>(L, area, M, err, wl, st);
+    else if (tiles <= (long)g_snap_occ.sms * ps[1]) launch_v<16, 1, MIXED, false, FAS>(L, area, M, err, wl, st);
+    else launch_v<8, 7, MIXED, false, FAS>(L, area, M, err, wl, st);
 }
 
 }  // namespace
@@ -270,6 +287,12 @@ void prepare_snapshot_tma() {
     g_snap_occ.per_sm[1][2] = snap_attr<8, 7, true>();
     (void)snap_attr<8, 7, false, true>();
     (void)snap_attr<8, 7, true, true>();
+    (void)snap_attr<32, 1, false, false, true>();
+    (void)snap_attr<16, 1, false, false, true>();
+    (void)snap_attr<8, 7, false, false, true>();
+    (void)snap_attr<32, 1, true, false, true>();
+    (void)snap_attr<16, 1, true, false, true>();
+    (void)snap_attr<8, 7, true, false, true>();
 }
 
 bool encode_snapshot_maps(const LevelView<float> &L, SnapMaps *M) {
@@ -287,6 +310,12 @@ void launch_snapshot_tma(const LevelView<float> &L, const double *area, const Sn
                          long long wait_limit, cudaStream_t st) {
     if (M.mixed) launch_mixed<true>(L, area, M, err, wait_limit, st);
     else launch_mixed<false>(L, area, M, err, wait_limit, st);
+}
+
+void launch_snapshot_fas_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err,
+                             long long wait_limit, cudaStream_t st) {
+    if (M.mixed) launch_mixed<true, true>(L, area, M, err, wait_limit, st);
+    else launch_mixed<false, true>(L, area, M, err, wait_limit, st);
 }
 
 void launch_snapshot_norm_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, double *partials,
