@@ -261,6 +261,17 @@ __device__ __forceinline__ void load_tile32(T (*dA)[33], const T *sA, T (*dB)[33
     }
 }
 
+// One-dimensional bilinear taps (Sec. 3.1): fine 2I+1 takes coarse I; fine 2I+2 the mean of
+// coarse I and I+1; fine 0 (and fine n-1 for odd n) the single nearest coarse value.
+__device__ __forceinline__ int bl_taps(int p, int nc, int *idx, float *wt) {
+    if (p & 1) { idx[0] = (p - 1) / 2; wt[0] = 1.0f; return 1; }
+    if (p == 0) { idx[0] = 0; wt[0] = 1.0f; return 1; }
+    int I = p / 2 - 1;
+    if (I + 1 < nc) { idx[0] = I; idx[1] = I + 1; wt[0] = 0.5f; wt[1] = 0.5f; return 2; }
+    idx[0] = I; wt[0] = 1.0f;
+    return 1;
+}
+
 // One-dimensional full-weighting taps (Sec. 3.1): coarse I sits on fine 2I+1; (1/4, 1/2, 1/4)
 // on 2I, 2I+1, 2I+2, or (1/2, 1/2) on 2I, 2I+1 when fine 2I+2 does not exist.
 __device__ __forceinline__ int fw_taps(int I, int n, int *idx, float *wt) {

@@ -241,17 +241,6 @@ __global__ void __launch_bounds__(256) k_restrict(RestrictFields<T> F, int n, in
     if (c2) stc(c2, (size_t)I * pc + J, (size_t)nc * pc, kDbgResidual, s);
 }
 
-// One-dimensional bilinear taps (Sec. 3.1): fine 2I+1 takes coarse I; fine 2I+2 the mean of
-// coarse I and I+1; fine 0 (and fine n-1 for odd n) the single nearest coarse value.
-__device__ __forceinline__ int bl_taps(int p, int nc, int *idx, float *wt) {
-    if (p & 1) { idx[0] = (p - 1) / 2; wt[0] = 1.0f; return 1; }
-    if (p == 0) { idx[0] = 0; wt[0] = 1.0f; return 1; }
-    int I = p / 2 - 1;
-    if (I + 1 < nc) { idx[0] = I; idx[1] = I + 1; wt[0] = 0.5f; wt[1] = 0.5f; return 2; }
-    idx[0] = I; wt[0] = 1.0f;
-    return 1;
-}
-
 // Interpolation and correction: u_f += P (u_c - u0_c)  (Algorithm 1, "Interpolation").
 template <typename T>
 __global__ void __launch_bounds__(256) k_interp_add(LevelView<T> Lf, LevelView<T> Lc) {

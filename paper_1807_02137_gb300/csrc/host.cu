@@ -222,6 +222,7 @@ struct Solver final : SolverBase {
     int lb = -1;                  // first grid of the one-block bottom kernel (-1: not used)
     int lb_first = -1;            // the largest grid it can start at (-1: it does not apply)
     int fas_level = -1;           // the grid whose next snapshot completes its FAS right-hand side
+    int interp_level = -1;        // the grid whose next snapshot first applies the coarse correction
     int lc = -1;                  // first grid of the cluster bottom kernel (-1: not used); it runs
                                   // grids lc .. nlev-1 (lb is then unused)
     int lc_tiles = 0;
@@ -724,6 +725,10 @@ struct Solver final : SolverBase {
                 if constexpr (std::is_same<T, float>::value)
                     launch_snapshot_fas_tma(v, area_ptr(), lv[l].smaps, &dsc->err, wait_limit, st);
                 fas_level = -1;
+            } else if (l == interp_level) {   // the first snapshot after the coarse grid applies its correction
+                if constexpr (std::is_same<T, float>::value)
+                    launch_snapshot_interp_tma(v, view(l + 1), area_ptr(), lv[l].smaps, &dsc->err, wait_limit, st);
+                interp_level = -1;
             } else {
                 snapshot(l, v);
             }
@@ -788,8 +793,15 @@ struct Solver final : SolverBase {
             launches += area_launches(l) + area_launches(l + 1) + 1;
         }
         cycle(l + 1);
-        launch_interp_add<T>(view(l), view(l + 1), st);
-        ++launches;
+        // the coarse-grid correction: in the first post-smoothing snapshot (FP32 storage, the
+        // Spencer-Chen model: the Rada-Chen area term before a snapshot reads the corrected u),
+        // else its own launch
+        if (std::is_same<T, float>::value && p.nu2 >= 1 && p.model == MG_MODEL_SC) {
+            interp_level = l;
+        } else {
+            launch_interp_add<T>(view(l), view(l + 1), st);
+            ++launches;
+        }
         for (int t = 0; t < p.nu2; ++t) smooth(l);
     }
 

@@ -195,6 +195,11 @@ void launch_snapshot_tma(const LevelView<float> &L, const double *area, const Sn
 // residual launch then does not run).
 void launch_snapshot_fas_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err,
                              long long wait_limit, cudaStream_t st);
+// The first snapshot of grid L's post-smoothing: first applies the coarse-grid correction
+// u += P (u_c - u0_c) from grid C (Algorithm 1's interpolation) and writes u (the separate
+// interpolation launch then does not run).
+void launch_snapshot_interp_tma(const LevelView<float> &L, const LevelView<float> &C, const double *area,
+                                const SnapMaps &M, int *err, long long wait_limit, cudaStream_t st);
 void launch_snapshot_norm_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, double *partials,
                               int *err, long long wait_limit, cudaStream_t st);
 // Tensor maps of the TMA-staged residual kernels of one FP32 grid (residual_tma.cu): pn, u and w

@@ -29,6 +29,9 @@ namespace segmg {
 namespace {
 
 constexpr int kBR = 36, kBC = 40, kBCb = 48;   // box rows; FP32 and BF16 box columns
+// coarse rows and columns the box rows 0..35 and columns 2..37 interpolate from (fine i0-2 ..
+// i0+33 take coarse i0/2-2 .. i0/2+16)
+constexpr int kCR = 20;
 constexpr long long kSnapDrain = 1LL << 22;
 
 template <int WARPS, bool MIXED>
@@ -41,6 +44,7 @@ struct SnapTmaSmem {
     alignas(128) float R[32][32];
     uint32_t cm[2][WARPS][32];   // column member bits of sweeps C, D per warp
     double red[33];              // NORM: the block's sum of squares
+    float E[kCR][kCR + 1];       // interpolating snapshot: u_c - u0_c on the coarse cells used
     unsigned long long bar;
 };
 
@@ -49,17 +53,21 @@ struct SnapTmaSmem {
 // NORM (8 warps): the block also writes sum r^2 of its tile, r = rhs - L(pn + u) at the state
 // the snapshot reads, to partials[block]: the operations and the order of k_residual_tma's norm
 // (the same G box, faces, flux and per-thread order), so the partials are bitwise its partials.
-// FAS (the first snapshot of a coarse grid's pre-smoothing, right after the restriction, when
-// u = u0 there): the block also completes the grid's FAS right-hand side, rhs += L(pn + u0)
-// (Algorithm 1), with the G it forms anyway, writes it and takes it into f, instead of a
-// separate residual launch before the snapshot.  The same operations as that launch, so the
-// same values.
-template <int WARPS, int MINB, bool MIXED, bool NORM = false, bool FAS = false>
+// XT = 1, FAS (the first snapshot of a coarse grid's pre-smoothing, right after the
+// restriction, when u = u0 there): the block also completes the grid's FAS right-hand side,
+// rhs += L(pn + u0) (Algorithm 1), with the G it forms anyway, writes it and takes it into f,
+// instead of a separate residual launch before the snapshot.  XT = 2, interpolation (the first
+// snapshot of a grid's post-smoothing): the block first applies the coarse-grid correction
+// u += P (u_c - u0_c) (Algorithm 1) to the box cells it reads and writes its tile's corrected u,
+// instead of a separate interpolation launch.  Both take the separate launches' operations, so
+// the values are the same.
+template <int WARPS, int MINB, bool MIXED, bool NORM = false, int XT = 0>
 __global__ void __launch_bounds__(32 * WARPS, MINB)
     k_snapshot_tma(LevelView<float> L, const double *area, const __grid_constant__ CUtensorMap mP,
                    const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mW,
                    const __grid_constant__ CUtensorMap mF, const __grid_constant__ CUtensorMap mR, int *err,
-                   long long wait_limit, double *partials) {
+                   long long wait_limit, double *partials, LevelView<float> Cg) {
+    constexpr bool FAS = XT == 1, INTERP = XT == 2;
     static_assert(!NORM || WARPS == 8, "the norm's thread-to-cell map is that of 8 warps per tile");
     using T = float;
     using Smem = SnapTmaSmem<WARPS, MIXED>;
@@ -82,6 +90,21 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         tma_load(&S.F[0][0], &mF, j0, i0, &S.bar);
         if (L.has_rhs) tma_load(&S.R[0][0], &mR, j0, i0, &S.bar);
     }
+    int I0 = 0, J0 = 0;   // INTERP: the first coarse row and column of E
+    if (INTERP) {   // u_c - u0_c while the boxes are in flight
+        I0 = max(0, i0 / 2 - 2);
+        J0 = max(0, j0 / 2 - 2);
+        const size_t lc = (size_t)Cg.n * Cg.pitch;
+        for (int q = tid; q < kCR * kCR; q += NT) {
+            const int r = q / kCR, cc = q - r * kCR, I = I0 + r, J = J0 + cc;
+            float e = 0.f;
+            if (I < Cg.n && J < Cg.m) {
+                const size_t o = (size_t)I * Cg.pitch + J;
+                e = sub_rn(ldc(Cg.u, o, lc, kDbgInterp), ldc(Cg.u0, o, lc, kDbgInterp));
+            }
+            S.E[r][cc] = e;
+        }
+    }
     __syncthreads();   // the barrier's initialisation is visible before anyone waits on it
     bool ok = true;
     if (wy == 0) ok = mbar_wait(&S.bar, 0, wait_limit);   // the other warps wait at the block barrier
@@ -92,6 +115,32 @@ __global__ void __launch_bounds__(32 * WARPS, MINB)
         }
         __syncthreads();
         return;
+    }
+    if (INTERP) {
+        // u += P (u_c - u0_c) on the in-grid box cells of rows 0..35 and columns 2..37 (every u
+        // the G box, the class and the residuals read), as k_interp_add: then the tile's cells
+        // to u
+        for (int q = tid; q < kBR * (kBC - 4); q += NT) {
+            const int a = q / (kBC - 4), c = 2 + (q - a * (kBC - 4)), gi = i0 - 2 + a, gj = j0 - 4 + c;
+            if (gi < 0 || gi >= n || gj < 0 || gj >= m) continue;
+            int ri[2], ci[2];
+            float rw[2], cw[2];
+            const int nr = bl_taps(gi, Cg.n, ri, rw), nk = bl_taps(gj, Cg.m, ci, cw);
+            T sacc = T(0);
+            for (int x = 0; x < nr; ++x)
+                for (int y = 0; y < nk; ++y) {
+                    const int er = ri[x] - I0, ec = ci[y] - J0;
+                    if (!MG_DBG_OK(er, kCR, kDbgInterp) || !MG_DBG_OK(ec, kCR, kDbgInterp)) continue;
+                    sacc = fma_rn(T(rw[x] * cw[y]), S.E[er][ec], sacc);
+                }
+            S.U[a][c] = add_rn(S.U[a][c], sacc);
+        }
+        __syncthreads();
+        const size_t lim = (size_t)n * p;
+        for (int q = tid; q < 1024; q += NT) {
+            const int ti = q >> 5, tj = q & 31, gi = i0 + ti, gj = j0 + tj;
+            if (gi < n && gj < m) stc(L.u, (size_t)gi * p + gj, lim, kDbgInterp, S.U[ti + 2][tj + 4]);
+        }
     }
     // edge tiles: box cells of pn and u outside the grid take the clamped cell's values (the
     // source is an in-grid cell of the box, never itself overwritten); w is read only at cells
@@ -238,39 +287,39 @@ struct SnapTmaOcc {
 };
 SnapTmaOcc g_snap_occ;
 
-template <int WARPS, int MINB, bool MIXED, bool NORM = false, bool FAS = false>
+template <int WARPS, int MINB, bool MIXED, bool NORM = false, int XT = 0>
 int snap_attr() {
     const int smem = (int)snap_smem<WARPS, MINB, MIXED>();
-    cudaFuncSetAttribute(k_snapshot_tma<WARPS, MINB, MIXED, NORM, FAS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_snapshot_tma<WARPS, MINB, MIXED, NORM, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot_tma<WARPS, MINB, MIXED, NORM, FAS>, 32 * WARPS, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_snapshot_tma<WARPS, MINB, MIXED, NORM, XT>, 32 * WARPS, smem) !=
             cudaSuccess || v < 1)
         v = 1;
     return v;
 }
 
-template <int WARPS, int MINB, bool MIXED, bool NORM = false, bool FAS = false>
+template <int WARPS, int MINB, bool MIXED, bool NORM = false, int XT = 0>
 void launch_v(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err, long long wl,
-              cudaStream_t st, double *partials = nullptr) {
+              cudaStream_t st, double *partials = nullptr, const LevelView<float> *C = nullptr) {
     dim3 grid((L.m + 31) / 32, (L.n + 31) / 32), block(32, WARPS);
     const auto *mp = reinterpret_cast<const CUtensorMap *>(M.P);
     const auto *mu = reinterpret_cast<const CUtensorMap *>(M.U);
     const auto *mw = reinterpret_cast<const CUtensorMap *>(M.W);
     const auto *mf = reinterpret_cast<const CUtensorMap *>(M.F);
     const auto *mr = reinterpret_cast<const CUtensorMap *>(L.has_rhs ? M.R : M.F);
-    k_snapshot_tma<WARPS, MINB, MIXED, NORM, FAS><<<grid, block, snap_smem<WARPS, MINB, MIXED>(), st>>>(
-        L, area, *mp, *mu, *mw, *mf, *mr, err, wl, partials);
+    k_snapshot_tma<WARPS, MINB, MIXED, NORM, XT><<<grid, block, snap_smem<WARPS, MINB, MIXED>(), st>>>(
+        L, area, *mp, *mu, *mw, *mf, *mr, err, wl, partials, C ? *C : L);
 }
 
-template <bool MIXED, bool FAS = false>
+template <bool MIXED, int XT = 0>
 void launch_mixed(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err, long long wl,
-                  cudaStream_t st) {
+                  cudaStream_t st, const LevelView<float> *C = nullptr) {
     const long tiles = (long)((L.m + 31) / 32) * ((L.n + 31) / 32);
     const int *ps = g_snap_occ.per_sm[MIXED ? 1 : 0];
     // the most threads per tile with which every tile still gets a resident block
-    if (tiles <= (long)g_snap_occ.sms * ps[0]) launch_v<32, 1, MIXED, false, FAS>(L, area, M, err, wl, st);
-    else if (tiles <= (long)g_snap_occ.sms * ps[1]) launch_v<16, 1, MIXED, false, FAS>(L, area, M, err, wl, st);
-    else launch_v<8, 7, MIXED, false, FAS>(L, area, M, err, wl, st);
+    if (tiles <= (long)g_snap_occ.sms * ps[0]) launch_v<32, 1, MIXED, false, XT>(L, area, M, err, wl, st, nullptr, C);
+    else if (tiles <= (long)g_snap_occ.sms * ps[1]) launch_v<16, 1, MIXED, false, XT>(L, area, M, err, wl, st, nullptr, C);
+    else launch_v<8, 7, MIXED, false, XT>(L, area, M, err, wl, st, nullptr, C);
 }
 
 }  // namespace
@@ -287,12 +336,18 @@ void prepare_snapshot_tma() {
     g_snap_occ.per_sm[1][2] = snap_attr<8, 7, true>();
     (void)snap_attr<8, 7, false, true>();
     (void)snap_attr<8, 7, true, true>();
-    (void)snap_attr<32, 1, false, false, true>();
-    (void)snap_attr<16, 1, false, false, true>();
-    (void)snap_attr<8, 7, false, false, true>();
-    (void)snap_attr<32, 1, true, false, true>();
-    (void)snap_attr<16, 1, true, false, true>();
-    (void)snap_attr<8, 7, true, false, true>();
+    (void)snap_attr<32, 1, false, false, 1>();
+    (void)snap_attr<16, 1, false, false, 1>();
+    (void)snap_attr<8, 7, false, false, 1>();
+    (void)snap_attr<32, 1, true, false, 1>();
+    (void)snap_attr<16, 1, true, false, 1>();
+    (void)snap_attr<8, 7, true, false, 1>();
+    (void)snap_attr<32, 1, false, false, 2>();
+    (void)snap_attr<16, 1, false, false, 2>();
+    (void)snap_attr<8, 7, false, false, 2>();
+    (void)snap_attr<32, 1, true, false, 2>();
+    (void)snap_attr<16, 1, true, false, 2>();
+    (void)snap_attr<8, 7, true, false, 2>();
 }
 
 bool encode_snapshot_maps(const LevelView<float> &L, SnapMaps *M) {
@@ -314,8 +369,14 @@ void launch_snapshot_tma(const LevelView<float> &L, const double *area, const Sn
 
 void launch_snapshot_fas_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, int *err,
                              long long wait_limit, cudaStream_t st) {
-    if (M.mixed) launch_mixed<true, true>(L, area, M, err, wait_limit, st);
-    else launch_mixed<false, true>(L, area, M, err, wait_limit, st);
+    if (M.mixed) launch_mixed<true, 1>(L, area, M, err, wait_limit, st);
+    else launch_mixed<false, 1>(L, area, M, err, wait_limit, st);
+}
+
+void launch_snapshot_interp_tma(const LevelView<float> &L, const LevelView<float> &C, const double *area,
+                                const SnapMaps &M, int *err, long long wait_limit, cudaStream_t st) {
+    if (M.mixed) launch_mixed<true, 2>(L, area, M, err, wait_limit, st, &C);
+    else launch_mixed<false, 2>(L, area, M, err, wait_limit, st, &C);
 }
 
 void launch_snapshot_norm_tma(const LevelView<float> &L, const double *area, const SnapMaps &M, double *partials,
