@@ -747,6 +747,7 @@ struct Solver final : SolverBase {
                                                       "grid 6", "grid 7", "grid 8", "grid 9", "grid 10", "grid 11",
                                                       "grid 12", "grid 13", "grid 14", "grid 15"};
         Range range(kLevelNames[l]);
+        if (l == 0) fas_level = interp_level = -1;   // nothing pending from an enqueue cut short
         if (l == lc) {
             launch_bottom_cycle(true);
             ++launches;
