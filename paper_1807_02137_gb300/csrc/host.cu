@@ -143,6 +143,7 @@ struct SolverBase {
     virtual int vcycle(double *rho) = 0;
     virtual int end_step(double *eta) = 0;
     virtual int mask(unsigned char *out) = 0;
+    virtual int mask_async(unsigned char *out) = 0;   // enqueued only (the caller synchronises)
     virtual int get_phi(void *out) = 0;
     virtual int set_phi(const void *in) = 0;
     virtual int set_regions(double c1, double c2) = 0;
@@ -1386,10 +1387,15 @@ struct Solver final : SolverBase {
     }
 
     int mask(unsigned char *out) override {
+        if (int rc = mask_async(out)) return rc;
+        CK(cudaStreamSynchronize(st));
+        return MG_OK;
+    }
+
+    int mask_async(unsigned char *out) override {
         launch_mask<T>(view(0), out, st);
         ++launches;
         CKL();
-        CK(cudaStreamSynchronize(st));
         return MG_OK;
     }
 
@@ -2132,7 +2138,7 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
         }
     }
     if (!rc) rc = mg_solve(c.h, tol, max_cycles, eta_stop, max_steps, nullptr);
-    if (!rc) rc = mg_mask(c.h, c.dmask);
+    if (!rc) rc = c.h->s->mask_async(c.dmask);   // on the handle's stream: ordered before the copies below
     if (!rc && phi_host) rc = mg_get_phi(c.h, c.dphi);
     if (!rc && stats) rc = mg_get_stats(c.h, stats);
     if (!rc) {
