@@ -780,3 +780,19 @@ def test_time_residuals_reports_the_v_cycle_residual_kernels(segmg):
     # the timing runs leave the step's state usable: a fresh step still converges
     cyc, rho = s.solve_step(1e-6, 60)
     assert rho <= 1e-6
+
+
+def test_rada_chen_fp32_step_matches_oracle(segmg):
+    # the Rada-Chen model in FP32 storage: the area term on every grid, the FAS right-hand side
+    # completed by the coarse grids' first snapshots (the interpolation keeps its own launch for
+    # this model); one whole step against the FP64 oracle's converged solution of the same step
+    img, mk, _ = synth.ellipses(200, 170, 8, (15, 70), 6, 0.05, 31)
+    s, o, p = both(segmg, img.astype(np.float32), mk, precision=segmg.MG_F32, levels=5,
+                   model=segmg.MG_MODEL_RC)
+    cyc, rho = s.solve_step(1e-6, 60)
+    o.set_tau(s.stats()["tau"])
+    hist = o.solve_step(1e-9, 80)
+    assert rho <= 1e-6 and hist[-1] <= 1e-9
+    pg, po = s.phi().cpu().numpy(), o.phi
+    assert relmax(pg, po) < 1e-5
+    assert np.mean((pg > 0) != (po > 0)) <= 1e-4
