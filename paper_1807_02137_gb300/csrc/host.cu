@@ -149,6 +149,11 @@ struct SolverBase {
     virtual int set_regions(double c1, double c2) = 0;
     virtual int get_level(int l, int field, void *out) = 0;
     virtual int stats(mg_stats *s) = 0;
+    // host-side values that need no device read (stats() copies the device scalars and waits)
+    virtual int rows() const = 0;
+    virtual int cols() const = 0;
+    virtual int steps_done() const = 0;
+    virtual double last_eta() const = 0;
     virtual cudaStream_t stream() const = 0;
     virtual int time_kernels(int level, int reps, double *ms) = 0;
     virtual int time_residuals(int level, int reps, double *ms) = 0;
@@ -1441,6 +1446,11 @@ struct Solver final : SolverBase {
         return MG_OK;
     }
 
+    int rows() const override { return n; }
+    int cols() const override { return m; }
+    int steps_done() const override { return steps; }
+    double last_eta() const override { return eta; }
+
     int stats(mg_stats *s) override {
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1594,8 +1604,7 @@ int solve_step_controlled(SolverBase *s, double tol, int max_cycles, int *cycles
     int total = 0, rc = MG_OK;
     double r = 1.0;
     bool ok = false;
-    mg_stats st0;
-    s->stats(&st0);
+    const int step0 = s->steps_done();
     for (int attempt = 0;; ++attempt) {
         if ((rc = s->begin_step(nullptr))) return rc;
         std::vector<double> hist;
@@ -1607,7 +1616,7 @@ int solve_step_controlled(SolverBase *s, double tol, int max_cycles, int *cycles
         if (rc != MG_ERR_STATE || !hist.empty()) {
             const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             for (size_t k = 0; k < hist.size(); ++k)
-                log_cycle(st0.steps, attempt, (int)k + 1, hist[k], s->params().tau, ms / (double)hist.size());
+                log_cycle(step0, attempt, (int)k + 1, hist[k], s->params().tau, ms / (double)hist.size());
             total += (int)hist.size();
             if (!hist.empty()) r = hist.back();
             if (rc == MG_ERR_DIVERGED || rc == MG_ERR_NAN) {
@@ -1623,7 +1632,7 @@ int solve_step_controlled(SolverBase *s, double tol, int max_cycles, int *cycles
                 const auto t1 = std::chrono::steady_clock::now();
                 rc = s->vcycle(&r);
                 ++total;
-                log_cycle(st0.steps, attempt, j, r, s->params().tau,
+                log_cycle(step0, attempt, j, r, s->params().tau,
                           std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count());
                 if (rc == MG_ERR_DIVERGED || rc == MG_ERR_NAN) {
                     if (!control) return rc;
@@ -1983,9 +1992,7 @@ int mg_setup(mg_handle *out, const void *image, int n, int m, const double *mark
 
 int mg_reset(mg_handle h, const void *image, const double *markers_xy, int k) {
     if (!h || !image) return fail(MG_ERR_ARG, "NULL argument");
-    mg_stats s;
-    h->s->stats(&s);
-    int rc = check_markers(markers_xy, k, s.n, s.m);
+    int rc = check_markers(markers_xy, k, h->s->rows(), h->s->cols());
     if (rc) return rc;
     return h->s->reset(image, markers_xy, k);
 }
@@ -2006,9 +2013,7 @@ int mg_solve(mg_handle h, double tol, int max_cycles, double eta_stop, int max_s
         int rc = mg_solve_step(h, tol, max_cycles, nullptr, nullptr);
         ++taken;
         if (rc && rc != MG_ERR_TIMEOUT) { if (steps) *steps = taken; return rc; }
-        mg_stats s;
-        h->s->stats(&s);
-        if (s.eta < eta_stop) break;
+        if (h->s->last_eta() < eta_stop) break;
     }
     if (steps) *steps = taken;
     return MG_OK;
