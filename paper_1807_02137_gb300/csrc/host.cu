@@ -2145,7 +2145,6 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
     if (!rc) rc = mg_solve(c.h, tol, max_cycles, eta_stop, max_steps, nullptr);
     if (!rc) rc = c.h->s->mask_async(c.dmask);   // on the handle's stream: ordered before the copies below
     if (!rc && phi_host) rc = mg_get_phi(c.h, c.dphi);
-    if (!rc && stats) rc = mg_get_stats(c.h, stats);
     if (!rc) {
         e = cudaMemcpyAsync(mask_host, c.dmask, N, cudaMemcpyDeviceToHost, c.st);
         if (e == cudaSuccess && phi_host)
@@ -2153,6 +2152,7 @@ int mg_segment_host(const float *image_host, int n, int m, const double *markers
         if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
         if (e != cudaSuccess) rc = fail(MG_ERR_CUDA, cudaGetErrorString(e));
     }
+    if (!rc && stats) rc = mg_get_stats(c.h, stats);   // after the copies: the stream is idle by now
     if (rc) {   // a failed call keeps nothing
         std::string keep = g_err;
         c.release();
