@@ -444,9 +444,9 @@ int mg_time_residuals(mg_handle h, int level, int reps, double *ms);
  * Its scratch is one file-scope device array sized for 65,536 tiles of 32 x 32 cells (for example
  * 8192 x 8192); larger grids, and grids of more than 65,535 tile rows, get MG_ERR_ARG before any
  * device access.  The array's device address is looked up on the first call made on each device
- * (with that device current) and kept for the life of the process, so make that first call before
- * any stream capture; after cudaDeviceReset on a device the kept address is no longer valid, and
- * this entry point must not be called on that device again.  Every call shares the array: calls
+ * (with that device current) and kept for the life of the process; after cudaDeviceReset on a
+ * device the kept address is no longer valid, and this entry point must not be called on that
+ * device again.  Every call shares the array: calls
  * that overlap on the GPU race on it.  The call waits for its stream.  Errors: MG_ERR_ARG,
  * MG_ERR_CUDA (mg_last_error is not updated). */
 int mg_residual_norm_noalloc(const void *phi, const void *w, const void *F, int n, int m,
