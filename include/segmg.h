@@ -175,7 +175,8 @@ int mg_begin_step(mg_handle h, double *res0);
 int mg_vcycle(mg_handle h, double *rho);
 
 /* Ends the step: new c1, c2 from the current phi (Sec. 5) and
- * eta = ||phi - phi^n|| / ||phi^n|| (to *eta if not NULL; waits). */
+ * eta = ||phi - phi^n|| / ||phi^n|| (to *eta if not NULL, and the call waits for the stream;
+ * with eta NULL the call only enqueues, and mg_stats reads eta later). */
 int mg_end_step(mg_handle h, double *eta);
 
 /* mg_begin_step, then V-cycles until rho <= tol or max_cycles, then mg_end_step.

@@ -140,6 +140,9 @@ struct SolverBase {
     virtual ~SolverBase() {}
     virtual int reset(const void *image, const double *mk, int k) = 0;
     virtual int begin_step(double *res0) = 0;
+    // begin_step without its host round trip; finish_begin (after the attempt) reads the norm
+    virtual int begin_step_deferred() = 0;
+    virtual int finish_begin() = 0;
     virtual int vcycle(double *rho) = 0;
     virtual int end_step(double *eta) = 0;
     virtual int mask(unsigned char *out) = 0;
@@ -211,9 +214,15 @@ struct Solver final : SolverBase {
     double *coarse = nullptr;
     double *dmk = nullptr;    // markers (2 * kcap)
     double *dhull = nullptr;  // hull (2 * kcap + 4)
-    double *hstage = nullptr; // pinned host staging of markers, hull and A1 / (n m) (6 kcap + 9)
+    double *hstage = nullptr; // pinned host staging of markers, hull, A1 / (n m) and the eta sums (6 kcap + 11)
     int kcap = 0;
-    double A1 = 0, res0 = 0, rho = 0, eta = 0;
+    double A1 = 0, res0 = 0, rho = 0;
+    bool res0_pending = false;   // a step begun without waiting: res0 not read yet
+    bool res0_in_hsc = false;    // ... and the host mirror holds it (an attempt's graph copied it)
+    // eta of the last step: end_step enqueues the copy of its two sums to the staging buffer and
+    // the first reader waits for the stream (a step needs no host round trip for it)
+    mutable double eta = 0;
+    mutable bool eta_pending = false;
     int steps = 0, cycles_step = 0, cycles_total = 0;
     int rejected = 0;             // step attempts rejected by the step control
     double tau0 = 1.0;            // tau of the parameters (the step control halves p.tau)
@@ -371,7 +380,7 @@ struct Solver final : SolverBase {
         dmk = (double *)(base + o_mk);
         dhull = (double *)(base + o_hull);
         CK(cudaMallocHost(&hsc, sizeof(Scalars)));
-        CK(cudaMallocHost(&hstage, sizeof(double) * (6 * (size_t)kcap + 9)));
+        CK(cudaMallocHost(&hstage, sizeof(double) * (6 * (size_t)kcap + 11)));
         if constexpr (std::is_same<T, float>::value) {
             if (p.smoother == MG_SMOOTH_FUSED)
                 for (int l = 0; l < nlev; ++l)
@@ -556,6 +565,7 @@ struct Solver final : SolverBase {
         rejected = 0;
         steps = cycles_step = cycles_total = 0;
         rho = eta = res0 = 0;
+        eta_pending = res0_pending = res0_in_hsc = false;
         Level<T> &L0 = lv[0];
         CK(cudaMemsetAsync(dsc, 0, sizeof(Scalars), st));
         // the image's finiteness is checked while it is copied in and read back at the end of
@@ -630,7 +640,29 @@ struct Solver final : SolverBase {
 
     const double *area_ptr() const { return p.model == MG_MODEL_RC ? dsc->area : nullptr; }
 
-    int begin_step(double *r0out) override {
+    int begin_step(double *r0out) override { return begin_step_impl(r0out, true); }
+    int begin_step_deferred() override { return begin_step_impl(nullptr, false); }
+
+    // The reference norm of a step begun by begin_step_deferred: read from the scalars that the
+    // attempt's graph launch copied back, else copied and waited for here.
+    int finish_begin() override {
+        if (!res0_pending) return MG_OK;
+        if (!res0_in_hsc) {
+            CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        res0 = std::sqrt(hsc->norm2_0);
+        res0_pending = res0_in_hsc = false;
+        if (!std::isfinite(res0)) {
+            in_step = false;
+            return fail(MG_ERR_NAN, "non-finite initial residual");
+        }
+        return MG_OK;
+    }
+
+    // wait = false: everything is enqueued and the reference norm is read later (finish_begin),
+    // so a step's first host round trip is the one after its V-cycles
+    int begin_step_impl(double *r0out, bool wait) {
         Range range("begin step");
         launch_fold<T>(view(0), st);
         for (int l = 1; l < nlev; ++l) {
@@ -644,9 +676,11 @@ struct Solver final : SolverBase {
         norm_residual(&dsc->norm2_0);
         launches += 1 + (nlev - 1) + 1 + area_launches() + norm_launches();   // fold, restrictions, fitting, norm
         CKL();
-        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        res0 = std::sqrt(hsc->norm2_0);
+        if (wait) {
+            CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            res0 = std::sqrt(hsc->norm2_0);
+        }
         rho = 1.0;
         plain_rate = -1.0;
         learn_since = 0;
@@ -655,9 +689,11 @@ struct Solver final : SolverBase {
         // the last residual norm starts at the reference one (rho = 1 until a V-cycle runs)
         CK(cudaMemcpyAsync(&dsc->norm2, &dsc->norm2_0, sizeof(double), cudaMemcpyDeviceToDevice, st));
         CK(cudaMemsetAsync(&dsc->halt, 0, sizeof(int), st));
-        if (!std::isfinite(res0)) return fail(MG_ERR_NAN, "non-finite initial residual");
+        if (wait && !std::isfinite(res0)) return fail(MG_ERR_NAN, "non-finite initial residual");
         in_step = true;
         cycles_step = 0;
+        res0_pending = !wait;
+        res0_in_hsc = false;
         if (r0out) *r0out = res0;
         return MG_OK;
     }
@@ -1321,6 +1357,7 @@ struct Solver final : SolverBase {
         }
         CK(cudaGraphLaunch(gloop, st));
         CK(cudaStreamSynchronize(st));
+        res0_in_hsc = res0_pending;   // the graph copied the scalars back, the reference norm with them
         const int j = hsc->loop_j;
         stop = hsc->loop_stop;
         hist.assign(hsc->loop_rho + 1, hsc->loop_rho + 1 + j);
@@ -1382,14 +1419,19 @@ struct Solver final : SolverBase {
         launch_region_sums<T>(view(0), p.eps, partials, npart, dsc, 1, st);
         launches += norm_launches();   // region partials and their (chunked) sums
         CKL();
-        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        eta = hsc->sums[5] > 0 ? std::sqrt(hsc->sums[4] / hsc->sums[5]) : std::sqrt(hsc->sums[4]);
+        CK(cudaMemcpyAsync(eta_sums(), &dsc->sums[4], 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        eta_pending = true;
         ++steps;
         in_step = false;
-        if (etaout) *etaout = eta;
+        if (etaout) {
+            CK(cudaStreamSynchronize(st));
+            *etaout = last_eta();
+        }
         return MG_OK;
     }
+
+    // the two sums of eta (sum of u^2, sum of phi_n^2) in the pinned staging buffer
+    double *eta_sums() const { return hstage + 6 * (size_t)kcap + 9; }
 
     int mask(unsigned char *out) override {
         if (int rc = mask_async(out)) return rc;
@@ -1449,7 +1491,15 @@ struct Solver final : SolverBase {
     int rows() const override { return n; }
     int cols() const override { return m; }
     int steps_done() const override { return steps; }
-    double last_eta() const override { return eta; }
+    double last_eta() const override {
+        if (eta_pending) {
+            cudaStreamSynchronize(st);   // the copy of end_step's sums; an error here reaches the next call
+            const double *e = eta_sums();
+            eta = e[1] > 0 ? std::sqrt(e[0] / e[1]) : std::sqrt(e[0]);
+            eta_pending = false;
+        }
+        return eta;
+    }
 
     int stats(mg_stats *s) override {
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -1457,7 +1507,7 @@ struct Solver final : SolverBase {
         s->n = n; s->m = m; s->levels = nlev; s->precision = p.precision;
         s->steps = steps; s->cycles_step = cycles_step; s->cycles_total = cycles_total;
         s->picard_last = hsc->picard;
-        s->rho = rho; s->res0 = res0; s->eta = eta;
+        s->rho = rho; s->res0 = res0; s->eta = last_eta();
         s->c1 = hsc->c1; s->c2 = hsc->c2; s->A1 = A1;
         s->device_bytes = pool_bytes;
         s->launches = launches;
@@ -1606,13 +1656,14 @@ int solve_step_controlled(SolverBase *s, double tol, int max_cycles, int *cycles
     bool ok = false;
     const int step0 = s->steps_done();
     for (int attempt = 0;; ++attempt) {
-        if ((rc = s->begin_step(nullptr))) return rc;
+        if ((rc = s->begin_step_deferred())) return rc;
         std::vector<double> hist;
         bool bad = false;   // diverged or non-finite: the state is not kept
         // the attempt's V-cycles in one graph launch, the step control's tests on the device ...
         int stop = 0;
         const auto t0 = std::chrono::steady_clock::now();
         rc = s->loop_attempt(tol, max_cycles, hist, stop);
+        if (int rb = s->finish_begin()) return rb;   // a non-finite reference norm ends the step
         if (rc != MG_ERR_STATE || !hist.empty()) {
             const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             for (size_t k = 0; k < hist.size(); ++k)
