@@ -614,7 +614,10 @@ def test_successive_steps_each_reach_the_tolerance_and_match_the_oracle(segmg):
         pg, po = s.phi().cpu().numpy(), o.phi
         assert relmax(pg, po) < 1e-5, step
         assert np.mean((pg > 0) != (po > 0)) <= 1e-4, step
-        o.end_step()
+        # eta of the step, read by stats() after the step end only enqueued its sums: this
+        # step's, not the previous one's (phi agrees to 1e-5 of max |phi|, so eta to ~1e-5)
+        eo = o.end_step()
+        assert abs(st["eta"] - eo) <= 1e-4 * max(1.0, eo), (step, st["eta"], eo)
         so = o.scalars()
         assert abs(st["c1"] - so["c1"]) <= 1e-5 and abs(st["c2"] - so["c2"]) <= 1e-5
     assert all(b <= a for a, b in zip(taus, taus[1:]))
