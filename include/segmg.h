@@ -431,6 +431,15 @@ int mg_time_kernels(mg_handle h, int level, int reps, double *ms);
  * does.  MG_ERR_STATE outside a step, MG_ERR_ARG for a bad level or reps < 1.  Waits. */
 int mg_time_residuals(mg_handle h, int level, int reps, double *ms);
 
+/* Times the Hybrid Smoother 2 sweeps of grid `level` as a V-cycle's graph replays them: one
+ * snapshot at the current state, then the sweeps A..D of `reps` outer iterations (1..256)
+ * captured back to back in one CUDA graph (the snapshot's lagged coefficients and member masks
+ * serve every sweep), launched once untimed and once between two CUDA events on the handle's
+ * stream; ms[0] gets the mean milliseconds per sweep, the graph's kernel boundaries included.
+ * Changes phi like real smoothing does.  MG_ERR_STATE outside a step; MG_ERR_ARG for a bad
+ * level or reps, or another smoother.  Waits. */
+int mg_time_sweeps_graph(mg_handle h, int level, int reps, double *ms);
+
 /* Residual norm ||L(phi)||_2 of one grid function, with no device allocation.  The paper has no
  * counterpart: this serves callers that cannot allocate device memory when they need the norm,
  * such as code whose device memory is owned by a framework's pool or a running real-time loop

@@ -160,6 +160,7 @@ struct SolverBase {
     virtual cudaStream_t stream() const = 0;
     virtual int time_kernels(int level, int reps, double *ms) = 0;
     virtual int time_residuals(int level, int reps, double *ms) = 0;
+    virtual int time_sweeps_graph(int level, int reps, double *ms) = 0;
     virtual int autotune(int reps, int *out) = 0;
     virtual int set_shapes(const int *shapes) = 0;
     virtual int set_bottom(int enable) = 0;
@@ -1560,6 +1561,51 @@ struct Solver final : SolverBase {
         return MG_OK;
     }
 
+    // The sweeps of grid l as a V-cycle's graph replays them: one snapshot at the current state,
+    // then the sweeps A..D of `reps` outer iterations captured back to back in one graph (the
+    // snapshot's lagged coefficients and member masks serve every sweep), launched once
+    // untimed and once between two events; ms[0] = mean ms per sweep, kernel boundaries of the
+    // graph included.
+    int time_sweeps_graph(int l, int reps, double *ms) override {
+        if (l < 0 || l >= nlev || reps < 1 || reps > 256) return fail(MG_ERR_ARG, "level / reps");
+        if (!in_step) return fail(MG_ERR_STATE, "mg_time_sweeps_graph outside a step");
+        if (p.smoother == MG_SMOOTH_GSLINE || p.smoother == MG_SMOOTH_HS1)
+            return fail(MG_ERR_ARG, "mg_time_sweeps_graph times the Hybrid Smoother 2 sweeps");
+        const LevelView<T> v = view(l);
+        area_term(l, lv[l].u);
+        snapshot(l, v);
+        launches += area_launches(l) + 1;
+        CKL();
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int r = 0; r < reps; ++r)
+            for (int k = 0; k < 4; ++k) sweep(l, v, k, shape[l]);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        float t = 0;
+        e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        for (int it = 0; it < 2 && e == cudaSuccess; ++it) {   // the first launch warms up
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaGraphExecDestroy(ge);
+        if (e != cudaSuccess) return fail(MG_ERR_CUDA, cudaGetErrorString(e));
+        launches += 2LL * reps * smoother_launches(l);
+        ms[0] = (double)t / (4.0 * reps);
+        return MG_OK;
+    }
+
     // The residual kernels a V-cycle runs on grid l: [0] the residual norm (the tile kernel and
     // the final sum; the norm goes to a scratch slot), [1] the residual with full weighting into
     // grid l + 1 (-1 on the coarsest grid).  Writes grid l + 1's rhs, u and u0.
@@ -2488,6 +2534,10 @@ int mg_time_kernels(mg_handle h, int level, int reps, double *ms) {
 
 int mg_time_residuals(mg_handle h, int level, int reps, double *ms) {
     return (h && ms) ? h->s->time_residuals(level, reps, ms) : fail(MG_ERR_ARG, "NULL argument");
+}
+
+int mg_time_sweeps_graph(mg_handle h, int level, int reps, double *ms) {
+    return (h && ms) ? h->s->time_sweeps_graph(level, reps, ms) : fail(MG_ERR_ARG, "NULL argument");
 }
 
 const char *mg_strerror(int code) {

@@ -23,7 +23,7 @@ ERRORS = {0: "MG_OK", -1: "MG_ERR_ARG", -2: "MG_ERR_NAN", -3: "MG_ERR_CUDA", -4:
 EXPORTS = ["mg_default_params", "mg_setup", "mg_reset", "mg_begin_step", "mg_vcycle", "mg_end_step",
            "mg_solve_step", "mg_solve", "mg_mask", "mg_get_phi", "mg_set_phi", "mg_set_regions",
            "mg_get_level", "mg_get_stats", "mg_set_wait_limit", "mg_inject_divergence", "mg_debug_status", "mg_debug_selftest", "mg_segment_host", "mg_segment_host_release", "mg_get_stream", "mg_destroy",
-           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_time_residuals", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_set_cluster_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
+           "mg_strerror", "mg_last_error", "mg_time_kernels", "mg_time_residuals", "mg_time_sweeps_graph", "mg_residual_norm_noalloc", "mg_autotune", "mg_set_tile_shapes", "mg_set_bottom_kernel", "mg_set_bottom_level", "mg_set_cluster_level", "mg_energy", "mg_aos", "mg_set_learned", "mg_set_omega", "mg_learned_nparam",
            "mg_trainer_create", "mg_trainer_record", "mg_trainer_load", "mg_trainer_count", "mg_trainer_set_loss", "mg_trainer_grad",
            "mg_trainer_train", "mg_trainer_get", "mg_trainer_destroy",
            "mg_batch_setup", "mg_batch_solve_step", "mg_batch_autotune", "mg_batch_handle",
@@ -120,6 +120,7 @@ def lib():
             "mg_get_stream": ([vp], vp),
             "mg_time_kernels": ([vp, i, i, D], i),
             "mg_time_residuals": ([vp, i, i, D], i),
+            "mg_time_sweeps_graph": ([vp, i, i, D], i),
             "mg_residual_norm_noalloc": ([vp, vp, vp, i, i, P, D, vp], i),
             "mg_autotune": ([vp, i, C.POINTER(i)], i),
             "mg_set_tile_shapes": ([vp, C.POINTER(i)], i),
@@ -381,6 +382,13 @@ class Solver:
         out = (C.c_double * 2)()
         _check(lib().mg_time_residuals(self._h, level, reps, out), "mg_time_residuals")
         return list(out)
+
+    def time_sweeps_graph(self, level=0, reps=8):
+        """Mean ms per Hybrid Smoother 2 sweep on `level`, the sweeps of `reps` outer iterations
+        replayed from one CUDA graph (mg_time_sweeps_graph)."""
+        out = (C.c_double * 1)()
+        _check(lib().mg_time_sweeps_graph(self._h, level, reps, out), "mg_time_sweeps_graph")
+        return out[0]
 
     def set_wait_limit(self, rounds):
         """Bound of the fused sweep's device-side waits (mg_set_wait_limit); 0 gives up at once."""

@@ -785,6 +785,24 @@ def test_time_residuals_reports_the_v_cycle_residual_kernels(segmg):
     assert rho <= 1e-6
 
 
+def test_time_sweeps_graph_times_the_replayed_sweeps(segmg):
+    img, mk, _ = synth.ellipses(256, 200, 6, (20, 80), 5, 0.05, 4)
+    s, p = gpu_solver(segmg, img, mk, levels=5)
+    with pytest.raises(segmg.SegmgError) as e:
+        s.time_sweeps_graph(0, 2)
+    assert e.value.code == -8          # outside a step
+    s.begin_step()
+    for l in range(p.levels):
+        assert s.time_sweeps_graph(l, 2) > 0
+    for level, reps in ((0, 0), (0, 257), (p.levels, 1)):
+        with pytest.raises(segmg.SegmgError):
+            s.time_sweeps_graph(level, reps)
+    s.end_step()
+    # the timing runs leave the handle usable: a fresh step still converges
+    cyc, rho = s.solve_step(1e-6, 60)
+    assert rho <= 1e-6
+
+
 def test_rada_chen_fp32_step_matches_oracle(segmg):
     # the Rada-Chen model in FP32 storage: the area term on every grid, the FAS right-hand side
     # completed by the coarse grids' first snapshots (the interpolation keeps its own launch for
